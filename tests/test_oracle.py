@@ -293,3 +293,71 @@ def test_kernel_discrepancy_shrinks_with_spacing(oracle):
         assert abs(out[25][q] - 1) < 0.3
         assert abs(out[25][q] - 1) < 0.7 * abs(out[13][q] - 1)
     assert out[13][1] > 0.3 and out[25][1] > 0.3
+
+
+def test_spherical_uniform_slowness_kernel(oracle):
+    """Spherical grid at 60 deg latitude (cos(theta) far from 1, so metric and area factors
+    matter): in a homogeneous medium T = s * chord exactly, so a uniform relative change of s
+    changes chi by sum_m R_m T_m; Eq. 9 with Eq. 6 must reproduce it."""
+    g = I.GridSpec(25, 25, 25, 0.0, 30.0, 60.0, 60.25, 10.0, 10.5)
+    gd = g.as_dict()
+    s, z = np.full(g.shape, 1 / 6.0), np.zeros(g.shape)
+    src = np.array([24.0, 60.05, 10.1])
+    rec = np.array([[0.0, 60.2, 10.4], [0.0, 60.18, 10.15], [0.0, 60.08, 10.42]])
+    data = dict(abs_rec=np.arange(3), abs_tobs=np.array([3.0, 3.1, 2.9]), abs_w=np.ones(3),
+                cs_m=np.array([0]), cs_i=np.array([2]), cs_dtobs=np.array([0.05]),
+                cs_w=np.ones(1))
+    r = oracle.solve_source(gd, s, z, z, src, rec, data, tol_fwd=1e-12, tol_adj=1e-12)
+    K = [np.zeros(g.shape) for _ in range(3)]
+    oracle.kernel_add(gd, s, r["T"], r["P"], *K)
+    chord = np.linalg.norm(_cart(g, rec) - _cart(g, src)[0], axis=-1)
+    pred = np.sum(K[0] * oracle.node_volumes(gd))
+    assert pred / np.sum(r["R"] * chord / 6.0) == pytest.approx(1.0, abs=0.06)
+
+
+@pytest.mark.parametrize("eta0", [0.1, -0.08])
+def test_adjoint_follows_straight_anisotropic_ray(oracle, eta0):
+    """Eq. 5 transports the adjoint source along -M grad T. In a homogeneous anisotropic
+    flat medium M grad T is parallel to x - x_s, so the adjoint field of one receiver is
+    centred on the straight segment from the receiver to the source at every depth."""
+    g = I.GridSpec(31, 41, 41, 0.0, 15.0, 0.0, 0.2, 0.0, 0.2, flat=1)
+    gd = g.as_dict()
+    s, xi, eta = np.full(g.shape, 1 / 6.0), np.zeros(g.shape), np.full(g.shape, eta0)
+    src, rec = np.array([14.0, 0.05, 0.06]), np.array([[0.0, 0.15, 0.14]])
+    _, T, _, _, _ = oracle.forward(gd, s, xi, eta, src, 1e-12, 1000)
+    P, _, conv, _ = oracle.adjoint(gd, T, xi, eta, src, rec, np.array([1.0]), 1e-12, 1000)
+    assert conv
+    depth, lat, lon = g.axes()
+    cell = lat[1] - lat[0]
+    for i in (8, 15, 22):
+        w = P[i].sum()
+        ct, cp = (P[i].sum(1) * lat).sum() / w, (P[i].sum(0) * lon).sum() / w
+        f = (depth[i] - rec[0, 0]) / (src[0] - rec[0, 0])
+        assert abs(ct - (rec[0, 1] + f * (src[1] - rec[0, 1]))) < 0.75 * cell
+        assert abs(cp - (rec[0, 2] + f * (src[2] - rec[0, 2]))) < 0.75 * cell
+
+
+def test_anisotropic_linear_gradient_first_order(oracle):
+    """Constant M with velocity linear in x: the substitution y = M^-1/2 x makes the
+    equation isotropic with velocity still linear, so T = arccosh(1 + |A G|^2 q /
+    (2 v v_s)) / |A G| with q = D^T M^-1 D and A = M^1/2. First-order convergence."""
+    xi0, eta0 = 0.04, -0.03
+    M = np.array([[1, 0, 0], [0, 1 - 2 * xi0, 2 * eta0], [0, 2 * eta0, 1 + 2 * xi0]])
+    w_, V = np.linalg.eigh(M)
+    A = V @ np.diag(np.sqrt(w_)) @ V.T
+    errs = []
+    for n in (11, 21, 41):
+        g = I.GridSpec(n, n, n, 0.0, 30.0, 0.0, 0.27, 0.0, 0.27, flat=1)
+        X = _cart(g, _node_points(g))
+        src = np.array([15.0, 0.135, 0.135])
+        D = X - _cart(g, src)[0]
+        Gv = np.array([-0.05, 0.01, 0.02])
+        v = 6.0 + D @ Gv
+        _, T, _, conv, _ = oracle.forward(g.as_dict(), 1.0 / v, np.full(g.shape, xi0),
+                                          np.full(g.shape, eta0), src, 1e-10, 1000)
+        AG = np.linalg.norm(A @ Gv)
+        q = np.einsum("...a,ab,...b->...", D, np.linalg.inv(M), D)
+        exact = np.arccosh(1 + AG ** 2 * q / (2 * v * 6.0)) / AG
+        assert conv
+        errs.append(np.abs(T - exact).max())
+    assert np.log2(errs[0] / errs[1]) >= 0.8 and np.log2(errs[1] / errs[2]) >= 0.8
