@@ -1,0 +1,157 @@
+/*
+ * tt.h — C ABI of the GB300 adjoint-state traveltime tomography library (libttgb.so).
+ *
+ * The library computes, for a batch of seismic sources on one spherical grid, the hot path
+ * of Eikonal-based adjoint-state traveltime tomography (TomoATT, arXiv 2412.00031):
+ *   tt_forward  factored fast-sweeping solve of the anisotropic Eikonal equation (Eq. "4"
+ *               of Sec. 2.1, with T = T0 * tau, Sec. 3.1), hyperplane-parallel (Sec. 3.4)
+ *   tt_misfit   receiver traveltimes, misfits chi_t and chi_cs (Eqs. 2-3) and adjoint
+ *               sources R = dchi/dT (Eqs. A1-A3)
+ *   tt_adjoint  upwind fast-sweeping solve of the adjoint equation (Eq. 5)
+ *   tt_kernel   FP64 accumulation of the sensitivity kernels K_s, K_xi, K_eta (Eqs. 6-8)
+ *
+ * Conventions shared by every call:
+ *  - Grid: n_r x n_t x n_p nodes, uniform in radius r (index i, i = 0 is the deepest
+ *    layer), latitude theta (index j) and longitude phi (index k). A scalar field is stored
+ *    [n_r][n_t][n_p] with k fastest. r = earth_radius_km - depth.
+ *  - Batched fields (tau, T, P) hold one value per node and source, stored node-major with
+ *    the source index fastest: element (node n, source b) is at n * n_src + b. Consecutive
+ *    GPU lanes then read consecutive sources of one node.
+ *  - dtype TT_F32 or TT_F64 selects float or double for every model and batched field of a
+ *    call. Misfit quantities, adjoint sources and kernels are always double.
+ *  - Pointers named d_* are device pointers; h_* are host pointers. The caller allocates
+ *    and frees every buffer it passes; the library never frees caller memory. The context
+ *    owns only its workspace (schedules, tables, per-source state, barrier words).
+ *  - Calls are issued on the context's CUDA stream. A call returns after its kernels are
+ *    enqueued, except where noted: tt_forward and tt_adjoint wait for their iteration
+ *    counts (one small device-to-host copy) to report convergence.
+ *  - Errors are returned as tt_status; tt_last_error gives a one-line message. No call
+ *    throws, aborts or traps. After TT_ECUDA the context should be destroyed.
+ *  - One context per host thread; a context is not thread-safe.
+ */
+#ifndef TT_H
+#define TT_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TT_API_VERSION 1
+#define TT_MAX_BATCH 4096 /* sources per forward/adjoint call */
+#define TT_MAX_DIM 1024   /* nodes per axis */
+
+typedef enum {
+    TT_OK = 0,
+    TT_EINVAL = 1,         /* invalid argument: sizes, positions, model values (see each call) */
+    TT_ENOTCONVERGED = 2,  /* some source reached max_iter; outputs hold the last iterate */
+    TT_ECUDA = 3,          /* a CUDA runtime call failed */
+    TT_ETIMEOUT = 4,       /* a device-side wait exceeded opts.spin_limit_ns; outputs undefined */
+    TT_ENOMEM = 5          /* workspace allocation failed */
+} tt_status;
+
+typedef enum { TT_F32 = 0, TT_F64 = 1 } tt_dtype;
+typedef enum { TT_GEOM_SPHERICAL = 0, TT_GEOM_FLAT = 1 } tt_geometry;
+
+/* Study region (Sec. 2.1 problem statement; Sec. 4 for the spherical parameterisation).
+ * TT_GEOM_FLAT is a Cartesian test geometry: theta and phi become lengths R_E*theta and
+ * R_E*phi and the metric factors r and r cos(theta) are replaced by R_E. */
+typedef struct {
+    int n_r, n_t, n_p;            /* nodes per axis, 4 .. TT_MAX_DIM */
+    double depth_min_km, depth_max_km;
+    double lat_min_deg, lat_max_deg;
+    double lon_min_deg, lon_max_deg;
+    double earth_radius_km;       /* 6371 for the Earth */
+    int geometry;                 /* tt_geometry */
+} tt_grid;
+
+/* Model: slowness s (s/km, > 0) and azimuthal anisotropy xi, eta (Eq. "4"; the matrix M is
+ * positive definite only for xi^2 + eta^2 < 1/4). Device arrays [n_r][n_t][n_p]. */
+typedef struct {
+    const void *d_s, *d_xi, *d_eta;
+    int dtype;                    /* tt_dtype of the three arrays */
+} tt_model;
+
+typedef struct {
+    double depth_km, lat_deg, lon_deg;
+} tt_point;
+
+/* Observations of a batch of n_src sources at a global list of n_rec receivers
+ * (Eqs. 2-3). Absolute times: for source b, records abs_off[b] .. abs_off[b+1]-1, each a
+ * receiver index, an observed time and a weight w_{n|m}. Common-source differential times:
+ * for source b, unordered pairs cs_off[b] .. cs_off[b+1]-1, each (m, i, dT_obs, w) meaning
+ * T(x_m) - T(x_i) observed as dT_obs with weight w; an unordered pair stands for the two
+ * ordered terms of Eq. 3 with weight w/2 each. alpha and beta weight chi_t and chi_cs
+ * (Eq. 1). Receiver positions are host memory; every other array is device memory. */
+typedef struct {
+    int n_src, n_rec;
+    const tt_point *h_rec;
+    const int *d_abs_off, *d_abs_rec;
+    const double *d_abs_tobs, *d_abs_w;
+    const int *d_cs_off, *d_cs_m, *d_cs_i;
+    const double *d_cs_dtobs, *d_cs_w;
+    double alpha, beta;
+} tt_data;
+
+typedef struct {
+    double tol_fwd;         /* stop when the largest |tau change| of one iteration < tol_fwd */
+    double tol_adj;         /* stop when the largest |P change| <= tol_adj * max |P| */
+    int max_iter_fwd, max_iter_adj;
+    int init;               /* tt_forward: 0 = start from tau = 1, 1 = start from the tau passed in */
+    long long spin_limit_ns;/* bound on every device-side wait; 0 = 2 s */
+    int launch_blocks;      /* persistent sweep launch: 0 = automatic, else at most this many
+                               blocks (results do not depend on it) */
+} tt_opts;
+
+typedef struct tt_ctx tt_ctx;
+
+/* Fills opts with the defaults for dtype: tol_fwd 1e-6 (F32) / 1e-8 (F64), tol_adj the
+ * same, 500 iterations, init 0, spin limit 2 s. */
+void tt_default_opts(tt_opts *opts, int dtype);
+
+/* Creates a context for one grid on one CUDA stream (cudaStream_t passed as void*, NULL for
+ * the default stream) of the current device. Validates the grid (TT_EINVAL) and builds the
+ * hyperplane schedules and coordinate tables (TT_ENOMEM / TT_ECUDA on failure). */
+tt_status tt_ctx_create(tt_ctx **out, const tt_grid *grid, void *cuda_stream);
+void tt_ctx_destroy(tt_ctx *ctx);
+const char *tt_last_error(const tt_ctx *ctx);
+
+/* Forward solve (Eq. "4", Sec. 3.1) for n_src sources at h_src (host, inside the grid).
+ * d_tau: device [N][n_src] of the model's dtype, the factored traveltime tau; read as the
+ * starting value when opts->init = 1, always written. d_T: device [N][n_src], written with
+ * T = T0 * tau (may be NULL). h_iters: host [n_src], iterations taken per source (may be
+ * NULL). Each source stops on its own criterion; sweeps of converged sources are skipped.
+ * TT_EINVAL: bad sizes, a source outside the grid, s <= 0 or xi^2 + eta^2 >= 1/4 somewhere.
+ * Synchronises the stream once at the end. */
+tt_status tt_forward(tt_ctx *ctx, const tt_model *model, const tt_point *h_src, int n_src,
+                     void *d_tau, void *d_T, const tt_opts *opts, int *h_iters);
+
+/* Misfit (Eqs. 2-3) and adjoint sources (Eqs. A2-A3) of a batch. d_T: device [N][n_src]
+ * traveltimes from tt_forward, dtype as given. Outputs (device, double): d_Tr [n_src][n_rec]
+ * trilinearly interpolated receiver times, d_chi [n_src][2] (chi_t, chi_cs per source),
+ * d_R [n_src][n_rec] = alpha dchi_t/dT + beta dchi_cs/dT. Any output may be NULL except
+ * d_R. TT_EINVAL: receiver outside the grid, index out of range. */
+tt_status tt_misfit(tt_ctx *ctx, const void *d_T, int dtype, const tt_data *data,
+                    double *d_Tr, double *d_chi, double *d_R);
+
+/* Adjoint solve (Eq. 5) for the same n_src sources. d_T: the forward traveltimes; d_R:
+ * device double [n_src][n_rec] adjoint sources at the receivers h_rec (host, n_rec);
+ * d_P: device [N][n_src] output adjoint field (P = 0 on the 3x3x3 source set). xi and eta
+ * of the model enter the flux velocity -M grad T. h_iters as in tt_forward. */
+tt_status tt_adjoint(tt_ctx *ctx, const tt_model *model, const tt_point *h_src, int n_src,
+                     const void *d_T, int n_rec, const tt_point *h_rec, const double *d_R,
+                     void *d_P, const tt_opts *opts, int *h_iters);
+
+/* Kernel accumulation (Eqs. 6-8): for every node adds sum_b P s^2 to d_Ks,
+ * sum_b P ((d_theta T / r)^2 - (d_phi T / (r cos theta))^2) to d_Kxi and
+ * sum_b -2 P (d_theta T / r)(d_phi T / (r cos theta)) to d_Keta (device double [N], read
+ * and written; zero them before the first batch). The source sum runs in a fixed order, so
+ * the result is bitwise reproducible. */
+tt_status tt_kernel(tt_ctx *ctx, const tt_model *model, int n_src, const void *d_T,
+                    const void *d_P, double *d_Ks, double *d_Kxi, double *d_Keta);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,260 @@
+"""Python binding of libttgb, the GB300 adjoint-state traveltime tomography library.
+
+Argument marshalling only: every step runs in the CUDA kernels behind the C ABI declared in
+include/tt.h. Device arrays are torch CUDA tensors (PyTorch provides device memory and the
+stream); host arrays are numpy. The functions carry the C names:
+
+    ctx = tt_ctx_create(grid)                      # grid: dict / object with tt_grid fields
+    iters = tt_forward(ctx, model, src, tau, T)    # model = (s, xi, eta) CUDA tensors
+    tt_misfit(ctx, T, data, Tr, chi, R)            # data: DeviceData
+    iters = tt_adjoint(ctx, model, src, T, rec, R, P)
+    tt_kernel(ctx, model, T, P, Ks, Kxi, Keta)
+
+Batched fields (tau, T, P) are tensors of shape (n_r, n_t, n_p, n_src), i.e. node-major with
+the source index fastest, as the C ABI stores them. There is no CPU fallback: importing this
+module fails if libttgb.so has not been built.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libttgb.so")
+
+TT_OK, TT_EINVAL, TT_ENOTCONVERGED, TT_ECUDA, TT_ETIMEOUT, TT_ENOMEM = range(6)
+TT_F32, TT_F64 = 0, 1
+STATUS_NAMES = {0: "TT_OK", 1: "TT_EINVAL", 2: "TT_ENOTCONVERGED", 3: "TT_ECUDA",
+                4: "TT_ETIMEOUT", 5: "TT_ENOMEM"}
+TT_MAX_BATCH = 4096
+
+
+class TTGrid(C.Structure):
+    _fields_ = [("n_r", C.c_int), ("n_t", C.c_int), ("n_p", C.c_int),
+                ("depth_min_km", C.c_double), ("depth_max_km", C.c_double),
+                ("lat_min_deg", C.c_double), ("lat_max_deg", C.c_double),
+                ("lon_min_deg", C.c_double), ("lon_max_deg", C.c_double),
+                ("earth_radius_km", C.c_double), ("geometry", C.c_int)]
+
+
+class TTModel(C.Structure):
+    _fields_ = [("d_s", C.c_void_p), ("d_xi", C.c_void_p), ("d_eta", C.c_void_p),
+                ("dtype", C.c_int)]
+
+
+class TTPoint(C.Structure):
+    _fields_ = [("depth_km", C.c_double), ("lat_deg", C.c_double), ("lon_deg", C.c_double)]
+
+
+class TTData(C.Structure):
+    _fields_ = [("n_src", C.c_int), ("n_rec", C.c_int), ("h_rec", C.POINTER(TTPoint)),
+                ("d_abs_off", C.c_void_p), ("d_abs_rec", C.c_void_p),
+                ("d_abs_tobs", C.c_void_p), ("d_abs_w", C.c_void_p),
+                ("d_cs_off", C.c_void_p), ("d_cs_m", C.c_void_p), ("d_cs_i", C.c_void_p),
+                ("d_cs_dtobs", C.c_void_p), ("d_cs_w", C.c_void_p),
+                ("alpha", C.c_double), ("beta", C.c_double)]
+
+
+class TTOpts(C.Structure):
+    _fields_ = [("tol_fwd", C.c_double), ("tol_adj", C.c_double),
+                ("max_iter_fwd", C.c_int), ("max_iter_adj", C.c_int), ("init", C.c_int),
+                ("spin_limit_ns", C.c_longlong), ("launch_blocks", C.c_int)]
+
+
+EXPORTED = ["tt_default_opts", "tt_ctx_create", "tt_ctx_destroy", "tt_last_error",
+            "tt_forward", "tt_misfit", "tt_adjoint", "tt_kernel"]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libttgb.so is not built; run __graft_entry__.build() first")
+    L = C.CDLL(LIB_PATH)
+    L.tt_default_opts.argtypes = [C.POINTER(TTOpts), C.c_int]
+    L.tt_default_opts.restype = None
+    L.tt_ctx_create.argtypes = [C.POINTER(C.c_void_p), C.POINTER(TTGrid), C.c_void_p]
+    L.tt_ctx_destroy.argtypes = [C.c_void_p]
+    L.tt_ctx_destroy.restype = None
+    L.tt_last_error.argtypes = [C.c_void_p]
+    L.tt_last_error.restype = C.c_char_p
+    L.tt_forward.argtypes = [C.c_void_p, C.POINTER(TTModel), C.POINTER(TTPoint), C.c_int,
+                             C.c_void_p, C.c_void_p, C.POINTER(TTOpts), C.POINTER(C.c_int)]
+    L.tt_misfit.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.POINTER(TTData), C.c_void_p,
+                            C.c_void_p, C.c_void_p]
+    L.tt_adjoint.argtypes = [C.c_void_p, C.POINTER(TTModel), C.POINTER(TTPoint), C.c_int,
+                             C.c_void_p, C.c_int, C.POINTER(TTPoint), C.c_void_p, C.c_void_p,
+                             C.POINTER(TTOpts), C.POINTER(C.c_int)]
+    L.tt_kernel.argtypes = [C.c_void_p, C.POINTER(TTModel), C.c_int, C.c_void_p, C.c_void_p,
+                            C.c_void_p, C.c_void_p, C.c_void_p]
+    for name in ("tt_ctx_create", "tt_forward", "tt_misfit", "tt_adjoint", "tt_kernel"):
+        getattr(L, name).restype = C.c_int
+    return L
+
+
+lib = _load()
+
+
+class TTError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), message))
+        self.status = status
+
+
+def _check(ctx, status, allow=()):
+    if status != TT_OK and status not in allow:
+        msg = lib.tt_last_error(ctx.handle if ctx is not None else None)
+        raise TTError(status, msg.decode() if msg else "")
+    return status
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _dtype_code(t):
+    import torch
+    if t.dtype == torch.float32:
+        return TT_F32
+    if t.dtype == torch.float64:
+        return TT_F64
+    raise TypeError("fields must be float32 or float64, got %s" % t.dtype)
+
+
+def _points(pts):
+    pts = np.asarray(pts, dtype=np.float64).reshape(-1, 3)
+    arr = (TTPoint * len(pts))()
+    for q, p in enumerate(pts):
+        arr[q] = TTPoint(*p)
+    return arr, len(pts)
+
+
+def _cuda_ok(*tensors):
+    for t in tensors:
+        if t is not None and (not t.is_cuda or not t.is_contiguous()):
+            raise ValueError("device arguments must be contiguous CUDA tensors")
+
+
+def default_opts(dtype=TT_F32, **kw):
+    o = TTOpts()
+    lib.tt_default_opts(C.byref(o), dtype)
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+class Context:
+    """Owns a tt_ctx (one grid, one CUDA stream)."""
+
+    def __init__(self, handle, grid):
+        self.handle = handle
+        self.grid = grid
+
+    def close(self):
+        if self.handle:
+            lib.tt_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def make_grid(g):
+    get = (lambda k: g[k]) if isinstance(g, dict) else (lambda k: getattr(g, k))
+    return TTGrid(get("n_r"), get("n_t"), get("n_p"), get("depth_min_km"), get("depth_max_km"),
+                  get("lat_min_deg"), get("lat_max_deg"), get("lon_min_deg"), get("lon_max_deg"),
+                  get("earth_radius_km"), int(get("flat")))
+
+
+def tt_ctx_create(grid, stream=None):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    h = C.c_void_p()
+    G = make_grid(grid)
+    st = lib.tt_ctx_create(C.byref(h), C.byref(G), C.c_void_p(stream.cuda_stream))
+    if st != TT_OK:
+        raise TTError(st, "tt_ctx_create rejected the grid or failed to allocate")
+    return Context(h, G)
+
+
+def _model(model):
+    s, xi, eta = model
+    _cuda_ok(s, xi, eta)
+    return TTModel(_ptr(s), _ptr(xi), _ptr(eta), _dtype_code(s))
+
+
+def tt_forward(ctx, model, src, tau, T=None, opts=None, allow_unconverged=False):
+    """Forward solve; tau (in/out) and T have shape (n_r, n_t, n_p, n_src). Returns the
+    per-source iteration counts (numpy int32)."""
+    M = _model(model)
+    _cuda_ok(tau, T)
+    pts, n = _points(src)
+    if opts is None:
+        opts = default_opts(M.dtype)
+    iters = (C.c_int * n)()
+    st = lib.tt_forward(ctx.handle, C.byref(M), pts, n, _ptr(tau), _ptr(T), C.byref(opts), iters)
+    _check(ctx, st, (TT_ENOTCONVERGED,) if allow_unconverged else ())
+    return np.frombuffer(iters, dtype=np.int32).copy()
+
+
+class DeviceData:
+    """Observations on the device, in the layout of tt_data."""
+
+    def __init__(self, rec, abs_off, abs_rec, abs_tobs, abs_w, cs_off, cs_m, cs_i, cs_dtobs,
+                 cs_w, alpha=1.0, beta=1.0, device="cuda"):
+        import torch
+        i32 = lambda a: torch.as_tensor(np.asarray(a, dtype=np.int32), device=device)
+        f64 = lambda a: torch.as_tensor(np.asarray(a, dtype=np.float64), device=device)
+        self.rec = np.asarray(rec, dtype=np.float64).reshape(-1, 3)
+        self.abs_off, self.abs_rec = i32(abs_off), i32(abs_rec)
+        self.abs_tobs, self.abs_w = f64(abs_tobs), f64(abs_w)
+        self.cs_off, self.cs_m, self.cs_i = i32(cs_off), i32(cs_m), i32(cs_i)
+        self.cs_dtobs, self.cs_w = f64(cs_dtobs), f64(cs_w)
+        self.alpha, self.beta = float(alpha), float(beta)
+        self.n_src = len(abs_off) - 1
+        self.n_rec = len(self.rec)
+        self._pts, _ = _points(self.rec)
+
+    @classmethod
+    def from_workload(cls, w, alpha=1.0, beta=1.0, device="cuda"):
+        return cls(w.rec, w.abs_off, w.abs_rec, w.abs_tobs, w.abs_w, w.cs_off, w.cs_m, w.cs_i,
+                   w.cs_dtobs, w.cs_w, alpha, beta, device)
+
+    def c_struct(self):
+        return TTData(self.n_src, self.n_rec, self._pts, _ptr(self.abs_off), _ptr(self.abs_rec),
+                      _ptr(self.abs_tobs), _ptr(self.abs_w), _ptr(self.cs_off), _ptr(self.cs_m),
+                      _ptr(self.cs_i), _ptr(self.cs_dtobs), _ptr(self.cs_w), self.alpha,
+                      self.beta)
+
+
+def tt_misfit(ctx, T, data, Tr=None, chi=None, R=None):
+    """Receiver times, misfits and adjoint sources; Tr, chi, R are float64 CUDA tensors of
+    shape (n_src, n_rec), (n_src, 2), (n_src, n_rec)."""
+    _cuda_ok(T, Tr, chi, R)
+    D = data.c_struct()
+    _check(ctx, lib.tt_misfit(ctx.handle, _ptr(T), _dtype_code(T), C.byref(D), _ptr(Tr),
+                              _ptr(chi), _ptr(R)))
+
+
+def tt_adjoint(ctx, model, src, T, rec, R, P, opts=None, allow_unconverged=False):
+    M = _model(model)
+    _cuda_ok(T, R, P)
+    pts, n = _points(src)
+    rpts, nr = _points(rec)
+    if opts is None:
+        opts = default_opts(M.dtype)
+    iters = (C.c_int * n)()
+    st = lib.tt_adjoint(ctx.handle, C.byref(M), pts, n, _ptr(T), nr, rpts, _ptr(R), _ptr(P),
+                        C.byref(opts), iters)
+    _check(ctx, st, (TT_ENOTCONVERGED,) if allow_unconverged else ())
+    return np.frombuffer(iters, dtype=np.int32).copy()
+
+
+def tt_kernel(ctx, model, T, P, Ks, Kxi, Keta):
+    M = _model(model)
+    _cuda_ok(T, P, Ks, Kxi, Keta)
+    n_src = T.shape[-1]
+    _check(ctx, lib.tt_kernel(ctx.handle, C.byref(M), n_src, _ptr(T), _ptr(P), _ptr(Ks),
+                              _ptr(Kxi), _ptr(Keta)))

@@ -1,0 +1,499 @@
+// Set-up and non-sweep kernels of libttgb: per-source factor constants, per-node model
+// records, the T = T0 tau output, receiver interpolation tables, the misfit and adjoint
+// sources (Eqs. 2-3, A2-A3), the point-source term of Eq. 5 and the kernel accumulation
+// (Eqs. 6-8).
+#include <cuda_runtime.h>
+
+#include "tt_aux.h"
+
+namespace ttgb {
+
+namespace {
+
+template <typename F> __device__ inline double ld_model(const F *p, long long n) {
+    return (double)__ldg(p + n);
+}
+
+// Trilinear cell of a point (in fractional grid indices): base corner and 8 weights, corner
+// c = di*4 + dj*2 + dk.
+__device__ inline void cell_of(const GridC &g, double fr, double ft, double fp, int base[3],
+                               double w[8]) {
+    double f[3] = {fr, ft, fp};
+    int n[3] = {g.nr, g.nt, g.np};
+    double u[3];
+    for (int a = 0; a < 3; ++a) {
+        int i0 = (int)floor(f[a]);
+        i0 = i0 < 0 ? 0 : (i0 > n[a] - 2 ? n[a] - 2 : i0);
+        base[a] = i0;
+        u[a] = f[a] - i0;
+    }
+    for (int c = 0; c < 8; ++c) {
+        double wr = (c & 4) ? u[0] : 1.0 - u[0];
+        double wt = (c & 2) ? u[1] : 1.0 - u[1];
+        double wp = (c & 1) ? u[2] : 1.0 - u[2];
+        w[c] = wr * wt * wp;
+    }
+}
+
+__device__ inline long long corner_node(const GridC &g, const int base[3], int c) {
+    return node_index(g, base[0] + ((c >> 2) & 1), base[1] + ((c >> 1) & 1), base[2] + (c & 1));
+}
+
+__device__ inline void frac_of(const GridC &g, const PointD &p, double &fr, double &ft,
+                               double &fp) {
+    const double deg = 3.14159265358979323846 / 180.0;
+    fr = ((g.re - p.depth) - g.r0) / g.dr;
+    ft = (p.lat * deg - g.t0) / g.dt;
+    fp = (p.lon * deg - g.p0) / g.dp;
+}
+
+// One thread per source: interpolated (s0, xi0, eta0), M0^-1, frame sines, fixed set.
+template <typename F>
+__global__ void source_setup_kernel(GridC g, const F *s, const F *xi, const F *eta,
+                                    const PointD *pts, int n_src, SrcC *out) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n_src) return;
+    SrcC S;
+    frac_of(g, pts[b], S.fr, S.ft, S.fp);
+    int base[3];
+    double w[8];
+    cell_of(g, S.fr, S.ft, S.fp, base, w);
+    double s0 = 0, x0 = 0, e0 = 0;
+    for (int c = 0; c < 8; ++c) {
+        long long n = corner_node(g, base, c);
+        s0 += w[c] * ld_model(s, n);
+        x0 += w[c] * ld_model(xi, n);
+        e0 += w[c] * ld_model(eta, n);
+    }
+    double det = (1.0 - 2.0 * x0) * (1.0 + 2.0 * x0) - 4.0 * e0 * e0;
+    S.b11 = (1.0 + 2.0 * x0) / det;
+    S.b12 = -2.0 * e0 / det;
+    S.b22 = (1.0 - 2.0 * x0) / det;
+    S.s0 = s0;
+    S.inv_s0 = 1.0 / s0;
+    const double deg = 3.14159265358979323846 / 180.0;
+    S.sts = sin(pts[b].lat * deg);
+    S.cts = cos(pts[b].lat * deg);
+    S.ir = (int)floor(S.fr);
+    S.frr = S.fr - S.ir;
+    int n[3] = {g.nr, g.nt, g.np};
+    double f[3] = {S.fr, S.ft, S.fp};
+    int c3[3];
+    for (int a = 0; a < 3; ++a) {
+        int c = (int)floor(f[a] + 0.5);
+        c3[a] = c < 0 ? 0 : (c > n[a] - 1 ? n[a] - 1 : c);
+    }
+    S.ci = c3[0]; S.cj = c3[1]; S.ck = c3[2];
+    out[b] = S;
+}
+
+// Angle tables per (latitude row or longitude column, source): (sin d, 1 - cos d) with
+// d = (index - f_source) * spacing, or (R_E d, 0) in the flat geometry. Layout [row][source].
+template <typename F>
+__global__ void angle_table_kernel(GridC g, const SrcC *S, int n_src, int axis, Vec2<F> *tab) {
+    int n_rows = axis == 1 ? g.nt : g.np;
+    long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= (long long)n_rows * n_src) return;
+    int row = (int)(q / n_src), b = (int)(q % n_src);
+    double f = axis == 1 ? S[b].ft : S[b].fp;
+    double h = axis == 1 ? g.dt : g.dp;
+    double d = ((double)row - f) * h;
+    Vec2<F> v;
+    if (g.flat) {
+        v.x = (F)(g.re * d);
+        v.y = (F)0;
+    } else {
+        double sh = sin(0.5 * d);
+        v.x = (F)sin(d);
+        v.y = (F)(2.0 * sh * sh);
+    }
+    tab[q] = v;
+}
+
+// Per-node record of the forward sweep (s, xi, eta and the Lax-Friedrichs coefficients).
+template <typename F>
+__global__ void node_record_kernel(GridC g, const F *s, const F *xi, const F *eta,
+                                   const double *h2, const double *cost, NodeRec<F> *rec,
+                                   int *bad) {
+    long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= g.N) return;
+    int k = (int)(n % g.np);
+    long long t = n / g.np;
+    int j = (int)(t % g.nt);
+    int i = (int)(t / g.nt);
+    double sv = ld_model(s, n), xv = ld_model(xi, n), ev = ld_model(eta, n);
+    if (!(sv > 0.0) || !(xv * xv + ev * ev < 0.25)) atomicExch(bad, 1);
+    double er = 0.5 / g.dr;
+    double et = 0.5 / (g.dt * h2[i]);
+    double ep = 0.5 / (g.dp * h2[i] * cost[j]);
+    double kt = sqrt(fmax(1.0 - 2.0 * xv, 0.0)), kp = sqrt(fmax(1.0 + 2.0 * xv, 0.0));
+    NodeRec<F> R;
+    R.s = (F)sv; R.xi = (F)xv; R.eta = (F)ev;
+    R.ct = (F)(kt * et); R.cp = (F)(kp * ep);
+    R.invW = (F)(0.5 / (er + kt * et + kp * ep));
+    R.et = (F)et; R.ep = (F)ep;
+    rec[n] = R;
+}
+
+template <typename F>
+__global__ void fill_kernel(F *p, long long n, F v) {
+    long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < n) p[q] = v;
+}
+
+// tau = 1 on each source's 3x3x3 fixed set (Sec. 3.1: T = T0 there).
+template <typename F>
+__global__ void fix_set_kernel(GridC g, const SrcC *S, int n_src, F *tau) {
+    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n_src * 27) return;
+    int b = q / 27, c = q % 27;
+    int i = S[b].ci + c / 9 - 1, j = S[b].cj + (c / 3) % 3 - 1, k = S[b].ck + c % 3 - 1;
+    if (i < 0 || j < 0 || k < 0 || i >= g.nr || j >= g.nt || k >= g.np) return;
+    tau[node_index(g, i, j, k) * n_src + b] = (F)1;
+}
+
+// T = T0 tau at every (node, source).
+template <typename F>
+__global__ void traveltime_kernel(GridC g, int B, const SrcC *src, const Vec2<F> *tabT,
+                                  const Vec2<F> *tabP, const F *rad, const F *cost,
+                                  const F *sint, const F *tau, F *T) {
+    long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= g.N * B) return;
+    int b = (int)(q % B);
+    long long n = q / B;
+    int k = (int)(n % g.np);
+    long long t = n / g.np;
+    int j = (int)(t % g.nt);
+    int i = (int)(t / g.nt);
+    SrcReg<F> S = load_src<F>(src, b, g.dr);
+    F ur, ut, up;
+    F invT0 = factor_T0<F>(S, i, rad[i], cost[j], sint[j], tabT[(long long)j * B + b],
+                           tabP[(long long)k * B + b], g.flat != 0, ur, ut, up);
+    // invT0 is infinite only at a node that coincides with the source, where T0 = 0.
+    T[q] = isinf(invT0) ? (F)0 : tau[q] / invT0;
+}
+
+// Receiver cells: for receiver m, corner q = 8 m + c has node cq[q], trilinear weight wq[q].
+__global__ void receiver_setup_kernel(GridC g, const PointD *rec, int n_rec, long long *cq,
+                                      double *wq, int *bad) {
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= n_rec) return;
+    double fr, ft, fp;
+    frac_of(g, rec[m], fr, ft, fp);
+    const double eps = 1e-9;
+    if (!(fr >= -eps && fr <= g.nr - 1 + eps && ft >= -eps && ft <= g.nt - 1 + eps &&
+          fp >= -eps && fp <= g.np - 1 + eps))
+        atomicExch(bad, 1);
+    int base[3];
+    double w[8];
+    cell_of(g, fr, ft, fp, base, w);
+    for (int c = 0; c < 8; ++c) {
+        cq[8 * m + c] = corner_node(g, base, c);
+        wq[8 * m + c] = w[c];
+    }
+}
+
+// Chain of receiver corners sharing a node, in increasing corner order: head = smallest q.
+__global__ void corner_head_kernel(const long long *cq, int S, int *sidx) {
+    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < S) atomicMin(&sidx[cq[q]], q);
+}
+
+__global__ void corner_next_kernel(const long long *cq, int S, int *next) {
+    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= S) return;
+    int nx = kNone;
+    for (int r = q + 1; r < S; ++r)
+        if (cq[r] == cq[q]) { nx = r; break; }
+    next[q] = nx;
+}
+
+__global__ void corner_compact_kernel(const long long *cq, int S, const int *sidx, int *heads,
+                                      int *n_heads) {
+    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < S && sidx[cq[q]] == q) heads[atomicAdd(n_heads, 1)] = q;
+}
+
+__global__ void corner_relabel_kernel(const long long *cq, const int *heads, const int *n_heads,
+                                      int *sidx) {
+    int h = blockIdx.x * blockDim.x + threadIdx.x;
+    if (h < *n_heads) sidx[cq[heads[h]]] = h;
+}
+
+// J_c S_c of Eq. 5 at every node that holds a receiver corner, per source:
+// sum over the node's corners (in corner order) of R[b][m] w / (dr dt dp), in FP64.
+template <typename F>
+__global__ void point_source_kernel(const int *heads, const int *n_heads, const int *next,
+                                    const double *wq, const double *R, int n_rec, int B,
+                                    double inv_vol, F *JS) {
+    long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= (long long)(*n_heads) * B) return;
+    int h = (int)(q / B), b = (int)(q % B);
+    double acc = 0.0;
+    for (int c = heads[h]; c != kNone; c = next[c])
+        acc += R[(long long)b * n_rec + c / 8] * wq[c] * inv_vol;
+    JS[q] = (F)acc;
+}
+
+// Misfit of one source per warp. Lanes own receivers m = lane (mod 32); every record is
+// applied by the owner lanes in record order, so the adjoint sources are bitwise
+// reproducible. Dynamic shared memory: per warp, Tr[n_rec] and R[n_rec] in double.
+template <typename F>
+__global__ void misfit_kernel(int B, int n_rec, const F *T, const long long *cq,
+                              const double *wq, const int *abs_off, const int *abs_rec,
+                              const double *abs_tobs, const double *abs_w, const int *cs_off,
+                              const int *cs_m, const int *cs_i, const double *cs_dtobs,
+                              const double *cs_w, double alpha, double beta, double *Tr_out,
+                              double *chi_out, double *R_out, int *bad) {
+    extern __shared__ double sh[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int b = blockIdx.x * (blockDim.x >> 5) + warp;
+    if (b >= B) return;
+    double *Tr = sh + (size_t)warp * 2 * n_rec;
+    double *R = Tr + n_rec;
+    for (int m = lane; m < n_rec; m += 32) {
+        double acc = 0.0;
+        for (int c = 0; c < 8; ++c)
+            acc += wq[8 * m + c] * (double)T[cq[8 * m + c] * B + b];
+        Tr[m] = acc;
+        R[m] = 0.0;
+        if (Tr_out) Tr_out[(long long)b * n_rec + m] = acc;
+    }
+    __syncwarp();
+    double chi_t = 0.0, chi_cs = 0.0;
+    // absolute times, Eq. 2 / A2
+    const int a0 = abs_off[b], a1 = abs_off[b + 1];
+    for (int base = a0; base < a1; base += 32) {
+        int q = base + lane;
+        int m = -1;
+        double v = 0.0;
+        if (q < a1) {
+            m = abs_rec[q];
+            if (m < 0 || m >= n_rec) { atomicExch(bad, 1); m = -1; }
+            else {
+                double e = Tr[m] - abs_tobs[q];
+                chi_t += 0.5 * abs_w[q] * e * e;
+                v = alpha * abs_w[q] * e;
+            }
+        }
+        int cnt = min(32, a1 - base);
+        for (int l = 0; l < cnt; ++l) {
+            int ml = __shfl_sync(0xffffffffu, m, l);
+            double vl = __shfl_sync(0xffffffffu, v, l);
+            if (ml >= 0 && (ml & 31) == lane) R[ml] += vl;
+        }
+    }
+    // common-source pairs, Eq. 3 / A3
+    const int c0 = cs_off[b], c1 = cs_off[b + 1];
+    for (int base = c0; base < c1; base += 32) {
+        int q = base + lane;
+        int m = -1, i = -1;
+        double v = 0.0;
+        if (q < c1) {
+            m = cs_m[q];
+            i = cs_i[q];
+            if (m < 0 || m >= n_rec || i < 0 || i >= n_rec) { atomicExch(bad, 1); m = i = -1; }
+            else {
+                double e = (Tr[m] - Tr[i]) - cs_dtobs[q];
+                chi_cs += 0.5 * cs_w[q] * e * e;
+                v = beta * cs_w[q] * e;
+            }
+        }
+        int cnt = min(32, c1 - base);
+        for (int l = 0; l < cnt; ++l) {
+            int ml = __shfl_sync(0xffffffffu, m, l);
+            int il = __shfl_sync(0xffffffffu, i, l);
+            double vl = __shfl_sync(0xffffffffu, v, l);
+            if (ml >= 0 && (ml & 31) == lane) R[ml] += vl;
+            if (il >= 0 && (il & 31) == lane) R[il] -= vl;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        chi_t += __shfl_xor_sync(0xffffffffu, chi_t, o);
+        chi_cs += __shfl_xor_sync(0xffffffffu, chi_cs, o);
+    }
+    __syncwarp();
+    for (int m = lane; m < n_rec; m += 32) R_out[(long long)b * n_rec + m] = R[m];
+    if (lane == 0 && chi_out) {
+        chi_out[2 * b] = chi_t;
+        chi_out[2 * b + 1] = chi_cs;
+    }
+}
+
+// Kernels of Eqs. 6-8, one warp per node; lanes stride over the sources and the warp sum
+// runs in a fixed shuffle order.
+template <typename F>
+__global__ void kernel_accum_kernel(GridC g, int B, const F *s, const F *T, const F *P,
+                                    const double *h2, const double *cost, double *Ks,
+                                    double *Kxi, double *Keta) {
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const double idt = 1.0 / g.dt, idp = 1.0 / g.dp;
+    for (long long n = warp; n < g.N; n += nwarps) {
+        int k = (int)(n % g.np);
+        long long t = n / g.np;
+        int j = (int)(t % g.nt);
+        int i = (int)(t / g.nt);
+        const double ht = h2[i], hp = h2[i] * cost[j];
+        const long long st = (long long)g.np * B, sp = B;
+        double aP = 0, aX = 0, aE = 0;
+        for (int b = lane; b < B; b += 32) {
+            const long long x = n * B + b;
+            const double Tc = (double)T[x];
+            double gt, gp;
+            if (j == 0) gt = ((double)T[x + st] - Tc) * idt;
+            else if (j == g.nt - 1) gt = (Tc - (double)T[x - st]) * idt;
+            else gt = ((double)T[x + st] - (double)T[x - st]) * 0.5 * idt;
+            if (k == 0) gp = ((double)T[x + sp] - Tc) * idp;
+            else if (k == g.np - 1) gp = (Tc - (double)T[x - sp]) * idp;
+            else gp = ((double)T[x + sp] - (double)T[x - sp]) * 0.5 * idp;
+            gt /= ht;
+            gp /= hp;
+            const double p = (double)P[x];
+            aP += p;
+            aX += p * (gt * gt - gp * gp);
+            aE += -2.0 * p * gt * gp;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            aP += __shfl_xor_sync(0xffffffffu, aP, o);
+            aX += __shfl_xor_sync(0xffffffffu, aX, o);
+            aE += __shfl_xor_sync(0xffffffffu, aE, o);
+        }
+        if (lane == 0) {
+            const double sv = (double)s[n];
+            Ks[n] += sv * sv * aP;
+            Kxi[n] += aX;
+            Keta[n] += aE;
+        }
+    }
+}
+
+inline unsigned blocks_for(long long n, int threads) {
+    return (unsigned)((n + threads - 1) / threads);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------ host launchers
+
+template <typename F>
+cudaError_t run_source_setup(const GridC &g, const void *s, const void *xi, const void *eta,
+                             const PointD *d_pts, int n_src, SrcC *d_src, Vec2<F> *tabT,
+                             Vec2<F> *tabP, cudaStream_t st) {
+    source_setup_kernel<F><<<blocks_for(n_src, 128), 128, 0, st>>>(
+        g, (const F *)s, (const F *)xi, (const F *)eta, d_pts, n_src, d_src);
+    angle_table_kernel<F><<<blocks_for((long long)g.nt * n_src, 256), 256, 0, st>>>(
+        g, d_src, n_src, 1, tabT);
+    angle_table_kernel<F><<<blocks_for((long long)g.np * n_src, 256), 256, 0, st>>>(
+        g, d_src, n_src, 2, tabP);
+    return cudaGetLastError();
+}
+
+template <typename F>
+cudaError_t run_node_records(const GridC &g, const void *s, const void *xi, const void *eta,
+                             const double *h2, const double *cost, NodeRec<F> *rec, int *bad,
+                             cudaStream_t st) {
+    node_record_kernel<F><<<blocks_for(g.N, 256), 256, 0, st>>>(
+        g, (const F *)s, (const F *)xi, (const F *)eta, h2, cost, rec, bad);
+    return cudaGetLastError();
+}
+
+template <typename F>
+cudaError_t run_tau_init(const GridC &g, int n_src, const SrcC *d_src, F *tau, bool fill,
+                         cudaStream_t st) {
+    if (fill)
+        fill_kernel<F><<<blocks_for(g.N * n_src, 256), 256, 0, st>>>(tau, g.N * n_src, (F)1);
+    fix_set_kernel<F><<<blocks_for(27LL * n_src, 128), 128, 0, st>>>(g, d_src, n_src, tau);
+    return cudaGetLastError();
+}
+
+template <typename F>
+cudaError_t run_traveltime(const GridC &g, int B, const SrcC *src, const Vec2<F> *tabT,
+                           const Vec2<F> *tabP, const F *rad, const F *cost, const F *sint,
+                           const F *tau, F *T, cudaStream_t st) {
+    traveltime_kernel<F><<<blocks_for(g.N * B, 256), 256, 0, st>>>(g, B, src, tabT, tabP, rad,
+                                                                   cost, sint, tau, T);
+    return cudaGetLastError();
+}
+
+cudaError_t run_receiver_setup(const GridC &g, const PointD *d_rec, int n_rec, long long *cq,
+                               double *wq, int *bad, cudaStream_t st) {
+    receiver_setup_kernel<<<blocks_for(n_rec, 128), 128, 0, st>>>(g, d_rec, n_rec, cq, wq, bad);
+    return cudaGetLastError();
+}
+
+template <typename F>
+cudaError_t run_point_sources(const GridC &g, int n_rec, const long long *cq, const double *wq,
+                              int *sidx, int *next, int *heads, int *n_heads, const double *R,
+                              int B, F *JS, cudaStream_t st) {
+    const int S = 8 * n_rec;
+    cudaMemsetAsync(sidx, 0x7f, (size_t)g.N * sizeof(int), st);  // every entry = kNone
+    cudaMemsetAsync(n_heads, 0, sizeof(int), st);
+    corner_head_kernel<<<blocks_for(S, 256), 256, 0, st>>>(cq, S, sidx);
+    corner_next_kernel<<<blocks_for(S, 256), 256, 0, st>>>(cq, S, next);
+    corner_compact_kernel<<<blocks_for(S, 256), 256, 0, st>>>(cq, S, sidx, heads, n_heads);
+    corner_relabel_kernel<<<blocks_for(S, 256), 256, 0, st>>>(cq, heads, n_heads, sidx);
+    const double inv_vol = 1.0 / (g.dr * g.dt * g.dp);
+    point_source_kernel<F><<<blocks_for((long long)S * B, 256), 256, 0, st>>>(
+        heads, n_heads, next, wq, R, n_rec, B, inv_vol, JS);
+    return cudaGetLastError();
+}
+
+template <typename F>
+cudaError_t run_misfit(int B, int n_rec, const void *T, const long long *cq, const double *wq,
+                       const tt_data &d, double *Tr, double *chi, double *R, int *bad,
+                       cudaStream_t st) {
+    const int warps = 4;
+    size_t smem = (size_t)warps * 2 * n_rec * sizeof(double);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(misfit_kernel<F>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    misfit_kernel<F><<<blocks_for(B, warps), warps * 32, smem, st>>>(
+        B, n_rec, (const F *)T, cq, wq, d.d_abs_off, d.d_abs_rec, d.d_abs_tobs, d.d_abs_w,
+        d.d_cs_off, d.d_cs_m, d.d_cs_i, d.d_cs_dtobs, d.d_cs_w, d.alpha, d.beta, Tr, chi, R, bad);
+    return cudaGetLastError();
+}
+
+template <typename F>
+cudaError_t run_kernel_accum(const GridC &g, int B, const void *s, const void *T, const void *P,
+                             const double *h2, const double *cost, double *Ks, double *Kxi,
+                             double *Keta, int n_sm, cudaStream_t st) {
+    long long warps = g.N;
+    long long cap = (long long)n_sm * 64;  // 64 warps per SM resident at most
+    unsigned blocks = (unsigned)((warps < cap ? warps : cap) * 32 / 256);
+    if (blocks == 0) blocks = 1;
+    kernel_accum_kernel<F><<<blocks, 256, 0, st>>>(g, B, (const F *)s, (const F *)T,
+                                                   (const F *)P, h2, cost, Ks, Kxi, Keta);
+    return cudaGetLastError();
+}
+
+#define TTGB_INST(F)                                                                           \
+    template cudaError_t run_source_setup<F>(const GridC &, const void *, const void *,        \
+                                             const void *, const PointD *, int, SrcC *,        \
+                                             Vec2<F> *, Vec2<F> *, cudaStream_t);              \
+    template cudaError_t run_node_records<F>(const GridC &, const void *, const void *,        \
+                                             const void *, const double *, const double *,     \
+                                             NodeRec<F> *, int *, cudaStream_t);               \
+    template cudaError_t run_tau_init<F>(const GridC &, int, const SrcC *, F *, bool,          \
+                                         cudaStream_t);                                        \
+    template cudaError_t run_traveltime<F>(const GridC &, int, const SrcC *, const Vec2<F> *,  \
+                                           const Vec2<F> *, const F *, const F *, const F *,   \
+                                           const F *, F *, cudaStream_t);                      \
+    template cudaError_t run_point_sources<F>(const GridC &, int, const long long *,           \
+                                              const double *, int *, int *, int *, int *,      \
+                                              const double *, int, F *, cudaStream_t);         \
+    template cudaError_t run_misfit<F>(int, int, const void *, const long long *,              \
+                                       const double *, const tt_data &, double *, double *,    \
+                                       double *, int *, cudaStream_t);                         \
+    template cudaError_t run_kernel_accum<F>(const GridC &, int, const void *, const void *,   \
+                                             const void *, const double *, const double *,     \
+                                             double *, double *, double *, int, cudaStream_t);
+TTGB_INST(float)
+TTGB_INST(double)
+#undef TTGB_INST
+
+}  // namespace ttgb

@@ -1,0 +1,45 @@
+// Host launchers of the set-up and non-sweep kernels (tt_aux.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "tt.h"
+#include "tt_common.cuh"
+
+namespace ttgb {
+
+struct PointD {  // same layout as tt_point
+    double depth, lat, lon;
+};
+
+template <typename F>
+cudaError_t run_source_setup(const GridC &g, const void *s, const void *xi, const void *eta,
+                             const PointD *d_pts, int n_src, SrcC *d_src, Vec2<F> *tabT,
+                             Vec2<F> *tabP, cudaStream_t st);
+template <typename F>
+cudaError_t run_node_records(const GridC &g, const void *s, const void *xi, const void *eta,
+                             const double *h2, const double *cost, NodeRec<F> *rec, int *bad,
+                             cudaStream_t st);
+template <typename F>
+cudaError_t run_tau_init(const GridC &g, int n_src, const SrcC *d_src, F *tau, bool fill,
+                         cudaStream_t st);
+template <typename F>
+cudaError_t run_traveltime(const GridC &g, int B, const SrcC *src, const Vec2<F> *tabT,
+                           const Vec2<F> *tabP, const F *rad, const F *cost, const F *sint,
+                           const F *tau, F *T, cudaStream_t st);
+cudaError_t run_receiver_setup(const GridC &g, const PointD *d_rec, int n_rec, long long *cq,
+                               double *wq, int *bad, cudaStream_t st);
+template <typename F>
+cudaError_t run_point_sources(const GridC &g, int n_rec, const long long *cq, const double *wq,
+                              int *sidx, int *next, int *heads, int *n_heads, const double *R,
+                              int B, F *JS, cudaStream_t st);
+template <typename F>
+cudaError_t run_misfit(int B, int n_rec, const void *T, const long long *cq, const double *wq,
+                       const tt_data &d, double *Tr, double *chi, double *R, int *bad,
+                       cudaStream_t st);
+template <typename F>
+cudaError_t run_kernel_accum(const GridC &g, int B, const void *s, const void *T, const void *P,
+                             const double *h2, const double *cost, double *Ks, double *Kxi,
+                             double *Keta, int n_sm, cudaStream_t st);
+
+}  // namespace ttgb

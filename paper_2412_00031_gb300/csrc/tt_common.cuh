@@ -1,0 +1,186 @@
+// Device-side building blocks shared by the CUDA kernels of libttgb: grid constants, the
+// per-source factor T0 (Sec. 3.1), the per-node model record and a bounded grid barrier.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ttgb {
+
+// Empty slot in integer index maps. A byte pattern, so that cudaMemset(p, 0x7f, n) fills a
+// map with it; larger than any index the library builds.
+constexpr int kNone = 0x7f7f7f7f;
+
+// Status word written by kernels (0 = ok). Values mirror tt_status.
+enum DevStatus : int { kDevOk = 0, kDevTimeout = 4, kDevBadIndex = 1 };
+
+// Uniform grid (r ascending from r0, theta = latitude, phi = longitude), Sec. 2.1.
+struct GridC {
+    int nr, nt, np;
+    int flat;
+    long long N;
+    double r0, dr, t0, dt, p0, dp, re;
+};
+
+__host__ __device__ inline long long node_index(const GridC &g, int i, int j, int k) {
+    return ((long long)i * g.nt + j) * g.np + k;
+}
+
+// Per-source constants of the multiplicative factor T0 = s0 sqrt(D^T M0^-1 D), D the offset
+// to the source in the source's local (up, north, east) frame, M0 = M(xi0, eta0) of Eq. "4".
+// Built once per call in FP64 by the source set-up kernel.
+struct SrcC {
+    double fr, ft, fp;     // fractional grid index of the source
+    double frr;            // fr - ir, so that i - fr = (i - ir) - frr without cancellation
+    double s0, inv_s0;
+    double b11, b12, b22;  // theta-phi block of M0^-1 (the r-r entry is 1)
+    double sts, cts;       // sin, cos of the source latitude
+    int ir;                // floor(fr)
+    int ci, cj, ck;        // node nearest the source: centre of the 3x3x3 fixed set
+};
+
+// Per-node model record of the forward sweep (shared by all sources of a batch):
+// s, xi, eta, and the Lax-Friedrichs coefficients c_t = sqrt(1-2xi) e_t,
+// c_p = sqrt(1+2xi) e_p, invW = 1 / (2 (e_r + c_t + c_p)), with e_d = 1 / (2 delta_d h_d).
+template <typename F> struct alignas(sizeof(F) * 8) NodeRec {
+    F s, xi, eta, ct, cp, invW, et, ep;
+};
+
+template <typename F> struct Vec2 { F x, y; };
+
+__device__ __forceinline__ bool in_fixed_set(int ci, int cj, int ck, int i, int j, int k) {
+    return abs(i - ci) <= 1 && abs(j - cj) <= 1 && abs(k - ck) <= 1;
+}
+
+// Per-source values held in registers by the sweep kernels.
+template <typename F> struct SrcReg {
+    F frr, dr, s0, inv_s0, b11, b12, b22, sts, cts;
+    int ir, ci, cj, ck;
+};
+
+template <typename F> __device__ __forceinline__ SrcReg<F> load_src(const SrcC *S, int b, double dr) {
+    SrcReg<F> r;
+    const SrcC &c = S[b];
+    r.frr = (F)c.frr; r.ir = c.ir; r.dr = (F)dr; r.s0 = (F)c.s0; r.inv_s0 = (F)c.inv_s0;
+    r.b11 = (F)c.b11; r.b12 = (F)c.b12; r.b22 = (F)c.b22;
+    r.sts = (F)c.sts; r.cts = (F)c.cts;
+    r.ci = c.ci; r.cj = c.cj; r.ck = c.ck;
+    return r;
+}
+
+__device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsqrt_(double x) { return rsqrt(x); }
+__device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+__device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+
+// T0 at node (i, j, k) for one source, returned as 1/T0 and u = p0 / T0, where p0 is the
+// gradient of T0 in the node's physical components (d_r, d_theta / r, d_phi / (r cos theta)).
+// Spherical geometry: with dth = theta - theta_s and dph = phi - phi_s,
+//   D_up    = (r - r_s) - r [(1 - cos dth) + cos th_s cos th (1 - cos dph)]
+//   D_north = r [sin dth + sin th_s cos th (1 - cos dph)]
+//   D_east  = r cos th sin dph
+// (no cancellation: the small angle terms come from tables built in FP64), and p0 is the
+// source-frame gradient s0^2 M0^-1 D / T0 rotated into the node frame by Q_ab = e_a . E_b.
+// tabT = (sin dth, 1 - cos dth) at the node's latitude, tabP = (sin dph, 1 - cos dph).
+// Flat geometry: tabT = (R_E dth, 0), tabP = (R_E dph, 0), D = (r - r_s, tabT.x, tabP.x), Q = I.
+template <typename F>
+__device__ __forceinline__ F factor_T0(const SrcReg<F> &S, int i, F r, F cth, F sth,
+                                       Vec2<F> tT, Vec2<F> tP, bool flat, F &ur, F &ut, F &up) {
+    F du = ((F)(i - S.ir) - S.frr) * S.dr;
+    F dn, de;
+    if (flat) {
+        dn = tT.x;
+        de = tP.x;
+    } else {
+        du = du - r * (tT.y + S.cts * cth * tP.y);
+        dn = r * (tT.x + S.sts * cth * tP.y);
+        de = r * cth * tP.x;
+    }
+    F wn = S.b11 * dn + S.b12 * de;
+    F we = S.b12 * dn + S.b22 * de;
+    F q = du * du + dn * wn + de * we;
+    F rho = rsqrt_(q);
+    F rho2 = rho * rho;
+    if (flat) {
+        ur = rho2 * du; ut = rho2 * wn; up = rho2 * we;
+    } else {
+        F omc = (F)1 - tT.y;
+        F Qrr = omc - S.cts * cth * tP.y, Qrt = tT.x + S.sts * cth * tP.y, Qrp = cth * tP.x;
+        F Qtr = -tT.x + sth * S.cts * tP.y, Qtt = omc - sth * S.sts * tP.y, Qtp = -sth * tP.x;
+        F Qpr = -S.cts * tP.x, Qpt = S.sts * tP.x, Qpp = (F)1 - tP.y;
+        ur = rho2 * (Qrr * du + Qrt * wn + Qrp * we);
+        ut = rho2 * (Qtr * du + Qtt * wn + Qtp * we);
+        up = rho2 * (Qpr * du + Qpt * wn + Qpp * we);
+    }
+    return rho * S.inv_s0;  // 1 / T0 = 1 / (s0 sqrt(q))
+}
+
+// ---------------------------------------------------------------------------------------
+// Grid-wide barrier for persistent cooperative launches. Every wait is bounded by a
+// deadline on the global nanosecond timer; on expiry the status word gets kDevTimeout and
+// the caller returns. All blocks eventually leave: a block that gave up never arrives
+// again, so the others' waits expire too.
+struct BarrierState {
+    unsigned int count;
+    unsigned int gen;
+    int status;
+    int pad;
+};
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned int ld_acquire(const unsigned int *p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(unsigned int *p, unsigned int v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ int ld_status(const int *p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Returns false when the barrier (or an earlier one in another block) timed out.
+__device__ __forceinline__ bool grid_barrier(BarrierState *bs, unsigned long long limit_ns) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int good = 1;
+        unsigned int gen = ld_acquire(&bs->gen);
+        __threadfence();
+        unsigned int arrived = atomicAdd(&bs->count, 1u);
+        if (arrived == gridDim.x - 1) {
+            atomicExch(&bs->count, 0u);
+            __threadfence();
+            st_release(&bs->gen, gen + 1);
+        } else {
+            unsigned long long t0 = global_ns();
+            unsigned int ns = 32;
+            while (ld_acquire(&bs->gen) == gen) {
+                if (global_ns() - t0 > limit_ns) {
+                    atomicExch(&bs->status, (int)kDevTimeout);
+                    good = 0;
+                    break;
+                }
+                __nanosleep(ns);
+                if (ns < 256) ns <<= 1;
+            }
+        }
+        __threadfence();
+        if (good && ld_status(&bs->status) != 0) good = 0;
+        ok = good;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+}  // namespace ttgb

@@ -1,0 +1,174 @@
+"""GPU path against the FP64 oracle, through the C ABI (needs a GB300)."""
+import numpy as np
+import pytest
+
+import tt_inputs as I
+from gpu_helpers import gpu_solve, oracle_solve, rel_l2, rel_linf, rounded_model, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tt():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2412_00031_gb300 as m
+    return m
+
+
+def test_homogeneous_41_fp64_is_closed_form(tt):
+    """41^3 spherical grid, Vp = 6 km/s, surface source: T = s * chord (FP64, 1e-12)."""
+    w = I.homogeneous_41()
+    out = gpu_solve(w, "f64", opts=tt.default_opts(tt.TT_F64, tol_fwd=1e-7, tol_adj=1e-7))
+    from test_oracle import _cart, _node_points
+    exact = np.linalg.norm(_cart(w.grid, _node_points(w.grid)) - _cart(w.grid, w.src[0])[0],
+                           axis=-1) / 6.0
+    assert out["iters_fwd"][0] == 1
+    assert rel_linf(out["T"][..., 0], exact) <= 1e-12
+    res, K = oracle_solve(w, tol=1e-7)
+    assert rel_l2(out["P"][..., 0], res[0]["P"]) <= 1e-9
+    for a, b in zip(out["K"], K):
+        assert rel_l2(a, b) <= 1e-9
+
+
+@pytest.mark.parametrize("seed,shape,flat", [(1, (13, 15, 17), 0), (2, (9, 21, 11), 0),
+                                              (3, (12, 11, 14), 1)])
+def test_small_fp64_matches_oracle(tt, seed, shape, flat):
+    """Ragged grids, several sources, anisotropic heterogeneous model: FP64 GPU = oracle up to
+    rounding order."""
+    w = I.small_case(seed, shape=shape, n_src=3, n_rec=6, flat=flat)
+    o = tt.default_opts(tt.TT_F64, tol_fwd=1e-12, tol_adj=1e-12, max_iter_fwd=2000,
+                        max_iter_adj=2000)
+    out = gpu_solve(w, "f64", opts=o)
+    res, K = oracle_solve(w, tol=1e-12)
+    for b, r in enumerate(res):
+        assert abs(int(out["iters_fwd"][b]) - r["iters_fwd"]) <= 1
+        assert rel_linf(out["T"][..., b], r["T"]) <= 1e-10
+        assert rel_linf(out["Tr"][b], r["Tr"]) <= 1e-10
+        assert out["chi"][b] == pytest.approx([r["chi_t"], r["chi_cs"]], rel=1e-8, abs=1e-12)
+        assert np.abs(out["R"][b] - r["R"]).max() <= 1e-8 * max(1.0, np.abs(r["R"]).max())
+        assert rel_l2(out["P"][..., b], r["P"]) <= 1e-8
+    for a, b in zip(out["K"], K):
+        assert rel_l2(a, b) <= 1e-8
+
+
+@pytest.mark.parametrize("seed,shape,flat", [(4, (13, 15, 17), 0), (5, (21, 19, 23), 0),
+                                              (6, (11, 13, 9), 1)])
+def test_small_fp32_within_tolerance(tt, seed, shape, flat):
+    """FP32 sweeps with FP64 reductions against the FP64 oracle: relative L-infinity T error
+    <= 1e-5 and relative L2 kernel error <= 1e-3."""
+    w = I.small_case(seed, shape=shape, n_src=4, n_rec=7, flat=flat)
+    out = gpu_solve(w, "f32")
+    res, K = oracle_solve(w, model=rounded_model(w, "f32"), tol=1e-10)
+    for b, r in enumerate(res):
+        assert rel_linf(out["T"][..., b], r["T"]) <= 1e-5
+        assert rel_l2(out["P"][..., b], r["P"]) <= 1e-3
+    for a, b in zip(out["K"], K):
+        assert rel_l2(a, b) <= 1e-3
+
+
+def test_batch_equals_single_sources_bitwise(tt):
+    """Each source's result does not depend on the rest of the batch (same arithmetic, same
+    hyperplane order, own convergence test)."""
+    w = I.small_case(7, shape=(14, 16, 15), n_src=5, n_rec=6)
+    full = gpu_solve(w, "f32")
+    for b in range(w.n_src):
+        one = gpu_solve(w.subset([b]), "f32")
+        assert one["iters_fwd"][0] == full["iters_fwd"][b]
+        assert np.array_equal(one["tau"][..., 0], full["tau"][..., b])
+        assert np.array_equal(one["P"][..., 0], full["P"][..., b])
+
+
+@pytest.mark.parametrize("blocks", [1, 3, 7])
+def test_launch_shape_does_not_change_bits(tt, blocks):
+    """A 7-point Gauss-Seidel sweep gives the same bits under every schedule that respects
+    the hyperplane order, whatever the number of blocks and slots."""
+    w = I.small_case(8, shape=(15, 13, 17), n_src=3, n_rec=5)
+    ref = gpu_solve(w, "f32")
+    o = tt.default_opts(tt.TT_F32, launch_blocks=blocks)
+    out = gpu_solve(w, "f32", opts=o)
+    assert np.array_equal(out["tau"], ref["tau"])
+    assert np.array_equal(out["P"], ref["P"])
+    for a, b in zip(out["K"], ref["K"]):
+        assert np.array_equal(a, b)
+
+
+def test_kernels_bitwise_reproducible(tt):
+    w = I.small_case(9, shape=(13, 13, 13), n_src=6, n_rec=6)
+    a = gpu_solve(w, "f32")
+    b = gpu_solve(w, "f32")
+    for x, y in zip(a["K"], b["K"]):
+        assert np.array_equal(x, y)
+    assert np.array_equal(a["R"], b["R"])
+
+
+def test_warm_start_from_converged_tau_takes_one_iteration(tt):
+    w = I.small_case(10, shape=(13, 14, 15), n_src=2, n_rec=5)
+    cold = gpu_solve(w, "f32", steps=("fwd",))
+    o = tt.default_opts(tt.TT_F32, init=1)
+    warm = gpu_solve(w, "f32", opts=o, steps=("fwd",), tau_init=cold["tau"])
+    assert (warm["iters_fwd"] <= 2).all()
+    assert rel_linf(warm["T"], cold["T"]) <= 1e-6
+
+
+# ------------------------------------------------------------------------- error paths
+
+def _ctx_and_model(tt, w, dt="f32"):
+    import torch
+    ctx = tt.tt_ctx_create(w.grid.as_dict())
+    d = torch.float32 if dt == "f32" else torch.float64
+    return ctx, tuple(to_dev(a, d) for a in (w.s, w.xi, w.eta))
+
+
+def test_invalid_inputs_are_rejected(tt):
+    import torch
+    w = I.small_case(11, shape=(9, 9, 9), n_src=1, n_rec=4)
+    ctx, model = _ctx_and_model(tt, w)
+    tau = torch.empty(w.grid.shape + (1,), device="cuda")
+    bad_src = np.array([[500.0, 0.05, 0.05]])
+    with pytest.raises(tt.TTError) as e:
+        tt.tt_forward(ctx, model, bad_src, tau)
+    assert e.value.status == tt.TT_EINVAL
+    xi_bad = model[1].clone()
+    xi_bad[3, 3, 3] = 0.6
+    with pytest.raises(tt.TTError) as e:
+        tt.tt_forward(ctx, (model[0], xi_bad, model[2]), w.src, tau)
+    assert e.value.status == tt.TT_EINVAL
+    s_bad = model[0].clone()
+    s_bad[1, 2, 3] = -1.0
+    with pytest.raises(tt.TTError) as e:
+        tt.tt_forward(ctx, (s_bad, model[1], model[2]), w.src, tau)
+    assert e.value.status == tt.TT_EINVAL
+    # the context is still usable
+    tt.tt_forward(ctx, model, w.src, tau)
+    ctx.close()
+
+
+def test_iteration_limit_reports_not_converged(tt):
+    import torch
+    w = I.small_case(12, shape=(11, 11, 11), n_src=2, n_rec=4)
+    ctx, model = _ctx_and_model(tt, w)
+    tau = torch.empty(w.grid.shape + (2,), device="cuda")
+    o = tt.default_opts(tt.TT_F32, max_iter_fwd=1)
+    with pytest.raises(tt.TTError) as e:
+        tt.tt_forward(ctx, model, w.src, tau, None, o)
+    assert e.value.status == tt.TT_ENOTCONVERGED
+    it = tt.tt_forward(ctx, model, w.src, tau, None, o, allow_unconverged=True)
+    assert (it == 1).all()
+    ctx.close()
+
+
+def test_device_wait_limit_returns_timeout(tt):
+    """A wait limit far below a barrier's real duration makes the persistent launch give up
+    with TT_ETIMEOUT; the kernel returns on its own and the context stays usable."""
+    import torch
+    w = I.small_case(13, shape=(40, 40, 40), n_src=64, n_rec=4)
+    ctx, model = _ctx_and_model(tt, w)
+    tau = torch.empty(w.grid.shape + (64,), device="cuda")
+    o = tt.default_opts(tt.TT_F32, spin_limit_ns=1)
+    with pytest.raises(tt.TTError) as e:
+        tt.tt_forward(ctx, model, w.src, tau, None, o)
+    assert e.value.status == tt.TT_ETIMEOUT
+    tt.tt_forward(ctx, model, w.src, tau)
+    ctx.close()
