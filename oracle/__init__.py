@@ -164,3 +164,25 @@ def solve_source(g, s, xi, eta, src, rec, data, alpha=1.0, beta=1.0, tol_fwd=1e-
     P, ita, ca, _ = adjoint(g, T, xi, eta, src, rec, R, tol_adj, max_iter)
     return dict(tau=tau, T=T, Tr=Tr, chi_t=chi_t, chi_cs=chi_cs, R=R, P=P, iters_fwd=itf,
                 iters_adj=ita, conv_fwd=cf, conv_adj=ca)
+
+
+def forward_sweeps(g, s, xi, eta, src, n_sweeps):
+    """n_sweeps forward sweeps from tau = 1 (CPU-baseline timing unit). Returns tau."""
+    G = make_grid(g)
+    s, ps = _f(s); xi, px = _f(xi); eta, pe = _f(eta)
+    tau = np.zeros((G.n_r, G.n_t, G.n_p))
+    lib().or_forward_sweeps(C.byref(G), ps, px, pe, Point(*src), C.c_int(n_sweeps),
+                            tau.ctypes.data_as(_dp))
+    return tau
+
+
+def adjoint_sweeps(g, T, xi, eta, src, rec, R, n_sweeps):
+    """n_sweeps adjoint sweeps from P = 0 (CPU-baseline timing unit). Returns P."""
+    G = make_grid(g)
+    T, pT = _f(T); xi, px = _f(xi); eta, pe = _f(eta)
+    arr, n = _points(rec)
+    R, pR = _f(R)
+    P = np.zeros((G.n_r, G.n_t, G.n_p))
+    lib().or_adjoint_sweeps(C.byref(G), pT, px, pe, Point(*src), C.c_int(n), arr, pR,
+                            C.c_int(n_sweeps), P.ctypes.data_as(_dp))
+    return P

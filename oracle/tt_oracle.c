@@ -540,32 +540,66 @@ static double adj_update(const geo *G, const source_factor *S, const double *T,
     return (src + in) / out;
 }
 
+/* One adjoint sweep in ordering o over every node (R9); returns the largest |change|. */
+static double adj_sweep(const geo *G, const source_factor *S, const double *T, const double *xi,
+                        const double *eta, double *P, const double *JS, int o)
+{
+    int dr = (o & 4) ? -1 : 1, dt = (o & 2) ? -1 : 1, dp = (o & 1) ? -1 : 1;
+    double err = 0.0;
+    for (int a = 0; a < G->nr; a++)
+        for (int bb = 0; bb < G->nt; bb++)
+            for (int cc = 0; cc < G->np; cc++) {
+                int i = swept(a, dr, 0, G->nr - 1);
+                int j = swept(bb, dt, 0, G->nt - 1);
+                int k = swept(cc, dp, 0, G->np - 1);
+                if (is_fixed(S, i, j, k)) continue;
+                long n = idx(G, i, j, k);
+                double v = adj_update(G, S, T, xi, eta, P, JS[n], i, j, k);
+                err = fmax(err, fabs(v - P[n]));
+                P[n] = v;
+            }
+    return err;
+}
+
+/* J_c S_c at every node: R_m spread with trilinear weights over the node volume
+ * J_c dr dt dp; the J_c cancels (R9). */
+static double *point_sources(const geo *G, int n_rec, const or_point *rec, const double *R)
+{
+    long N = (long)G->nr * G->nt * G->np;
+    double *JS = (double *)calloc((size_t)N, sizeof(double));
+    for (int m = 0; m < n_rec; m++) {
+        int b[3];
+        double w[8];
+        trilinear(G, rec[m], b, w);
+        for (int c = 0; c < 8; c++)
+            JS[idx(G, b[0] + ((c >> 2) & 1), b[1] + ((c >> 1) & 1), b[2] + (c & 1))] +=
+                R[m] * w[c] / (G->dr * G->dt * G->dp);
+    }
+    return JS;
+}
+
+/* The fixed set only needs the source position; the adjoint does not use T0, so the factor
+ * is built with unit slowness and isotropy. */
+static source_factor adjoint_source(const geo *G, or_point src)
+{
+    long N = (long)G->nr * G->nt * G->np;
+    double *ones = (double *)calloc((size_t)N, sizeof(double));
+    double *zeros = (double *)calloc((size_t)N, sizeof(double));
+    for (long q = 0; q < N; q++) ones[q] = 1.0;
+    source_factor S = make_source(G, ones, zeros, zeros, src);
+    free(ones);
+    free(zeros);
+    return S;
+}
+
 int or_adjoint(const or_grid *g, const double *T, const double *xi, const double *eta,
                or_point src, int n_rec, const or_point *rec, const double *R,
                double tol, int max_iter, double *P, int *conv, double *last_err)
 {
     geo G = make_geo(g);
     long N = (long)G.nr * G.nt * G.np;
-    /* The fixed set only needs the source position; s is not used by the adjoint, so the
-     * factor is built with unit slowness and isotropy (its T0 is never evaluated here). */
-    double *ones = (double *)calloc((size_t)N, sizeof(double));
-    double *zeros = (double *)calloc((size_t)N, sizeof(double));
-    for (long q = 0; q < N; q++) ones[q] = 1.0;
-    source_factor S = make_source(&G, ones, zeros, zeros, src);
-    free(ones);
-    free(zeros);
-
-    /* J_c S_c at every node: R_m spread with trilinear weights, over the node volume
-     * J_c dr dt dp; the J_c cancels (R9). */
-    double *JS = (double *)calloc((size_t)N, sizeof(double));
-    for (int m = 0; m < n_rec; m++) {
-        int b[3];
-        double w[8];
-        trilinear(&G, rec[m], b, w);
-        for (int c = 0; c < 8; c++)
-            JS[idx(&G, b[0] + ((c >> 2) & 1), b[1] + ((c >> 1) & 1), b[2] + (c & 1))] +=
-                R[m] * w[c] / (G.dr * G.dt * G.dp);
-    }
+    source_factor S = adjoint_source(&G, src);
+    double *JS = point_sources(&G, n_rec, rec, R);
 
     for (long q = 0; q < N; q++) P[q] = 0.0;
     int it = 0;
@@ -573,21 +607,7 @@ int or_adjoint(const or_grid *g, const double *T, const double *xi, const double
     *conv = 0;
     while (it < max_iter) {
         err = 0.0;
-        for (int o = 0; o < 8; o++) {
-            int dr = (o & 4) ? -1 : 1, dt = (o & 2) ? -1 : 1, dp = (o & 1) ? -1 : 1;
-            for (int a = 0; a < G.nr; a++)
-                for (int bb = 0; bb < G.nt; bb++)
-                    for (int cc = 0; cc < G.np; cc++) {
-                        int i = swept(a, dr, 0, G.nr - 1);
-                        int j = swept(bb, dt, 0, G.nt - 1);
-                        int k = swept(cc, dp, 0, G.np - 1);
-                        if (is_fixed(&S, i, j, k)) continue;
-                        long n = idx(&G, i, j, k);
-                        double v = adj_update(&G, &S, T, xi, eta, P, JS[n], i, j, k);
-                        err = fmax(err, fabs(v - P[n]));
-                        P[n] = v;
-                    }
-        }
+        for (int o = 0; o < 8; o++) err = fmax(err, adj_sweep(&G, &S, T, xi, eta, P, JS, o));
         it++;
         double pmax = 0.0;
         for (long q = 0; q < N; q++) pmax = fmax(pmax, fabs(P[q]));
@@ -602,13 +622,7 @@ double or_fixed_set_inflow(const or_grid *g, const double *T, const double *xi,
                            const double *eta, or_point src, const double *P)
 {
     geo G = make_geo(g);
-    long N = (long)G.nr * G.nt * G.np;
-    double *ones = (double *)calloc((size_t)N, sizeof(double));
-    double *zeros = (double *)calloc((size_t)N, sizeof(double));
-    for (long q = 0; q < N; q++) ones[q] = 1.0;
-    source_factor S = make_source(&G, ones, zeros, zeros, src);
-    free(ones);
-    free(zeros);
+    source_factor S = adjoint_source(&G, src);
     int n[3] = {G.nr, G.nt, G.np};
     double del[3] = {G.dr, G.dt, G.dp};
     double vol = G.dr * G.dt * G.dp, flux = 0.0;
@@ -670,4 +684,35 @@ void or_node_volumes(const or_grid *g, double *dV)
                 double J = h2_at(&G, r) * h3_at(&G, r, th);
                 dV[idx(&G, i, j, k)] = J * G.dr * G.dt * G.dp;
             }
+}
+
+/* ---------------------------------------------------------------- timing samples */
+
+/* n_sweeps forward sweeps (orderings 0, 1, ...) with face extrapolation, from tau = 1: the
+ * unit of work the CPU baseline times. */
+void or_forward_sweeps(const or_grid *g, const double *s, const double *xi, const double *eta,
+                       or_point src, int n_sweeps, double *tau)
+{
+    geo G = make_geo(g);
+    source_factor S = make_source(&G, s, xi, eta, src);
+    long N = (long)G.nr * G.nt * G.np;
+    for (long n = 0; n < N; n++) tau[n] = 1.0;
+    for (int q = 0; q < n_sweeps; q++) {
+        sweep_lex(&G, &S, s, xi, eta, tau, q % 8);
+        extrapolate_faces(&G, &S, tau);
+    }
+}
+
+/* n_sweeps adjoint sweeps from P = 0 (same unit of work for the adjoint). */
+void or_adjoint_sweeps(const or_grid *g, const double *T, const double *xi, const double *eta,
+                       or_point src, int n_rec, const or_point *rec, const double *R,
+                       int n_sweeps, double *P)
+{
+    geo G = make_geo(g);
+    long N = (long)G.nr * G.nt * G.np;
+    source_factor S = adjoint_source(&G, src);
+    double *JS = point_sources(&G, n_rec, rec, R);
+    for (long q = 0; q < N; q++) P[q] = 0.0;
+    for (int q = 0; q < n_sweeps; q++) adj_sweep(&G, &S, T, xi, eta, P, JS, q % 8);
+    free(JS);
 }

@@ -88,6 +88,14 @@ int or_forward_hyperplane(const or_grid *g, const double *s, const double *xi,
                           const double *tau_init, double *tau, double *T, int *conv,
                           double *last_err);
 
+/* Timing units of the CPU baseline: n_sweeps forward sweeps from tau = 1, or n_sweeps
+ * adjoint sweeps from P = 0 (orderings 0, 1, ... as in a solve). */
+void or_forward_sweeps(const or_grid *g, const double *s, const double *xi, const double *eta,
+                       or_point src, int n_sweeps, double *tau);
+void or_adjoint_sweeps(const or_grid *g, const double *T, const double *xi, const double *eta,
+                       or_point src, int n_rec, const or_point *rec, const double *R,
+                       int n_sweeps, double *P);
+
 #ifdef __cplusplus
 }
 #endif
