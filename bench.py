@@ -1,0 +1,420 @@
+"""Benchmark: forward + adjoint source-solves per second on one GB300.
+
+One step is one pass of the whole hot path over one batch of sources: the factored
+fast-sweeping forward solve of every source to convergence, receiver misfits and adjoint
+sources, the adjoint solve of every source to convergence and the FP64 accumulation of the
+sensitivity kernels. The default workload is the anisotropic batch: a 121 x 161 x 161
+spherical grid (depth 0-100 km, 3 x 4 deg), Vp 5 -> 8 km/s with a +-4 % checkerboard, xi
+and eta checkerboards of amplitude 0.04, 256 sources with 20-200 receivers each; FP32 sweeps
+with FP64 reductions; synthetic inputs (tt_inputs.anisotropic_batch).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank solves its own batch (sources are independent); timing
+is the maximum over ranks. Prints one JSON line on rank 0.
+
+--impl reference times the FP64 CPU oracle on the host cores instead (bounded samples of the
+same workload, scaled to the same metric).
+"""
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import tt_inputs as I  # noqa: E402
+
+METRIC = "forward+adjoint source-solves/s on 1 GB300 at 121×161×161; % HBM roofline"
+UNIT = "source-solves/s"
+FWD_BYTES_PER_UPDATE = 8      # FP32 tau read + write per (node, source) update
+FWD_BYTES_PER_NODE_SWEEP = 12  # s, xi, eta once per node per sweep (shared by the batch)
+ADJ_BYTES_PER_UPDATE = 12     # FP32 P read + write and T read per (node, source) update
+ADJ_BYTES_PER_NODE_SWEEP = 8  # xi, eta once per node per sweep
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def workload_config(w, n_gpus):
+    g = w.grid
+    return {"workload": "anisotropic batch %dx%dx%d (r x lat x lon), depth %g-%g km, "
+                        "%gx%g deg, %d sources, 20-200 receivers each"
+                        % (g.n_r, g.n_t, g.n_p, g.depth_min_km, g.depth_max_km,
+                           g.lat_max_deg - g.lat_min_deg, g.lon_max_deg - g.lon_min_deg, w.n_src),
+            "grid": [g.n_r, g.n_t, g.n_p], "n_src_per_gpu": w.n_src,
+            "receivers": int(len(w.rec)), "abs_records": int(len(w.abs_rec)),
+            "cs_pairs": int(len(w.cs_m)), "precision": "fp32 sweeps, fp64 misfit and kernels",
+            "tol_fwd": 1e-6, "tol_adj": 1e-6,
+            "l2": "inputs larger than L2 (tau, T and P are 3.2 GB each)",
+            "parallelism": "sources sharded across %d GPU(s)" % n_gpus}
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (SM clock, reasons)."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.idx = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+class GpuPath:
+    """Device buffers and one step of the hot path through the C ABI."""
+
+    def __init__(self, w, device):
+        import torch
+        import paper_2412_00031_gb300 as tt
+        self.tt, self.torch, self.w, self.dev = tt, torch, w, device
+        g = w.grid
+        B = w.n_src
+        f32 = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32), device=device)
+        self.model = (f32(w.s), f32(w.xi), f32(w.eta))
+        self.ctx = tt.tt_ctx_create(g.as_dict())
+        shape = g.shape + (B,)
+        self.tau = torch.empty(shape, dtype=torch.float32, device=device)
+        self.T = torch.empty_like(self.tau)
+        self.P = torch.empty_like(self.tau)
+        self.data = tt.DeviceData.from_workload(w, device=device)
+        nr = self.data.n_rec
+        self.R = torch.empty((B, nr), dtype=torch.float64, device=device)
+        self.chi = torch.empty((B, 2), dtype=torch.float64, device=device)
+        self.K = [torch.zeros(g.shape, dtype=torch.float64, device=device) for _ in range(3)]
+        self.opts = tt.default_opts(tt.TT_F32)
+        self.iters = []
+
+    def step(self):
+        tt = self.tt
+        for k in self.K:
+            k.zero_()
+        itf = tt.tt_forward(self.ctx, self.model, self.w.src, self.tau, self.T, self.opts)
+        tt.tt_misfit(self.ctx, self.T, self.data, None, self.chi, self.R)
+        ita = tt.tt_adjoint(self.ctx, self.model, self.w.src, self.T, self.w.rec, self.R,
+                            self.P, self.opts)
+        tt.tt_kernel(self.ctx, self.model, self.T, self.P, *self.K)
+        fs = tt.tt_get_stats(self.ctx, tt.TT_STATS_FORWARD)
+        as_ = tt.tt_get_stats(self.ctx, tt.TT_STATS_ADJOINT)
+        self.iters.append((itf, ita, fs, as_))
+
+    def launches(self):
+        return self.tt.tt_get_stats(self.ctx, self.tt.TT_STATS_FORWARD)["launches"]
+
+
+def run_e2e(gp, w, steps):
+    """Same metric through the public API with host inputs: every step copies the model and
+    the observations from pinned host memory and reads back the misfits and the kernels."""
+    torch = gp.torch
+    host = [torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).pin_memory()
+            for a in (w.s, w.xi, w.eta)]
+    d = gp.data
+    dev_data = [d.abs_off, d.abs_rec, d.abs_tobs, d.abs_w, d.cs_off, d.cs_m, d.cs_i, d.cs_dtobs,
+                d.cs_w]
+    host_data = [t.cpu().pin_memory() for t in dev_data]
+    out_chi = torch.empty(gp.chi.shape, dtype=torch.float64).pin_memory()
+    out_K = [torch.empty(k.shape, dtype=torch.float64).pin_memory() for k in gp.K]
+    h2d = sum(t.numel() * t.element_size() for t in host + host_data)
+    d2h = out_chi.numel() * 8 + sum(k.numel() * 8 for k in out_K)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        for dst, src in zip(gp.model, host):
+            dst.copy_(src, non_blocking=True)
+        for dst, src in zip(dev_data, host_data):
+            dst.copy_(src, non_blocking=True)
+        gp.step()
+        out_chi.copy_(gp.chi, non_blocking=True)
+        for dst, src in zip(out_K, gp.K):
+            dst.copy_(src, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    return ms, h2d, d2h
+
+
+def kernel_source_digest():
+    h = hashlib.sha256()
+    for name in ("tt_sweep.cu", "tt_common.cuh", "tt_internal.h"):
+        with open(os.path.join(ROOT, "paper_2412_00031_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(digest, updates_per_launch):
+    """DRAM bytes per launch of the forward sweep from the committed ncu summary, scaled by
+    node updates; None if the summary is missing or was taken on different kernel source."""
+    path = os.path.join(ROOT, "profiles", "fwd_sweep_kernel_anisotropic.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    m_d = re.search(r"kernel source digest:\s*`?([0-9a-f]{16})", text)
+    m_b = re.search(r"dram bytes per node update:\s*([0-9.eE+-]+)", text)
+    if not m_d or not m_b or m_d.group(1) != digest:
+        return None
+    return float(m_b.group(1)) * updates_per_launch
+
+
+def gpu_arm(args, rank, world):
+    import torch
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    w = I.anisotropic_batch(seed=I.SEED_BASE + 2 + rank, n_src=args.n_src)
+    gp = GpuPath(w, dev)
+    for _ in range(args.warmup):
+        gp.step()
+    gp.iters.clear()
+    dist_barrier(world)
+    torch.cuda.synchronize()
+    launches0 = gp.launches()
+    clocks = ClockSampler(dev.index if dev.index is not None else 0)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        gp.step()
+    e1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = gp.launches() - launches0
+    ms = e0.elapsed_time(e1) / args.steps
+    ms = dist_max(ms, world)
+    dist_barrier(world)
+
+    e2e_ms, h2d, d2h = run_e2e(gp, w, max(1, args.steps))
+    e2e_ms = dist_max(e2e_ms, world)
+
+    # roofline of the dominant kernel (forward sweep) and the adjoint sweep
+    hbm, peak_kind = peaks()
+    fwd = [s[2] for s in gp.iters]
+    adj = [s[3] for s in gp.iters]
+    f_ms = float(np.mean([s["sweep_ms"] for s in fwd]))
+    a_ms = float(np.mean([s["sweep_ms"] for s in adj]))
+    f_upd = float(np.mean([s["node_updates"] for s in fwd]))
+    f_sw = float(np.mean([s["node_sweeps"] for s in fwd]))
+    a_upd = float(np.mean([s["node_updates"] for s in adj]))
+    a_sw = float(np.mean([s["node_sweeps"] for s in adj]))
+    f_bytes = f_upd * FWD_BYTES_PER_UPDATE + f_sw * FWD_BYTES_PER_NODE_SWEEP
+    a_bytes = a_upd * ADJ_BYTES_PER_UPDATE + a_sw * ADJ_BYTES_PER_NODE_SWEEP
+    f_gbs = f_bytes / (f_ms * 1e-3) / 1e9
+    a_gbs = a_bytes / (a_ms * 1e-3) / 1e9
+    digest = kernel_source_digest()
+    traffic = profiled_traffic(digest, f_upd)
+    itf = np.concatenate([s[0] for s in gp.iters])
+    ita = np.concatenate([s[1] for s in gp.iters])
+    value = world * w.n_src / (ms * 1e-3)
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": workload_config(w, world),
+        "roofline": {"bound": "hbm", "kernel": "fwd_sweep_kernel<float>", "achieved": f_gbs,
+                     "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s", "frac": f_gbs / hbm,
+                     "traffic": traffic, "algorithmic_bytes_per_launch": f_bytes,
+                     "launch_ms": f_ms, "kernel_source_digest": digest},
+        "kernels": {
+            "fwd_sweep": {"ms": f_ms, "node_updates": f_upd, "GBps": f_gbs,
+                          "frac_hbm": f_gbs / hbm, "iters_mean": float(itf.mean()),
+                          "iters_max": int(itf.max())},
+            "adj_sweep": {"ms": a_ms, "node_updates": a_upd, "GBps": a_gbs,
+                          "frac_hbm": a_gbs / hbm, "iters_mean": float(ita.mean()),
+                          "iters_max": int(ita.max())},
+            "rest_ms": ms - f_ms - a_ms},
+        "e2e": {"value": world * w.n_src / (e2e_ms * 1e-3), "unit": UNIT,
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                "ms_per_step": e2e_ms},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    return result, w, (float(itf.mean()), float(ita.mean()))
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+
+def oracle_sample(w, n_threads, n_src_sample, sweeps=1):
+    """Times the FP64 oracle on the host cores: each thread runs `sweeps` forward sweeps and
+    `sweeps` adjoint sweeps of one source of the workload. Returns seconds per forward and
+    adjoint (node, source) update, per thread, and the threads used."""
+    import oracle as O
+    g = w.grid.as_dict()
+    O.lib()
+    srcs = list(range(min(n_src_sample, w.n_src)))
+    n_int = (w.grid.n_r - 2) * (w.grid.n_t - 2) * (w.grid.n_p - 2)
+    n_all = w.grid.n_nodes
+    T0 = O.T0(g, w.s, w.xi, w.eta, w.src[0])[0]
+    R = np.zeros(len(w.rec))
+    d = w.source_data(0)
+    R[d["abs_rec"]] = 0.1
+    times = {}
+
+    def run(kind):
+        def work(b):
+            if kind == "fwd":
+                O.forward_sweeps(g, w.s, w.xi, w.eta, w.src[b], sweeps)
+            else:
+                O.adjoint_sweeps(g, T0, w.xi, w.eta, w.src[b], w.rec, R, sweeps)
+        ths = [threading.Thread(target=work, args=(b,)) for b in srcs[:n_threads]]
+        t0 = time.perf_counter()
+        for t in ths:
+            t.start()
+        for t in ths:
+            t.join()
+        times[kind] = time.perf_counter() - t0
+
+    run("fwd")
+    run("adj")
+    nth = min(n_threads, len(srcs))
+    t_fu = times["fwd"] / (sweeps * n_int)   # wall per update per thread (threads in parallel)
+    t_au = times["adj"] / (sweeps * n_all)
+    return t_fu, t_au, nth, times
+
+
+def cpu_baseline(w, iters_f, iters_a, cores):
+    t_fu, t_au, nth, times = oracle_sample(w, cores, cores)
+    n_int = (w.grid.n_r - 2) * (w.grid.n_t - 2) * (w.grid.n_p - 2)
+    per_solve = 8 * n_int * iters_f * t_fu + 8 * w.grid.n_nodes * iters_a * t_au
+    value = nth / per_solve
+    return {"value": value, "unit": UNIT, "cores": nth, "kind": "oracle",
+            "sample": "FP64 oracle, %d threads each running 1 forward and 1 adjoint sweep of "
+                      "one source on the 121x161x161 grid (%.1f s + %.1f s wall); scaled to a "
+                      "solve with %.1f forward and %.1f adjoint iterations (the GPU run's means)"
+                      % (nth, times["fwd"], times["adj"], iters_f, iters_a)}
+
+
+def reference_arm(args):
+    """The oracle as the reference implementation: each step is a bounded sample."""
+    w = I.anisotropic_batch(n_src=args.n_src)
+    cores = os.cpu_count() or 1
+    # iteration counts: FP32 sweeps of this workload converge in about this many iterations
+    # (measured by the GPU arm); the oracle would need at least as many at its FP64 tolerance
+    iters_f, iters_a = args.ref_iters_fwd, args.ref_iters_adj
+    vals, walls = [], []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        cb = cpu_baseline(w, iters_f, iters_a, cores)
+        walls.append(time.perf_counter() - t0)
+        vals.append(cb["value"])
+    value = float(np.mean(vals))
+    cb["value"] = value
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * np.mean(walls),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(w, 1), "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+# ----------------------------------------------------------------------------- distributed
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    return rank, world
+
+
+def dist_barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def dist_max(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n-src", type=int, default=256)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-iters-fwd", type=float, default=30.0)
+    ap.add_argument("--ref-iters-adj", type=float, default=4.0)
+    args = ap.parse_args()
+    rank, world = dist_init()
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(reference_arm(args)))
+        return
+    result, w, (itf, ita) = gpu_arm(args, rank, world)
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            result["cpu_baseline"] = cpu_baseline(w, itf, ita, os.cpu_count() or 1)
+        print(json.dumps(result))
+
+
+if __name__ == "__main__":
+    main()

@@ -106,6 +106,20 @@ typedef struct {
 
 typedef struct tt_ctx tt_ctx;
 
+/* Measurements of the last persistent sweep of one kind (forward or adjoint). */
+typedef struct {
+    double sweep_ms;          /* device time of the sweep launch, CUDA events on the context's
+                                 stream around that launch only */
+    long long node_updates;   /* (node, source) updates it performed, fixed sets excluded */
+    long long node_sweeps;    /* node visits counted once per batch: nodes x 8 x max iterations */
+    int iters_max;            /* largest per-source iteration count */
+    int grid_blocks, block_threads;
+    long long launches;       /* kernels this context has launched since it was created */
+} tt_stats;
+
+#define TT_STATS_FORWARD 0
+#define TT_STATS_ADJOINT 1
+
 /* Fills opts with the defaults for dtype: tol_fwd 1e-6 (F32) / 1e-8 (F64), tol_adj the
  * same, 500 iterations, init 0, spin limit 2 s. */
 void tt_default_opts(tt_opts *opts, int dtype);
@@ -150,6 +164,10 @@ tt_status tt_adjoint(tt_ctx *ctx, const tt_model *model, const tt_point *h_src, 
  * the result is bitwise reproducible. */
 tt_status tt_kernel(tt_ctx *ctx, const tt_model *model, int n_src, const void *d_T,
                     const void *d_P, double *d_Ks, double *d_Kxi, double *d_Keta);
+
+/* Copies the measurements of the last forward (which = TT_STATS_FORWARD) or adjoint
+ * (TT_STATS_ADJOINT) sweep. Host only; call after the solve returned. */
+tt_status tt_get_stats(const tt_ctx *ctx, int which, tt_stats *out);
 
 #ifdef __cplusplus
 }

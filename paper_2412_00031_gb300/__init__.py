@@ -61,8 +61,16 @@ class TTOpts(C.Structure):
                 ("spin_limit_ns", C.c_longlong), ("launch_blocks", C.c_int)]
 
 
+class TTStats(C.Structure):
+    _fields_ = [("sweep_ms", C.c_double), ("node_updates", C.c_longlong),
+                ("node_sweeps", C.c_longlong), ("iters_max", C.c_int), ("grid_blocks", C.c_int),
+                ("block_threads", C.c_int), ("launches", C.c_longlong)]
+
+
+TT_STATS_FORWARD, TT_STATS_ADJOINT = 0, 1
+
 EXPORTED = ["tt_default_opts", "tt_ctx_create", "tt_ctx_destroy", "tt_last_error",
-            "tt_forward", "tt_misfit", "tt_adjoint", "tt_kernel"]
+            "tt_forward", "tt_misfit", "tt_adjoint", "tt_kernel", "tt_get_stats"]
 
 
 def _load():
@@ -85,7 +93,9 @@ def _load():
                              C.POINTER(TTOpts), C.POINTER(C.c_int)]
     L.tt_kernel.argtypes = [C.c_void_p, C.POINTER(TTModel), C.c_int, C.c_void_p, C.c_void_p,
                             C.c_void_p, C.c_void_p, C.c_void_p]
-    for name in ("tt_ctx_create", "tt_forward", "tt_misfit", "tt_adjoint", "tt_kernel"):
+    L.tt_get_stats.argtypes = [C.c_void_p, C.c_int, C.POINTER(TTStats)]
+    for name in ("tt_ctx_create", "tt_forward", "tt_misfit", "tt_adjoint", "tt_kernel",
+                 "tt_get_stats"):
         getattr(L, name).restype = C.c_int
     return L
 
@@ -258,3 +268,10 @@ def tt_kernel(ctx, model, T, P, Ks, Kxi, Keta):
     n_src = T.shape[-1]
     _check(ctx, lib.tt_kernel(ctx.handle, C.byref(M), n_src, _ptr(T), _ptr(P), _ptr(Ks),
                               _ptr(Kxi), _ptr(Keta)))
+
+
+def tt_get_stats(ctx, which=TT_STATS_FORWARD):
+    """Measurements of the last forward or adjoint sweep, as a dict."""
+    s = TTStats()
+    _check(ctx, lib.tt_get_stats(ctx.handle, which, C.byref(s)))
+    return {k: getattr(s, k) for k, _ in TTStats._fields_}

@@ -40,6 +40,10 @@ struct tt_ctx {
     int *h_pinned = nullptr;  // readback: [0..TT_MAX_BATCH) iterations, then flags
     PointD *h_pts = nullptr;  // staging for source / receiver positions
     size_t h_pts_cap = 0;
+
+    cudaEvent_t ev_start[2] = {nullptr, nullptr}, ev_stop[2] = {nullptr, nullptr};
+    tt_stats stats[2] = {};
+    long long launches = 0;   // kernels launched by this context
 };
 
 namespace {
@@ -256,7 +260,27 @@ tt_status reset_solver_state(tt_ctx *ctx, int B) {
 
 // Reads back iterations, convergence flags, the barrier status and the validation flag,
 // waits for the stream and turns them into a status.
-tt_status finish_solve(tt_ctx *ctx, int B, int *h_iters, int max_iter, const char *what) {
+// Nodes a source updates per sweep: the swept box minus the part of its 3x3x3 fixed set
+// inside that box.
+long long updated_nodes(const tt_ctx *ctx, const PointD &p, int lo) {
+    const GridC &g = ctx->g;
+    const double deg = 3.14159265358979323846 / 180.0;
+    double f[3] = {((g.re - p.depth) - g.r0) / g.dr, (p.lat * deg - g.t0) / g.dt,
+                   (p.lon * deg - g.p0) / g.dp};
+    int n[3] = {g.nr, g.nt, g.np};
+    long long box = 1, fixed = 1;
+    for (int a = 0; a < 3; ++a) {
+        int c = (int)std::floor(f[a] + 0.5);
+        c = c < 0 ? 0 : (c > n[a] - 1 ? n[a] - 1 : c);
+        int l0 = c - 1 > lo ? c - 1 : lo, l1 = c + 1 < n[a] - 1 - lo ? c + 1 : n[a] - 1 - lo;
+        fixed *= l1 >= l0 ? (l1 - l0 + 1) : 0;
+        box *= n[a] - 2 * lo;
+    }
+    return box - fixed;
+}
+
+tt_status finish_solve(tt_ctx *ctx, int B, int *h_iters, int max_iter, const char *what,
+                       int which) {
     int *h = ctx->h_pinned;
     CK(cudaMemcpyAsync(h, ctx->iters.p, sizeof(int) * (size_t)B, cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaMemcpyAsync(h + TT_MAX_BATCH, ctx->conv.p, sizeof(int) * (size_t)B,
@@ -271,6 +295,23 @@ tt_status finish_solve(tt_ctx *ctx, int B, int *h_iters, int max_iter, const cha
     if (h[2 * TT_MAX_BATCH] == kDevTimeout)
         return fail(ctx, TT_ETIMEOUT, "%s: a device-side barrier wait exceeded its limit", what);
     if (h_iters) memcpy(h_iters, h, sizeof(int) * (size_t)B);
+    {
+        tt_stats &S = ctx->stats[which];
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, ctx->ev_start[which], ctx->ev_stop[which]));
+        S.sweep_ms = ms;
+        const int lo = which == TT_STATS_FORWARD ? 1 : 0;
+        long long upd = 0;
+        int imax = 0;
+        for (int b = 0; b < B; ++b) {
+            upd += 8LL * h[b] * updated_nodes(ctx, ctx->h_pts[b], lo);
+            imax = h[b] > imax ? h[b] : imax;
+        }
+        const GridC &g = ctx->g;
+        S.node_updates = upd;
+        S.iters_max = imax;
+        S.node_sweeps = 8LL * imax * (long long)(g.nr - 2 * lo) * (g.nt - 2 * lo) * (g.np - 2 * lo);
+    }
     int nc = 0;
     for (int b = 0; b < B; ++b) nc += h[TT_MAX_BATCH + b] == 0;
     if (nc)
@@ -300,6 +341,7 @@ tt_status forward_impl(tt_ctx *ctx, const tt_model *m, const tt_point *h_src, in
     CK(run_node_records<F>(g, m->d_s, m->d_xi, m->d_eta, ctx->gd.h2, ctx->gd.cost,
                            (NodeRec<F> *)ctx->rec.p, (int *)ctx->flags.p, ctx->st));
     CK(run_tau_init<F>(g, B, src, (F *)d_tau, o->init == 0, ctx->st));
+    ctx->launches += 4 + (o->init == 0 ? 2 : 1);
 
     int grid, block, slots;
     if ((s = sweep_shape<F>(ctx, true, B, ctx->interior, o->launch_blocks, grid, block, slots)) != TT_OK) return s;
@@ -329,11 +371,18 @@ tt_status forward_impl(tt_ctx *ctx, const tt_model *m, const tt_point *h_src, in
     a.tol = (F)o->tol_fwd;
     a.max_iter = o->max_iter_fwd;
     a.spin_ns = spin_ns(o);
+    CK(cudaEventRecord(ctx->ev_start[TT_STATS_FORWARD], ctx->st));
     CK(launch_forward<F>(a, grid, block, ctx->st));
-    if (d_T)
+    CK(cudaEventRecord(ctx->ev_stop[TT_STATS_FORWARD], ctx->st));
+    ctx->launches += 1;
+    ctx->stats[TT_STATS_FORWARD].grid_blocks = grid;
+    ctx->stats[TT_STATS_FORWARD].block_threads = block;
+    if (d_T) {
         CK(run_traveltime<F>(g, B, src, a.tabT, a.tabP, t.rad, t.cost, t.sint, (const F *)d_tau,
                              (F *)d_T, ctx->st));
-    return finish_solve(ctx, B, h_iters, o->max_iter_fwd, "tt_forward");
+        ctx->launches += 1;
+    }
+    return finish_solve(ctx, B, h_iters, o->max_iter_fwd, "tt_forward", TT_STATS_FORWARD);
 }
 
 tt_status receivers_impl(tt_ctx *ctx, const tt_point *h_rec, int n_rec) {
@@ -349,6 +398,7 @@ tt_status receivers_impl(tt_ctx *ctx, const tt_point *h_rec, int n_rec) {
     ENSURE(ctx->flags, 4 * sizeof(int));
     CK(run_receiver_setup(ctx->g, (const PointD *)ctx->pts.p, n_rec, (long long *)ctx->cq.p,
                           (double *)ctx->wq.p, (int *)ctx->flags.p + 2, ctx->st));
+    ctx->launches += 1;
     return TT_OK;
 }
 
@@ -369,6 +419,7 @@ tt_status adjoint_impl(tt_ctx *ctx, const tt_model *m, const tt_point *h_src, in
     CK(run_point_sources<F>(g, n_rec, (const long long *)ctx->cq.p, (const double *)ctx->wq.p,
                             (int *)ctx->sidx.p, (int *)ctx->next.p, (int *)ctx->heads.p,
                             (int *)ctx->nheads.p, d_R, B, (F *)ctx->JS.p, ctx->st));
+    ctx->launches += 5;
     if ((s = stage_points(ctx, h_src, B, ctx->pts)) != TT_OK) return s;
     ENSURE(ctx->src, sizeof(SrcC) * (size_t)B);
     ENSURE(ctx->tabT, sizeof(Vec2<F>) * (size_t)g.nt * B);
@@ -376,6 +427,7 @@ tt_status adjoint_impl(tt_ctx *ctx, const tt_model *m, const tt_point *h_src, in
     SrcC *src = (SrcC *)ctx->src.p;
     CK(run_source_setup<F>(g, m->d_s, m->d_xi, m->d_eta, (const PointD *)ctx->pts.p, B, src,
                            (Vec2<F> *)ctx->tabT.p, (Vec2<F> *)ctx->tabP.p, ctx->st));
+    ctx->launches += 3;
     CK(cudaMemsetAsync(d_P, 0, sizeof(F) * (size_t)g.N * B, ctx->st));
 
     int grid, block, slots;
@@ -409,8 +461,13 @@ tt_status adjoint_impl(tt_ctx *ctx, const tt_model *m, const tt_point *h_src, in
     a.tol = (F)o->tol_adj;
     a.max_iter = o->max_iter_adj;
     a.spin_ns = spin_ns(o);
+    CK(cudaEventRecord(ctx->ev_start[TT_STATS_ADJOINT], ctx->st));
     CK(launch_adjoint<F>(a, grid, block, ctx->st));
-    tt_status r = finish_solve(ctx, B, h_iters, o->max_iter_adj, "tt_adjoint");
+    CK(cudaEventRecord(ctx->ev_stop[TT_STATS_ADJOINT], ctx->st));
+    ctx->launches += 1;
+    ctx->stats[TT_STATS_ADJOINT].grid_blocks = grid;
+    ctx->stats[TT_STATS_ADJOINT].block_threads = block;
+    tt_status r = finish_solve(ctx, B, h_iters, o->max_iter_adj, "tt_adjoint", TT_STATS_ADJOINT);
     if (r == TT_OK && ctx->h_pinned[2 * TT_MAX_BATCH + 1] == 0) {
         int *h = ctx->h_pinned + 2 * TT_MAX_BATCH + 2;
         CK(cudaMemcpy(h, (int *)ctx->flags.p + 2, sizeof(int), cudaMemcpyDeviceToHost));
@@ -475,6 +532,10 @@ tt_status tt_ctx_create(tt_ctx **out, const tt_grid *grid, void *cuda_stream) {
     if (s == TT_OK) s = build_schedule(ctx, ctx->full, 0);
     if (s == TT_OK) s = upload_geo<float>(ctx, ctx->gf);
     if (s == TT_OK) s = upload_geo<double>(ctx, ctx->gd);
+    for (int q = 0; q < 2 && s == TT_OK; ++q)
+        if (cudaEventCreate(&ctx->ev_start[q]) != cudaSuccess ||
+            cudaEventCreate(&ctx->ev_stop[q]) != cudaSuccess)
+            s = fail(ctx, TT_ECUDA, "cudaEventCreate failed");
     if (s == TT_OK && cudaMallocHost((void **)&ctx->h_pinned,
                                      sizeof(int) * (2 * TT_MAX_BATCH + 8)) != cudaSuccess)
         s = fail(ctx, TT_ENOMEM, "pinned host allocation failed");
@@ -502,6 +563,10 @@ void tt_ctx_destroy(tt_ctx *ctx) {
                       &ctx->wq, &ctx->sidx, &ctx->next, &ctx->heads, &ctx->nheads, &ctx->JS};
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
+    for (int q = 0; q < 2; ++q) {
+        if (ctx->ev_start[q]) cudaEventDestroy(ctx->ev_start[q]);
+        if (ctx->ev_stop[q]) cudaEventDestroy(ctx->ev_stop[q]);
+    }
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
     if (ctx->h_pts) cudaFreeHost(ctx->h_pts);
     delete ctx;
@@ -541,6 +606,7 @@ tt_status tt_misfit(tt_ctx *ctx, const void *d_T, int dtype, const tt_data *d, d
     else
         CK(run_misfit<double>(d->n_src, d->n_rec, d_T, (const long long *)ctx->cq.p,
                               (const double *)ctx->wq.p, *d, d_Tr, d_chi, d_R, bad, ctx->st));
+    ctx->launches += 1;
     int *h = ctx->h_pinned + 2 * TT_MAX_BATCH + 4;
     CK(cudaMemcpyAsync(h, (int *)ctx->flags.p + 1, 2 * sizeof(int), cudaMemcpyDeviceToHost,
                        ctx->st));
@@ -581,6 +647,15 @@ tt_status tt_kernel(tt_ctx *ctx, const tt_model *model, int n_src, const void *d
     else
         CK(run_kernel_accum<double>(ctx->g, n_src, model->d_s, d_T, d_P, ctx->gd.h2,
                                     ctx->gd.cost, d_Ks, d_Kxi, d_Keta, ctx->n_sm, ctx->st));
+    ctx->launches += 1;
+    return TT_OK;
+}
+
+tt_status tt_get_stats(const tt_ctx *ctx, int which, tt_stats *out) {
+    if (!ctx || !out || (which != TT_STATS_FORWARD && which != TT_STATS_ADJOINT))
+        return TT_EINVAL;
+    *out = ctx->stats[which];
+    out->launches = ctx->launches;
     return TT_OK;
 }
 

@@ -193,11 +193,11 @@ def build_data(grid, src, rec, tobs, rng, counts=None, cs_max_deg=1.0, weight=1.
         abs_tobs.extend(tobs[n, sub].tolist())
         abs_off.append(len(abs_rec))
         lat, lon = rec[sub, 1], rec[sub, 2]
-        for a in range(len(sub)):
-            for b in range(a + 1, len(sub)):
-                if np.hypot(lat[a] - lat[b], lon[a] - lon[b]) <= cs_max_deg:
-                    m, i = sub[a], sub[b]
-                    cs_m.append(m); cs_i.append(i); cs_dt.append(tobs[n, m] - tobs[n, i])
+        a, b = np.triu_indices(len(sub), k=1)
+        keep = np.hypot(lat[a] - lat[b], lon[a] - lon[b]) <= cs_max_deg
+        m, i = sub[a[keep]], sub[b[keep]]
+        cs_m.extend(m.tolist()); cs_i.extend(i.tolist())
+        cs_dt.extend((tobs[n, m] - tobs[n, i]).tolist())
         cs_off.append(len(cs_m))
     f64 = lambda x: np.asarray(x, dtype=np.float64)
     i32 = lambda x: np.asarray(x, dtype=np.int32)
