@@ -142,16 +142,19 @@ class GpuPath:
         self.chi = torch.empty((B, 2), dtype=torch.float64, device=device)
         self.K = [torch.zeros(g.shape, dtype=torch.float64, device=device) for _ in range(3)]
         self.opts = tt.default_opts(tt.TT_F32)
+        self.allow_unconverged = False
         self.iters = []
 
     def step(self):
         tt = self.tt
         for k in self.K:
             k.zero_()
-        itf = tt.tt_forward(self.ctx, self.model, self.w.src, self.tau, self.T, self.opts)
+        au = self.allow_unconverged
+        itf = tt.tt_forward(self.ctx, self.model, self.w.src, self.tau, self.T, self.opts,
+                            allow_unconverged=au)
         tt.tt_misfit(self.ctx, self.T, self.data, None, self.chi, self.R)
         ita = tt.tt_adjoint(self.ctx, self.model, self.w.src, self.T, self.w.rec, self.R,
-                            self.P, self.opts)
+                            self.P, self.opts, allow_unconverged=au)
         tt.tt_kernel(self.ctx, self.model, self.T, self.P, *self.K)
         fs = tt.tt_get_stats(self.ctx, tt.TT_STATS_FORWARD)
         as_ = tt.tt_get_stats(self.ctx, tt.TT_STATS_ADJOINT)
@@ -223,6 +226,10 @@ def gpu_arm(args, rank, world):
     torch.cuda.set_device(dev)
     w = I.anisotropic_batch(seed=I.SEED_BASE + 2 + rank, n_src=args.n_src)
     gp = GpuPath(w, dev)
+    if args.max_iter_fwd or args.max_iter_adj:  # profiling runs only: bounded iterations
+        gp.opts.max_iter_fwd = args.max_iter_fwd or gp.opts.max_iter_fwd
+        gp.opts.max_iter_adj = args.max_iter_adj or gp.opts.max_iter_adj
+        gp.allow_unconverged = True
     for _ in range(args.warmup):
         gp.step()
     gp.iters.clear()
@@ -243,8 +250,11 @@ def gpu_arm(args, rank, world):
     ms = dist_max(ms, world)
     dist_barrier(world)
 
-    e2e_ms, h2d, d2h = run_e2e(gp, w, max(1, args.steps))
-    e2e_ms = dist_max(e2e_ms, world)
+    if args.no_e2e:
+        e2e_ms, h2d, d2h = float("nan"), 0, 0
+    else:
+        e2e_ms, h2d, d2h = run_e2e(gp, w, max(1, args.steps))
+        e2e_ms = dist_max(e2e_ms, world)
 
     # roofline of the dominant kernel (forward sweep) and the adjoint sweep
     hbm, peak_kind = peaks()
@@ -401,6 +411,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n-src", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="profiling runs: skip the e2e leg")
+    ap.add_argument("--max-iter-fwd", type=int, default=0, help="profiling runs only")
+    ap.add_argument("--max-iter-adj", type=int, default=0, help="profiling runs only")
     ap.add_argument("--ref-iters-fwd", type=float, default=30.0)
     ap.add_argument("--ref-iters-adj", type=float, default=4.0)
     args = ap.parse_args()
