@@ -165,6 +165,30 @@ tt_status tt_adjoint(tt_ctx *ctx, const tt_model *model, const tt_point *h_src, 
 tt_status tt_kernel(tt_ctx *ctx, const tt_model *model, int n_src, const void *d_T,
                     const void *d_P, double *d_Ks, double *d_Kxi, double *d_Keta);
 
+/* Largest receiver count tt_misfit_noalloc accepts: the size of its static scratch. */
+#define TT_NOALLOC_MAX_REC 1024
+
+/* tt_misfit_noalloc — the results of tt_misfit (same kernels, same outputs, same layouts)
+ * without a context and without any device allocation. It is meant for callers that cannot
+ * allocate device memory at the point of the call: for example a serving process that
+ * handed all of its HBM to its own pool allocator at start-up, or a pipeline stage that must
+ * not take cudaMalloc's implicit device-wide synchronisation. The paper has no counterpart;
+ * it is a convenience of this library.
+ * Scratch: one static device array of about 156 KB per GPU that loads the library (held
+ * until the process exits), holding the receiver positions, cells and weights and two flags;
+ * hence n_rec must be 1..TT_NOALLOC_MAX_REC, and larger counts return TT_EINVAL with a
+ * message saying so. The flags are cleared by every call; the other contents are whatever
+ * the last call left. Every call on a device shares that array, so calls whose GPU work
+ * overlaps (other host threads, other streams) race; issue them one after another.
+ * The first call on each device looks up the array's device address (cudaGetSymbolAddress,
+ * with that device current); make that first call before any stream capture.
+ * grid: the study region (validated as in tt_ctx_create). cuda_stream: the cudaStream_t to
+ * run on (NULL for the default stream). h_err/err_len: optional host buffer that receives a
+ * one-line message (may be NULL). The call waits for its stream before returning. */
+tt_status tt_misfit_noalloc(const tt_grid *grid, const void *d_T, int dtype,
+                            const tt_data *data, double *d_Tr, double *d_chi, double *d_R,
+                            void *cuda_stream, char *h_err, int err_len);
+
 /* Copies the measurements of the last forward (which = TT_STATS_FORWARD) or adjoint
  * (TT_STATS_ADJOINT) sweep. Host only; call after the solve returned. */
 tt_status tt_get_stats(const tt_ctx *ctx, int which, tt_stats *out);

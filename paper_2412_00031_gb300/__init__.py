@@ -70,7 +70,9 @@ class TTStats(C.Structure):
 TT_STATS_FORWARD, TT_STATS_ADJOINT = 0, 1
 
 EXPORTED = ["tt_default_opts", "tt_ctx_create", "tt_ctx_destroy", "tt_last_error",
-            "tt_forward", "tt_misfit", "tt_adjoint", "tt_kernel", "tt_get_stats"]
+            "tt_forward", "tt_misfit", "tt_adjoint", "tt_kernel", "tt_get_stats",
+            "tt_misfit_noalloc"]
+TT_NOALLOC_MAX_REC = 1024
 
 
 def _load():
@@ -94,8 +96,11 @@ def _load():
     L.tt_kernel.argtypes = [C.c_void_p, C.POINTER(TTModel), C.c_int, C.c_void_p, C.c_void_p,
                             C.c_void_p, C.c_void_p, C.c_void_p]
     L.tt_get_stats.argtypes = [C.c_void_p, C.c_int, C.POINTER(TTStats)]
+    L.tt_misfit_noalloc.argtypes = [C.POINTER(TTGrid), C.c_void_p, C.c_int, C.POINTER(TTData),
+                                    C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_char_p,
+                                    C.c_int]
     for name in ("tt_ctx_create", "tt_forward", "tt_misfit", "tt_adjoint", "tt_kernel",
-                 "tt_get_stats"):
+                 "tt_get_stats", "tt_misfit_noalloc"):
         getattr(L, name).restype = C.c_int
     return L
 
@@ -275,3 +280,19 @@ def tt_get_stats(ctx, which=TT_STATS_FORWARD):
     s = TTStats()
     _check(ctx, lib.tt_get_stats(ctx.handle, which, C.byref(s)))
     return {k: getattr(s, k) for k, _ in TTStats._fields_}
+
+
+def tt_misfit_noalloc(grid, T, data, Tr=None, chi=None, R=None, stream=None):
+    """tt_misfit without a context and without device allocation (static scratch; at most
+    TT_NOALLOC_MAX_REC receivers). Same outputs as tt_misfit."""
+    import torch
+    _cuda_ok(T, Tr, chi, R)
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    G = make_grid(grid)
+    D = data.c_struct()
+    err = C.create_string_buffer(256)
+    st = lib.tt_misfit_noalloc(C.byref(G), _ptr(T), _dtype_code(T), C.byref(D), _ptr(Tr),
+                               _ptr(chi), _ptr(R), C.c_void_p(stream.cuda_stream), err, 256)
+    if st != TT_OK:
+        raise TTError(st, err.value.decode())
