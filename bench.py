@@ -226,6 +226,7 @@ def gpu_arm(args, rank, world):
     torch.cuda.set_device(dev)
     w = I.anisotropic_batch(seed=I.SEED_BASE + 2 + rank, n_src=args.n_src)
     gp = GpuPath(w, dev)
+    gp.opts.sweep_schedule = args.schedule
     if args.max_iter_fwd or args.max_iter_adj:  # profiling runs only: bounded iterations
         gp.opts.max_iter_fwd = args.max_iter_fwd or gp.opts.max_iter_fwd
         gp.opts.max_iter_adj = args.max_iter_adj or gp.opts.max_iter_adj
@@ -414,6 +415,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="profiling runs: skip the e2e leg")
     ap.add_argument("--max-iter-fwd", type=int, default=0, help="profiling runs only")
     ap.add_argument("--max-iter-adj", type=int, default=0, help="profiling runs only")
+    ap.add_argument("--schedule", type=int, default=0,
+                    help="forward sweep schedule (tt_opts.sweep_schedule; 0 = automatic)")
     ap.add_argument("--ref-iters-fwd", type=float, default=30.0)
     ap.add_argument("--ref-iters-adj", type=float, default=4.0)
     args = ap.parse_args()

@@ -102,6 +102,9 @@ typedef struct {
     long long spin_limit_ns;/* bound on every device-side wait; 0 = 2 s */
     int launch_blocks;      /* persistent sweep launch: 0 = automatic, else at most this many
                                blocks (results do not depend on it) */
+    int sweep_schedule;     /* forward sweep schedule: 0 = automatic; 1 = node hyperplanes;
+                               2, 3, 4 = tile hyperplanes with 4x8x8, 4x4x8, 2x8x8 tiles
+                               (r x theta x phi). Results do not depend on it. */
 } tt_opts;
 
 typedef struct tt_ctx tt_ctx;

@@ -1,10 +1,13 @@
 // C ABI of libttgb (declared in include/tt.h): context, validation, workspace and the
 // orchestration of the kernels in tt_sweep.cu and tt_aux.cu.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstddef>
 #include <cstring>
 #include <vector>
 
@@ -31,12 +34,13 @@ struct tt_ctx {
     char err[512] = {0};
 
     Schedule interior, full;
+    TileSchedule tiled[kNumTileShapes];
     GeoTab<float> gf;
     GeoTab<double> gd;
 
     // workspace, grown on demand
     DevBuf src, pts, tabT, tabP, rec, partial, conv, iters, nact, bar, flags;
-    DevBuf cq, wq, sidx, next, heads, nheads, JS;
+    DevBuf cq, wq, sidx, next, heads, nheads, JS, coef;
     int *h_pinned = nullptr;  // readback: [0..TT_MAX_BATCH) iterations, then flags
     PointD *h_pts = nullptr;  // staging for source / receiver positions
     size_t h_pts_cap = 0;
@@ -49,6 +53,8 @@ struct tt_ctx {
 namespace {
 
 constexpr long long kDefaultSpinNs = 2000000000LL;
+// Largest per-(node, source) coefficient array the adjoint keeps in its workspace.
+constexpr size_t kCoefBudgetBytes = 64ull << 30;
 
 tt_status fail(tt_ctx *c, tt_status s, const char *fmt, ...) {
     if (c) {
@@ -148,6 +154,69 @@ tt_status build_schedule(tt_ctx *ctx, Schedule &S, int lo) {
     return TT_OK;
 }
 
+tt_status build_tile_schedule(tt_ctx *ctx, TileSchedule &S, const TileShape &sh) {
+    const GridC &g = ctx->g;
+    const int nI = (g.nr - 2 + sh.ta - 1) / sh.ta, nJ = (g.nt - 2 + sh.tb - 1) / sh.tb;
+    const int nK = (g.np - 2 + sh.tc - 1) / sh.tc;
+    S.n_planes = nI + nJ + nK - 2;
+    std::vector<unsigned int> tiles;
+    std::vector<int> off(S.n_planes + 1, 0);
+    for (int L = 0; L < S.n_planes; ++L) {
+        off[L] = (int)tiles.size();
+        for (int I = 0; I < nI && I <= L; ++I)
+            for (int J = 0; J < nJ && I + J <= L; ++J) {
+                int K = L - I - J;
+                if (K < nK) tiles.push_back(((unsigned)I << 20) | ((unsigned)J << 10) | (unsigned)K);
+            }
+    }
+    off[S.n_planes] = (int)tiles.size();
+    CK(cudaMalloc((void **)&S.tiles, tiles.size() * sizeof(unsigned int)));
+    CK(cudaMalloc((void **)&S.off, off.size() * sizeof(int)));
+    CK(cudaMemcpy(S.tiles, tiles.data(), tiles.size() * sizeof(unsigned int),
+                  cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(S.off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice));
+    return TT_OK;
+}
+
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// 4-D tiled tensor map over an [n_r][n_t][n_p][inner] array of F (inner innermost).
+template <typename F>
+tt_status encode_map4(tt_ctx *ctx, CUtensorMap *map, const void *base, long long inner,
+                      const unsigned box[4]) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return fail(ctx, TT_ECUDA, "cuTensorMapEncodeTiled is unavailable");
+    const GridC &g = ctx->g;
+    const cuuint64_t es = sizeof(F);
+    cuuint64_t dims[4] = {(cuuint64_t)inner, (cuuint64_t)g.np, (cuuint64_t)g.nt, (cuuint64_t)g.nr};
+    cuuint64_t strides[3] = {inner * es, (cuuint64_t)g.np * inner * es,
+                             (cuuint64_t)g.nt * g.np * inner * es};
+    cuuint32_t boxd[4] = {box[0], box[1], box[2], box[3]};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUresult r = enc(map, sizeof(F) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
+                     4, const_cast<void *>(base), dims, strides, boxd, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(ctx, TT_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return TT_OK;
+}
+
 template <typename F>
 tt_status upload_tab(tt_ctx *ctx, F *&dst, const std::vector<double> &v) {
     std::vector<F> tmp(v.begin(), v.end());
@@ -236,6 +305,8 @@ tt_status check_opts(tt_ctx *ctx, const tt_opts *o) {
     if (!o) return fail(ctx, TT_EINVAL, "opts is NULL");
     if (!(o->tol_fwd > 0) || !(o->tol_adj > 0) || o->max_iter_fwd < 1 || o->max_iter_adj < 1)
         return fail(ctx, TT_EINVAL, "tolerances must be > 0 and iteration limits >= 1");
+    if (o->sweep_schedule < 0 || o->sweep_schedule > 1 + kNumTileShapes)
+        return fail(ctx, TT_EINVAL, "sweep_schedule %d unknown", o->sweep_schedule);
     return TT_OK;
 }
 
@@ -247,13 +318,13 @@ unsigned long long spin_ns(const tt_opts *o) {
 tt_status reset_solver_state(tt_ctx *ctx, int B) {
     ENSURE(ctx->conv, sizeof(int) * (size_t)B);
     ENSURE(ctx->iters, sizeof(int) * (size_t)B);
-    ENSURE(ctx->nact, sizeof(int));
-    ENSURE(ctx->bar, sizeof(BarrierState));
+    ENSURE(ctx->nact, sizeof(int) * kMaxBarrierGroups);
+    ENSURE(ctx->bar, sizeof(BarrierState) * kMaxBarrierGroups);
     ENSURE(ctx->flags, 4 * sizeof(int));
     CK(cudaMemsetAsync(ctx->conv.p, 0, sizeof(int) * (size_t)B, ctx->st));
     CK(cudaMemsetAsync(ctx->iters.p, 0, sizeof(int) * (size_t)B, ctx->st));
-    CK(cudaMemsetAsync(ctx->nact.p, 0, sizeof(int), ctx->st));
-    CK(cudaMemsetAsync(ctx->bar.p, 0, sizeof(BarrierState), ctx->st));
+    CK(cudaMemsetAsync(ctx->nact.p, 0, sizeof(int) * kMaxBarrierGroups, ctx->st));
+    CK(cudaMemsetAsync(ctx->bar.p, 0, sizeof(BarrierState) * kMaxBarrierGroups, ctx->st));
     CK(cudaMemsetAsync(ctx->flags.p, 0, 4 * sizeof(int), ctx->st));
     return TT_OK;
 }
@@ -285,15 +356,20 @@ tt_status finish_solve(tt_ctx *ctx, int B, int *h_iters, int max_iter, const cha
     CK(cudaMemcpyAsync(h, ctx->iters.p, sizeof(int) * (size_t)B, cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaMemcpyAsync(h + TT_MAX_BATCH, ctx->conv.p, sizeof(int) * (size_t)B,
                        cudaMemcpyDeviceToHost, ctx->st));
-    CK(cudaMemcpyAsync(h + 2 * TT_MAX_BATCH, &((BarrierState *)ctx->bar.p)->status, sizeof(int),
+    unsigned char *hb = (unsigned char *)(ctx->h_pinned + 2 * TT_MAX_BATCH + 8);
+    CK(cudaMemcpyAsync(hb, ctx->bar.p, sizeof(BarrierState) * kMaxBarrierGroups,
                        cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaMemcpyAsync(h + 2 * TT_MAX_BATCH + 1, ctx->flags.p, sizeof(int),
                        cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
     if (h[2 * TT_MAX_BATCH + 1])
         return fail(ctx, TT_EINVAL, "%s: model has s <= 0 or xi^2 + eta^2 >= 1/4", what);
-    if (h[2 * TT_MAX_BATCH] == kDevTimeout)
-        return fail(ctx, TT_ETIMEOUT, "%s: a device-side barrier wait exceeded its limit", what);
+    for (int q = 0; q < kMaxBarrierGroups; ++q) {
+        int st;
+        memcpy(&st, hb + q * sizeof(BarrierState) + offsetof(BarrierState, status), sizeof st);
+        if (st == kDevTimeout)
+            return fail(ctx, TT_ETIMEOUT, "%s: a device-side wait exceeded its limit", what);
+    }
     if (h_iters) memcpy(h_iters, h, sizeof(int) * (size_t)B);
     {
         tt_stats &S = ctx->stats[which];
@@ -344,7 +420,52 @@ tt_status forward_impl(tt_ctx *ctx, const tt_model *m, const tt_point *h_src, in
     ctx->launches += 4 + (o->init == 0 ? 2 : 1);
 
     int grid, block, slots;
-    if ((s = sweep_shape<F>(ctx, true, B, ctx->interior, o->launch_blocks, grid, block, slots)) != TT_OK) return s;
+    // Tile schedules stage 32 sources per task with TMA: they need B >= 32 and rows of tau
+    // (B values) that are a multiple of 16 bytes. Automatic: node hyperplanes.
+    const bool tiles_ok = B >= 32 && (B * sizeof(F)) % 16 == 0;
+    int sched = o->sweep_schedule == 0 ? 1 : o->sweep_schedule;
+    if (sched >= 2 && !tiles_ok) sched = 1;
+    int n_bgroups = 1, grp_blocks = 0, grp_src = B;
+    if (sched == 1) {
+        // 256-thread blocks; one barrier group per resident block slot of an SM, so each SM
+        // interleaves the groups; each group gets a multiple of 32 sources.
+        block = 256;
+        size_t smem = (size_t)B * sizeof(F);
+        int per_sm = forward_blocks_per_sm<F>(block, smem);
+        if (per_sm <= 0) return fail(ctx, TT_ECUDA, "sweep kernel cannot be resident (B = %d)", B);
+        if (per_sm > kMaxBarrierGroups) per_sm = kMaxBarrierGroups;
+        int max_grid = per_sm * ctx->n_sm;
+        if (o->launch_blocks > 0 && o->launch_blocks < max_grid) max_grid = o->launch_blocks;
+        n_bgroups = per_sm;
+        if (n_bgroups > (B + 31) / 32) n_bgroups = (B + 31) / 32;
+        if (n_bgroups > max_grid) n_bgroups = max_grid;
+        grp_src = ((B + n_bgroups - 1) / n_bgroups + 31) / 32 * 32;
+        n_bgroups = (B + grp_src - 1) / grp_src;
+        grp_blocks = max_grid / n_bgroups;
+        if ((long long)grp_blocks * block < grp_src) {
+            int need = (grp_src + block - 1) / block;
+            if ((long long)need * n_bgroups > (long long)per_sm * ctx->n_sm)
+                return fail(ctx, TT_EINVAL, "batch of %d sources exceeds one resident launch", B);
+            grp_blocks = need;
+        }
+        grid = grp_blocks * n_bgroups;
+        slots = 0;
+    } else {
+        int per_sm = forward_tiled_blocks_per_sm<F>(sched - 2, B);
+        if (per_sm <= 0) return fail(ctx, TT_ECUDA, "tiled sweep cannot be resident (B = %d)", B);
+        if (per_sm > 2) per_sm = 2;
+        int max_grid = per_sm * ctx->n_sm;
+        if (o->launch_blocks > 0 && o->launch_blocks < max_grid) max_grid = o->launch_blocks;
+        block = kTileThreads;
+        grid = max_grid;
+        if ((long long)grid * block < B) {
+            int need = (B + block - 1) / block;
+            if (need > per_sm * ctx->n_sm)
+                return fail(ctx, TT_EINVAL, "batch of %d sources exceeds one resident launch", B);
+            grid = need;
+        }
+        slots = (int)(((long long)grid * block) / B);
+    }
     ENSURE(ctx->partial, sizeof(F) * 2 * (size_t)B * grid);
     const GeoTab<F> &t = geo<F>(ctx);
     FwdArgs<F> a;
@@ -371,8 +492,29 @@ tt_status forward_impl(tt_ctx *ctx, const tt_model *m, const tt_point *h_src, in
     a.tol = (F)o->tol_fwd;
     a.max_iter = o->max_iter_fwd;
     a.spin_ns = spin_ns(o);
+    CUtensorMap map_tau, map_rec;
+    a.n_bgroups = n_bgroups;
+    a.grp_blocks = grp_blocks;
+    a.grp_src = grp_src;
+    if (sched >= 2) {
+        const TileShape sh = kTileShapes[sched - 2];
+        const unsigned box_tau[4] = {32u, (unsigned)sh.tc + 2, (unsigned)sh.tb + 2,
+                                     (unsigned)sh.ta + 2};
+        const unsigned box_rec[4] = {8u, (unsigned)sh.tc, (unsigned)sh.tb, (unsigned)sh.ta};
+        if ((s = encode_map4<F>(ctx, &map_tau, d_tau, B, box_tau)) != TT_OK) return s;
+        if ((s = encode_map4<F>(ctx, &map_rec, ctx->rec.p, 8, box_rec)) != TT_OK) return s;
+        const TileSchedule &ts = ctx->tiled[sched - 2];
+        a.tiles = ts.tiles;
+        a.toff = ts.off;
+        a.n_tplanes = ts.n_planes;
+        a.na = g.nr - 2;
+        a.nb = g.nt - 2;
+        a.nc = g.np - 2;
+        a.ngroups = (B + 31) / 32;
+    }
     CK(cudaEventRecord(ctx->ev_start[TT_STATS_FORWARD], ctx->st));
-    CK(launch_forward<F>(a, grid, block, ctx->st));
+    if (sched == 1) CK(launch_forward<F>(a, grid, block, ctx->st));
+    else CK(launch_forward_tiled<F>(map_tau, map_rec, a, sched - 2, grid, ctx->st));
     CK(cudaEventRecord(ctx->ev_stop[TT_STATS_FORWARD], ctx->st));
     ctx->launches += 1;
     ctx->stats[TT_STATS_FORWARD].grid_blocks = grid;
@@ -430,8 +572,42 @@ tt_status adjoint_impl(tt_ctx *ctx, const tt_model *m, const tt_point *h_src, in
     ctx->launches += 3;
     CK(cudaMemsetAsync(d_P, 0, sizeof(F) * (size_t)g.N * B, ctx->st));
 
+    // Face-coefficient sweep when the per-(node, source) coefficients fit the workspace
+    // budget; otherwise the sweep that evaluates the flux velocities at every update.
+    const size_t coef_bytes = sizeof(Vec4<F>) * (size_t)g.N * B;
+    const bool faces = coef_bytes <= kCoefBudgetBytes;
     int grid, block, slots;
-    if ((s = sweep_shape<F>(ctx, false, B, ctx->full, o->launch_blocks, grid, block, slots)) != TT_OK) return s;
+    int n_bgroups = 1, grp_blocks = 0, grp_src = B;
+    if (faces) {
+        block = 256;
+        int per_sm = 0;
+        for (int tries = 0; tries < 2; ++tries) {
+            size_t smem = (size_t)grp_src * 2 * sizeof(F);
+            per_sm = adjoint_faces_blocks_per_sm<F>(block, smem);
+            if (per_sm > kMaxBarrierGroups) per_sm = kMaxBarrierGroups;
+            n_bgroups = per_sm < 1 ? 1 : per_sm;
+            if (n_bgroups > (B + 31) / 32) n_bgroups = (B + 31) / 32;
+            grp_src = ((B + n_bgroups - 1) / n_bgroups + 31) / 32 * 32;
+            n_bgroups = (B + grp_src - 1) / grp_src;
+        }
+        if (per_sm <= 0) return fail(ctx, TT_ECUDA, "adjoint sweep cannot be resident");
+        int max_grid = per_sm * ctx->n_sm;
+        if (o->launch_blocks > 0 && o->launch_blocks < max_grid) max_grid = o->launch_blocks;
+        if (max_grid < n_bgroups) max_grid = n_bgroups;
+        grp_blocks = max_grid / n_bgroups;
+        if ((long long)grp_blocks * block < grp_src) {
+            int need = (grp_src + block - 1) / block;
+            if ((long long)need * n_bgroups > (long long)per_sm * ctx->n_sm)
+                return fail(ctx, TT_EINVAL, "batch of %d sources exceeds one resident launch", B);
+            grp_blocks = need;
+        }
+        grid = grp_blocks * n_bgroups;
+        slots = 0;
+        ENSURE(ctx->coef, coef_bytes);
+    } else if ((s = sweep_shape<F>(ctx, false, B, ctx->full, o->launch_blocks, grid, block,
+                                   slots)) != TT_OK) {
+        return s;
+    }
     ENSURE(ctx->partial, sizeof(F) * 2 * (size_t)B * grid);
     const GeoTab<F> &t = geo<F>(ctx);
     AdjArgs<F> a;
@@ -461,8 +637,17 @@ tt_status adjoint_impl(tt_ctx *ctx, const tt_model *m, const tt_point *h_src, in
     a.tol = (F)o->tol_adj;
     a.max_iter = o->max_iter_adj;
     a.spin_ns = spin_ns(o);
+    a.coef = faces ? (Vec4<F> *)ctx->coef.p : nullptr;
+    a.n_bgroups = n_bgroups;
+    a.grp_blocks = grp_blocks;
+    a.grp_src = grp_src;
+    if (faces) {
+        CK(launch_adjoint_coefs<F>(a, ctx->st));
+        ctx->launches += 1;
+    }
     CK(cudaEventRecord(ctx->ev_start[TT_STATS_ADJOINT], ctx->st));
-    CK(launch_adjoint<F>(a, grid, block, ctx->st));
+    if (faces) CK(launch_adjoint_faces<F>(a, grid, block, ctx->st));
+    else CK(launch_adjoint<F>(a, grid, block, ctx->st));
     CK(cudaEventRecord(ctx->ev_stop[TT_STATS_ADJOINT], ctx->st));
     ctx->launches += 1;
     ctx->stats[TT_STATS_ADJOINT].grid_blocks = grid;
@@ -490,6 +675,7 @@ void tt_default_opts(tt_opts *o, int dtype) {
     o->init = 0;
     o->spin_limit_ns = 0;
     o->launch_blocks = 0;
+    o->sweep_schedule = 0;
 }
 
 const char *tt_last_error(const tt_ctx *ctx) { return ctx ? ctx->err : "no context"; }
@@ -530,6 +716,8 @@ tt_status tt_ctx_create(tt_ctx **out, const tt_grid *grid, void *cuda_stream) {
         s = fail(ctx, TT_ECUDA, "no CUDA device");
     if (s == TT_OK) s = build_schedule(ctx, ctx->interior, 1);
     if (s == TT_OK) s = build_schedule(ctx, ctx->full, 0);
+    for (int q = 0; q < kNumTileShapes && s == TT_OK; ++q)
+        s = build_tile_schedule(ctx, ctx->tiled[q], kTileShapes[q]);
     if (s == TT_OK) s = upload_geo<float>(ctx, ctx->gf);
     if (s == TT_OK) s = upload_geo<double>(ctx, ctx->gd);
     for (int q = 0; q < 2 && s == TT_OK; ++q)
@@ -537,7 +725,8 @@ tt_status tt_ctx_create(tt_ctx **out, const tt_grid *grid, void *cuda_stream) {
             cudaEventCreate(&ctx->ev_stop[q]) != cudaSuccess)
             s = fail(ctx, TT_ECUDA, "cudaEventCreate failed");
     if (s == TT_OK && cudaMallocHost((void **)&ctx->h_pinned,
-                                     sizeof(int) * (2 * TT_MAX_BATCH + 8)) != cudaSuccess)
+                                     sizeof(int) * (2 * TT_MAX_BATCH + 8) +
+                                         sizeof(BarrierState) * kMaxBarrierGroups) != cudaSuccess)
         s = fail(ctx, TT_ENOMEM, "pinned host allocation failed");
     if (s != TT_OK) {
         tt_ctx_destroy(ctx);
@@ -556,11 +745,16 @@ void tt_ctx_destroy(tt_ctx *ctx) {
         if (S->nodes) cudaFree(S->nodes);
         if (S->off) cudaFree(S->off);
     }
+    for (TileSchedule &S : ctx->tiled) {
+        if (S.tiles) cudaFree(S.tiles);
+        if (S.off) cudaFree(S.off);
+    }
     free_geo(ctx->gf);
     free_geo(ctx->gd);
     DevBuf *bufs[] = {&ctx->src, &ctx->pts, &ctx->tabT, &ctx->tabP, &ctx->rec, &ctx->partial,
                       &ctx->conv, &ctx->iters, &ctx->nact, &ctx->bar, &ctx->flags, &ctx->cq,
-                      &ctx->wq, &ctx->sidx, &ctx->next, &ctx->heads, &ctx->nheads, &ctx->JS};
+                      &ctx->wq, &ctx->sidx, &ctx->next, &ctx->heads, &ctx->nheads, &ctx->JS,
+                      &ctx->coef};
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     for (int q = 0; q < 2; ++q) {

@@ -47,6 +47,7 @@ template <typename F> struct alignas(sizeof(F) * 8) NodeRec {
 };
 
 template <typename F> struct Vec2 { F x, y; };
+template <typename F> struct alignas(sizeof(F) * 4) Vec4 { F x, y, z, w; };
 
 __device__ __forceinline__ bool in_fixed_set(int ci, int cj, int ck, int i, int j, int k) {
     return abs(i - ci) <= 1 && abs(j - cj) <= 1 && abs(k - ck) <= 1;
@@ -115,16 +116,40 @@ __device__ __forceinline__ F factor_T0(const SrcReg<F> &S, int i, F r, F cth, F 
     return rho * S.inv_s0;  // 1 / T0 = 1 / (s0 sqrt(q))
 }
 
+// Lax-Friedrichs update of tau at an interior node for one source (Sec. 3.1 with the
+// factor of factor_T0). Dividing the update by T0, with u = p0 / T0 and
+// e_d = 1 / (2 delta_d h_d):
+//   v = tau_c u + ((tau_d+ - tau_d-) e_d)_d,     H / T0 = sqrt(v^T M v)
+//   tau_new = [s / T0 - H / T0 + sum_d c_d (tau_d+ + tau_d-)] / (2 sum_d c_d)
+// with c_d = kappa_d e_d, kappa = (1, sqrt(1 - 2 xi), sqrt(1 + 2 xi)): the Cauchy-Schwarz
+// bounds of |dH/dp_d| that make the scheme monotone (the Lax-Friedrichs viscosity).
+// trp/trm etc. are tau at the + and - neighbours along r, theta, phi in physical order.
+template <typename F>
+__device__ __forceinline__ F lf_update(const SrcReg<F> &S, int i, F tc, F trp, F trm, F ttp,
+                                       F ttm, F tpp, F tpm, const NodeRec<F> &R, F r, F cth,
+                                       F sth, Vec2<F> tT, Vec2<F> tP, bool flat, F er) {
+    F ur, ut, up;
+    F invT0 = factor_T0<F>(S, i, r, cth, sth, tT, tP, flat, ur, ut, up);
+    F vr = tc * ur + (trp - trm) * er;
+    F vt = tc * ut + (ttp - ttm) * R.et;
+    F vp = tc * up + (tpp - tpm) * R.ep;
+    F q = vr * vr + ((F)1 - (F)2 * R.xi) * vt * vt + ((F)1 + (F)2 * R.xi) * vp * vp
+          + (F)4 * R.eta * vt * vp;
+    F H = sqrt_(q);
+    F num = R.s * invT0 - H + er * (trp + trm) + R.ct * (ttp + ttm) + R.cp * (tpp + tpm);
+    return num * R.invW;
+}
+
 // ---------------------------------------------------------------------------------------
 // Grid-wide barrier for persistent cooperative launches. Every wait is bounded by a
 // deadline on the global nanosecond timer; on expiry the status word gets kDevTimeout and
 // the caller returns. All blocks eventually leave: a block that gave up never arrives
 // again, so the others' waits expire too.
-struct BarrierState {
+struct alignas(128) BarrierState {  // one L2 line per barrier group
     unsigned int count;
     unsigned int gen;
     int status;
-    int pad;
+    int pad[29];
 };
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -149,8 +174,10 @@ __device__ __forceinline__ int ld_status(const int *p) {
     return v;
 }
 
-// Returns false when the barrier (or an earlier one in another block) timed out.
-__device__ __forceinline__ bool grid_barrier(BarrierState *bs, unsigned long long limit_ns) {
+// Returns false when the barrier (or an earlier one in another block) timed out. nblocks is
+// the number of blocks that take part (all blocks of the launch, or one barrier group).
+__device__ __forceinline__ bool grid_barrier(BarrierState *bs, unsigned long long limit_ns,
+                                             unsigned int nblocks) {
     __shared__ int ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -158,7 +185,7 @@ __device__ __forceinline__ bool grid_barrier(BarrierState *bs, unsigned long lon
         unsigned int gen = ld_acquire(&bs->gen);
         __threadfence();
         unsigned int arrived = atomicAdd(&bs->count, 1u);
-        if (arrived == gridDim.x - 1) {
+        if (arrived == nblocks - 1) {
             atomicExch(&bs->count, 0u);
             __threadfence();
             st_release(&bs->gen, gen + 1);
@@ -172,7 +199,7 @@ __device__ __forceinline__ bool grid_barrier(BarrierState *bs, unsigned long lon
                     break;
                 }
                 __nanosleep(ns);
-                if (ns < 256) ns <<= 1;
+                if (ns < 64) ns <<= 1;
             }
         }
         __threadfence();
@@ -181,6 +208,10 @@ __device__ __forceinline__ bool grid_barrier(BarrierState *bs, unsigned long lon
     }
     __syncthreads();
     return ok != 0;
+}
+
+__device__ __forceinline__ bool grid_barrier(BarrierState *bs, unsigned long long limit_ns) {
+    return grid_barrier(bs, limit_ns, gridDim.x);
 }
 
 }  // namespace ttgb

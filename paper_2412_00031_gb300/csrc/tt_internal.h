@@ -1,6 +1,7 @@
 // Host-side declarations shared by the translation units of libttgb.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "tt_common.cuh"
@@ -16,6 +17,13 @@ struct Schedule {
     int n_planes = 0;
     int lo = 0;  // first swept index on every axis (1 = interior sweep, 0 = all nodes)
     int na = 0, nb = 0, nc = 0;
+};
+
+// Tile schedule of one tile shape: tiles (I << 20 | J << 10 | K) grouped by I + J + K.
+struct TileSchedule {
+    unsigned int *tiles = nullptr;
+    int *off = nullptr;
+    int n_planes = 0;
 };
 
 template <typename F> struct GeoTab {
@@ -44,6 +52,15 @@ template <typename F> struct FwdArgs {
     F tol;
     int max_iter;
     unsigned long long spin_ns;
+    // tile-wavefront schedule (fwd_tile_kernel): tiles of one sweep grouped by tile hyperplane
+    const unsigned int *tiles;
+    const int *toff;
+    int n_tplanes;
+    int na, nb, nc;   // interior extent swept
+    int ngroups;      // groups of 32 sources
+    // barrier groups of the node schedule: blocks [g * grp_blocks, (g + 1) * grp_blocks) solve
+    // the sources [g * grp_src, min(B, (g + 1) * grp_src)) with their own barrier bar[g]
+    int n_bgroups, grp_blocks, grp_src;
 };
 
 template <typename F> struct AdjArgs {
@@ -56,6 +73,8 @@ template <typename F> struct AdjArgs {
     const F *cost, *costf, *h2, *arf;
     const int *sidx;           // [N] index into JS or kNone
     const F *JS;               // [n_heads][B] J_c S_c of Eq. 5's point sources
+    Vec4<F> *coef;             // [N][B]: A a / delta on the +r, +theta, +phi faces; J_c S_c
+    int n_bgroups, grp_blocks, grp_src;  // barrier groups (as in FwdArgs)
     const unsigned int *nodes;
     const int *off;
     BarrierState *bar;
@@ -72,6 +91,25 @@ template <typename F> cudaError_t launch_forward(const FwdArgs<F> &a, int grid, 
 template <typename F> cudaError_t launch_adjoint(const AdjArgs<F> &a, int grid, int block,
                                                  cudaStream_t st);
 template <typename F> int forward_blocks_per_sm(int block, size_t smem);
+
+// Tile shapes of the tile-wavefront forward sweep (sweep-local a = r, b = theta, c = phi).
+struct TileShape {
+    int ta, tb, tc;
+};
+constexpr int kNumTileShapes = 3;
+constexpr TileShape kTileShapes[kNumTileShapes] = {{4, 8, 8}, {4, 4, 8}, {2, 8, 8}};
+template <typename F> size_t forward_tiled_smem(int shape, int B);
+template <typename F>
+cudaError_t launch_forward_tiled(const CUtensorMap &map_tau, const CUtensorMap &map_rec,
+                                 const FwdArgs<F> &a, int shape, int grid, cudaStream_t st);
+template <typename F> int forward_tiled_blocks_per_sm(int shape, int B);
+constexpr int kTileThreads = 256;
+constexpr int kMaxBarrierGroups = 8;
 template <typename F> int adjoint_blocks_per_sm(int block, size_t smem);
+// Face-coefficient adjoint: coefficients once per solve, then the sweep over P.
+template <typename F> cudaError_t launch_adjoint_coefs(const AdjArgs<F> &a, cudaStream_t st);
+template <typename F> cudaError_t launch_adjoint_faces(const AdjArgs<F> &a, int grid, int block,
+                                                       cudaStream_t st);
+template <typename F> int adjoint_faces_blocks_per_sm(int block, size_t smem);
 
 }  // namespace ttgb

@@ -7,6 +7,7 @@
 // stride over the plane's nodes. With B >= 32 a warp reads 32 consecutive sources of one
 // node, so every field access is a coalesced 128-byte line and the per-node model values
 // are warp-wide broadcasts. Between hyperplanes the launch crosses a bounded grid barrier.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "tt_internal.h"
@@ -31,12 +32,8 @@ __device__ __forceinline__ void unpack(unsigned int pk, int &a, int &b, int &c) 
 
 // ------------------------------------------------------------------------ forward sweep
 
-// Lax-Friedrichs update of tau at interior node (i, j, k) for source b. Dividing the
-// update by T0: with u = p0 / T0 and e_d = 1 / (2 delta_d h_d),
-//   v = tau_c u + ((tau_d+ - tau_d-) e_d)_d,     H / T0 = sqrt(v^T M v)
-//   tau_new = [s / T0 - H / T0 + sum_d c_d (tau_d+ + tau_d-)] / (2 sum_d c_d)
-// where c_d = kappa_d e_d and kappa = (1, sqrt(1 - 2 xi), sqrt(1 + 2 xi)) bounds
-// |dH/dp_d| / sqrt... (Cauchy-Schwarz), the Lax-Friedrichs viscosity.
+// Lax-Friedrichs update of tau at interior node (i, j, k) for source b, reading the six
+// neighbours from global memory (node-hyperplane schedule).
 template <typename F>
 __device__ __forceinline__ F fwd_update(const FwdArgs<F> &a, const SrcReg<F> &S, int b, int i,
                                         int j, int k, long long n, F &told) {
@@ -52,23 +49,15 @@ __device__ __forceinline__ F fwd_update(const FwdArgs<F> &a, const SrcReg<F> &S,
     F r = __ldg(a.rad + i), cth = __ldg(a.cost + j), sth = __ldg(a.sint + j);
     Vec2<F> tT = a.tabT[(long long)j * B + b];
     Vec2<F> tP = a.tabP[(long long)k * B + b];
-    F ur, ut, up;
-    F invT0 = factor_T0<F>(S, i, r, cth, sth, tT, tP, a.g.flat != 0, ur, ut, up);
-    F vr = tc * ur + (trp - trm) * a.er;
-    F vt = tc * ut + (ttp - ttm) * R.et;
-    F vp = tc * up + (tpp - tpm) * R.ep;
-    F q = vr * vr + ((F)1 - (F)2 * R.xi) * vt * vt + ((F)1 + (F)2 * R.xi) * vp * vp
-          + (F)4 * R.eta * vt * vp;
-    F H = sqrt_(q);
-    F num = R.s * invT0 - H + a.er * (trp + trm) + R.ct * (ttp + ttm) + R.cp * (tpp + tpm);
     told = tc;
-    return num * R.invW;
+    return lf_update<F>(S, i, tc, trp, trm, ttp, ttm, tpp, tpm, R, r, cth, sth, tT, tP,
+                        a.g.flat != 0, a.er);
 }
 
 // tau on one face layer = max(2 tau_1 - tau_2, tau_2); q enumerates both faces of an axis.
 template <typename F>
 __device__ __forceinline__ void extrapolate(const FwdArgs<F> &a, const SrcReg<F> &S, int b,
-                                            int axis, int slot) {
+                                            int axis, int slot, int slots) {
     const GridC &g = a.g;
     const long long B = a.B;
     int n1, n2, nface;
@@ -77,7 +66,7 @@ __device__ __forceinline__ void extrapolate(const FwdArgs<F> &a, const SrcReg<F>
     else if (axis == 1) { n1 = g.nr; n2 = g.np; nface = g.nt; stride = g.np; }
     else { n1 = g.nr; n2 = g.nt; nface = g.np; stride = 1; }
     const int per_face = n1 * n2;
-    for (int q = slot; q < 2 * per_face; q += a.slots) {
+    for (int q = slot; q < 2 * per_face; q += slots) {
         int hi = q >= per_face;
         int rem = hi ? q - per_face : q;
         int u = rem / n2, v = rem - u * n2;
@@ -96,6 +85,11 @@ __device__ __forceinline__ void extrapolate(const FwdArgs<F> &a, const SrcReg<F>
     }
 }
 
+// Node-hyperplane schedule. The launch is split into barrier groups: group g owns a
+// contiguous slice of the sources and a contiguous range of blocks, runs the whole solve of
+// its slice with its own grid barrier and convergence test, and so never waits for another
+// group; on each SM the warps of one group keep issuing while another group's warps wait at
+// their barrier.
 template <typename F>
 __global__ void __launch_bounds__(512) fwd_sweep_kernel(FwdArgs<F> a) {
     extern __shared__ unsigned char smem_raw[];
@@ -103,10 +97,18 @@ __global__ void __launch_bounds__(512) fwd_sweep_kernel(FwdArgs<F> a) {
     __shared__ int s_cnt;
     const GridC &g = a.g;
     const int B = a.B;
-    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool lane_ok = tid < (long long)a.slots * B;
-    const int b = lane_ok ? (int)(tid % B) : 0;
-    const int slot = lane_ok ? (int)(tid / B) : 0;
+    const int grp = blockIdx.x / a.grp_blocks;
+    const int blk = blockIdx.x - grp * a.grp_blocks;   // block index within the group
+    const int src0 = grp * a.grp_src;
+    const int Bg = min(B, src0 + a.grp_src) - src0;   // sources of this group
+    if (Bg <= 0) return;
+    BarrierState *bar = a.bar + grp;
+    const unsigned nblk = (unsigned)a.grp_blocks;
+    const int slots = (int)(((long long)a.grp_blocks * blockDim.x) / Bg);
+    const long long tid = (long long)blk * blockDim.x + threadIdx.x;
+    const bool lane_ok = tid < (long long)slots * Bg;
+    const int b = src0 + (lane_ok ? (int)(tid % Bg) : 0);
+    const int slot = lane_ok ? (int)(tid / Bg) : 0;
     const SrcReg<F> S = load_src<F>(a.src, b, g.dr);
 
     for (int it = 0; it < a.max_iter; ++it) {
@@ -117,7 +119,7 @@ __global__ void __launch_bounds__(512) fwd_sweep_kernel(FwdArgs<F> a) {
             for (int L = 0; L < a.n_planes; ++L) {
                 if (active) {
                     const int q1 = __ldg(a.off + L + 1);
-                    for (int q = __ldg(a.off + L) + slot; q < q1; q += a.slots) {
+                    for (int q = __ldg(a.off + L) + slot; q < q1; q += slots) {
                         int aa, bb, cc;
                         unpack(__ldg(a.nodes + q), aa, bb, cc);
                         const int i = rr ? g.nr - 2 - aa : 1 + aa;
@@ -131,19 +133,289 @@ __global__ void __launch_bounds__(512) fwd_sweep_kernel(FwdArgs<F> a) {
                         err = fmax_(err, fabs(tn - told));
                     }
                 }
-                if (!grid_barrier(a.bar, a.spin_ns)) return;
+                if (!grid_barrier(bar, a.spin_ns, nblk)) return;
             }
             for (int axis = 0; axis < 3; ++axis) {
-                if (active) extrapolate<F>(a, S, b, axis, slot);
-                if (!grid_barrier(a.bar, a.spin_ns)) return;
+                if (active) extrapolate<F>(a, S, b, axis, slot, slots);
+                if (!grid_barrier(bar, a.spin_ns, nblk)) return;
             }
         }
         // Per-source largest update of this iteration: block maximum, then a fixed-order
-        // maximum over blocks by block 0, which also decides convergence.
+        // maximum over the group's blocks by its first block, which also decides convergence.
+        for (int x = threadIdx.x; x < Bg; x += blockDim.x) s_err[x] = 0;
+        __syncthreads();
+        if (active) atomic_max_nonneg(&s_err[b - src0], err);
+        __syncthreads();
+        for (int x = threadIdx.x; x < Bg; x += blockDim.x)
+            a.partial[(long long)blockIdx.x * B + src0 + x] = s_err[x];
+        if (!grid_barrier(bar, a.spin_ns, nblk)) return;
+        if (blk == 0) {
+            if (threadIdx.x == 0) s_cnt = 0;
+            __syncthreads();
+            for (int x = src0 + threadIdx.x; x < src0 + Bg; x += blockDim.x) {
+                if (a.conv[x]) continue;
+                F m = 0;
+                for (int c = grp * a.grp_blocks; c < (grp + 1) * a.grp_blocks; ++c)
+                    m = fmax_(m, ((volatile F *)a.partial)[(long long)c * B + x]);
+                a.iters[x] = it + 1;
+                if (m < a.tol) a.conv[x] = 1;
+                else atomicAdd(&s_cnt, 1);
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) ((volatile int *)a.n_active)[grp] = s_cnt;
+        }
+        if (!grid_barrier(bar, a.spin_ns, nblk)) return;
+        if (((volatile int *)a.n_active)[grp] == 0) break;
+    }
+}
+
+// ------------------------------------------------------------------------ tiled forward sweep
+//
+// Tile wavefront (Sec. 3.4 applied to tiles). The interior swept by one ordering is cut into
+// TA x TB x TC tiles in sweep-local coordinates; tiles with the same I + J + K share no
+// face, so they run concurrently, and one bounded grid barrier separates consecutive tile
+// hyperplanes. A block task is (tile, group of 32 sources). One thread issues two TMA
+// tensor copies: the tile with a one-node halo of tau for those 32 sources (a 4-D box
+// sources x phi x theta x r of the [node][source] field) and the tile's per-node records.
+// The box lands in shared memory in physical order, so the six neighbours of a node are at
+// fixed offsets. The block then runs the tile's node hyperplanes in sweep order with block
+// barriers (every node sees exactly the neighbour values of the lexicographic sweep) and
+// writes the tile back with coalesced 128-byte stores (lanes = sources).
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// Bounded wait on an mbarrier phase; false when the limit expired.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity,
+                                          unsigned long long limit_ns) {
+    const unsigned sa = smem_u32(bar);
+    unsigned long long t0 = 0;
+    for (int spin = 0;; ++spin) {
+        unsigned ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(sa), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (spin == 0) t0 = global_ns();
+        else if (global_ns() - t0 > limit_ns) return false;
+    }
+}
+
+__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, int c0, int c1,
+                                            int c2, int c3, unsigned long long *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3),
+        "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+template <int TA, int TB, int TC> struct TileDims {
+    static constexpr int HA = TA + 2, HB = TB + 2, HC = TC + 2;
+    static constexpr int ROWS = HA * HB * HC;              // halo'd nodes staged per task
+    static constexpr int NODES = TA * TB * TC;
+    static constexpr int PLANES = TA + TB + TC - 2;
+    static constexpr int SA = HB * HC * 32, SB = HC * 32;  // smem strides (elements)
+};
+
+template <typename F, int TA, int TB, int TC> struct TileSmem {
+    using D = TileDims<TA, TB, TC>;
+    static constexpr size_t tau = 0;
+    static constexpr size_t rec = tau + sizeof(F) * D::ROWS * 32;
+    static constexpr size_t tabT = rec + sizeof(NodeRec<F>) * D::NODES;
+    static constexpr size_t tabP = tabT + sizeof(Vec2<F>) * TB * 32;
+    static constexpr size_t plist = tabP + sizeof(Vec2<F>) * TC * 32;
+    static constexpr size_t poff = plist + sizeof(unsigned short) * D::NODES;
+    static constexpr size_t err = (poff + sizeof(int) * (D::PLANES + 1) + 15) / 16 * 16;
+    static_assert(rec % 128 == 0, "TMA destinations need 128-byte alignment");
+};
+
+template <typename F, int TA, int TB, int TC>
+__device__ __forceinline__ bool forward_tile(const FwdArgs<F> &a, const CUtensorMap *map_tau,
+                                             const CUtensorMap *map_rec, int I, int J, int K,
+                                             int grp, bool rr, bool rt, bool rp,
+                                             unsigned char *smem, unsigned long long *bar,
+                                             unsigned &parity, F *s_err) {
+    using D = TileDims<TA, TB, TC>;
+    using L = TileSmem<F, TA, TB, TC>;
+    F *s_tau = reinterpret_cast<F *>(smem + L::tau);
+    const NodeRec<F> *s_rec = reinterpret_cast<const NodeRec<F> *>(smem + L::rec);
+    Vec2<F> *s_tT = reinterpret_cast<Vec2<F> *>(smem + L::tabT);
+    Vec2<F> *s_tP = reinterpret_cast<Vec2<F> *>(smem + L::tabP);
+    const unsigned short *s_plist = reinterpret_cast<const unsigned short *>(smem + L::plist);
+    const int *s_poff = reinterpret_cast<const int *>(smem + L::poff);
+    const GridC &g = a.g;
+    const int B = a.B;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    const int a0 = I * TA, b0 = J * TB, c0 = K * TC;
+    // physical index of the tile's first interior node on each axis (lowest index)
+    const int i_lo = rr ? g.nr - 1 - a0 - TA : 1 + a0;
+    const int j_lo = rt ? g.nt - 1 - b0 - TB : 1 + b0;
+    const int k_lo = rp ? g.np - 1 - c0 - TC : 1 + c0;
+
+    if (threadIdx.x == 0) {
+        fence_proxy_async_smem();
+        mbar_expect_tx(bar, (unsigned)(sizeof(F) * (D::ROWS * 32 + D::NODES * 8)));
+        tma_load_4d(s_tau, map_tau, grp * 32, k_lo - 1, j_lo - 1, i_lo - 1, bar);
+        tma_load_4d(smem + L::rec, map_rec, 0, k_lo, j_lo, i_lo, bar);
+    }
+    const int bsrc = grp * 32 + lane;
+    const bool valid = bsrc < B;
+    const bool active = valid && ((volatile int *)a.conv)[bsrc] == 0;
+    const SrcReg<F> S = load_src<F>(a.src, valid ? bsrc : 0, g.dr);
+    for (int q = warp; q < TB; q += nwarps) {
+        const int lb = b0 + q;
+        Vec2<F> v = {(F)0, (F)0};
+        if (valid && lb < a.nb) v = a.tabT[(long long)(rt ? g.nt - 2 - lb : 1 + lb) * B + bsrc];
+        s_tT[q * 32 + lane] = v;
+    }
+    for (int q = warp; q < TC; q += nwarps) {
+        const int lc = c0 + q;
+        Vec2<F> v = {(F)0, (F)0};
+        if (valid && lc < a.nc) v = a.tabP[(long long)(rp ? g.np - 2 - lc : 1 + lc) * B + bsrc];
+        s_tP[q * 32 + lane] = v;
+    }
+    const bool landed = mbar_wait(bar, parity, a.spin_ns);
+    if (!landed) {
+        // record the failure, then give the copies in flight one more bounded wait before
+        // this block stops using its shared memory
+        atomicExch(&a.bar->status, (int)kDevTimeout);
+        mbar_wait(bar, parity, a.spin_ns);
+    }
+    parity ^= 1u;
+    __syncthreads();
+    if (ld_status(&a.bar->status) != 0) return false;
+
+    F err = 0;
+    for (int l = 0; l < D::PLANES; ++l) {
+        for (int e = s_poff[l] + warp; e < s_poff[l + 1]; e += nwarps) {
+            const unsigned pk = s_plist[e];
+            const int ta = pk >> 10, tb = (pk >> 5) & 31, tc = pk & 31;
+            const int la = a0 + ta, lb = b0 + tb, lc = c0 + tc;
+            if (la >= a.na || lb >= a.nb || lc >= a.nc) continue;
+            const int i = rr ? g.nr - 2 - la : 1 + la;
+            const int j = rt ? g.nt - 2 - lb : 1 + lb;
+            const int k = rp ? g.np - 2 - lc : 1 + lc;
+            if (!active || in_fixed_set(S.ci, S.cj, S.ck, i, j, k)) continue;
+            const int pa = i - i_lo + 1, pb = j - j_lo + 1, pc = k - k_lo + 1;
+            F *p = s_tau + ((pa * D::HB + pb) * D::HC + pc) * 32 + lane;
+            const F t0 = p[0];
+            const NodeRec<F> R = s_rec[((pa - 1) * TB + (pb - 1)) * TC + (pc - 1)];
+            const F r = __ldg(a.rad + i), cth = __ldg(a.cost + j), sth = __ldg(a.sint + j);
+            const F tn = lf_update<F>(S, i, t0, p[D::SA], p[-D::SA], p[D::SB], p[-D::SB], p[32],
+                                      p[-32], R, r, cth, sth, s_tT[tb * 32 + lane],
+                                      s_tP[tc * 32 + lane], g.flat != 0, a.er);
+            p[0] = tn;
+            err = fmax_(err, fabs(tn - t0));
+        }
+        __syncthreads();
+    }
+
+    // write the tile back (only sources that are still iterating changed anything)
+    if (active) {
+        for (int e = warp; e < D::NODES; e += nwarps) {
+            const int qa = e / (TB * TC), rem = e - qa * (TB * TC);
+            const int qb = rem / TC, qc = rem - qb * TC;
+            const int i = i_lo + qa, j = j_lo + qb, k = k_lo + qc;
+            if (i < 1 || j < 1 || k < 1 || i > g.nr - 2 || j > g.nt - 2 || k > g.np - 2) continue;
+            a.tau[node_index(g, i, j, k) * B + bsrc] =
+                s_tau[(((qa + 1) * D::HB + (qb + 1)) * D::HC + (qc + 1)) * 32 + lane];
+        }
+        atomic_max_nonneg(&s_err[bsrc], err);
+    }
+    __syncthreads();
+    return true;
+}
+
+template <typename F, int TA, int TB, int TC>
+__global__ void __launch_bounds__(kTileThreads)
+    fwd_tile_kernel(const __grid_constant__ CUtensorMap map_tau,
+                    const __grid_constant__ CUtensorMap map_rec, FwdArgs<F> a) {
+    using D = TileDims<TA, TB, TC>;
+    using L = TileSmem<F, TA, TB, TC>;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    F *s_err = reinterpret_cast<F *>(smem + L::err);
+    int *s_gact = reinterpret_cast<int *>(s_err + a.B);
+    __shared__ int s_cnt;
+    __shared__ __align__(8) unsigned long long bar;
+    const GridC &g = a.g;
+    const int B = a.B;
+    // per-plane node lists of one tile, in sweep-local coordinates (ta << 10 | tb << 5 | tc)
+    if (threadIdx.x == 0) {
+        unsigned short *plist = reinterpret_cast<unsigned short *>(smem + L::plist);
+        int *poff = reinterpret_cast<int *>(smem + L::poff);
+        int q = 0;
+        for (int l = 0; l < D::PLANES; ++l) {
+            poff[l] = q;
+            for (int ta = 0; ta < TA; ++ta)
+                for (int tb = 0; tb < TB; ++tb) {
+                    const int tc = l - ta - tb;
+                    if (tc >= 0 && tc < TC) plist[q++] = (unsigned short)((ta << 10) | (tb << 5) | tc);
+                }
+        }
+        poff[D::PLANES] = q;
+        mbar_init(&bar);
+    }
+    __syncthreads();
+    unsigned parity = 0;
+    // face extrapolation keeps the one-source-per-thread mapping of the node schedule
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool lane_ok = tid < (long long)a.slots * B;
+    const int bx = lane_ok ? (int)(tid % B) : 0;
+    const int slot = lane_ok ? (int)(tid / B) : 0;
+    const SrcReg<F> Sx = load_src<F>(a.src, bx, g.dr);
+
+    for (int it = 0; it < a.max_iter; ++it) {
+        const bool act_x = lane_ok && ((volatile int *)a.conv)[bx] == 0;
         for (int x = threadIdx.x; x < B; x += blockDim.x) s_err[x] = 0;
+        for (int q = threadIdx.x; q < a.ngroups; q += blockDim.x) {
+            int any = 0;
+            for (int x = q * 32; x < min(B, q * 32 + 32); ++x)
+                any |= ((volatile int *)a.conv)[x] == 0;
+            s_gact[q] = any;
+        }
         __syncthreads();
-        if (active) atomic_max_nonneg(&s_err[b], err);
-        __syncthreads();
+        for (int o = 0; o < 8; ++o) {
+            const bool rr = o & 4, rt = o & 2, rp = o & 1;
+            for (int Lp = 0; Lp < a.n_tplanes; ++Lp) {
+                const int t0 = __ldg(a.toff + Lp);
+                const int ntask = (__ldg(a.toff + Lp + 1) - t0) * a.ngroups;
+                for (int task = blockIdx.x; task < ntask; task += gridDim.x) {
+                    const int grp = task % a.ngroups;
+                    if (!s_gact[grp]) continue;
+                    int I, J, K;
+                    unpack(__ldg(a.tiles + t0 + task / a.ngroups), I, J, K);
+                    if (!forward_tile<F, TA, TB, TC>(a, &map_tau, &map_rec, I, J, K, grp, rr, rt,
+                                                     rp, smem, &bar, parity, s_err))
+                        return;
+                }
+                if (!grid_barrier(a.bar, a.spin_ns)) return;
+            }
+            for (int axis = 0; axis < 3; ++axis) {
+                if (act_x) extrapolate<F>(a, Sx, bx, axis, slot, a.slots);
+                if (!grid_barrier(a.bar, a.spin_ns)) return;
+            }
+        }
         for (int x = threadIdx.x; x < B; x += blockDim.x)
             a.partial[(long long)blockIdx.x * B + x] = s_err[x];
         if (!grid_barrier(a.bar, a.spin_ns)) return;
@@ -359,6 +631,182 @@ __global__ void __launch_bounds__(512) adj_sweep_kernel(AdjArgs<F> a) {
     }
 }
 
+// ------------------------------------------------------------------------ face-coefficient adjoint
+//
+// The flux velocities of Eq. 5 depend only on T, xi and eta, which stay fixed during the
+// adjoint solve. adj_coef_kernel evaluates, once per solve and per (node, source), the
+// signed coefficients c_d = A_d a_d / delta_d on the node's +r, +theta and +phi faces (zero
+// on the outer boundary) and J_c S_c; the sweep then needs only P and these coefficients:
+//   out = sum_d [max(c_d+, 0) - min(c_d-, 0)],
+//   in  = sum_d [max(c_d-, 0) P_d- - min(c_d+, 0) P_d+],   P_c = (J_c S_c + in) / out,
+// where c_d- is the +face coefficient of the - neighbour (the same face). These are the
+// same products as in adj_update, evaluated once instead of every sweep.
+
+template <typename F>
+__device__ __forceinline__ void plus_face_coefs(const AdjArgs<F> &a, int b, int i, int j, int k,
+                                                long long n, F &cr, F &ct, F &cp) {
+    const GridC &g = a.g;
+    const long long B = a.B;
+    const long long sp = B, st = (long long)g.np * B, sr = (long long)g.nt * g.np * B;
+    const long long x = n * B + b;
+    const F *T = a.T;
+    const bool hr = i < g.nr - 1, ht = j < g.nt - 1, lt = j > 0, hp = k < g.np - 1, lp = k > 0;
+    const F dr = (F)g.dr, dt = (F)g.dt, dp = (F)g.dp;
+    const F idt = (F)1 / dt, idp = (F)1 / dp, i2dt = (F)0.5 * idt, i2dp = (F)0.5 * idp;
+    const F idr = (F)1 / dr;
+    const F Tc = T[x];
+    const F Ttp = ht ? T[x + st] : Tc, Ttm = lt ? T[x - st] : Tc;
+    const F Tpp = hp ? T[x + sp] : Tc, Tpm = lp ? T[x - sp] : Tc;
+    const F Tpp_tp = (ht && hp) ? T[x + st + sp] : Tc, Tpm_tp = (ht && lp) ? T[x + st - sp] : Tc;
+    const F Tpp_tm = (lt && hp) ? T[x - st + sp] : Tc;
+    const F xic = __ldg(a.xi + n), etc = __ldg(a.eta + n);
+    const F h2 = __ldg(a.h2 + i), cth = __ldg(a.cost + j);
+    const F h3 = h2 * cth;
+    const F dphi_c = d_axis<F>(Tpm, Tc, Tpp, k, g.np, idp, i2dp);
+    const F dth_c = d_axis<F>(Ttm, Tc, Ttp, j, g.nt, idt, i2dt);
+    cr = ct = cp = (F)0;
+    if (hr) {
+        F av = -(T[x + sr] - Tc) * idr;
+        F A = __ldg(a.arf + i) * cth * idr;
+        cr = A * av;
+    }
+    if (ht) {
+        const long long nn = n + g.np;
+        F xh = (F)0.5 * (xic + __ldg(a.xi + nn)), eh = (F)0.5 * (etc + __ldg(a.eta + nn));
+        F h3f = h2 * __ldg(a.costf + j);
+        F dphi_n = d_axis<F>(Tpm_tp, Ttp, Tpp_tp, k, g.np, idp, i2dp);
+        F pt = (Ttp - Tc) * idt / h2;
+        F pp = (F)0.5 * (dphi_c + dphi_n) / h3f;
+        F av = -(((F)1 - (F)2 * xh) * pt + (F)2 * eh * pp);
+        F A = h3f * idt;
+        ct = A * av;
+    }
+    if (hp) {
+        const long long nn = n + 1;
+        F xh = (F)0.5 * (xic + __ldg(a.xi + nn)), eh = (F)0.5 * (etc + __ldg(a.eta + nn));
+        F dth_n = d_axis<F>(Tpp_tm, Tpp, Tpp_tp, j, g.nt, idt, i2dt);
+        F pp = (Tpp - Tc) * idp / h3;
+        F pt = (F)0.5 * (dth_c + dth_n) / h2;
+        F av = -((F)2 * eh * pt + ((F)1 + (F)2 * xh) * pp);
+        F A = h2 * idp;
+        cp = A * av;
+    }
+}
+
+template <typename F> __global__ void adj_coef_kernel(AdjArgs<F> a) {
+    const GridC &g = a.g;
+    const long long total = g.N * a.B;
+    for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < total;
+         x += (long long)gridDim.x * blockDim.x) {
+        const int b = (int)(x % a.B);
+        const long long n = x / a.B;
+        const int k = (int)(n % g.np);
+        const long long t = n / g.np;
+        const int j = (int)(t % g.nt), i = (int)(t / g.nt);
+        Vec4<F> c;
+        plus_face_coefs<F>(a, b, i, j, k, n, c.x, c.y, c.z);
+        const int h = __ldg(a.sidx + n);
+        c.w = h != kNone ? a.JS[(long long)h * a.B + b] : (F)0;
+        a.coef[x] = c;
+    }
+}
+
+template <typename F>
+__global__ void __launch_bounds__(256) adj_face_kernel(AdjArgs<F> a) {
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ int s_cnt;
+    const GridC &g = a.g;
+    const int B = a.B;
+    const int grp = blockIdx.x / a.grp_blocks;
+    const int blk = blockIdx.x - grp * a.grp_blocks;
+    const int src0 = grp * a.grp_src;
+    const int Bg = min(B, src0 + a.grp_src) - src0;
+    if (Bg <= 0) return;
+    F *s_err = reinterpret_cast<F *>(smem_raw);
+    F *s_pmax = s_err + Bg;
+    BarrierState *bar = a.bar + grp;
+    const unsigned nblk = (unsigned)a.grp_blocks;
+    const int slots = (int)(((long long)a.grp_blocks * blockDim.x) / Bg);
+    const long long tid = (long long)blk * blockDim.x + threadIdx.x;
+    const bool lane_ok = tid < (long long)slots * Bg;
+    const int b = src0 + (lane_ok ? (int)(tid % Bg) : 0);
+    const int slot = lane_ok ? (int)(tid / Bg) : 0;
+    const int ci = a.src[b].ci, cj = a.src[b].cj, ck = a.src[b].ck;
+    const long long sp = B, st = (long long)g.np * B, sr = (long long)g.nt * g.np * B;
+
+    for (int it = 0; it < a.max_iter; ++it) {
+        const bool active = lane_ok && ((volatile int *)a.conv)[b] == 0;
+        F err = 0, pmax = 0;
+        for (int o = 0; o < 8; ++o) {
+            const bool rr = o & 4, rt = o & 2, rp = o & 1;
+            for (int L = 0; L < a.n_planes; ++L) {
+                if (active) {
+                    const int q1 = __ldg(a.off + L + 1);
+                    for (int q = __ldg(a.off + L) + slot; q < q1; q += slots) {
+                        int aa, bb, cc;
+                        unpack(__ldg(a.nodes + q), aa, bb, cc);
+                        const int i = rr ? g.nr - 1 - aa : aa;
+                        const int j = rt ? g.nt - 1 - bb : bb;
+                        const int k = rp ? g.np - 1 - cc : cc;
+                        if (in_fixed_set(ci, cj, ck, i, j, k)) continue;
+                        const long long x = node_index(g, i, j, k) * B + b;
+                        const Vec4<F> c = a.coef[x];
+                        const F cr_m = i > 0 ? a.coef[x - sr].x : (F)0;
+                        const F ct_m = j > 0 ? a.coef[x - st].y : (F)0;
+                        const F cp_m = k > 0 ? a.coef[x - sp].z : (F)0;
+                        F *P = a.P;
+                        const F Prp = i < g.nr - 1 ? P[x + sr] : (F)0, Prm = i > 0 ? P[x - sr] : (F)0;
+                        const F Ptp = j < g.nt - 1 ? P[x + st] : (F)0, Ptm = j > 0 ? P[x - st] : (F)0;
+                        const F Ppp = k < g.np - 1 ? P[x + sp] : (F)0, Ppm = k > 0 ? P[x - sp] : (F)0;
+                        const F out = fmax_(c.x, (F)0) - fmin(cr_m, (F)0) + fmax_(c.y, (F)0) -
+                                      fmin(ct_m, (F)0) + fmax_(c.z, (F)0) - fmin(cp_m, (F)0);
+                        const F in = fmax_(cr_m, (F)0) * Prm - fmin(c.x, (F)0) * Prp +
+                                     fmax_(ct_m, (F)0) * Ptm - fmin(c.y, (F)0) * Ptp +
+                                     fmax_(cp_m, (F)0) * Ppm - fmin(c.z, (F)0) * Ppp;
+                        const F pn = out <= (F)1e-30 ? (F)0 : (c.w + in) / out;
+                        const F pold = P[x];
+                        P[x] = pn;
+                        err = fmax_(err, fabs(pn - pold));
+                        if (o == 7) pmax = fmax_(pmax, fabs(pn));
+                    }
+                }
+                if (!grid_barrier(bar, a.spin_ns, nblk)) return;
+            }
+        }
+        for (int x = threadIdx.x; x < Bg; x += blockDim.x) { s_err[x] = 0; s_pmax[x] = 0; }
+        __syncthreads();
+        if (active) {
+            atomic_max_nonneg(&s_err[b - src0], err);
+            atomic_max_nonneg(&s_pmax[b - src0], pmax);
+        }
+        __syncthreads();
+        for (int x = threadIdx.x; x < Bg; x += blockDim.x) {
+            a.partial[((long long)blockIdx.x * 2) * B + src0 + x] = s_err[x];
+            a.partial[((long long)blockIdx.x * 2 + 1) * B + src0 + x] = s_pmax[x];
+        }
+        if (!grid_barrier(bar, a.spin_ns, nblk)) return;
+        if (blk == 0) {
+            if (threadIdx.x == 0) s_cnt = 0;
+            __syncthreads();
+            for (int x = src0 + threadIdx.x; x < src0 + Bg; x += blockDim.x) {
+                if (a.conv[x]) continue;
+                F m = 0, pm = 0;
+                for (int c = grp * a.grp_blocks; c < (grp + 1) * a.grp_blocks; ++c) {
+                    m = fmax_(m, ((volatile F *)a.partial)[((long long)c * 2) * B + x]);
+                    pm = fmax_(pm, ((volatile F *)a.partial)[((long long)c * 2 + 1) * B + x]);
+                }
+                a.iters[x] = it + 1;
+                if (m <= a.tol * pm) a.conv[x] = 1;
+                else atomicAdd(&s_cnt, 1);
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) ((volatile int *)a.n_active)[grp] = s_cnt;
+        }
+        if (!grid_barrier(bar, a.spin_ns, nblk)) return;
+        if (((volatile int *)a.n_active)[grp] == 0) break;
+    }
+}
+
 // ------------------------------------------------------------------------ launchers
 
 template <typename F>
@@ -392,6 +840,91 @@ template <typename F> int adjoint_blocks_per_sm(int block, size_t smem) {
         return 0;
     return n;
 }
+
+template <typename F, int TA, int TB, int TC> static size_t tiled_smem_bytes(int B) {
+    using L = TileSmem<F, TA, TB, TC>;
+    return L::err + (size_t)B * sizeof(F) + (size_t)((B + 31) / 32) * sizeof(int);
+}
+
+template <typename F> size_t forward_tiled_smem(int shape, int B) {
+    switch (shape) {
+    case 0: return tiled_smem_bytes<F, 4, 8, 8>(B);
+    case 1: return tiled_smem_bytes<F, 4, 4, 8>(B);
+    default: return tiled_smem_bytes<F, 2, 8, 8>(B);
+    }
+}
+
+template <typename F> static const void *tiled_kernel_ptr(int shape) {
+    switch (shape) {
+    case 0: return (const void *)fwd_tile_kernel<F, 4, 8, 8>;
+    case 1: return (const void *)fwd_tile_kernel<F, 4, 4, 8>;
+    default: return (const void *)fwd_tile_kernel<F, 2, 8, 8>;
+    }
+}
+
+template <typename F> int forward_tiled_blocks_per_sm(int shape, int B) {
+    const void *k = tiled_kernel_ptr<F>(shape);
+    size_t smem = forward_tiled_smem<F>(shape, B);
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kTileThreads, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
+template <typename F>
+cudaError_t launch_forward_tiled(const CUtensorMap &map_tau, const CUtensorMap &map_rec,
+                                 const FwdArgs<F> &a, int shape, int grid, cudaStream_t st) {
+    void *args[] = {const_cast<CUtensorMap *>(&map_tau), const_cast<CUtensorMap *>(&map_rec),
+                    const_cast<FwdArgs<F> *>(&a)};
+    return cudaLaunchCooperativeKernel(tiled_kernel_ptr<F>(shape), dim3(grid), dim3(kTileThreads),
+                                       args, forward_tiled_smem<F>(shape, a.B), st);
+}
+
+template <typename F> cudaError_t launch_adjoint_coefs(const AdjArgs<F> &a, cudaStream_t st) {
+    long long total = a.g.N * a.B;
+    long long blocks = (total + 255) / 256;
+    if (blocks > 152LL * 16) blocks = 152LL * 16;
+    adj_coef_kernel<F><<<(unsigned)blocks, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename F>
+cudaError_t launch_adjoint_faces(const AdjArgs<F> &a, int grid, int block, cudaStream_t st) {
+    void *args[] = {const_cast<AdjArgs<F> *>(&a)};
+    size_t smem = (size_t)a.grp_src * 2 * sizeof(F);
+    return cudaLaunchCooperativeKernel((void *)adj_face_kernel<F>, dim3(grid), dim3(block), args,
+                                       smem, st);
+}
+
+template <typename F> int adjoint_faces_blocks_per_sm(int block, size_t smem) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, adj_face_kernel<F>, block, smem) !=
+        cudaSuccess)
+        return 0;
+    return n;
+}
+
+template size_t forward_tiled_smem<float>(int, int);
+template size_t forward_tiled_smem<double>(int, int);
+template int forward_tiled_blocks_per_sm<float>(int, int);
+template int forward_tiled_blocks_per_sm<double>(int, int);
+template cudaError_t launch_forward_tiled<float>(const CUtensorMap &, const CUtensorMap &,
+                                                 const FwdArgs<float> &, int, int, cudaStream_t);
+template cudaError_t launch_forward_tiled<double>(const CUtensorMap &, const CUtensorMap &,
+                                                  const FwdArgs<double> &, int, int, cudaStream_t);
+template cudaError_t launch_adjoint_coefs<float>(const AdjArgs<float> &, cudaStream_t);
+template cudaError_t launch_adjoint_coefs<double>(const AdjArgs<double> &, cudaStream_t);
+template cudaError_t launch_adjoint_faces<float>(const AdjArgs<float> &, int, int, cudaStream_t);
+template cudaError_t launch_adjoint_faces<double>(const AdjArgs<double> &, int, int, cudaStream_t);
+template int adjoint_faces_blocks_per_sm<float>(int, size_t);
+template int adjoint_faces_blocks_per_sm<double>(int, size_t);
 
 template cudaError_t launch_forward<float>(const FwdArgs<float> &, int, int, cudaStream_t);
 template cudaError_t launch_forward<double>(const FwdArgs<double> &, int, int, cudaStream_t);

@@ -94,6 +94,20 @@ def test_launch_shape_does_not_change_bits(tt, blocks):
         assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("schedule,blocks", [(1, 0), (2, 0), (2, 5), (3, 0), (4, 0), (4, 2)])
+def test_sweep_schedules_give_identical_bits(tt, schedule, blocks):
+    """Node hyperplanes and tile hyperplanes of every shape visit each node after its
+    upstream neighbours and before its downstream ones, so the forward result is the same
+    bits whatever the schedule, tile shape or launch size (ragged tiles included)."""
+    w = I.small_case(14, shape=(14, 19, 23), n_src=37, n_rec=5)
+    ref = gpu_solve(w, "f32", opts=tt.default_opts(tt.TT_F32, sweep_schedule=1),
+                    steps=("fwd",))
+    o = tt.default_opts(tt.TT_F32, sweep_schedule=schedule, launch_blocks=blocks)
+    out = gpu_solve(w, "f32", opts=o, steps=("fwd",))
+    assert np.array_equal(out["iters_fwd"], ref["iters_fwd"])
+    assert np.array_equal(out["tau"], ref["tau"])
+
+
 def test_kernels_bitwise_reproducible(tt):
     w = I.small_case(9, shape=(13, 13, 13), n_src=6, n_rec=6)
     a = gpu_solve(w, "f32")
