@@ -227,6 +227,7 @@ def gpu_arm(args, rank, world):
     w = I.anisotropic_batch(seed=I.SEED_BASE + 2 + rank, n_src=args.n_src)
     gp = GpuPath(w, dev)
     gp.opts.sweep_schedule = args.schedule
+    gp.opts.adj_chunk = args.adj_chunk
     if args.max_iter_fwd or args.max_iter_adj:  # profiling runs only: bounded iterations
         gp.opts.max_iter_fwd = args.max_iter_fwd or gp.opts.max_iter_fwd
         gp.opts.max_iter_adj = args.max_iter_adj or gp.opts.max_iter_adj
@@ -415,6 +416,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="profiling runs: skip the e2e leg")
     ap.add_argument("--max-iter-fwd", type=int, default=0, help="profiling runs only")
     ap.add_argument("--max-iter-adj", type=int, default=0, help="profiling runs only")
+    ap.add_argument("--adj-chunk", type=int, default=0,
+                    help="adjoint sources per launch (tt_opts.adj_chunk; 0 = automatic)")
     ap.add_argument("--schedule", type=int, default=0,
                     help="forward sweep schedule (tt_opts.sweep_schedule; 0 = automatic)")
     ap.add_argument("--ref-iters-fwd", type=float, default=30.0)

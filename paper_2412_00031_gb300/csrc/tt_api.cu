@@ -579,29 +579,27 @@ tt_status adjoint_impl(tt_ctx *ctx, const tt_model *m, const tt_point *h_src, in
     int grid, block, slots;
     int n_bgroups = 1, grp_blocks = 0, grp_src = B;
     if (faces) {
+        // Source slices of adj_chunk sources, one cooperative launch each, run one after
+        // another: a hyperplane of one slice (coefficients of two planes, P of three) then
+        // stays in L2. Automatic: slices of at most 128 sources.
         block = 256;
-        int per_sm = 0;
-        for (int tries = 0; tries < 2; ++tries) {
-            size_t smem = (size_t)grp_src * 2 * sizeof(F);
-            per_sm = adjoint_faces_blocks_per_sm<F>(block, smem);
-            if (per_sm > kMaxBarrierGroups) per_sm = kMaxBarrierGroups;
-            n_bgroups = per_sm < 1 ? 1 : per_sm;
-            if (n_bgroups > (B + 31) / 32) n_bgroups = (B + 31) / 32;
-            grp_src = ((B + n_bgroups - 1) / n_bgroups + 31) / 32 * 32;
-            n_bgroups = (B + grp_src - 1) / grp_src;
-        }
+        int chunk = o->adj_chunk > 0 ? o->adj_chunk : 128;
+        grp_src = chunk >= B ? B : (chunk + 31) / 32 * 32;
+        n_bgroups = (B + grp_src - 1) / grp_src;
+        size_t smem = (size_t)grp_src * 2 * sizeof(F);
+        int per_sm = adjoint_faces_blocks_per_sm<F>(block, smem);
         if (per_sm <= 0) return fail(ctx, TT_ECUDA, "adjoint sweep cannot be resident");
+        if (per_sm > 4) per_sm = 4;
         int max_grid = per_sm * ctx->n_sm;
         if (o->launch_blocks > 0 && o->launch_blocks < max_grid) max_grid = o->launch_blocks;
-        if (max_grid < n_bgroups) max_grid = n_bgroups;
-        grp_blocks = max_grid / n_bgroups;
+        grp_blocks = max_grid;
         if ((long long)grp_blocks * block < grp_src) {
             int need = (grp_src + block - 1) / block;
-            if ((long long)need * n_bgroups > (long long)per_sm * ctx->n_sm)
+            if (need > per_sm * ctx->n_sm)
                 return fail(ctx, TT_EINVAL, "batch of %d sources exceeds one resident launch", B);
             grp_blocks = need;
         }
-        grid = grp_blocks * n_bgroups;
+        grid = grp_blocks;
         slots = 0;
         ENSURE(ctx->coef, coef_bytes);
     } else if ((s = sweep_shape<F>(ctx, false, B, ctx->full, o->launch_blocks, grid, block,
@@ -646,10 +644,17 @@ tt_status adjoint_impl(tt_ctx *ctx, const tt_model *m, const tt_point *h_src, in
         ctx->launches += 1;
     }
     CK(cudaEventRecord(ctx->ev_start[TT_STATS_ADJOINT], ctx->st));
-    if (faces) CK(launch_adjoint_faces<F>(a, grid, block, ctx->st));
-    else CK(launch_adjoint<F>(a, grid, block, ctx->st));
+    if (faces) {
+        for (int q = 0; q < n_bgroups; ++q) {
+            a.grp_base = q;
+            CK(launch_adjoint_faces<F>(a, grid, block, ctx->st));
+            ctx->launches += 1;
+        }
+    } else {
+        CK(launch_adjoint<F>(a, grid, block, ctx->st));
+        ctx->launches += 1;
+    }
     CK(cudaEventRecord(ctx->ev_stop[TT_STATS_ADJOINT], ctx->st));
-    ctx->launches += 1;
     ctx->stats[TT_STATS_ADJOINT].grid_blocks = grid;
     ctx->stats[TT_STATS_ADJOINT].block_threads = block;
     tt_status r = finish_solve(ctx, B, h_iters, o->max_iter_adj, "tt_adjoint", TT_STATS_ADJOINT);
@@ -676,6 +681,7 @@ void tt_default_opts(tt_opts *o, int dtype) {
     o->spin_limit_ns = 0;
     o->launch_blocks = 0;
     o->sweep_schedule = 0;
+    o->adj_chunk = 0;
 }
 
 const char *tt_last_error(const tt_ctx *ctx) { return ctx ? ctx->err : "no context"; }

@@ -75,6 +75,7 @@ template <typename F> struct AdjArgs {
     const F *JS;               // [n_heads][B] J_c S_c of Eq. 5's point sources
     Vec4<F> *coef;             // [N][B]: A a / delta on the +r, +theta, +phi faces; J_c S_c
     int n_bgroups, grp_blocks, grp_src;  // barrier groups (as in FwdArgs)
+    int grp_base;              // group index of this launch's first group
     const unsigned int *nodes;
     const int *off;
     BarrierState *bar;

@@ -693,6 +693,8 @@ __device__ __forceinline__ void plus_face_coefs(const AdjArgs<F> &a, int b, int 
     }
 }
 
+constexpr int kAdjBatch = 4;  // nodes whose loads one thread issues together
+
 template <typename F> __global__ void adj_coef_kernel(AdjArgs<F> a) {
     const GridC &g = a.g;
     const long long total = g.N * a.B;
@@ -717,14 +719,15 @@ __global__ void __launch_bounds__(256) adj_face_kernel(AdjArgs<F> a) {
     __shared__ int s_cnt;
     const GridC &g = a.g;
     const int B = a.B;
-    const int grp = blockIdx.x / a.grp_blocks;
-    const int blk = blockIdx.x - grp * a.grp_blocks;
+    const int lgrp = blockIdx.x / a.grp_blocks;         // group within this launch
+    const int blk = blockIdx.x - lgrp * a.grp_blocks;
+    const int grp = a.grp_base + lgrp;
     const int src0 = grp * a.grp_src;
     const int Bg = min(B, src0 + a.grp_src) - src0;
     if (Bg <= 0) return;
     F *s_err = reinterpret_cast<F *>(smem_raw);
     F *s_pmax = s_err + Bg;
-    BarrierState *bar = a.bar + grp;
+    BarrierState *bar = a.bar + lgrp;  // launches of a chunked solve reuse the same words
     const unsigned nblk = (unsigned)a.grp_blocks;
     const int slots = (int)(((long long)a.grp_blocks * blockDim.x) / Bg);
     const long long tid = (long long)blk * blockDim.x + threadIdx.x;
@@ -741,33 +744,56 @@ __global__ void __launch_bounds__(256) adj_face_kernel(AdjArgs<F> a) {
             const bool rr = o & 4, rt = o & 2, rp = o & 1;
             for (int L = 0; L < a.n_planes; ++L) {
                 if (active) {
+                    // Nodes of one hyperplane are independent: load the inputs of up to
+                    // kAdjBatch nodes first, then update them, so their memory latencies
+                    // overlap instead of following one another.
                     const int q1 = __ldg(a.off + L + 1);
-                    for (int q = __ldg(a.off + L) + slot; q < q1; q += slots) {
-                        int aa, bb, cc;
-                        unpack(__ldg(a.nodes + q), aa, bb, cc);
-                        const int i = rr ? g.nr - 1 - aa : aa;
-                        const int j = rt ? g.nt - 1 - bb : bb;
-                        const int k = rp ? g.np - 1 - cc : cc;
-                        if (in_fixed_set(ci, cj, ck, i, j, k)) continue;
-                        const long long x = node_index(g, i, j, k) * B + b;
-                        const Vec4<F> c = a.coef[x];
-                        const F cr_m = i > 0 ? a.coef[x - sr].x : (F)0;
-                        const F ct_m = j > 0 ? a.coef[x - st].y : (F)0;
-                        const F cp_m = k > 0 ? a.coef[x - sp].z : (F)0;
-                        F *P = a.P;
-                        const F Prp = i < g.nr - 1 ? P[x + sr] : (F)0, Prm = i > 0 ? P[x - sr] : (F)0;
-                        const F Ptp = j < g.nt - 1 ? P[x + st] : (F)0, Ptm = j > 0 ? P[x - st] : (F)0;
-                        const F Ppp = k < g.np - 1 ? P[x + sp] : (F)0, Ppm = k > 0 ? P[x - sp] : (F)0;
-                        const F out = fmax_(c.x, (F)0) - fmin(cr_m, (F)0) + fmax_(c.y, (F)0) -
-                                      fmin(ct_m, (F)0) + fmax_(c.z, (F)0) - fmin(cp_m, (F)0);
-                        const F in = fmax_(cr_m, (F)0) * Prm - fmin(c.x, (F)0) * Prp +
-                                     fmax_(ct_m, (F)0) * Ptm - fmin(c.y, (F)0) * Ptp +
-                                     fmax_(cp_m, (F)0) * Ppm - fmin(c.z, (F)0) * Ppp;
-                        const F pn = out <= (F)1e-30 ? (F)0 : (c.w + in) / out;
-                        const F pold = P[x];
-                        P[x] = pn;
-                        err = fmax_(err, fabs(pn - pold));
-                        if (o == 7) pmax = fmax_(pmax, fabs(pn));
+                    for (int q0 = __ldg(a.off + L) + slot; q0 < q1; q0 += kAdjBatch * slots) {
+                        long long xs[kAdjBatch];
+                        bool ok[kAdjBatch];
+                        Vec4<F> c[kAdjBatch];
+                        F cm[kAdjBatch][3], Pn[kAdjBatch][6], Po[kAdjBatch];
+#pragma unroll
+                        for (int u = 0; u < kAdjBatch; ++u) {
+                            const int q = q0 + u * slots;
+                            ok[u] = q < q1;
+                            int aa = 0, bb = 0, cc = 0;
+                            if (ok[u]) unpack(__ldg(a.nodes + q), aa, bb, cc);
+                            const int i = rr ? g.nr - 1 - aa : aa;
+                            const int j = rt ? g.nt - 1 - bb : bb;
+                            const int k = rp ? g.np - 1 - cc : cc;
+                            ok[u] = ok[u] && !in_fixed_set(ci, cj, ck, i, j, k);
+                            const long long x = node_index(g, i, j, k) * B + b;
+                            xs[u] = x;
+                            if (ok[u]) {
+                                const F *P = a.P;
+                                c[u] = a.coef[x];
+                                cm[u][0] = i > 0 ? a.coef[x - sr].x : (F)0;
+                                cm[u][1] = j > 0 ? a.coef[x - st].y : (F)0;
+                                cm[u][2] = k > 0 ? a.coef[x - sp].z : (F)0;
+                                Pn[u][0] = i < g.nr - 1 ? P[x + sr] : (F)0;
+                                Pn[u][1] = i > 0 ? P[x - sr] : (F)0;
+                                Pn[u][2] = j < g.nt - 1 ? P[x + st] : (F)0;
+                                Pn[u][3] = j > 0 ? P[x - st] : (F)0;
+                                Pn[u][4] = k < g.np - 1 ? P[x + sp] : (F)0;
+                                Pn[u][5] = k > 0 ? P[x - sp] : (F)0;
+                                Po[u] = P[x];
+                            }
+                        }
+#pragma unroll
+                        for (int u = 0; u < kAdjBatch; ++u) {
+                            if (!ok[u]) continue;
+                            const F out = fmax_(c[u].x, (F)0) - fmin(cm[u][0], (F)0) +
+                                          fmax_(c[u].y, (F)0) - fmin(cm[u][1], (F)0) +
+                                          fmax_(c[u].z, (F)0) - fmin(cm[u][2], (F)0);
+                            const F in = fmax_(cm[u][0], (F)0) * Pn[u][1] - fmin(c[u].x, (F)0) * Pn[u][0] +
+                                         fmax_(cm[u][1], (F)0) * Pn[u][3] - fmin(c[u].y, (F)0) * Pn[u][2] +
+                                         fmax_(cm[u][2], (F)0) * Pn[u][5] - fmin(c[u].z, (F)0) * Pn[u][4];
+                            const F pn = out <= (F)1e-30 ? (F)0 : (c[u].w + in) / out;
+                            a.P[xs[u]] = pn;
+                            err = fmax_(err, fabs(pn - Po[u]));
+                            if (o == 7) pmax = fmax_(pmax, fabs(pn));
+                        }
                     }
                 }
                 if (!grid_barrier(bar, a.spin_ns, nblk)) return;
@@ -791,7 +817,7 @@ __global__ void __launch_bounds__(256) adj_face_kernel(AdjArgs<F> a) {
             for (int x = src0 + threadIdx.x; x < src0 + Bg; x += blockDim.x) {
                 if (a.conv[x]) continue;
                 F m = 0, pm = 0;
-                for (int c = grp * a.grp_blocks; c < (grp + 1) * a.grp_blocks; ++c) {
+                for (int c = lgrp * a.grp_blocks; c < (lgrp + 1) * a.grp_blocks; ++c) {
                     m = fmax_(m, ((volatile F *)a.partial)[((long long)c * 2) * B + x]);
                     pm = fmax_(pm, ((volatile F *)a.partial)[((long long)c * 2 + 1) * B + x]);
                 }
@@ -800,10 +826,10 @@ __global__ void __launch_bounds__(256) adj_face_kernel(AdjArgs<F> a) {
                 else atomicAdd(&s_cnt, 1);
             }
             __syncthreads();
-            if (threadIdx.x == 0) ((volatile int *)a.n_active)[grp] = s_cnt;
+            if (threadIdx.x == 0) ((volatile int *)a.n_active)[lgrp] = s_cnt;
         }
         if (!grid_barrier(bar, a.spin_ns, nblk)) return;
-        if (((volatile int *)a.n_active)[grp] == 0) break;
+        if (((volatile int *)a.n_active)[lgrp] == 0) break;
     }
 }
 
