@@ -40,7 +40,7 @@ struct tt_ctx {
 
     // workspace, grown on demand
     DevBuf src, pts, tabT, tabP, rec, partial, conv, iters, nact, bar, flags;
-    DevBuf cq, wq, sidx, next, heads, nheads, JS, coef;
+    DevBuf cq, wq, sidx, next, heads, nheads, JS, coef, t0c;
     int *h_pinned = nullptr;  // readback: [0..TT_MAX_BATCH) iterations, then flags
     PointD *h_pts = nullptr;  // staging for source / receiver positions
     size_t h_pts_cap = 0;
@@ -55,6 +55,8 @@ namespace {
 constexpr long long kDefaultSpinNs = 2000000000LL;
 // Largest per-(node, source) coefficient array the adjoint keeps in its workspace.
 constexpr size_t kCoefBudgetBytes = 64ull << 30;
+// Largest factor cache (1/T0 and grad T0 / T0 per node and source) one forward slice keeps.
+constexpr size_t kFactorCacheBudgetBytes = 32ull << 30;
 
 tt_status fail(tt_ctx *c, tt_status s, const char *fmt, ...) {
     if (c) {
@@ -419,59 +421,25 @@ tt_status forward_impl(tt_ctx *ctx, const tt_model *m, const tt_point *h_src, in
     CK(run_tau_init<F>(g, B, src, (F *)d_tau, o->init == 0, ctx->st));
     ctx->launches += 4 + (o->init == 0 ? 2 : 1);
 
-    int grid, block, slots;
     // Tile schedules stage 32 sources per task with TMA: they need B >= 32 and rows of tau
     // (B values) that are a multiple of 16 bytes. Automatic: node hyperplanes.
     const bool tiles_ok = B >= 32 && (B * sizeof(F)) % 16 == 0;
     int sched = o->sweep_schedule == 0 ? 1 : o->sweep_schedule;
     if (sched >= 2 && !tiles_ok) sched = 1;
-    int n_bgroups = 1, grp_blocks = 0, grp_src = B;
-    if (sched == 1) {
-        // 256-thread blocks; one barrier group per resident block slot of an SM, so each SM
-        // interleaves the groups; each group gets a multiple of 32 sources.
-        block = 256;
-        size_t smem = (size_t)B * sizeof(F);
-        int per_sm = forward_blocks_per_sm<F>(block, smem);
-        if (per_sm <= 0) return fail(ctx, TT_ECUDA, "sweep kernel cannot be resident (B = %d)", B);
-        if (per_sm > kMaxBarrierGroups) per_sm = kMaxBarrierGroups;
-        int max_grid = per_sm * ctx->n_sm;
-        if (o->launch_blocks > 0 && o->launch_blocks < max_grid) max_grid = o->launch_blocks;
-        n_bgroups = per_sm;
-        if (n_bgroups > (B + 31) / 32) n_bgroups = (B + 31) / 32;
-        if (n_bgroups > max_grid) n_bgroups = max_grid;
-        grp_src = ((B + n_bgroups - 1) / n_bgroups + 31) / 32 * 32;
-        n_bgroups = (B + grp_src - 1) / grp_src;
-        grp_blocks = max_grid / n_bgroups;
-        if ((long long)grp_blocks * block < grp_src) {
-            int need = (grp_src + block - 1) / block;
-            if ((long long)need * n_bgroups > (long long)per_sm * ctx->n_sm)
-                return fail(ctx, TT_EINVAL, "batch of %d sources exceeds one resident launch", B);
-            grp_blocks = need;
-        }
-        grid = grp_blocks * n_bgroups;
-        slots = 0;
-    } else {
-        int per_sm = forward_tiled_blocks_per_sm<F>(sched - 2, B);
-        if (per_sm <= 0) return fail(ctx, TT_ECUDA, "tiled sweep cannot be resident (B = %d)", B);
-        if (per_sm > 2) per_sm = 2;
-        int max_grid = per_sm * ctx->n_sm;
-        if (o->launch_blocks > 0 && o->launch_blocks < max_grid) max_grid = o->launch_blocks;
-        block = kTileThreads;
-        grid = max_grid;
-        if ((long long)grid * block < B) {
-            int need = (B + block - 1) / block;
-            if (need > per_sm * ctx->n_sm)
-                return fail(ctx, TT_EINVAL, "batch of %d sources exceeds one resident launch", B);
-            grid = need;
-        }
-        slots = (int)(((long long)grid * block) / B);
+    // Source slices: the factor cache of one slice must fit the workspace budget.
+    const size_t per_src = sizeof(Vec4<F>) * (size_t)g.N;
+    int slice = B;
+    if (per_src * (size_t)B > kFactorCacheBudgetBytes) {
+        slice = (int)(kFactorCacheBudgetBytes / per_src) / 32 * 32;
+        if (slice < 32) slice = 32;
     }
-    ENSURE(ctx->partial, sizeof(F) * 2 * (size_t)B * grid);
+    ENSURE(ctx->t0c, per_src * (size_t)(slice < B ? slice : B));
+
     const GeoTab<F> &t = geo<F>(ctx);
     FwdArgs<F> a;
+    memset(&a, 0, sizeof a);
     a.g = g;
     a.B = B;
-    a.slots = slots;
     a.n_planes = ctx->interior.n_planes;
     a.er = (F)(0.5 / g.dr);
     a.rec = (const NodeRec<F> *)ctx->rec.p;
@@ -485,17 +453,17 @@ tt_status forward_impl(tt_ctx *ctx, const tt_model *m, const tt_point *h_src, in
     a.nodes = ctx->interior.nodes;
     a.off = ctx->interior.off;
     a.bar = (BarrierState *)ctx->bar.p;
-    a.partial = (F *)ctx->partial.p;
     a.conv = (int *)ctx->conv.p;
     a.iters = (int *)ctx->iters.p;
     a.n_active = (int *)ctx->nact.p;
     a.tol = (F)o->tol_fwd;
     a.max_iter = o->max_iter_fwd;
     a.spin_ns = spin_ns(o);
+    a.t0c = (Vec4<F> *)ctx->t0c.p;
+    a.na = g.nr - 2;
+    a.nb = g.nt - 2;
+    a.nc = g.np - 2;
     CUtensorMap map_tau, map_rec;
-    a.n_bgroups = n_bgroups;
-    a.grp_blocks = grp_blocks;
-    a.grp_src = grp_src;
     if (sched >= 2) {
         const TileShape sh = kTileShapes[sched - 2];
         const unsigned box_tau[4] = {32u, (unsigned)sh.tc + 2, (unsigned)sh.tb + 2,
@@ -507,18 +475,73 @@ tt_status forward_impl(tt_ctx *ctx, const tt_model *m, const tt_point *h_src, in
         a.tiles = ts.tiles;
         a.toff = ts.off;
         a.n_tplanes = ts.n_planes;
-        a.na = g.nr - 2;
-        a.nb = g.nt - 2;
-        a.nc = g.np - 2;
-        a.ngroups = (B + 31) / 32;
     }
+
+    int max_grid_used = 0;
     CK(cudaEventRecord(ctx->ev_start[TT_STATS_FORWARD], ctx->st));
-    if (sched == 1) CK(launch_forward<F>(a, grid, block, ctx->st));
-    else CK(launch_forward_tiled<F>(map_tau, map_rec, a, sched - 2, grid, ctx->st));
+    for (int s0 = 0; s0 < B; s0 += slice) {
+        const int n = slice < B - s0 ? slice : B - s0;
+        a.src_lo = s0;
+        a.src_n = n;
+        int grid = 0;
+        if (sched == 1) {
+            // 256-thread blocks; one barrier group per resident block slot of an SM, so
+            // each SM interleaves the groups; each group gets a multiple of 32 sources.
+            const int block = 256;
+            int per_sm = forward_blocks_per_sm<F>(block, (size_t)n * sizeof(F));
+            if (per_sm <= 0) return fail(ctx, TT_ECUDA, "sweep kernel cannot be resident");
+            if (per_sm > kMaxBarrierGroups) per_sm = kMaxBarrierGroups;
+            int max_grid = per_sm * ctx->n_sm;
+            if (o->launch_blocks > 0 && o->launch_blocks < max_grid) max_grid = o->launch_blocks;
+            int groups = per_sm;
+            if (groups > (n + 31) / 32) groups = (n + 31) / 32;
+            if (groups > max_grid) groups = max_grid;
+            int gsrc = ((n + groups - 1) / groups + 31) / 32 * 32;
+            groups = (n + gsrc - 1) / gsrc;
+            int gblocks = max_grid / groups;
+            if ((long long)gblocks * block < gsrc) {
+                int need = (gsrc + block - 1) / block;
+                if ((long long)need * groups > (long long)per_sm * ctx->n_sm)
+                    return fail(ctx, TT_EINVAL, "slice of %d sources exceeds one resident launch", n);
+                gblocks = need;
+            }
+            grid = gblocks * groups;
+            a.n_bgroups = groups;
+            a.grp_blocks = gblocks;
+            a.grp_src = gsrc;
+            ENSURE(ctx->partial, sizeof(F) * 2 * (size_t)B * grid);
+            a.partial = (F *)ctx->partial.p;
+            CK(launch_t0_cache<F>(a, ctx->st));
+            CK(launch_forward<F>(a, grid, block, ctx->st));
+            ctx->stats[TT_STATS_FORWARD].block_threads = block;
+        } else {
+            int per_sm = forward_tiled_blocks_per_sm<F>(sched - 2, B);
+            if (per_sm <= 0) return fail(ctx, TT_ECUDA, "tiled sweep cannot be resident");
+            if (per_sm > 2) per_sm = 2;
+            grid = per_sm * ctx->n_sm;
+            if (o->launch_blocks > 0 && o->launch_blocks < grid) grid = o->launch_blocks;
+            if ((long long)grid * kTileThreads < n) {
+                int need = (n + kTileThreads - 1) / kTileThreads;
+                if (need > per_sm * ctx->n_sm)
+                    return fail(ctx, TT_EINVAL, "slice of %d sources exceeds one resident launch", n);
+                grid = need;
+            }
+            a.slots = (int)(((long long)grid * kTileThreads) / n);
+            a.ngroups = (n + 31) / 32;
+            a.n_bgroups = 1;
+            a.grp_blocks = grid;
+            a.grp_src = n;
+            ENSURE(ctx->partial, sizeof(F) * 2 * (size_t)B * grid);
+            a.partial = (F *)ctx->partial.p;
+            CK(launch_t0_cache<F>(a, ctx->st));
+            CK(launch_forward_tiled<F>(map_tau, map_rec, a, sched - 2, grid, ctx->st));
+            ctx->stats[TT_STATS_FORWARD].block_threads = kTileThreads;
+        }
+        ctx->launches += 2;
+        if (grid > max_grid_used) max_grid_used = grid;
+    }
     CK(cudaEventRecord(ctx->ev_stop[TT_STATS_FORWARD], ctx->st));
-    ctx->launches += 1;
-    ctx->stats[TT_STATS_FORWARD].grid_blocks = grid;
-    ctx->stats[TT_STATS_FORWARD].block_threads = block;
+    ctx->stats[TT_STATS_FORWARD].grid_blocks = max_grid_used;
     if (d_T) {
         CK(run_traveltime<F>(g, B, src, a.tabT, a.tabP, t.rad, t.cost, t.sint, (const F *)d_tau,
                              (F *)d_T, ctx->st));
@@ -760,7 +783,7 @@ void tt_ctx_destroy(tt_ctx *ctx) {
     DevBuf *bufs[] = {&ctx->src, &ctx->pts, &ctx->tabT, &ctx->tabP, &ctx->rec, &ctx->partial,
                       &ctx->conv, &ctx->iters, &ctx->nact, &ctx->bar, &ctx->flags, &ctx->cq,
                       &ctx->wq, &ctx->sidx, &ctx->next, &ctx->heads, &ctx->nheads, &ctx->JS,
-                      &ctx->coef};
+                      &ctx->coef, &ctx->t0c};
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     for (int q = 0; q < 2; ++q) {

@@ -123,13 +123,11 @@ __device__ __forceinline__ F factor_T0(const SrcReg<F> &S, int i, F r, F cth, F 
 //   tau_new = [s / T0 - H / T0 + sum_d c_d (tau_d+ + tau_d-)] / (2 sum_d c_d)
 // with c_d = kappa_d e_d, kappa = (1, sqrt(1 - 2 xi), sqrt(1 + 2 xi)): the Cauchy-Schwarz
 // bounds of |dH/dp_d| that make the scheme monotone (the Lax-Friedrichs viscosity).
-// trp/trm etc. are tau at the + and - neighbours along r, theta, phi in physical order.
+// trp/trm etc. are tau at the + and - neighbours along r, theta, phi in physical order;
+// (invT0, ur, ut, up) are 1/T0 and u, as returned by factor_T0.
 template <typename F>
-__device__ __forceinline__ F lf_update(const SrcReg<F> &S, int i, F tc, F trp, F trm, F ttp,
-                                       F ttm, F tpp, F tpm, const NodeRec<F> &R, F r, F cth,
-                                       F sth, Vec2<F> tT, Vec2<F> tP, bool flat, F er) {
-    F ur, ut, up;
-    F invT0 = factor_T0<F>(S, i, r, cth, sth, tT, tP, flat, ur, ut, up);
+__device__ __forceinline__ F lf_core(F invT0, F ur, F ut, F up, F tc, F trp, F trm, F ttp,
+                                     F ttm, F tpp, F tpm, const NodeRec<F> &R, F er) {
     F vr = tc * ur + (trp - trm) * er;
     F vt = tc * ut + (ttp - ttm) * R.et;
     F vp = tc * up + (tpp - tpm) * R.ep;

@@ -61,6 +61,10 @@ template <typename F> struct FwdArgs {
     // barrier groups of the node schedule: blocks [g * grp_blocks, (g + 1) * grp_blocks) solve
     // the sources [g * grp_src, min(B, (g + 1) * grp_src)) with their own barrier bar[g]
     int n_bgroups, grp_blocks, grp_src;
+    // sources of this launch: [src_lo, src_lo + src_n); t0c caches 1/T0 and grad T0 / T0 of
+    // the factor for them, [node][src_n]
+    int src_lo, src_n;
+    Vec4<F> *t0c;
 };
 
 template <typename F> struct AdjArgs {
@@ -92,6 +96,7 @@ template <typename F> cudaError_t launch_forward(const FwdArgs<F> &a, int grid, 
 template <typename F> cudaError_t launch_adjoint(const AdjArgs<F> &a, int grid, int block,
                                                  cudaStream_t st);
 template <typename F> int forward_blocks_per_sm(int block, size_t smem);
+template <typename F> cudaError_t launch_t0_cache(const FwdArgs<F> &a, cudaStream_t st);
 
 // Tile shapes of the tile-wavefront forward sweep (sweep-local a = r, b = theta, c = phi).
 struct TileShape {

@@ -32,26 +32,45 @@ __device__ __forceinline__ void unpack(unsigned int pk, int &a, int &b, int &c) 
 
 // ------------------------------------------------------------------------ forward sweep
 
-// Lax-Friedrichs update of tau at interior node (i, j, k) for source b, reading the six
-// neighbours from global memory (node-hyperplane schedule).
+// Factor cache: 1/T0 and u = grad T0 / T0 (factor_T0) of every (node, source) of a launch,
+// computed once per solve. Every schedule reads the same cached values, so every schedule
+// performs exactly the same arithmetic.
+template <typename F> __global__ void t0_cache_kernel(FwdArgs<F> a) {
+    const GridC &g = a.g;
+    const long long total = g.N * a.src_n;
+    for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < total;
+         x += (long long)gridDim.x * blockDim.x) {
+        const int bl = (int)(x % a.src_n);
+        const int b = a.src_lo + bl;
+        const long long n = x / a.src_n;
+        const int k = (int)(n % g.np);
+        const long long t = n / g.np;
+        const int j = (int)(t % g.nt), i = (int)(t / g.nt);
+        const SrcReg<F> S = load_src<F>(a.src, b, g.dr);
+        Vec4<F> c;
+        c.x = factor_T0<F>(S, i, __ldg(a.rad + i), __ldg(a.cost + j), __ldg(a.sint + j),
+                           a.tabT[(long long)j * a.B + b], a.tabP[(long long)k * a.B + b],
+                           g.flat != 0, c.y, c.z, c.w);
+        a.t0c[x] = c;
+    }
+}
+
+// Lax-Friedrichs update of tau at interior node n for source b, reading the six neighbours
+// from global memory (node-hyperplane schedule).
 template <typename F>
-__device__ __forceinline__ F fwd_update(const FwdArgs<F> &a, const SrcReg<F> &S, int b, int i,
-                                        int j, int k, long long n, F &told) {
+__device__ __forceinline__ F fwd_update(const FwdArgs<F> &a, int b, long long n, F &told) {
     const long long B = a.B;
     const long long sp = B, st = (long long)a.g.np * B, sr = (long long)a.g.nt * a.g.np * B;
     const long long x = n * B + b;
-    F *tau = a.tau;
-    F tc = tau[x];
-    F trp = tau[x + sr], trm = tau[x - sr];
-    F ttp = tau[x + st], ttm = tau[x - st];
-    F tpp = tau[x + sp], tpm = tau[x - sp];
+    const F *tau = a.tau;
+    const F tc = tau[x];
+    const F trp = tau[x + sr], trm = tau[x - sr];
+    const F ttp = tau[x + st], ttm = tau[x - st];
+    const F tpp = tau[x + sp], tpm = tau[x - sp];
     const NodeRec<F> R = a.rec[n];
-    F r = __ldg(a.rad + i), cth = __ldg(a.cost + j), sth = __ldg(a.sint + j);
-    Vec2<F> tT = a.tabT[(long long)j * B + b];
-    Vec2<F> tP = a.tabP[(long long)k * B + b];
+    const Vec4<F> c = a.t0c[n * a.src_n + (b - a.src_lo)];
     told = tc;
-    return lf_update<F>(S, i, tc, trp, trm, ttp, ttm, tpp, tpm, R, r, cth, sth, tT, tP,
-                        a.g.flat != 0, a.er);
+    return lf_core<F>(c.x, c.y, c.z, c.w, tc, trp, trm, ttp, ttm, tpp, tpm, R, a.er);
 }
 
 // tau on one face layer = max(2 tau_1 - tau_2, tau_2); q enumerates both faces of an axis.
@@ -86,10 +105,10 @@ __device__ __forceinline__ void extrapolate(const FwdArgs<F> &a, const SrcReg<F>
 }
 
 // Node-hyperplane schedule. The launch is split into barrier groups: group g owns a
-// contiguous slice of the sources and a contiguous range of blocks, runs the whole solve of
-// its slice with its own grid barrier and convergence test, and so never waits for another
-// group; on each SM the warps of one group keep issuing while another group's warps wait at
-// their barrier.
+// contiguous slice of the launch's sources and a contiguous range of blocks, runs the whole
+// solve of its slice with its own grid barrier and convergence test, and so never waits for
+// another group; on each SM the warps of one group keep issuing while another group's warps
+// wait at their barrier.
 template <typename F>
 __global__ void __launch_bounds__(512) fwd_sweep_kernel(FwdArgs<F> a) {
     extern __shared__ unsigned char smem_raw[];
@@ -99,8 +118,8 @@ __global__ void __launch_bounds__(512) fwd_sweep_kernel(FwdArgs<F> a) {
     const int B = a.B;
     const int grp = blockIdx.x / a.grp_blocks;
     const int blk = blockIdx.x - grp * a.grp_blocks;   // block index within the group
-    const int src0 = grp * a.grp_src;
-    const int Bg = min(B, src0 + a.grp_src) - src0;   // sources of this group
+    const int src0 = a.src_lo + grp * a.grp_src;
+    const int Bg = min(a.src_lo + a.src_n, src0 + a.grp_src) - src0;  // sources of the group
     if (Bg <= 0) return;
     BarrierState *bar = a.bar + grp;
     const unsigned nblk = (unsigned)a.grp_blocks;
@@ -128,7 +147,7 @@ __global__ void __launch_bounds__(512) fwd_sweep_kernel(FwdArgs<F> a) {
                         if (in_fixed_set(S.ci, S.cj, S.ck, i, j, k)) continue;
                         const long long n = node_index(g, i, j, k);
                         F told;
-                        F tn = fwd_update<F>(a, S, b, i, j, k, n, told);
+                        F tn = fwd_update<F>(a, b, n, told);
                         a.tau[n * B + b] = tn;
                         err = fmax_(err, fabs(tn - told));
                     }
@@ -242,9 +261,7 @@ template <typename F, int TA, int TB, int TC> struct TileSmem {
     using D = TileDims<TA, TB, TC>;
     static constexpr size_t tau = 0;
     static constexpr size_t rec = tau + sizeof(F) * D::ROWS * 32;
-    static constexpr size_t tabT = rec + sizeof(NodeRec<F>) * D::NODES;
-    static constexpr size_t tabP = tabT + sizeof(Vec2<F>) * TB * 32;
-    static constexpr size_t plist = tabP + sizeof(Vec2<F>) * TC * 32;
+    static constexpr size_t plist = rec + sizeof(NodeRec<F>) * D::NODES;
     static constexpr size_t poff = plist + sizeof(unsigned short) * D::NODES;
     static constexpr size_t err = (poff + sizeof(int) * (D::PLANES + 1) + 15) / 16 * 16;
     static_assert(rec % 128 == 0, "TMA destinations need 128-byte alignment");
@@ -260,8 +277,6 @@ __device__ __forceinline__ bool forward_tile(const FwdArgs<F> &a, const CUtensor
     using L = TileSmem<F, TA, TB, TC>;
     F *s_tau = reinterpret_cast<F *>(smem + L::tau);
     const NodeRec<F> *s_rec = reinterpret_cast<const NodeRec<F> *>(smem + L::rec);
-    Vec2<F> *s_tT = reinterpret_cast<Vec2<F> *>(smem + L::tabT);
-    Vec2<F> *s_tP = reinterpret_cast<Vec2<F> *>(smem + L::tabP);
     const unsigned short *s_plist = reinterpret_cast<const unsigned short *>(smem + L::plist);
     const int *s_poff = reinterpret_cast<const int *>(smem + L::poff);
     const GridC &g = a.g;
@@ -276,25 +291,13 @@ __device__ __forceinline__ bool forward_tile(const FwdArgs<F> &a, const CUtensor
     if (threadIdx.x == 0) {
         fence_proxy_async_smem();
         mbar_expect_tx(bar, (unsigned)(sizeof(F) * (D::ROWS * 32 + D::NODES * 8)));
-        tma_load_4d(s_tau, map_tau, grp * 32, k_lo - 1, j_lo - 1, i_lo - 1, bar);
+        tma_load_4d(s_tau, map_tau, a.src_lo + grp * 32, k_lo - 1, j_lo - 1, i_lo - 1, bar);
         tma_load_4d(smem + L::rec, map_rec, 0, k_lo, j_lo, i_lo, bar);
     }
-    const int bsrc = grp * 32 + lane;
-    const bool valid = bsrc < B;
+    const int bsrc = a.src_lo + grp * 32 + lane;
+    const bool valid = bsrc < a.src_lo + a.src_n;
     const bool active = valid && ((volatile int *)a.conv)[bsrc] == 0;
-    const SrcReg<F> S = load_src<F>(a.src, valid ? bsrc : 0, g.dr);
-    for (int q = warp; q < TB; q += nwarps) {
-        const int lb = b0 + q;
-        Vec2<F> v = {(F)0, (F)0};
-        if (valid && lb < a.nb) v = a.tabT[(long long)(rt ? g.nt - 2 - lb : 1 + lb) * B + bsrc];
-        s_tT[q * 32 + lane] = v;
-    }
-    for (int q = warp; q < TC; q += nwarps) {
-        const int lc = c0 + q;
-        Vec2<F> v = {(F)0, (F)0};
-        if (valid && lc < a.nc) v = a.tabP[(long long)(rp ? g.np - 2 - lc : 1 + lc) * B + bsrc];
-        s_tP[q * 32 + lane] = v;
-    }
+    const SrcReg<F> S = load_src<F>(a.src, valid ? bsrc : a.src_lo, g.dr);
     const bool landed = mbar_wait(bar, parity, a.spin_ns);
     if (!landed) {
         // record the failure, then give the copies in flight one more bounded wait before
@@ -321,10 +324,9 @@ __device__ __forceinline__ bool forward_tile(const FwdArgs<F> &a, const CUtensor
             F *p = s_tau + ((pa * D::HB + pb) * D::HC + pc) * 32 + lane;
             const F t0 = p[0];
             const NodeRec<F> R = s_rec[((pa - 1) * TB + (pb - 1)) * TC + (pc - 1)];
-            const F r = __ldg(a.rad + i), cth = __ldg(a.cost + j), sth = __ldg(a.sint + j);
-            const F tn = lf_update<F>(S, i, t0, p[D::SA], p[-D::SA], p[D::SB], p[-D::SB], p[32],
-                                      p[-32], R, r, cth, sth, s_tT[tb * 32 + lane],
-                                      s_tP[tc * 32 + lane], g.flat != 0, a.er);
+            const Vec4<F> c = a.t0c[node_index(g, i, j, k) * a.src_n + (bsrc - a.src_lo)];
+            const F tn = lf_core<F>(c.x, c.y, c.z, c.w, t0, p[D::SA], p[-D::SA], p[D::SB],
+                                    p[-D::SB], p[32], p[-32], R, a.er);
             p[0] = tn;
             err = fmax_(err, fabs(tn - t0));
         }
@@ -380,17 +382,18 @@ __global__ void __launch_bounds__(kTileThreads)
     unsigned parity = 0;
     // face extrapolation keeps the one-source-per-thread mapping of the node schedule
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool lane_ok = tid < (long long)a.slots * B;
-    const int bx = lane_ok ? (int)(tid % B) : 0;
-    const int slot = lane_ok ? (int)(tid / B) : 0;
+    const bool lane_ok = tid < (long long)a.slots * a.src_n;
+    const int bx = a.src_lo + (lane_ok ? (int)(tid % a.src_n) : 0);
+    const int slot = lane_ok ? (int)(tid / a.src_n) : 0;
     const SrcReg<F> Sx = load_src<F>(a.src, bx, g.dr);
+    const int s_end = a.src_lo + a.src_n;
 
     for (int it = 0; it < a.max_iter; ++it) {
         const bool act_x = lane_ok && ((volatile int *)a.conv)[bx] == 0;
         for (int x = threadIdx.x; x < B; x += blockDim.x) s_err[x] = 0;
         for (int q = threadIdx.x; q < a.ngroups; q += blockDim.x) {
             int any = 0;
-            for (int x = q * 32; x < min(B, q * 32 + 32); ++x)
+            for (int x = a.src_lo + q * 32; x < min(s_end, a.src_lo + q * 32 + 32); ++x)
                 any |= ((volatile int *)a.conv)[x] == 0;
             s_gact[q] = any;
         }
@@ -422,7 +425,7 @@ __global__ void __launch_bounds__(kTileThreads)
         if (blockIdx.x == 0) {
             if (threadIdx.x == 0) s_cnt = 0;
             __syncthreads();
-            for (int x = threadIdx.x; x < B; x += blockDim.x) {
+            for (int x = a.src_lo + threadIdx.x; x < s_end; x += blockDim.x) {
                 if (a.conv[x]) continue;
                 F m = 0;
                 for (int c = 0; c < (int)gridDim.x; ++c)
@@ -838,7 +841,7 @@ __global__ void __launch_bounds__(256) adj_face_kernel(AdjArgs<F> a) {
 template <typename F>
 cudaError_t launch_forward(const FwdArgs<F> &a, int grid, int block, cudaStream_t st) {
     void *args[] = {const_cast<FwdArgs<F> *>(&a)};
-    size_t smem = (size_t)a.B * sizeof(F);
+    size_t smem = (size_t)a.grp_src * sizeof(F);
     return cudaLaunchCooperativeKernel((void *)fwd_sweep_kernel<F>, dim3(grid), dim3(block),
                                        args, smem, st);
 }
@@ -912,6 +915,17 @@ cudaError_t launch_forward_tiled(const CUtensorMap &map_tau, const CUtensorMap &
     return cudaLaunchCooperativeKernel(tiled_kernel_ptr<F>(shape), dim3(grid), dim3(kTileThreads),
                                        args, forward_tiled_smem<F>(shape, a.B), st);
 }
+
+template <typename F> cudaError_t launch_t0_cache(const FwdArgs<F> &a, cudaStream_t st) {
+    long long total = a.g.N * a.src_n;
+    long long blocks = (total + 255) / 256;
+    if (blocks > 152LL * 16) blocks = 152LL * 16;
+    t0_cache_kernel<F><<<(unsigned)blocks, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_t0_cache<float>(const FwdArgs<float> &, cudaStream_t);
+template cudaError_t launch_t0_cache<double>(const FwdArgs<double> &, cudaStream_t);
 
 template <typename F> cudaError_t launch_adjoint_coefs(const AdjArgs<F> &a, cudaStream_t st) {
     long long total = a.g.N * a.B;
