@@ -103,7 +103,7 @@ typedef struct {
     int launch_blocks;      /* persistent sweep launch: 0 = automatic, else at most this many
                                blocks (results do not depend on it) */
     int sweep_schedule;     /* forward sweep schedule: 0 = automatic; 1 = node hyperplanes;
-                               2, 3, 4 = tile hyperplanes with 4x8x8, 4x4x8, 2x8x8 tiles
+                               2, 3, 4 = tile hyperplanes with 2x4x8, 4x4x4, 2x8x8 tiles
                                (r x theta x phi). Results do not depend on it. */
     int adj_chunk;          /* adjoint: sources per launch (the slices run one after another so
                                that each launch's working set stays in L2); 0 = automatic */

@@ -20,8 +20,9 @@ NVCC = os.environ.get("NVCC", "nvcc")
 
 
 def _flags():
+    extra = os.environ.get("TTGB_NVCC_FLAGS", "").split()  # e.g. tuning macros
     return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,
-                   "-I", CSRC]
+                   "-I", CSRC] + extra
 
 
 def _deps():

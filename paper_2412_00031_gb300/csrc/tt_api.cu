@@ -484,7 +484,7 @@ tt_status forward_impl(tt_ctx *ctx, const tt_model *m, const tt_point *h_src, in
         a.src_lo = s0;
         a.src_n = n;
         int grid = 0;
-        if (sched == 1) {
+        if (sched == 1 || n < 32) {  // a tile task stages 32 sources: short slices use nodes
             // 256-thread blocks; one barrier group per resident block slot of an SM, so
             // each SM interleaves the groups; each group gets a multiple of 32 sources.
             const int block = 256;
@@ -517,7 +517,7 @@ tt_status forward_impl(tt_ctx *ctx, const tt_model *m, const tt_point *h_src, in
         } else {
             int per_sm = forward_tiled_blocks_per_sm<F>(sched - 2, B);
             if (per_sm <= 0) return fail(ctx, TT_ECUDA, "tiled sweep cannot be resident");
-            if (per_sm > 2) per_sm = 2;
+            if (per_sm > 4) per_sm = 4;
             grid = per_sm * ctx->n_sm;
             if (o->launch_blocks > 0 && o->launch_blocks < grid) grid = o->launch_blocks;
             if ((long long)grid * kTileThreads < n) {
@@ -533,8 +533,12 @@ tt_status forward_impl(tt_ctx *ctx, const tt_model *m, const tt_point *h_src, in
             a.grp_src = n;
             ENSURE(ctx->partial, sizeof(F) * 2 * (size_t)B * grid);
             a.partial = (F *)ctx->partial.p;
+            CUtensorMap map_t0c;
+            const TileShape sh = kTileShapes[sched - 2];
+            const unsigned box_c[4] = {128u, (unsigned)sh.tc, (unsigned)sh.tb, (unsigned)sh.ta};
+            if ((s = encode_map4<F>(ctx, &map_t0c, ctx->t0c.p, 4LL * n, box_c)) != TT_OK) return s;
             CK(launch_t0_cache<F>(a, ctx->st));
-            CK(launch_forward_tiled<F>(map_tau, map_rec, a, sched - 2, grid, ctx->st));
+            CK(launch_forward_tiled<F>(map_tau, map_rec, map_t0c, a, sched - 2, grid, ctx->st));
             ctx->stats[TT_STATS_FORWARD].block_threads = kTileThreads;
         }
         ctx->launches += 2;

@@ -103,11 +103,12 @@ struct TileShape {
     int ta, tb, tc;
 };
 constexpr int kNumTileShapes = 3;
-constexpr TileShape kTileShapes[kNumTileShapes] = {{4, 8, 8}, {4, 4, 8}, {2, 8, 8}};
+constexpr TileShape kTileShapes[kNumTileShapes] = {{2, 4, 8}, {4, 4, 4}, {2, 8, 8}};
 template <typename F> size_t forward_tiled_smem(int shape, int B);
 template <typename F>
 cudaError_t launch_forward_tiled(const CUtensorMap &map_tau, const CUtensorMap &map_rec,
-                                 const FwdArgs<F> &a, int shape, int grid, cudaStream_t st);
+                                 const CUtensorMap &map_t0c, const FwdArgs<F> &a, int shape,
+                                 int grid, cudaStream_t st);
 template <typename F> int forward_tiled_blocks_per_sm(int shape, int B);
 constexpr int kTileThreads = 256;
 constexpr int kMaxBarrierGroups = 8;

@@ -75,7 +75,7 @@ __device__ __forceinline__ F fwd_update(const FwdArgs<F> &a, int b, long long n,
 
 // tau on one face layer = max(2 tau_1 - tau_2, tau_2); q enumerates both faces of an axis.
 template <typename F>
-__device__ __forceinline__ void extrapolate(const FwdArgs<F> &a, const SrcReg<F> &S, int b,
+__device__ __forceinline__ void extrapolate(const FwdArgs<F> &a, int ci, int cj, int ck, int b,
                                             int axis, int slot, int slots) {
     const GridC &g = a.g;
     const long long B = a.B;
@@ -94,7 +94,7 @@ __device__ __forceinline__ void extrapolate(const FwdArgs<F> &a, const SrcReg<F>
         if (axis == 0) { i = f0; j = u; k = v; }
         else if (axis == 1) { i = u; j = f0; k = v; }
         else { i = u; j = v; k = f0; }
-        if (in_fixed_set(S.ci, S.cj, S.ck, i, j, k)) continue;
+        if (in_fixed_set(ci, cj, ck, i, j, k)) continue;
         long long n = node_index(g, i, j, k);
         long long x0 = n * B + b;
         long long x1 = x0 + (long long)(f1 - f0) * stride * B;
@@ -110,7 +110,7 @@ __device__ __forceinline__ void extrapolate(const FwdArgs<F> &a, const SrcReg<F>
 // another group; on each SM the warps of one group keep issuing while another group's warps
 // wait at their barrier.
 template <typename F>
-__global__ void __launch_bounds__(512) fwd_sweep_kernel(FwdArgs<F> a) {
+__global__ void __launch_bounds__(256) fwd_sweep_kernel(FwdArgs<F> a) {
     extern __shared__ unsigned char smem_raw[];
     F *s_err = reinterpret_cast<F *>(smem_raw);
     __shared__ int s_cnt;
@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(512) fwd_sweep_kernel(FwdArgs<F> a) {
     const bool lane_ok = tid < (long long)slots * Bg;
     const int b = src0 + (lane_ok ? (int)(tid % Bg) : 0);
     const int slot = lane_ok ? (int)(tid / Bg) : 0;
-    const SrcReg<F> S = load_src<F>(a.src, b, g.dr);
+    const int ci = a.src[b].ci, cj = a.src[b].cj, ck = a.src[b].ck;  // fixed set centre
 
     for (int it = 0; it < a.max_iter; ++it) {
         const bool active = lane_ok && ((volatile int *)a.conv)[b] == 0;
@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(512) fwd_sweep_kernel(FwdArgs<F> a) {
                         const int i = rr ? g.nr - 2 - aa : 1 + aa;
                         const int j = rt ? g.nt - 2 - bb : 1 + bb;
                         const int k = rp ? g.np - 2 - cc : 1 + cc;
-                        if (in_fixed_set(S.ci, S.cj, S.ck, i, j, k)) continue;
+                        if (in_fixed_set(ci, cj, ck, i, j, k)) continue;
                         const long long n = node_index(g, i, j, k);
                         F told;
                         F tn = fwd_update<F>(a, b, n, told);
@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(512) fwd_sweep_kernel(FwdArgs<F> a) {
                 if (!grid_barrier(bar, a.spin_ns, nblk)) return;
             }
             for (int axis = 0; axis < 3; ++axis) {
-                if (active) extrapolate<F>(a, S, b, axis, slot, slots);
+                if (active) extrapolate<F>(a, ci, cj, ck, b, axis, slot, slots);
                 if (!grid_barrier(bar, a.spin_ns, nblk)) return;
             }
         }
@@ -261,15 +261,17 @@ template <typename F, int TA, int TB, int TC> struct TileSmem {
     using D = TileDims<TA, TB, TC>;
     static constexpr size_t tau = 0;
     static constexpr size_t rec = tau + sizeof(F) * D::ROWS * 32;
-    static constexpr size_t plist = rec + sizeof(NodeRec<F>) * D::NODES;
+    static constexpr size_t cache = rec + sizeof(NodeRec<F>) * D::NODES;
+    static constexpr size_t plist = cache + sizeof(Vec4<F>) * D::NODES * 32;
     static constexpr size_t poff = plist + sizeof(unsigned short) * D::NODES;
     static constexpr size_t err = (poff + sizeof(int) * (D::PLANES + 1) + 15) / 16 * 16;
-    static_assert(rec % 128 == 0, "TMA destinations need 128-byte alignment");
+    static_assert(rec % 128 == 0 && cache % 128 == 0, "TMA destinations need 128-byte alignment");
 };
 
 template <typename F, int TA, int TB, int TC>
 __device__ __forceinline__ bool forward_tile(const FwdArgs<F> &a, const CUtensorMap *map_tau,
-                                             const CUtensorMap *map_rec, int I, int J, int K,
+                                             const CUtensorMap *map_rec,
+                                             const CUtensorMap *map_t0c, int I, int J, int K,
                                              int grp, bool rr, bool rt, bool rp,
                                              unsigned char *smem, unsigned long long *bar,
                                              unsigned &parity, F *s_err) {
@@ -277,6 +279,7 @@ __device__ __forceinline__ bool forward_tile(const FwdArgs<F> &a, const CUtensor
     using L = TileSmem<F, TA, TB, TC>;
     F *s_tau = reinterpret_cast<F *>(smem + L::tau);
     const NodeRec<F> *s_rec = reinterpret_cast<const NodeRec<F> *>(smem + L::rec);
+    const Vec4<F> *s_t0c = reinterpret_cast<const Vec4<F> *>(smem + L::cache);
     const unsigned short *s_plist = reinterpret_cast<const unsigned short *>(smem + L::plist);
     const int *s_poff = reinterpret_cast<const int *>(smem + L::poff);
     const GridC &g = a.g;
@@ -290,9 +293,10 @@ __device__ __forceinline__ bool forward_tile(const FwdArgs<F> &a, const CUtensor
 
     if (threadIdx.x == 0) {
         fence_proxy_async_smem();
-        mbar_expect_tx(bar, (unsigned)(sizeof(F) * (D::ROWS * 32 + D::NODES * 8)));
+        mbar_expect_tx(bar, (unsigned)(sizeof(F) * (D::ROWS * 32 + D::NODES * (8 + 128))));
         tma_load_4d(s_tau, map_tau, a.src_lo + grp * 32, k_lo - 1, j_lo - 1, i_lo - 1, bar);
         tma_load_4d(smem + L::rec, map_rec, 0, k_lo, j_lo, i_lo, bar);
+        tma_load_4d(smem + L::cache, map_t0c, grp * 128, k_lo, j_lo, i_lo, bar);
     }
     const int bsrc = a.src_lo + grp * 32 + lane;
     const bool valid = bsrc < a.src_lo + a.src_n;
@@ -323,8 +327,9 @@ __device__ __forceinline__ bool forward_tile(const FwdArgs<F> &a, const CUtensor
             const int pa = i - i_lo + 1, pb = j - j_lo + 1, pc = k - k_lo + 1;
             F *p = s_tau + ((pa * D::HB + pb) * D::HC + pc) * 32 + lane;
             const F t0 = p[0];
-            const NodeRec<F> R = s_rec[((pa - 1) * TB + (pb - 1)) * TC + (pc - 1)];
-            const Vec4<F> c = a.t0c[node_index(g, i, j, k) * a.src_n + (bsrc - a.src_lo)];
+            const int nl = ((pa - 1) * TB + (pb - 1)) * TC + (pc - 1);
+            const NodeRec<F> R = s_rec[nl];
+            const Vec4<F> c = s_t0c[nl * 32 + lane];
             const F tn = lf_core<F>(c.x, c.y, c.z, c.w, t0, p[D::SA], p[-D::SA], p[D::SB],
                                     p[-D::SB], p[32], p[-32], R, a.er);
             p[0] = tn;
@@ -352,7 +357,8 @@ __device__ __forceinline__ bool forward_tile(const FwdArgs<F> &a, const CUtensor
 template <typename F, int TA, int TB, int TC>
 __global__ void __launch_bounds__(kTileThreads)
     fwd_tile_kernel(const __grid_constant__ CUtensorMap map_tau,
-                    const __grid_constant__ CUtensorMap map_rec, FwdArgs<F> a) {
+                    const __grid_constant__ CUtensorMap map_rec,
+                    const __grid_constant__ CUtensorMap map_t0c, FwdArgs<F> a) {
     using D = TileDims<TA, TB, TC>;
     using L = TileSmem<F, TA, TB, TC>;
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -408,14 +414,14 @@ __global__ void __launch_bounds__(kTileThreads)
                     if (!s_gact[grp]) continue;
                     int I, J, K;
                     unpack(__ldg(a.tiles + t0 + task / a.ngroups), I, J, K);
-                    if (!forward_tile<F, TA, TB, TC>(a, &map_tau, &map_rec, I, J, K, grp, rr, rt,
-                                                     rp, smem, &bar, parity, s_err))
+                    if (!forward_tile<F, TA, TB, TC>(a, &map_tau, &map_rec, &map_t0c, I, J, K,
+                                                     grp, rr, rt, rp, smem, &bar, parity, s_err))
                         return;
                 }
                 if (!grid_barrier(a.bar, a.spin_ns)) return;
             }
             for (int axis = 0; axis < 3; ++axis) {
-                if (act_x) extrapolate<F>(a, Sx, bx, axis, slot, a.slots);
+                if (act_x) extrapolate<F>(a, Sx.ci, Sx.cj, Sx.ck, bx, axis, slot, a.slots);
                 if (!grid_barrier(a.bar, a.spin_ns)) return;
             }
         }
@@ -877,16 +883,16 @@ template <typename F, int TA, int TB, int TC> static size_t tiled_smem_bytes(int
 
 template <typename F> size_t forward_tiled_smem(int shape, int B) {
     switch (shape) {
-    case 0: return tiled_smem_bytes<F, 4, 8, 8>(B);
-    case 1: return tiled_smem_bytes<F, 4, 4, 8>(B);
+    case 0: return tiled_smem_bytes<F, 2, 4, 8>(B);
+    case 1: return tiled_smem_bytes<F, 4, 4, 4>(B);
     default: return tiled_smem_bytes<F, 2, 8, 8>(B);
     }
 }
 
 template <typename F> static const void *tiled_kernel_ptr(int shape) {
     switch (shape) {
-    case 0: return (const void *)fwd_tile_kernel<F, 4, 8, 8>;
-    case 1: return (const void *)fwd_tile_kernel<F, 4, 4, 8>;
+    case 0: return (const void *)fwd_tile_kernel<F, 2, 4, 8>;
+    case 1: return (const void *)fwd_tile_kernel<F, 4, 4, 4>;
     default: return (const void *)fwd_tile_kernel<F, 2, 8, 8>;
     }
 }
@@ -909,9 +915,10 @@ template <typename F> int forward_tiled_blocks_per_sm(int shape, int B) {
 
 template <typename F>
 cudaError_t launch_forward_tiled(const CUtensorMap &map_tau, const CUtensorMap &map_rec,
-                                 const FwdArgs<F> &a, int shape, int grid, cudaStream_t st) {
+                                 const CUtensorMap &map_t0c, const FwdArgs<F> &a, int shape,
+                                 int grid, cudaStream_t st) {
     void *args[] = {const_cast<CUtensorMap *>(&map_tau), const_cast<CUtensorMap *>(&map_rec),
-                    const_cast<FwdArgs<F> *>(&a)};
+                    const_cast<CUtensorMap *>(&map_t0c), const_cast<FwdArgs<F> *>(&a)};
     return cudaLaunchCooperativeKernel(tiled_kernel_ptr<F>(shape), dim3(grid), dim3(kTileThreads),
                                        args, forward_tiled_smem<F>(shape, a.B), st);
 }
@@ -956,9 +963,11 @@ template size_t forward_tiled_smem<double>(int, int);
 template int forward_tiled_blocks_per_sm<float>(int, int);
 template int forward_tiled_blocks_per_sm<double>(int, int);
 template cudaError_t launch_forward_tiled<float>(const CUtensorMap &, const CUtensorMap &,
-                                                 const FwdArgs<float> &, int, int, cudaStream_t);
+                                                 const CUtensorMap &, const FwdArgs<float> &, int,
+                                                 int, cudaStream_t);
 template cudaError_t launch_forward_tiled<double>(const CUtensorMap &, const CUtensorMap &,
-                                                  const FwdArgs<double> &, int, int, cudaStream_t);
+                                                  const CUtensorMap &, const FwdArgs<double> &,
+                                                  int, int, cudaStream_t);
 template cudaError_t launch_adjoint_coefs<float>(const AdjArgs<float> &, cudaStream_t);
 template cudaError_t launch_adjoint_coefs<double>(const AdjArgs<double> &, cudaStream_t);
 template cudaError_t launch_adjoint_faces<float>(const AdjArgs<float> &, int, int, cudaStream_t);
