@@ -144,9 +144,22 @@ class GpuPath:
         self.opts = tt.default_opts(tt.TT_F32)
         self.allow_unconverged = False
         self.iters = []
+        self.plan = None
+
+    def use_plan(self):
+        """Captures the whole step into a CUDA graph (tt_plan) and replays it from then on."""
+        tt = self.tt
+        self.plan = tt.tt_plan_create(self.ctx, self.model, self.w.src, self.data, self.tau,
+                                      self.T, self.P, self.chi, self.R, *self.K, opts=self.opts)
 
     def step(self):
         tt = self.tt
+        if self.plan is not None:
+            itf, ita = tt.tt_plan_run(self.plan, allow_unconverged=self.allow_unconverged)
+            fs = tt.tt_get_stats(self.ctx, tt.TT_STATS_FORWARD)
+            as_ = tt.tt_get_stats(self.ctx, tt.TT_STATS_ADJOINT)
+            self.iters.append((itf, ita, fs, as_))
+            return
         for k in self.K:
             k.zero_()
         au = self.allow_unconverged
@@ -232,6 +245,8 @@ def gpu_arm(args, rank, world):
         gp.opts.max_iter_fwd = args.max_iter_fwd or gp.opts.max_iter_fwd
         gp.opts.max_iter_adj = args.max_iter_adj or gp.opts.max_iter_adj
         gp.allow_unconverged = True
+    if args.plan:
+        gp.use_plan()
     for _ in range(args.warmup):
         gp.step()
     gp.iters.clear()
@@ -281,7 +296,9 @@ def gpu_arm(args, rank, world):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": workload_config(w, world),
+        "config": dict(workload_config(w, world),
+                       step="one captured CUDA graph per step (tt_plan)" if args.plan
+                       else "four C-ABI calls per step"),
         "roofline": {"bound": "hbm", "kernel": "fwd_sweep_kernel<float>", "achieved": f_gbs,
                      "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s", "frac": f_gbs / hbm,
                      "traffic": traffic, "algorithmic_bytes_per_launch": f_bytes,
@@ -416,6 +433,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="profiling runs: skip the e2e leg")
     ap.add_argument("--max-iter-fwd", type=int, default=0, help="profiling runs only")
     ap.add_argument("--max-iter-adj", type=int, default=0, help="profiling runs only")
+    ap.add_argument("--plan", type=int, default=1,
+                    help="1: replay the step as one captured CUDA graph (tt_plan); 0: the four "
+                         "individual calls")
     ap.add_argument("--adj-chunk", type=int, default=0,
                     help="adjoint sources per launch (tt_opts.adj_chunk; 0 = automatic)")
     ap.add_argument("--schedule", type=int, default=0,

@@ -194,6 +194,25 @@ tt_status tt_misfit_noalloc(const tt_grid *grid, const void *d_T, int dtype,
                             const tt_data *data, double *d_Tr, double *d_chi, double *d_R,
                             void *cuda_stream, char *h_err, int err_len);
 
+/* A plan: one whole step over one batch (forward, misfit and adjoint sources, adjoint,
+ * kernels) captured once into a CUDA graph and replayed by tt_plan_run, so that a step costs
+ * one graph launch and one small read-back. The plan binds the model arrays, the data and the
+ * output buffers given here (their contents may change between runs: an inversion updates
+ * s, xi, eta in place) and owns its own workspace; the source and receiver positions are
+ * fixed at creation. Each run overwrites tau, T, P, chi, R and the kernels Ks, Kxi, Keta
+ * (which then hold this batch's sums only). Shapes as in the individual calls: tau, T, P
+ * [N][n_src] of the model's dtype, d_chi [n_src][2] (may be NULL), d_R [n_src][n_rec].
+ * Creation synchronises the stream; the graph uses the context's stream. */
+typedef struct tt_plan tt_plan;
+tt_status tt_plan_create(tt_plan **out, tt_ctx *ctx, const tt_model *model,
+                         const tt_point *h_src, int n_src, const tt_data *data,
+                         const tt_opts *opts, void *d_tau, void *d_T, void *d_P, double *d_chi,
+                         double *d_R, double *d_Ks, double *d_Kxi, double *d_Keta);
+/* Replays the step and waits for it; h_iters_fwd / h_iters_adj (host [n_src], may be NULL)
+ * receive the iteration counts. Statuses as tt_forward and tt_adjoint. */
+tt_status tt_plan_run(tt_plan *plan, int *h_iters_fwd, int *h_iters_adj);
+void tt_plan_destroy(tt_plan *plan);
+
 /* Copies the measurements of the last forward (which = TT_STATS_FORWARD) or adjoint
  * (TT_STATS_ADJOINT) sweep. Host only; call after the solve returned. */
 tt_status tt_get_stats(const tt_ctx *ctx, int which, tt_stats *out);

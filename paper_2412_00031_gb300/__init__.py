@@ -72,7 +72,7 @@ TT_STATS_FORWARD, TT_STATS_ADJOINT = 0, 1
 
 EXPORTED = ["tt_default_opts", "tt_ctx_create", "tt_ctx_destroy", "tt_last_error",
             "tt_forward", "tt_misfit", "tt_adjoint", "tt_kernel", "tt_get_stats",
-            "tt_misfit_noalloc"]
+            "tt_misfit_noalloc", "tt_plan_create", "tt_plan_run", "tt_plan_destroy"]
 TT_NOALLOC_MAX_REC = 1024
 
 
@@ -100,8 +100,14 @@ def _load():
     L.tt_misfit_noalloc.argtypes = [C.POINTER(TTGrid), C.c_void_p, C.c_int, C.POINTER(TTData),
                                     C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_char_p,
                                     C.c_int]
+    L.tt_plan_create.argtypes = [C.POINTER(C.c_void_p), C.c_void_p, C.POINTER(TTModel),
+                                 C.POINTER(TTPoint), C.c_int, C.POINTER(TTData),
+                                 C.POINTER(TTOpts)] + [C.c_void_p] * 8
+    L.tt_plan_run.argtypes = [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    L.tt_plan_destroy.argtypes = [C.c_void_p]
+    L.tt_plan_destroy.restype = None
     for name in ("tt_ctx_create", "tt_forward", "tt_misfit", "tt_adjoint", "tt_kernel",
-                 "tt_get_stats", "tt_misfit_noalloc"):
+                 "tt_get_stats", "tt_misfit_noalloc", "tt_plan_create", "tt_plan_run"):
         getattr(L, name).restype = C.c_int
     return L
 
@@ -297,3 +303,46 @@ def tt_misfit_noalloc(grid, T, data, Tr=None, chi=None, R=None, stream=None):
                                _ptr(chi), _ptr(R), C.c_void_p(stream.cuda_stream), err, 256)
     if st != TT_OK:
         raise TTError(st, err.value.decode())
+
+
+class Plan:
+    """A whole step over one batch captured into a CUDA graph (tt_plan). Keeps references to
+    every buffer it binds."""
+
+    def __init__(self, ctx, handle, n_src, refs):
+        self.ctx, self.handle, self.n_src, self._refs = ctx, handle, n_src, refs
+
+    def close(self):
+        if self.handle:
+            lib.tt_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def tt_plan_create(ctx, model, src, data, tau, T, P, chi, R, Ks, Kxi, Keta, opts=None):
+    M = _model(model)
+    _cuda_ok(tau, T, P, chi, R, Ks, Kxi, Keta)
+    pts, n = _points(src)
+    if opts is None:
+        opts = default_opts(M.dtype)
+    D = data.c_struct()
+    h = C.c_void_p()
+    st = lib.tt_plan_create(C.byref(h), ctx.handle, C.byref(M), pts, n, C.byref(D),
+                            C.byref(opts), _ptr(tau), _ptr(T), _ptr(P), _ptr(chi), _ptr(R),
+                            _ptr(Ks), _ptr(Kxi), _ptr(Keta))
+    _check(ctx, st)
+    return Plan(ctx, h, n, (model, data, tau, T, P, chi, R, Ks, Kxi, Keta, pts, D, opts))
+
+
+def tt_plan_run(plan, allow_unconverged=False):
+    """Replays the step; returns (forward iterations, adjoint iterations)."""
+    itf = (C.c_int * plan.n_src)()
+    ita = (C.c_int * plan.n_src)()
+    st = lib.tt_plan_run(plan.handle, itf, ita)
+    _check(plan.ctx, st, (TT_ENOTCONVERGED,) if allow_unconverged else ())
+    return (np.frombuffer(itf, dtype=np.int32).copy(), np.frombuffer(ita, dtype=np.int32).copy())

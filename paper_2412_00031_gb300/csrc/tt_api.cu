@@ -39,7 +39,7 @@ struct tt_ctx {
     GeoTab<double> gd;
 
     // workspace, grown on demand
-    DevBuf src, pts, tabT, tabP, rec, partial, conv, iters, nact, bar, flags;
+    DevBuf src, pts, rpts, tabT, tabP, rec, partial, conv, iters, nact, bar, flags;
     DevBuf cq, wq, sidx, next, heads, nheads, JS, coef, t0c;
     int *h_pinned = nullptr;  // readback: [0..TT_MAX_BATCH) iterations, then flags
     PointD *h_pts = nullptr;  // staging for source / receiver positions
@@ -95,23 +95,6 @@ tt_status ensure(tt_ctx *ctx, DevBuf &b, size_t bytes) {
         tt_status s_ = ensure(ctx, buf, (bytes)); \
         if (s_ != TT_OK) return s_;               \
     } while (0)
-
-tt_status stage_points(tt_ctx *ctx, const tt_point *h, int n, DevBuf &dst) {
-    if ((size_t)n > ctx->h_pts_cap) {
-        if (ctx->h_pts) cudaFreeHost(ctx->h_pts);
-        ctx->h_pts = nullptr;
-        ctx->h_pts_cap = 0;
-        CK(cudaMallocHost((void **)&ctx->h_pts, sizeof(PointD) * (size_t)n));
-        ctx->h_pts_cap = n;
-    }
-    // The stream may still read the staging buffer from an earlier call.
-    CK(cudaStreamSynchronize(ctx->st));
-    for (int q = 0; q < n; ++q) ctx->h_pts[q] = PointD{h[q].depth_km, h[q].lat_deg, h[q].lon_deg};
-    ENSURE(dst, sizeof(PointD) * (size_t)n);
-    CK(cudaMemcpyAsync(dst.p, ctx->h_pts, sizeof(PointD) * (size_t)n, cudaMemcpyHostToDevice,
-                       ctx->st));
-    return TT_OK;
-}
 
 bool inside(const tt_ctx *ctx, const tt_point &p) {
     const tt_grid &G = ctx->grid;
@@ -316,85 +299,105 @@ unsigned long long spin_ns(const tt_opts *o) {
     return (unsigned long long)(o->spin_limit_ns > 0 ? o->spin_limit_ns : kDefaultSpinNs);
 }
 
-// Resets convergence state and the barrier, then launches.
-tt_status reset_solver_state(tt_ctx *ctx, int B) {
+// Device buffers of one solve step. A context call fills it from the context's grow-on-demand
+// workspace; a plan (tt_plan) owns its buffers for the plan's lifetime.
+template <typename F> struct Work {
+    PointD *src_pts = nullptr, *rec_pts = nullptr;
+    SrcC *src = nullptr;
+    Vec2<F> *tabT = nullptr, *tabP = nullptr;
+    NodeRec<F> *rec = nullptr;
+    Vec4<F> *t0c = nullptr, *coef = nullptr;
+    F *partial = nullptr;
+    int *conv_f = nullptr, *iters_f = nullptr, *conv_a = nullptr, *iters_a = nullptr;
+    int *nact = nullptr, *flags = nullptr;  // flags: model, data index, receiver position
+    BarrierState *bar = nullptr;
+    long long *cq = nullptr;
+    double *wq = nullptr;
+    int *sidx = nullptr, *next = nullptr, *heads = nullptr, *nheads = nullptr;
+    F *JS = nullptr;
+    int t0c_slice = 0;  // sources per forward slice the factor cache holds
+    bool coef_ok = false;
+};
+
+int factor_slice(const GridC &g, int B, size_t es) {
+    const size_t per_src = 4 * es * (size_t)g.N;
+    if (per_src * (size_t)B <= kFactorCacheBudgetBytes) return B;
+    int slice = (int)(kFactorCacheBudgetBytes / per_src) / 32 * 32;
+    return slice < 32 ? 32 : slice;
+}
+
+size_t partial_bytes(const tt_ctx *ctx, int B, size_t es) {
+    return 2 * es * (size_t)B * (size_t)(kMaxBarrierGroups * ctx->n_sm);
+}
+
+// Fills W from the context workspace for a step over B sources and n_rec receivers (0 for
+// a forward-only call).
+template <typename F> tt_status work_from_ctx(tt_ctx *ctx, Work<F> &W, int B, int n_rec) {
+    const GridC &g = ctx->g;
+    const int slice = factor_slice(g, B, sizeof(F));
+    ENSURE(ctx->src, sizeof(SrcC) * (size_t)B);
+    ENSURE(ctx->tabT, sizeof(Vec2<F>) * (size_t)g.nt * B);
+    ENSURE(ctx->tabP, sizeof(Vec2<F>) * (size_t)g.np * B);
+    ENSURE(ctx->rec, sizeof(NodeRec<F>) * (size_t)g.N);
+    ENSURE(ctx->t0c, sizeof(Vec4<F>) * (size_t)g.N * slice);
+    ENSURE(ctx->partial, partial_bytes(ctx, B, sizeof(F)));
     ENSURE(ctx->conv, sizeof(int) * (size_t)B);
     ENSURE(ctx->iters, sizeof(int) * (size_t)B);
     ENSURE(ctx->nact, sizeof(int) * kMaxBarrierGroups);
     ENSURE(ctx->bar, sizeof(BarrierState) * kMaxBarrierGroups);
     ENSURE(ctx->flags, 4 * sizeof(int));
-    CK(cudaMemsetAsync(ctx->conv.p, 0, sizeof(int) * (size_t)B, ctx->st));
-    CK(cudaMemsetAsync(ctx->iters.p, 0, sizeof(int) * (size_t)B, ctx->st));
-    CK(cudaMemsetAsync(ctx->nact.p, 0, sizeof(int) * kMaxBarrierGroups, ctx->st));
-    CK(cudaMemsetAsync(ctx->bar.p, 0, sizeof(BarrierState) * kMaxBarrierGroups, ctx->st));
-    CK(cudaMemsetAsync(ctx->flags.p, 0, 4 * sizeof(int), ctx->st));
+    W.src = (SrcC *)ctx->src.p;
+    W.tabT = (Vec2<F> *)ctx->tabT.p;
+    W.tabP = (Vec2<F> *)ctx->tabP.p;
+    W.rec = (NodeRec<F> *)ctx->rec.p;
+    W.t0c = (Vec4<F> *)ctx->t0c.p;
+    W.t0c_slice = slice;
+    W.partial = (F *)ctx->partial.p;
+    W.conv_f = W.conv_a = (int *)ctx->conv.p;
+    W.iters_f = W.iters_a = (int *)ctx->iters.p;
+    W.nact = (int *)ctx->nact.p;
+    W.bar = (BarrierState *)ctx->bar.p;
+    W.flags = (int *)ctx->flags.p;
+    W.src_pts = (PointD *)ctx->pts.p;
+    if (n_rec > 0) {
+        const int S = 8 * n_rec;
+        ENSURE(ctx->cq, sizeof(long long) * S);
+        ENSURE(ctx->wq, sizeof(double) * S);
+        ENSURE(ctx->sidx, sizeof(int) * (size_t)g.N);
+        ENSURE(ctx->next, sizeof(int) * S);
+        ENSURE(ctx->heads, sizeof(int) * S);
+        ENSURE(ctx->nheads, sizeof(int));
+        ENSURE(ctx->JS, sizeof(F) * (size_t)S * B);
+        W.cq = (long long *)ctx->cq.p;
+        W.wq = (double *)ctx->wq.p;
+        W.sidx = (int *)ctx->sidx.p;
+        W.next = (int *)ctx->next.p;
+        W.heads = (int *)ctx->heads.p;
+        W.nheads = (int *)ctx->nheads.p;
+        W.JS = (F *)ctx->JS.p;
+        const size_t coef_bytes = sizeof(Vec4<F>) * (size_t)g.N * B;
+        W.coef_ok = coef_bytes <= kCoefBudgetBytes;
+        if (W.coef_ok) {
+            ENSURE(ctx->coef, coef_bytes);
+            W.coef = (Vec4<F> *)ctx->coef.p;
+        }
+    }
     return TT_OK;
 }
 
-// Reads back iterations, convergence flags, the barrier status and the validation flag,
-// waits for the stream and turns them into a status.
-// Nodes a source updates per sweep: the swept box minus the part of its 3x3x3 fixed set
-// inside that box.
-long long updated_nodes(const tt_ctx *ctx, const PointD &p, int lo) {
-    const GridC &g = ctx->g;
-    const double deg = 3.14159265358979323846 / 180.0;
-    double f[3] = {((g.re - p.depth) - g.r0) / g.dr, (p.lat * deg - g.t0) / g.dt,
-                   (p.lon * deg - g.p0) / g.dp};
-    int n[3] = {g.nr, g.nt, g.np};
-    long long box = 1, fixed = 1;
-    for (int a = 0; a < 3; ++a) {
-        int c = (int)std::floor(f[a] + 0.5);
-        c = c < 0 ? 0 : (c > n[a] - 1 ? n[a] - 1 : c);
-        int l0 = c - 1 > lo ? c - 1 : lo, l1 = c + 1 < n[a] - 1 - lo ? c + 1 : n[a] - 1 - lo;
-        fixed *= l1 >= l0 ? (l1 - l0 + 1) : 0;
-        box *= n[a] - 2 * lo;
+// Host positions -> pinned staging -> device (synchronises the stream first: the staging
+// buffer may still be read by an earlier call).
+tt_status stage_to(tt_ctx *ctx, const tt_point *h, int n, PointD *d) {
+    if ((size_t)n > ctx->h_pts_cap) {
+        if (ctx->h_pts) cudaFreeHost(ctx->h_pts);
+        ctx->h_pts = nullptr;
+        ctx->h_pts_cap = 0;
+        CK(cudaMallocHost((void **)&ctx->h_pts, sizeof(PointD) * (size_t)n));
+        ctx->h_pts_cap = n;
     }
-    return box - fixed;
-}
-
-tt_status finish_solve(tt_ctx *ctx, int B, int *h_iters, int max_iter, const char *what,
-                       int which) {
-    int *h = ctx->h_pinned;
-    CK(cudaMemcpyAsync(h, ctx->iters.p, sizeof(int) * (size_t)B, cudaMemcpyDeviceToHost, ctx->st));
-    CK(cudaMemcpyAsync(h + TT_MAX_BATCH, ctx->conv.p, sizeof(int) * (size_t)B,
-                       cudaMemcpyDeviceToHost, ctx->st));
-    unsigned char *hb = (unsigned char *)(ctx->h_pinned + 2 * TT_MAX_BATCH + 8);
-    CK(cudaMemcpyAsync(hb, ctx->bar.p, sizeof(BarrierState) * kMaxBarrierGroups,
-                       cudaMemcpyDeviceToHost, ctx->st));
-    CK(cudaMemcpyAsync(h + 2 * TT_MAX_BATCH + 1, ctx->flags.p, sizeof(int),
-                       cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
-    if (h[2 * TT_MAX_BATCH + 1])
-        return fail(ctx, TT_EINVAL, "%s: model has s <= 0 or xi^2 + eta^2 >= 1/4", what);
-    for (int q = 0; q < kMaxBarrierGroups; ++q) {
-        int st;
-        memcpy(&st, hb + q * sizeof(BarrierState) + offsetof(BarrierState, status), sizeof st);
-        if (st == kDevTimeout)
-            return fail(ctx, TT_ETIMEOUT, "%s: a device-side wait exceeded its limit", what);
-    }
-    if (h_iters) memcpy(h_iters, h, sizeof(int) * (size_t)B);
-    {
-        tt_stats &S = ctx->stats[which];
-        float ms = 0.f;
-        CK(cudaEventElapsedTime(&ms, ctx->ev_start[which], ctx->ev_stop[which]));
-        S.sweep_ms = ms;
-        const int lo = which == TT_STATS_FORWARD ? 1 : 0;
-        long long upd = 0;
-        int imax = 0;
-        for (int b = 0; b < B; ++b) {
-            upd += 8LL * h[b] * updated_nodes(ctx, ctx->h_pts[b], lo);
-            imax = h[b] > imax ? h[b] : imax;
-        }
-        const GridC &g = ctx->g;
-        S.node_updates = upd;
-        S.iters_max = imax;
-        S.node_sweeps = 8LL * imax * (long long)(g.nr - 2 * lo) * (g.nt - 2 * lo) * (g.np - 2 * lo);
-    }
-    int nc = 0;
-    for (int b = 0; b < B; ++b) nc += h[TT_MAX_BATCH + b] == 0;
-    if (nc)
-        return fail(ctx, TT_ENOTCONVERGED, "%s: %d of %d sources did not converge in %d iterations",
-                    what, nc, B, max_iter);
+    for (int q = 0; q < n; ++q) ctx->h_pts[q] = PointD{h[q].depth_km, h[q].lat_deg, h[q].lon_deg};
+    CK(cudaMemcpyAsync(d, ctx->h_pts, sizeof(PointD) * (size_t)n, cudaMemcpyHostToDevice, ctx->st));
     return TT_OK;
 }
 
@@ -402,38 +405,50 @@ template <typename F> GeoTab<F> &geo(tt_ctx *ctx);
 template <> GeoTab<float> &geo<float>(tt_ctx *ctx) { return ctx->gf; }
 template <> GeoTab<double> &geo<double>(tt_ctx *ctx) { return ctx->gd; }
 
+// ---------------------------------------------------------------- enqueue-only steps
+// Each enqueues kernels and memsets on ctx->st and nothing else: no synchronisation and no
+// host access, so that a whole step can be captured into a CUDA graph.
+
+// Timing events: while the stream is being captured, a plain record is only a dependency
+// marker, so the record becomes an event node of the graph instead.
+cudaError_t record(tt_ctx *ctx, cudaEvent_t ev) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(ctx->st, &cs);
+    if (e != cudaSuccess) return e;
+    return cs == cudaStreamCaptureStatusActive
+               ? cudaEventRecordWithFlags(ev, ctx->st, cudaEventRecordExternal)
+               : cudaEventRecord(ev, ctx->st);
+}
+
 template <typename F>
-tt_status forward_impl(tt_ctx *ctx, const tt_model *m, const tt_point *h_src, int B, void *d_tau,
-                       void *d_T, const tt_opts *o, int *h_iters) {
+tt_status enq_sources(tt_ctx *ctx, Work<F> &W, const tt_model *m, int B) {
+    CK(run_source_setup<F>(ctx->g, m->d_s, m->d_xi, m->d_eta, W.src_pts, B, W.src, W.tabT,
+                           W.tabP, ctx->st));
+    ctx->launches += 3;
+    return TT_OK;
+}
+
+template <typename F>
+tt_status enq_forward(tt_ctx *ctx, Work<F> &W, const tt_model *m, int B, void *d_tau,
+                      void *d_T, const tt_opts *o) {
     const GridC &g = ctx->g;
     tt_status s;
-    if ((s = stage_points(ctx, h_src, B, ctx->pts)) != TT_OK) return s;
-    ENSURE(ctx->src, sizeof(SrcC) * (size_t)B);
-    ENSURE(ctx->tabT, sizeof(Vec2<F>) * (size_t)g.nt * B);
-    ENSURE(ctx->tabP, sizeof(Vec2<F>) * (size_t)g.np * B);
-    ENSURE(ctx->rec, sizeof(NodeRec<F>) * (size_t)g.N);
-    if ((s = reset_solver_state(ctx, B)) != TT_OK) return s;
-    SrcC *src = (SrcC *)ctx->src.p;
-    CK(run_source_setup<F>(g, m->d_s, m->d_xi, m->d_eta, (const PointD *)ctx->pts.p, B, src,
-                           (Vec2<F> *)ctx->tabT.p, (Vec2<F> *)ctx->tabP.p, ctx->st));
-    CK(run_node_records<F>(g, m->d_s, m->d_xi, m->d_eta, ctx->gd.h2, ctx->gd.cost,
-                           (NodeRec<F> *)ctx->rec.p, (int *)ctx->flags.p, ctx->st));
-    CK(run_tau_init<F>(g, B, src, (F *)d_tau, o->init == 0, ctx->st));
-    ctx->launches += 4 + (o->init == 0 ? 2 : 1);
+    CK(cudaMemsetAsync(W.conv_f, 0, sizeof(int) * (size_t)B, ctx->st));
+    CK(cudaMemsetAsync(W.iters_f, 0, sizeof(int) * (size_t)B, ctx->st));
+    CK(cudaMemsetAsync(W.nact, 0, sizeof(int) * kMaxBarrierGroups, ctx->st));
+    CK(cudaMemsetAsync(W.bar, 0, sizeof(BarrierState) * kMaxBarrierGroups, ctx->st));
+    CK(cudaMemsetAsync(W.flags, 0, sizeof(int), ctx->st));
+    CK(run_node_records<F>(g, m->d_s, m->d_xi, m->d_eta, ctx->gd.h2, ctx->gd.cost, W.rec,
+                           W.flags, ctx->st));
+    CK(run_tau_init<F>(g, B, W.src, (F *)d_tau, o->init == 0, ctx->st));
+    ctx->launches += 1 + (o->init == 0 ? 2 : 1);
 
     // Tile schedules stage 32 sources per task with TMA: they need B >= 32 and rows of tau
     // (B values) that are a multiple of 16 bytes. Automatic: node hyperplanes.
     const bool tiles_ok = B >= 32 && (B * sizeof(F)) % 16 == 0;
     int sched = o->sweep_schedule == 0 ? 1 : o->sweep_schedule;
     if (sched >= 2 && !tiles_ok) sched = 1;
-    // Source slices: the factor cache of one slice must fit the workspace budget.
-    const size_t per_src = sizeof(Vec4<F>) * (size_t)g.N;
-    int slice = B;
-    if (per_src * (size_t)B > kFactorCacheBudgetBytes) {
-        slice = (int)(kFactorCacheBudgetBytes / per_src) / 32 * 32;
-        if (slice < 32) slice = 32;
-    }
-    ENSURE(ctx->t0c, per_src * (size_t)(slice < B ? slice : B));
+    const int slice = W.t0c_slice;
 
     const GeoTab<F> &t = geo<F>(ctx);
     FwdArgs<F> a;
@@ -442,24 +457,25 @@ tt_status forward_impl(tt_ctx *ctx, const tt_model *m, const tt_point *h_src, in
     a.B = B;
     a.n_planes = ctx->interior.n_planes;
     a.er = (F)(0.5 / g.dr);
-    a.rec = (const NodeRec<F> *)ctx->rec.p;
+    a.rec = W.rec;
     a.tau = (F *)d_tau;
-    a.src = src;
-    a.tabT = (const Vec2<F> *)ctx->tabT.p;
-    a.tabP = (const Vec2<F> *)ctx->tabP.p;
+    a.src = W.src;
+    a.tabT = W.tabT;
+    a.tabP = W.tabP;
     a.rad = t.rad;
     a.cost = t.cost;
     a.sint = t.sint;
     a.nodes = ctx->interior.nodes;
     a.off = ctx->interior.off;
-    a.bar = (BarrierState *)ctx->bar.p;
-    a.conv = (int *)ctx->conv.p;
-    a.iters = (int *)ctx->iters.p;
-    a.n_active = (int *)ctx->nact.p;
+    a.bar = W.bar;
+    a.partial = W.partial;
+    a.conv = W.conv_f;
+    a.iters = W.iters_f;
+    a.n_active = W.nact;
     a.tol = (F)o->tol_fwd;
     a.max_iter = o->max_iter_fwd;
     a.spin_ns = spin_ns(o);
-    a.t0c = (Vec4<F> *)ctx->t0c.p;
+    a.t0c = W.t0c;
     a.na = g.nr - 2;
     a.nb = g.nt - 2;
     a.nc = g.np - 2;
@@ -470,7 +486,7 @@ tt_status forward_impl(tt_ctx *ctx, const tt_model *m, const tt_point *h_src, in
                                      (unsigned)sh.ta + 2};
         const unsigned box_rec[4] = {8u, (unsigned)sh.tc, (unsigned)sh.tb, (unsigned)sh.ta};
         if ((s = encode_map4<F>(ctx, &map_tau, d_tau, B, box_tau)) != TT_OK) return s;
-        if ((s = encode_map4<F>(ctx, &map_rec, ctx->rec.p, 8, box_rec)) != TT_OK) return s;
+        if ((s = encode_map4<F>(ctx, &map_rec, W.rec, 8, box_rec)) != TT_OK) return s;
         const TileSchedule &ts = ctx->tiled[sched - 2];
         a.tiles = ts.tiles;
         a.toff = ts.off;
@@ -478,7 +494,7 @@ tt_status forward_impl(tt_ctx *ctx, const tt_model *m, const tt_point *h_src, in
     }
 
     int max_grid_used = 0;
-    CK(cudaEventRecord(ctx->ev_start[TT_STATS_FORWARD], ctx->st));
+    CK(record(ctx, ctx->ev_start[TT_STATS_FORWARD]));
     for (int s0 = 0; s0 < B; s0 += slice) {
         const int n = slice < B - s0 ? slice : B - s0;
         a.src_lo = s0;
@@ -509,8 +525,6 @@ tt_status forward_impl(tt_ctx *ctx, const tt_model *m, const tt_point *h_src, in
             a.n_bgroups = groups;
             a.grp_blocks = gblocks;
             a.grp_src = gsrc;
-            ENSURE(ctx->partial, sizeof(F) * 2 * (size_t)B * grid);
-            a.partial = (F *)ctx->partial.p;
             CK(launch_t0_cache<F>(a, ctx->st));
             CK(launch_forward<F>(a, grid, block, ctx->st));
             ctx->stats[TT_STATS_FORWARD].block_threads = block;
@@ -531,12 +545,10 @@ tt_status forward_impl(tt_ctx *ctx, const tt_model *m, const tt_point *h_src, in
             a.n_bgroups = 1;
             a.grp_blocks = grid;
             a.grp_src = n;
-            ENSURE(ctx->partial, sizeof(F) * 2 * (size_t)B * grid);
-            a.partial = (F *)ctx->partial.p;
             CUtensorMap map_t0c;
             const TileShape sh = kTileShapes[sched - 2];
             const unsigned box_c[4] = {128u, (unsigned)sh.tc, (unsigned)sh.tb, (unsigned)sh.ta};
-            if ((s = encode_map4<F>(ctx, &map_t0c, ctx->t0c.p, 4LL * n, box_c)) != TT_OK) return s;
+            if ((s = encode_map4<F>(ctx, &map_t0c, W.t0c, 4LL * n, box_c)) != TT_OK) return s;
             CK(launch_t0_cache<F>(a, ctx->st));
             CK(launch_forward_tiled<F>(map_tau, map_rec, map_t0c, a, sched - 2, grid, ctx->st));
             ctx->stats[TT_STATS_FORWARD].block_threads = kTileThreads;
@@ -544,65 +556,52 @@ tt_status forward_impl(tt_ctx *ctx, const tt_model *m, const tt_point *h_src, in
         ctx->launches += 2;
         if (grid > max_grid_used) max_grid_used = grid;
     }
-    CK(cudaEventRecord(ctx->ev_stop[TT_STATS_FORWARD], ctx->st));
+    CK(record(ctx, ctx->ev_stop[TT_STATS_FORWARD]));
     ctx->stats[TT_STATS_FORWARD].grid_blocks = max_grid_used;
     if (d_T) {
-        CK(run_traveltime<F>(g, B, src, a.tabT, a.tabP, t.rad, t.cost, t.sint, (const F *)d_tau,
+        CK(run_traveltime<F>(g, B, W.src, W.tabT, W.tabP, t.rad, t.cost, t.sint, (const F *)d_tau,
                              (F *)d_T, ctx->st));
         ctx->launches += 1;
     }
-    return finish_solve(ctx, B, h_iters, o->max_iter_fwd, "tt_forward", TT_STATS_FORWARD);
+    return TT_OK;
 }
 
-tt_status receivers_impl(tt_ctx *ctx, const tt_point *h_rec, int n_rec) {
-    if (n_rec < 1 || !h_rec) return fail(ctx, TT_EINVAL, "need at least one receiver");
-    for (int m = 0; m < n_rec; ++m)
-        if (!inside(ctx, h_rec[m]))
-            return fail(ctx, TT_EINVAL, "receiver %d (%g km, %g, %g) outside the grid", m,
-                        h_rec[m].depth_km, h_rec[m].lat_deg, h_rec[m].lon_deg);
-    tt_status s;
-    if ((s = stage_points(ctx, h_rec, n_rec, ctx->pts)) != TT_OK) return s;
-    ENSURE(ctx->cq, sizeof(long long) * 8 * (size_t)n_rec);
-    ENSURE(ctx->wq, sizeof(double) * 8 * (size_t)n_rec);
-    ENSURE(ctx->flags, 4 * sizeof(int));
-    CK(run_receiver_setup(ctx->g, (const PointD *)ctx->pts.p, n_rec, (long long *)ctx->cq.p,
-                          (double *)ctx->wq.p, (int *)ctx->flags.p + 2, ctx->st));
+tt_status enq_receivers(tt_ctx *ctx, const PointD *rec_pts, int n_rec, long long *cq,
+                        double *wq, int *flags) {
+    CK(run_receiver_setup(ctx->g, rec_pts, n_rec, cq, wq, flags + 2, ctx->st));
+    ctx->launches += 1;
+    return TT_OK;
+}
+
+tt_status enq_misfit(tt_ctx *ctx, const void *d_T, int dtype, const tt_data *d,
+                     const long long *cq, const double *wq, int *flags, double *d_Tr,
+                     double *d_chi, double *d_R) {
+    int *bad = flags + 1;
+    if (dtype == TT_F32)
+        CK(run_misfit<float>(d->n_src, d->n_rec, d_T, cq, wq, *d, d_Tr, d_chi, d_R, bad, ctx->st));
+    else
+        CK(run_misfit<double>(d->n_src, d->n_rec, d_T, cq, wq, *d, d_Tr, d_chi, d_R, bad, ctx->st));
     ctx->launches += 1;
     return TT_OK;
 }
 
 template <typename F>
-tt_status adjoint_impl(tt_ctx *ctx, const tt_model *m, const tt_point *h_src, int B,
-                       const void *d_T, int n_rec, const tt_point *h_rec, const double *d_R,
-                       void *d_P, const tt_opts *o, int *h_iters) {
+tt_status enq_adjoint(tt_ctx *ctx, Work<F> &W, const tt_model *m, int B, const void *d_T,
+                      int n_rec, const double *d_R, void *d_P, const tt_opts *o) {
     const GridC &g = ctx->g;
     tt_status s;
-    if ((s = reset_solver_state(ctx, B)) != TT_OK) return s;
-    if ((s = receivers_impl(ctx, h_rec, n_rec)) != TT_OK) return s;
-    const int S = 8 * n_rec;
-    ENSURE(ctx->sidx, sizeof(int) * (size_t)g.N);
-    ENSURE(ctx->next, sizeof(int) * (size_t)S);
-    ENSURE(ctx->heads, sizeof(int) * (size_t)S);
-    ENSURE(ctx->nheads, sizeof(int));
-    ENSURE(ctx->JS, sizeof(F) * (size_t)S * B);
-    CK(run_point_sources<F>(g, n_rec, (const long long *)ctx->cq.p, (const double *)ctx->wq.p,
-                            (int *)ctx->sidx.p, (int *)ctx->next.p, (int *)ctx->heads.p,
-                            (int *)ctx->nheads.p, d_R, B, (F *)ctx->JS.p, ctx->st));
+    CK(cudaMemsetAsync(W.conv_a, 0, sizeof(int) * (size_t)B, ctx->st));
+    CK(cudaMemsetAsync(W.iters_a, 0, sizeof(int) * (size_t)B, ctx->st));
+    CK(cudaMemsetAsync(W.nact, 0, sizeof(int) * kMaxBarrierGroups, ctx->st));
+    CK(cudaMemsetAsync(W.bar, 0, sizeof(BarrierState) * kMaxBarrierGroups, ctx->st));
+    CK(run_point_sources<F>(g, n_rec, W.cq, W.wq, W.sidx, W.next, W.heads, W.nheads, d_R, B, W.JS,
+                            ctx->st));
     ctx->launches += 5;
-    if ((s = stage_points(ctx, h_src, B, ctx->pts)) != TT_OK) return s;
-    ENSURE(ctx->src, sizeof(SrcC) * (size_t)B);
-    ENSURE(ctx->tabT, sizeof(Vec2<F>) * (size_t)g.nt * B);
-    ENSURE(ctx->tabP, sizeof(Vec2<F>) * (size_t)g.np * B);
-    SrcC *src = (SrcC *)ctx->src.p;
-    CK(run_source_setup<F>(g, m->d_s, m->d_xi, m->d_eta, (const PointD *)ctx->pts.p, B, src,
-                           (Vec2<F> *)ctx->tabT.p, (Vec2<F> *)ctx->tabP.p, ctx->st));
-    ctx->launches += 3;
     CK(cudaMemsetAsync(d_P, 0, sizeof(F) * (size_t)g.N * B, ctx->st));
 
     // Face-coefficient sweep when the per-(node, source) coefficients fit the workspace
     // budget; otherwise the sweep that evaluates the flux velocities at every update.
-    const size_t coef_bytes = sizeof(Vec4<F>) * (size_t)g.N * B;
-    const bool faces = coef_bytes <= kCoefBudgetBytes;
+    const bool faces = W.coef_ok;
     int grid, block, slots;
     int n_bgroups = 1, grp_blocks = 0, grp_src = B;
     if (faces) {
@@ -628,14 +627,13 @@ tt_status adjoint_impl(tt_ctx *ctx, const tt_model *m, const tt_point *h_src, in
         }
         grid = grp_blocks;
         slots = 0;
-        ENSURE(ctx->coef, coef_bytes);
     } else if ((s = sweep_shape<F>(ctx, false, B, ctx->full, o->launch_blocks, grid, block,
                                    slots)) != TT_OK) {
         return s;
     }
-    ENSURE(ctx->partial, sizeof(F) * 2 * (size_t)B * grid);
     const GeoTab<F> &t = geo<F>(ctx);
     AdjArgs<F> a;
+    memset(&a, 0, sizeof a);
     a.g = g;
     a.B = B;
     a.slots = slots;
@@ -645,24 +643,24 @@ tt_status adjoint_impl(tt_ctx *ctx, const tt_model *m, const tt_point *h_src, in
     a.P = (F *)d_P;
     a.xi = (const F *)m->d_xi;
     a.eta = (const F *)m->d_eta;
-    a.src = src;
+    a.src = W.src;
     a.cost = t.cost;
     a.costf = t.costf;
     a.h2 = t.h2;
     a.arf = t.arf;
-    a.sidx = (const int *)ctx->sidx.p;
-    a.JS = (const F *)ctx->JS.p;
+    a.sidx = W.sidx;
+    a.JS = W.JS;
     a.nodes = ctx->full.nodes;
     a.off = ctx->full.off;
-    a.bar = (BarrierState *)ctx->bar.p;
-    a.partial = (F *)ctx->partial.p;
-    a.conv = (int *)ctx->conv.p;
-    a.iters = (int *)ctx->iters.p;
-    a.n_active = (int *)ctx->nact.p;
+    a.bar = W.bar;
+    a.partial = W.partial;
+    a.conv = W.conv_a;
+    a.iters = W.iters_a;
+    a.n_active = W.nact;
     a.tol = (F)o->tol_adj;
     a.max_iter = o->max_iter_adj;
     a.spin_ns = spin_ns(o);
-    a.coef = faces ? (Vec4<F> *)ctx->coef.p : nullptr;
+    a.coef = faces ? W.coef : nullptr;
     a.n_bgroups = n_bgroups;
     a.grp_blocks = grp_blocks;
     a.grp_src = grp_src;
@@ -670,7 +668,7 @@ tt_status adjoint_impl(tt_ctx *ctx, const tt_model *m, const tt_point *h_src, in
         CK(launch_adjoint_coefs<F>(a, ctx->st));
         ctx->launches += 1;
     }
-    CK(cudaEventRecord(ctx->ev_start[TT_STATS_ADJOINT], ctx->st));
+    CK(record(ctx, ctx->ev_start[TT_STATS_ADJOINT]));
     if (faces) {
         for (int q = 0; q < n_bgroups; ++q) {
             a.grp_base = q;
@@ -681,16 +679,179 @@ tt_status adjoint_impl(tt_ctx *ctx, const tt_model *m, const tt_point *h_src, in
         CK(launch_adjoint<F>(a, grid, block, ctx->st));
         ctx->launches += 1;
     }
-    CK(cudaEventRecord(ctx->ev_stop[TT_STATS_ADJOINT], ctx->st));
+    CK(record(ctx, ctx->ev_stop[TT_STATS_ADJOINT]));
     ctx->stats[TT_STATS_ADJOINT].grid_blocks = grid;
     ctx->stats[TT_STATS_ADJOINT].block_threads = block;
-    tt_status r = finish_solve(ctx, B, h_iters, o->max_iter_adj, "tt_adjoint", TT_STATS_ADJOINT);
-    if (r == TT_OK && ctx->h_pinned[2 * TT_MAX_BATCH + 1] == 0) {
-        int *h = ctx->h_pinned + 2 * TT_MAX_BATCH + 2;
-        CK(cudaMemcpy(h, (int *)ctx->flags.p + 2, sizeof(int), cudaMemcpyDeviceToHost));
-        if (*h) return fail(ctx, TT_EINVAL, "tt_adjoint: receiver outside the grid");
+    return TT_OK;
+}
+
+tt_status enq_kernel(tt_ctx *ctx, const tt_model *m, int B, const void *d_T, const void *d_P,
+                     double *Ks, double *Kxi, double *Keta) {
+    if (m->dtype == TT_F32)
+        CK(run_kernel_accum<float>(ctx->g, B, m->d_s, d_T, d_P, ctx->gd.h2, ctx->gd.cost, Ks, Kxi,
+                                   Keta, ctx->n_sm, ctx->st));
+    else
+        CK(run_kernel_accum<double>(ctx->g, B, m->d_s, d_T, d_P, ctx->gd.h2, ctx->gd.cost, Ks,
+                                    Kxi, Keta, ctx->n_sm, ctx->st));
+    ctx->launches += 1;
+    return TT_OK;
+}
+
+// ---------------------------------------------------------------- read-back
+
+// Nodes a source updates per sweep: the swept box minus the part of its 3x3x3 fixed set
+// inside that box.
+long long updated_nodes(const tt_ctx *ctx, const PointD &p, int lo) {
+    const GridC &g = ctx->g;
+    const double deg = 3.14159265358979323846 / 180.0;
+    double f[3] = {((g.re - p.depth) - g.r0) / g.dr, (p.lat * deg - g.t0) / g.dt,
+                   (p.lon * deg - g.p0) / g.dp};
+    int n[3] = {g.nr, g.nt, g.np};
+    long long box = 1, fixed = 1;
+    for (int a = 0; a < 3; ++a) {
+        int c = (int)std::floor(f[a] + 0.5);
+        c = c < 0 ? 0 : (c > n[a] - 1 ? n[a] - 1 : c);
+        int l0 = c - 1 > lo ? c - 1 : lo, l1 = c + 1 < n[a] - 1 - lo ? c + 1 : n[a] - 1 - lo;
+        fixed *= l1 >= l0 ? (l1 - l0 + 1) : 0;
+        box *= n[a] - 2 * lo;
     }
+    return box - fixed;
+}
+
+// Host copy of the state a step leaves on the device.
+struct Readback {
+    int *iters_f, *conv_f, *iters_a, *conv_a;  // [TT_MAX_BATCH] each
+    int *flags;                                // [4]
+    unsigned char *bar_f, *bar_a;              // barrier words after the forward / adjoint
+};
+
+Readback readback_view(tt_ctx *ctx) {
+    Readback r;
+    r.iters_f = ctx->h_pinned;
+    r.conv_f = ctx->h_pinned + TT_MAX_BATCH;
+    r.iters_a = ctx->h_pinned + 2 * TT_MAX_BATCH;
+    r.conv_a = ctx->h_pinned + 3 * TT_MAX_BATCH;
+    r.flags = ctx->h_pinned + 4 * TT_MAX_BATCH;
+    r.bar_f = (unsigned char *)(ctx->h_pinned + 4 * TT_MAX_BATCH + 8);
+    r.bar_a = r.bar_f + sizeof(BarrierState) * kMaxBarrierGroups;
     return r;
+}
+
+size_t pinned_bytes() {
+    return sizeof(int) * (4 * TT_MAX_BATCH + 8) + 2 * sizeof(BarrierState) * kMaxBarrierGroups;
+}
+
+// Enqueues the copies of one solve's state (forward or adjoint) into the pinned buffer.
+tt_status enq_readback(tt_ctx *ctx, int B, const int *iters, const int *conv, const int *flags,
+                       const BarrierState *bar, int which) {
+    Readback r = readback_view(ctx);
+    int *hi = which == TT_STATS_FORWARD ? r.iters_f : r.iters_a;
+    int *hc = which == TT_STATS_FORWARD ? r.conv_f : r.conv_a;
+    CK(cudaMemcpyAsync(hi, iters, sizeof(int) * (size_t)B, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaMemcpyAsync(hc, conv, sizeof(int) * (size_t)B, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaMemcpyAsync(r.flags, flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaMemcpyAsync(which == TT_STATS_FORWARD ? r.bar_f : r.bar_a, bar,
+                       sizeof(BarrierState) * kMaxBarrierGroups, cudaMemcpyDeviceToHost, ctx->st));
+    return TT_OK;
+}
+
+// After the stream has finished: statuses of one solve and its statistics. src are the
+// host positions of the sources (for the update counts).
+tt_status solve_status(tt_ctx *ctx, int B, const PointD *src, int *h_iters, int max_iter,
+                       const char *what, int which) {
+    Readback r = readback_view(ctx);
+    const int *hi = which == TT_STATS_FORWARD ? r.iters_f : r.iters_a;
+    const int *hc = which == TT_STATS_FORWARD ? r.conv_f : r.conv_a;
+    if (which == TT_STATS_FORWARD && r.flags[0])
+        return fail(ctx, TT_EINVAL, "%s: model has s <= 0 or xi^2 + eta^2 >= 1/4", what);
+    for (int q = 0; q < kMaxBarrierGroups; ++q) {
+        int st;
+        const unsigned char *bar = which == TT_STATS_FORWARD ? r.bar_f : r.bar_a;
+        memcpy(&st, bar + q * sizeof(BarrierState) + offsetof(BarrierState, status), sizeof st);
+        if (st == kDevTimeout)
+            return fail(ctx, TT_ETIMEOUT, "%s: a device-side wait exceeded its limit", what);
+    }
+    if (h_iters) memcpy(h_iters, hi, sizeof(int) * (size_t)B);
+    tt_stats &S = ctx->stats[which];
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, ctx->ev_start[which], ctx->ev_stop[which]));
+    S.sweep_ms = ms;
+    const int lo = which == TT_STATS_FORWARD ? 1 : 0;
+    long long upd = 0;
+    int imax = 0;
+    for (int b = 0; b < B; ++b) {
+        upd += 8LL * hi[b] * updated_nodes(ctx, src[b], lo);
+        imax = hi[b] > imax ? hi[b] : imax;
+    }
+    const GridC &g = ctx->g;
+    S.node_updates = upd;
+    S.iters_max = imax;
+    S.node_sweeps = 8LL * imax * (long long)(g.nr - 2 * lo) * (g.nt - 2 * lo) * (g.np - 2 * lo);
+    int nc = 0;
+    for (int b = 0; b < B; ++b) nc += hc[b] == 0;
+    if (nc)
+        return fail(ctx, TT_ENOTCONVERGED, "%s: %d of %d sources did not converge in %d iterations",
+                    what, nc, B, max_iter);
+    return TT_OK;
+}
+
+// ---------------------------------------------------------------- immediate calls
+
+template <typename F>
+tt_status forward_impl(tt_ctx *ctx, const tt_model *m, const tt_point *h_src, int B, void *d_tau,
+                       void *d_T, const tt_opts *o, int *h_iters) {
+    tt_status s;
+    ENSURE(ctx->pts, sizeof(PointD) * (size_t)B);
+    Work<F> W;
+    if ((s = work_from_ctx<F>(ctx, W, B, 0)) != TT_OK) return s;
+    if ((s = stage_to(ctx, h_src, B, W.src_pts)) != TT_OK) return s;
+    if ((s = enq_sources<F>(ctx, W, m, B)) != TT_OK) return s;
+    if ((s = enq_forward<F>(ctx, W, m, B, d_tau, d_T, o)) != TT_OK) return s;
+    if ((s = enq_readback(ctx, B, W.iters_f, W.conv_f, W.flags, W.bar, TT_STATS_FORWARD)) != TT_OK)
+        return s;
+    CK(cudaStreamSynchronize(ctx->st));
+    return solve_status(ctx, B, ctx->h_pts, h_iters, o->max_iter_fwd, "tt_forward",
+                        TT_STATS_FORWARD);
+}
+
+template <typename F>
+tt_status adjoint_impl(tt_ctx *ctx, const tt_model *m, const tt_point *h_src, int B,
+                       const void *d_T, int n_rec, const tt_point *h_rec, const double *d_R,
+                       void *d_P, const tt_opts *o, int *h_iters) {
+    tt_status s;
+    ENSURE(ctx->pts, sizeof(PointD) * (size_t)(B > n_rec ? B : n_rec));
+    ENSURE(ctx->rpts, sizeof(PointD) * (size_t)n_rec);
+    Work<F> W;
+    if ((s = work_from_ctx<F>(ctx, W, B, n_rec)) != TT_OK) return s;
+    W.rec_pts = (PointD *)ctx->rpts.p;
+    CK(cudaMemsetAsync(W.flags, 0, 4 * sizeof(int), ctx->st));
+    if ((s = stage_to(ctx, h_rec, n_rec, W.rec_pts)) != TT_OK) return s;
+    if ((s = enq_receivers(ctx, W.rec_pts, n_rec, W.cq, W.wq, W.flags)) != TT_OK) return s;
+    if ((s = stage_to(ctx, h_src, B, W.src_pts)) != TT_OK) return s;
+    if ((s = enq_sources<F>(ctx, W, m, B)) != TT_OK) return s;
+    if ((s = enq_adjoint<F>(ctx, W, m, B, d_T, n_rec, d_R, d_P, o)) != TT_OK) return s;
+    if ((s = enq_readback(ctx, B, W.iters_a, W.conv_a, W.flags, W.bar, TT_STATS_ADJOINT)) != TT_OK)
+        return s;
+    CK(cudaStreamSynchronize(ctx->st));
+    if (readback_view(ctx).flags[2])
+        return fail(ctx, TT_EINVAL, "tt_adjoint: receiver outside the grid");
+    return solve_status(ctx, B, ctx->h_pts, h_iters, o->max_iter_adj, "tt_adjoint",
+                        TT_STATS_ADJOINT);
+}
+
+tt_status check_data(tt_ctx *ctx, const tt_data *d) {
+    if (!d || !d->d_abs_off || !d->d_cs_off || !d->h_rec)
+        return fail(ctx, TT_EINVAL, "data: NULL argument");
+    if (d->n_src < 1 || d->n_src > TT_MAX_BATCH)
+        return fail(ctx, TT_EINVAL, "n_src = %d outside 1..%d", d->n_src, TT_MAX_BATCH);
+    if (d->n_rec < 1) return fail(ctx, TT_EINVAL, "need at least one receiver");
+    if ((size_t)d->n_rec * 2 * 4 * sizeof(double) > 200 * 1024)
+        return fail(ctx, TT_EINVAL, "n_rec = %d too large for the misfit kernel", d->n_rec);
+    for (int q = 0; q < d->n_rec; ++q)
+        if (!inside(ctx, d->h_rec[q]))
+            return fail(ctx, TT_EINVAL, "receiver %d (%g km, %g, %g) outside the grid", q,
+                        d->h_rec[q].depth_km, d->h_rec[q].lat_deg, d->h_rec[q].lon_deg);
+    return TT_OK;
 }
 
 }  // namespace
@@ -757,9 +918,7 @@ tt_status tt_ctx_create(tt_ctx **out, const tt_grid *grid, void *cuda_stream) {
         if (cudaEventCreate(&ctx->ev_start[q]) != cudaSuccess ||
             cudaEventCreate(&ctx->ev_stop[q]) != cudaSuccess)
             s = fail(ctx, TT_ECUDA, "cudaEventCreate failed");
-    if (s == TT_OK && cudaMallocHost((void **)&ctx->h_pinned,
-                                     sizeof(int) * (2 * TT_MAX_BATCH + 8) +
-                                         sizeof(BarrierState) * kMaxBarrierGroups) != cudaSuccess)
+    if (s == TT_OK && cudaMallocHost((void **)&ctx->h_pinned, pinned_bytes()) != cudaSuccess)
         s = fail(ctx, TT_ENOMEM, "pinned host allocation failed");
     if (s != TT_OK) {
         tt_ctx_destroy(ctx);
@@ -784,7 +943,7 @@ void tt_ctx_destroy(tt_ctx *ctx) {
     }
     free_geo(ctx->gf);
     free_geo(ctx->gd);
-    DevBuf *bufs[] = {&ctx->src, &ctx->pts, &ctx->tabT, &ctx->tabP, &ctx->rec, &ctx->partial,
+    DevBuf *bufs[] = {&ctx->src, &ctx->pts, &ctx->rpts, &ctx->tabT, &ctx->tabP, &ctx->rec, &ctx->partial,
                       &ctx->conv, &ctx->iters, &ctx->nact, &ctx->bar, &ctx->flags, &ctx->cq,
                       &ctx->wq, &ctx->sidx, &ctx->next, &ctx->heads, &ctx->nheads, &ctx->JS,
                       &ctx->coef, &ctx->t0c};
@@ -815,31 +974,29 @@ tt_status tt_forward(tt_ctx *ctx, const tt_model *model, const tt_point *h_src, 
 tt_status tt_misfit(tt_ctx *ctx, const void *d_T, int dtype, const tt_data *d, double *d_Tr,
                     double *d_chi, double *d_R) {
     if (!ctx) return TT_EINVAL;
-    if (!d || !d_T || !d_R || !d->d_abs_off || !d->d_cs_off)
-        return fail(ctx, TT_EINVAL, "tt_misfit: NULL argument");
-    if (dtype != TT_F32 && dtype != TT_F64) return fail(ctx, TT_EINVAL, "bad dtype %d", dtype);
-    if (d->n_src < 1 || d->n_src > TT_MAX_BATCH)
-        return fail(ctx, TT_EINVAL, "n_src = %d outside 1..%d", d->n_src, TT_MAX_BATCH);
-    if ((size_t)d->n_rec * 2 * 4 * sizeof(double) > 200 * 1024)
-        return fail(ctx, TT_EINVAL, "n_rec = %d too large for the misfit kernel", d->n_rec);
     tt_status s;
+    if ((s = check_data(ctx, d)) != TT_OK) return s;
+    if (!d_T || !d_R) return fail(ctx, TT_EINVAL, "tt_misfit: NULL argument");
+    if (dtype != TT_F32 && dtype != TT_F64) return fail(ctx, TT_EINVAL, "bad dtype %d", dtype);
+    const int S = 8 * d->n_rec;
     ENSURE(ctx->flags, 4 * sizeof(int));
-    CK(cudaMemsetAsync(ctx->flags.p, 0, 4 * sizeof(int), ctx->st));
-    if ((s = receivers_impl(ctx, d->h_rec, d->n_rec)) != TT_OK) return s;
-    int *bad = (int *)ctx->flags.p + 1;
-    if (dtype == TT_F32)
-        CK(run_misfit<float>(d->n_src, d->n_rec, d_T, (const long long *)ctx->cq.p,
-                             (const double *)ctx->wq.p, *d, d_Tr, d_chi, d_R, bad, ctx->st));
-    else
-        CK(run_misfit<double>(d->n_src, d->n_rec, d_T, (const long long *)ctx->cq.p,
-                              (const double *)ctx->wq.p, *d, d_Tr, d_chi, d_R, bad, ctx->st));
-    ctx->launches += 1;
-    int *h = ctx->h_pinned + 2 * TT_MAX_BATCH + 4;
-    CK(cudaMemcpyAsync(h, (int *)ctx->flags.p + 1, 2 * sizeof(int), cudaMemcpyDeviceToHost,
-                       ctx->st));
+    ENSURE(ctx->rpts, sizeof(PointD) * (size_t)d->n_rec);
+    ENSURE(ctx->cq, sizeof(long long) * S);
+    ENSURE(ctx->wq, sizeof(double) * S);
+    int *flags = (int *)ctx->flags.p;
+    CK(cudaMemsetAsync(flags, 0, 4 * sizeof(int), ctx->st));
+    if ((s = stage_to(ctx, d->h_rec, d->n_rec, (PointD *)ctx->rpts.p)) != TT_OK) return s;
+    if ((s = enq_receivers(ctx, (const PointD *)ctx->rpts.p, d->n_rec, (long long *)ctx->cq.p,
+                           (double *)ctx->wq.p, flags)) != TT_OK)
+        return s;
+    if ((s = enq_misfit(ctx, d_T, dtype, d, (const long long *)ctx->cq.p,
+                        (const double *)ctx->wq.p, flags, d_Tr, d_chi, d_R)) != TT_OK)
+        return s;
+    Readback r = readback_view(ctx);
+    CK(cudaMemcpyAsync(r.flags, flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
-    if (h[0]) return fail(ctx, TT_EINVAL, "tt_misfit: receiver index out of range in the data");
-    if (h[1]) return fail(ctx, TT_EINVAL, "tt_misfit: receiver outside the grid");
+    if (r.flags[1]) return fail(ctx, TT_EINVAL, "tt_misfit: receiver index out of range in the data");
+    if (r.flags[2]) return fail(ctx, TT_EINVAL, "tt_misfit: receiver outside the grid");
     return TT_OK;
 }
 
@@ -852,6 +1009,11 @@ tt_status tt_adjoint(tt_ctx *ctx, const tt_model *model, const tt_point *h_src, 
     if ((s = check_sources(ctx, h_src, n_src)) != TT_OK) return s;
     if ((s = check_opts(ctx, opts)) != TT_OK) return s;
     if (!d_T || !d_R || !d_P) return fail(ctx, TT_EINVAL, "tt_adjoint: NULL field");
+    if (n_rec < 1 || !h_rec) return fail(ctx, TT_EINVAL, "need at least one receiver");
+    for (int q = 0; q < n_rec; ++q)
+        if (!inside(ctx, h_rec[q]))
+            return fail(ctx, TT_EINVAL, "receiver %d (%g km, %g, %g) outside the grid", q,
+                        h_rec[q].depth_km, h_rec[q].lat_deg, h_rec[q].lon_deg);
     if (model->dtype == TT_F32)
         return adjoint_impl<float>(ctx, model, h_src, n_src, d_T, n_rec, h_rec, d_R, d_P, opts,
                                    h_iters);
@@ -868,14 +1030,7 @@ tt_status tt_kernel(tt_ctx *ctx, const tt_model *model, int n_src, const void *d
         return fail(ctx, TT_EINVAL, "n_src = %d outside 1..%d", n_src, TT_MAX_BATCH);
     if (!d_T || !d_P || !d_Ks || !d_Kxi || !d_Keta)
         return fail(ctx, TT_EINVAL, "tt_kernel: NULL argument");
-    if (model->dtype == TT_F32)
-        CK(run_kernel_accum<float>(ctx->g, n_src, model->d_s, d_T, d_P, ctx->gd.h2, ctx->gd.cost,
-                                   d_Ks, d_Kxi, d_Keta, ctx->n_sm, ctx->st));
-    else
-        CK(run_kernel_accum<double>(ctx->g, n_src, model->d_s, d_T, d_P, ctx->gd.h2,
-                                    ctx->gd.cost, d_Ks, d_Kxi, d_Keta, ctx->n_sm, ctx->st));
-    ctx->launches += 1;
-    return TT_OK;
+    return enq_kernel(ctx, model, n_src, d_T, d_P, d_Ks, d_Kxi, d_Keta);
 }
 
 tt_status tt_get_stats(const tt_ctx *ctx, int which, tt_stats *out) {
@@ -884,6 +1039,214 @@ tt_status tt_get_stats(const tt_ctx *ctx, int which, tt_stats *out) {
     *out = ctx->stats[which];
     out->launches = ctx->launches;
     return TT_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- plans (graph-captured steps)
+
+struct tt_plan {
+    tt_ctx *ctx = nullptr;
+    tt_model model;
+    tt_data data;
+    tt_opts opts;
+    int B = 0, n_rec = 0;
+    void *tau = nullptr, *T = nullptr, *P = nullptr;
+    double *chi = nullptr, *R = nullptr, *K[3] = {nullptr, nullptr, nullptr};
+    std::vector<void *> allocs;
+    std::vector<PointD> h_src;
+    Work<float> wf;
+    Work<double> wd;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    long long launches_per_run = 0;  // kernels in the graph, added to ctx->launches per run
+};
+
+namespace {
+
+template <typename F> tt_status plan_alloc(tt_plan *p, Work<F> &W) {
+    tt_ctx *ctx = p->ctx;
+    const GridC &g = ctx->g;
+    const int B = p->B, S = 8 * p->n_rec;
+    auto get = [&](size_t bytes, void **out) -> tt_status {
+        void *q = nullptr;
+        if (cudaMalloc(&q, bytes < 256 ? 256 : bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, TT_ENOMEM, "plan workspace allocation of %zu bytes failed", bytes);
+        }
+        p->allocs.push_back(q);
+        *out = q;
+        return TT_OK;
+    };
+    tt_status s;
+    W.t0c_slice = factor_slice(g, B, sizeof(F));
+    const size_t coef_bytes = sizeof(Vec4<F>) * (size_t)g.N * B;
+    W.coef_ok = coef_bytes <= kCoefBudgetBytes;
+#define TTGB_GET(field, bytes)                                              \
+    do {                                                                    \
+        void *q_;                                                           \
+        if ((s = get((bytes), &q_)) != TT_OK) return s;                     \
+        W.field = reinterpret_cast<decltype(W.field)>(q_);                  \
+    } while (0)
+    TTGB_GET(src_pts, sizeof(PointD) * B);
+    TTGB_GET(rec_pts, sizeof(PointD) * p->n_rec);
+    TTGB_GET(src, sizeof(SrcC) * B);
+    TTGB_GET(tabT, sizeof(Vec2<F>) * (size_t)g.nt * B);
+    TTGB_GET(tabP, sizeof(Vec2<F>) * (size_t)g.np * B);
+    TTGB_GET(rec, sizeof(NodeRec<F>) * (size_t)g.N);
+    TTGB_GET(t0c, sizeof(Vec4<F>) * (size_t)g.N * W.t0c_slice);
+    if (W.coef_ok) TTGB_GET(coef, coef_bytes);
+    TTGB_GET(partial, partial_bytes(ctx, B, sizeof(F)));
+    TTGB_GET(conv_f, sizeof(int) * B);
+    TTGB_GET(iters_f, sizeof(int) * B);
+    TTGB_GET(conv_a, sizeof(int) * B);
+    TTGB_GET(iters_a, sizeof(int) * B);
+    TTGB_GET(nact, sizeof(int) * kMaxBarrierGroups);
+    TTGB_GET(flags, 4 * sizeof(int));
+    TTGB_GET(bar, sizeof(BarrierState) * kMaxBarrierGroups);
+    TTGB_GET(cq, sizeof(long long) * S);
+    TTGB_GET(wq, sizeof(double) * S);
+    TTGB_GET(sidx, sizeof(int) * (size_t)g.N);
+    TTGB_GET(next, sizeof(int) * S);
+    TTGB_GET(heads, sizeof(int) * S);
+    TTGB_GET(nheads, sizeof(int));
+    TTGB_GET(JS, sizeof(F) * (size_t)S * B);
+#undef TTGB_GET
+    return TT_OK;
+}
+
+// Everything one step enqueues, in order; captured once into the plan's graph.
+template <typename F> tt_status plan_enqueue(tt_plan *p, Work<F> &W) {
+    tt_ctx *ctx = p->ctx;
+    const GridC &g = ctx->g;
+    tt_status s;
+    CK(cudaMemsetAsync(W.flags, 0, 4 * sizeof(int), ctx->st));
+    if ((s = enq_receivers(ctx, W.rec_pts, p->n_rec, W.cq, W.wq, W.flags)) != TT_OK) return s;
+    if ((s = enq_sources<F>(ctx, W, &p->model, p->B)) != TT_OK) return s;
+    if ((s = enq_forward<F>(ctx, W, &p->model, p->B, p->tau, p->T, &p->opts)) != TT_OK) return s;
+    if ((s = enq_readback(ctx, p->B, W.iters_f, W.conv_f, W.flags, W.bar, TT_STATS_FORWARD)) !=
+        TT_OK)
+        return s;
+    if ((s = enq_misfit(ctx, p->T, p->model.dtype, &p->data, W.cq, W.wq, W.flags, nullptr, p->chi,
+                        p->R)) != TT_OK)
+        return s;
+    if ((s = enq_adjoint<F>(ctx, W, &p->model, p->B, p->T, p->n_rec, p->R, p->P, &p->opts)) !=
+        TT_OK)
+        return s;
+    for (int q = 0; q < 3; ++q)
+        CK(cudaMemsetAsync(p->K[q], 0, sizeof(double) * (size_t)g.N, ctx->st));
+    if ((s = enq_kernel(ctx, &p->model, p->B, p->T, p->P, p->K[0], p->K[1], p->K[2])) != TT_OK)
+        return s;
+    return enq_readback(ctx, p->B, W.iters_a, W.conv_a, W.flags, W.bar, TT_STATS_ADJOINT);
+}
+
+template <typename F> tt_status plan_build(tt_plan *p, Work<F> &W, const tt_point *h_src) {
+    tt_ctx *ctx = p->ctx;
+    tt_status s;
+    if ((s = plan_alloc<F>(p, W)) != TT_OK) return s;
+    if ((s = stage_to(ctx, p->data.h_rec, p->n_rec, W.rec_pts)) != TT_OK) return s;
+    if ((s = stage_to(ctx, h_src, p->B, W.src_pts)) != TT_OK) return s;
+    CK(cudaStreamSynchronize(ctx->st));
+    // Sizes and launch shapes are decided on the host while capturing; the kernels and copies
+    // go into the graph. The legacy default stream cannot be captured, so the capture runs on
+    // a private stream; the graph is launched on the context's stream.
+    cudaStream_t cap = nullptr;
+    CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaStream_t own = ctx->st;
+    ctx->st = cap;
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    cudaGraph_t graph = nullptr;
+    const long long launches0 = ctx->launches;
+    if (e == cudaSuccess) {
+        s = plan_enqueue<F>(p, W);
+        e = cudaStreamEndCapture(cap, &graph);
+    }
+    p->launches_per_run = ctx->launches - launches0;
+    ctx->launches = launches0;
+    ctx->st = own;
+    cudaStreamDestroy(cap);
+    if (s != TT_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return s;
+    }
+    if (e != cudaSuccess)
+        return fail(ctx, TT_ECUDA, "stream capture of the step failed: %s", cudaGetErrorString(e));
+    p->graph = graph;
+    CK(cudaGraphInstantiate(&p->exec, graph, 0));
+    return TT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+tt_status tt_plan_create(tt_plan **out, tt_ctx *ctx, const tt_model *model,
+                         const tt_point *h_src, int n_src, const tt_data *data,
+                         const tt_opts *opts, void *d_tau, void *d_T, void *d_P, double *d_chi,
+                         double *d_R, double *d_Ks, double *d_Kxi, double *d_Keta) {
+    if (!out || !ctx) return TT_EINVAL;
+    *out = nullptr;
+    tt_status s;
+    if ((s = check_model(ctx, model)) != TT_OK) return s;
+    if ((s = check_sources(ctx, h_src, n_src)) != TT_OK) return s;
+    if ((s = check_opts(ctx, opts)) != TT_OK) return s;
+    if ((s = check_data(ctx, data)) != TT_OK) return s;
+    if (data->n_src != n_src) return fail(ctx, TT_EINVAL, "data describe %d sources, not %d",
+                                          data->n_src, n_src);
+    if (!d_tau || !d_T || !d_P || !d_R || !d_Ks || !d_Kxi || !d_Keta)
+        return fail(ctx, TT_EINVAL, "tt_plan_create: NULL buffer");
+    tt_plan *p = new tt_plan();
+    p->ctx = ctx;
+    p->model = *model;
+    p->data = *data;
+    p->opts = *opts;
+    p->B = n_src;
+    p->n_rec = data->n_rec;
+    p->tau = d_tau;
+    p->T = d_T;
+    p->P = d_P;
+    p->chi = d_chi;
+    p->R = d_R;
+    p->K[0] = d_Ks;
+    p->K[1] = d_Kxi;
+    p->K[2] = d_Keta;
+    p->h_src.resize(n_src);
+    for (int b = 0; b < n_src; ++b)
+        p->h_src[b] = PointD{h_src[b].depth_km, h_src[b].lat_deg, h_src[b].lon_deg};
+    s = model->dtype == TT_F32 ? plan_build<float>(p, p->wf, h_src)
+                               : plan_build<double>(p, p->wd, h_src);
+    if (s != TT_OK) {
+        tt_plan_destroy(p);
+        return s;
+    }
+    *out = p;
+    return TT_OK;
+}
+
+tt_status tt_plan_run(tt_plan *p, int *h_iters_fwd, int *h_iters_adj) {
+    if (!p) return TT_EINVAL;
+    tt_ctx *ctx = p->ctx;
+    CK(cudaGraphLaunch(p->exec, ctx->st));
+    ctx->launches += p->launches_per_run;
+    CK(cudaStreamSynchronize(ctx->st));
+    Readback r = readback_view(ctx);
+    if (r.flags[1]) return fail(ctx, TT_EINVAL, "tt_plan_run: receiver index out of range");
+    if (r.flags[2]) return fail(ctx, TT_EINVAL, "tt_plan_run: receiver outside the grid");
+    tt_status sf = solve_status(ctx, p->B, p->h_src.data(), h_iters_fwd, p->opts.max_iter_fwd,
+                                "tt_plan_run (forward)", TT_STATS_FORWARD);
+    if (sf != TT_OK && sf != TT_ENOTCONVERGED) return sf;
+    tt_status sa = solve_status(ctx, p->B, p->h_src.data(), h_iters_adj, p->opts.max_iter_adj,
+                                "tt_plan_run (adjoint)", TT_STATS_ADJOINT);
+    return sa != TT_OK ? sa : sf;
+}
+
+void tt_plan_destroy(tt_plan *p) {
+    if (!p) return;
+    if (p->ctx && p->ctx->st) cudaStreamSynchronize(p->ctx->st);
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    for (void *q : p->allocs) cudaFree(q);
+    delete p;
 }
 
 }  // extern "C"

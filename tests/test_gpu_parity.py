@@ -186,3 +186,29 @@ def test_device_wait_limit_returns_timeout(tt):
     assert e.value.status == tt.TT_ETIMEOUT
     tt.tt_forward(ctx, model, w.src, tau)
     ctx.close()
+
+
+def test_plan_replays_the_step_bitwise(tt):
+    """A captured plan gives the bits of the individual calls, run after run."""
+    import torch
+    w = I.small_case(15, shape=(13, 14, 16), n_src=33, n_rec=6)
+    ref = gpu_solve(w, "f32")
+    ctx = tt.tt_ctx_create(w.grid.as_dict())
+    model = tuple(to_dev(a, torch.float32) for a in (w.s, w.xi, w.eta))
+    shape = w.grid.shape + (w.n_src,)
+    tau, T, P = (torch.empty(shape, device="cuda") for _ in range(3))
+    data = tt.DeviceData.from_workload(w)
+    chi = torch.empty((w.n_src, 2), dtype=torch.float64, device="cuda")
+    R = torch.empty((w.n_src, data.n_rec), dtype=torch.float64, device="cuda")
+    K = [torch.empty(w.grid.shape, dtype=torch.float64, device="cuda") for _ in range(3)]
+    plan = tt.tt_plan_create(ctx, model, w.src, data, tau, T, P, chi, R, *K)
+    for _ in range(2):
+        itf, ita = tt.tt_plan_run(plan)
+        assert np.array_equal(itf, ref["iters_fwd"]) and np.array_equal(ita, ref["iters_adj"])
+        assert np.array_equal(tau.cpu().numpy(), ref["tau"])
+        assert np.array_equal(P.cpu().numpy(), ref["P"])
+        assert np.array_equal(R.cpu().numpy(), ref["R"])
+        for a, b in zip(K, ref["K"]):
+            assert np.array_equal(a.cpu().numpy(), b)
+    plan.close()
+    ctx.close()
