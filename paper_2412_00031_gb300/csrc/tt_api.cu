@@ -247,7 +247,8 @@ tt_status sweep_shape(tt_ctx *ctx, bool fwd, int B, const Schedule &S, int cap, 
                       int &block, int &slots) {
     block = sizeof(F) == 4 ? 512 : 256;
     size_t smem = (size_t)B * sizeof(F) * (fwd ? 1 : 2);
-    int per_sm = fwd ? forward_blocks_per_sm<F>(block, smem) : adjoint_blocks_per_sm<F>(block, smem);
+    int per_sm = fwd ? forward_blocks_per_sm<F>(block, smem, false)
+                     : adjoint_blocks_per_sm<F>(block, smem);
     if (per_sm <= 0) return fail(ctx, TT_ECUDA, "sweep kernel cannot be resident (B = %d)", B);
     if (per_sm > 2) per_sm = 2;
     long long max_grid = (long long)per_sm * ctx->n_sm;
@@ -479,6 +480,7 @@ tt_status enq_forward(tt_ctx *ctx, Work<F> &W, const tt_model *m, int B, void *d
     a.na = g.nr - 2;
     a.nb = g.nt - 2;
     a.nc = g.np - 2;
+    a.idx32 = (unsigned long long)g.N * (unsigned long long)(B > 8 ? B : 8) < (1ull << 32);
     CUtensorMap map_tau, map_rec;
     if (sched >= 2) {
         const TileShape sh = kTileShapes[sched - 2];
@@ -504,7 +506,7 @@ tt_status enq_forward(tt_ctx *ctx, Work<F> &W, const tt_model *m, int B, void *d
             // 256-thread blocks; one barrier group per resident block slot of an SM, so
             // each SM interleaves the groups; each group gets a multiple of 32 sources.
             const int block = 256;
-            int per_sm = forward_blocks_per_sm<F>(block, (size_t)n * sizeof(F));
+            int per_sm = forward_blocks_per_sm<F>(block, (size_t)n * sizeof(F), a.idx32 != 0);
             if (per_sm <= 0) return fail(ctx, TT_ECUDA, "sweep kernel cannot be resident");
             if (per_sm > kMaxBarrierGroups) per_sm = kMaxBarrierGroups;
             int max_grid = per_sm * ctx->n_sm;

@@ -116,6 +116,18 @@ __device__ __forceinline__ F factor_T0(const SrcReg<F> &S, int i, F r, F cth, F 
     return rho * S.inv_s0;  // 1 / T0 = 1 / (s0 sqrt(q))
 }
 
+// Rounding-explicit arithmetic: each call is one IEEE operation that the compiler neither
+// contracts nor reorders, so every kernel that calls lf_core performs bit-identical
+// arithmetic whatever code surrounds it.
+__device__ __forceinline__ float fma_(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float mul_(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float add_(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float sub_(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double sub_(double a, double b) { return __dsub_rn(a, b); }
+
 // Lax-Friedrichs update of tau at an interior node for one source (Sec. 3.1 with the
 // factor of factor_T0). Dividing the update by T0, with u = p0 / T0 and
 // e_d = 1 / (2 delta_d h_d):
@@ -128,27 +140,36 @@ __device__ __forceinline__ F factor_T0(const SrcReg<F> &S, int i, F r, F cth, F 
 template <typename F>
 __device__ __forceinline__ F lf_core(F invT0, F ur, F ut, F up, F tc, F trp, F trm, F ttp,
                                      F ttm, F tpp, F tpm, const NodeRec<F> &R, F er) {
-    F vr = tc * ur + (trp - trm) * er;
-    F vt = tc * ut + (ttp - ttm) * R.et;
-    F vp = tc * up + (tpp - tpm) * R.ep;
-    F q = vr * vr + ((F)1 - (F)2 * R.xi) * vt * vt + ((F)1 + (F)2 * R.xi) * vp * vp
-          + (F)4 * R.eta * vt * vp;
-    F H = sqrt_(q);
-    F num = R.s * invT0 - H + er * (trp + trm) + R.ct * (ttp + ttm) + R.cp * (tpp + tpm);
-    return num * R.invW;
+    const F vr = fma_(tc, ur, mul_(sub_(trp, trm), er));
+    const F vt = fma_(tc, ut, mul_(sub_(ttp, ttm), R.et));
+    const F vp = fma_(tc, up, mul_(sub_(tpp, tpm), R.ep));
+    const F kt = fma_((F)-2, R.xi, (F)1), kp = fma_((F)2, R.xi, (F)1);
+    // q = v_r^2 + (1 - 2 xi) v_t^2 + (1 + 2 xi) v_p^2 + 4 eta v_t v_p
+    const F q = fma_(vr, vr, fma_(mul_(kt, vt), vt,
+                                  fma_(mul_(kp, vp), vp, mul_(mul_((F)4 * R.eta, vt), vp))));
+    const F H = sqrt_(q);
+    const F num = fma_(er, add_(trp, trm),
+                       fma_(R.ct, add_(ttp, ttm), fma_(R.cp, add_(tpp, tpm), fma_(R.s, invT0, -H))));
+    return mul_(num, R.invW);
 }
 
 // ---------------------------------------------------------------------------------------
-// Grid-wide barrier for persistent cooperative launches. Every wait is bounded by a
-// deadline on the global nanosecond timer; on expiry the status word gets kDevTimeout and
-// the caller returns. All blocks eventually leave: a block that gave up never arrives
-// again, so the others' waits expire too.
+// Grid-wide barrier for persistent cooperative launches. Arrivals go to a monotonic
+// per-launch counter: barrier number m of a launch is complete once m * nblocks arrivals
+// have been counted, so a barrier costs one fire-and-forget atomic and the polling of one
+// L2 line. Every wait is bounded by a deadline on the global nanosecond timer; on expiry
+// the status word gets kDevTimeout and the caller returns. All blocks eventually leave: a
+// block that gave up never arrives again, so the others' waits expire too. The status word
+// is sticky, so later launches of the same solve stop at their first barrier.
 struct alignas(128) BarrierState {  // one L2 line per barrier group
-    unsigned int count;
-    unsigned int gen;
+    unsigned long long arrived;     // arrivals since the launch started
+    unsigned int left;              // blocks that have finished the launch
     int status;
-    int pad[29];
+    int pad[28];
 };
+
+// Arrivals the calling block waits for at its next barrier (read and written by thread 0).
+static __shared__ unsigned long long s_bar_target;
 
 __device__ __forceinline__ unsigned long long global_ns() {
     unsigned long long t;
@@ -156,20 +177,25 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
-__device__ __forceinline__ unsigned int ld_acquire(const unsigned int *p) {
-    unsigned int v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
 
-__device__ __forceinline__ void st_release(unsigned int *p, unsigned int v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+__device__ __forceinline__ void red_release_add(unsigned long long *p, unsigned long long v) {
+    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
 __device__ __forceinline__ int ld_status(const int *p) {
     int v;
     asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
+}
+
+// Called by every block of a launch before its first barrier.
+__device__ __forceinline__ void barrier_begin() {
+    if (threadIdx.x == 0) s_bar_target = 0;
 }
 
 // Returns false when the barrier (or an earlier one in another block) timed out. nblocks is
@@ -180,17 +206,14 @@ __device__ __forceinline__ bool grid_barrier(BarrierState *bs, unsigned long lon
     __syncthreads();
     if (threadIdx.x == 0) {
         int good = 1;
-        unsigned int gen = ld_acquire(&bs->gen);
+        const unsigned long long target = s_bar_target + nblocks;
+        s_bar_target = target;
         __threadfence();
-        unsigned int arrived = atomicAdd(&bs->count, 1u);
-        if (arrived == nblocks - 1) {
-            atomicExch(&bs->count, 0u);
-            __threadfence();
-            st_release(&bs->gen, gen + 1);
-        } else {
-            unsigned long long t0 = global_ns();
-            unsigned int ns = 32;
-            while (ld_acquire(&bs->gen) == gen) {
+        red_release_add(&bs->arrived, 1ull);
+        if (ld_acquire(&bs->arrived) < target) {
+            const unsigned long long t0 = global_ns();
+            unsigned int ns = 16;
+            while (ld_acquire(&bs->arrived) < target) {
                 if (global_ns() - t0 > limit_ns) {
                     atomicExch(&bs->status, (int)kDevTimeout);
                     good = 0;
@@ -210,6 +233,20 @@ __device__ __forceinline__ bool grid_barrier(BarrierState *bs, unsigned long lon
 
 __device__ __forceinline__ bool grid_barrier(BarrierState *bs, unsigned long long limit_ns) {
     return grid_barrier(bs, limit_ns, gridDim.x);
+}
+
+// Called by every block that reached the normal end of the launch: the last one to leave
+// clears the counters, so that the next launch on the same words starts from zero (launches
+// on one stream do not overlap).
+__device__ __forceinline__ void barrier_end(BarrierState *bs, unsigned int nblocks) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&bs->left, 1u) == nblocks - 1) {
+            atomicExch(&bs->arrived, 0ull);
+            atomicExch(&bs->left, 0u);
+        }
+    }
 }
 
 }  // namespace ttgb

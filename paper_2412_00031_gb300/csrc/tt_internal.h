@@ -65,6 +65,7 @@ template <typename F> struct FwdArgs {
     // the factor for them, [node][src_n]
     int src_lo, src_n;
     Vec4<F> *t0c;
+    int idx32;        // every [node][source] index fits in 32 bits
 };
 
 template <typename F> struct AdjArgs {
@@ -95,7 +96,7 @@ template <typename F> cudaError_t launch_forward(const FwdArgs<F> &a, int grid, 
                                                  cudaStream_t st);
 template <typename F> cudaError_t launch_adjoint(const AdjArgs<F> &a, int grid, int block,
                                                  cudaStream_t st);
-template <typename F> int forward_blocks_per_sm(int block, size_t smem);
+template <typename F> int forward_blocks_per_sm(int block, size_t smem, bool idx32);
 template <typename F> cudaError_t launch_t0_cache(const FwdArgs<F> &a, cudaStream_t st);
 
 // Tile shapes of the tile-wavefront forward sweep (sweep-local a = r, b = theta, c = phi).

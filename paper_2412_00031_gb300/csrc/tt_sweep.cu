@@ -33,7 +33,7 @@ __device__ __forceinline__ void unpack(unsigned int pk, int &a, int &b, int &c) 
 // ------------------------------------------------------------------------ forward sweep
 
 // Factor cache: 1/T0 and u = grad T0 / T0 (factor_T0) of every (node, source) of a launch,
-// computed once per solve. Every schedule reads the same cached values, so every schedule
+// computed once per solve; 1/T0 = -1 marks the nodes of the source's fixed set. Every schedule reads the same cached values, so every schedule
 // performs exactly the same arithmetic.
 template <typename F> __global__ void t0_cache_kernel(FwdArgs<F> a) {
     const GridC &g = a.g;
@@ -51,33 +51,18 @@ template <typename F> __global__ void t0_cache_kernel(FwdArgs<F> a) {
         c.x = factor_T0<F>(S, i, __ldg(a.rad + i), __ldg(a.cost + j), __ldg(a.sint + j),
                            a.tabT[(long long)j * a.B + b], a.tabP[(long long)k * a.B + b],
                            g.flat != 0, c.y, c.z, c.w);
+        // nodes of the fixed set are never swept: mark them with 1/T0 = -1
+        if (in_fixed_set(S.ci, S.cj, S.ck, i, j, k)) c.x = (F)-1;
         a.t0c[x] = c;
     }
 }
 
-// Lax-Friedrichs update of tau at interior node n for source b, reading the six neighbours
-// from global memory (node-hyperplane schedule).
-template <typename F>
-__device__ __forceinline__ F fwd_update(const FwdArgs<F> &a, int b, long long n, F &told) {
-    const long long B = a.B;
-    const long long sp = B, st = (long long)a.g.np * B, sr = (long long)a.g.nt * a.g.np * B;
-    const long long x = n * B + b;
-    const F *tau = a.tau;
-    const F tc = tau[x];
-    const F trp = tau[x + sr], trm = tau[x - sr];
-    const F ttp = tau[x + st], ttm = tau[x - st];
-    const F tpp = tau[x + sp], tpm = tau[x - sp];
-    const NodeRec<F> R = a.rec[n];
-    const Vec4<F> c = a.t0c[n * a.src_n + (b - a.src_lo)];
-    told = tc;
-    return lf_core<F>(c.x, c.y, c.z, c.w, tc, trp, trm, ttp, ttm, tpp, tpm, R, a.er);
-}
-
 // tau on one face layer = max(2 tau_1 - tau_2, tau_2); q enumerates both faces of an axis.
 template <typename F>
-__device__ __forceinline__ void extrapolate(const FwdArgs<F> &a, int ci, int cj, int ck, int b,
-                                            int axis, int slot, int slots) {
+__device__ __forceinline__ void extrapolate(const FwdArgs<F> &a, int b, int axis, int slot,
+                                            int slots) {
     const GridC &g = a.g;
+    const int ci = a.src[b].ci, cj = a.src[b].cj, ck = a.src[b].ck;  // fixed set centre
     const long long B = a.B;
     int n1, n2, nface;
     long long stride;
@@ -109,8 +94,50 @@ __device__ __forceinline__ void extrapolate(const FwdArgs<F> &a, int ci, int cj,
 // solve of its slice with its own grid barrier and convergence test, and so never waits for
 // another group; on each SM the warps of one group keep issuing while another group's warps
 // wait at their barrier.
-template <typename F>
-__global__ void __launch_bounds__(256) fwd_sweep_kernel(FwdArgs<F> a) {
+//
+// Within a group, a warp covers 64 consecutive sources of one node: lane l holds sources
+// l and l + 32 of its 64, so both of a lane's accesses are coalesced 128-byte lines and the
+// second is the first plus a constant offset. A slot is the set of warps that cover the
+// group's sources (padded to whole warps); on a hyperplane each slot takes the nodes slot,
+// slot + slots, ... and a thread handles kFwdBatch of them at once: it decodes all of them,
+// issues every load of the batch, and only then computes. The node record (8 values shared
+// by the warp) is loaded by lanes 0-7 in one 32-byte transaction and broadcast by shuffles.
+// The factor cache is read once per sweep and streamed past L2 (evict-first), so that it
+// does not push out the tau lines the next hyperplane reads again.
+#ifndef TTGB_FWD_BATCH
+#define TTGB_FWD_BATCH 1
+#endif
+#ifndef TTGB_FWD_MIN_BLOCKS
+#define TTGB_FWD_MIN_BLOCKS 4
+#endif
+constexpr int kFwdBatch = TTGB_FWD_BATCH;
+
+template <typename F> __device__ __forceinline__ NodeRec<F> rec_from_lanes(F v) {
+    NodeRec<F> R;
+    R.s = __shfl_sync(0xffffffffu, v, 0);
+    R.xi = __shfl_sync(0xffffffffu, v, 1);
+    R.eta = __shfl_sync(0xffffffffu, v, 2);
+    R.ct = __shfl_sync(0xffffffffu, v, 3);
+    R.cp = __shfl_sync(0xffffffffu, v, 4);
+    R.invW = __shfl_sync(0xffffffffu, v, 5);
+    R.et = __shfl_sync(0xffffffffu, v, 6);
+    R.ep = __shfl_sync(0xffffffffu, v, 7);
+    return R;
+}
+
+__device__ __forceinline__ Vec4<float> ld_stream(const Vec4<float> *p) {
+    const float4 v = __ldcs(reinterpret_cast<const float4 *>(p));
+    return Vec4<float>{v.x, v.y, v.z, v.w};
+}
+__device__ __forceinline__ Vec4<double> ld_stream(const Vec4<double> *p) {
+    const double2 v0 = __ldcs(reinterpret_cast<const double2 *>(p));
+    const double2 v1 = __ldcs(reinterpret_cast<const double2 *>(p) + 1);
+    return Vec4<double>{v0.x, v0.y, v1.x, v1.y};
+}
+
+// I: index type of the [node][source] fields (32-bit when every index fits).
+template <typename F, typename I>
+__global__ void __launch_bounds__(256, TTGB_FWD_MIN_BLOCKS) fwd_sweep_kernel(FwdArgs<F> a) {
     extern __shared__ unsigned char smem_raw[];
     F *s_err = reinterpret_cast<F *>(smem_raw);
     __shared__ int s_cnt;
@@ -121,41 +148,110 @@ __global__ void __launch_bounds__(256) fwd_sweep_kernel(FwdArgs<F> a) {
     const int src0 = a.src_lo + grp * a.grp_src;
     const int Bg = min(a.src_lo + a.src_n, src0 + a.grp_src) - src0;  // sources of the group
     if (Bg <= 0) return;
+    barrier_begin();
+    const int Bw = ((Bg + 63) >> 6) << 5;               // lanes of one slot
     BarrierState *bar = a.bar + grp;
     const unsigned nblk = (unsigned)a.grp_blocks;
-    const int slots = (int)(((long long)a.grp_blocks * blockDim.x) / Bg);
+    const int slots = (int)(((long long)a.grp_blocks * blockDim.x) / Bw);
     const long long tid = (long long)blk * blockDim.x + threadIdx.x;
-    const bool lane_ok = tid < (long long)slots * Bg;
-    const int b = src0 + (lane_ok ? (int)(tid % Bg) : 0);
-    const int slot = lane_ok ? (int)(tid / Bg) : 0;
-    const int ci = a.src[b].ci, cj = a.src[b].cj, ck = a.src[b].ck;  // fixed set centre
+    const bool lane_ok = tid < (long long)slots * Bw;   // uniform over a warp
+    const int bl = lane_ok ? (int)(tid % Bw) : 0;
+    const int slot = lane_ok ? (int)(tid / Bw) : 0;
+    const int lane = threadIdx.x & 31;
+    const int l0 = ((bl >> 5) << 6) + lane;             // the lane's first source in the group
+    const bool ok0 = lane_ok && l0 < Bg, ok1 = lane_ok && l0 + 32 < Bg;
+    const int b = src0 + (ok0 ? l0 : 0);                // second source: b + 32
+    const I sp = (I)B, st = (I)g.np * (I)B, sr = (I)g.nt * (I)g.np * (I)B;
+    const I snode_r = (I)g.nt * (I)g.np, snode_t = (I)g.np;
+    const F *recf = reinterpret_cast<const F *>(a.rec);
+    const Vec4<F> *t0c = a.t0c + (b - a.src_lo);
+    const I src_n = (I)a.src_n;
+    F *tau = a.tau;
 
     for (int it = 0; it < a.max_iter; ++it) {
-        const bool active = lane_ok && ((volatile int *)a.conv)[b] == 0;
-        F err = 0;
+        const bool act0 = ok0 && ((volatile int *)a.conv)[b] == 0;
+        const bool act1 = ok1 && ((volatile int *)a.conv)[b + 32] == 0;
+        const bool warp_active = __any_sync(0xffffffffu, act0 || act1);
+        F err0 = 0, err1 = 0;
         for (int o = 0; o < 8; ++o) {
             const bool rr = o & 4, rt = o & 2, rp = o & 1;
+            // node index of sweep-local (aa, bb, cc): n0 + aa * sa + bb * sb + cc * sc
+            const I n0 = (I)(rr ? g.nr - 2 : 1) * snode_r + (I)(rt ? g.nt - 2 : 1) * snode_t +
+                         (I)(rp ? g.np - 2 : 1);
+            const I sa = rr ? (I)0 - snode_r : snode_r, sb = rt ? (I)0 - snode_t : snode_t;
+            const I sc = rp ? (I)0 - (I)1 : (I)1;
             for (int L = 0; L < a.n_planes; ++L) {
-                if (active) {
+                if (warp_active && lane_ok) {
                     const int q1 = __ldg(a.off + L + 1);
-                    for (int q = __ldg(a.off + L) + slot; q < q1; q += slots) {
-                        int aa, bb, cc;
-                        unpack(__ldg(a.nodes + q), aa, bb, cc);
-                        const int i = rr ? g.nr - 2 - aa : 1 + aa;
-                        const int j = rt ? g.nt - 2 - bb : 1 + bb;
-                        const int k = rp ? g.np - 2 - cc : 1 + cc;
-                        if (in_fixed_set(ci, cj, ck, i, j, k)) continue;
-                        const long long n = node_index(g, i, j, k);
-                        F told;
-                        F tn = fwd_update<F>(a, b, n, told);
-                        a.tau[n * B + b] = tn;
-                        err = fmax_(err, fabs(tn - told));
+                    for (int qb = __ldg(a.off + L) + slot; qb < q1; qb += kFwdBatch * slots) {
+                        I n[kFwdBatch];
+                        bool nok[kFwdBatch];
+#pragma unroll
+                        for (int u = 0; u < kFwdBatch; ++u) {
+                            const int q = qb + u * slots;
+                            nok[u] = q < q1;  // uniform over the warp
+                            int aa = 0, bb = 0, cc = 0;
+                            if (nok[u]) unpack(__ldg(a.nodes + q), aa, bb, cc);
+                            n[u] = n0 + (I)aa * sa + (I)bb * sb + (I)cc * sc;
+                        }
+                        F t[kFwdBatch][2][7], rv[kFwdBatch];
+                        Vec4<F> c[kFwdBatch][2];
+#pragma unroll
+                        for (int u = 0; u < kFwdBatch; ++u) {
+                            const I x = n[u] * (I)B + (I)b;
+                            const F *p = tau + x;
+                            const Vec4<F> *pc = t0c + n[u] * src_n;
+                            if (nok[u] && act0) {
+                                t[u][0][0] = p[0];
+                                t[u][0][1] = p[sr];
+                                t[u][0][2] = *(p - sr);
+                                t[u][0][3] = p[st];
+                                t[u][0][4] = *(p - st);
+                                t[u][0][5] = p[sp];
+                                t[u][0][6] = *(p - sp);
+                                c[u][0] = ld_stream(pc);
+                            }
+                            if (nok[u] && act1) {
+                                t[u][1][0] = p[32];
+                                t[u][1][1] = p[sr + 32];
+                                t[u][1][2] = *(p - sr + 32);
+                                t[u][1][3] = p[st + 32];
+                                t[u][1][4] = *(p - st + 32);
+                                t[u][1][5] = p[sp + 32];
+                                t[u][1][6] = *(p - sp + 32);
+                                c[u][1] = ld_stream(pc + 32);
+                            }
+                            if (nok[u] && lane < 8) rv[u] = __ldg(recf + n[u] * (I)8 + (I)lane);
+                        }
+#pragma unroll
+                        for (int u = 0; u < kFwdBatch; ++u) {
+                            if (!nok[u]) continue;  // uniform: the shuffles see the whole warp
+                            const NodeRec<F> R = rec_from_lanes<F>(rv[u]);
+                            F *p = tau + (n[u] * (I)B + (I)b);
+                            if (act0 && c[u][0].x > (F)0) {
+                                const F *v = t[u][0];
+                                const F tn = lf_core<F>(c[u][0].x, c[u][0].y, c[u][0].z,
+                                                        c[u][0].w, v[0], v[1], v[2], v[3], v[4],
+                                                        v[5], v[6], R, a.er);
+                                p[0] = tn;
+                                err0 = fmax_(err0, fabs(tn - v[0]));
+                            }
+                            if (act1 && c[u][1].x > (F)0) {
+                                const F *v = t[u][1];
+                                const F tn = lf_core<F>(c[u][1].x, c[u][1].y, c[u][1].z,
+                                                        c[u][1].w, v[0], v[1], v[2], v[3], v[4],
+                                                        v[5], v[6], R, a.er);
+                                p[32] = tn;
+                                err1 = fmax_(err1, fabs(tn - v[0]));
+                            }
+                        }
                     }
                 }
                 if (!grid_barrier(bar, a.spin_ns, nblk)) return;
             }
             for (int axis = 0; axis < 3; ++axis) {
-                if (active) extrapolate<F>(a, ci, cj, ck, b, axis, slot, slots);
+                if (act0) extrapolate<F>(a, b, axis, slot, slots);
+                if (act1) extrapolate<F>(a, b + 32, axis, slot, slots);
                 if (!grid_barrier(bar, a.spin_ns, nblk)) return;
             }
         }
@@ -163,7 +259,8 @@ __global__ void __launch_bounds__(256) fwd_sweep_kernel(FwdArgs<F> a) {
         // maximum over the group's blocks by its first block, which also decides convergence.
         for (int x = threadIdx.x; x < Bg; x += blockDim.x) s_err[x] = 0;
         __syncthreads();
-        if (active) atomic_max_nonneg(&s_err[b - src0], err);
+        if (act0) atomic_max_nonneg(&s_err[b - src0], err0);
+        if (act1) atomic_max_nonneg(&s_err[b + 32 - src0], err1);
         __syncthreads();
         for (int x = threadIdx.x; x < Bg; x += blockDim.x)
             a.partial[(long long)blockIdx.x * B + src0 + x] = s_err[x];
@@ -186,6 +283,7 @@ __global__ void __launch_bounds__(256) fwd_sweep_kernel(FwdArgs<F> a) {
         if (!grid_barrier(bar, a.spin_ns, nblk)) return;
         if (((volatile int *)a.n_active)[grp] == 0) break;
     }
+    barrier_end(bar, nblk);
 }
 
 // ------------------------------------------------------------------------ tiled forward sweep
@@ -391,8 +489,8 @@ __global__ void __launch_bounds__(kTileThreads)
     const bool lane_ok = tid < (long long)a.slots * a.src_n;
     const int bx = a.src_lo + (lane_ok ? (int)(tid % a.src_n) : 0);
     const int slot = lane_ok ? (int)(tid / a.src_n) : 0;
-    const SrcReg<F> Sx = load_src<F>(a.src, bx, g.dr);
     const int s_end = a.src_lo + a.src_n;
+    barrier_begin();
 
     for (int it = 0; it < a.max_iter; ++it) {
         const bool act_x = lane_ok && ((volatile int *)a.conv)[bx] == 0;
@@ -421,7 +519,7 @@ __global__ void __launch_bounds__(kTileThreads)
                 if (!grid_barrier(a.bar, a.spin_ns)) return;
             }
             for (int axis = 0; axis < 3; ++axis) {
-                if (act_x) extrapolate<F>(a, Sx.ci, Sx.cj, Sx.ck, bx, axis, slot, a.slots);
+                if (act_x) extrapolate<F>(a, bx, axis, slot, a.slots);
                 if (!grid_barrier(a.bar, a.spin_ns)) return;
             }
         }
@@ -446,6 +544,7 @@ __global__ void __launch_bounds__(kTileThreads)
         if (!grid_barrier(a.bar, a.spin_ns)) return;
         if (*((volatile int *)a.n_active) == 0) break;
     }
+    barrier_end(a.bar, gridDim.x);
 }
 
 // ------------------------------------------------------------------------ adjoint sweep
@@ -579,6 +678,7 @@ __global__ void __launch_bounds__(512) adj_sweep_kernel(AdjArgs<F> a) {
     const int slot = lane_ok ? (int)(tid / B) : 0;
     const SrcC &sc = a.src[b];
     const int ci = sc.ci, cj = sc.cj, ck = sc.ck;
+    barrier_begin();
 
     for (int it = 0; it < a.max_iter; ++it) {
         const bool active = lane_ok && ((volatile int *)a.conv)[b] == 0;
@@ -638,6 +738,7 @@ __global__ void __launch_bounds__(512) adj_sweep_kernel(AdjArgs<F> a) {
         if (!grid_barrier(a.bar, a.spin_ns)) return;
         if (*((volatile int *)a.n_active) == 0) break;
     }
+    barrier_end(a.bar, gridDim.x);
 }
 
 // ------------------------------------------------------------------------ face-coefficient adjoint
@@ -734,6 +835,7 @@ __global__ void __launch_bounds__(256) adj_face_kernel(AdjArgs<F> a) {
     const int src0 = grp * a.grp_src;
     const int Bg = min(B, src0 + a.grp_src) - src0;
     if (Bg <= 0) return;
+    barrier_begin();
     F *s_err = reinterpret_cast<F *>(smem_raw);
     F *s_pmax = s_err + Bg;
     BarrierState *bar = a.bar + lgrp;  // launches of a chunked solve reuse the same words
@@ -840,6 +942,7 @@ __global__ void __launch_bounds__(256) adj_face_kernel(AdjArgs<F> a) {
         if (!grid_barrier(bar, a.spin_ns, nblk)) return;
         if (((volatile int *)a.n_active)[lgrp] == 0) break;
     }
+    barrier_end(bar, nblk);
 }
 
 // ------------------------------------------------------------------------ launchers
@@ -848,8 +951,8 @@ template <typename F>
 cudaError_t launch_forward(const FwdArgs<F> &a, int grid, int block, cudaStream_t st) {
     void *args[] = {const_cast<FwdArgs<F> *>(&a)};
     size_t smem = (size_t)a.grp_src * sizeof(F);
-    return cudaLaunchCooperativeKernel((void *)fwd_sweep_kernel<F>, dim3(grid), dim3(block),
-                                       args, smem, st);
+    void *fn = a.idx32 ? (void *)fwd_sweep_kernel<F, unsigned> : (void *)fwd_sweep_kernel<F, long long>;
+    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(block), args, smem, st);
 }
 
 template <typename F>
@@ -860,12 +963,13 @@ cudaError_t launch_adjoint(const AdjArgs<F> &a, int grid, int block, cudaStream_
                                        args, smem, st);
 }
 
-template <typename F> int forward_blocks_per_sm(int block, size_t smem) {
+template <typename F> int forward_blocks_per_sm(int block, size_t smem, bool idx32) {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fwd_sweep_kernel<F>, block, smem) !=
-        cudaSuccess)
-        return 0;
-    return n;
+    cudaError_t e = idx32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                &n, fwd_sweep_kernel<F, unsigned>, block, smem)
+                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                &n, fwd_sweep_kernel<F, long long>, block, smem);
+    return e == cudaSuccess ? n : 0;
 }
 
 template <typename F> int adjoint_blocks_per_sm(int block, size_t smem) {
@@ -979,8 +1083,8 @@ template cudaError_t launch_forward<float>(const FwdArgs<float> &, int, int, cud
 template cudaError_t launch_forward<double>(const FwdArgs<double> &, int, int, cudaStream_t);
 template cudaError_t launch_adjoint<float>(const AdjArgs<float> &, int, int, cudaStream_t);
 template cudaError_t launch_adjoint<double>(const AdjArgs<double> &, int, int, cudaStream_t);
-template int forward_blocks_per_sm<float>(int, size_t);
-template int forward_blocks_per_sm<double>(int, size_t);
+template int forward_blocks_per_sm<float>(int, size_t, bool);
+template int forward_blocks_per_sm<double>(int, size_t, bool);
 template int adjoint_blocks_per_sm<float>(int, size_t);
 template int adjoint_blocks_per_sm<double>(int, size_t);
 
