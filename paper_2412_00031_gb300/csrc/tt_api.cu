@@ -506,7 +506,7 @@ tt_status enq_forward(tt_ctx *ctx, Work<F> &W, const tt_model *m, int B, void *d
             // 256-thread blocks; one barrier group per resident block slot of an SM, so
             // each SM interleaves the groups; each group gets a multiple of 32 sources.
             const int block = 256;
-            int per_sm = forward_blocks_per_sm<F>(block, (size_t)n * sizeof(F), a.idx32 != 0);
+            int per_sm = forward_blocks_per_sm<F>(block, fwd_smem_bytes<F>(n, block), a.idx32 != 0);
             if (per_sm <= 0) return fail(ctx, TT_ECUDA, "sweep kernel cannot be resident");
             if (per_sm > kMaxBarrierGroups) per_sm = kMaxBarrierGroups;
             int max_grid = per_sm * ctx->n_sm;

@@ -71,7 +71,19 @@ template <typename F> __device__ __forceinline__ SrcReg<F> load_src(const SrcC *
 
 __device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsqrt_(double x) { return rsqrt(x); }
+#ifndef TTGB_SQRT_APPROX
+#define TTGB_SQRT_APPROX 1
+#endif
+// FP32: the hardware square root (sqrt.approx.f32), a single deterministic instruction.
+#if TTGB_SQRT_APPROX
+__device__ __forceinline__ float sqrt_(float x) {
+    float y;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+#else
 __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+#endif
 __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
 
 // T0 at node (i, j, k) for one source, returned as 1/T0 and u = p0 / T0, where p0 is the
@@ -156,8 +168,8 @@ __device__ __forceinline__ F lf_core(F invT0, F ur, F ut, F up, F tc, F trp, F t
 // ---------------------------------------------------------------------------------------
 // Grid-wide barrier for persistent cooperative launches. Arrivals go to a monotonic
 // per-launch counter: barrier number m of a launch is complete once m * nblocks arrivals
-// have been counted, so a barrier costs one fire-and-forget atomic and the polling of one
-// L2 line. Every wait is bounded by a deadline on the global nanosecond timer; on expiry
+// have been counted, so a barrier costs one acquire-release fence, one fire-and-forget
+// atomic and the polling of one L2 line. Every wait is bounded by a deadline on the global nanosecond timer; on expiry
 // the status word gets kDevTimeout and the caller returns. All blocks eventually leave: a
 // block that gave up never arrives again, so the others' waits expire too. The status word
 // is sticky, so later launches of the same solve stop at their first barrier.
@@ -183,8 +195,12 @@ __device__ __forceinline__ unsigned long long ld_acquire(const unsigned long lon
     return v;
 }
 
-__device__ __forceinline__ void red_release_add(unsigned long long *p, unsigned long long v) {
-    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+__device__ __forceinline__ void red_relaxed_add(unsigned long long *p, unsigned long long v) {
+    asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ void fence_acq_rel_gpu() {
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
 }
 
 __device__ __forceinline__ int ld_status(const int *p) {
@@ -208,8 +224,11 @@ __device__ __forceinline__ bool grid_barrier(BarrierState *bs, unsigned long lon
         int good = 1;
         const unsigned long long target = s_bar_target + nblocks;
         s_bar_target = target;
-        __threadfence();
-        red_release_add(&bs->arrived, 1ull);
+        // release: the fence orders the block's writes (made visible to this thread by
+        // __syncthreads) before the arrival; the acquiring load below pairs with the other
+        // blocks' fences, and __syncthreads passes the ordering on to the whole block
+        fence_acq_rel_gpu();
+        red_relaxed_add(&bs->arrived, 1ull);
         if (ld_acquire(&bs->arrived) < target) {
             const unsigned long long t0 = global_ns();
             unsigned int ns = 16;
@@ -223,7 +242,6 @@ __device__ __forceinline__ bool grid_barrier(BarrierState *bs, unsigned long lon
                 if (ns < 64) ns <<= 1;
             }
         }
-        __threadfence();
         if (good && ld_status(&bs->status) != 0) good = 0;
         ok = good;
     }

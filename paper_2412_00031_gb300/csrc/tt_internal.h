@@ -91,6 +91,13 @@ template <typename F> struct AdjArgs {
     unsigned long long spin_ns;
 };
 
+// Dynamic shared memory of the node-hyperplane forward sweep: the per-source maxima of a
+// barrier group, then (staged kernel) the two-stage copy buffers of every thread.
+template <typename F> __host__ __device__ inline size_t fwd_err_bytes(int grp_src) {
+    return ((size_t)grp_src * sizeof(F) + 127) / 128 * 128;
+}
+template <typename F> size_t fwd_smem_bytes(int grp_src, int block);
+
 // Launchers (tt_sweep.cu). They return a cudaError_t of the launch itself.
 template <typename F> cudaError_t launch_forward(const FwdArgs<F> &a, int grid, int block,
                                                  cudaStream_t st);

@@ -24,6 +24,10 @@ __device__ __forceinline__ void atomic_max_nonneg(double *p, double v) {
               (unsigned long long)__double_as_longlong(v));
 }
 
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
 __device__ __forceinline__ void unpack(unsigned int pk, int &a, int &b, int &c) {
     a = (int)(pk >> 20);
     b = (int)((pk >> 10) & 1023u);
@@ -99,18 +103,23 @@ __device__ __forceinline__ void extrapolate(const FwdArgs<F> &a, int b, int axis
 // l and l + 32 of its 64, so both of a lane's accesses are coalesced 128-byte lines and the
 // second is the first plus a constant offset. A slot is the set of warps that cover the
 // group's sources (padded to whole warps); on a hyperplane each slot takes the nodes slot,
-// slot + slots, ... and a thread handles kFwdBatch of them at once: it decodes all of them,
-// issues every load of the batch, and only then computes. The node record (8 values shared
-// by the warp) is loaded by lanes 0-7 in one 32-byte transaction and broadcast by shuffles.
-// The factor cache is read once per sweep and streamed past L2 (evict-first), so that it
-// does not push out the tau lines the next hyperplane reads again.
-#ifndef TTGB_FWD_BATCH
-#define TTGB_FWD_BATCH 1
-#endif
+// slot + slots, ... The schedule is static, so the index of a thread's next node, the
+// bounds of the next hyperplane and the index of its first node there are read one step
+// ahead (the latter two before the barrier), off the critical path. The node record (8
+// values shared by the warp) is loaded by lanes 0-7 in one 32-byte transaction and
+// broadcast by shuffles. The factor cache is read once per sweep and streamed past L2
+// (evict-first), so that it does not push out the tau lines the next hyperplane reads.
 #ifndef TTGB_FWD_MIN_BLOCKS
 #define TTGB_FWD_MIN_BLOCKS 4
 #endif
-constexpr int kFwdBatch = TTGB_FWD_BATCH;
+
+// Sweep-local node (aa, bb, cc) -> offset of its node index from the sweep's first node.
+template <typename I>
+__device__ __forceinline__ I node_local(unsigned pk, I sa, I sb, I sc) {
+    int aa, bb, cc;
+    unpack(pk, aa, bb, cc);
+    return (I)aa * sa + (I)bb * sb + (I)cc * sc;
+}
 
 template <typename F> __device__ __forceinline__ NodeRec<F> rec_from_lanes(F v) {
     NodeRec<F> R;
@@ -133,6 +142,17 @@ __device__ __forceinline__ Vec4<double> ld_stream(const Vec4<double> *p) {
     const double2 v0 = __ldcs(reinterpret_cast<const double2 *>(p));
     const double2 v1 = __ldcs(reinterpret_cast<const double2 *>(p) + 1);
     return Vec4<double>{v0.x, v0.y, v1.x, v1.y};
+}
+
+// Lax-Friedrichs update of one (node, source): tau at p, its six neighbours at p +- sr,
+// p +- st, p +- sp; c = the cached factors. Returns |change| (0 on the fixed set).
+template <typename F>
+__device__ __forceinline__ F update_one(F *p, const F *v, const Vec4<F> &c, const NodeRec<F> &R,
+                                        F er) {
+    if (!(c.x > (F)0)) return (F)0;
+    const F tn = lf_core<F>(c.x, c.y, c.z, c.w, v[0], v[1], v[2], v[3], v[4], v[5], v[6], R, er);
+    *p = tn;
+    return fabs(tn - v[0]);
 }
 
 // I: index type of the [node][source] fields (32-bit when every index fits).
@@ -171,7 +191,7 @@ __global__ void __launch_bounds__(256, TTGB_FWD_MIN_BLOCKS) fwd_sweep_kernel(Fwd
     for (int it = 0; it < a.max_iter; ++it) {
         const bool act0 = ok0 && ((volatile int *)a.conv)[b] == 0;
         const bool act1 = ok1 && ((volatile int *)a.conv)[b + 32] == 0;
-        const bool warp_active = __any_sync(0xffffffffu, act0 || act1);
+        const bool busy = lane_ok && __any_sync(0xffffffffu, act0 || act1);  // uniform
         F err0 = 0, err1 = 0;
         for (int o = 0; o < 8; ++o) {
             const bool rr = o & 4, rt = o & 2, rp = o & 1;
@@ -180,74 +200,54 @@ __global__ void __launch_bounds__(256, TTGB_FWD_MIN_BLOCKS) fwd_sweep_kernel(Fwd
                          (I)(rp ? g.np - 2 : 1);
             const I sa = rr ? (I)0 - snode_r : snode_r, sb = rt ? (I)0 - snode_t : snode_t;
             const I sc = rp ? (I)0 - (I)1 : (I)1;
+            // this thread's nodes of plane L: q = qa, qa + slots, ... < qe; pk = index of qa
+            int qa = __ldg(a.off) + slot, qe = __ldg(a.off + 1);
+            unsigned pk = busy && qa < qe ? __ldg(a.nodes + qa) : 0u;
             for (int L = 0; L < a.n_planes; ++L) {
-                if (warp_active && lane_ok) {
-                    const int q1 = __ldg(a.off + L + 1);
-                    for (int qb = __ldg(a.off + L) + slot; qb < q1; qb += kFwdBatch * slots) {
-                        I n[kFwdBatch];
-                        bool nok[kFwdBatch];
-#pragma unroll
-                        for (int u = 0; u < kFwdBatch; ++u) {
-                            const int q = qb + u * slots;
-                            nok[u] = q < q1;  // uniform over the warp
-                            int aa = 0, bb = 0, cc = 0;
-                            if (nok[u]) unpack(__ldg(a.nodes + q), aa, bb, cc);
-                            n[u] = n0 + (I)aa * sa + (I)bb * sb + (I)cc * sc;
+                const bool last = L + 1 == a.n_planes;
+                const int qe_next = last ? 0 : __ldg(a.off + L + 2);
+                if (busy) {
+                    for (int q = qa; q < qe; q += slots) {
+                        const int qn = q + slots;
+                        const unsigned pkn = qn < qe ? __ldg(a.nodes + qn) : 0u;
+                        const I n = n0 + node_local(pk, sa, sb, sc);
+                        F *p = tau + (n * (I)B + (I)b);
+                        const Vec4<F> *pc = t0c + n * src_n;
+                        F v0[7], v1[7], rv = 0;
+                        Vec4<F> c0, c1;
+                        if (act0) {
+                            v0[0] = p[0];
+                            v0[1] = p[sr];
+                            v0[2] = *(p - sr);
+                            v0[3] = p[st];
+                            v0[4] = *(p - st);
+                            v0[5] = p[sp];
+                            v0[6] = *(p - sp);
+                            c0 = ld_stream(pc);
                         }
-                        F t[kFwdBatch][2][7], rv[kFwdBatch];
-                        Vec4<F> c[kFwdBatch][2];
-#pragma unroll
-                        for (int u = 0; u < kFwdBatch; ++u) {
-                            const I x = n[u] * (I)B + (I)b;
-                            const F *p = tau + x;
-                            const Vec4<F> *pc = t0c + n[u] * src_n;
-                            if (nok[u] && act0) {
-                                t[u][0][0] = p[0];
-                                t[u][0][1] = p[sr];
-                                t[u][0][2] = *(p - sr);
-                                t[u][0][3] = p[st];
-                                t[u][0][4] = *(p - st);
-                                t[u][0][5] = p[sp];
-                                t[u][0][6] = *(p - sp);
-                                c[u][0] = ld_stream(pc);
-                            }
-                            if (nok[u] && act1) {
-                                t[u][1][0] = p[32];
-                                t[u][1][1] = p[sr + 32];
-                                t[u][1][2] = *(p - sr + 32);
-                                t[u][1][3] = p[st + 32];
-                                t[u][1][4] = *(p - st + 32);
-                                t[u][1][5] = p[sp + 32];
-                                t[u][1][6] = *(p - sp + 32);
-                                c[u][1] = ld_stream(pc + 32);
-                            }
-                            if (nok[u] && lane < 8) rv[u] = __ldg(recf + n[u] * (I)8 + (I)lane);
+                        if (act1) {
+                            v1[0] = p[32];
+                            v1[1] = p[sr + 32];
+                            v1[2] = *(p - sr + 32);
+                            v1[3] = p[st + 32];
+                            v1[4] = *(p - st + 32);
+                            v1[5] = p[sp + 32];
+                            v1[6] = *(p - sp + 32);
+                            c1 = ld_stream(pc + 32);
                         }
-#pragma unroll
-                        for (int u = 0; u < kFwdBatch; ++u) {
-                            if (!nok[u]) continue;  // uniform: the shuffles see the whole warp
-                            const NodeRec<F> R = rec_from_lanes<F>(rv[u]);
-                            F *p = tau + (n[u] * (I)B + (I)b);
-                            if (act0 && c[u][0].x > (F)0) {
-                                const F *v = t[u][0];
-                                const F tn = lf_core<F>(c[u][0].x, c[u][0].y, c[u][0].z,
-                                                        c[u][0].w, v[0], v[1], v[2], v[3], v[4],
-                                                        v[5], v[6], R, a.er);
-                                p[0] = tn;
-                                err0 = fmax_(err0, fabs(tn - v[0]));
-                            }
-                            if (act1 && c[u][1].x > (F)0) {
-                                const F *v = t[u][1];
-                                const F tn = lf_core<F>(c[u][1].x, c[u][1].y, c[u][1].z,
-                                                        c[u][1].w, v[0], v[1], v[2], v[3], v[4],
-                                                        v[5], v[6], R, a.er);
-                                p[32] = tn;
-                                err1 = fmax_(err1, fabs(tn - v[0]));
-                            }
-                        }
+                        if (lane < 8) rv = __ldg(recf + n * (I)8 + (I)lane);
+                        const NodeRec<F> R = rec_from_lanes<F>(rv);  // uniform loop: whole warp
+                        if (act0) err0 = fmax_(err0, update_one<F>(p, v0, c0, R, a.er));
+                        if (act1) err1 = fmax_(err1, update_one<F>(p + 32, v1, c1, R, a.er));
+                        pk = pkn;
                     }
                 }
+                // first node of the next plane (static: needs no barrier)
+                const int qa_next = qe + slot;
+                if (busy && !last && qa_next < qe_next) pk = __ldg(a.nodes + qa_next);
                 if (!grid_barrier(bar, a.spin_ns, nblk)) return;
+                qa = qa_next;
+                qe = qe_next;
             }
             for (int axis = 0; axis < 3; ++axis) {
                 if (act0) extrapolate<F>(a, b, axis, slot, slots);
@@ -299,9 +299,6 @@ __global__ void __launch_bounds__(256, TTGB_FWD_MIN_BLOCKS) fwd_sweep_kernel(Fwd
 // barriers (every node sees exactly the neighbour values of the lexicographic sweep) and
 // writes the tile back with coalesced 128-byte stores (lanes = sources).
 
-__device__ __forceinline__ unsigned smem_u32(const void *p) {
-    return (unsigned)__cvta_generic_to_shared(p);
-}
 
 __device__ __forceinline__ void mbar_init(unsigned long long *bar) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
@@ -950,8 +947,10 @@ __global__ void __launch_bounds__(256) adj_face_kernel(AdjArgs<F> a) {
 template <typename F>
 cudaError_t launch_forward(const FwdArgs<F> &a, int grid, int block, cudaStream_t st) {
     void *args[] = {const_cast<FwdArgs<F> *>(&a)};
-    size_t smem = (size_t)a.grp_src * sizeof(F);
+    const size_t smem = fwd_smem_bytes<F>(a.grp_src, block);
     void *fn = a.idx32 ? (void *)fwd_sweep_kernel<F, unsigned> : (void *)fwd_sweep_kernel<F, long long>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
     return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(block), args, smem, st);
 }
 
@@ -963,12 +962,17 @@ cudaError_t launch_adjoint(const AdjArgs<F> &a, int grid, int block, cudaStream_
                                        args, smem, st);
 }
 
+template <typename F> size_t fwd_smem_bytes(int grp_src, int) {
+    return fwd_err_bytes<F>(grp_src);
+}
+
 template <typename F> int forward_blocks_per_sm(int block, size_t smem, bool idx32) {
     int n = 0;
-    cudaError_t e = idx32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                                &n, fwd_sweep_kernel<F, unsigned>, block, smem)
-                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                                &n, fwd_sweep_kernel<F, long long>, block, smem);
+    void *fn = idx32 ? (void *)fwd_sweep_kernel<F, unsigned> : (void *)fwd_sweep_kernel<F, long long>;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, block, smem);
     return e == cudaSuccess ? n : 0;
 }
 
@@ -1083,6 +1087,8 @@ template cudaError_t launch_forward<float>(const FwdArgs<float> &, int, int, cud
 template cudaError_t launch_forward<double>(const FwdArgs<double> &, int, int, cudaStream_t);
 template cudaError_t launch_adjoint<float>(const AdjArgs<float> &, int, int, cudaStream_t);
 template cudaError_t launch_adjoint<double>(const AdjArgs<double> &, int, int, cudaStream_t);
+template size_t fwd_smem_bytes<float>(int, int);
+template size_t fwd_smem_bytes<double>(int, int);
 template int forward_blocks_per_sm<float>(int, size_t, bool);
 template int forward_blocks_per_sm<double>(int, size_t, bool);
 template int adjoint_blocks_per_sm<float>(int, size_t);
