@@ -241,6 +241,7 @@ def gpu_arm(args, rank, world):
     gp = GpuPath(w, dev)
     gp.opts.sweep_schedule = args.schedule
     gp.opts.adj_chunk = args.adj_chunk
+    gp.opts.launch_blocks = args.launch_blocks
     if args.max_iter_fwd or args.max_iter_adj:  # profiling runs only: bounded iterations
         gp.opts.max_iter_fwd = args.max_iter_fwd or gp.opts.max_iter_fwd
         gp.opts.max_iter_adj = args.max_iter_adj or gp.opts.max_iter_adj
@@ -436,6 +437,8 @@ def main():
     ap.add_argument("--plan", type=int, default=1,
                     help="1: replay the step as one captured CUDA graph (tt_plan); 0: the four "
                          "individual calls")
+    ap.add_argument("--launch-blocks", type=int, default=0,
+                    help="profiling runs: cap on the blocks of a persistent launch")
     ap.add_argument("--adj-chunk", type=int, default=0,
                     help="adjoint sources per launch (tt_opts.adj_chunk; 0 = automatic)")
     ap.add_argument("--schedule", type=int, default=0,
