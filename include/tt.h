@@ -98,7 +98,8 @@ typedef struct {
     double tol_fwd;         /* stop when the largest |tau change| of one iteration < tol_fwd */
     double tol_adj;         /* stop when the largest |P change| <= tol_adj * max |P| */
     int max_iter_fwd, max_iter_adj;
-    int init;               /* tt_forward: 0 = start from tau = 1, 1 = start from the tau passed in */
+    int init;               /* tt_forward: 0 = start from tau = 1, 1 = start from the tau passed
+                               in, 2 = start from the warm-start network (tt_net_set_weights) */
     long long spin_limit_ns;/* bound on every device-side wait; 0 = 2 s */
     int launch_blocks;      /* persistent sweep launch: 0 = automatic, else at most this many
                                blocks (results do not depend on it) */
@@ -193,6 +194,44 @@ tt_status tt_kernel(tt_ctx *ctx, const tt_model *model, int n_src, const void *d
 tt_status tt_misfit_noalloc(const tt_grid *grid, const void *d_T, int dtype,
                             const tt_data *data, double *d_Tr, double *d_chi, double *d_R,
                             void *cuda_stream, char *h_err, int err_len);
+
+/* ---- Warm-start network. A small 3D convolutional network predicts the factored correction
+ * tau of Sec. 3.1 (T = T0 tau) from local quantities, so that the forward sweep of Sec. 3.1
+ * starts closer to its fixed point (opts.init = 2); the sweep still runs to tol_fwd, so the
+ * result meets the same tolerance whatever the network predicts.
+ *
+ * Input: six channels per node, s / s0 - 1 (s0 = slowness at the source), xi, eta, and the
+ * offset D to the source in the source's (up, north, east) frame in units of 100 km (the
+ * offset that defines T0). Network: four 3x3x3 convolutions 6 -> 32 -> 32 -> 32 -> 1, zero
+ * padding outside the grid, ReLU after the first three; output y; warm start
+ * tau = 1 + clamp(y, -0.5, 1) (the fixed set keeps tau = 1).
+ * Parameters: one FP32 vector of tt_net_param_count() values: for each layer l, weights
+ * W[27][C_in][C_out] (tap (dz * 3 + dy) * 3 + dx reads the node at offset (dz-1, dy-1, dx-1)
+ * along (r, theta, phi)), then biases b[C_out].
+ * Fields are channels-last FP32 on the context's grid: features [n][N][6], outputs [n][N].
+ * All calls below wait for the context's stream before returning. */
+int tt_net_param_count(void);
+/* d_x (device [n_src][N][6] float) = the network input for each source. */
+tt_status tt_net_features(tt_ctx *ctx, const tt_model *model, const tt_point *h_src, int n_src,
+                          float *d_x);
+/* d_y (device [n_grids][N] float) = network output y for n_grids inputs d_x, FP32 weights. */
+tt_status tt_net_forward(tt_ctx *ctx, const float *d_theta, const float *d_x, int n_grids,
+                         float *d_y);
+/* Masked mean squared error loss = sum m (y - (tau - 1))^2 / sum m over n_grids grids
+ * (d_target = the converged tau and d_mask, device [n_grids][N] float) and its gradient
+ * with respect to the parameters
+ * (d_grad, device [tt_net_param_count()], overwritten). The loss goes to *h_loss (may be
+ * NULL). Deterministic: fixed-order reductions. */
+tt_status tt_net_loss_grad(tt_ctx *ctx, const float *d_theta, const float *d_x,
+                           const float *d_target, const float *d_mask, int n_grids,
+                           float *d_grad, double *h_loss);
+/* One Adam step (Kingma & Ba) on d_theta with first and second moments d_m, d_v (device,
+ * zero before step 1); step counts from 1. */
+tt_status tt_net_adam(tt_ctx *ctx, float *d_theta, const float *d_grad, float *d_m, float *d_v,
+                      int step, float lr, float beta1, float beta2, float eps);
+/* Stores the weights the warm start uses (device FP32 vector, rounded to BF16 and kept by
+ * the context; inference accumulates in FP32). Needed before opts.init = 2. */
+tt_status tt_net_set_weights(tt_ctx *ctx, const float *d_theta);
 
 /* A plan: one whole step over one batch (forward, misfit and adjoint sources, adjoint,
  * kernels) captured once into a CUDA graph and replayed by tt_plan_run, so that a step costs

@@ -72,7 +72,9 @@ TT_STATS_FORWARD, TT_STATS_ADJOINT = 0, 1
 
 EXPORTED = ["tt_default_opts", "tt_ctx_create", "tt_ctx_destroy", "tt_last_error",
             "tt_forward", "tt_misfit", "tt_adjoint", "tt_kernel", "tt_get_stats",
-            "tt_misfit_noalloc", "tt_plan_create", "tt_plan_run", "tt_plan_destroy"]
+            "tt_misfit_noalloc", "tt_plan_create", "tt_plan_run", "tt_plan_destroy",
+            "tt_net_param_count", "tt_net_features", "tt_net_forward", "tt_net_loss_grad",
+            "tt_net_adam", "tt_net_set_weights"]
 TT_NOALLOC_MAX_REC = 1024
 
 
@@ -106,8 +108,18 @@ def _load():
     L.tt_plan_run.argtypes = [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]
     L.tt_plan_destroy.argtypes = [C.c_void_p]
     L.tt_plan_destroy.restype = None
+    L.tt_net_param_count.argtypes = []
+    L.tt_net_features.argtypes = [C.c_void_p, C.POINTER(TTModel), C.POINTER(TTPoint), C.c_int,
+                                  C.c_void_p]
+    L.tt_net_forward.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]
+    L.tt_net_loss_grad.argtypes = [C.c_void_p] + [C.c_void_p] * 4 + [C.c_int, C.c_void_p,
+                                                                       C.POINTER(C.c_double)]
+    L.tt_net_adam.argtypes = [C.c_void_p] + [C.c_void_p] * 4 + [C.c_int] + [C.c_float] * 4
+    L.tt_net_set_weights.argtypes = [C.c_void_p, C.c_void_p]
     for name in ("tt_ctx_create", "tt_forward", "tt_misfit", "tt_adjoint", "tt_kernel",
-                 "tt_get_stats", "tt_misfit_noalloc", "tt_plan_create", "tt_plan_run"):
+                 "tt_get_stats", "tt_misfit_noalloc", "tt_plan_create", "tt_plan_run",
+                 "tt_net_param_count", "tt_net_features", "tt_net_forward", "tt_net_loss_grad",
+                 "tt_net_adam", "tt_net_set_weights"):
         getattr(L, name).restype = C.c_int
     return L
 
@@ -346,3 +358,55 @@ def tt_plan_run(plan, allow_unconverged=False):
     st = lib.tt_plan_run(plan.handle, itf, ita)
     _check(plan.ctx, st, (TT_ENOTCONVERGED,) if allow_unconverged else ())
     return (np.frombuffer(itf, dtype=np.int32).copy(), np.frombuffer(ita, dtype=np.int32).copy())
+
+
+# ----------------------------------------------------------------------- warm-start network
+
+def tt_net_param_count():
+    return int(lib.tt_net_param_count())
+
+
+def _f32(*tensors):
+    import torch
+    for x in tensors:
+        if x.dtype != torch.float32 or not x.is_contiguous():
+            raise TypeError("network buffers must be contiguous float32 CUDA tensors")
+
+
+def tt_net_features(ctx, model, src, x):
+    """x: float32 [n_src, N_r, N_t, N_p, 6] (or any contiguous shape of that size)."""
+    M = _model(model)
+    _cuda_ok(x)
+    _f32(x)
+    pts, n = _points(src)
+    _check(ctx, lib.tt_net_features(ctx.handle, C.byref(M), pts, n, _ptr(x)))
+
+
+def tt_net_forward(ctx, theta, x, y):
+    """y[n] = network(x[n]) for the n = x.shape[0] grids of the context."""
+    _cuda_ok(theta, x, y)
+    _f32(theta, x, y)
+    _check(ctx, lib.tt_net_forward(ctx.handle, _ptr(theta), _ptr(x), x.shape[0], _ptr(y)))
+
+
+def tt_net_loss_grad(ctx, theta, x, target, mask, grad):
+    """Masked MSE of the network output against target; writes grad, returns the loss."""
+    _cuda_ok(theta, x, target, mask, grad)
+    _f32(theta, x, target, mask, grad)
+    loss = C.c_double()
+    _check(ctx, lib.tt_net_loss_grad(ctx.handle, _ptr(theta), _ptr(x), _ptr(target), _ptr(mask),
+                                     x.shape[0], _ptr(grad), C.byref(loss)))
+    return loss.value
+
+
+def tt_net_adam(ctx, theta, grad, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+    _cuda_ok(theta, grad, m, v)
+    _f32(theta, grad, m, v)
+    _check(ctx, lib.tt_net_adam(ctx.handle, _ptr(theta), _ptr(grad), _ptr(m), _ptr(v), int(step),
+                                lr, beta1, beta2, eps))
+
+
+def tt_net_set_weights(ctx, theta):
+    _cuda_ok(theta)
+    _f32(theta)
+    _check(ctx, lib.tt_net_set_weights(ctx.handle, _ptr(theta)))

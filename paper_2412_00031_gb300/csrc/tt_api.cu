@@ -14,6 +14,7 @@
 #include "tt.h"
 #include "tt_aux.h"
 #include "tt_internal.h"
+#include "tt_net.h"
 
 using namespace ttgb;
 
@@ -41,6 +42,11 @@ struct tt_ctx {
     // workspace, grown on demand
     DevBuf src, pts, rpts, tabT, tabP, rec, partial, conv, iters, nact, bar, flags;
     DevBuf cq, wq, sidx, next, heads, nheads, JS, coef, t0c;
+    // warm-start network: inference weights (BF16-rounded) and its workspace
+    DevBuf net_theta, net_x, net_a, net_b, net_y, net_d1, net_d2, net_dy, net_wt, net_part,
+        net_scr;
+    bool has_net = false;
+    double *h_loss = nullptr;  // pinned
     int *h_pinned = nullptr;  // readback: [0..TT_MAX_BATCH) iterations, then flags
     PointD *h_pts = nullptr;  // staging for source / receiver positions
     size_t h_pts_cap = 0;
@@ -293,6 +299,9 @@ tt_status check_opts(tt_ctx *ctx, const tt_opts *o) {
         return fail(ctx, TT_EINVAL, "tolerances must be > 0 and iteration limits >= 1");
     if (o->sweep_schedule < 0 || o->sweep_schedule > 1 + kNumTileShapes)
         return fail(ctx, TT_EINVAL, "sweep_schedule %d unknown", o->sweep_schedule);
+    if (o->init < 0 || o->init > 2) return fail(ctx, TT_EINVAL, "init %d unknown", o->init);
+    if (o->init == 2 && !ctx->has_net)
+        return fail(ctx, TT_EINVAL, "init = 2 (warm start) needs tt_net_set_weights first");
     return TT_OK;
 }
 
@@ -318,7 +327,20 @@ template <typename F> struct Work {
     F *JS = nullptr;
     int t0c_slice = 0;  // sources per forward slice the factor cache holds
     bool coef_ok = false;
+    // warm start: features [chunk][N][6], activations [chunk][N][32] (two), output [chunk][N]
+    float *net_x = nullptr, *net_a = nullptr, *net_b = nullptr, *net_y = nullptr;
+    const float *net_theta = nullptr;
+    int net_chunk = 0;
 };
+
+// Sources per warm-start inference pass: two activation buffers of at most ~8 GB together.
+int net_chunk(const GridC &g, int B) {
+    const size_t per_src = (size_t)g.N * kNetHidden * sizeof(float);
+    long long c = (long long)((4ull << 30) / per_src);
+    if (c < 1) c = 1;
+    if (c > 8) c = 8;
+    return (int)(c < B ? c : B);
+}
 
 int factor_slice(const GridC &g, int B, size_t es) {
     const size_t per_src = 4 * es * (size_t)g.N;
@@ -386,6 +408,23 @@ template <typename F> tt_status work_from_ctx(tt_ctx *ctx, Work<F> &W, int B, in
     return TT_OK;
 }
 
+// Warm-start inference buffers from the context workspace.
+template <typename F> tt_status net_work_from_ctx(tt_ctx *ctx, Work<F> &W, int B) {
+    const GridC &g = ctx->g;
+    const int c = net_chunk(g, B);
+    ENSURE(ctx->net_x, sizeof(float) * kNetFeatures * (size_t)g.N * c);
+    ENSURE(ctx->net_a, sizeof(float) * kNetHidden * (size_t)g.N * c);
+    ENSURE(ctx->net_b, sizeof(float) * kNetHidden * (size_t)g.N * c);
+    ENSURE(ctx->net_y, sizeof(float) * (size_t)g.N * c);
+    W.net_x = (float *)ctx->net_x.p;
+    W.net_a = (float *)ctx->net_a.p;
+    W.net_b = (float *)ctx->net_b.p;
+    W.net_y = (float *)ctx->net_y.p;
+    W.net_theta = (const float *)ctx->net_theta.p;
+    W.net_chunk = c;
+    return TT_OK;
+}
+
 // Host positions -> pinned staging -> device (synchronises the stream first: the staging
 // buffer may still be read by an earlier call).
 tt_status stage_to(tt_ctx *ctx, const tt_point *h, int n, PointD *d) {
@@ -429,6 +468,43 @@ tt_status enq_sources(tt_ctx *ctx, Work<F> &W, const tt_model *m, int B) {
     return TT_OK;
 }
 
+// Network forward over d.nb grids: x (6 channels) -> a1 -> a2 -> a3 -> y. For inference
+// a3 may alias a1.
+tt_status enq_net_forward(tt_ctx *ctx, const float *theta, const float *x, const ConvDims &d,
+                          float *a1, float *a2, float *a3, float *y) {
+    const float *in = x;
+    float *outs[kNetLayers] = {a1, a2, a3, y};
+    for (int l = 0; l < kNetLayers; ++l) {
+        const float *w = theta + net_weight_offset(l);
+        const float *bias = w + 27 * kNetCin[l] * kNetCout[l];
+        CK(run_conv3d(d, kNetCin[l], kNetCout[l], in, l > 0, w, bias, nullptr, outs[l], ctx->st));
+        in = outs[l];
+    }
+    ctx->launches += kNetLayers;
+    return TT_OK;
+}
+
+// tau = 1 + clamp(net(features), -0.5, 1) for every source, in chunks of W.net_chunk.
+template <typename F>
+tt_status enq_warm_start(tt_ctx *ctx, Work<F> &W, const tt_model *m, int B, F *tau) {
+    const GridC &g = ctx->g;
+    const GeoTab<F> &t = geo<F>(ctx);
+    tt_status s;
+    for (int b0 = 0; b0 < B; b0 += W.net_chunk) {
+        const int nb = W.net_chunk < B - b0 ? W.net_chunk : B - b0;
+        CK(run_net_features<F>(g, B, b0, nb, W.src, W.tabT, W.tabP, t.rad, t.cost,
+                               (const F *)m->d_s, (const F *)m->d_xi, (const F *)m->d_eta,
+                               W.net_x, ctx->st));
+        const ConvDims d{nb, g.nr, g.nt, g.np};
+        if ((s = enq_net_forward(ctx, W.net_theta, W.net_x, d, W.net_a, W.net_b, W.net_a,
+                                 W.net_y)) != TT_OK)
+            return s;
+        CK(run_warm_tau<F>(g.N, B, b0, nb, W.net_y, tau, ctx->st));
+        ctx->launches += 2;
+    }
+    return TT_OK;
+}
+
 template <typename F>
 tt_status enq_forward(tt_ctx *ctx, Work<F> &W, const tt_model *m, int B, void *d_tau,
                       void *d_T, const tt_opts *o) {
@@ -441,6 +517,7 @@ tt_status enq_forward(tt_ctx *ctx, Work<F> &W, const tt_model *m, int B, void *d
     CK(cudaMemsetAsync(W.flags, 0, sizeof(int), ctx->st));
     CK(run_node_records<F>(g, m->d_s, m->d_xi, m->d_eta, ctx->gd.h2, ctx->gd.cost, W.rec,
                            W.flags, ctx->st));
+    if (o->init == 2 && (s = enq_warm_start<F>(ctx, W, m, B, (F *)d_tau)) != TT_OK) return s;
     CK(run_tau_init<F>(g, B, W.src, (F *)d_tau, o->init == 0, ctx->st));
     ctx->launches += 1 + (o->init == 0 ? 2 : 1);
 
@@ -806,6 +883,7 @@ tt_status forward_impl(tt_ctx *ctx, const tt_model *m, const tt_point *h_src, in
     ENSURE(ctx->pts, sizeof(PointD) * (size_t)B);
     Work<F> W;
     if ((s = work_from_ctx<F>(ctx, W, B, 0)) != TT_OK) return s;
+    if (o->init == 2 && (s = net_work_from_ctx<F>(ctx, W, B)) != TT_OK) return s;
     if ((s = stage_to(ctx, h_src, B, W.src_pts)) != TT_OK) return s;
     if ((s = enq_sources<F>(ctx, W, m, B)) != TT_OK) return s;
     if ((s = enq_forward<F>(ctx, W, m, B, d_tau, d_T, o)) != TT_OK) return s;
@@ -948,9 +1026,12 @@ void tt_ctx_destroy(tt_ctx *ctx) {
     DevBuf *bufs[] = {&ctx->src, &ctx->pts, &ctx->rpts, &ctx->tabT, &ctx->tabP, &ctx->rec, &ctx->partial,
                       &ctx->conv, &ctx->iters, &ctx->nact, &ctx->bar, &ctx->flags, &ctx->cq,
                       &ctx->wq, &ctx->sidx, &ctx->next, &ctx->heads, &ctx->nheads, &ctx->JS,
-                      &ctx->coef, &ctx->t0c};
+                      &ctx->coef, &ctx->t0c, &ctx->net_theta, &ctx->net_x, &ctx->net_a,
+                      &ctx->net_b, &ctx->net_y, &ctx->net_d1, &ctx->net_d2, &ctx->net_dy,
+                      &ctx->net_wt, &ctx->net_part, &ctx->net_scr};
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
+    if (ctx->h_loss) cudaFreeHost(ctx->h_loss);
     for (int q = 0; q < 2; ++q) {
         if (ctx->ev_start[q]) cudaEventDestroy(ctx->ev_start[q]);
         if (ctx->ev_stop[q]) cudaEventDestroy(ctx->ev_stop[q]);
@@ -1045,6 +1126,139 @@ tt_status tt_get_stats(const tt_ctx *ctx, int which, tt_stats *out) {
 
 }  // extern "C"
 
+// ---------------------------------------------------------------- warm-start network
+
+namespace {
+
+template <typename F>
+tt_status net_features_impl(tt_ctx *ctx, const tt_model *m, const tt_point *h_src, int B,
+                            float *d_x) {
+    tt_status s;
+    ENSURE(ctx->pts, sizeof(PointD) * (size_t)B);
+    Work<F> W;
+    if ((s = work_from_ctx<F>(ctx, W, B, 0)) != TT_OK) return s;
+    if ((s = stage_to(ctx, h_src, B, W.src_pts)) != TT_OK) return s;
+    if ((s = enq_sources<F>(ctx, W, m, B)) != TT_OK) return s;
+    const GeoTab<F> &t = geo<F>(ctx);
+    CK(run_net_features<F>(ctx->g, B, 0, B, W.src, W.tabT, W.tabP, t.rad, t.cost,
+                           (const F *)m->d_s, (const F *)m->d_xi, (const F *)m->d_eta, d_x,
+                           ctx->st));
+    ctx->launches += 1;
+    CK(cudaStreamSynchronize(ctx->st));
+    return TT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int tt_net_param_count(void) { return net_param_count(); }
+
+tt_status tt_net_set_weights(tt_ctx *ctx, const float *d_theta) {
+    if (!ctx) return TT_EINVAL;
+    if (!d_theta) return fail(ctx, TT_EINVAL, "tt_net_set_weights: NULL weights");
+    const int P = net_param_count();
+    ENSURE(ctx->net_theta, sizeof(float) * P);
+    CK(run_round_bf16(P, d_theta, (float *)ctx->net_theta.p, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    ctx->launches += 1;
+    ctx->has_net = true;
+    return TT_OK;
+}
+
+tt_status tt_net_features(tt_ctx *ctx, const tt_model *model, const tt_point *h_src, int n_src,
+                          float *d_x) {
+    if (!ctx) return TT_EINVAL;
+    tt_status s;
+    if ((s = check_model(ctx, model)) != TT_OK) return s;
+    if ((s = check_sources(ctx, h_src, n_src)) != TT_OK) return s;
+    if (!d_x) return fail(ctx, TT_EINVAL, "tt_net_features: NULL output");
+    return model->dtype == TT_F32 ? net_features_impl<float>(ctx, model, h_src, n_src, d_x)
+                                  : net_features_impl<double>(ctx, model, h_src, n_src, d_x);
+}
+
+tt_status tt_net_forward(tt_ctx *ctx, const float *d_theta, const float *d_x, int n_grids,
+                         float *d_y) {
+    if (!ctx) return TT_EINVAL;
+    if (!d_theta || !d_x || !d_y || n_grids < 1)
+        return fail(ctx, TT_EINVAL, "tt_net_forward: NULL buffer or n_grids < 1");
+    const GridC &g = ctx->g;
+    const size_t M = (size_t)g.N * n_grids;
+    ENSURE(ctx->net_a, sizeof(float) * kNetHidden * M);
+    ENSURE(ctx->net_b, sizeof(float) * kNetHidden * M);
+    const ConvDims d{n_grids, g.nr, g.nt, g.np};
+    tt_status s = enq_net_forward(ctx, d_theta, d_x, d, (float *)ctx->net_a.p,
+                                  (float *)ctx->net_b.p, (float *)ctx->net_a.p, d_y);
+    if (s != TT_OK) return s;
+    CK(cudaStreamSynchronize(ctx->st));
+    return TT_OK;
+}
+
+tt_status tt_net_loss_grad(tt_ctx *ctx, const float *d_theta, const float *d_x,
+                           const float *d_target, const float *d_mask, int n_grids,
+                           float *d_grad, double *h_loss) {
+    if (!ctx) return TT_EINVAL;
+    if (!d_theta || !d_x || !d_target || !d_mask || !d_grad || n_grids < 1)
+        return fail(ctx, TT_EINVAL, "tt_net_loss_grad: NULL buffer or n_grids < 1");
+    const GridC &g = ctx->g;
+    const size_t M = (size_t)g.N * n_grids;
+    ENSURE(ctx->net_a, sizeof(float) * kNetHidden * M * 3);
+    ENSURE(ctx->net_y, sizeof(float) * M);
+    ENSURE(ctx->net_dy, sizeof(float) * M);
+    ENSURE(ctx->net_d1, sizeof(float) * kNetHidden * M);
+    ENSURE(ctx->net_d2, sizeof(float) * kNetHidden * M);
+    ENSURE(ctx->net_wt, sizeof(float) * 27 * kNetHidden * kNetHidden);
+    ENSURE(ctx->net_part, sizeof(float) * wgrad_partial_floats());
+    ENSURE(ctx->net_scr, sizeof(double) * 4096);
+    if (!ctx->h_loss) CK(cudaMallocHost((void **)&ctx->h_loss, sizeof(double)));
+    float *a[3] = {(float *)ctx->net_a.p, (float *)ctx->net_a.p + kNetHidden * M,
+                   (float *)ctx->net_a.p + 2 * kNetHidden * M};
+    float *y = (float *)ctx->net_y.p, *dy = (float *)ctx->net_dy.p;
+    float *wt = (float *)ctx->net_wt.p, *part = (float *)ctx->net_part.p;
+    double *scr = (double *)ctx->net_scr.p, *loss = scr + 4000;
+    const ConvDims d{n_grids, g.nr, g.nt, g.np};
+    tt_status s = enq_net_forward(ctx, d_theta, d_x, d, a[0], a[1], a[2], y);
+    if (s != TT_OK) return s;
+    CK(run_mse((long long)M, y, d_target, d_mask, dy, scr, loss, ctx->st));
+    // backward, last layer first: weight gradient of layer l from its input and the
+    // gradient of its output; the gradient of its input through the transposed
+    // convolution and the ReLU derivative of the previous layer
+    const float *gout = dy;
+    float *bufs[2] = {(float *)ctx->net_d1.p, (float *)ctx->net_d2.p};
+    for (int l = kNetLayers - 1; l >= 0; --l) {
+        const int ci = kNetCin[l], co = kNetCout[l];
+        const float *in = l == 0 ? d_x : a[l - 1];
+        float *gw = d_grad + net_weight_offset(l);
+        CK(run_conv3d_wgrad(d, ci, co, in, l > 0, gout, part, gw, gw + 27 * ci * co, ctx->st));
+        if (l > 0) {
+            const float *w = d_theta + net_weight_offset(l);
+            CK(run_conv3d_flip(ci, co, w, wt, ctx->st));
+            float *gin = bufs[l & 1];
+            CK(run_conv3d(d, co, ci, gout, false, wt, nullptr, a[l - 1], gin, ctx->st));
+            gout = gin;
+        }
+    }
+    ctx->launches += 3 + 2 * kNetLayers + 2 * (kNetLayers - 1);
+    CK(cudaMemcpyAsync(ctx->h_loss, loss, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    if (h_loss) *h_loss = *ctx->h_loss;
+    return TT_OK;
+}
+
+tt_status tt_net_adam(tt_ctx *ctx, float *d_theta, const float *d_grad, float *d_m, float *d_v,
+                      int step, float lr, float beta1, float beta2, float eps) {
+    if (!ctx) return TT_EINVAL;
+    if (!d_theta || !d_grad || !d_m || !d_v || step < 1)
+        return fail(ctx, TT_EINVAL, "tt_net_adam: NULL buffer or step < 1");
+    CK(run_adam(net_param_count(), d_theta, d_grad, d_m, d_v, step, lr, beta1, beta2, eps,
+                ctx->st));
+    ctx->launches += 1;
+    CK(cudaStreamSynchronize(ctx->st));
+    return TT_OK;
+}
+
+}  // extern "C"
+
 // ---------------------------------------------------------------- plans (graph-captured steps)
 
 struct tt_plan {
@@ -1113,6 +1327,14 @@ template <typename F> tt_status plan_alloc(tt_plan *p, Work<F> &W) {
     TTGB_GET(heads, sizeof(int) * S);
     TTGB_GET(nheads, sizeof(int));
     TTGB_GET(JS, sizeof(F) * (size_t)S * B);
+    if (p->opts.init == 2) {
+        W.net_chunk = net_chunk(g, B);
+        TTGB_GET(net_x, sizeof(float) * kNetFeatures * (size_t)g.N * W.net_chunk);
+        TTGB_GET(net_a, sizeof(float) * kNetHidden * (size_t)g.N * W.net_chunk);
+        TTGB_GET(net_b, sizeof(float) * kNetHidden * (size_t)g.N * W.net_chunk);
+        TTGB_GET(net_y, sizeof(float) * (size_t)g.N * W.net_chunk);
+        W.net_theta = (const float *)ctx->net_theta.p;
+    }
 #undef TTGB_GET
     return TT_OK;
 }

@@ -96,11 +96,11 @@ __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
 // source-frame gradient s0^2 M0^-1 D / T0 rotated into the node frame by Q_ab = e_a . E_b.
 // tabT = (sin dth, 1 - cos dth) at the node's latitude, tabP = (sin dph, 1 - cos dph).
 // Flat geometry: tabT = (R_E dth, 0), tabP = (R_E dph, 0), D = (r - r_s, tabT.x, tabP.x), Q = I.
+// Offset D = (up, north, east) of node (i, r, theta) from the source in the source's frame.
 template <typename F>
-__device__ __forceinline__ F factor_T0(const SrcReg<F> &S, int i, F r, F cth, F sth,
-                                       Vec2<F> tT, Vec2<F> tP, bool flat, F &ur, F &ut, F &up) {
-    F du = ((F)(i - S.ir) - S.frr) * S.dr;
-    F dn, de;
+__device__ __forceinline__ void source_offset(const SrcReg<F> &S, int i, F r, F cth, Vec2<F> tT,
+                                              Vec2<F> tP, bool flat, F &du, F &dn, F &de) {
+    du = ((F)(i - S.ir) - S.frr) * S.dr;
     if (flat) {
         dn = tT.x;
         de = tP.x;
@@ -109,6 +109,13 @@ __device__ __forceinline__ F factor_T0(const SrcReg<F> &S, int i, F r, F cth, F 
         dn = r * (tT.x + S.sts * cth * tP.y);
         de = r * cth * tP.x;
     }
+}
+
+template <typename F>
+__device__ __forceinline__ F factor_T0(const SrcReg<F> &S, int i, F r, F cth, F sth,
+                                       Vec2<F> tT, Vec2<F> tP, bool flat, F &ur, F &ut, F &up) {
+    F du, dn, de;
+    source_offset<F>(S, i, r, cth, tT, tP, flat, du, dn, de);
     F wn = S.b11 * dn + S.b12 * de;
     F we = S.b12 * dn + S.b22 * de;
     F q = du * du + dn * wn + de * we;

@@ -1,0 +1,69 @@
+// Kernels of the warm-start network (tt_net.cu): input features, 3x3x3 convolutions and
+// their gradients, the masked mean squared error and the Adam step. Fields are
+// channels-last, [grid][n_r][n_t][n_p][C], FP32.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "tt_common.cuh"
+
+namespace ttgb {
+
+constexpr int kNetLayers = 4;
+constexpr int kNetCin[kNetLayers] = {6, 32, 32, 32};
+constexpr int kNetCout[kNetLayers] = {32, 32, 32, 1};
+constexpr int kNetHidden = 32;
+constexpr int kNetFeatures = 6;
+constexpr float kNetFeatureScaleKm = 100.0f;
+constexpr float kNetClampLo = -0.5f, kNetClampHi = 1.0f;
+
+// Offset of layer l's weights W[27][cin][cout] in the flat parameter vector; its biases
+// follow them.
+inline int net_weight_offset(int l) {
+    int k = 0;
+    for (int q = 0; q < l; ++q) k += 27 * kNetCin[q] * kNetCout[q] + kNetCout[q];
+    return k;
+}
+inline int net_param_count() { return net_weight_offset(kNetLayers); }
+
+struct ConvDims {
+    int nb, D, H, W;  // grids in the batch and their extent
+};
+
+// Partial sums of the weight gradient: one row of 28 x 32 x 32 per reduction block.
+constexpr int kWgradBlocks = 152;
+inline size_t wgrad_partial_floats() { return (size_t)kWgradBlocks * 28 * 32 * 32; }
+
+// out = conv(in) (+ bias), ReLU applied to the inputs when relu_in, and the outputs
+// zeroed where gate <= 0 when gate is given. cout is 32 or 1.
+cudaError_t run_conv3d(const ConvDims &d, int cin, int cout, const float *in, bool relu_in,
+                       const float *w, const float *bias, const float *gate, float *out,
+                       cudaStream_t st);
+// Gradient of sum(dy * conv(act(in))) with respect to W[27][cin][cout] and b[cout],
+// written (overwriting) to gw and gb; partial is the scratch of wgrad_partial_floats().
+cudaError_t run_conv3d_wgrad(const ConvDims &d, int cin, int cout, const float *in,
+                             bool relu_in, const float *dy, float *partial, float *gw,
+                             float *gb, cudaStream_t st);
+// wt[26 - t][co][ci] = w[t][ci][co]: the weights of the transposed convolution.
+cudaError_t run_conv3d_flip(int cin, int cout, const float *w, float *wt, cudaStream_t st);
+// Masked mean squared error of y against tau - 1 (target = tau) over `total` nodes: *loss
+// (device double) and dy = d loss / d y. scratch: at least 2 * 1024 + 1 doubles.
+cudaError_t run_mse(long long total, const float *y, const float *target, const float *mask,
+                    float *dy, double *scratch, double *loss, cudaStream_t st);
+cudaError_t run_adam(int n, float *theta, const float *grad, float *m, float *v, int step,
+                     float lr, float beta1, float beta2, float eps, cudaStream_t st);
+// Features of sources [b0, b0 + nb) of a set-up batch (SrcC, angle tables of B sources):
+// x[b - b0][node][6] = (s / s0 - 1, xi, eta, D / 100 km).
+template <typename F>
+cudaError_t run_net_features(const GridC &g, int B, int b0, int nb, const SrcC *src,
+                             const Vec2<F> *tabT, const Vec2<F> *tabP, const F *rad,
+                             const F *cost, const F *s, const F *xi, const F *eta, float *x,
+                             cudaStream_t st);
+// tau[node][b0 + b] = 1 + clamp(y[b][node], -0.5, 1) for b < nb.
+template <typename F>
+cudaError_t run_warm_tau(long long N, int B, int b0, int nb, const float *y, F *tau,
+                         cudaStream_t st);
+// Rounds every value to the nearest BF16 (kept in FP32 storage).
+cudaError_t run_round_bf16(int n, const float *in, float *out, cudaStream_t st);
+
+}  // namespace ttgb

@@ -262,6 +262,26 @@ def anisotropic_batch(seed=SEED_BASE + 2, n_src=256, n_pool=200, shape=(121, 161
     return Workload(g, s, xi, eta, src, rec, name="anisotropic-121x161x161", **d)
 
 
+def random_field_models(seed=SEED_BASE + 3, n_models=250, shape=(81, 81, 81),
+                        depth_km=60.0, extent_deg=2.0, corr_km=10.0, sigma_v=0.03,
+                        sigma_aniso=0.02, clip_aniso=0.04, n_src=8, depth_range=(5.0, 40.0)):
+    """Training models of the warm-start network: on an n_r x n_t x n_p grid (depth 0 to
+    depth_km, extent_deg square), Vp = (5 -> 8 km/s with depth) x (1 + GRF), the GRF of
+    correlation length corr_km and standard deviation sigma_v; xi, eta independent GRFs of
+    standard deviation sigma_aniso clipped to +-clip_aniso; n_src sources per model uniform
+    in depth_range. Returns the grid and a list of (s, xi, eta, src) per model."""
+    rng = np.random.default_rng(seed)
+    g = GridSpec(shape[0], shape[1], shape[2], 0.0, depth_km, 0.0, extent_deg, 0.0, extent_deg)
+    vb = background_velocity(g)
+    out = []
+    for _ in range(n_models):
+        v = vb * (1.0 + gaussian_random_field(g, corr_km, sigma_v, rng))
+        xi = np.clip(gaussian_random_field(g, corr_km, sigma_aniso, rng), -clip_aniso, clip_aniso)
+        eta = np.clip(gaussian_random_field(g, corr_km, sigma_aniso, rng), -clip_aniso, clip_aniso)
+        out.append((1.0 / v, xi, eta, random_sources(g, n_src, depth_range, rng)))
+    return g, out
+
+
 def small_case(seed, shape=(13, 15, 17), n_src=3, n_rec=6, aniso=0.03, flat=0,
                depth_max=12.0, extent_deg=0.12):
     """Small heterogeneous anisotropic case with ragged dimensions for parity tests."""
