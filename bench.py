@@ -318,7 +318,74 @@ def gpu_arm(args, rank, world):
         "gpu_launches": int(launches),
         "clocks": clk,
     }
+    if args.unbatched > 0:
+        result["unbatched"] = unbatched_leg(args, w, dev, world)
+    if args.warm_start and os.path.exists(args.warm_start):
+        result["warm_start"] = warm_leg(args, gp, world)
     return result, w, (float(itf.mean()), float(ita.mean()))
+
+
+def unbatched_leg(args, w, dev, world):
+    """The plain FP32 path one source at a time (the same step on a one-source batch) for
+    the first args.unbatched sources of the workload."""
+    torch = __import__("torch")
+    ms = []
+    for b in range(min(args.unbatched, w.n_src)):
+        one = GpuPath(w.subset([b]), dev)
+        one.use_plan()
+        one.step()                     # warm-up (allocation, graph upload)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        one.step()
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        one.plan.close()
+        one.ctx.close()
+    ms_mean = dist_max(float(np.mean(ms)), world)
+    return {"value": world / (ms_mean * 1e-3), "unit": UNIT, "ms_per_solve": ms_mean,
+            "sources": len(ms), "note": "one source per step, same kernels and graph"}
+
+
+def warm_leg(args, gp, world):
+    """The same step with the learned warm start (opts.init = 2): the forward sweep starts
+    from the network's tau and still runs to the same tolerance."""
+    import json as _json
+    torch, tt = gp.torch, gp.tt
+    z = np.load(args.warm_start)
+    theta = torch.as_tensor(z["theta"], device=gp.dev)
+    tt.tt_net_set_weights(gp.ctx, theta)
+    if gp.plan is not None:
+        gp.plan.close()
+    gp.opts.init = 2
+    if args.plan:
+        gp.use_plan()
+    for _ in range(args.warmup):
+        gp.step()
+    gp.iters.clear()
+    dist_barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        gp.step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = dist_max(e0.elapsed_time(e1) / args.steps, world)
+    itf = np.concatenate([s[0] for s in gp.iters])
+    fwd = [s[2] for s in gp.iters]
+    meta = _json.loads(str(z["summary"]))
+    return {"value": world * gp.w.n_src / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+            "iters_fwd_mean": float(itf.mean()), "iters_fwd_max": int(itf.max()),
+            "inference_ms": float(np.mean([s["warm_ms"] for s in fwd])),
+            "sweep_ms": float(np.mean([s["sweep_ms"] for s in fwd])),
+            "inference": "FP32 CUDA-core 3x3x3 convolutions, BF16-rounded weights",
+            "weights": "%s: trained on %d forward solves on %s random-field models, held-out "
+                       "sweeps %.1f -> %.1f" % (os.path.basename(args.warm_start),
+                                                meta["solves_train"], "x".join(map(str, meta["grid"])),
+                                                meta["held_out_sweeps_cold"],
+                                                meta["held_out_sweeps_warm"])}
 
 
 # ----------------------------------------------------------------------------- CPU oracle
@@ -437,6 +504,11 @@ def main():
     ap.add_argument("--plan", type=int, default=1,
                     help="1: replay the step as one captured CUDA graph (tt_plan); 0: the four "
                          "individual calls")
+    ap.add_argument("--warm-start", default=os.path.join(ROOT, "paper_2412_00031_gb300",
+                                                      "warmstart_81.npz"),
+                    help="weights of the warm-start network; '' skips the warm-started leg")
+    ap.add_argument("--unbatched", type=int, default=2,
+                    help="sources timed one per step for the unbatched line (0 skips it)")
     ap.add_argument("--launch-blocks", type=int, default=0,
                     help="profiling runs: cap on the blocks of a persistent launch")
     ap.add_argument("--adj-chunk", type=int, default=0,

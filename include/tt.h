@@ -121,6 +121,8 @@ typedef struct {
     int iters_max;            /* largest per-source iteration count */
     int grid_blocks, block_threads;
     long long launches;       /* kernels this context has launched since it was created */
+    double warm_ms;           /* forward: device time of the warm-start inference (opts.init = 2),
+                                 0 otherwise */
 } tt_stats;
 
 #define TT_STATS_FORWARD 0

@@ -65,7 +65,7 @@ class TTOpts(C.Structure):
 class TTStats(C.Structure):
     _fields_ = [("sweep_ms", C.c_double), ("node_updates", C.c_longlong),
                 ("node_sweeps", C.c_longlong), ("iters_max", C.c_int), ("grid_blocks", C.c_int),
-                ("block_threads", C.c_int), ("launches", C.c_longlong)]
+                ("block_threads", C.c_int), ("launches", C.c_longlong), ("warm_ms", C.c_double)]
 
 
 TT_STATS_FORWARD, TT_STATS_ADJOINT = 0, 1

@@ -52,6 +52,8 @@ struct tt_ctx {
     size_t h_pts_cap = 0;
 
     cudaEvent_t ev_start[2] = {nullptr, nullptr}, ev_stop[2] = {nullptr, nullptr};
+    cudaEvent_t ev_net[2] = {nullptr, nullptr};  // around the warm-start inference
+    bool warm_last = false;                      // the last forward used the warm start
     tt_stats stats[2] = {};
     long long launches = 0;   // kernels launched by this context
 };
@@ -517,7 +519,11 @@ tt_status enq_forward(tt_ctx *ctx, Work<F> &W, const tt_model *m, int B, void *d
     CK(cudaMemsetAsync(W.flags, 0, sizeof(int), ctx->st));
     CK(run_node_records<F>(g, m->d_s, m->d_xi, m->d_eta, ctx->gd.h2, ctx->gd.cost, W.rec,
                            W.flags, ctx->st));
-    if (o->init == 2 && (s = enq_warm_start<F>(ctx, W, m, B, (F *)d_tau)) != TT_OK) return s;
+    if (o->init == 2) {
+        CK(record(ctx, ctx->ev_net[0]));
+        if ((s = enq_warm_start<F>(ctx, W, m, B, (F *)d_tau)) != TT_OK) return s;
+        CK(record(ctx, ctx->ev_net[1]));
+    }
     CK(run_tau_init<F>(g, B, W.src, (F *)d_tau, o->init == 0, ctx->st));
     ctx->launches += 1 + (o->init == 0 ? 2 : 1);
 
@@ -855,6 +861,11 @@ tt_status solve_status(tt_ctx *ctx, int B, const PointD *src, int *h_iters, int 
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, ctx->ev_start[which], ctx->ev_stop[which]));
     S.sweep_ms = ms;
+    S.warm_ms = 0.0;
+    if (which == TT_STATS_FORWARD && ctx->warm_last) {
+        CK(cudaEventElapsedTime(&ms, ctx->ev_net[0], ctx->ev_net[1]));
+        S.warm_ms = ms;
+    }
     const int lo = which == TT_STATS_FORWARD ? 1 : 0;
     long long upd = 0;
     int imax = 0;
@@ -890,6 +901,7 @@ tt_status forward_impl(tt_ctx *ctx, const tt_model *m, const tt_point *h_src, in
     if ((s = enq_readback(ctx, B, W.iters_f, W.conv_f, W.flags, W.bar, TT_STATS_FORWARD)) != TT_OK)
         return s;
     CK(cudaStreamSynchronize(ctx->st));
+    ctx->warm_last = o->init == 2;
     return solve_status(ctx, B, ctx->h_pts, h_iters, o->max_iter_fwd, "tt_forward",
                         TT_STATS_FORWARD);
 }
@@ -996,7 +1008,8 @@ tt_status tt_ctx_create(tt_ctx **out, const tt_grid *grid, void *cuda_stream) {
     if (s == TT_OK) s = upload_geo<double>(ctx, ctx->gd);
     for (int q = 0; q < 2 && s == TT_OK; ++q)
         if (cudaEventCreate(&ctx->ev_start[q]) != cudaSuccess ||
-            cudaEventCreate(&ctx->ev_stop[q]) != cudaSuccess)
+            cudaEventCreate(&ctx->ev_stop[q]) != cudaSuccess ||
+            cudaEventCreate(&ctx->ev_net[q]) != cudaSuccess)
             s = fail(ctx, TT_ECUDA, "cudaEventCreate failed");
     if (s == TT_OK && cudaMallocHost((void **)&ctx->h_pinned, pinned_bytes()) != cudaSuccess)
         s = fail(ctx, TT_ENOMEM, "pinned host allocation failed");
@@ -1035,6 +1048,7 @@ void tt_ctx_destroy(tt_ctx *ctx) {
     for (int q = 0; q < 2; ++q) {
         if (ctx->ev_start[q]) cudaEventDestroy(ctx->ev_start[q]);
         if (ctx->ev_stop[q]) cudaEventDestroy(ctx->ev_stop[q]);
+        if (ctx->ev_net[q]) cudaEventDestroy(ctx->ev_net[q]);
     }
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
     if (ctx->h_pts) cudaFreeHost(ctx->h_pts);
@@ -1456,6 +1470,7 @@ tt_status tt_plan_run(tt_plan *p, int *h_iters_fwd, int *h_iters_adj) {
     Readback r = readback_view(ctx);
     if (r.flags[1]) return fail(ctx, TT_EINVAL, "tt_plan_run: receiver index out of range");
     if (r.flags[2]) return fail(ctx, TT_EINVAL, "tt_plan_run: receiver outside the grid");
+    ctx->warm_last = p->opts.init == 2;
     tt_status sf = solve_status(ctx, p->B, p->h_src.data(), h_iters_fwd, p->opts.max_iter_fwd,
                                 "tt_plan_run (forward)", TT_STATS_FORWARD);
     if (sf != TT_OK && sf != TT_ENOTCONVERGED) return sf;
