@@ -246,6 +246,12 @@ def gpu_arm(args, rank, world):
         gp.opts.max_iter_fwd = args.max_iter_fwd or gp.opts.max_iter_fwd
         gp.opts.max_iter_adj = args.max_iter_adj or gp.opts.max_iter_adj
         gp.allow_unconverged = True
+    tuned = None
+    if args.autotune and args.schedule == 0:
+        ms = gp.tt.tt_autotune(gp.ctx, gp.model, w.src, gp.opts)
+        tuned = {"ms_per_iteration": {k: round(v, 3) for k, v in ms.items()},
+                 "chosen": {"sweep_schedule": gp.opts.sweep_schedule,
+                            "fwd_groups": gp.opts.fwd_groups}}
     if args.plan:
         gp.use_plan()
     for _ in range(args.warmup):
@@ -315,6 +321,7 @@ def gpu_arm(args, rank, world):
         "e2e": {"value": world * w.n_src / (e2e_ms * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "ms_per_step": e2e_ms},
+        "autotune": tuned,
         "gpu_launches": int(launches),
         "clocks": clk,
     }
@@ -507,6 +514,8 @@ def main():
     ap.add_argument("--warm-start", default=os.path.join(ROOT, "paper_2412_00031_gb300",
                                                       "warmstart_81.npz"),
                     help="weights of the warm-start network; '' skips the warm-started leg")
+    ap.add_argument("--autotune", type=int, default=1,
+                    help="1: pick the forward launch configuration with tt_autotune first")
     ap.add_argument("--unbatched", type=int, default=2,
                     help="sources timed one per step for the unbatched line (0 skips it)")
     ap.add_argument("--launch-blocks", type=int, default=0,

@@ -108,6 +108,8 @@ typedef struct {
                                (r x theta x phi). Results do not depend on it. */
     int adj_chunk;          /* adjoint: sources per launch (the slices run one after another so
                                that each launch's working set stays in L2); 0 = automatic */
+    int fwd_groups;         /* node-hyperplane forward sweep: barrier groups per launch
+                               (1..8), 0 = automatic. Results do not depend on it. */
 } tt_opts;
 
 typedef struct tt_ctx tt_ctx;
@@ -196,6 +198,17 @@ tt_status tt_kernel(tt_ctx *ctx, const tt_model *model, int n_src, const void *d
 tt_status tt_misfit_noalloc(const tt_grid *grid, const void *d_T, int dtype,
                             const tt_data *data, double *d_Tr, double *d_chi, double *d_R,
                             void *cuda_stream, char *h_err, int err_len);
+
+/* Autotuner: times the candidate launch configurations of the forward sweep on this
+ * workload and writes the fastest into opts (sweep_schedule, fwd_groups). Candidates, in
+ * this order: node hyperplanes with 1, 2, 4 and 8 barrier groups, then tile hyperplanes
+ * 2x4x8, 4x4x4, 2x8x8 (tiles need n_src >= 32 and rows of 16-byte multiples; skipped
+ * ones time 0). Each runs max_iter_fwd = 2 iterations on a scratch tau owned by the context;
+ * every candidate gives the same results, so only time decides. h_ms (host [7], may be NULL)
+ * receives each candidate's device time per iteration. The choice is cached per
+ * (n_src, dtype): a later call with the same pair only writes it into opts. */
+tt_status tt_autotune(tt_ctx *ctx, const tt_model *model, const tt_point *h_src, int n_src,
+                      tt_opts *opts, double *h_ms);
 
 /* ---- Warm-start network. A small 3D convolutional network predicts the factored correction
  * tau of Sec. 3.1 (T = T0 tau) from local quantities, so that the forward sweep of Sec. 3.1

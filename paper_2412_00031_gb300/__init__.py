@@ -59,7 +59,7 @@ class TTOpts(C.Structure):
     _fields_ = [("tol_fwd", C.c_double), ("tol_adj", C.c_double),
                 ("max_iter_fwd", C.c_int), ("max_iter_adj", C.c_int), ("init", C.c_int),
                 ("spin_limit_ns", C.c_longlong), ("launch_blocks", C.c_int),
-                ("sweep_schedule", C.c_int), ("adj_chunk", C.c_int)]
+                ("sweep_schedule", C.c_int), ("adj_chunk", C.c_int), ("fwd_groups", C.c_int)]
 
 
 class TTStats(C.Structure):
@@ -74,7 +74,7 @@ EXPORTED = ["tt_default_opts", "tt_ctx_create", "tt_ctx_destroy", "tt_last_error
             "tt_forward", "tt_misfit", "tt_adjoint", "tt_kernel", "tt_get_stats",
             "tt_misfit_noalloc", "tt_plan_create", "tt_plan_run", "tt_plan_destroy",
             "tt_net_param_count", "tt_net_features", "tt_net_forward", "tt_net_loss_grad",
-            "tt_net_adam", "tt_net_set_weights"]
+            "tt_net_adam", "tt_net_set_weights", "tt_autotune"]
 TT_NOALLOC_MAX_REC = 1024
 
 
@@ -116,10 +116,12 @@ def _load():
                                                                        C.POINTER(C.c_double)]
     L.tt_net_adam.argtypes = [C.c_void_p] + [C.c_void_p] * 4 + [C.c_int] + [C.c_float] * 4
     L.tt_net_set_weights.argtypes = [C.c_void_p, C.c_void_p]
+    L.tt_autotune.argtypes = [C.c_void_p, C.POINTER(TTModel), C.POINTER(TTPoint), C.c_int,
+                              C.POINTER(TTOpts), C.POINTER(C.c_double)]
     for name in ("tt_ctx_create", "tt_forward", "tt_misfit", "tt_adjoint", "tt_kernel",
                  "tt_get_stats", "tt_misfit_noalloc", "tt_plan_create", "tt_plan_run",
                  "tt_net_param_count", "tt_net_features", "tt_net_forward", "tt_net_loss_grad",
-                 "tt_net_adam", "tt_net_set_weights"):
+                 "tt_net_adam", "tt_net_set_weights", "tt_autotune"):
         getattr(L, name).restype = C.c_int
     return L
 
@@ -410,3 +412,17 @@ def tt_net_set_weights(ctx, theta):
     _cuda_ok(theta)
     _f32(theta)
     _check(ctx, lib.tt_net_set_weights(ctx.handle, _ptr(theta)))
+
+
+AUTOTUNE_CANDIDATES = ("nodes/1 group", "nodes/2 groups", "nodes/4 groups", "nodes/8 groups",
+                       "tiles 2x4x8", "tiles 4x4x4", "tiles 2x8x8")
+
+
+def tt_autotune(ctx, model, src, opts):
+    """Times the forward sweep's launch configurations on this workload and writes the
+    fastest into opts; returns {candidate: ms per iteration} (0 = skipped or cached)."""
+    M = _model(model)
+    pts, n = _points(src)
+    ms = (C.c_double * len(AUTOTUNE_CANDIDATES))()
+    _check(ctx, lib.tt_autotune(ctx.handle, C.byref(M), pts, n, C.byref(opts), ms))
+    return dict(zip(AUTOTUNE_CANDIDATES, list(ms)))

@@ -47,6 +47,10 @@ struct tt_ctx {
         net_scr;
     bool has_net = false;
     double *h_loss = nullptr;  // pinned
+    // autotuner: scratch tau and the choices made, per (n_src, dtype)
+    DevBuf tune_tau;
+    struct Tuned { int n_src, dtype, schedule, groups; };
+    std::vector<Tuned> tuned;
     int *h_pinned = nullptr;  // readback: [0..TT_MAX_BATCH) iterations, then flags
     PointD *h_pts = nullptr;  // staging for source / receiver positions
     size_t h_pts_cap = 0;
@@ -302,6 +306,9 @@ tt_status check_opts(tt_ctx *ctx, const tt_opts *o) {
     if (o->sweep_schedule < 0 || o->sweep_schedule > 1 + kNumTileShapes)
         return fail(ctx, TT_EINVAL, "sweep_schedule %d unknown", o->sweep_schedule);
     if (o->init < 0 || o->init > 2) return fail(ctx, TT_EINVAL, "init %d unknown", o->init);
+    if (o->fwd_groups < 0 || o->fwd_groups > kMaxBarrierGroups)
+        return fail(ctx, TT_EINVAL, "fwd_groups %d outside 0..%d", o->fwd_groups,
+                    kMaxBarrierGroups);
     if (o->init == 2 && !ctx->has_net)
         return fail(ctx, TT_EINVAL, "init = 2 (warm start) needs tt_net_set_weights first");
     return TT_OK;
@@ -594,7 +601,8 @@ tt_status enq_forward(tt_ctx *ctx, Work<F> &W, const tt_model *m, int B, void *d
             if (per_sm > kMaxBarrierGroups) per_sm = kMaxBarrierGroups;
             int max_grid = per_sm * ctx->n_sm;
             if (o->launch_blocks > 0 && o->launch_blocks < max_grid) max_grid = o->launch_blocks;
-            int groups = per_sm;
+            int groups = o->fwd_groups > 0 ? o->fwd_groups : per_sm;
+            if (groups > kMaxBarrierGroups) groups = kMaxBarrierGroups;
             if (groups > (n + 31) / 32) groups = (n + 31) / 32;
             if (groups > max_grid) groups = max_grid;
             int gsrc = ((n + groups - 1) / groups + 31) / 32 * 32;
@@ -962,6 +970,7 @@ void tt_default_opts(tt_opts *o, int dtype) {
     o->launch_blocks = 0;
     o->sweep_schedule = 0;
     o->adj_chunk = 0;
+    o->fwd_groups = 0;
 }
 
 const char *tt_last_error(const tt_ctx *ctx) { return ctx ? ctx->err : "no context"; }
@@ -1041,7 +1050,7 @@ void tt_ctx_destroy(tt_ctx *ctx) {
                       &ctx->wq, &ctx->sidx, &ctx->next, &ctx->heads, &ctx->nheads, &ctx->JS,
                       &ctx->coef, &ctx->t0c, &ctx->net_theta, &ctx->net_x, &ctx->net_a,
                       &ctx->net_b, &ctx->net_y, &ctx->net_d1, &ctx->net_d2, &ctx->net_dy,
-                      &ctx->net_wt, &ctx->net_part, &ctx->net_scr};
+                      &ctx->net_wt, &ctx->net_part, &ctx->net_scr, &ctx->tune_tau};
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     if (ctx->h_loss) cudaFreeHost(ctx->h_loss);
@@ -1139,6 +1148,69 @@ tt_status tt_get_stats(const tt_ctx *ctx, int which, tt_stats *out) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- autotuner
+
+namespace {
+
+constexpr int kTuneCandidates = 7;
+
+template <typename F>
+tt_status autotune_impl(tt_ctx *ctx, const tt_model *m, const tt_point *h_src, int B,
+                        tt_opts *opts, double *h_ms) {
+    tt_status s;
+    ENSURE(ctx->tune_tau, sizeof(F) * (size_t)ctx->g.N * B);
+    const bool tiles_ok = B >= 32 && (B * sizeof(F)) % 16 == 0;
+    double best = 1e300;
+    int best_sched = 1, best_groups = 0;
+    std::vector<int> it(B);
+    for (int c = 0; c < kTuneCandidates; ++c) {
+        tt_opts o = *opts;
+        o.init = 0;
+        o.max_iter_fwd = 2;
+        o.sweep_schedule = c < 4 ? 1 : c - 2;
+        o.fwd_groups = c < 4 ? (1 << c) : 0;
+        double ms = 0.0;
+        if (c < 4 || tiles_ok) {
+            s = forward_impl<F>(ctx, m, h_src, B, ctx->tune_tau.p, nullptr, &o, it.data());
+            if (s != TT_OK && s != TT_ENOTCONVERGED) return s;
+            int imax = 0;
+            for (int b = 0; b < B; ++b) imax = it[b] > imax ? it[b] : imax;
+            ms = ctx->stats[TT_STATS_FORWARD].sweep_ms / (imax > 0 ? imax : 1);
+            if (ms < best) {
+                best = ms;
+                best_sched = o.sweep_schedule;
+                best_groups = o.fwd_groups;
+            }
+        }
+        if (h_ms) h_ms[c] = ms;
+    }
+    ctx->tuned.push_back({B, m->dtype, best_sched, best_groups});
+    opts->sweep_schedule = best_sched;
+    opts->fwd_groups = best_groups;
+    return TT_OK;
+}
+
+}  // namespace
+
+extern "C" tt_status tt_autotune(tt_ctx *ctx, const tt_model *model, const tt_point *h_src,
+                                 int n_src, tt_opts *opts, double *h_ms) {
+    if (!ctx) return TT_EINVAL;
+    tt_status s;
+    if ((s = check_model(ctx, model)) != TT_OK) return s;
+    if ((s = check_sources(ctx, h_src, n_src)) != TT_OK) return s;
+    if ((s = check_opts(ctx, opts)) != TT_OK) return s;
+    for (const auto &t : ctx->tuned)
+        if (t.n_src == n_src && t.dtype == model->dtype) {
+            opts->sweep_schedule = t.schedule;
+            opts->fwd_groups = t.groups;
+            if (h_ms)
+                for (int c = 0; c < kTuneCandidates; ++c) h_ms[c] = 0.0;
+            return TT_OK;
+        }
+    return model->dtype == TT_F32 ? autotune_impl<float>(ctx, model, h_src, n_src, opts, h_ms)
+                                  : autotune_impl<double>(ctx, model, h_src, n_src, opts, h_ms);
+}
 
 // ---------------------------------------------------------------- warm-start network
 

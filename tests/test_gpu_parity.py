@@ -212,3 +212,31 @@ def test_plan_replays_the_step_bitwise(tt):
             assert np.array_equal(a.cpu().numpy(), b)
     plan.close()
     ctx.close()
+
+
+def test_autotuner_picks_a_measured_candidate_with_identical_results(tt):
+    """The tuner times every launch configuration and keeps the fastest; the tuned solve
+    gives the default solve's bits, and a second call reuses the cached choice."""
+    import torch
+    w = I.small_case(16, shape=(14, 17, 19), n_src=40, n_rec=5)
+    ctx = tt.tt_ctx_create(w.grid.as_dict())
+    model = tuple(to_dev(a, torch.float32) for a in (w.s, w.xi, w.eta))
+    o = tt.default_opts(tt.TT_F32)
+    ms = tt.tt_autotune(ctx, model, w.src, o)
+    timed = {k: v for k, v in ms.items() if v > 0}
+    assert len(timed) == 7          # 40 sources: the tile schedules run too
+    best = min(timed, key=timed.get)
+    want = (1, [1, 2, 4, 8][list(ms).index(best)]) if best.startswith("nodes") else \
+        (2 + ["tiles 2x4x8", "tiles 4x4x4", "tiles 2x8x8"].index(best), 0)
+    assert (o.sweep_schedule, o.fwd_groups) == want
+    ref = gpu_solve(w, "f32", steps=("fwd",), ctx=ctx)
+    tuned = gpu_solve(w, "f32", opts=o, steps=("fwd",), ctx=ctx)
+    assert np.array_equal(ref["tau"], tuned["tau"])
+    o2 = tt.default_opts(tt.TT_F32)
+    assert all(v == 0 for v in tt.tt_autotune(ctx, model, w.src, o2).values())
+    assert (o2.sweep_schedule, o2.fwd_groups) == want
+    for g in (1, 2, 3, 8):          # any group count gives the same bits
+        out = gpu_solve(w, "f32", opts=tt.default_opts(tt.TT_F32, fwd_groups=g), steps=("fwd",),
+                        ctx=ctx)
+        assert np.array_equal(ref["tau"], out["tau"])
+    ctx.close()
