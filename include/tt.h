@@ -247,6 +247,11 @@ tt_status tt_net_adam(tt_ctx *ctx, float *d_theta, const float *d_grad, float *d
 /* Stores the weights the warm start uses (device FP32 vector, rounded to BF16 and kept by
  * the context; inference accumulates in FP32). Needed before opts.init = 2. */
 tt_status tt_net_set_weights(tt_ctx *ctx, const float *d_theta);
+/* The warm start's inference with the stored weights: d_y (device [n_grids][N] float) =
+ * network output for d_x. Layers 2 and 3 run on the tensor cores (BF16 operands, FP32
+ * accumulation), layers 1 and 4 on the CUDA cores; activations between layers are BF16.
+ * Agrees with tt_net_forward to BF16 accuracy. */
+tt_status tt_net_infer(tt_ctx *ctx, const float *d_x, int n_grids, float *d_y);
 
 /* A plan: one whole step over one batch (forward, misfit and adjoint sources, adjoint,
  * kernels) captured once into a CUDA graph and replayed by tt_plan_run, so that a step costs

@@ -74,7 +74,7 @@ EXPORTED = ["tt_default_opts", "tt_ctx_create", "tt_ctx_destroy", "tt_last_error
             "tt_forward", "tt_misfit", "tt_adjoint", "tt_kernel", "tt_get_stats",
             "tt_misfit_noalloc", "tt_plan_create", "tt_plan_run", "tt_plan_destroy",
             "tt_net_param_count", "tt_net_features", "tt_net_forward", "tt_net_loss_grad",
-            "tt_net_adam", "tt_net_set_weights", "tt_autotune"]
+            "tt_net_adam", "tt_net_set_weights", "tt_autotune", "tt_net_infer"]
 TT_NOALLOC_MAX_REC = 1024
 
 
@@ -116,12 +116,13 @@ def _load():
                                                                        C.POINTER(C.c_double)]
     L.tt_net_adam.argtypes = [C.c_void_p] + [C.c_void_p] * 4 + [C.c_int] + [C.c_float] * 4
     L.tt_net_set_weights.argtypes = [C.c_void_p, C.c_void_p]
+    L.tt_net_infer.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]
     L.tt_autotune.argtypes = [C.c_void_p, C.POINTER(TTModel), C.POINTER(TTPoint), C.c_int,
                               C.POINTER(TTOpts), C.POINTER(C.c_double)]
     for name in ("tt_ctx_create", "tt_forward", "tt_misfit", "tt_adjoint", "tt_kernel",
                  "tt_get_stats", "tt_misfit_noalloc", "tt_plan_create", "tt_plan_run",
                  "tt_net_param_count", "tt_net_features", "tt_net_forward", "tt_net_loss_grad",
-                 "tt_net_adam", "tt_net_set_weights", "tt_autotune"):
+                 "tt_net_adam", "tt_net_set_weights", "tt_autotune", "tt_net_infer"):
         getattr(L, name).restype = C.c_int
     return L
 
@@ -426,3 +427,10 @@ def tt_autotune(ctx, model, src, opts):
     ms = (C.c_double * len(AUTOTUNE_CANDIDATES))()
     _check(ctx, lib.tt_autotune(ctx.handle, C.byref(M), pts, n, C.byref(opts), ms))
     return dict(zip(AUTOTUNE_CANDIDATES, list(ms)))
+
+
+def tt_net_infer(ctx, x, y):
+    """Warm-start inference with the weights of tt_net_set_weights (tensor cores)."""
+    _cuda_ok(x, y)
+    _f32(x, y)
+    _check(ctx, lib.tt_net_infer(ctx.handle, _ptr(x), x.shape[0], _ptr(y)))

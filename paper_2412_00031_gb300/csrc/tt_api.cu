@@ -2,6 +2,7 @@
 // orchestration of the kernels in tt_sweep.cu and tt_aux.cu.
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -44,7 +45,7 @@ struct tt_ctx {
     DevBuf cq, wq, sidx, next, heads, nheads, JS, coef, t0c;
     // warm-start network: inference weights (BF16-rounded) and its workspace
     DevBuf net_theta, net_x, net_a, net_b, net_y, net_d1, net_d2, net_dy, net_wt, net_part,
-        net_scr;
+        net_scr, net_wbf;  // net_wbf: BF16 weights of layers 2 and 3, [tap][co][ci]
     bool has_net = false;
     double *h_loss = nullptr;  // pinned
     // autotuner: scratch tau and the choices made, per (n_src, dtype)
@@ -337,17 +338,20 @@ template <typename F> struct Work {
     int t0c_slice = 0;  // sources per forward slice the factor cache holds
     bool coef_ok = false;
     // warm start: features [chunk][N][6], activations [chunk][N][32] (two), output [chunk][N]
-    float *net_x = nullptr, *net_a = nullptr, *net_b = nullptr, *net_y = nullptr;
+    float *net_x = nullptr, *net_y = nullptr;
+    __nv_bfloat16 *net_a = nullptr, *net_b = nullptr;   // BF16 activations
     const float *net_theta = nullptr;
+    const __nv_bfloat16 *net_wbf = nullptr;
     int net_chunk = 0;
 };
 
-// Sources per warm-start inference pass: two activation buffers of at most ~8 GB together.
+// Sources per warm-start inference pass: two BF16 activation buffers of at most ~8 GB
+// together.
 int net_chunk(const GridC &g, int B) {
-    const size_t per_src = (size_t)g.N * kNetHidden * sizeof(float);
+    const size_t per_src = (size_t)g.N * kNetHidden * sizeof(__nv_bfloat16);
     long long c = (long long)((4ull << 30) / per_src);
     if (c < 1) c = 1;
-    if (c > 8) c = 8;
+    if (c > 16) c = 16;
     return (int)(c < B ? c : B);
 }
 
@@ -422,14 +426,15 @@ template <typename F> tt_status net_work_from_ctx(tt_ctx *ctx, Work<F> &W, int B
     const GridC &g = ctx->g;
     const int c = net_chunk(g, B);
     ENSURE(ctx->net_x, sizeof(float) * kNetFeatures * (size_t)g.N * c);
-    ENSURE(ctx->net_a, sizeof(float) * kNetHidden * (size_t)g.N * c);
-    ENSURE(ctx->net_b, sizeof(float) * kNetHidden * (size_t)g.N * c);
+    ENSURE(ctx->net_a, sizeof(__nv_bfloat16) * kNetHidden * (size_t)g.N * c);
+    ENSURE(ctx->net_b, sizeof(__nv_bfloat16) * kNetHidden * (size_t)g.N * c);
     ENSURE(ctx->net_y, sizeof(float) * (size_t)g.N * c);
     W.net_x = (float *)ctx->net_x.p;
-    W.net_a = (float *)ctx->net_a.p;
-    W.net_b = (float *)ctx->net_b.p;
+    W.net_a = (__nv_bfloat16 *)ctx->net_a.p;
+    W.net_b = (__nv_bfloat16 *)ctx->net_b.p;
     W.net_y = (float *)ctx->net_y.p;
     W.net_theta = (const float *)ctx->net_theta.p;
+    W.net_wbf = (const __nv_bfloat16 *)ctx->net_wbf.p;
     W.net_chunk = c;
     return TT_OK;
 }
@@ -505,11 +510,10 @@ tt_status enq_warm_start(tt_ctx *ctx, Work<F> &W, const tt_model *m, int B, F *t
                                (const F *)m->d_s, (const F *)m->d_xi, (const F *)m->d_eta,
                                W.net_x, ctx->st));
         const ConvDims d{nb, g.nr, g.nt, g.np};
-        if ((s = enq_net_forward(ctx, W.net_theta, W.net_x, d, W.net_a, W.net_b, W.net_a,
-                                 W.net_y)) != TT_OK)
-            return s;
+        CK(run_net_infer(d, W.net_theta, W.net_wbf, W.net_wbf + 27 * 32 * 32, W.net_x,
+                         W.net_a, W.net_b, W.net_y, ctx->n_sm, ctx->st));
         CK(run_warm_tau<F>(g.N, B, b0, nb, W.net_y, tau, ctx->st));
-        ctx->launches += 2;
+        ctx->launches += 6;
     }
     return TT_OK;
 }
@@ -1050,7 +1054,8 @@ void tt_ctx_destroy(tt_ctx *ctx) {
                       &ctx->wq, &ctx->sidx, &ctx->next, &ctx->heads, &ctx->nheads, &ctx->JS,
                       &ctx->coef, &ctx->t0c, &ctx->net_theta, &ctx->net_x, &ctx->net_a,
                       &ctx->net_b, &ctx->net_y, &ctx->net_d1, &ctx->net_d2, &ctx->net_dy,
-                      &ctx->net_wt, &ctx->net_part, &ctx->net_scr, &ctx->tune_tau};
+                      &ctx->net_wt, &ctx->net_part, &ctx->net_scr, &ctx->tune_tau,
+                      &ctx->net_wbf};
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     if (ctx->h_loss) cudaFreeHost(ctx->h_loss);
@@ -1245,10 +1250,32 @@ tt_status tt_net_set_weights(tt_ctx *ctx, const float *d_theta) {
     if (!d_theta) return fail(ctx, TT_EINVAL, "tt_net_set_weights: NULL weights");
     const int P = net_param_count();
     ENSURE(ctx->net_theta, sizeof(float) * P);
+    ENSURE(ctx->net_wbf, sizeof(__nv_bfloat16) * 2 * 27 * 32 * 32);
     CK(run_round_bf16(P, d_theta, (float *)ctx->net_theta.p, ctx->st));
+    __nv_bfloat16 *wbf = (__nv_bfloat16 *)ctx->net_wbf.p;
+    CK(run_mma_weights(d_theta + net_weight_offset(1), wbf, ctx->st));
+    CK(run_mma_weights(d_theta + net_weight_offset(2), wbf + 27 * 32 * 32, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
-    ctx->launches += 1;
+    ctx->launches += 3;
     ctx->has_net = true;
+    return TT_OK;
+}
+
+tt_status tt_net_infer(tt_ctx *ctx, const float *d_x, int n_grids, float *d_y) {
+    if (!ctx) return TT_EINVAL;
+    if (!d_x || !d_y || n_grids < 1)
+        return fail(ctx, TT_EINVAL, "tt_net_infer: NULL buffer or n_grids < 1");
+    if (!ctx->has_net) return fail(ctx, TT_EINVAL, "tt_net_infer: no weights (tt_net_set_weights)");
+    const GridC &g = ctx->g;
+    const size_t M = (size_t)g.N * n_grids;
+    ENSURE(ctx->net_a, sizeof(__nv_bfloat16) * kNetHidden * M);
+    ENSURE(ctx->net_b, sizeof(__nv_bfloat16) * kNetHidden * M);
+    const __nv_bfloat16 *wbf = (const __nv_bfloat16 *)ctx->net_wbf.p;
+    CK(run_net_infer(ConvDims{n_grids, g.nr, g.nt, g.np}, (const float *)ctx->net_theta.p, wbf,
+                     wbf + 27 * 32 * 32, d_x, (__nv_bfloat16 *)ctx->net_a.p,
+                     (__nv_bfloat16 *)ctx->net_b.p, d_y, ctx->n_sm, ctx->st));
+    ctx->launches += 4;
+    CK(cudaStreamSynchronize(ctx->st));
     return TT_OK;
 }
 
@@ -1416,10 +1443,11 @@ template <typename F> tt_status plan_alloc(tt_plan *p, Work<F> &W) {
     if (p->opts.init == 2) {
         W.net_chunk = net_chunk(g, B);
         TTGB_GET(net_x, sizeof(float) * kNetFeatures * (size_t)g.N * W.net_chunk);
-        TTGB_GET(net_a, sizeof(float) * kNetHidden * (size_t)g.N * W.net_chunk);
-        TTGB_GET(net_b, sizeof(float) * kNetHidden * (size_t)g.N * W.net_chunk);
+        TTGB_GET(net_a, sizeof(__nv_bfloat16) * kNetHidden * (size_t)g.N * W.net_chunk);
+        TTGB_GET(net_b, sizeof(__nv_bfloat16) * kNetHidden * (size_t)g.N * W.net_chunk);
         TTGB_GET(net_y, sizeof(float) * (size_t)g.N * W.net_chunk);
         W.net_theta = (const float *)ctx->net_theta.p;
+        W.net_wbf = (const __nv_bfloat16 *)ctx->net_wbf.p;
     }
 #undef TTGB_GET
     return TT_OK;

@@ -185,3 +185,36 @@ def test_trained_network_gains_over_the_cold_start(tt, capsys):
               % (err_net, err_one, cold_iters.mean(), warm_iters.mean()))
     assert warm_iters.mean() <= cold_iters.mean()
     ctx.close()
+
+
+def _bf16(a):
+    """Round float32 values to the nearest BF16 (ties to even), kept as float32."""
+    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32)
+    r = (u + np.uint32(0x7FFF) + ((u >> np.uint32(16)) & np.uint32(1))) & np.uint32(0xFFFF0000)
+    return r.view(np.float32)
+
+
+def test_tensor_core_inference_matches_oracle(tt):
+    """The warm start's inference (layers 2-3 on the tensor cores, BF16 operands and
+    activations, FP32 accumulation) against the FP64 network with the same BF16 weights.
+    Bound: three BF16 roundings of the activations (2^-9 relative each) through layers of
+    gain ~1 leave the output within 2 % of its range; ragged tiles on every axis."""
+    import torch
+    w, xs = _oracle_inputs(65, shape=(13, 12, 17), n=2)
+    theta = _theta(11)
+    ctx = tt.tt_ctx_create(w.grid.as_dict())
+    tt.tt_net_set_weights(ctx, torch.as_tensor(theta, device="cuda"))
+    x = torch.as_tensor(np.stack(xs), device="cuda")
+    y = torch.empty(x.shape[:-1], dtype=torch.float32, device="cuda")
+    tt.tt_net_infer(ctx, x, y)
+    y32 = torch.empty_like(y)
+    tt.tt_net_forward(ctx, torch.as_tensor(theta, device="cuda"), x, y32)
+    ctx.close()
+    tb = _bf16(theta).astype(np.float64)
+    for b in range(len(xs)):
+        ref = N.forward(tb, xs[b].astype(np.float64))
+        scale = np.abs(ref).max()
+        got = y[b].cpu().numpy()
+        assert np.abs(got - ref).max() <= 2e-2 * scale
+        assert np.corrcoef(got.ravel(), ref.ravel())[0, 1] > 0.9999
+        assert np.abs(got - y32[b].cpu().numpy()).max() <= 2e-2 * scale
