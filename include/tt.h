@@ -106,8 +106,9 @@ typedef struct {
     int sweep_schedule;     /* forward sweep schedule: 0 = automatic; 1 = node hyperplanes;
                                2, 3, 4 = tile hyperplanes with 2x4x8, 4x4x4, 2x8x8 tiles
                                (r x theta x phi). Results do not depend on it. */
-    int adj_chunk;          /* adjoint: sources per launch (the slices run one after another so
-                               that each launch's working set stays in L2); 0 = automatic */
+    int adj_chunk;          /* adjoint: sources per launch (the slices run one after another);
+                               0 = all sources in one launch. A launch runs its sources as up
+                               to 4 barrier groups side by side. Results do not depend on it. */
     int fwd_groups;         /* node-hyperplane forward sweep: barrier groups per launch
                                (1..8), 0 = automatic. Results do not depend on it. */
 } tt_opts;

@@ -70,6 +70,11 @@ constexpr long long kDefaultSpinNs = 2000000000LL;
 constexpr size_t kCoefBudgetBytes = 64ull << 30;
 // Largest factor cache (1/T0 and grad T0 / T0 per node and source) one forward slice keeps.
 constexpr size_t kFactorCacheBudgetBytes = 32ull << 30;
+// Barrier groups that one face-adjoint launch runs side by side.
+#ifndef TTGB_ADJ_GROUPS
+#define TTGB_ADJ_GROUPS 4
+#endif
+constexpr int kAdjGroups = TTGB_ADJ_GROUPS;
 
 tt_status fail(tt_ctx *c, tt_status s, const char *fmt, ...) {
     if (c) {
@@ -700,29 +705,36 @@ tt_status enq_adjoint(tt_ctx *ctx, Work<F> &W, const tt_model *m, int B, const v
     // budget; otherwise the sweep that evaluates the flux velocities at every update.
     const bool faces = W.coef_ok;
     int grid, block, slots;
-    int n_bgroups = 1, grp_blocks = 0, grp_src = B;
+    int n_bgroups = 1, grp_blocks = 0, grp_src = B, adj_launch_groups = 1;
     if (faces) {
         // Source slices of adj_chunk sources, one cooperative launch each, run one after
         // another: a hyperplane of one slice (coefficients of two planes, P of three) then
         // stays in L2. Automatic: slices of at most 128 sources.
+        // Each launch covers `chunk` sources (default: all), split into up to
+        // TTGB_ADJ_GROUPS barrier groups of >= 64 sources that run side by side.
         block = 256;
-        int chunk = o->adj_chunk > 0 ? o->adj_chunk : 128;
-        grp_src = chunk >= B ? B : (chunk + 31) / 32 * 32;
-        n_bgroups = (B + grp_src - 1) / grp_src;
+        int chunk = o->adj_chunk > 0 ? o->adj_chunk : B;
+        chunk = chunk >= B ? B : (chunk + 31) / 32 * 32;
+        int groups = (chunk + 63) / 64;
+        if (groups > kAdjGroups) groups = kAdjGroups;
+        grp_src = ((chunk + groups - 1) / groups + 31) / 32 * 32;
+        groups = (chunk + grp_src - 1) / grp_src;
+        n_bgroups = (B + grp_src - 1) / grp_src;  // groups over the whole batch
+        adj_launch_groups = groups;
         size_t smem = (size_t)grp_src * 2 * sizeof(F);
         int per_sm = adjoint_faces_blocks_per_sm<F>(block, smem);
         if (per_sm <= 0) return fail(ctx, TT_ECUDA, "adjoint sweep cannot be resident");
         if (per_sm > 4) per_sm = 4;
         int max_grid = per_sm * ctx->n_sm;
         if (o->launch_blocks > 0 && o->launch_blocks < max_grid) max_grid = o->launch_blocks;
-        grp_blocks = max_grid;
+        grp_blocks = max_grid / groups;
         if ((long long)grp_blocks * block < grp_src) {
             int need = (grp_src + block - 1) / block;
-            if (need > per_sm * ctx->n_sm)
+            if ((long long)need * groups > (long long)per_sm * ctx->n_sm)
                 return fail(ctx, TT_EINVAL, "batch of %d sources exceeds one resident launch", B);
             grp_blocks = need;
         }
-        grid = grp_blocks;
+        grid = grp_blocks * groups;
         slots = 0;
     } else if ((s = sweep_shape<F>(ctx, false, B, ctx->full, o->launch_blocks, grid, block,
                                    slots)) != TT_OK) {
@@ -757,7 +769,7 @@ tt_status enq_adjoint(tt_ctx *ctx, Work<F> &W, const tt_model *m, int B, const v
     a.tol = (F)o->tol_adj;
     a.max_iter = o->max_iter_adj;
     a.spin_ns = spin_ns(o);
-    a.coef = faces ? W.coef : nullptr;
+    a.coef = faces ? reinterpret_cast<F *>(W.coef) : nullptr;
     a.n_bgroups = n_bgroups;
     a.grp_blocks = grp_blocks;
     a.grp_src = grp_src;
@@ -767,9 +779,10 @@ tt_status enq_adjoint(tt_ctx *ctx, Work<F> &W, const tt_model *m, int B, const v
     }
     CK(record(ctx, ctx->ev_start[TT_STATS_ADJOINT]));
     if (faces) {
-        for (int q = 0; q < n_bgroups; ++q) {
+        for (int q = 0; q < n_bgroups; q += adj_launch_groups) {
             a.grp_base = q;
-            CK(launch_adjoint_faces<F>(a, grid, block, ctx->st));
+            const int ng = n_bgroups - q < adj_launch_groups ? n_bgroups - q : adj_launch_groups;
+            CK(launch_adjoint_faces<F>(a, grp_blocks * ng, block, ctx->st));
             ctx->launches += 1;
         }
     } else {

@@ -78,7 +78,9 @@ template <typename F> struct AdjArgs {
     const F *cost, *costf, *h2, *arf;
     const int *sidx;           // [N] index into JS or kNone
     const F *JS;               // [n_heads][B] J_c S_c of Eq. 5's point sources
-    Vec4<F> *coef;             // [N][B]: A a / delta on the +r, +theta, +phi faces; J_c S_c
+    // Face coefficients, four planes of [N][B] (plane stride N * B): A a / delta on the +r,
+    // +theta, +phi faces and J_c S_c (NaN on the source's fixed set)
+    F *coef;
     int n_bgroups, grp_blocks, grp_src;  // barrier groups (as in FwdArgs)
     int grp_base;              // group index of this launch's first group
     const unsigned int *nodes;

@@ -800,7 +800,12 @@ __device__ __forceinline__ void plus_face_coefs(const AdjArgs<F> &a, int b, int 
     }
 }
 
-constexpr int kAdjBatch = 4;  // nodes whose loads one thread issues together
+
+template <typename F> __device__ __forceinline__ F quiet_nan();
+template <> __device__ __forceinline__ float quiet_nan<float>() { return __int_as_float(0x7fc00000); }
+template <> __device__ __forceinline__ double quiet_nan<double>() {
+    return __longlong_as_double(0x7ff8000000000000LL);
+}
 
 template <typename F> __global__ void adj_coef_kernel(AdjArgs<F> a) {
     const GridC &g = a.g;
@@ -812,16 +817,50 @@ template <typename F> __global__ void adj_coef_kernel(AdjArgs<F> a) {
         const int k = (int)(n % g.np);
         const long long t = n / g.np;
         const int j = (int)(t % g.nt), i = (int)(t / g.nt);
-        Vec4<F> c;
-        plus_face_coefs<F>(a, b, i, j, k, n, c.x, c.y, c.z);
+        F cr, ct, cp;
+        plus_face_coefs<F>(a, b, i, j, k, n, cr, ct, cp);
         const int h = __ldg(a.sidx + n);
-        c.w = h != kNone ? a.JS[(long long)h * a.B + b] : (F)0;
-        a.coef[x] = c;
+        F w = h != kNone ? a.JS[(long long)h * a.B + b] : (F)0;
+        const SrcC &sc = a.src[b];
+        if (in_fixed_set(sc.ci, sc.cj, sc.ck, i, j, k)) w = quiet_nan<F>();  // never updated
+        a.coef[x] = cr;
+        a.coef[x + total] = ct;
+        a.coef[x + 2 * total] = cp;
+        a.coef[x + 3 * total] = w;
     }
 }
 
+// Upwind update of one (node, source) from its face coefficients (Eq. 5 discretised as in
+// adj_update): c = (+r, +theta, +phi face coefficients, J S), cm = the -r, -theta, -phi
+// neighbours' plus-face coefficients, Pn = P at (+r, -r, +theta, -theta, +phi, -phi).
+// Rounding-explicit, so both lanes' copies give identical bits.
 template <typename F>
-__global__ void __launch_bounds__(256) adj_face_kernel(AdjArgs<F> a) {
+__device__ __forceinline__ F face_update(F cx, F cy, F cz, F cw, F cmx, F cmy, F cmz,
+                                         const F (&Pn)[6]) {
+    const F zero = (F)0;
+    const F out = add_(add_(sub_(fmax_(cx, zero), fmin(cmx, zero)),
+                            sub_(fmax_(cy, zero), fmin(cmy, zero))),
+                       sub_(fmax_(cz, zero), fmin(cmz, zero)));
+    const F in = fma_(fmax_(cmx, zero), Pn[1],
+                 fma_(-fmin(cx, zero), Pn[0],
+                 fma_(fmax_(cmy, zero), Pn[3],
+                 fma_(-fmin(cy, zero), Pn[2],
+                 fma_(fmax_(cmz, zero), Pn[5], mul_(-fmin(cz, zero), Pn[4]))))));
+    return out <= (F)1e-30 ? zero : div_(add_(cw, in), out);
+}
+
+// Face-coefficient adjoint sweep. Same organisation as the node-hyperplane forward sweep:
+// barrier groups of consecutive sources; a warp covers 64 sources of one node, lane l
+// holding sources l and l + 32; on each hyperplane the slots take the nodes slot,
+// slot + slots, ...; the schedule is static, so the next node's index and the next
+// hyperplane's bounds are read one step ahead. The coefficient planes are separate arrays,
+// so every load (a node's four coefficients, each upstream neighbour's one) is a coalesced
+// line. Sweeps cover every node (boundary faces carry no flux).
+#ifndef TTGB_ADJ_MIN_BLOCKS
+#define TTGB_ADJ_MIN_BLOCKS 3
+#endif
+template <typename F>
+__global__ void __launch_bounds__(256, TTGB_ADJ_MIN_BLOCKS) adj_face_kernel(AdjArgs<F> a) {
     extern __shared__ unsigned char smem_raw[];
     __shared__ int s_cnt;
     const GridC &g = a.g;
@@ -837,81 +876,100 @@ __global__ void __launch_bounds__(256) adj_face_kernel(AdjArgs<F> a) {
     F *s_pmax = s_err + Bg;
     BarrierState *bar = a.bar + lgrp;  // launches of a chunked solve reuse the same words
     const unsigned nblk = (unsigned)a.grp_blocks;
-    const int slots = (int)(((long long)a.grp_blocks * blockDim.x) / Bg);
+    const int Bw = ((Bg + 63) >> 6) << 5;               // lanes of one slot
+    const int slots = (int)(((long long)a.grp_blocks * blockDim.x) / Bw);
     const long long tid = (long long)blk * blockDim.x + threadIdx.x;
-    const bool lane_ok = tid < (long long)slots * Bg;
-    const int b = src0 + (lane_ok ? (int)(tid % Bg) : 0);
-    const int slot = lane_ok ? (int)(tid / Bg) : 0;
-    const int ci = a.src[b].ci, cj = a.src[b].cj, ck = a.src[b].ck;
+    const bool lane_ok = tid < (long long)slots * Bw;   // uniform over a warp
+    const int bl = lane_ok ? (int)(tid % Bw) : 0;
+    const int slot = lane_ok ? (int)(tid / Bw) : 0;
+    const int lane = threadIdx.x & 31;
+    const int l0 = ((bl >> 5) << 6) + lane;
+    const bool ok0 = lane_ok && l0 < Bg, ok1 = lane_ok && l0 + 32 < Bg;
+    const int b = src0 + (ok0 ? l0 : 0);                // second source: b + 32
     const long long sp = B, st = (long long)g.np * B, sr = (long long)g.nt * g.np * B;
+    const long long plane = g.N * B;                    // coefficient plane stride
+    const F *cX = a.coef, *cY = a.coef + plane, *cZ = a.coef + 2 * plane, *cW = a.coef + 3 * plane;
+    F *P = a.P;
 
     for (int it = 0; it < a.max_iter; ++it) {
-        const bool active = lane_ok && ((volatile int *)a.conv)[b] == 0;
-        F err = 0, pmax = 0;
+        const bool act0 = ok0 && ((volatile int *)a.conv)[b] == 0;
+        const bool act1 = ok1 && ((volatile int *)a.conv)[b + 32] == 0;
+        const bool busy = lane_ok && __any_sync(0xffffffffu, act0 || act1);  // uniform
+        F err0 = 0, err1 = 0, pmax0 = 0, pmax1 = 0;
         for (int o = 0; o < 8; ++o) {
             const bool rr = o & 4, rt = o & 2, rp = o & 1;
+            int qa = __ldg(a.off) + slot, qe = __ldg(a.off + 1);
+            unsigned pk = busy && qa < qe ? __ldg(a.nodes + qa) : 0u;
             for (int L = 0; L < a.n_planes; ++L) {
-                if (active) {
-                    // Nodes of one hyperplane are independent: load the inputs of up to
-                    // kAdjBatch nodes first, then update them, so their memory latencies
-                    // overlap instead of following one another.
-                    const int q1 = __ldg(a.off + L + 1);
-                    for (int q0 = __ldg(a.off + L) + slot; q0 < q1; q0 += kAdjBatch * slots) {
-                        long long xs[kAdjBatch];
-                        bool ok[kAdjBatch];
-                        Vec4<F> c[kAdjBatch];
-                        F cm[kAdjBatch][3], Pn[kAdjBatch][6], Po[kAdjBatch];
+                const bool last = L + 1 == a.n_planes;
+                const int qe_next = last ? 0 : __ldg(a.off + L + 2);
+                if (busy) {
+                    for (int q = qa; q < qe; q += slots) {
+                        const int qn = q + slots;
+                        const unsigned pkn = qn < qe ? __ldg(a.nodes + qn) : 0u;
+                        int aa, bb, cc;
+                        unpack(pk, aa, bb, cc);
+                        const int i = rr ? g.nr - 1 - aa : aa;
+                        const int j = rt ? g.nt - 1 - bb : bb;
+                        const int k = rp ? g.np - 1 - cc : cc;
+                        const bool hr = i < g.nr - 1, lr = i > 0, ht = j < g.nt - 1, lt = j > 0;
+                        const bool hp = k < g.np - 1, lp = k > 0;
+                        const long long x = node_index(g, i, j, k) * B + b;
+                        // both sources' loads first, then the two updates
+                        F cx[2], cy[2], cz[2], w[2], cmx[2], cmy[2], cmz[2], Pn[2][6], po[2];
 #pragma unroll
-                        for (int u = 0; u < kAdjBatch; ++u) {
-                            const int q = q0 + u * slots;
-                            ok[u] = q < q1;
-                            int aa = 0, bb = 0, cc = 0;
-                            if (ok[u]) unpack(__ldg(a.nodes + q), aa, bb, cc);
-                            const int i = rr ? g.nr - 1 - aa : aa;
-                            const int j = rt ? g.nt - 1 - bb : bb;
-                            const int k = rp ? g.np - 1 - cc : cc;
-                            ok[u] = ok[u] && !in_fixed_set(ci, cj, ck, i, j, k);
-                            const long long x = node_index(g, i, j, k) * B + b;
-                            xs[u] = x;
-                            if (ok[u]) {
-                                const F *P = a.P;
-                                c[u] = a.coef[x];
-                                cm[u][0] = i > 0 ? a.coef[x - sr].x : (F)0;
-                                cm[u][1] = j > 0 ? a.coef[x - st].y : (F)0;
-                                cm[u][2] = k > 0 ? a.coef[x - sp].z : (F)0;
-                                Pn[u][0] = i < g.nr - 1 ? P[x + sr] : (F)0;
-                                Pn[u][1] = i > 0 ? P[x - sr] : (F)0;
-                                Pn[u][2] = j < g.nt - 1 ? P[x + st] : (F)0;
-                                Pn[u][3] = j > 0 ? P[x - st] : (F)0;
-                                Pn[u][4] = k < g.np - 1 ? P[x + sp] : (F)0;
-                                Pn[u][5] = k > 0 ? P[x - sp] : (F)0;
-                                Po[u] = P[x];
+                        for (int h = 0; h < 2; ++h) {
+                            if (!(h == 0 ? act0 : act1)) continue;
+                            const long long y = x + 32 * h;
+                            w[h] = cW[y];
+                            cx[h] = cX[y];
+                            cy[h] = cY[y];
+                            cz[h] = cZ[y];
+                            cmx[h] = lr ? cX[y - sr] : (F)0;
+                            cmy[h] = lt ? cY[y - st] : (F)0;
+                            cmz[h] = lp ? cZ[y - sp] : (F)0;
+                            Pn[h][0] = hr ? P[y + sr] : (F)0;
+                            Pn[h][1] = lr ? P[y - sr] : (F)0;
+                            Pn[h][2] = ht ? P[y + st] : (F)0;
+                            Pn[h][3] = lt ? P[y - st] : (F)0;
+                            Pn[h][4] = hp ? P[y + sp] : (F)0;
+                            Pn[h][5] = lp ? P[y - sp] : (F)0;
+                            po[h] = P[y];
+                        }
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            if (!(h == 0 ? act0 : act1)) continue;
+                            if (w[h] != w[h]) continue;  // fixed set: P stays 0
+                            const F pn = face_update<F>(cx[h], cy[h], cz[h], w[h], cmx[h],
+                                                        cmy[h], cmz[h], Pn[h]);
+                            P[x + 32 * h] = pn;
+                            if (h == 0) {
+                                err0 = fmax_(err0, fabs(pn - po[0]));
+                                if (o == 7) pmax0 = fmax_(pmax0, fabs(pn));
+                            } else {
+                                err1 = fmax_(err1, fabs(pn - po[1]));
+                                if (o == 7) pmax1 = fmax_(pmax1, fabs(pn));
                             }
                         }
-#pragma unroll
-                        for (int u = 0; u < kAdjBatch; ++u) {
-                            if (!ok[u]) continue;
-                            const F out = fmax_(c[u].x, (F)0) - fmin(cm[u][0], (F)0) +
-                                          fmax_(c[u].y, (F)0) - fmin(cm[u][1], (F)0) +
-                                          fmax_(c[u].z, (F)0) - fmin(cm[u][2], (F)0);
-                            const F in = fmax_(cm[u][0], (F)0) * Pn[u][1] - fmin(c[u].x, (F)0) * Pn[u][0] +
-                                         fmax_(cm[u][1], (F)0) * Pn[u][3] - fmin(c[u].y, (F)0) * Pn[u][2] +
-                                         fmax_(cm[u][2], (F)0) * Pn[u][5] - fmin(c[u].z, (F)0) * Pn[u][4];
-                            const F pn = out <= (F)1e-30 ? (F)0 : (c[u].w + in) / out;
-                            a.P[xs[u]] = pn;
-                            err = fmax_(err, fabs(pn - Po[u]));
-                            if (o == 7) pmax = fmax_(pmax, fabs(pn));
-                        }
+                        pk = pkn;
                     }
                 }
+                const int qa_next = qe + slot;
+                if (busy && !last && qa_next < qe_next) pk = __ldg(a.nodes + qa_next);
                 if (!grid_barrier(bar, a.spin_ns, nblk)) return;
+                qa = qa_next;
+                qe = qe_next;
             }
         }
         for (int x = threadIdx.x; x < Bg; x += blockDim.x) { s_err[x] = 0; s_pmax[x] = 0; }
         __syncthreads();
-        if (active) {
-            atomic_max_nonneg(&s_err[b - src0], err);
-            atomic_max_nonneg(&s_pmax[b - src0], pmax);
+        if (act0) {
+            atomic_max_nonneg(&s_err[b - src0], err0);
+            atomic_max_nonneg(&s_pmax[b - src0], pmax0);
+        }
+        if (act1) {
+            atomic_max_nonneg(&s_err[b + 32 - src0], err1);
+            atomic_max_nonneg(&s_pmax[b + 32 - src0], pmax1);
         }
         __syncthreads();
         for (int x = threadIdx.x; x < Bg; x += blockDim.x) {
