@@ -111,6 +111,11 @@ typedef struct {
                                to 4 barrier groups side by side. Results do not depend on it. */
     int fwd_groups;         /* node-hyperplane forward sweep: barrier groups per launch
                                (1..8), 0 = automatic. Results do not depend on it. */
+    int fwd_slots;          /* forward sweep: 0 = every source of the call resident at once;
+                               S > 0 (rounded up to a multiple of 32, below n_src) = retire and
+                               refill: one launch keeps S sources in flight and a source that
+                               converges (or reaches max_iter_fwd) hands its slot to the next
+                               one. Results and iteration counts do not depend on it. */
 } tt_opts;
 
 typedef struct tt_ctx tt_ctx;

@@ -59,7 +59,8 @@ class TTOpts(C.Structure):
     _fields_ = [("tol_fwd", C.c_double), ("tol_adj", C.c_double),
                 ("max_iter_fwd", C.c_int), ("max_iter_adj", C.c_int), ("init", C.c_int),
                 ("spin_limit_ns", C.c_longlong), ("launch_blocks", C.c_int),
-                ("sweep_schedule", C.c_int), ("adj_chunk", C.c_int), ("fwd_groups", C.c_int)]
+                ("sweep_schedule", C.c_int), ("adj_chunk", C.c_int), ("fwd_groups", C.c_int),
+                ("fwd_slots", C.c_int)]
 
 
 class TTStats(C.Structure):

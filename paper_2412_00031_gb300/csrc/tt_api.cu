@@ -49,7 +49,7 @@ struct tt_ctx {
     bool has_net = false;
     double *h_loss = nullptr;  // pinned
     // autotuner: scratch tau and the choices made, per (n_src, dtype)
-    DevBuf tune_tau;
+    DevBuf tune_tau, tau_w, slot_srcc, slot_int;
     struct Tuned { int n_src, dtype, schedule, groups; };
     std::vector<Tuned> tuned;
     int *h_pinned = nullptr;  // readback: [0..TT_MAX_BATCH) iterations, then flags
@@ -312,6 +312,7 @@ tt_status check_opts(tt_ctx *ctx, const tt_opts *o) {
     if (o->sweep_schedule < 0 || o->sweep_schedule > 1 + kNumTileShapes)
         return fail(ctx, TT_EINVAL, "sweep_schedule %d unknown", o->sweep_schedule);
     if (o->init < 0 || o->init > 2) return fail(ctx, TT_EINVAL, "init %d unknown", o->init);
+    if (o->fwd_slots < 0) return fail(ctx, TT_EINVAL, "fwd_slots %d < 0", o->fwd_slots);
     if (o->fwd_groups < 0 || o->fwd_groups > kMaxBarrierGroups)
         return fail(ctx, TT_EINVAL, "fwd_groups %d outside 0..%d", o->fwd_groups,
                     kMaxBarrierGroups);
@@ -341,6 +342,11 @@ template <typename F> struct Work {
     int *sidx = nullptr, *next = nullptr, *heads = nullptr, *nheads = nullptr;
     F *JS = nullptr;
     int t0c_slice = 0;  // sources per forward slice the factor cache holds
+    // retire-and-refill forward: slot working columns and slot table
+    F *tau_w = nullptr;
+    SrcC *slot_srcc = nullptr;
+    int *slot_int = nullptr;  // slot_src, slot_prev, slot_it, slot_fill ([slots] each), queue
+    int n_slots = 0;
     bool coef_ok = false;
     // warm start: features [chunk][N][6], activations [chunk][N][32] (two), output [chunk][N]
     float *net_x = nullptr, *net_y = nullptr;
@@ -423,6 +429,26 @@ template <typename F> tt_status work_from_ctx(tt_ctx *ctx, Work<F> &W, int B, in
             W.coef = (Vec4<F> *)ctx->coef.p;
         }
     }
+    return TT_OK;
+}
+
+// Slots of the retire-and-refill forward (0: every source resident): opts->fwd_slots
+// rounded up to a multiple of 32, at most the factor cache's slice.
+int refill_slots_for(const tt_opts *o, int B, int slice) {
+    if (o->fwd_slots <= 0 || o->fwd_slots >= B) return 0;
+    int S = (o->fwd_slots + 31) / 32 * 32;
+    if (S > slice) S = slice / 32 * 32;
+    return S >= B ? 0 : S;
+}
+
+template <typename F> tt_status refill_work_from_ctx(tt_ctx *ctx, Work<F> &W, int S) {
+    ENSURE(ctx->tau_w, sizeof(F) * (size_t)ctx->g.N * S);
+    ENSURE(ctx->slot_srcc, sizeof(SrcC) * (size_t)S);
+    ENSURE(ctx->slot_int, sizeof(int) * (4 * (size_t)S + 1));
+    W.tau_w = (F *)ctx->tau_w.p;
+    W.slot_srcc = (SrcC *)ctx->slot_srcc.p;
+    W.slot_int = (int *)ctx->slot_int.p;
+    W.n_slots = S;
     return TT_OK;
 }
 
@@ -547,7 +573,7 @@ tt_status enq_forward(tt_ctx *ctx, Work<F> &W, const tt_model *m, int B, void *d
     // (B values) that are a multiple of 16 bytes. Automatic: node hyperplanes.
     const bool tiles_ok = B >= 32 && (B * sizeof(F)) % 16 == 0;
     int sched = o->sweep_schedule == 0 ? 1 : o->sweep_schedule;
-    if (sched >= 2 && !tiles_ok) sched = 1;
+    if ((sched >= 2 && !tiles_ok) || W.n_slots > 0) sched = 1;
     const int slice = W.t0c_slice;
 
     const GeoTab<F> &t = geo<F>(ctx);
@@ -596,7 +622,55 @@ tt_status enq_forward(tt_ctx *ctx, Work<F> &W, const tt_model *m, int B, void *d
 
     int max_grid_used = 0;
     CK(record(ctx, ctx->ev_start[TT_STATS_FORWARD]));
-    for (int s0 = 0; s0 < B; s0 += slice) {
+    if (W.n_slots > 0) {
+        // Retire-and-refill: one launch over S slots; converged sources hand their slot to
+        // the next queued source (each source's arithmetic is that of the resident launch).
+        const int S = W.n_slots;
+        a.refill = 1;
+        a.n_all = B;
+        a.init_from_out = o->init != 0;
+        a.tau_out = (F *)d_tau;
+        a.tau = W.tau_w;
+        a.B = S;
+        a.src_all = W.src;
+        a.tabT_all = W.tabT;
+        a.tabP_all = W.tabP;
+        a.slot_srcc = W.slot_srcc;
+        a.src = W.slot_srcc;
+        a.slot_src = W.slot_int;
+        a.slot_prev = W.slot_int + S;
+        a.slot_it = W.slot_int + 2 * S;
+        a.slot_fill = W.slot_int + 3 * S;
+        a.queue = W.slot_int + 4 * S;
+        a.src_lo = 0;
+        a.src_n = S;
+        a.idx32 = (unsigned long long)g.N * (unsigned long long)(S > 8 ? S : 8) < (1ull << 32);
+        const int block = 256;
+        int per_sm = forward_blocks_per_sm<F>(block, fwd_smem_bytes<F>(S, block), a.idx32 != 0);
+        if (per_sm <= 0) return fail(ctx, TT_ECUDA, "sweep kernel cannot be resident");
+        if (per_sm > kMaxBarrierGroups) per_sm = kMaxBarrierGroups;
+        int max_grid = per_sm * ctx->n_sm;
+        if (o->launch_blocks > 0 && o->launch_blocks < max_grid) max_grid = o->launch_blocks;
+        int groups = o->fwd_groups > 0 ? o->fwd_groups : per_sm;
+        if (groups > kMaxBarrierGroups) groups = kMaxBarrierGroups;
+        if (groups > (S + 31) / 32) groups = (S + 31) / 32;
+        if (groups > max_grid) groups = max_grid;
+        int gsrc = ((S + groups - 1) / groups + 31) / 32 * 32;
+        groups = (S + gsrc - 1) / gsrc;
+        int gblocks = max_grid / groups;
+        if ((long long)gblocks * block < gsrc) gblocks = (gsrc + block - 1) / block;
+        if ((long long)gblocks * groups > (long long)per_sm * ctx->n_sm)
+            return fail(ctx, TT_EINVAL, "%d slots exceed one resident launch", S);
+        a.n_bgroups = groups;
+        a.grp_blocks = gblocks;
+        a.grp_src = gsrc;
+        CK(launch_refill_setup<F>(a, ctx->st));
+        CK(launch_forward<F>(a, gblocks * groups, block, ctx->st));
+        ctx->stats[TT_STATS_FORWARD].block_threads = block;
+        ctx->launches += 2;
+        max_grid_used = gblocks * groups;
+    }
+    for (int s0 = 0; s0 < (W.n_slots > 0 ? 0 : B); s0 += slice) {
         const int n = slice < B - s0 ? slice : B - s0;
         a.src_lo = s0;
         a.src_n = n;
@@ -920,6 +994,8 @@ tt_status forward_impl(tt_ctx *ctx, const tt_model *m, const tt_point *h_src, in
     Work<F> W;
     if ((s = work_from_ctx<F>(ctx, W, B, 0)) != TT_OK) return s;
     if (o->init == 2 && (s = net_work_from_ctx<F>(ctx, W, B)) != TT_OK) return s;
+    const int S = refill_slots_for(o, B, W.t0c_slice);
+    if (S > 0 && (s = refill_work_from_ctx<F>(ctx, W, S)) != TT_OK) return s;
     if ((s = stage_to(ctx, h_src, B, W.src_pts)) != TT_OK) return s;
     if ((s = enq_sources<F>(ctx, W, m, B)) != TT_OK) return s;
     if ((s = enq_forward<F>(ctx, W, m, B, d_tau, d_T, o)) != TT_OK) return s;
@@ -988,6 +1064,7 @@ void tt_default_opts(tt_opts *o, int dtype) {
     o->sweep_schedule = 0;
     o->adj_chunk = 0;
     o->fwd_groups = 0;
+    o->fwd_slots = 0;
 }
 
 const char *tt_last_error(const tt_ctx *ctx) { return ctx ? ctx->err : "no context"; }
@@ -1067,7 +1144,8 @@ void tt_ctx_destroy(tt_ctx *ctx) {
                       &ctx->wq, &ctx->sidx, &ctx->next, &ctx->heads, &ctx->nheads, &ctx->JS,
                       &ctx->coef, &ctx->t0c, &ctx->net_theta, &ctx->net_x, &ctx->net_a,
                       &ctx->net_b, &ctx->net_y, &ctx->net_d1, &ctx->net_d2, &ctx->net_dy,
-                      &ctx->net_wt, &ctx->net_part, &ctx->net_scr, &ctx->tune_tau,
+                      &ctx->net_wt, &ctx->net_part, &ctx->net_scr, &ctx->tune_tau, &ctx->tau_w,
+                      &ctx->slot_srcc, &ctx->slot_int,
                       &ctx->net_wbf};
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
@@ -1453,6 +1531,13 @@ template <typename F> tt_status plan_alloc(tt_plan *p, Work<F> &W) {
     TTGB_GET(heads, sizeof(int) * S);
     TTGB_GET(nheads, sizeof(int));
     TTGB_GET(JS, sizeof(F) * (size_t)S * B);
+    const int n_slots = refill_slots_for(&p->opts, B, W.t0c_slice);
+    if (n_slots > 0) {
+        TTGB_GET(tau_w, sizeof(F) * (size_t)g.N * n_slots);
+        TTGB_GET(slot_srcc, sizeof(SrcC) * (size_t)n_slots);
+        TTGB_GET(slot_int, sizeof(int) * (4 * (size_t)n_slots + 1));
+        W.n_slots = n_slots;
+    }
     if (p->opts.init == 2) {
         W.net_chunk = net_chunk(g, B);
         TTGB_GET(net_x, sizeof(float) * kNetFeatures * (size_t)g.N * W.net_chunk);

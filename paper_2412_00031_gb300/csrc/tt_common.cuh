@@ -86,55 +86,6 @@ __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
 #endif
 __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
 
-// T0 at node (i, j, k) for one source, returned as 1/T0 and u = p0 / T0, where p0 is the
-// gradient of T0 in the node's physical components (d_r, d_theta / r, d_phi / (r cos theta)).
-// Spherical geometry: with dth = theta - theta_s and dph = phi - phi_s,
-//   D_up    = (r - r_s) - r [(1 - cos dth) + cos th_s cos th (1 - cos dph)]
-//   D_north = r [sin dth + sin th_s cos th (1 - cos dph)]
-//   D_east  = r cos th sin dph
-// (no cancellation: the small angle terms come from tables built in FP64), and p0 is the
-// source-frame gradient s0^2 M0^-1 D / T0 rotated into the node frame by Q_ab = e_a . E_b.
-// tabT = (sin dth, 1 - cos dth) at the node's latitude, tabP = (sin dph, 1 - cos dph).
-// Flat geometry: tabT = (R_E dth, 0), tabP = (R_E dph, 0), D = (r - r_s, tabT.x, tabP.x), Q = I.
-// Offset D = (up, north, east) of node (i, r, theta) from the source in the source's frame.
-template <typename F>
-__device__ __forceinline__ void source_offset(const SrcReg<F> &S, int i, F r, F cth, Vec2<F> tT,
-                                              Vec2<F> tP, bool flat, F &du, F &dn, F &de) {
-    du = ((F)(i - S.ir) - S.frr) * S.dr;
-    if (flat) {
-        dn = tT.x;
-        de = tP.x;
-    } else {
-        du = du - r * (tT.y + S.cts * cth * tP.y);
-        dn = r * (tT.x + S.sts * cth * tP.y);
-        de = r * cth * tP.x;
-    }
-}
-
-template <typename F>
-__device__ __forceinline__ F factor_T0(const SrcReg<F> &S, int i, F r, F cth, F sth,
-                                       Vec2<F> tT, Vec2<F> tP, bool flat, F &ur, F &ut, F &up) {
-    F du, dn, de;
-    source_offset<F>(S, i, r, cth, tT, tP, flat, du, dn, de);
-    F wn = S.b11 * dn + S.b12 * de;
-    F we = S.b12 * dn + S.b22 * de;
-    F q = du * du + dn * wn + de * we;
-    F rho = rsqrt_(q);
-    F rho2 = rho * rho;
-    if (flat) {
-        ur = rho2 * du; ut = rho2 * wn; up = rho2 * we;
-    } else {
-        F omc = (F)1 - tT.y;
-        F Qrr = omc - S.cts * cth * tP.y, Qrt = tT.x + S.sts * cth * tP.y, Qrp = cth * tP.x;
-        F Qtr = -tT.x + sth * S.cts * tP.y, Qtt = omc - sth * S.sts * tP.y, Qtp = -sth * tP.x;
-        F Qpr = -S.cts * tP.x, Qpt = S.sts * tP.x, Qpp = (F)1 - tP.y;
-        ur = rho2 * (Qrr * du + Qrt * wn + Qrp * we);
-        ut = rho2 * (Qtr * du + Qtt * wn + Qtp * we);
-        up = rho2 * (Qpr * du + Qpt * wn + Qpp * we);
-    }
-    return rho * S.inv_s0;  // 1 / T0 = 1 / (s0 sqrt(q))
-}
-
 // Rounding-explicit arithmetic: each call is one IEEE operation that the compiler neither
 // contracts nor reorders, so every kernel that calls lf_core performs bit-identical
 // arithmetic whatever code surrounds it.
@@ -148,6 +99,61 @@ __device__ __forceinline__ float sub_(float a, float b) { return __fsub_rn(a, b)
 __device__ __forceinline__ double sub_(double a, double b) { return __dsub_rn(a, b); }
 __device__ __forceinline__ float div_(float a, float b) { return __fdiv_rn(a, b); }
 __device__ __forceinline__ double div_(double a, double b) { return __ddiv_rn(a, b); }
+
+// Offset D = (up, north, east) of node (i, r, theta) from the source in the source's frame.
+// Rounding-explicit (like every function below), so the factor is the same bits in every
+// kernel that computes it.
+template <typename F>
+__device__ __forceinline__ void source_offset(const SrcReg<F> &S, int i, F r, F cth, Vec2<F> tT,
+                                              Vec2<F> tP, bool flat, F &du, F &dn, F &de) {
+    du = mul_(sub_((F)(i - S.ir), S.frr), S.dr);
+    if (flat) {
+        dn = tT.x;
+        de = tP.x;
+    } else {
+        du = sub_(du, mul_(r, fma_(mul_(S.cts, cth), tP.y, tT.y)));
+        dn = mul_(r, fma_(mul_(S.sts, cth), tP.y, tT.x));
+        de = mul_(mul_(r, cth), tP.x);
+    }
+}
+
+// T0 at node (i, j, k) for one source, returned as 1/T0 and u = p0 / T0, where p0 is the
+// gradient of T0 in the node's physical components (d_r, d_theta / r, d_phi / (r cos theta)).
+// Spherical geometry: with dth = theta - theta_s and dph = phi - phi_s,
+//   D_up    = (r - r_s) - r [(1 - cos dth) + cos th_s cos th (1 - cos dph)]
+//   D_north = r [sin dth + sin th_s cos th (1 - cos dph)]
+//   D_east  = r cos th sin dph
+// (no cancellation: the small angle terms come from tables built in FP64), and p0 is the
+// source-frame gradient s0^2 M0^-1 D / T0 rotated into the node frame by Q_ab = e_a . E_b.
+// tabT = (sin dth, 1 - cos dth) at the node's latitude, tabP = (sin dph, 1 - cos dph).
+// Flat geometry: tabT = (R_E dth, 0), tabP = (R_E dph, 0), D = (r - r_s, tabT.x, tabP.x), Q = I.
+template <typename F>
+__device__ __forceinline__ F factor_T0(const SrcReg<F> &S, int i, F r, F cth, F sth,
+                                       Vec2<F> tT, Vec2<F> tP, bool flat, F &ur, F &ut, F &up) {
+    F du, dn, de;
+    source_offset<F>(S, i, r, cth, tT, tP, flat, du, dn, de);
+    const F wn = fma_(S.b11, dn, mul_(S.b12, de));
+    const F we = fma_(S.b12, dn, mul_(S.b22, de));
+    const F q = fma_(du, du, fma_(dn, wn, mul_(de, we)));
+    const F rho = rsqrt_(q);
+    const F rho2 = mul_(rho, rho);
+    if (flat) {
+        ur = mul_(rho2, du);
+        ut = mul_(rho2, wn);
+        up = mul_(rho2, we);
+    } else {
+        const F omc = sub_((F)1, tT.y);
+        const F Qrr = sub_(omc, mul_(mul_(S.cts, cth), tP.y));
+        const F Qrt = fma_(mul_(S.sts, cth), tP.y, tT.x), Qrp = mul_(cth, tP.x);
+        const F Qtr = fma_(mul_(sth, S.cts), tP.y, -tT.x);
+        const F Qtt = sub_(omc, mul_(mul_(sth, S.sts), tP.y)), Qtp = -mul_(sth, tP.x);
+        const F Qpr = -mul_(S.cts, tP.x), Qpt = mul_(S.sts, tP.x), Qpp = sub_((F)1, tP.y);
+        ur = mul_(rho2, fma_(Qrr, du, fma_(Qrt, wn, mul_(Qrp, we))));
+        ut = mul_(rho2, fma_(Qtr, du, fma_(Qtt, wn, mul_(Qtp, we))));
+        up = mul_(rho2, fma_(Qpr, du, fma_(Qpt, wn, mul_(Qpp, we))));
+    }
+    return mul_(rho, S.inv_s0);  // 1 / T0 = 1 / (s0 sqrt(q))
+}
 
 // Lax-Friedrichs update of tau at an interior node for one source (Sec. 3.1 with the
 // factor of factor_T0). Dividing the update by T0, with u = p0 / T0 and

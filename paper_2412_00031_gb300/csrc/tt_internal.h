@@ -66,6 +66,17 @@ template <typename F> struct FwdArgs {
     int src_lo, src_n;
     Vec4<F> *t0c;
     int idx32;        // every [node][source] index fits in 32 bits
+    // Retire-and-refill mode (refill != 0): the launch works on B slots; tau and t0c are
+    // the slots' working columns ([N][B]) and src their SrcC copies. Sources 0..n_all-1
+    // come from a queue: when a slot's source converges (or reaches max_iter) its column is
+    // copied to tau_out[N][n_all], and the slot takes the next source. iters / conv are
+    // per source then ([n_all]).
+    int refill, n_all, init_from_out;
+    F *tau_out;
+    const SrcC *src_all;                    // [n_all]
+    const Vec2<F> *tabT_all, *tabP_all;     // [n_t][n_all], [n_p][n_all]
+    SrcC *slot_srcc;                        // [B]
+    int *slot_src, *slot_prev, *slot_it, *slot_fill, *queue;  // [B] each; queue: 1 int
 };
 
 template <typename F> struct AdjArgs {
@@ -107,6 +118,8 @@ template <typename F> cudaError_t launch_adjoint(const AdjArgs<F> &a, int grid, 
                                                  cudaStream_t st);
 template <typename F> int forward_blocks_per_sm(int block, size_t smem, bool idx32);
 template <typename F> cudaError_t launch_t0_cache(const FwdArgs<F> &a, cudaStream_t st);
+// Slot table of the retire-and-refill mode: slot s < n_slots takes source s.
+template <typename F> cudaError_t launch_refill_setup(const FwdArgs<F> &a, cudaStream_t st);
 
 // Tile shapes of the tile-wavefront forward sweep (sweep-local a = r, b = theta, c = phi).
 struct TileShape {

@@ -93,6 +93,52 @@ __device__ __forceinline__ void extrapolate(const FwdArgs<F> &a, int b, int axis
     }
 }
 
+// Retire-and-refill: for every slot x of a group whose fill flag is set, copy the
+// retiring source's column of tau to the output and load the new source into the slot:
+// tau = 1 (or the caller's tau), the fixed set tau = 1, and its factor cache column,
+// computed exactly as t0_cache_kernel does. The group's threads stride over the nodes.
+template <typename F>
+__device__ void refill_slots(const FwdArgs<F> &a, int src0, int Bg, int blk) {
+    const GridC &g = a.g;
+    const long long S = a.B, NA = a.n_all;
+    const long long stride = (long long)a.grp_blocks * blockDim.x;
+    const long long first = (long long)blk * blockDim.x + threadIdx.x;
+    for (int x = src0; x < src0 + Bg; ++x) {
+        if (((volatile int *)a.slot_fill)[x] == 0) continue;
+        const int old = ((volatile int *)a.slot_prev)[x], nw = ((volatile int *)a.slot_src)[x];
+        SrcReg<F> S_;
+        if (nw >= 0) S_ = load_src<F>(a.src_all, nw, g.dr);
+        for (long long n = first; n < g.N; n += stride) {
+            const long long xs = n * S + x;
+            if (old >= 0) a.tau_out[n * NA + old] = a.tau[xs];
+            if (nw < 0) continue;
+            const int k = (int)(n % g.np);
+            const long long tq = n / g.np;
+            const int j = (int)(tq % g.nt), i = (int)(tq / g.nt);
+            Vec4<F> c;
+            c.x = factor_T0<F>(S_, i, __ldg(a.rad + i), __ldg(a.cost + j), __ldg(a.sint + j),
+                               a.tabT_all[(long long)j * NA + nw], a.tabP_all[(long long)k * NA + nw],
+                               g.flat != 0, c.y, c.z, c.w);
+            const bool fixed = in_fixed_set(S_.ci, S_.cj, S_.ck, i, j, k);
+            if (fixed) c.x = (F)-1;
+            a.t0c[xs] = c;
+            a.tau[xs] = fixed || !a.init_from_out ? (F)1 : a.tau_out[n * NA + nw];
+        }
+    }
+}
+
+template <typename F> __global__ void refill_setup_kernel(FwdArgs<F> a) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x == 0) *a.queue = a.B < a.n_all ? a.B : a.n_all;
+    if (x >= a.B) return;
+    const bool has = x < a.n_all;
+    a.slot_src[x] = has ? x : -1;
+    a.slot_prev[x] = -1;
+    a.slot_it[x] = 0;
+    a.slot_fill[x] = has ? 1 : 0;
+    if (has) a.slot_srcc[x] = a.src_all[x];
+}
+
 // Node-hyperplane schedule. The launch is split into barrier groups: group g owns a
 // contiguous slice of the launch's sources and a contiguous range of blocks, runs the whole
 // solve of its slice with its own grid barrier and convergence test, and so never waits for
@@ -156,7 +202,9 @@ __device__ __forceinline__ F update_one(F *p, const F *v, const Vec4<F> &c, cons
 }
 
 // I: index type of the [node][source] fields (32-bit when every index fits).
-template <typename F, typename I>
+// REFILL: the retire-and-refill mode (compiled separately, so that the resident launch
+// carries none of its code).
+template <typename F, typename I, bool REFILL>
 __global__ void __launch_bounds__(256, TTGB_FWD_MIN_BLOCKS) fwd_sweep_kernel(FwdArgs<F> a) {
     extern __shared__ unsigned char smem_raw[];
     F *s_err = reinterpret_cast<F *>(smem_raw);
@@ -188,9 +236,18 @@ __global__ void __launch_bounds__(256, TTGB_FWD_MIN_BLOCKS) fwd_sweep_kernel(Fwd
     const I src_n = (I)a.src_n;
     F *tau = a.tau;
 
-    for (int it = 0; it < a.max_iter; ++it) {
-        const bool act0 = ok0 && ((volatile int *)a.conv)[b] == 0;
-        const bool act1 = ok1 && ((volatile int *)a.conv)[b + 32] == 0;
+    // retire-and-refill: load the group's first sources into their slots
+    if (REFILL) {
+        refill_slots<F>(a, src0, Bg, blk);
+        if (!grid_barrier(bar, a.spin_ns, nblk)) return;
+    }
+    // with refill a group runs until its queue is empty; each source still stops at max_iter
+    const long long it_end = REFILL ? (long long)a.max_iter * (a.n_all + 1) : a.max_iter;
+    for (long long it = 0; it < it_end; ++it) {
+        const bool act0 = ok0 && (REFILL ? ((volatile int *)a.slot_src)[b] >= 0
+                                           : ((volatile int *)a.conv)[b] == 0);
+        const bool act1 = ok1 && (REFILL ? ((volatile int *)a.slot_src)[b + 32] >= 0
+                                           : ((volatile int *)a.conv)[b + 32] == 0);
         const bool busy = lane_ok && __any_sync(0xffffffffu, act0 || act1);  // uniform
         F err0 = 0, err1 = 0;
         for (int o = 0; o < 8; ++o) {
@@ -269,11 +326,40 @@ __global__ void __launch_bounds__(256, TTGB_FWD_MIN_BLOCKS) fwd_sweep_kernel(Fwd
             if (threadIdx.x == 0) s_cnt = 0;
             __syncthreads();
             for (int x = src0 + threadIdx.x; x < src0 + Bg; x += blockDim.x) {
+                if (REFILL) {
+                    // slots: a finished source hands its slot to the next queued source
+                    a.slot_fill[x] = 0;
+                    const int s = a.slot_src[x];
+                    if (s < 0) continue;
+                    F m = 0;
+                    for (int c = grp * a.grp_blocks; c < (grp + 1) * a.grp_blocks; ++c)
+                        m = fmax_(m, ((volatile F *)a.partial)[(long long)c * B + x]);
+                    const int its = a.slot_it[x] + 1;
+                    a.slot_it[x] = its;
+                    if (!(m < a.tol) && its < a.max_iter) {
+                        atomicAdd(&s_cnt, 1);
+                        continue;
+                    }
+                    a.iters[s] = its;
+                    a.conv[s] = m < a.tol ? 1 : 0;
+                    const int nw = atomicAdd(a.queue, 1);
+                    a.slot_prev[x] = s;
+                    a.slot_fill[x] = 1;
+                    a.slot_it[x] = 0;
+                    if (nw < a.n_all) {
+                        a.slot_src[x] = nw;
+                        a.slot_srcc[x] = a.src_all[nw];
+                        atomicAdd(&s_cnt, 1);
+                    } else {
+                        a.slot_src[x] = -1;
+                    }
+                    continue;
+                }
                 if (a.conv[x]) continue;
                 F m = 0;
                 for (int c = grp * a.grp_blocks; c < (grp + 1) * a.grp_blocks; ++c)
                     m = fmax_(m, ((volatile F *)a.partial)[(long long)c * B + x]);
-                a.iters[x] = it + 1;
+                a.iters[x] = (int)it + 1;
                 if (m < a.tol) a.conv[x] = 1;
                 else atomicAdd(&s_cnt, 1);
             }
@@ -281,6 +367,11 @@ __global__ void __launch_bounds__(256, TTGB_FWD_MIN_BLOCKS) fwd_sweep_kernel(Fwd
             if (threadIdx.x == 0) ((volatile int *)a.n_active)[grp] = s_cnt;
         }
         if (!grid_barrier(bar, a.spin_ns, nblk)) return;
+        if (REFILL) {
+            // retire the finished columns and load the new sources, then start them together
+            refill_slots<F>(a, src0, Bg, blk);
+            if (!grid_barrier(bar, a.spin_ns, nblk)) return;
+        }
         if (((volatile int *)a.n_active)[grp] == 0) break;
     }
     barrier_end(bar, nblk);
@@ -1006,7 +1097,10 @@ template <typename F>
 cudaError_t launch_forward(const FwdArgs<F> &a, int grid, int block, cudaStream_t st) {
     void *args[] = {const_cast<FwdArgs<F> *>(&a)};
     const size_t smem = fwd_smem_bytes<F>(a.grp_src, block);
-    void *fn = a.idx32 ? (void *)fwd_sweep_kernel<F, unsigned> : (void *)fwd_sweep_kernel<F, long long>;
+    void *fn = a.refill ? (a.idx32 ? (void *)fwd_sweep_kernel<F, unsigned, true>
+                                   : (void *)fwd_sweep_kernel<F, long long, true>)
+                        : (a.idx32 ? (void *)fwd_sweep_kernel<F, unsigned, false>
+                                   : (void *)fwd_sweep_kernel<F, long long, false>);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(block), args, smem, st);
@@ -1020,13 +1114,19 @@ cudaError_t launch_adjoint(const AdjArgs<F> &a, int grid, int block, cudaStream_
                                        args, smem, st);
 }
 
+template <typename F> cudaError_t launch_refill_setup(const FwdArgs<F> &a, cudaStream_t st) {
+    refill_setup_kernel<F><<<(a.B + 255) / 256, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
 template <typename F> size_t fwd_smem_bytes(int grp_src, int) {
     return fwd_err_bytes<F>(grp_src);
 }
 
 template <typename F> int forward_blocks_per_sm(int block, size_t smem, bool idx32) {
     int n = 0;
-    void *fn = idx32 ? (void *)fwd_sweep_kernel<F, unsigned> : (void *)fwd_sweep_kernel<F, long long>;
+    void *fn = idx32 ? (void *)fwd_sweep_kernel<F, unsigned, false>
+                     : (void *)fwd_sweep_kernel<F, long long, false>;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return 0;
@@ -1099,6 +1199,8 @@ template <typename F> cudaError_t launch_t0_cache(const FwdArgs<F> &a, cudaStrea
 
 template cudaError_t launch_t0_cache<float>(const FwdArgs<float> &, cudaStream_t);
 template cudaError_t launch_t0_cache<double>(const FwdArgs<double> &, cudaStream_t);
+template cudaError_t launch_refill_setup<float>(const FwdArgs<float> &, cudaStream_t);
+template cudaError_t launch_refill_setup<double>(const FwdArgs<double> &, cudaStream_t);
 
 template <typename F> cudaError_t launch_adjoint_coefs(const AdjArgs<F> &a, cudaStream_t st) {
     long long total = a.g.N * a.B;

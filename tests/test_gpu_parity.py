@@ -240,3 +240,51 @@ def test_autotuner_picks_a_measured_candidate_with_identical_results(tt):
                         ctx=ctx)
         assert np.array_equal(ref["tau"], out["tau"])
     ctx.close()
+
+
+@pytest.mark.parametrize("slots", [32, 64])
+def test_retire_and_refill_gives_the_resident_bits(tt, slots):
+    """One launch with `slots` sources in flight, each converged source handing its slot to
+    the next queued one, performs every source's arithmetic as the all-resident launch:
+    same tau, T and iteration counts, from tau = 1 and from a given tau, under an
+    iteration cap (statuses and counts), and inside a captured plan."""
+    import torch
+    w = I.small_case(17, shape=(13, 15, 16), n_src=80, n_rec=5)
+    ref = gpu_solve(w, "f32", steps=("fwd",))
+    o = tt.default_opts(tt.TT_F32, fwd_slots=slots)
+    out = gpu_solve(w, "f32", opts=o, steps=("fwd",))
+    assert np.array_equal(out["iters_fwd"], ref["iters_fwd"])
+    assert np.array_equal(out["tau"], ref["tau"]) and np.array_equal(out["T"], ref["T"])
+    start = (1.0 + 0.97 * (ref["tau"] - 1.0)).astype(np.float32)
+    a = gpu_solve(w, "f32", opts=tt.default_opts(tt.TT_F32, init=1), steps=("fwd",), tau_init=start)
+    b = gpu_solve(w, "f32", opts=tt.default_opts(tt.TT_F32, init=1, fwd_slots=slots),
+                  steps=("fwd",), tau_init=start)
+    assert np.array_equal(a["iters_fwd"], b["iters_fwd"]) and np.array_equal(a["tau"], b["tau"])
+    ctx = tt.tt_ctx_create(w.grid.as_dict())
+    model = tuple(to_dev(x, torch.float32) for x in (w.s, w.xi, w.eta))
+    res = []
+    for s in (0, slots):
+        tau = torch.empty(w.grid.shape + (w.n_src,), device="cuda")
+        oc = tt.default_opts(tt.TT_F32, max_iter_fwd=3, fwd_slots=s)
+        with pytest.raises(tt.TTError) as e:
+            tt.tt_forward(ctx, model, w.src, tau, None, oc)
+        assert e.value.status == tt.TT_ENOTCONVERGED
+        res.append((tt.tt_forward(ctx, model, w.src, tau, None, oc, allow_unconverged=True),
+                    tau.cpu().numpy()))
+    assert np.array_equal(res[0][0], res[1][0]) and (res[1][0] == 3).all()
+    assert np.array_equal(res[0][1], res[1][1])
+    # a plan with refill replays the step with the same bits
+    full = gpu_solve(w, "f32")
+    shape = w.grid.shape + (w.n_src,)
+    tau, T, P = (torch.empty(shape, device="cuda") for _ in range(3))
+    data = tt.DeviceData.from_workload(w)
+    chi = torch.empty((w.n_src, 2), dtype=torch.float64, device="cuda")
+    R = torch.empty((w.n_src, data.n_rec), dtype=torch.float64, device="cuda")
+    K = [torch.empty(w.grid.shape, dtype=torch.float64, device="cuda") for _ in range(3)]
+    plan = tt.tt_plan_create(ctx, model, w.src, data, tau, T, P, chi, R, *K, opts=o)
+    itf, _ = tt.tt_plan_run(plan)
+    assert np.array_equal(itf, full["iters_fwd"])
+    assert np.array_equal(tau.cpu().numpy(), full["tau"])
+    assert np.array_equal(P.cpu().numpy(), full["P"])
+    plan.close()
+    ctx.close()
