@@ -327,9 +327,55 @@ def gpu_arm(args, rank, world):
     }
     if args.unbatched > 0:
         result["unbatched"] = unbatched_leg(args, w, dev, world)
+    if args.refill_sources > w.n_src:
+        result["refill"] = refill_leg(args, dev, world, w.n_src, gp)
     if args.warm_start and os.path.exists(args.warm_start):
         result["warm_start"] = warm_leg(args, gp, world)
     return result, w, (float(itf.mean()), float(ita.mean()))
+
+
+def refill_leg(args, dev, world, slots, gp):
+    """Forward sweeps of a workload larger than one batch (args.refill_sources sources on
+    the same grid) with `slots` sources in flight: one retire-and-refill launch against
+    consecutive resident batches of `slots` sources (what a caller does without refill)."""
+    torch, tt = gp.torch, gp.tt
+    big = I.anisotropic_batch(seed=I.SEED_BASE + 2 + 100, n_src=args.refill_sources)
+    f32 = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32), device=dev)
+    model = (f32(big.s), f32(big.xi), f32(big.eta))
+    ctx = tt.tt_ctx_create(big.grid.as_dict())
+    tau = torch.empty(big.grid.shape + (big.n_src,), dtype=torch.float32, device=dev)
+    o_refill = tt.default_opts(tt.TT_F32, fwd_slots=slots, fwd_groups=gp.opts.fwd_groups)
+    o_batch = tt.default_opts(tt.TT_F32, fwd_groups=gp.opts.fwd_groups)
+    starts = list(range(0, big.n_src, slots))
+    taus = [torch.empty(big.grid.shape + (min(slots, big.n_src - s0),), dtype=torch.float32,
+                        device=dev) for s0 in starts]
+
+    def refill():
+        return tt.tt_forward(ctx, model, big.src, tau, None, o_refill)
+
+    def batches():
+        return np.concatenate([tt.tt_forward(ctx, model, big.src[s0:s0 + slots], tb, None,
+                                             o_batch) for s0, tb in zip(starts, taus)])
+
+    out = {}
+    for name, fn in (("refill", refill), ("batches", batches)):
+        fn()                                  # warm-up: allocation
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        it = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        out[name] = (dist_max(e0.elapsed_time(e1), world), it)
+    ctx.close()
+    return {"sources": big.n_src, "slots": slots, "forward_ms_refill": out["refill"][0],
+            "forward_ms_batches": out["batches"][0],
+            "speedup": out["batches"][0] / out["refill"][0],
+            "iters_fwd_mean": float(out["refill"][1].mean()),
+            "iters_fwd_max": int(out["refill"][1].max()),
+            "same_iterations": bool(np.array_equal(out["refill"][1], out["batches"][1])),
+            "note": "forward only; refill = one launch with %d slots; batches = %d resident "
+                    "launches of up to %d sources" % (slots, len(starts), slots)}
 
 
 def unbatched_leg(args, w, dev, world):
@@ -517,6 +563,8 @@ def main():
                     help="weights of the warm-start network; '' skips the warm-started leg")
     ap.add_argument("--autotune", type=int, default=1,
                     help="1: pick the forward launch configuration with tt_autotune first")
+    ap.add_argument("--refill-sources", type=int, default=768,
+                    help="sources of the retire-and-refill line (forward only; 0 skips it)")
     ap.add_argument("--unbatched", type=int, default=2,
                     help="sources timed one per step for the unbatched line (0 skips it)")
     ap.add_argument("--launch-blocks", type=int, default=0,
