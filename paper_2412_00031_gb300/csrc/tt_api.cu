@@ -653,9 +653,10 @@ tt_status enq_forward(tt_ctx *ctx, Work<F> &W, const tt_model *m, int B, void *d
         if (o->launch_blocks > 0 && o->launch_blocks < max_grid) max_grid = o->launch_blocks;
         int groups = o->fwd_groups > 0 ? o->fwd_groups : per_sm;
         if (groups > kMaxBarrierGroups) groups = kMaxBarrierGroups;
-        if (groups > (S + 31) / 32) groups = (S + 31) / 32;
+        const int wsrc = 32 * kFwdSourcesPerLane;
+        if (groups > (S + wsrc - 1) / wsrc) groups = (S + wsrc - 1) / wsrc;
         if (groups > max_grid) groups = max_grid;
-        int gsrc = ((S + groups - 1) / groups + 31) / 32 * 32;
+        int gsrc = ((S + groups - 1) / groups + wsrc - 1) / wsrc * wsrc;
         groups = (S + gsrc - 1) / gsrc;
         int gblocks = max_grid / groups;
         if ((long long)gblocks * block < gsrc) gblocks = (gsrc + block - 1) / block;
@@ -684,11 +685,12 @@ tt_status enq_forward(tt_ctx *ctx, Work<F> &W, const tt_model *m, int B, void *d
             if (per_sm > kMaxBarrierGroups) per_sm = kMaxBarrierGroups;
             int max_grid = per_sm * ctx->n_sm;
             if (o->launch_blocks > 0 && o->launch_blocks < max_grid) max_grid = o->launch_blocks;
+            const int wsrc = 32 * kFwdSourcesPerLane;  // sources of one warp
             int groups = o->fwd_groups > 0 ? o->fwd_groups : per_sm;
             if (groups > kMaxBarrierGroups) groups = kMaxBarrierGroups;
-            if (groups > (n + 31) / 32) groups = (n + 31) / 32;
+            if (groups > (n + wsrc - 1) / wsrc) groups = (n + wsrc - 1) / wsrc;
             if (groups > max_grid) groups = max_grid;
-            int gsrc = ((n + groups - 1) / groups + 31) / 32 * 32;
+            int gsrc = ((n + groups - 1) / groups + wsrc - 1) / wsrc * wsrc;
             groups = (n + gsrc - 1) / gsrc;
             int gblocks = max_grid / groups;
             if ((long long)gblocks * block < gsrc) {

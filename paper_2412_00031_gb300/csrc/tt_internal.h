@@ -134,6 +134,12 @@ cudaError_t launch_forward_tiled(const CUtensorMap &map_tau, const CUtensorMap &
                                  int grid, cudaStream_t st);
 template <typename F> int forward_tiled_blocks_per_sm(int shape, int B);
 constexpr int kTileThreads = 256;
+// Sources one lane of the node-hyperplane forward sweep updates at each node (a warp covers
+// 32 x this many consecutive sources); barrier groups are sized in multiples of a warp's.
+#ifndef TTGB_FWD_NS
+#define TTGB_FWD_NS 2
+#endif
+constexpr int kFwdSourcesPerLane = TTGB_FWD_NS;
 constexpr int kMaxBarrierGroups = 8;
 template <typename F> int adjoint_blocks_per_sm(int block, size_t smem);
 // Face-coefficient adjoint: coefficients once per solve, then the sweep over P.

@@ -206,6 +206,7 @@ __device__ __forceinline__ F update_one(F *p, const F *v, const Vec4<F> &c, cons
 // carries none of its code).
 template <typename F, typename I, bool REFILL>
 __global__ void __launch_bounds__(256, TTGB_FWD_MIN_BLOCKS) fwd_sweep_kernel(FwdArgs<F> a) {
+    constexpr int NS = kFwdSourcesPerLane;              // sources of one lane: l0 + 32 h
     extern __shared__ unsigned char smem_raw[];
     F *s_err = reinterpret_cast<F *>(smem_raw);
     __shared__ int s_cnt;
@@ -217,7 +218,7 @@ __global__ void __launch_bounds__(256, TTGB_FWD_MIN_BLOCKS) fwd_sweep_kernel(Fwd
     const int Bg = min(a.src_lo + a.src_n, src0 + a.grp_src) - src0;  // sources of the group
     if (Bg <= 0) return;
     barrier_begin();
-    const int Bw = ((Bg + 63) >> 6) << 5;               // lanes of one slot
+    const int Bw = (Bg + 32 * NS - 1) / (32 * NS) * 32; // lanes of one slot
     BarrierState *bar = a.bar + grp;
     const unsigned nblk = (unsigned)a.grp_blocks;
     const int slots = (int)(((long long)a.grp_blocks * blockDim.x) / Bw);
@@ -226,9 +227,11 @@ __global__ void __launch_bounds__(256, TTGB_FWD_MIN_BLOCKS) fwd_sweep_kernel(Fwd
     const int bl = lane_ok ? (int)(tid % Bw) : 0;
     const int slot = lane_ok ? (int)(tid / Bw) : 0;
     const int lane = threadIdx.x & 31;
-    const int l0 = ((bl >> 5) << 6) + lane;             // the lane's first source in the group
-    const bool ok0 = lane_ok && l0 < Bg, ok1 = lane_ok && l0 + 32 < Bg;
-    const int b = src0 + (ok0 ? l0 : 0);                // second source: b + 32
+    const int l0 = (bl >> 5) * (32 * NS) + lane;        // the lane's first source in the group
+    bool okh[NS];
+#pragma unroll
+    for (int h = 0; h < NS; ++h) okh[h] = lane_ok && l0 + 32 * h < Bg;
+    const int b = src0 + (okh[0] ? l0 : 0);             // the lane's sources: b + 32 h
     const I sp = (I)B, st = (I)g.np * (I)B, sr = (I)g.nt * (I)g.np * (I)B;
     const I snode_r = (I)g.nt * (I)g.np, snode_t = (I)g.np;
     const F *recf = reinterpret_cast<const F *>(a.rec);
@@ -244,12 +247,18 @@ __global__ void __launch_bounds__(256, TTGB_FWD_MIN_BLOCKS) fwd_sweep_kernel(Fwd
     // with refill a group runs until its queue is empty; each source still stops at max_iter
     const long long it_end = REFILL ? (long long)a.max_iter * (a.n_all + 1) : a.max_iter;
     for (long long it = 0; it < it_end; ++it) {
-        const bool act0 = ok0 && (REFILL ? ((volatile int *)a.slot_src)[b] >= 0
-                                           : ((volatile int *)a.conv)[b] == 0);
-        const bool act1 = ok1 && (REFILL ? ((volatile int *)a.slot_src)[b + 32] >= 0
-                                           : ((volatile int *)a.conv)[b + 32] == 0);
-        const bool busy = lane_ok && __any_sync(0xffffffffu, act0 || act1);  // uniform
-        F err0 = 0, err1 = 0;
+        bool act[NS];
+        bool any = false;
+#pragma unroll
+        for (int h = 0; h < NS; ++h) {
+            act[h] = okh[h] && (REFILL ? ((volatile int *)a.slot_src)[b + 32 * h] >= 0
+                                       : ((volatile int *)a.conv)[b + 32 * h] == 0);
+            any = any || act[h];
+        }
+        const bool busy = lane_ok && __any_sync(0xffffffffu, any);  // uniform
+        F err[NS];
+#pragma unroll
+        for (int h = 0; h < NS; ++h) err[h] = 0;
         for (int o = 0; o < 8; ++o) {
             const bool rr = o & 4, rt = o & 2, rp = o & 1;
             // node index of sweep-local (aa, bb, cc): n0 + aa * sa + bb * sb + cc * sc
@@ -270,32 +279,27 @@ __global__ void __launch_bounds__(256, TTGB_FWD_MIN_BLOCKS) fwd_sweep_kernel(Fwd
                         const I n = n0 + node_local(pk, sa, sb, sc);
                         F *p = tau + (n * (I)B + (I)b);
                         const Vec4<F> *pc = t0c + n * src_n;
-                        F v0[7], v1[7], rv = 0;
-                        Vec4<F> c0, c1;
-                        if (act0) {
-                            v0[0] = p[0];
-                            v0[1] = p[sr];
-                            v0[2] = *(p - sr);
-                            v0[3] = p[st];
-                            v0[4] = *(p - st);
-                            v0[5] = p[sp];
-                            v0[6] = *(p - sp);
-                            c0 = ld_stream(pc);
-                        }
-                        if (act1) {
-                            v1[0] = p[32];
-                            v1[1] = p[sr + 32];
-                            v1[2] = *(p - sr + 32);
-                            v1[3] = p[st + 32];
-                            v1[4] = *(p - st + 32);
-                            v1[5] = p[sp + 32];
-                            v1[6] = *(p - sp + 32);
-                            c1 = ld_stream(pc + 32);
+                        F v[NS][7], rv = 0;
+                        Vec4<F> c[NS];
+#pragma unroll
+                        for (int h = 0; h < NS; ++h) {
+                            if (!act[h]) continue;
+                            const F *ph = p + 32 * h;
+                            v[h][0] = ph[0];
+                            v[h][1] = ph[sr];
+                            v[h][2] = *(ph - sr);
+                            v[h][3] = ph[st];
+                            v[h][4] = *(ph - st);
+                            v[h][5] = ph[sp];
+                            v[h][6] = *(ph - sp);
+                            c[h] = ld_stream(pc + 32 * h);
                         }
                         if (lane < 8) rv = __ldg(recf + n * (I)8 + (I)lane);
                         const NodeRec<F> R = rec_from_lanes<F>(rv);  // uniform loop: whole warp
-                        if (act0) err0 = fmax_(err0, update_one<F>(p, v0, c0, R, a.er));
-                        if (act1) err1 = fmax_(err1, update_one<F>(p + 32, v1, c1, R, a.er));
+#pragma unroll
+                        for (int h = 0; h < NS; ++h)
+                            if (act[h])
+                                err[h] = fmax_(err[h], update_one<F>(p + 32 * h, v[h], c[h], R, a.er));
                         pk = pkn;
                     }
                 }
@@ -307,8 +311,9 @@ __global__ void __launch_bounds__(256, TTGB_FWD_MIN_BLOCKS) fwd_sweep_kernel(Fwd
                 qe = qe_next;
             }
             for (int axis = 0; axis < 3; ++axis) {
-                if (act0) extrapolate<F>(a, b, axis, slot, slots);
-                if (act1) extrapolate<F>(a, b + 32, axis, slot, slots);
+#pragma unroll
+                for (int h = 0; h < NS; ++h)
+                    if (act[h]) extrapolate<F>(a, b + 32 * h, axis, slot, slots);
                 if (!grid_barrier(bar, a.spin_ns, nblk)) return;
             }
         }
@@ -316,8 +321,9 @@ __global__ void __launch_bounds__(256, TTGB_FWD_MIN_BLOCKS) fwd_sweep_kernel(Fwd
         // maximum over the group's blocks by its first block, which also decides convergence.
         for (int x = threadIdx.x; x < Bg; x += blockDim.x) s_err[x] = 0;
         __syncthreads();
-        if (act0) atomic_max_nonneg(&s_err[b - src0], err0);
-        if (act1) atomic_max_nonneg(&s_err[b + 32 - src0], err1);
+#pragma unroll
+        for (int h = 0; h < NS; ++h)
+            if (act[h]) atomic_max_nonneg(&s_err[b + 32 * h - src0], err[h]);
         __syncthreads();
         for (int x = threadIdx.x; x < Bg; x += blockDim.x)
             a.partial[(long long)blockIdx.x * B + src0 + x] = s_err[x];
