@@ -329,31 +329,30 @@ __global__ void kernel_accum_kernel(GridC g, int B, const F *s, const F *T, cons
     const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    const double idt = 1.0 / g.dt, idp = 1.0 / g.dp;
+    // Each source's term in the fields' precision F (its inputs are F values; reciprocals
+    // instead of divisions), the sum over sources in FP64 in a fixed order.
+    const F idt = (F)(1.0 / g.dt), idp = (F)(1.0 / g.dp);
     for (long long n = warp; n < g.N; n += nwarps) {
         int k = (int)(n % g.np);
         long long t = n / g.np;
         int j = (int)(t % g.nt);
         int i = (int)(t / g.nt);
-        const double ht = h2[i], hp = h2[i] * cost[j];
+        const F iht = (F)(1.0 / h2[i]), ihp = (F)(1.0 / (h2[i] * cost[j]));
+        const F ct = iht * (j == 0 || j == g.nt - 1 ? idt : (F)0.5 * idt);
+        const F cp = ihp * (k == 0 || k == g.np - 1 ? idp : (F)0.5 * idp);
         const long long st = (long long)g.np * B, sp = B;
+        const long long ot_hi = j < g.nt - 1 ? st : 0, ot_lo = j > 0 ? st : 0;
+        const long long op_hi = k < g.np - 1 ? sp : 0, op_lo = k > 0 ? sp : 0;
         double aP = 0, aX = 0, aE = 0;
         for (int b = lane; b < B; b += 32) {
             const long long x = n * B + b;
-            const double Tc = (double)T[x];
-            double gt, gp;
-            if (j == 0) gt = ((double)T[x + st] - Tc) * idt;
-            else if (j == g.nt - 1) gt = (Tc - (double)T[x - st]) * idt;
-            else gt = ((double)T[x + st] - (double)T[x - st]) * 0.5 * idt;
-            if (k == 0) gp = ((double)T[x + sp] - Tc) * idp;
-            else if (k == g.np - 1) gp = (Tc - (double)T[x - sp]) * idp;
-            else gp = ((double)T[x + sp] - (double)T[x - sp]) * 0.5 * idp;
-            gt /= ht;
-            gp /= hp;
-            const double p = (double)P[x];
-            aP += p;
-            aX += p * (gt * gt - gp * gp);
-            aE += -2.0 * p * gt * gp;
+            // central differences inside, one-sided on the faces (R10)
+            const F gt = (T[x + ot_hi] - T[x - ot_lo]) * ct;
+            const F gp = (T[x + op_hi] - T[x - op_lo]) * cp;
+            const F p = P[x];
+            aP += (double)p;
+            aX += (double)(p * (gt * gt - gp * gp));
+            aE += (double)((F)-2 * p * gt * gp);
         }
         for (int o = 16; o > 0; o >>= 1) {
             aP += __shfl_xor_sync(0xffffffffu, aP, o);
