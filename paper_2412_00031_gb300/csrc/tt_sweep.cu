@@ -93,6 +93,61 @@ __device__ __forceinline__ void extrapolate(const FwdArgs<F> &a, int b, int axis
     }
 }
 
+// The same extrapolation for all NS sources of a lane (b + 32 h, those with act[h]): the
+// loads of all of them are issued before the stores (K face nodes at a time; more than one
+// costs the sweep kernel registers). Within one axis the
+// written layer (0 or n - 1) is never a layer read (1, 2 or n - 2, n - 3; n >= 4), so the
+// order of the face nodes does not matter and the bits equal extrapolate()'s.
+template <typename F, int NS>
+__device__ __forceinline__ void extrapolate_lane(const FwdArgs<F> &a, int b, const bool (&act)[NS],
+                                                 int axis, int slot, int slots) {
+    constexpr int K = 1;
+    const GridC &g = a.g;
+    const long long B = a.B;
+    int n1, n2, nface;
+    long long stride;
+    if (axis == 0) { n1 = g.nt; n2 = g.np; nface = g.nr; stride = (long long)g.nt * g.np; }
+    else if (axis == 1) { n1 = g.nr; n2 = g.np; nface = g.nt; stride = g.np; }
+    else { n1 = g.nr; n2 = g.nt; nface = g.np; stride = 1; }
+    const long long sB = stride * B;   // one layer inwards from the low face
+    const int per_face = n1 * n2;
+    for (int q0 = slot; q0 < 2 * per_face; q0 += K * slots) {
+        long long x0[K];
+        int ii[K], jj[K], kk[K];
+        bool okq[K], hiq[K];
+        F t1[K][NS], t2[K][NS];
+#pragma unroll
+        for (int u = 0; u < K; ++u) {
+            const int q = q0 + u * slots;
+            okq[u] = q < 2 * per_face;
+            hiq[u] = q >= per_face;
+            const int rem = okq[u] ? (hiq[u] ? q - per_face : q) : 0;
+            const int uu = rem / n2, vv = rem - uu * n2;
+            const int f0 = hiq[u] ? nface - 1 : 0;
+            if (axis == 0) { ii[u] = f0; jj[u] = uu; kk[u] = vv; }
+            else if (axis == 1) { ii[u] = uu; jj[u] = f0; kk[u] = vv; }
+            else { ii[u] = uu; jj[u] = vv; kk[u] = f0; }
+            x0[u] = node_index(g, ii[u], jj[u], kk[u]) * B + b;
+            const long long d = hiq[u] ? -sB : sB;
+#pragma unroll
+            for (int h = 0; h < NS; ++h)
+                if (okq[u] && act[h]) {
+                    t1[u][h] = a.tau[x0[u] + d + 32 * h];
+                    t2[u][h] = a.tau[x0[u] + 2 * d + 32 * h];
+                }
+        }
+#pragma unroll
+        for (int u = 0; u < K; ++u)
+#pragma unroll
+            for (int h = 0; h < NS; ++h) {
+                if (!(okq[u] && act[h])) continue;
+                const SrcC &sc = a.src[b + 32 * h];
+                if (!in_fixed_set(sc.ci, sc.cj, sc.ck, ii[u], jj[u], kk[u]))
+                    a.tau[x0[u] + 32 * h] = fmax_((F)2 * t1[u][h] - t2[u][h], t2[u][h]);
+            }
+    }
+}
+
 // Retire-and-refill: for every slot x of a group whose fill flag is set, copy the
 // retiring source's column of tau to the output and load the new source into the slot:
 // tau = 1 (or the caller's tau), the fixed set tau = 1, and its factor cache column,
@@ -311,9 +366,7 @@ __global__ void __launch_bounds__(256, TTGB_FWD_MIN_BLOCKS) fwd_sweep_kernel(Fwd
                 qe = qe_next;
             }
             for (int axis = 0; axis < 3; ++axis) {
-#pragma unroll
-                for (int h = 0; h < NS; ++h)
-                    if (act[h]) extrapolate<F>(a, b + 32 * h, axis, slot, slots);
+                if (any) extrapolate_lane<F, NS>(a, b, act, axis, slot, slots);
                 if (!grid_barrier(bar, a.spin_ns, nblk)) return;
             }
         }
