@@ -237,7 +237,7 @@ def gpu_arm(args, rank, world):
     import torch
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
-    w = I.anisotropic_batch(seed=I.SEED_BASE + 2 + rank, n_src=args.n_src)
+    w = I.anisotropic_batch(seed=rank_seed(rank), n_src=args.n_src)
     gp = GpuPath(w, dev)
     gp.opts.sweep_schedule = args.schedule
     gp.opts.adj_chunk = args.adj_chunk
@@ -519,12 +519,18 @@ def reference_arm(args):
 
 # ----------------------------------------------------------------------------- distributed
 
+# One process per GPU. Sources are independent, so each rank solves its own batch (seeded by
+# its rank) and nothing crosses ranks on the data path; the only collectives are the
+# barriers around the timed region and the max of the per-rank times (weak scaling).
+
 def dist_init():
+    """Joins the process group under torchrun (NCCL with GPUs, gloo without)."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if world > 1:
+        import torch
         import torch.distributed as dist
-        dist.init_process_group("nccl")
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     return rank, world
 
 
@@ -535,13 +541,20 @@ def dist_barrier(world):
 
 
 def dist_max(x, world):
+    """The maximum of x over the ranks (every rank gets it)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def rank_seed(rank):
+    """Seed of a rank's batch: every rank solves different sources of the same workload."""
+    return I.SEED_BASE + 2 + rank
 
 
 def main():
