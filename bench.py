@@ -433,8 +433,8 @@ def warm_leg(args, gp, world):
             "iters_fwd_mean": float(itf.mean()), "iters_fwd_max": int(itf.max()),
             "inference_ms": float(np.mean([s["warm_ms"] for s in fwd])),
             "sweep_ms": float(np.mean([s["sweep_ms"] for s in fwd])),
-            "inference": "3x3x3 convolutions: layers 2-3 on the tensor cores (mma.sync, BF16 "
-                         "operands, FP32 accumulation), layers 1 and 4 on the CUDA cores",
+            "inference": "3x3x3 convolutions, all four layers on the tensor cores (tcgen05, BF16 "
+                         "operands, FP32 accumulation in tensor memory)",
             "weights": "%s: trained on %d forward solves on %s random-field models, held-out "
                        "sweeps %.1f -> %.1f" % (os.path.basename(args.warm_start),
                                                 meta["solves_train"], "x".join(map(str, meta["grid"])),

@@ -254,9 +254,10 @@ tt_status tt_net_adam(tt_ctx *ctx, float *d_theta, const float *d_grad, float *d
  * the context; inference accumulates in FP32). Needed before opts.init = 2. */
 tt_status tt_net_set_weights(tt_ctx *ctx, const float *d_theta);
 /* The warm start's inference with the stored weights: d_y (device [n_grids][N] float) =
- * network output for d_x. Layers 2 and 3 run on the tensor cores (BF16 operands, FP32
- * accumulation), layers 1 and 4 on the CUDA cores; activations between layers are BF16.
- * Agrees with tt_net_forward to BF16 accuracy. */
+ * network output for d_x (device [n_grids][N][6] float, as tt_net_features writes it). All
+ * four layers run on the tensor cores (tcgen05, BF16 operands: the features are rounded
+ * to BF16; FP32 accumulation); activations between layers are BF16. Agrees with
+ * tt_net_forward to BF16 accuracy. TT_ETIMEOUT if a device-side wait exceeds 2 s. */
 tt_status tt_net_infer(tt_ctx *ctx, const float *d_x, int n_grids, float *d_y);
 
 /* A plan: one whole step over one batch (forward, misfit and adjoint sources, adjoint,

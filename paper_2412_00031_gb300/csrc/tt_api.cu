@@ -45,7 +45,7 @@ struct tt_ctx {
     DevBuf cq, wq, sidx, next, heads, nheads, JS, coef, t0c;
     // warm-start network: inference weights (BF16-rounded) and its workspace
     DevBuf net_theta, net_x, net_a, net_b, net_y, net_d1, net_d2, net_dy, net_wt, net_part,
-        net_scr, net_wbf;  // net_wbf: BF16 weights of layers 2 and 3, [tap][co][ci]
+        net_scr, net_wbf;  // net_wbf: BF16 weight images of the four layers (tensor cores)
     bool has_net = false;
     double *h_loss = nullptr;  // pinned
     // autotuner: scratch tau and the choices made, per (n_src, dtype)
@@ -356,10 +356,13 @@ template <typename F> struct Work {
     int net_chunk = 0;
 };
 
+// Rows of one grid in the padded row layout of the tensor-core inference.
+size_t net_grid_rows(const GridC &g) { return net_rows(ConvDims{1, g.nr, g.nt, g.np}); }
+
 // Sources per warm-start inference pass: two BF16 activation buffers of at most ~8 GB
 // together.
 int net_chunk(const GridC &g, int B) {
-    const size_t per_src = (size_t)g.N * kNetHidden * sizeof(__nv_bfloat16);
+    const size_t per_src = net_grid_rows(g) * kNetHidden * sizeof(__nv_bfloat16);
     long long c = (long long)((4ull << 30) / per_src);
     if (c < 1) c = 1;
     if (c > 16) c = 16;
@@ -457,8 +460,8 @@ template <typename F> tt_status net_work_from_ctx(tt_ctx *ctx, Work<F> &W, int B
     const GridC &g = ctx->g;
     const int c = net_chunk(g, B);
     ENSURE(ctx->net_x, sizeof(float) * kNetFeatures * (size_t)g.N * c);
-    ENSURE(ctx->net_a, sizeof(__nv_bfloat16) * kNetHidden * (size_t)g.N * c);
-    ENSURE(ctx->net_b, sizeof(__nv_bfloat16) * kNetHidden * (size_t)g.N * c);
+    ENSURE(ctx->net_a, sizeof(__nv_bfloat16) * kNetHidden * net_grid_rows(g) * c);
+    ENSURE(ctx->net_b, sizeof(__nv_bfloat16) * kNetHidden * net_grid_rows(g) * c);
     ENSURE(ctx->net_y, sizeof(float) * (size_t)g.N * c);
     W.net_x = (float *)ctx->net_x.p;
     W.net_a = (__nv_bfloat16 *)ctx->net_a.p;
@@ -529,9 +532,11 @@ tt_status enq_net_forward(tt_ctx *ctx, const float *theta, const float *x, const
     return TT_OK;
 }
 
-// tau = 1 + clamp(net(features), -0.5, 1) for every source, in chunks of W.net_chunk.
+// tau = 1 + clamp(net(features), -0.5, 1) for every source, in chunks of W.net_chunk. A
+// device-side wait of the tensor-core kernels that exceeds spin sets flags[3].
 template <typename F>
-tt_status enq_warm_start(tt_ctx *ctx, Work<F> &W, const tt_model *m, int B, F *tau) {
+tt_status enq_warm_start(tt_ctx *ctx, Work<F> &W, const tt_model *m, int B, F *tau,
+                         unsigned long long spin) {
     const GridC &g = ctx->g;
     const GeoTab<F> &t = geo<F>(ctx);
     tt_status s;
@@ -541,10 +546,10 @@ tt_status enq_warm_start(tt_ctx *ctx, Work<F> &W, const tt_model *m, int B, F *t
                                (const F *)m->d_s, (const F *)m->d_xi, (const F *)m->d_eta,
                                W.net_x, ctx->st));
         const ConvDims d{nb, g.nr, g.nt, g.np};
-        CK(run_net_infer(d, W.net_theta, W.net_wbf, W.net_wbf + 27 * 32 * 32, W.net_x,
-                         W.net_a, W.net_b, W.net_y, ctx->n_sm, ctx->st));
+        CK(run_net_infer(d, W.net_theta, W.net_wbf, W.net_x, W.net_a, W.net_b, W.net_y,
+                         ctx->n_sm, W.flags + 3, spin, ctx->st));
         CK(run_warm_tau<F>(g.N, B, b0, nb, W.net_y, tau, ctx->st));
-        ctx->launches += 6;
+        ctx->launches += 3 + kNetLayers;
     }
     return TT_OK;
 }
@@ -563,7 +568,8 @@ tt_status enq_forward(tt_ctx *ctx, Work<F> &W, const tt_model *m, int B, void *d
                            W.flags, ctx->st));
     if (o->init == 2) {
         CK(record(ctx, ctx->ev_net[0]));
-        if ((s = enq_warm_start<F>(ctx, W, m, B, (F *)d_tau)) != TT_OK) return s;
+        CK(cudaMemsetAsync(W.flags + 3, 0, sizeof(int), ctx->st));
+        if ((s = enq_warm_start<F>(ctx, W, m, B, (F *)d_tau, spin_ns(o))) != TT_OK) return s;
         CK(record(ctx, ctx->ev_net[1]));
     }
     CK(run_tau_init<F>(g, B, W.src, (F *)d_tau, o->init == 0, ctx->st));
@@ -950,6 +956,9 @@ tt_status solve_status(tt_ctx *ctx, int B, const PointD *src, int *h_iters, int 
     const int *hc = which == TT_STATS_FORWARD ? r.conv_f : r.conv_a;
     if (which == TT_STATS_FORWARD && r.flags[0])
         return fail(ctx, TT_EINVAL, "%s: model has s <= 0 or xi^2 + eta^2 >= 1/4", what);
+    if (which == TT_STATS_FORWARD && ctx->warm_last && r.flags[3])
+        return fail(ctx, TT_ETIMEOUT, "%s: a device-side wait of the warm start exceeded its limit",
+                    what);
     for (int q = 0; q < kMaxBarrierGroups; ++q) {
         int st;
         const unsigned char *bar = which == TT_STATS_FORWARD ? r.bar_f : r.bar_a;
@@ -1343,13 +1352,12 @@ tt_status tt_net_set_weights(tt_ctx *ctx, const float *d_theta) {
     if (!d_theta) return fail(ctx, TT_EINVAL, "tt_net_set_weights: NULL weights");
     const int P = net_param_count();
     ENSURE(ctx->net_theta, sizeof(float) * P);
-    ENSURE(ctx->net_wbf, sizeof(__nv_bfloat16) * 2 * 27 * 32 * 32);
+    ENSURE(ctx->net_wbf, sizeof(__nv_bfloat16) * net_weight_image_elems());
     CK(run_round_bf16(P, d_theta, (float *)ctx->net_theta.p, ctx->st));
-    __nv_bfloat16 *wbf = (__nv_bfloat16 *)ctx->net_wbf.p;
-    CK(run_mma_weights(d_theta + net_weight_offset(1), wbf, ctx->st));
-    CK(run_mma_weights(d_theta + net_weight_offset(2), wbf + 27 * 32 * 32, ctx->st));
+    CK(run_net_weight_images((const float *)ctx->net_theta.p, (__nv_bfloat16 *)ctx->net_wbf.p,
+                             ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
-    ctx->launches += 3;
+    ctx->launches += 1 + kNetLayers;
     ctx->has_net = true;
     return TT_OK;
 }
@@ -1360,15 +1368,20 @@ tt_status tt_net_infer(tt_ctx *ctx, const float *d_x, int n_grids, float *d_y) {
         return fail(ctx, TT_EINVAL, "tt_net_infer: NULL buffer or n_grids < 1");
     if (!ctx->has_net) return fail(ctx, TT_EINVAL, "tt_net_infer: no weights (tt_net_set_weights)");
     const GridC &g = ctx->g;
-    const size_t M = (size_t)g.N * n_grids;
+    const size_t M = net_grid_rows(g) * n_grids;
     ENSURE(ctx->net_a, sizeof(__nv_bfloat16) * kNetHidden * M);
     ENSURE(ctx->net_b, sizeof(__nv_bfloat16) * kNetHidden * M);
-    const __nv_bfloat16 *wbf = (const __nv_bfloat16 *)ctx->net_wbf.p;
-    CK(run_net_infer(ConvDims{n_grids, g.nr, g.nt, g.np}, (const float *)ctx->net_theta.p, wbf,
-                     wbf + 27 * 32 * 32, d_x, (__nv_bfloat16 *)ctx->net_a.p,
-                     (__nv_bfloat16 *)ctx->net_b.p, d_y, ctx->n_sm, ctx->st));
-    ctx->launches += 4;
+    ENSURE(ctx->flags, 4 * sizeof(int));
+    int *err = (int *)ctx->flags.p + 3;
+    CK(cudaMemsetAsync(err, 0, sizeof(int), ctx->st));
+    CK(run_net_infer(ConvDims{n_grids, g.nr, g.nt, g.np}, (const float *)ctx->net_theta.p,
+                     (const __nv_bfloat16 *)ctx->net_wbf.p, d_x, (__nv_bfloat16 *)ctx->net_a.p,
+                     (__nv_bfloat16 *)ctx->net_b.p, d_y, ctx->n_sm, err, kDefaultSpinNs, ctx->st));
+    ctx->launches += 1 + kNetLayers;
+    int h_err = 0;
+    CK(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
+    if (h_err) return fail(ctx, TT_ETIMEOUT, "tt_net_infer: a device-side wait exceeded its limit");
     return TT_OK;
 }
 
@@ -1543,8 +1556,8 @@ template <typename F> tt_status plan_alloc(tt_plan *p, Work<F> &W) {
     if (p->opts.init == 2) {
         W.net_chunk = net_chunk(g, B);
         TTGB_GET(net_x, sizeof(float) * kNetFeatures * (size_t)g.N * W.net_chunk);
-        TTGB_GET(net_a, sizeof(__nv_bfloat16) * kNetHidden * (size_t)g.N * W.net_chunk);
-        TTGB_GET(net_b, sizeof(__nv_bfloat16) * kNetHidden * (size_t)g.N * W.net_chunk);
+        TTGB_GET(net_a, sizeof(__nv_bfloat16) * kNetHidden * net_grid_rows(g) * W.net_chunk);
+        TTGB_GET(net_b, sizeof(__nv_bfloat16) * kNetHidden * net_grid_rows(g) * W.net_chunk);
         TTGB_GET(net_y, sizeof(float) * (size_t)g.N * W.net_chunk);
         W.net_theta = (const float *)ctx->net_theta.p;
         W.net_wbf = (const __nv_bfloat16 *)ctx->net_wbf.p;

@@ -93,129 +93,6 @@ __global__ void __launch_bounds__(kConvThreads)
     }
 }
 
-// Tensor-core 3x3x3 convolution, 32 -> 32 channels, for inference: mma.sync m16n8k16 with
-// BF16 operands and FP32 accumulation. Implicit GEMM per 4x4x8 output tile: M = 128 nodes
-// (four warps of 32 rows), N = 32 output channels, K = 27 taps x 32 input channels. Input:
-// post-ReLU BF16 activations [grid][node][32]; output: ReLU(conv + bias) in BF16. A block
-// keeps the weights ([tap][co][ci], BF16) in shared memory for all the tiles it takes;
-// each tile's input with its one-node halo is staged in shared memory. Rows are padded to
-// 20 words, which makes every fragment load bank-conflict free.
-constexpr int kMmaRow = 20;                       // 32-bit words per staged row
-constexpr int kMmaSmemBytes = (27 * 32 + kHalo) * kMmaRow * 4;
-
-__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], uint32_t b0,
-                                         uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, "
-        "{%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-__global__ void __launch_bounds__(kConvThreads)
-    conv3d_mma_kernel(ConvDims d, const __nv_bfloat16 *__restrict__ in,
-                      const uint32_t *__restrict__ wt, const float *__restrict__ bias,
-                      __nv_bfloat16 *__restrict__ out) {
-    extern __shared__ __align__(16) uint32_t sm[];
-    uint32_t *s_w = sm;                      // [27 * 32 rows (tap, co)][kMmaRow]
-    uint32_t *s_in = sm + 27 * 32 * kMmaRow; // [kHalo rows][kMmaRow]
-    for (int e = threadIdx.x; e < 27 * 32 * 16; e += kConvThreads)
-        s_w[(e >> 4) * kMmaRow + (e & 15)] = wt[e];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, tg = lane & 3;
-    int hb[2][2];  // halo row of tap (0, 0, 0) for the thread's rows g and g + 8 of both m16 tiles
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int m = warp * 32 + mt * 16 + g + 8 * h;
-            hb[mt][h] = ((m / (kTX * kTY)) * kHY + (m / kTX) % kTY) * kHX + m % kTX;
-        }
-    float bz[4][2];
-#pragma unroll
-    for (int nt = 0; nt < 4; ++nt) {
-        bz[nt][0] = bias[nt * 8 + 2 * tg];
-        bz[nt][1] = bias[nt * 8 + 2 * tg + 1];
-    }
-    const int tiles_x = (d.W + kTX - 1) / kTX, tiles_y = (d.H + kTY - 1) / kTY;
-    const int tiles_z = (d.D + kTZ - 1) / kTZ;
-    const long long per_grid = (long long)tiles_x * tiles_y * tiles_z;
-    const long long total = per_grid * d.nb;
-    const size_t grid_nodes = (size_t)d.D * d.H * d.W;
-    for (long long T = blockIdx.x; T < total; T += gridDim.x) {
-        const int b = (int)(T / per_grid);
-        long long tile = T - (long long)b * per_grid;
-        const int x0 = (int)(tile % tiles_x) * kTX;
-        tile /= tiles_x;
-        const int y0 = (int)(tile % tiles_y) * kTY;
-        const int z0 = (int)(tile / tiles_y) * kTZ;
-        const uint4 *inb = reinterpret_cast<const uint4 *>(in + (size_t)b * grid_nodes * 32);
-        __syncthreads();  // the previous tile's fragments have been read
-        for (int e = threadIdx.x; e < kHalo * 4; e += kConvThreads) {
-            const int node = e >> 2, q = e & 3;
-            const int hx = node % kHX, hy = (node / kHX) % kHY, hz = node / (kHX * kHY);
-            const int z = z0 + hz - 1, y = y0 + hy - 1, x = x0 + hx - 1;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (z >= 0 && z < d.D && y >= 0 && y < d.H && x >= 0 && x < d.W)
-                v = inb[(((size_t)z * d.H + y) * d.W + x) * 4 + q];
-            *reinterpret_cast<uint4 *>(s_in + node * kMmaRow + q * 4) = v;
-        }
-        __syncthreads();
-        float acc[2][4][4];
-#pragma unroll
-        for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-            for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-                for (int q = 0; q < 4; ++q) acc[mt][nt][q] = 0.0f;
-        for (int t = 0; t < 27; ++t) {
-            const int toff = (t / 9) * (kHY * kHX) + ((t / 3) % 3) * kHX + t % 3;
-#pragma unroll
-            for (int kc = 0; kc < 2; ++kc) {
-                uint32_t a[2][4];
-#pragma unroll
-                for (int mt = 0; mt < 2; ++mt) {
-                    const int r0 = (hb[mt][0] + toff) * kMmaRow + kc * 8 + tg;
-                    const int r1 = (hb[mt][1] + toff) * kMmaRow + kc * 8 + tg;
-                    a[mt][0] = s_in[r0];
-                    a[mt][1] = s_in[r1];
-                    a[mt][2] = s_in[r0 + 4];
-                    a[mt][3] = s_in[r1 + 4];
-                }
-#pragma unroll
-                for (int nt = 0; nt < 4; ++nt) {
-                    const int wb = (t * 32 + nt * 8 + g) * kMmaRow + kc * 8 + tg;
-                    const uint32_t b0 = s_w[wb], b1 = s_w[wb + 4];
-#pragma unroll
-                    for (int mt = 0; mt < 2; ++mt) mma_bf16(acc[mt][nt], a[mt], b0, b1);
-                }
-            }
-        }
-#pragma unroll
-        for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int m = warp * 32 + mt * 16 + g + 8 * h;
-                const int z = z0 + m / (kTX * kTY), y = y0 + (m / kTX) % kTY, x = x0 + m % kTX;
-                if (z >= d.D || y >= d.H || x >= d.W) continue;
-                __nv_bfloat16 *o = out + ((size_t)b * grid_nodes + ((size_t)z * d.H + y) * d.W + x) * 32;
-#pragma unroll
-                for (int nt = 0; nt < 4; ++nt) {
-                    const float v0 = fmaxf(acc[mt][nt][2 * h] + bz[nt][0], 0.0f);
-                    const float v1 = fmaxf(acc[mt][nt][2 * h + 1] + bz[nt][1], 0.0f);
-                    *reinterpret_cast<__nv_bfloat162 *>(o + nt * 8 + 2 * tg) = __floats2bfloat162_rn(v0, v1);
-                }
-            }
-    }
-}
-
-// w[27][32 ci][32 co] (FP32) -> wt[27][32 co][32 ci] (BF16) for conv3d_mma_kernel.
-__global__ void mma_weights_kernel(const float *__restrict__ w, __nv_bfloat16 *__restrict__ wt) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= 27 * 32 * 32) return;
-    const int t = e / 1024, r = e % 1024, ci = r / 32, co = r % 32;
-    wt[(t * 32 + co) * 32 + ci] = __float2bfloat16_rn(w[e]);
-}
-
 // Weight gradient, stage 1. Block (r, t): taps t < 27 accumulate
 // sum_p act(in[p + off(t)][ci]) dy[p][co] over the positions of chunks r, r + R, ...;
 // t = 27 accumulates sum_p dy[p][co] (the bias). Chunks are 128 consecutive positions.
@@ -435,43 +312,6 @@ cudaError_t run_conv3d(const ConvDims &d, int cin, int cout, const float *in, bo
         conv3d_kernel<1><<<grid, kConvThreads, 0, st>>>(d, cin, in, relu_in, w, bias, gate, out);
     else
         return cudaErrorInvalidValue;
-    return cudaGetLastError();
-}
-
-cudaError_t run_net_infer(const ConvDims &d, const float *theta, const __nv_bfloat16 *wt2,
-                          const __nv_bfloat16 *wt3, const float *x, __nv_bfloat16 *a,
-                          __nv_bfloat16 *b, float *y, int n_sm, cudaStream_t st) {
-    static_assert(kNetHidden == 32, "the tensor-core layers are 32 -> 32");
-    const int tiles = ((d.W + kTX - 1) / kTX) * ((d.H + kTY - 1) / kTY) * ((d.D + kTZ - 1) / kTZ);
-    const float *w1 = theta + net_weight_offset(0), *w4 = theta + net_weight_offset(3);
-    // layer 1 (6 -> 32) on the CUDA cores, BF16 ReLU output
-    conv3d_kernel<32, float, true><<<dim3(tiles, d.nb), kConvThreads, 0, st>>>(
-        d, 6, x, 0, w1, w1 + 27 * 6 * 32, nullptr, a);
-    // layers 2 and 3 (32 -> 32) on the tensor cores
-    cudaError_t e = cudaFuncSetAttribute(conv3d_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kMmaSmemBytes);
-    if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, conv3d_mma_kernel, kConvThreads,
-                                                      kMmaSmemBytes);
-    if (e != cudaSuccess) return e;
-    const long long total = (long long)tiles * d.nb;
-    long long blocks = (long long)(per_sm > 0 ? per_sm : 1) * n_sm;
-    if (blocks > total) blocks = total;
-    const float *b2 = theta + net_weight_offset(1) + 27 * 32 * 32;
-    const float *b3 = theta + net_weight_offset(2) + 27 * 32 * 32;
-    conv3d_mma_kernel<<<(unsigned)blocks, kConvThreads, kMmaSmemBytes, st>>>(
-        d, a, reinterpret_cast<const uint32_t *>(wt2), b2, b);
-    conv3d_mma_kernel<<<(unsigned)blocks, kConvThreads, kMmaSmemBytes, st>>>(
-        d, b, reinterpret_cast<const uint32_t *>(wt3), b3, a);
-    // layer 4 (32 -> 1) on the CUDA cores from the BF16 activations
-    conv3d_kernel<1, __nv_bfloat16, false><<<dim3(tiles, d.nb), kConvThreads, 0, st>>>(
-        d, 32, a, 0, w4, w4 + 27 * 32, nullptr, y);
-    return cudaGetLastError();
-}
-
-cudaError_t run_mma_weights(const float *w, __nv_bfloat16 *wt, cudaStream_t st) {
-    mma_weights_kernel<<<blocks_of(27 * 32 * 32, 256), 256, 0, st>>>(w, wt);
     return cudaGetLastError();
 }
 

@@ -64,14 +64,18 @@ cudaError_t run_net_features(const GridC &g, int B, int b0, int nb, const SrcC *
 template <typename F>
 cudaError_t run_warm_tau(long long N, int B, int b0, int nb, const float *y, F *tau,
                          cudaStream_t st);
-// Inference (warm start): layer 1 and layer 4 on the CUDA cores, layers 2 and 3 on the
-// tensor cores (mma.sync, BF16 operands, FP32 accumulation); activations a, b are BF16
-// [nb][node][32]; theta holds the FP32 (BF16-rounded) parameters, wt2 / wt3 the BF16
-// weights of layers 2 and 3 transposed to [tap][co][ci] (run_mma_weights).
-cudaError_t run_net_infer(const ConvDims &d, const float *theta, const __nv_bfloat16 *wt2,
-                          const __nv_bfloat16 *wt3, const float *x, __nv_bfloat16 *a,
-                          __nv_bfloat16 *b, float *y, int n_sm, cudaStream_t st);
-cudaError_t run_mma_weights(const float *w, __nv_bfloat16 *wt, cudaStream_t st);
+// Inference (warm start, tt_umma.cu): the four convolutions on the tensor cores (tcgen05,
+// BF16 operands, FP32 accumulation in tensor memory) over the padded row layout of the
+// activations: features x [nb][node][6] (FP32) are packed into b, the layers run
+// b -> a -> b -> a -> y, y [nb][node] FP32. a and b hold net_rows(d) rows of 32 BF16 per
+// grid. theta: the FP32 (BF16-rounded) parameters (biases); img: the weight images of
+// run_net_weight_images. A device-side wait that exceeds limit_ns sets *err = 1.
+size_t net_rows(const ConvDims &d);
+size_t net_weight_image_elems();
+cudaError_t run_net_weight_images(const float *theta, __nv_bfloat16 *img, cudaStream_t st);
+cudaError_t run_net_infer(const ConvDims &d, const float *theta, const __nv_bfloat16 *img,
+                          const float *x, __nv_bfloat16 *a, __nv_bfloat16 *b, float *y, int n_sm,
+                          int *err, unsigned long long limit_ns, cudaStream_t st);
 // Rounds every value to the nearest BF16 (kept in FP32 storage).
 cudaError_t run_round_bf16(int n, const float *in, float *out, cudaStream_t st);
 

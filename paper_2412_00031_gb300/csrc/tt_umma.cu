@@ -1,0 +1,617 @@
+// Warm-start inference on the 5th-generation tensor cores: the four 3x3x3 convolutions of
+// the network (tt_net.h) as implicit GEMMs issued with tcgen05.mma (BF16 operands, FP32
+// accumulators in tensor memory), operands staged by TMA tensor copies.
+//
+// Row layout of the activations. The nodes of one grid are rows
+//   r = (i (n_t + 1) + j) (n_p + 1) + k,   i < n_r, j <= n_t, k <= n_p,   r < R = n_r Si,
+// of C BF16 channels (C = 16 for the input features, padded from 6; 32 for the hidden
+// layers), the rows j = n_t and k = n_p being zero. A tap (di, dj, dk) of the convolution at
+// row r reads row r + (di - 1) Si + (dj - 1) Sj + (dk - 1), with Sj = n_p + 1 and
+// Si = (n_t + 1) Sj: every tap is a fixed row shift, the zero rows give the zero padding at
+// the theta and phi faces, and rows outside [0, R) (the radial faces) are zero-filled by the
+// tensor copy. Buffer [grid][R][C].
+//
+// GEMM of one tile: M = 128 consecutive rows r0 + m, K = 9 (di, dj) x C, and N = 3 x output
+// channels: the three dk taps' weights side by side, so that the accumulator holds, for each
+// dk, D_dk[m] = sum over (di, dj) of x[r0 + m + (di-1) Si + (dj-1) Sj - 1] W(di, dj, dk).
+// Output row r0 + m is D_0[m] + D_1[m + 1] + D_2[m + 2]: the epilogue combines neighbouring
+// TMEM lanes (warp shuffles, and a small shared-memory exchange across the four lane
+// quarters), so a tile of 128 accumulator rows yields 126 outputs and the tiles step by 126
+// rows. Every operand is thus an aligned block of whole rows, which lets both the A slabs
+// (one TMA tensor copy of 128 rows per (di, dj)) and the weights use the swizzled K-major
+// layout (64-byte swizzle for rows of 32 channels, 32-byte for 16): consecutive rows' 16-byte
+// chunks fall in different shared-memory banks.
+//
+// Roles (320 threads, one persistent CTA per SM): warp 0 issues the tensor copies into a
+// ring of slab stages; warp 1 allocates tensor memory and issues the MMAs (one elected
+// thread), committing each stage back to the copier and each finished tile to the
+// epilogue; two epilogue warpgroups (warps 2-5 and 6-9) take alternate tiles, each with its
+// own accumulator buffer: they read the accumulators (tcgen05.ld, one TMEM lane quarter per
+// warp), add the bias, apply ReLU and store BF16 rows (or, in the last layer, the FP32
+// output of the real nodes). The epilogue is the longest role per tile, so two tiles of it
+// run at once while the MMAs of a third proceed. Every wait is bounded: on expiry the CTA raises its abort flag and the error word,
+// drains its copies and MMAs in flight, frees its tensor memory and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "tt_net.h"
+
+namespace ttgb {
+
+namespace {
+
+constexpr int kTileRows = 128;                 // M
+constexpr int kTileStep = kTileRows - 2;       // output rows of one tile
+#ifndef TTGB_TC_STAGES
+#define TTGB_TC_STAGES 16
+#endif
+constexpr int kStages = TTGB_TC_STAGES;
+#ifndef TTGB_TC_SLAB_FENCE
+#define TTGB_TC_SLAB_FENCE 0
+#endif
+constexpr int kThreads = 320;                  // copier, MMA, two epilogue warpgroups
+// Two accumulator buffers of up to 3 x 32 columns.
+constexpr int kBufCols = 128;
+constexpr int kTmemCols = 256;
+
+// KC: 8-channel chunks of an input row (2: C = 16, 4: C = 32); NO: output channels per dk
+// (32, or 16 for the last layer).
+template <int KC, int NO> struct Smem {
+    static constexpr int ROW = KC * 16;                          // bytes of one row
+    static constexpr int QW = 3 * NO * ROW;                      // weights of one (di, dj)
+    static constexpr int W = 9 * QW;                             // [q][dk][co] rows, swizzled
+    static constexpr int SLAB = kTileRows * ROW;
+    static constexpr int A = (W + 1023) / 1024 * 1024;
+    static constexpr int EXCH = A + kStages * SLAB;              // [2][4 quarters][2][2][32] float
+    static constexpr int BAR = EXCH + 2 * 4 * 2 * 2 * 32 * 4;    // mbarriers
+    static constexpr int NBAR = 2 * kStages + 5;                 // full, empty, acc x 4, drain
+    static constexpr int MISC = BAR + NBAR * 8;                  // tmem address, abort flag
+    static constexpr int TOTAL = MISC + 16 + 1024;               // + alignment slack
+    // swizzle: 64 bytes for rows of 64 bytes, 32 for rows of 32 (descriptor layout code)
+    static constexpr unsigned LAYOUT = ROW == 64 ? 4u : 6u;
+    static constexpr unsigned SBO = 8 * ROW;                     // 8-row groups
+};
+static_assert(Smem<4, 32>::TOTAL <= 227 * 1024, "shared memory of one CTA");
+static_assert(Smem<4, 32>::QW % 1024 == 0 && Smem<2, 32>::QW % 256 == 0 &&
+                  Smem<4, 16>::QW % 512 == 0,
+              "every weight block starts on a swizzle atom");
+
+__device__ __forceinline__ unsigned saddr(const void *p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void bar_init(unsigned b, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(b), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void bar_expect_tx(unsigned b, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bar_arrive(unsigned b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(b) : "memory");
+}
+
+__device__ __forceinline__ bool bar_test(unsigned b, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(b), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the phase of the given parity. Returns false when the limit expired or
+// another role of the CTA has aborted (then the caller stops).
+__device__ __forceinline__ bool bar_wait(unsigned b, unsigned parity, unsigned long long limit,
+                                         volatile int *abort) {
+    unsigned long long t0 = 0;
+    for (int spin = 0;; ++spin) {
+        if (bar_test(b, parity)) return true;
+        if ((spin & 63) == 63) {
+            if (*abort) return false;
+            const unsigned long long t = global_ns();
+            if (t0 == 0) t0 = t;
+            else if (t - t0 > limit) {
+                *abort = 1;
+                return false;
+            }
+        }
+    }
+}
+
+// Bounded wait used while tearing down (ignores the abort flag).
+__device__ __forceinline__ void bar_drain(unsigned b, unsigned parity, unsigned long long limit) {
+    const unsigned long long t0 = global_ns();
+    while (!bar_test(b, parity) && global_ns() - t0 < limit) {
+    }
+}
+
+// 128 rows of one grid starting at row `row` (may be negative or past the end: zero fill).
+__device__ __forceinline__ void tma_rows(unsigned dst, const CUtensorMap *map, int row, int grid,
+                                         unsigned b) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(0), "r"(row), "r"(grid), "r"(b)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor, K-major with swizzle `layout` (4: 64 B, 6: 32 B): rows of
+// the swizzle width, 8-row groups sbo bytes apart; the leading offset is unused (encoded 1).
+__device__ __forceinline__ unsigned long long mdesc(unsigned addr, unsigned sbo, unsigned layout) {
+    return (unsigned long long)((addr >> 4) & 0x3FFFu) | (1ull << 16) |
+           ((unsigned long long)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46) |
+           ((unsigned long long)layout << 61);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both K-major, N x M.
+template <int N> __host__ __device__ constexpr unsigned idesc_bf16() {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(N >> 3) << 17) |
+           ((unsigned)(kTileRows >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(unsigned d, unsigned long long a, unsigned long long b,
+                                         unsigned id, unsigned acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(id), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(unsigned b) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(b)
+                 : "memory");
+}
+
+// 1 when c holds in every one of the 128 threads of epilogue group g (named barrier 1 + g).
+__device__ __forceinline__ bool epi_all(int g, bool c) {
+    unsigned r;
+    asm volatile(
+        "{\n .reg .pred pi, po;\n setp.ne.u32 pi, %2, 0;\n bar.red.and.pred po, %1, 128, pi;\n"
+        " selp.u32 %0, 1, 0, po;\n}\n"
+        : "=r"(r)
+        : "r"(1 + g), "r"((unsigned)c)
+        : "memory");
+    return r != 0;
+}
+
+__device__ __forceinline__ void epi_sync(int g) {
+    asm volatile("bar.sync %0, 128;" ::"r"(1 + g) : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Columns [taddr, +32), [+32, +64) and [+64, +96) of the thread's TMEM lane: three loads in
+// flight and one wait, in one statement (the registers are only defined after the wait).
+__device__ __forceinline__ void tmem_ld96(unsigned taddr, unsigned (&a)[32], unsigned (&b)[32],
+                                          unsigned (&c)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%96];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47, %48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63}, [%97];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%64, %65, %66, %67, %68, %69, %70, %71, %72, %73, %74, %75, %76, %77, %78, %79, %80, %81, %82, %83, %84, %85, %86, %87, %88, %89, %90, %91, %92, %93, %94, %95}, [%98];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3]), "=r"(a[4]), "=r"(a[5]), "=r"(a[6]), "=r"(a[7]),
+          "=r"(a[8]), "=r"(a[9]), "=r"(a[10]), "=r"(a[11]), "=r"(a[12]), "=r"(a[13]), "=r"(a[14]), "=r"(a[15]),
+          "=r"(a[16]), "=r"(a[17]), "=r"(a[18]), "=r"(a[19]), "=r"(a[20]), "=r"(a[21]), "=r"(a[22]), "=r"(a[23]),
+          "=r"(a[24]), "=r"(a[25]), "=r"(a[26]), "=r"(a[27]), "=r"(a[28]), "=r"(a[29]), "=r"(a[30]), "=r"(a[31]),
+          "=r"(b[0]), "=r"(b[1]), "=r"(b[2]), "=r"(b[3]), "=r"(b[4]), "=r"(b[5]), "=r"(b[6]), "=r"(b[7]),
+          "=r"(b[8]), "=r"(b[9]), "=r"(b[10]), "=r"(b[11]), "=r"(b[12]), "=r"(b[13]), "=r"(b[14]), "=r"(b[15]),
+          "=r"(b[16]), "=r"(b[17]), "=r"(b[18]), "=r"(b[19]), "=r"(b[20]), "=r"(b[21]), "=r"(b[22]), "=r"(b[23]),
+          "=r"(b[24]), "=r"(b[25]), "=r"(b[26]), "=r"(b[27]), "=r"(b[28]), "=r"(b[29]), "=r"(b[30]), "=r"(b[31]),
+          "=r"(c[0]), "=r"(c[1]), "=r"(c[2]), "=r"(c[3]), "=r"(c[4]), "=r"(c[5]), "=r"(c[6]), "=r"(c[7]),
+          "=r"(c[8]), "=r"(c[9]), "=r"(c[10]), "=r"(c[11]), "=r"(c[12]), "=r"(c[13]), "=r"(c[14]), "=r"(c[15]),
+          "=r"(c[16]), "=r"(c[17]), "=r"(c[18]), "=r"(c[19]), "=r"(c[20]), "=r"(c[21]), "=r"(c[22]), "=r"(c[23]),
+          "=r"(c[24]), "=r"(c[25]), "=r"(c[26]), "=r"(c[27]), "=r"(c[28]), "=r"(c[29]), "=r"(c[30]), "=r"(c[31])
+        : "r"(taddr), "r"(taddr + 32), "r"(taddr + 64)
+        : "memory");
+}
+
+__device__ __forceinline__ float tmem_ld1(unsigned taddr) {
+    unsigned r;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(taddr) : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    return __uint_as_float(r);
+}
+
+struct RowGeo {
+    int nb, nr, nt, np;
+    int Sj;             // n_p + 1
+    int Si;             // (n_t + 1) Sj
+    int R;              // rows of one grid: n_r Si
+    int tiles;          // ceil(R / 126) per grid
+};
+
+__device__ __forceinline__ bool pad_row(const RowGeo &G, int n) {
+    return n % G.Sj == G.np || (n / G.Sj) % (G.nt + 1) == G.nt;
+}
+
+// FINAL: write channel 0 + bias as FP32 y[grid][node] (real nodes), else ReLU(out + bias)
+// as BF16 rows of 32 channels (zero on the padding rows).
+template <int KC, int NO, bool FINAL>
+__global__ void __launch_bounds__(kThreads, 1)
+    conv3d_tc_kernel(const __grid_constant__ CUtensorMap map, RowGeo G,
+                     const uint4 *__restrict__ wimg, const float *__restrict__ bias,
+                     void *__restrict__ out_, int *err, unsigned long long limit) {
+    using L = Smem<KC, NO>;
+    extern __shared__ unsigned char smem_raw[];
+    const unsigned raw = saddr(smem_raw);
+    const unsigned base = (raw + 1023u) & ~1023u;
+    unsigned char *sm = smem_raw + (base - raw);
+    const unsigned sW = base, sA = base + L::A, sBar = base + L::BAR;
+    unsigned *s_tmem = reinterpret_cast<unsigned *>(sm + L::MISC);
+    volatile int *s_abort = reinterpret_cast<volatile int *>(sm + L::MISC + 4);
+    auto full = [&](int s) { return sBar + 8u * s; };
+    auto empty = [&](int s) { return sBar + 8u * (kStages + s); };
+    auto acc_full = [&](int a) { return sBar + 8u * (2 * kStages + a); };
+    auto acc_empty = [&](int a) { return sBar + 8u * (2 * kStages + 2 + a); };
+    const unsigned drain = sBar + 8u * (2 * kStages + 4);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // weights into shared memory (generic stores, made visible to the tensor cores below)
+    for (int e = threadIdx.x; e < L::W / 16; e += kThreads)
+        reinterpret_cast<uint4 *>(sm)[e] = wimg[e];
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            bar_init(full(s), 1);
+            bar_init(empty(s), 1);
+        }
+        bar_init(acc_full(0), 1);
+        bar_init(acc_full(1), 1);
+        bar_init(acc_empty(0), 128);
+        bar_init(acc_empty(1), 128);
+        bar_init(drain, 1);
+        *s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (warp == 1) {
+        __syncwarp();
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         saddr(s_tmem)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tmem = *s_tmem;
+    const long long total = (long long)G.nb * G.tiles;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // copier: the nine slabs of every tile of this CTA, in order, into the stage ring
+            int s = 0;
+            unsigned ph = 0, armed = 0, armed_par = 0;
+            bool ok = true;
+            for (long long T = blockIdx.x; ok && T < total; T += gridDim.x) {
+                const int g = (int)(T / G.tiles);
+                const int n0 = (int)(T - (long long)g * G.tiles) * kTileStep;
+                for (int q = 0; q < 9; ++q) {
+                    if (!bar_wait(empty(s), ph ^ 1u, limit, s_abort)) { ok = false; break; }
+                    bar_expect_tx(full(s), L::SLAB);
+                    tma_rows(sA + s * L::SLAB, &map, n0 + (q / 3 - 1) * G.Si + (q % 3 - 1) * G.Sj - 1,
+                             g, full(s));
+                    armed |= 1u << s;
+                    armed_par = (armed_par & ~(1u << s)) | (ph << s);
+                    if (++s == kStages) { s = 0; ph ^= 1u; }
+                }
+            }
+            // every copy issued has landed before the CTA may exit
+            for (int q = 0; q < kStages; ++q)
+                if (armed >> q & 1u) bar_drain(full(q), (armed_par >> q) & 1u, limit);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr unsigned ID = idesc_bf16<3 * NO>();
+            int s = 0, a = 0;
+            unsigned ph = 0, aph = 0;
+            bool ok = true;
+            for (long long T = blockIdx.x; ok && T < total; T += gridDim.x) {
+                if (!bar_wait(acc_empty(a), aph ^ 1u, limit, s_abort)) break;
+                tc_fence_after();
+                const unsigned d = tmem + (unsigned)(a * kBufCols);
+                for (int q = 0; q < 9; ++q) {
+                    if (!bar_wait(full(s), ph, limit, s_abort)) { ok = false; break; }
+#if TTGB_TC_SLAB_FENCE
+                    tc_fence_after();
+#endif
+                    const unsigned slab = sA + s * L::SLAB;
+#pragma unroll
+                    for (int h = 0; h < KC / 2; ++h) {
+                        // K half h: 32 bytes into the swizzled rows; B: the (di, dj) weights of
+                        // the three dk taps, rows [dk][co]
+                        const unsigned long long ad = mdesc(slab + 32 * h, L::SBO, L::LAYOUT);
+                        const unsigned long long bd = mdesc(sW + q * L::QW + 32 * h, L::SBO, L::LAYOUT);
+                        mma_bf16(d, ad, bd, ID, (q | h) != 0);
+                    }
+                    mma_commit(empty(s));   // the stage is free once these MMAs have read it
+                    if (++s == kStages) { s = 0; ph ^= 1u; }
+                }
+                if (!ok) break;
+                mma_commit(acc_full(a));
+                if (++a == 2) { a = 0; aph ^= 1u; }
+            }
+            // every MMA issued has completed before tensor memory is freed
+            mma_commit(drain);
+            bar_drain(drain, 0, limit);
+        }
+    } else {
+        // epilogue group a (warps 2-5: a = 0, warps 6-9: a = 1) takes this CTA's tiles of
+        // parity a, in accumulator buffer a; warp w reads TMEM lanes 32 (w % 4) ...
+        const int a = (warp - 2) >> 2;
+        const int quarter = warp & 3;
+        const int m = quarter * 32 + lane;
+        float *exch = reinterpret_cast<float *>(sm + L::EXCH);   // [2][4][2 lanes][2][32]
+        float bz[FINAL ? 1 : 32];
+#pragma unroll
+        for (int c = 0; c < (FINAL ? 1 : 32); ++c) bz[c] = bias[c];
+        unsigned aph = 0;
+        for (long long T = blockIdx.x + (long long)a * gridDim.x; T < total; T += 2LL * gridDim.x) {
+            // all 128 threads of the group agree (TMEM loads are warp-collective, the
+            // exchange spans the group)
+            if (!epi_all(a, bar_wait(acc_full(a), aph, limit, s_abort))) break;
+            tc_fence_after();
+            const unsigned taddr = tmem + ((unsigned)(quarter * 32) << 16) + (unsigned)(a * kBufCols);
+            float *ex = exch + a * 4 * 2 * 2 * 32;
+            const int g = (int)(T / G.tiles);
+            const int n = (int)(T - (long long)g * G.tiles) * kTileStep + m;
+            const bool out_ok = m < kTileStep && n < G.R;
+            if (FINAL) {
+                const float d0 = tmem_ld1(taddr), d1 = tmem_ld1(taddr + NO),
+                            d2 = tmem_ld1(taddr + 2 * NO);
+                tc_fence_before();
+                bar_arrive(acc_empty(a));
+                if (lane < 2) {
+                    ex[((quarter * 2 + lane) * 2 + 0) * 32] = d1;
+                    ex[((quarter * 2 + lane) * 2 + 1) * 32] = d2;
+                }
+                epi_sync(a);
+                float s1 = __shfl_down_sync(0xffffffffu, d1, 1);
+                float s2 = __shfl_down_sync(0xffffffffu, d2, 2);
+                if (quarter < 3) {
+                    if (lane == 31) s1 = ex[(((quarter + 1) * 2 + 0) * 2 + 0) * 32];
+                    if (lane >= 30) s2 = ex[(((quarter + 1) * 2 + lane - 30) * 2 + 1) * 32];
+                }
+                if (out_ok && !pad_row(G, n)) {
+                    const int k = n % G.Sj, j = (n / G.Sj) % (G.nt + 1), i = n / G.Si;
+                    const long long node = ((long long)i * G.nt + j) * G.np + k;
+                    reinterpret_cast<float *>(out_)[(long long)g * G.nr * G.nt * G.np + node] =
+                        (d0 + s1) + s2 + bz[0];
+                }
+            } else {
+                float d0[32], d1[32], d2[32];
+                {
+                    unsigned r0[32], r1[32], r2[32];
+                    tmem_ld96(taddr, r0, r1, r2);
+#pragma unroll
+                    for (int c = 0; c < 32; ++c) {
+                        d0[c] = __uint_as_float(r0[c]);
+                        d1[c] = __uint_as_float(r1[c]);
+                        d2[c] = __uint_as_float(r2[c]);
+                    }
+                }
+                tc_fence_before();
+                bar_arrive(acc_empty(a));
+                if (lane < 2) {
+#pragma unroll
+                    for (int c = 0; c < 32; ++c) {
+                        ex[((quarter * 2 + lane) * 2 + 0) * 32 + c] = d1[c];
+                        ex[((quarter * 2 + lane) * 2 + 1) * 32 + c] = d2[c];
+                    }
+                }
+                epi_sync(a);
+                const bool zero = !out_ok || pad_row(G, n);
+                unsigned w[16];
+#pragma unroll
+                for (int c = 0; c < 32; c += 2) {
+                    float v[2];
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        float s1 = __shfl_down_sync(0xffffffffu, d1[c + u], 1);
+                        float s2 = __shfl_down_sync(0xffffffffu, d2[c + u], 2);
+                        if (quarter < 3) {
+                            if (lane == 31) s1 = ex[(((quarter + 1) * 2 + 0) * 2 + 0) * 32 + c + u];
+                            if (lane >= 30) s2 = ex[(((quarter + 1) * 2 + lane - 30) * 2 + 1) * 32 + c + u];
+                        }
+                        v[u] = zero ? 0.0f : fmaxf((d0[c + u] + s1) + s2 + bz[c + u], 0.0f);
+                    }
+                    const __nv_bfloat162 p = __floats2bfloat162_rn(v[0], v[1]);
+                    w[c / 2] = *reinterpret_cast<const unsigned *>(&p);
+                }
+                if (out_ok) {
+                    uint4 *o = reinterpret_cast<uint4 *>(out_) + ((long long)g * G.R + n) * 4;
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        o[c] = make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
+                }
+            }
+            aph ^= 1u;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(kTmemCols)
+                     : "memory");
+    }
+    if (threadIdx.x == 0 && *s_abort) atomicExch(err, 1);
+}
+
+// Features [grid][node][6] (FP32) -> input rows [grid][R][16] (BF16; channels 6-15 and the
+// padding rows zero).
+__global__ void pack_features_kernel(RowGeo G, const float *__restrict__ x, uint4 *__restrict__ xp) {
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= (long long)G.nb * G.R) return;
+    const int g = (int)(q / G.R), n = (int)(q - (long long)g * G.R);
+    unsigned w[4] = {0u, 0u, 0u, 0u};
+    if (!pad_row(G, n)) {
+        const int k = n % G.Sj, j = (n / G.Sj) % (G.nt + 1), i = n / G.Si;
+        const float *f = x + ((long long)g * G.nr * G.nt * G.np + ((long long)i * G.nt + j) * G.np + k) *
+                                 kNetFeatures;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const __nv_bfloat162 p = __floats2bfloat162_rn(f[2 * c], f[2 * c + 1]);
+            w[c] = *reinterpret_cast<const unsigned *>(&p);
+        }
+    }
+    xp[2 * q] = make_uint4(w[0], w[1], w[2], w[3]);
+    xp[2 * q + 1] = make_uint4(0u, 0u, 0u, 0u);
+}
+
+// Layer l's weights W[27][cin][cout] (FP32) -> the shared-memory image of the B operands
+// (BF16): for q = (di, dj), rows (dk, co) of C = 8 KC input channels (tap t = 3 q + dk; zero
+// beyond cin and cout), each row's 16-byte chunks placed as the tensor cores' swizzle of the
+// row width expects them (chunk c of row r at c ^ ((r >> 1) & 3) for 64-byte rows,
+// c ^ ((r >> 2) & 1) for 32-byte rows).
+__global__ void weight_image_kernel(const float *__restrict__ w, int cin, int cout, int KC, int NO,
+                                    __nv_bfloat16 *__restrict__ img) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;   // logical element (q, dk, co, ci)
+    if (e >= 27 * NO * KC * 8) return;
+    const int C = 8 * KC;
+    const int ci = e % C, co = (e / C) % NO, dk = (e / (C * NO)) % 3, q = e / (3 * C * NO);
+    const int t = 3 * q + dk;
+    const float v = ci < cin && co < cout ? w[((size_t)t * cin + ci) * cout + co] : 0.0f;
+    const int r = dk * NO + co;                     // row within the (di, dj) block
+    const int c = ci / 8;
+    const int cs = KC == 4 ? c ^ ((r >> 1) & 3) : c ^ ((r >> 2) & 1);
+    img[((size_t)q * 3 * NO + r) * C + cs * 8 + ci % 8] = __float2bfloat16_rn(v);
+}
+
+inline unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+PFN_cuTensorMapEncodeTiled_v12000 map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// Tensor map over rows of 8 KC BF16 channels: dims (channels, R rows, nb grids); a box is
+// 128 rows of one grid, swizzled as the descriptors expect.
+cudaError_t encode_rows(CUtensorMap *map, const void *base, const RowGeo &G, int KC) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = map_encoder();
+    if (!enc) return cudaErrorNotSupported;
+    const cuuint64_t row = (cuuint64_t)KC * 16;
+    cuuint64_t dims[3] = {(cuuint64_t)KC * 8, (cuuint64_t)G.R, (cuuint64_t)G.nb};
+    cuuint64_t strides[2] = {row, row * (cuuint64_t)G.R};
+    cuuint32_t box[3] = {(cuuint32_t)KC * 8, (cuuint32_t)kTileRows, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), dims,
+                           strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           KC == 4 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+template <int KC, int NO, bool FINAL>
+cudaError_t launch_layer(const void *in, const RowGeo &G, const __nv_bfloat16 *wimg,
+                         const float *bias, void *out, int n_sm, int *err,
+                         unsigned long long limit, cudaStream_t st) {
+    CUtensorMap map;
+    cudaError_t e = encode_rows(&map, in, G, KC);
+    if (e != cudaSuccess) return e;
+    // more than half the shared memory of an SM: one CTA per SM, which owns its TMEM
+    constexpr int smem = Smem<KC, NO>::TOTAL > 120 * 1024 ? Smem<KC, NO>::TOTAL : 120 * 1024;
+    const void *fn = (const void *)conv3d_tc_kernel<KC, NO, FINAL>;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    const long long total = (long long)G.nb * G.tiles;
+    const unsigned grid = (unsigned)(total < n_sm ? total : n_sm);
+    conv3d_tc_kernel<KC, NO, FINAL><<<grid, kThreads, smem, st>>>(
+        map, G, reinterpret_cast<const uint4 *>(wimg), bias, out, err, limit);
+    return cudaGetLastError();
+}
+
+RowGeo row_geo(const ConvDims &d) {
+    RowGeo G;
+    G.nb = d.nb;
+    G.nr = d.D;
+    G.nt = d.H;
+    G.np = d.W;
+    G.Sj = d.W + 1;
+    G.Si = (d.H + 1) * G.Sj;
+    G.R = d.D * G.Si;
+    G.tiles = (G.R + kTileStep - 1) / kTileStep;
+    return G;
+}
+
+}  // namespace
+
+size_t net_rows(const ConvDims &d) { return (size_t)row_geo(d).R; }
+
+size_t net_weight_image_elems() {
+    return (size_t)27 * 8 * (2 * 32 + 4 * 32 + 4 * 32 + 4 * 16);
+}
+
+// Offsets of the four layers' images in the concatenated weight image.
+static size_t image_offset(int l) {
+    const size_t sz[kNetLayers] = {27u * 2 * 32 * 8, 27u * 4 * 32 * 8, 27u * 4 * 32 * 8,
+                                   27u * 4 * 16 * 8};
+    size_t o = 0;
+    for (int q = 0; q < l; ++q) o += sz[q];
+    return o;
+}
+
+cudaError_t run_net_weight_images(const float *theta, __nv_bfloat16 *img, cudaStream_t st) {
+    const int KC[kNetLayers] = {2, 4, 4, 4}, NO[kNetLayers] = {32, 32, 32, 16};
+    for (int l = 0; l < kNetLayers; ++l) {
+        const int n = 27 * KC[l] * NO[l] * 8;
+        weight_image_kernel<<<blocks_for(n, 256), 256, 0, st>>>(
+            theta + net_weight_offset(l), kNetCin[l], kNetCout[l], KC[l], NO[l], img + image_offset(l));
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t run_net_infer(const ConvDims &d, const float *theta, const __nv_bfloat16 *img,
+                          const float *x, __nv_bfloat16 *a, __nv_bfloat16 *b, float *y, int n_sm,
+                          int *err, unsigned long long limit, cudaStream_t st) {
+    static_assert(kNetHidden == 32 && kNetFeatures <= 16 && kNetCout[3] <= 16,
+                  "layer shapes of the tensor-core kernels");
+    const RowGeo G = row_geo(d);
+    // the input rows live in b until layer 2 overwrites it
+    pack_features_kernel<<<blocks_for((long long)G.nb * G.R, 256), 256, 0, st>>>(
+        G, x, reinterpret_cast<uint4 *>(b));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const float *bias[kNetLayers];
+    for (int l = 0; l < kNetLayers; ++l)
+        bias[l] = theta + net_weight_offset(l) + 27 * kNetCin[l] * kNetCout[l];
+    if ((e = launch_layer<2, 32, false>(b, G, img + image_offset(0), bias[0], a, n_sm, err, limit, st)) !=
+        cudaSuccess)
+        return e;
+    if ((e = launch_layer<4, 32, false>(a, G, img + image_offset(1), bias[1], b, n_sm, err, limit, st)) !=
+        cudaSuccess)
+        return e;
+    if ((e = launch_layer<4, 32, false>(b, G, img + image_offset(2), bias[2], a, n_sm, err, limit, st)) !=
+        cudaSuccess)
+        return e;
+    return launch_layer<4, 16, true>(a, G, img + image_offset(3), bias[3], y, n_sm, err, limit, st);
+}
+
+}  // namespace ttgb

@@ -195,10 +195,11 @@ def _bf16(a):
 
 
 def test_tensor_core_inference_matches_oracle(tt):
-    """The warm start's inference (layers 2-3 on the tensor cores, BF16 operands and
-    activations, FP32 accumulation) against the FP64 network with the same BF16 weights.
-    Bound: three BF16 roundings of the activations (2^-9 relative each) through layers of
-    gain ~1 leave the output within 2 % of its range; ragged tiles on every axis."""
+    """The warm start's inference (all four layers on the tensor cores with tcgen05: BF16
+    operands, features and activations, FP32 accumulation) against the FP64 network with the
+    same BF16 weights. Bound: four BF16 roundings of the layer inputs (2^-9 relative each)
+    through layers of gain ~1 leave the output within 2 % of its range. 13 x 12 x 17 grids:
+    24 tiles of 128 padded rows per grid, the last one ragged."""
     import torch
     w, xs = _oracle_inputs(65, shape=(13, 12, 17), n=2)
     theta = _theta(11)
