@@ -442,6 +442,62 @@ def warm_leg(args, gp, world):
                                                 meta["held_out_sweeps_warm"])}
 
 
+# Executed tensor-core FLOPs per 128-row tile of the four layers (M = 128, N = 3 x output
+# channels, K = 16 per MMA): layer 1 one K step per (di, dj), layers 2-3 two, layer 4 two
+# with N = 48), and the useful FLOPs of the network per node (unpadded channels).
+NET_TILE_FLOP = 9 * 2 * 128 * 16 * (96 * 1 + 96 * 2 + 96 * 2 + 48 * 2)
+NET_TILE_ROWS = 126
+NET_USEFUL_FLOP_PER_NODE = 2 * 27 * (6 * 32 + 32 * 32 + 32 * 32 + 32 * 1)
+
+
+def infer_only(args):
+    """Times the warm start's inference alone (tt_net_infer) on args.infer_only sources of the
+    benchmark grid, features computed beforehand; one JSON line."""
+    import torch
+    import paper_2412_00031_gb300 as tt
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    nb = args.infer_only
+    w = I.anisotropic_batch(seed=rank_seed(0), n_src=nb)
+    g = w.grid
+    ctx = tt.tt_ctx_create(g.as_dict())
+    z = np.load(args.warm_start)
+    tt.tt_net_set_weights(ctx, torch.as_tensor(z["theta"], device=dev))
+    f32 = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32), device=dev)
+    x = torch.empty((nb,) + g.shape + (6,), dtype=torch.float32, device=dev)
+    tt.tt_net_features(ctx, (f32(w.s), f32(w.xi), f32(w.eta)), w.src, x)
+    y = torch.empty(x.shape[:-1], dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        tt.tt_net_infer(ctx, x, y)
+    times = []
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        tt.tt_net_infer(ctx, x, y)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ctx.close()
+    ms = float(np.median(times))
+    nodes = int(np.prod(g.shape))
+    rows = g.shape[0] * (g.shape[1] + 1) * (g.shape[2] + 1)
+    tiles = -(-rows // NET_TILE_ROWS) * nb
+    executed = NET_TILE_FLOP * tiles / (ms * 1e-3) / 1e12
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peak, src = float(json.load(f)["bf16_tflops"]), "measured (burst)"
+    except Exception:
+        peak, src = 1900.0, "fallback"
+    return {"metric": "warm-start inference throughput", "value": nb / (ms * 1e-3),
+            "unit": "source-grids/s", "ms": ms, "grids": nb, "grid": list(g.shape),
+            "useful_tflops": NET_USEFUL_FLOP_PER_NODE * nodes * nb / (ms * 1e-3) / 1e12,
+            "roofline": {"bound": "tensor", "achieved": executed, "peak": peak, "unit": "TFLOP/s",
+                         "frac": executed / peak, "peak_source": src,
+                         "note": "executed MMA FLOPs (padded channels, 126 of 128 rows per tile)"},
+            "gpu_launches_per_call": 5}
+
+
 # ----------------------------------------------------------------------------- CPU oracle
 
 def oracle_sample(w, n_threads, n_src_sample, sweeps=1):
@@ -588,7 +644,12 @@ def main():
                     help="forward sweep schedule (tt_opts.sweep_schedule; 0 = automatic)")
     ap.add_argument("--ref-iters-fwd", type=float, default=30.0)
     ap.add_argument("--ref-iters-adj", type=float, default=4.0)
+    ap.add_argument("--infer-only", type=int, default=0,
+                    help="time only the warm start's inference on this many sources")
     args = ap.parse_args()
+    if args.infer_only > 0:
+        print(json.dumps(infer_only(args)))
+        return
     rank, world = dist_init()
     if args.impl == "reference":
         if rank == 0:

@@ -48,9 +48,6 @@ constexpr int kTileStep = kTileRows - 2;       // output rows of one tile
 #define TTGB_TC_STAGES 16
 #endif
 constexpr int kStages = TTGB_TC_STAGES;
-#ifndef TTGB_TC_SLAB_FENCE
-#define TTGB_TC_SLAB_FENCE 0
-#endif
 constexpr int kThreads = 320;                  // copier, MMA, two epilogue warpgroups
 // Two accumulator buffers of up to 3 x 32 columns.
 constexpr int kBufCols = 128;
@@ -325,9 +322,6 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const unsigned d = tmem + (unsigned)(a * kBufCols);
                 for (int q = 0; q < 9; ++q) {
                     if (!bar_wait(full(s), ph, limit, s_abort)) { ok = false; break; }
-#if TTGB_TC_SLAB_FENCE
-                    tc_fence_after();
-#endif
                     const unsigned slab = sA + s * L::SLAB;
 #pragma unroll
                     for (int h = 0; h < KC / 2; ++h) {
