@@ -219,3 +219,25 @@ def test_tensor_core_inference_matches_oracle(tt):
         assert np.abs(got - ref).max() <= 2e-2 * scale
         assert np.corrcoef(got.ravel(), ref.ravel())[0, 1] > 0.9999
         assert np.abs(got - y32[b].cpu().numpy()).max() <= 2e-2 * scale
+
+
+def test_tensor_core_inference_wide_and_small_grids(tt):
+    """The tensor-core inference where the 126-row tile steps do not line up with the grid:
+    a wide grid (260 phi nodes: a theta row spans three tiles) and a batch of three small
+    grids (7 x 5 x 9: 420 rows each, ragged last tiles). Against the FP64 network with the
+    same BF16 weights, to the bound of the test above."""
+    import torch
+    theta = _theta(12)
+    tb = _bf16(theta).astype(np.float64)
+    for seed, shape, n in ((66, (6, 5, 260), 1), (67, (7, 5, 9), 3)):
+        w, xs = _oracle_inputs(seed, shape=shape, n=n)
+        ctx = tt.tt_ctx_create(w.grid.as_dict())
+        tt.tt_net_set_weights(ctx, torch.as_tensor(theta, device="cuda"))
+        x = torch.as_tensor(np.stack(xs), device="cuda")
+        y = torch.empty(x.shape[:-1], dtype=torch.float32, device="cuda")
+        tt.tt_net_infer(ctx, x, y)
+        ctx.close()
+        for b in range(n):
+            ref = N.forward(tb, xs[b].astype(np.float64))
+            got = y[b].cpu().numpy()
+            assert np.abs(got - ref).max() <= 2e-2 * np.abs(ref).max(), (shape, b)
