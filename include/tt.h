@@ -9,6 +9,8 @@
  *               sources R = dchi/dT (Eqs. A1-A3)
  *   tt_adjoint  upwind fast-sweeping solve of the adjoint equation (Eq. 5)
  *   tt_kernel   FP64 accumulation of the sensitivity kernels K_s, K_xi, K_eta (Eqs. 6-8)
+ *   tt_kernel_density, tt_kernel_normalize, tt_mgrid_project, tt_mgrid_expand,
+ *   tt_model_update   regularisation and update of the inversion step (Eqs. 11-19)
  *
  * Conventions shared by every call:
  *  - Grid: n_r x n_t x n_p nodes, uniform in radius r (index i, i = 0 is the deepest
@@ -180,6 +182,50 @@ tt_status tt_adjoint(tt_ctx *ctx, const tt_model *model, const tt_point *h_src, 
  * the result is bitwise reproducible. */
 tt_status tt_kernel(tt_ctx *ctx, const tt_model *model, int n_src, const void *d_T,
                     const void *d_P, double *d_Ks, double *d_Kxi, double *d_Keta);
+
+/* ---- The inversion step's regularisation and update (Sec. 3.3; step 4 of Sec. 2). ---- */
+
+/* Kernel density (Eq. 19): adds sum over the n_src sources of d_P[node][b] to d_Kd (device
+ * double [N], read and written; zero it before the first batch). d_P: device [N][n_src] of
+ * dtype, the adjoint fields computed by tt_adjoint with every adjoint source R = 1 (Eq. 19
+ * defines K_d from those fields). FP64 sums in a fixed order (bitwise reproducible). */
+tt_status tt_kernel_density(tt_ctx *ctx, const void *d_P, int n_src, int dtype, double *d_Kd);
+
+/* Kernel-density normalisation (Eq. 18), in place on the three device double [N] kernels:
+ * K <- K / (d_Kd + eps)^zeta. eps > 0, zeta >= 0, else TT_EINVAL. */
+tt_status tt_kernel_normalize(tt_ctx *ctx, double *d_Ks, double *d_Kxi, double *d_Keta,
+                              const double *d_Kd, double eps, double zeta);
+
+/* H offset inversion grids of the multiple-grid parameterisation (Eqs. 11-14): n_grids
+ * grids of n_r x n_t x n_p nodes (3..4096 per axis; 1..64 grids). Along each axis grid h has
+ * its nodes at x_min + (a - h / n_grids) dc, a = 0..n-1, dc = (x_max - x_min) / (n - 2):
+ * every grid covers the forward domain, offset from the next by dc / n_grids. The basis
+ * function of node (a, b, c) of grid h is the product of the axes' hat functions / n_grids
+ * (Eq. 11). */
+typedef struct {
+    int n_r, n_t, n_p;
+    int n_grids;
+} tt_mgrid;
+
+/* Projection of a kernel onto the basis (Eq. 17): d_G[h][a][b][c] = sum over the forward
+ * nodes of d_K B^h_abc dV, with dV = r^2 cos(theta) dr dtheta dphi the node volume (the
+ * integral of Eq. 17 read as this nodal sum). d_K: device double [N]; d_G: device double
+ * [n_grids][n_r][n_t][n_p]. Fixed-order sums. */
+tt_status tt_mgrid_project(tt_ctx *ctx, const tt_mgrid *mg, const double *d_K, double *d_G);
+
+/* Expansion of coefficients onto the forward grid (Eq. 15): d_D[node] = sum over grids and
+ * basis functions of d_G B^h_l(node). Applied to the projected kernels it gives the smoothed
+ * descent direction. d_G as above, d_D device double [N]. */
+tt_status tt_mgrid_expand(tt_ctx *ctx, const tt_mgrid *mg, const double *d_G, double *d_D);
+
+/* Model update of one gradient-descent step (step 4 of Sec. 2), in place on the model's
+ * device arrays (cast from const): s <- s (1 - step d_Ds / max|d_Ds|),
+ * xi <- xi - step d_Dxi / max|d_Dxi|, eta <- eta - step d_Deta / max|d_Deta|. The kernels
+ * are derivatives of chi with respect to ln s, xi and eta (Eq. 9); a zero direction leaves
+ * its field unchanged. step in (0, 1), else TT_EINVAL. Step-size control (halving a step
+ * that raises chi) is the caller's loop. */
+tt_status tt_model_update(tt_ctx *ctx, const tt_model *model, const double *d_Ds,
+                          const double *d_Dxi, const double *d_Deta, double step);
 
 /* Largest receiver count tt_misfit_noalloc accepts: the size of its static scratch. */
 #define TT_NOALLOC_MAX_REC 1024

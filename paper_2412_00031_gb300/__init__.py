@@ -42,6 +42,10 @@ class TTModel(C.Structure):
                 ("dtype", C.c_int)]
 
 
+class TTMgrid(C.Structure):
+    _fields_ = [("n_r", C.c_int), ("n_t", C.c_int), ("n_p", C.c_int), ("n_grids", C.c_int)]
+
+
 class TTPoint(C.Structure):
     _fields_ = [("depth_km", C.c_double), ("lat_deg", C.c_double), ("lon_deg", C.c_double)]
 
@@ -75,7 +79,9 @@ EXPORTED = ["tt_default_opts", "tt_ctx_create", "tt_ctx_destroy", "tt_last_error
             "tt_forward", "tt_misfit", "tt_adjoint", "tt_kernel", "tt_get_stats",
             "tt_misfit_noalloc", "tt_plan_create", "tt_plan_run", "tt_plan_destroy",
             "tt_net_param_count", "tt_net_features", "tt_net_forward", "tt_net_loss_grad",
-            "tt_net_adam", "tt_net_set_weights", "tt_autotune", "tt_net_infer"]
+            "tt_net_adam", "tt_net_set_weights", "tt_autotune", "tt_net_infer",
+            "tt_kernel_density", "tt_kernel_normalize", "tt_mgrid_project", "tt_mgrid_expand",
+            "tt_model_update"]
 TT_NOALLOC_MAX_REC = 1024
 
 
@@ -120,10 +126,17 @@ def _load():
     L.tt_net_infer.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]
     L.tt_autotune.argtypes = [C.c_void_p, C.POINTER(TTModel), C.POINTER(TTPoint), C.c_int,
                               C.POINTER(TTOpts), C.POINTER(C.c_double)]
+    L.tt_kernel_density.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p]
+    L.tt_kernel_normalize.argtypes = [C.c_void_p] + [C.c_void_p] * 4 + [C.c_double] * 2
+    L.tt_mgrid_project.argtypes = [C.c_void_p, C.POINTER(TTMgrid), C.c_void_p, C.c_void_p]
+    L.tt_mgrid_expand.argtypes = [C.c_void_p, C.POINTER(TTMgrid), C.c_void_p, C.c_void_p]
+    L.tt_model_update.argtypes = [C.c_void_p, C.POINTER(TTModel)] + [C.c_void_p] * 3 + [C.c_double]
     for name in ("tt_ctx_create", "tt_forward", "tt_misfit", "tt_adjoint", "tt_kernel",
                  "tt_get_stats", "tt_misfit_noalloc", "tt_plan_create", "tt_plan_run",
                  "tt_net_param_count", "tt_net_features", "tt_net_forward", "tt_net_loss_grad",
-                 "tt_net_adam", "tt_net_set_weights", "tt_autotune", "tt_net_infer"):
+                 "tt_net_adam", "tt_net_set_weights", "tt_autotune", "tt_net_infer",
+                 "tt_kernel_density", "tt_kernel_normalize", "tt_mgrid_project",
+                 "tt_mgrid_expand", "tt_model_update"):
         getattr(L, name).restype = C.c_int
     return L
 
@@ -251,6 +264,8 @@ class DeviceData:
         self.cs_off, self.cs_m, self.cs_i = i32(cs_off), i32(cs_m), i32(cs_i)
         self.cs_dtobs, self.cs_w = f64(cs_dtobs), f64(cs_w)
         self.alpha, self.beta = float(alpha), float(beta)
+        self.h_abs_off = np.asarray(abs_off, dtype=np.int64)    # host copies (record masks)
+        self.h_abs_rec = np.asarray(abs_rec, dtype=np.int64)
         self.n_src = len(abs_off) - 1
         self.n_rec = len(self.rec)
         self._pts, _ = _points(self.rec)
@@ -296,6 +311,45 @@ def tt_kernel(ctx, model, T, P, Ks, Kxi, Keta):
     n_src = T.shape[-1]
     _check(ctx, lib.tt_kernel(ctx.handle, C.byref(M), n_src, _ptr(T), _ptr(P), _ptr(Ks),
                               _ptr(Kxi), _ptr(Keta)))
+
+
+def tt_kernel_density(ctx, P_hat, Kd):
+    """Kd += sum over sources of P_hat (Eq. 19); P_hat [..., n_src] from tt_adjoint with R = 1."""
+    _cuda_ok(P_hat, Kd)
+    _check(ctx, lib.tt_kernel_density(ctx.handle, _ptr(P_hat), P_hat.shape[-1],
+                                      _dtype_code(P_hat), _ptr(Kd)))
+
+
+def tt_kernel_normalize(ctx, Ks, Kxi, Keta, Kd, eps, zeta):
+    """Eq. 18 in place: K <- K / (Kd + eps)^zeta."""
+    _cuda_ok(Ks, Kxi, Keta, Kd)
+    _check(ctx, lib.tt_kernel_normalize(ctx.handle, _ptr(Ks), _ptr(Kxi), _ptr(Keta), _ptr(Kd),
+                                        float(eps), float(zeta)))
+
+
+def mgrid(n_r, n_t, n_p, n_grids):
+    """Description of n_grids offset inversion grids of n_r x n_t x n_p nodes."""
+    return TTMgrid(n_r, n_t, n_p, n_grids)
+
+
+def tt_mgrid_project(ctx, mg, K, G):
+    """Eq. 17: G [n_grids, n_r, n_t, n_p] (float64) from the kernel K (float64, grid shape)."""
+    _cuda_ok(K, G)
+    _check(ctx, lib.tt_mgrid_project(ctx.handle, C.byref(mg), _ptr(K), _ptr(G)))
+
+
+def tt_mgrid_expand(ctx, mg, G, D):
+    """Eq. 15: D (float64, grid shape) from the coefficients G."""
+    _cuda_ok(G, D)
+    _check(ctx, lib.tt_mgrid_expand(ctx.handle, C.byref(mg), _ptr(G), _ptr(D)))
+
+
+def tt_model_update(ctx, model, Ds, Dxi, Deta, step):
+    """One gradient-descent step on the model's arrays, in place (see tt.h)."""
+    M = _model(model)
+    _cuda_ok(Ds, Dxi, Deta)
+    _check(ctx, lib.tt_model_update(ctx.handle, C.byref(M), _ptr(Ds), _ptr(Dxi), _ptr(Deta),
+                                    float(step)))
 
 
 def tt_get_stats(ctx, which=TT_STATS_FORWARD):

@@ -15,6 +15,7 @@
 #include "tt.h"
 #include "tt_aux.h"
 #include "tt_internal.h"
+#include "tt_inv.h"
 #include "tt_net.h"
 
 using namespace ttgb;
@@ -50,6 +51,9 @@ struct tt_ctx {
     double *h_loss = nullptr;  // pinned
     // autotuner: scratch tau and the choices made, per (n_src, dtype)
     DevBuf tune_tau, tau_w, slot_srcc, slot_int;
+    // inversion step: multiple-grid tables (for mg_key), projection scratch, update scratch
+    DevBuf mg_tab, mg_scr, upd_part;
+    int mg_key[4] = {0, 0, 0, 0};
     struct Tuned { int n_src, dtype, schedule, groups; };
     std::vector<Tuned> tuned;
     int *h_pinned = nullptr;  // readback: [0..TT_MAX_BATCH) iterations, then flags
@@ -1157,7 +1161,7 @@ void tt_ctx_destroy(tt_ctx *ctx) {
                       &ctx->net_b, &ctx->net_y, &ctx->net_d1, &ctx->net_d2, &ctx->net_dy,
                       &ctx->net_wt, &ctx->net_part, &ctx->net_scr, &ctx->tune_tau, &ctx->tau_w,
                       &ctx->slot_srcc, &ctx->slot_int,
-                      &ctx->net_wbf};
+                      &ctx->net_wbf, &ctx->mg_tab, &ctx->mg_scr, &ctx->upd_part};
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     if (ctx->h_loss) cudaFreeHost(ctx->h_loss);
@@ -1244,6 +1248,131 @@ tt_status tt_kernel(tt_ctx *ctx, const tt_model *model, int n_src, const void *d
     if (!d_T || !d_P || !d_Ks || !d_Kxi || !d_Keta)
         return fail(ctx, TT_EINVAL, "tt_kernel: NULL argument");
     return enq_kernel(ctx, model, n_src, d_T, d_P, d_Ks, d_Kxi, d_Keta);
+}
+
+tt_status tt_kernel_density(tt_ctx *ctx, const void *d_P, int n_src, int dtype, double *d_Kd) {
+    if (!ctx) return TT_EINVAL;
+    if (n_src < 1 || n_src > TT_MAX_BATCH)
+        return fail(ctx, TT_EINVAL, "n_src = %d outside 1..%d", n_src, TT_MAX_BATCH);
+    if (dtype != TT_F32 && dtype != TT_F64)
+        return fail(ctx, TT_EINVAL, "dtype %d is neither TT_F32 nor TT_F64", dtype);
+    if (!d_P || !d_Kd) return fail(ctx, TT_EINVAL, "tt_kernel_density: NULL argument");
+    const long long N = ctx->g.N;
+    CK(dtype == TT_F32 ? run_kernel_density<float>(N, n_src, (const float *)d_P, d_Kd, ctx->st)
+                       : run_kernel_density<double>(N, n_src, (const double *)d_P, d_Kd, ctx->st));
+    ctx->launches += 1;
+    return TT_OK;
+}
+
+tt_status tt_kernel_normalize(tt_ctx *ctx, double *d_Ks, double *d_Kxi, double *d_Keta,
+                              const double *d_Kd, double eps, double zeta) {
+    if (!ctx) return TT_EINVAL;
+    if (!d_Ks || !d_Kxi || !d_Keta || !d_Kd)
+        return fail(ctx, TT_EINVAL, "tt_kernel_normalize: NULL argument");
+    if (!(eps > 0) || !(zeta >= 0))
+        return fail(ctx, TT_EINVAL, "tt_kernel_normalize: eps must be > 0 and zeta >= 0");
+    CK(run_kernel_normalize(ctx->g.N, d_Ks, d_Kxi, d_Keta, d_Kd, eps, zeta, ctx->st));
+    ctx->launches += 1;
+    return TT_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// The tables of the inversion grids of mg on the device, rebuilt when mg changes: Wr, Wt, Wp
+// (double) then lo for r, theta, phi (int).
+struct MgTabs {
+    const double *Wr, *Wt, *Wp;
+    const int *lo;
+};
+
+tt_status mgrid_tables(tt_ctx *ctx, const tt_mgrid *mg, MgDims &d, MgTabs &tb) {
+    if (!mg) return fail(ctx, TT_EINVAL, "inversion grid description is NULL");
+    if (mg->n_grids < 1 || mg->n_grids > 64 || mg->n_r < 3 || mg->n_t < 3 || mg->n_p < 3 ||
+        mg->n_r > 4096 || mg->n_t > 4096 || mg->n_p > 4096)
+        return fail(ctx, TT_EINVAL, "inversion grids: need 1..64 grids of 3..4096 nodes per axis");
+    const GridC &g = ctx->g;
+    d = MgDims{g.nr, g.nt, g.np, mg->n_r, mg->n_t, mg->n_p, mg->n_grids};
+    const size_t nw = (size_t)d.H * ((size_t)d.cr * d.nr + (size_t)d.ct * d.nt + (size_t)d.cp * d.np);
+    const size_t nl = (size_t)d.H * ((size_t)d.nr + d.nt + d.np);
+    ENSURE(ctx->mg_tab, sizeof(double) * nw + sizeof(int) * nl);
+    double *W = (double *)ctx->mg_tab.p;
+    tb.Wr = W;
+    tb.Wt = W + (size_t)d.H * d.cr * d.nr;
+    tb.Wp = tb.Wt + (size_t)d.H * d.ct * d.nt;
+    tb.lo = (const int *)(W + nw);
+    const int key[4] = {mg->n_r, mg->n_t, mg->n_p, mg->n_grids};
+    if (memcmp(key, ctx->mg_key, sizeof key) == 0) return TT_OK;
+    std::vector<double> hw, w;
+    std::vector<int> hl, l;
+    const int n[3] = {d.nr, d.nt, d.np}, c[3] = {d.cr, d.ct, d.cp};
+    for (int a = 0; a < 3; ++a) {
+        mgrid_axis_tables(n[a], c[a], d.H, w, l);
+        hw.insert(hw.end(), w.begin(), w.end());
+        hl.insert(hl.end(), l.begin(), l.end());
+    }
+    CK(cudaStreamSynchronize(ctx->st));   // the previous tables may still be read
+    CK(cudaMemcpy(W, hw.data(), sizeof(double) * nw, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(W + nw, hl.data(), sizeof(int) * nl, cudaMemcpyHostToDevice));
+    memcpy(ctx->mg_key, key, sizeof key);
+    return TT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+tt_status tt_mgrid_project(tt_ctx *ctx, const tt_mgrid *mg, const double *d_K, double *d_G) {
+    if (!ctx) return TT_EINVAL;
+    if (!d_K || !d_G) return fail(ctx, TT_EINVAL, "tt_mgrid_project: NULL argument");
+    MgDims d;
+    MgTabs tb;
+    tt_status s;
+    if ((s = mgrid_tables(ctx, mg, d, tb)) != TT_OK) return s;
+    const size_t n1 = (size_t)d.H * d.nr * d.nt * d.cp, n2 = (size_t)d.H * d.nr * d.ct * d.cp;
+    ENSURE(ctx->mg_scr, sizeof(double) * (n1 + n2));
+    double *T1 = (double *)ctx->mg_scr.p;
+    const GridC &g = ctx->g;
+    CK(run_mgrid_project(d, d_K, ctx->gd.h2, ctx->gd.cost, g.dr * g.dt * g.dp, tb.Wr, tb.Wt,
+                         tb.Wp, T1, T1 + n1, d_G, ctx->st));
+    ctx->launches += 3;
+    return TT_OK;
+}
+
+tt_status tt_mgrid_expand(tt_ctx *ctx, const tt_mgrid *mg, const double *d_G, double *d_D) {
+    if (!ctx) return TT_EINVAL;
+    if (!d_G || !d_D) return fail(ctx, TT_EINVAL, "tt_mgrid_expand: NULL argument");
+    MgDims d;
+    MgTabs tb;
+    tt_status s;
+    if ((s = mgrid_tables(ctx, mg, d, tb)) != TT_OK) return s;
+    CK(run_mgrid_expand(d, d_G, tb.lo, tb.Wr, tb.Wt, tb.Wp, d_D, ctx->st));
+    ctx->launches += 1;
+    return TT_OK;
+}
+
+tt_status tt_model_update(tt_ctx *ctx, const tt_model *model, const double *d_Ds,
+                          const double *d_Dxi, const double *d_Deta, double step) {
+    if (!ctx) return TT_EINVAL;
+    tt_status s;
+    if ((s = check_model(ctx, model)) != TT_OK) return s;
+    if (!d_Ds || !d_Dxi || !d_Deta) return fail(ctx, TT_EINVAL, "tt_model_update: NULL direction");
+    if (!(step > 0) || !(step < 1)) return fail(ctx, TT_EINVAL, "tt_model_update: step must be in (0, 1)");
+    constexpr int kParts = 304;   // 2 x 152 SMs
+    ENSURE(ctx->upd_part, sizeof(double) * (3 * kParts + 3));
+    double *part = (double *)ctx->upd_part.p;
+    const long long N = ctx->g.N;
+    if (model->dtype == TT_F32)
+        CK(run_model_update<float>(N, (float *)model->d_s, (float *)model->d_xi,
+                                   (float *)model->d_eta, d_Ds, d_Dxi, d_Deta, step, part, kParts,
+                                   ctx->st));
+    else
+        CK(run_model_update<double>(N, (double *)model->d_s, (double *)model->d_xi,
+                                    (double *)model->d_eta, d_Ds, d_Dxi, d_Deta, step, part,
+                                    kParts, ctx->st));
+    ctx->launches += 3;
+    return TT_OK;
 }
 
 tt_status tt_get_stats(const tt_ctx *ctx, int which, tt_stats *out) {

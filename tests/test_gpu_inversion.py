@@ -1,0 +1,159 @@
+"""Parity of the inversion step's kernels with the FP64 oracle (oracle/inversion.py), and the
+inversion loop on a small synthetic case (needs a GB300).
+
+- kernel density (Eq. 19), normalisation (Eq. 18), projection (Eq. 17) and expansion
+  (Eq. 15) on seeded inputs, element by element; grids of several inversion-grid cells and
+  ragged fine / coarse ratios; one projection at the 201 x 201 x 101 configuration size;
+- the model update (FP32 and FP64 models);
+- the loop: observations from the oracle's FP64 forward in a checkerboard model, inversion
+  from the background model: chi must fall.
+"""
+import numpy as np
+import pytest
+
+import tt_inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tt():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2412_00031_gb300 as m
+    return m
+
+
+def _dev(a, dtype=None):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype or torch.float64, device="cuda")
+
+
+def test_kernel_density_sums_sources(tt):
+    import torch
+    import oracle.inversion as V
+    w = I.small_case(81, shape=(9, 10, 11), n_src=1)
+    rng = np.random.default_rng(81)
+    ctx = tt.tt_ctx_create(w.grid.as_dict())
+    for dtype, B in ((torch.float32, 37), (torch.float64, 5)):
+        P = rng.standard_normal(w.grid.shape + (B,))
+        Pd = _dev(P, dtype)
+        Kd = _dev(np.full(w.grid.shape, 0.5))
+        tt.tt_kernel_density(ctx, Pd, Kd)
+        P64 = Pd.double().cpu().numpy()
+        ref = 0.5 + V.kernel_density([P64[..., b] for b in range(B)])
+        assert np.abs(Kd.cpu().numpy() - ref).max() <= 1e-12 * np.abs(ref).max()
+    ctx.close()
+
+
+def test_normalisation_matches_oracle(tt):
+    import oracle.inversion as V
+    w = I.small_case(82, shape=(9, 10, 11), n_src=1)
+    rng = np.random.default_rng(82)
+    K = [rng.standard_normal(w.grid.shape) for _ in range(3)]
+    Kd = rng.uniform(0.0, 5.0, w.grid.shape)
+    ctx = tt.tt_ctx_create(w.grid.as_dict())
+    Kdev = [_dev(k) for k in K]
+    tt.tt_kernel_normalize(ctx, *Kdev, _dev(Kd), 0.3, 0.7)
+    for a, k in zip(Kdev, K):
+        ref = V.normalize(k, Kd, 0.3, 0.7)
+        assert np.abs(a.cpu().numpy() - ref).max() <= 1e-13 * np.abs(ref).max()
+    ctx.close()
+
+
+@pytest.mark.parametrize("shape,coarse,H", [((9, 10, 11), (4, 5, 4), 3),
+                                            ((17, 23, 19), (11, 11, 11), 5),
+                                            ((13, 12, 33), (6, 3, 9), 2)])
+def test_projection_and_expansion_match_oracle(tt, shape, coarse, H):
+    import oracle as O
+    import oracle.inversion as V
+    w = I.small_case(83, shape=shape, n_src=1)
+    g = w.grid.as_dict()
+    rng = np.random.default_rng(83)
+    K = rng.standard_normal(shape)
+    Gin = rng.standard_normal((H,) + coarse)
+    B = V.bases(shape, coarse, H)
+    dV = O.node_volumes(g)
+    ctx = tt.tt_ctx_create(g)
+    mg = tt.mgrid(*coarse, H)
+    G = _dev(np.zeros((H,) + coarse))
+    tt.tt_mgrid_project(ctx, mg, _dev(K), G)
+    ref = V.project(K, dV, B, H)
+    assert np.abs(G.cpu().numpy() - ref).max() <= 1e-12 * np.abs(ref).max()
+    D = _dev(np.zeros(shape))
+    tt.tt_mgrid_expand(ctx, mg, _dev(Gin), D)
+    ref = V.expand(Gin, B, H)
+    assert np.abs(D.cpu().numpy() - ref).max() <= 1e-12 * np.abs(ref).max()
+    ctx.close()
+
+
+def test_projection_at_the_inversion_configuration_size(tt):
+    """201 (lat) x 201 (lon) x 101 (depth) nodes, 5 grids of 11^3: against the oracle on a
+    smooth kernel (the oracle contracts one axis at a time through einsum's path)."""
+    import oracle as O
+    import oracle.inversion as V
+    g = I.GridSpec(101, 201, 201, 0.0, 200.0, 0.0, 5.0, 0.0, 5.0).as_dict()
+    shape, coarse, H = (101, 201, 201), (11, 11, 11), 5
+    i, j, k = np.meshgrid(*[np.linspace(0, 1, n) for n in shape], indexing="ij")
+    K = np.sin(3 * i) * np.cos(2 * j) + k * k
+    ctx = tt.tt_ctx_create(g)
+    mg = tt.mgrid(*coarse, H)
+    G = _dev(np.zeros((H,) + coarse))
+    tt.tt_mgrid_project(ctx, mg, _dev(K), G)
+    B = V.bases(shape, coarse, H)
+    Ur, Ut, Up = B
+    KV = K * O.node_volumes(g)
+    ref = np.stack([np.einsum("ijk,ai,bj,ck->abc", KV, Ur[h], Ut[h], Up[h], optimize=True) / H
+                    for h in range(H)])
+    assert np.abs(G.cpu().numpy() - ref).max() <= 1e-11 * np.abs(ref).max()
+    ctx.close()
+
+
+def test_model_update_matches_oracle(tt):
+    import torch
+    import oracle.inversion as V
+    w = I.small_case(84, shape=(9, 10, 11), n_src=1)
+    rng = np.random.default_rng(84)
+    D = [rng.standard_normal(w.grid.shape) for _ in range(3)]
+    ctx = tt.tt_ctx_create(w.grid.as_dict())
+    for dtype, tol in ((torch.float32, 2e-7), (torch.float64, 1e-14)):
+        model = tuple(_dev(a, dtype) for a in (w.s, w.xi, w.eta))
+        before = [a.double().cpu().numpy() for a in model]
+        tt.tt_model_update(ctx, model, *[_dev(d) for d in D], 0.03)
+        ref = V.update(*before, *D, 0.03)
+        for a, r in zip(model, ref):
+            got = a.double().cpu().numpy()
+            assert np.abs(got - r).max() <= tol * np.abs(r).max() + 1e-12
+    ctx.close()
+
+
+def test_inversion_loop_reduces_the_misfit(tt):
+    """Observations: the oracle's FP64 forward in a 5 % checkerboard model; start: the
+    background. Three step attempts must lower chi by at least 20 %."""
+    import torch
+    import oracle as O
+    from paper_2412_00031_gb300.invert import Inversion
+    w = I.small_case(85, shape=(17, 17, 17), n_src=6, n_rec=12)
+    g = w.grid.as_dict()
+    shape = w.grid.shape
+    i, j, k = np.meshgrid(*[np.arange(n) for n in shape], indexing="ij")
+    cb = 0.05 * np.sin(np.pi * i / 8) * np.sin(np.pi * j / 8) * np.sin(np.pi * k / 8)
+    s_true = w.s / (1.0 + cb)
+    tobs = []
+    for b in range(w.n_src):
+        _, T, _, conv, _ = O.forward(g, s_true, w.xi, w.eta, w.src[b], tol=1e-9, max_iter=500)
+        assert conv
+        tobs.append(O.receiver_times(g, T, w.rec))
+    rec_all = np.arange(len(w.rec))
+    data = tt.DeviceData(w.rec, np.arange(w.n_src + 1) * len(w.rec), np.tile(rec_all, w.n_src),
+                         np.concatenate(tobs), np.ones(w.n_src * len(w.rec)),
+                         np.zeros(w.n_src + 1, dtype=np.int32), [], [], [], [])
+    model = tuple(_dev(a, torch.float32) for a in (w.s, w.xi, w.eta))
+    ctx = tt.tt_ctx_create(g)
+    inv = Inversion(ctx, model, w.src, data, shape, tt.mgrid(5, 5, 5, 3))
+    hist = inv.run(3, 0.03)
+    ctx.close()
+    chis = [h[0] for h in hist if h[2]]
+    print("\nchi per accepted step:", ["%.4g" % c for c in chis])
+    assert chis[-1] <= 0.8 * chis[0]
