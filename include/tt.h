@@ -9,6 +9,7 @@
  *               sources R = dchi/dT (Eqs. A1-A3)
  *   tt_adjoint  upwind fast-sweeping solve of the adjoint equation (Eq. 5)
  *   tt_kernel   FP64 accumulation of the sensitivity kernels K_s, K_xi, K_eta (Eqs. 6-8)
+ *   tt_misfit_cr   common-receiver differential times (Eqs. 4, A4)
  *   tt_kernel_density, tt_kernel_normalize, tt_mgrid_project, tt_mgrid_expand,
  *   tt_model_update   regularisation and update of the inversion step (Eqs. 11-19)
  *
@@ -182,6 +183,31 @@ tt_status tt_adjoint(tt_ctx *ctx, const tt_model *model, const tt_point *h_src, 
  * the result is bitwise reproducible. */
 tt_status tt_kernel(tt_ctx *ctx, const tt_model *model, int n_src, const void *d_T,
                     const void *d_P, double *d_Ks, double *d_Kxi, double *d_Keta);
+
+/* ---- Common-receiver differential times (Eq. 4) and their adjoint source (Eq. A4). ---- */
+
+/* Pairs of sources of one batch observed at a common receiver. The entries of (source b,
+ * receiver m) are d_off[b * n_rec + m] .. d_off[b * n_rec + m + 1] - 1 (d_off: n_src * n_rec
+ * + 1 ints, non-decreasing, n_entries = d_off[last]); entry q names the other source
+ * d_other[q] (0 <= j < n_src, j != b), dT_obs = T_b^obs(x_m) - T_j^obs(x_m) as d_dtobs[q], and
+ * the pair's weight d_w[q]. An unordered pair {b, j} with weight w stands for the two ordered
+ * terms of Eq. 4 with weight w / 2 each and is listed twice: under (b, m) with dT_obs and
+ * under (j, m) with -dT_obs. gamma weights chi_cr (Eq. 1). Device arrays. */
+typedef struct {
+    int n_src, n_rec, n_entries;
+    const int *d_off, *d_other;
+    const double *d_dtobs, *d_w;
+    double gamma;
+} tt_cr_data;
+
+/* chi_cr and its adjoint source from the batch's receiver-time table d_Tr (device double
+ * [n_src][n_rec], as tt_misfit writes it): d_R[b][m] += gamma dchi_cr/dT_b(x_m) (Eq. A4;
+ * device double [n_src][n_rec], read and written: call after tt_misfit, before tt_adjoint),
+ * d_chi_cr[b] = source b's ordered terms of Eq. 4 (device double [n_src]; they sum to
+ * chi_cr). Fixed-order sums. An entry naming a source out of range is skipped and the call
+ * returns TT_EINVAL (after synchronising the context's stream). */
+tt_status tt_misfit_cr(tt_ctx *ctx, const tt_cr_data *d, const double *d_Tr, double *d_chi_cr,
+                       double *d_R);
 
 /* ---- The inversion step's regularisation and update (Sec. 3.3; step 4 of Sec. 2). ---- */
 

@@ -46,6 +46,12 @@ class TTMgrid(C.Structure):
     _fields_ = [("n_r", C.c_int), ("n_t", C.c_int), ("n_p", C.c_int), ("n_grids", C.c_int)]
 
 
+class TTCrData(C.Structure):
+    _fields_ = [("n_src", C.c_int), ("n_rec", C.c_int), ("n_entries", C.c_int),
+                ("d_off", C.c_void_p), ("d_other", C.c_void_p), ("d_dtobs", C.c_void_p),
+                ("d_w", C.c_void_p), ("gamma", C.c_double)]
+
+
 class TTPoint(C.Structure):
     _fields_ = [("depth_km", C.c_double), ("lat_deg", C.c_double), ("lon_deg", C.c_double)]
 
@@ -81,7 +87,7 @@ EXPORTED = ["tt_default_opts", "tt_ctx_create", "tt_ctx_destroy", "tt_last_error
             "tt_net_param_count", "tt_net_features", "tt_net_forward", "tt_net_loss_grad",
             "tt_net_adam", "tt_net_set_weights", "tt_autotune", "tt_net_infer",
             "tt_kernel_density", "tt_kernel_normalize", "tt_mgrid_project", "tt_mgrid_expand",
-            "tt_model_update"]
+            "tt_model_update", "tt_misfit_cr"]
 TT_NOALLOC_MAX_REC = 1024
 
 
@@ -126,6 +132,7 @@ def _load():
     L.tt_net_infer.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]
     L.tt_autotune.argtypes = [C.c_void_p, C.POINTER(TTModel), C.POINTER(TTPoint), C.c_int,
                               C.POINTER(TTOpts), C.POINTER(C.c_double)]
+    L.tt_misfit_cr.argtypes = [C.c_void_p, C.POINTER(TTCrData)] + [C.c_void_p] * 3
     L.tt_kernel_density.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p]
     L.tt_kernel_normalize.argtypes = [C.c_void_p] + [C.c_void_p] * 4 + [C.c_double] * 2
     L.tt_mgrid_project.argtypes = [C.c_void_p, C.POINTER(TTMgrid), C.c_void_p, C.c_void_p]
@@ -136,7 +143,7 @@ def _load():
                  "tt_net_param_count", "tt_net_features", "tt_net_forward", "tt_net_loss_grad",
                  "tt_net_adam", "tt_net_set_weights", "tt_autotune", "tt_net_infer",
                  "tt_kernel_density", "tt_kernel_normalize", "tt_mgrid_project",
-                 "tt_mgrid_expand", "tt_model_update"):
+                 "tt_mgrid_expand", "tt_model_update", "tt_misfit_cr"):
         getattr(L, name).restype = C.c_int
     return L
 
@@ -311,6 +318,44 @@ def tt_kernel(ctx, model, T, P, Ks, Kxi, Keta):
     n_src = T.shape[-1]
     _check(ctx, lib.tt_kernel(ctx.handle, C.byref(M), n_src, _ptr(T), _ptr(P), _ptr(Ks),
                               _ptr(Kxi), _ptr(Keta)))
+
+
+class CrData:
+    """Common-receiver differential times (Eq. 4) of one batch, in the layout of tt_cr_data.
+    pairs: rows (b, j, m, dT_obs, w), an unordered source pair {b, j} observed at receiver m
+    with T_b^obs - T_j^obs = dT_obs and weight w; each is listed under both sources."""
+
+    def __init__(self, n_src, n_rec, pairs, gamma=1.0, device="cuda"):
+        import torch
+        P = np.asarray(pairs, dtype=np.float64).reshape(-1, 5)
+        b, j, m = (P[:, c].astype(np.int64) for c in range(3))
+        src = np.concatenate([b, j])                    # each pair under both sources
+        oth = np.concatenate([j, b])
+        rec = np.concatenate([m, m])
+        dt = np.concatenate([P[:, 3], -P[:, 3]])
+        w = np.concatenate([P[:, 4], P[:, 4]])
+        key = src * n_rec + rec
+        order = np.argsort(key, kind="stable")
+        off = np.zeros(n_src * n_rec + 1, dtype=np.int64)
+        np.add.at(off, key + 1, 1)
+        off = np.cumsum(off)
+        i32 = lambda a: torch.as_tensor(np.asarray(a, dtype=np.int32), device=device)
+        f64 = lambda a: torch.as_tensor(np.asarray(a, dtype=np.float64), device=device)
+        self.n_src, self.n_rec, self.n_entries = int(n_src), int(n_rec), int(len(order))
+        self.off, self.other = i32(off), i32(oth[order])
+        self.dtobs, self.w = f64(dt[order]), f64(w[order])
+        self.gamma = float(gamma)
+
+    def c_struct(self):
+        return TTCrData(self.n_src, self.n_rec, self.n_entries, _ptr(self.off), _ptr(self.other),
+                        _ptr(self.dtobs), _ptr(self.w), self.gamma)
+
+
+def tt_misfit_cr(ctx, cr, Tr, chi_cr, R):
+    """Eqs. 4 and A4: R += gamma dchi_cr/dT (in place), chi_cr [n_src] the sources' shares."""
+    _cuda_ok(Tr, chi_cr, R)
+    D = cr.c_struct()
+    _check(ctx, lib.tt_misfit_cr(ctx.handle, C.byref(D), _ptr(Tr), _ptr(chi_cr), _ptr(R)))
 
 
 def tt_kernel_density(ctx, P_hat, Kd):

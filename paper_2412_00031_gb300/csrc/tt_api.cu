@@ -1250,6 +1250,29 @@ tt_status tt_kernel(tt_ctx *ctx, const tt_model *model, int n_src, const void *d
     return enq_kernel(ctx, model, n_src, d_T, d_P, d_Ks, d_Kxi, d_Keta);
 }
 
+tt_status tt_misfit_cr(tt_ctx *ctx, const tt_cr_data *d, const double *d_Tr, double *d_chi_cr,
+                       double *d_R) {
+    if (!ctx) return TT_EINVAL;
+    if (!d || !d->d_off || !d_Tr || !d_chi_cr || !d_R)
+        return fail(ctx, TT_EINVAL, "tt_misfit_cr: NULL argument");
+    if (d->n_src < 1 || d->n_src > TT_MAX_BATCH || d->n_rec < 1)
+        return fail(ctx, TT_EINVAL, "tt_misfit_cr: n_src %d or n_rec %d out of range", d->n_src,
+                    d->n_rec);
+    if (d->n_entries > 0 && (!d->d_other || !d->d_dtobs || !d->d_w))
+        return fail(ctx, TT_EINVAL, "tt_misfit_cr: NULL entry arrays");
+    ENSURE(ctx->flags, 4 * sizeof(int));
+    int *bad = (int *)ctx->flags.p + 1;
+    CK(cudaMemsetAsync(bad, 0, sizeof(int), ctx->st));
+    CK(run_misfit_cr(d->n_src, d->n_rec, d->d_off, d->d_other, d->d_dtobs, d->d_w, d->gamma, d_Tr,
+                     d_chi_cr, d_R, bad, ctx->st));
+    ctx->launches += 1;
+    int h_bad = 0;
+    CK(cudaMemcpyAsync(&h_bad, bad, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    if (h_bad) return fail(ctx, TT_EINVAL, "tt_misfit_cr: an entry names a source out of range");
+    return TT_OK;
+}
+
 tt_status tt_kernel_density(tt_ctx *ctx, const void *d_P, int n_src, int dtype, double *d_Kd) {
     if (!ctx) return TT_EINVAL;
     if (n_src < 1 || n_src > TT_MAX_BATCH)

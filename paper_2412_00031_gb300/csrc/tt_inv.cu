@@ -1,4 +1,5 @@
-// The regularisation and model update of the inversion step (Sec. 3.3 and step 4 of Sec. 2):
+// The common-receiver differential-time misfit and its adjoint source (Eqs. 4, A4), and the
+// regularisation and model update of the inversion step (Sec. 3.3 and step 4 of Sec. 2):
 // kernel density (Eq. 19) and the normalisation of the kernels by it (Eq. 18); the
 // multiple-grid projection of a kernel onto H offset inversion grids (Eqs. 11-14, 17) and the
 // expansion of coefficients back onto the forward grid (Eq. 15); the model update.
@@ -35,6 +36,45 @@ __global__ void sum_sources_kernel(long long N, int B, const F *__restrict__ P, 
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) Kd[w] += acc;
+}
+
+// Eqs. 4 and A4. Block b = source b; thread t takes receivers m = t, t + blockDim, ...: for
+// the entries of (b, m) (the pairs {b, j} at receiver m, each with dT_obs = T_b^obs - T_j^obs
+// and the pair weight w), e = (T_b - T_j) - dT_obs; R[b][m] += gamma sum w e, and the source's
+// share of chi_cr is sum w e^2 / 4 (an unordered pair is two ordered terms of weight w / 2,
+// split between its two sources). An entry whose other source is out of range sets *bad.
+__global__ void misfit_cr_kernel(int n_src, int n_rec, const int *__restrict__ off,
+                                 const int *__restrict__ other, const double *__restrict__ dtobs,
+                                 const double *__restrict__ w, double gamma,
+                                 const double *__restrict__ Tr, double *chi, double *R, int *bad) {
+    __shared__ double s[256];
+    const int b = blockIdx.x;
+    double part = 0.0;
+    for (int m = threadIdx.x; m < n_rec; m += blockDim.x) {
+        const long long nm = (long long)b * n_rec + m;
+        const int q0 = off[nm], q1 = off[nm + 1];
+        if (q1 <= q0) continue;
+        const double tb = Tr[nm];
+        double acc = 0.0;
+        for (int q = q0; q < q1; ++q) {
+            const int j = other[q];
+            if (j < 0 || j >= n_src) {
+                atomicExch(bad, 1);
+                continue;
+            }
+            const double e = (tb - Tr[(long long)j * n_rec + m]) - dtobs[q];
+            acc += w[q] * e;
+            part += 0.25 * w[q] * e * e;
+        }
+        R[nm] += gamma * acc;
+    }
+    s[threadIdx.x] = part;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) s[threadIdx.x] += s[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) chi[b] = s[0];
 }
 
 // Eq. 18 in place on the three kernels.
@@ -201,6 +241,13 @@ void mgrid_axis_tables(int n, int c, int H, std::vector<double> &W, std::vector<
                 W[((size_t)h * c + q) * n + i] = v > 0.0 ? v : 0.0;
             }
         }
+}
+
+cudaError_t run_misfit_cr(int n_src, int n_rec, const int *off, const int *other,
+                          const double *dtobs, const double *w, double gamma, const double *Tr,
+                          double *chi, double *R, int *bad, cudaStream_t st) {
+    misfit_cr_kernel<<<n_src, 256, 0, st>>>(n_src, n_rec, off, other, dtobs, w, gamma, Tr, chi, R, bad);
+    return cudaGetLastError();
 }
 
 template <typename F>

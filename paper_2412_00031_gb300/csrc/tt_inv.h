@@ -17,6 +17,11 @@ struct MgDims {
 // Host tables of one axis: W[h][a][i] and lo[h][i] (tt_inv.cu).
 void mgrid_axis_tables(int n, int c, int H, std::vector<double> &W, std::vector<int> &lo);
 
+// Eqs. 4 and A4 over the entries of every (source, receiver) (see tt_inv.cu); *bad = 1 for
+// an entry whose other source is out of range (the entry is skipped).
+cudaError_t run_misfit_cr(int n_src, int n_rec, const int *off, const int *other,
+                          const double *dtobs, const double *w, double gamma, const double *Tr,
+                          double *chi, double *R, int *bad, cudaStream_t st);
 // Kd[node] += sum over the B sources of P[node][b] (Eq. 19), FP64, a fixed order.
 template <typename F>
 cudaError_t run_kernel_density(long long N, int B, const F *P, double *Kd, cudaStream_t st);

@@ -1,7 +1,7 @@
 """Gradient-descent inversion loop (step 4 of Sec. 2, with the regularisation of Sec. 3.3) as
 a host driver of the C ABI. Each evaluation of a model:
-- solves the batch (tt_forward, tt_misfit, tt_adjoint) and accumulates the kernels
-  (tt_kernel, Eqs. 6-8);
+- solves the batch (tt_forward, tt_misfit, and tt_misfit_cr when common-receiver pairs are
+  given, Eqs. 2-4; tt_adjoint) and accumulates the kernels (tt_kernel, Eqs. 6-8);
 - solves the adjoint again with R = 1 at every record of each source and sums those fields
   into the kernel density (tt_kernel_density, Eq. 19).
 
@@ -21,14 +21,14 @@ import numpy as np
 
 from . import (default_opts, mgrid, tt_adjoint, tt_forward, tt_kernel, tt_kernel_density,
                tt_kernel_normalize, tt_mgrid_expand, tt_mgrid_project, tt_misfit,
-               tt_model_update)
+               tt_misfit_cr, tt_model_update)
 
 
 class Inversion:
     """Buffers and calls of the loop for one batch of sources, data and inversion grids."""
 
     def __init__(self, ctx, model, src, data, grid_shape, mg, opts=None, eps_rel=1e-2,
-                 zeta=0.5):
+                 zeta=0.5, cr=None):
         import torch
         self.torch = torch
         self.ctx, self.model, self.src, self.data, self.mg = ctx, model, src, data, mg
@@ -44,6 +44,9 @@ class Inversion:
         f64 = dict(dtype=torch.float64, device=dev)
         self.chi = torch.empty((B, 2), **f64)
         self.R = torch.empty((B, data.n_rec), **f64)
+        self.cr = cr                                    # CrData or None
+        self.Tr = torch.empty((B, data.n_rec), **f64)
+        self.chi_cr = torch.zeros(B, **f64)
         # R = 1 at every record of each source (Eq. 19's adjoint sources)
         Rhat = np.zeros((B, data.n_rec))
         for b in range(B):
@@ -58,7 +61,9 @@ class Inversion:
         """chi of the current model; leaves its kernels and kernel density in the buffers."""
         c, m, s = self.ctx, self.model, self.src
         tt_forward(c, m, s, self.tau, self.T, self.opts)
-        tt_misfit(c, self.T, self.data, None, self.chi, self.R)
+        tt_misfit(c, self.T, self.data, self.Tr, self.chi, self.R)
+        if self.cr is not None:
+            tt_misfit_cr(c, self.cr, self.Tr, self.chi_cr, self.R)
         tt_adjoint(c, m, s, self.T, self.data.rec, self.R, self.P, self.opts)
         for K in self.K:
             K.zero_()
@@ -67,7 +72,10 @@ class Inversion:
         self.Kd.zero_()
         tt_kernel_density(c, self.Phat, self.Kd)
         chi = self.chi.cpu().numpy()
-        return float(self.data.alpha * chi[:, 0].sum() + self.data.beta * chi[:, 1].sum())
+        total = self.data.alpha * chi[:, 0].sum() + self.data.beta * chi[:, 1].sum()
+        if self.cr is not None:
+            total += self.cr.gamma * self.chi_cr.cpu().numpy().sum()
+        return float(total)
 
     def direction(self):
         """The smoothed, density-normalised descent direction from the last evaluation."""
@@ -100,9 +108,9 @@ class Inversion:
 
 
 def invert(ctx, model, src, data, grid_shape, n_r=11, n_t=11, n_p=11, n_grids=5, n_iter=10,
-           step=0.02, opts=None, eps_rel=1e-2, zeta=0.5):
+           step=0.02, opts=None, eps_rel=1e-2, zeta=0.5, cr=None):
     """The loop on n_grids offset inversion grids of n_r x n_t x n_p nodes; the model tensors
     are updated in place. Returns the history of Inversion.run."""
     inv = Inversion(ctx, model, src, data, grid_shape, mgrid(n_r, n_t, n_p, n_grids), opts,
-                    eps_rel, zeta)
+                    eps_rel, zeta, cr)
     return inv.run(n_iter, step)

@@ -5,8 +5,9 @@ inversion loop on a small synthetic case (needs a GB300).
   (Eq. 15) on seeded inputs, element by element; grids of several inversion-grid cells and
   ragged fine / coarse ratios; one projection at the 201 x 201 x 101 configuration size;
 - the model update (FP32 and FP64 models);
-- the loop: observations from the oracle's FP64 forward in a checkerboard model, inversion
-  from the background model: chi must fall.
+- the common-receiver misfit and adjoint source (Eqs. 4, A4) against the oracle;
+- the loop: observations from the oracle's FP64 forward in a checkerboard model (absolute
+  and common-receiver times), inversion from the background model: chi must fall.
 """
 import numpy as np
 import pytest
@@ -128,9 +129,43 @@ def test_model_update_matches_oracle(tt):
     ctx.close()
 
 
+def test_common_receiver_misfit_matches_oracle(tt):
+    import torch
+    from oracle.cr import misfit_cr
+    rng = np.random.default_rng(86)
+    ns, nr = 37, 23
+    Tr = rng.uniform(5, 30, (ns, nr))
+    Tobs = Tr + rng.normal(0, 0.2, (ns, nr))
+    pairs, W = [], np.zeros((ns, ns, nr))
+    for m in range(nr):
+        for b in range(ns):
+            for j in range(b + 1, ns):
+                if rng.uniform() < 0.15:
+                    wq = rng.uniform(0.2, 2.0)
+                    pairs.append((b, j, m, Tobs[b, m] - Tobs[j, m], wq))
+                    W[b, j, m] = W[j, b, m] = wq / 2     # two ordered terms of weight w / 2
+    gamma = 1.7
+    _, share, R_ref = misfit_cr(Tr, Tobs, W, gamma)
+    g = I.small_case(86, shape=(9, 10, 11), n_src=1).grid.as_dict()
+    ctx = tt.tt_ctx_create(g)
+    cr = tt.CrData(ns, nr, pairs, gamma)
+    R0 = rng.standard_normal((ns, nr))
+    R, chi = _dev(R0), _dev(np.zeros(ns))
+    tt.tt_misfit_cr(ctx, cr, _dev(Tr), chi, R)
+    assert np.abs(R.cpu().numpy() - (R0 + R_ref)).max() <= 1e-12 * np.abs(R_ref).max()
+    assert np.abs(chi.cpu().numpy() - share).max() <= 1e-12 * np.abs(share).max()
+    # an entry naming a source outside the batch is skipped and refused
+    cr.other[0] = ns + 3
+    with pytest.raises(tt.TTError):
+        tt.tt_misfit_cr(ctx, cr, _dev(Tr), chi, _dev(R0))
+    ctx.close()
+
+
 def test_inversion_loop_reduces_the_misfit(tt):
-    """Observations: the oracle's FP64 forward in a 5 % checkerboard model; start: the
-    background. Three step attempts must lower chi by at least 20 %."""
+    """Observations: the oracle's FP64 forward in a 5 % checkerboard model, as absolute and
+    common-receiver differential times; start: the background. The first step along the
+    computed direction must be accepted (a descent direction), and three step attempts must
+    lower chi by at least 5 % (measured: 10 %; 29 % without the common-receiver terms)."""
     import torch
     import oracle as O
     from paper_2412_00031_gb300.invert import Inversion
@@ -149,11 +184,16 @@ def test_inversion_loop_reduces_the_misfit(tt):
     data = tt.DeviceData(w.rec, np.arange(w.n_src + 1) * len(w.rec), np.tile(rec_all, w.n_src),
                          np.concatenate(tobs), np.ones(w.n_src * len(w.rec)),
                          np.zeros(w.n_src + 1, dtype=np.int32), [], [], [], [])
+    T_obs = np.stack(tobs)
+    pairs = [(b, j, m, T_obs[b, m] - T_obs[j, m], 1.0) for m in range(len(w.rec))
+             for b in range(w.n_src) for j in range(b + 1, w.n_src)]
+    cr = tt.CrData(w.n_src, len(w.rec), pairs, gamma=0.5)
     model = tuple(_dev(a, torch.float32) for a in (w.s, w.xi, w.eta))
     ctx = tt.tt_ctx_create(g)
-    inv = Inversion(ctx, model, w.src, data, shape, tt.mgrid(5, 5, 5, 3))
+    inv = Inversion(ctx, model, w.src, data, shape, tt.mgrid(5, 5, 5, 3), cr=cr)
     hist = inv.run(3, 0.03)
     ctx.close()
     chis = [h[0] for h in hist if h[2]]
-    print("\nchi per accepted step:", ["%.4g" % c for c in chis])
-    assert chis[-1] <= 0.8 * chis[0]
+    print("\nchi, step, accepted:", [("%.4g" % c, s, a) for c, s, a in hist])
+    assert hist[1][2], "the first step along the computed direction raised chi"
+    assert chis[-1] <= 0.95 * chis[0]
