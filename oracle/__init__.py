@@ -35,6 +35,7 @@ def lib():
         L = C.CDLL(_build.build())
         L.or_forward.restype = C.c_int
         L.or_forward_hyperplane.restype = C.c_int
+        L.or_forward_godunov.restype = C.c_int
         L.or_adjoint.restype = C.c_int
         L.or_fixed_set_inflow.restype = C.c_double
         _lib = L
@@ -76,8 +77,10 @@ def T0(g, s, xi, eta, src):
     return T0, p0
 
 
-def forward(g, s, xi, eta, src, tol=1e-8, max_iter=500, tau_init=None, hyperplane=False):
-    """Returns (tau, T, iterations, converged, last_err)."""
+def forward(g, s, xi, eta, src, tol=1e-8, max_iter=500, tau_init=None, hyperplane=False,
+            scheme="lf"):
+    """Returns (tau, T, iterations, converged, last_err). scheme: "lf" (Lax-Friedrichs, R4) or
+    "godunov" (R11; isotropic models only: xi = eta = 0)."""
     G = make_grid(g)
     shape = (G.n_r, G.n_t, G.n_p)
     s, ps = _f(s); xi, px = _f(xi); eta, pe = _f(eta)
@@ -86,7 +89,11 @@ def forward(g, s, xi, eta, src, tol=1e-8, max_iter=500, tau_init=None, hyperplan
     init = None
     if tau_init is not None:
         init, pinit = _f(tau_init)
-    fn = lib().or_forward_hyperplane if hyperplane else lib().or_forward
+    if scheme == "godunov":
+        assert not hyperplane and not xi.any() and not eta.any(), "Godunov: isotropic models"
+        fn = lib().or_forward_godunov
+    else:
+        fn = lib().or_forward_hyperplane if hyperplane else lib().or_forward
     it = fn(C.byref(G), ps, px, pe, Point(*src), C.c_double(tol), C.c_int(max_iter),
             pinit if init is not None else None, tau.ctypes.data_as(_dp), T.ctypes.data_as(_dp),
             C.byref(conv), C.byref(err))

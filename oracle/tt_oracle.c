@@ -21,6 +21,13 @@
  *      8 orderings over every node; the point source of Eq. 5 is spread to the 8 corners
  *      of the receiver's cell with the trilinear weights of R8, divided by the node volume.
  *  R10 Kernel gradients: central differences of nodal T, one-sided on the faces.
+ *  R11 Godunov local solver (isotropic models, xi = eta = 0; an alternative to R4): one-sided
+ *      differences of tau toward the upwind neighbour of each axis, the neighbour with the
+ *      smaller first-order estimate of T = T0 tau (T0 at the neighbour taken as
+ *      T0_c (1 +- u_d / e_d), u = grad T0 / T0, e_d = 1 / (delta_d h_d)); tau_c is the
+ *      smallest root, over the 7 non-empty subsets of axes, of
+ *      sum_d (a_d tau - b_d)^2 = (s / T0)^2 (the larger root of each quadratic) whose
+ *      one-sided differences all have the upwind sign; with no such root tau_c is kept.
  */
 #include "tt_oracle.h"
 
@@ -275,6 +282,49 @@ static double lf_update(const geo *G, const source_factor *S, const double *s,
     return num / den;
 }
 
+/* Godunov update of tau at interior node (i,j,k) (R11; xi = eta = 0). With sigma_d = +1 for a
+ * backward (lower-neighbour) difference and -1 for a forward one, the physical gradient over
+ * T0 along axis d is a_d tau_c - b_d, a_d = u_d + sigma_d e_d, b_d = sigma_d e_d tau_nb. */
+static double godunov_update(const geo *G, const source_factor *S, const double *s,
+                             const double *tau, int i, int j, int k)
+{
+    long c = idx(G, i, j, k);
+    double p0[3];
+    double T0 = factor_at(G, S, i, j, k, p0);
+    double r = rad_of(G, i), th = lat_of(G, j);
+    double h[3] = {1.0, h2_at(G, r), h3_at(G, r, th)};
+    double del[3] = {G->dr, G->dt, G->dp};
+    double tp[3], tm[3];
+    tp[0] = tau[idx(G, i + 1, j, k)]; tm[0] = tau[idx(G, i - 1, j, k)];
+    tp[1] = tau[idx(G, i, j + 1, k)]; tm[1] = tau[idx(G, i, j - 1, k)];
+    tp[2] = tau[idx(G, i, j, k + 1)]; tm[2] = tau[idx(G, i, j, k - 1)];
+    double a[3], b[3], sg[3];
+    for (int d = 0; d < 3; d++) {
+        double u = p0[d] / T0, e = 1.0 / (del[d] * h[d]);
+        /* T at the neighbours over T0_c, to first order */
+        double tlo = tm[d] * (1.0 - u / e), thi = tp[d] * (1.0 + u / e);
+        sg[d] = tlo <= thi ? 1.0 : -1.0;
+        double nb = tlo <= thi ? tm[d] : tp[d];
+        a[d] = u + sg[d] * e;
+        b[d] = sg[d] * e * nb;
+    }
+    double rhs = s[c] / T0;
+    double best = -1.0;
+    for (int mask = 1; mask < 8; mask++) {
+        double A = 0.0, B = 0.0, C = -rhs * rhs;
+        for (int d = 0; d < 3; d++)
+            if (mask >> d & 1) { A += a[d] * a[d]; B += a[d] * b[d]; C += b[d] * b[d]; }
+        double disc = B * B - A * C;
+        if (!(A > 0.0) || disc < 0.0) continue;
+        double t = (B + sqrt(disc)) / A;
+        int ok = 1;
+        for (int d = 0; d < 3; d++)
+            if ((mask >> d & 1) && sg[d] * (a[d] * t - b[d]) < 0.0) ok = 0;
+        if (ok && (best < 0.0 || t < best)) best = t;
+    }
+    return best < 0.0 ? tau[c] : best;
+}
+
 /* Face extrapolation after every sweep (R6). */
 static void extrapolate_faces(const geo *G, const source_factor *S, double *tau)
 {
@@ -319,8 +369,17 @@ static void extrapolate_faces(const geo *G, const source_factor *S, double *tau)
 static int swept(int q, int dir, int lo, int hi) { return dir > 0 ? lo + q : hi - q; }
 
 /* One sweep of the interior in lexicographic order (R5); returns the largest |change|. */
+/* The local solver of the chosen scheme: 0 = Lax-Friedrichs (R4), 1 = Godunov (R11). */
+static double local_update(const geo *G, const source_factor *S, const double *s,
+                           const double *xi, const double *eta, const double *tau, int i, int j,
+                           int k, int scheme)
+{
+    return scheme == 1 ? godunov_update(G, S, s, tau, i, j, k)
+                       : lf_update(G, S, s, xi, eta, tau, i, j, k);
+}
+
 static double sweep_lex(const geo *G, const source_factor *S, const double *s,
-                        const double *xi, const double *eta, double *tau, int o)
+                        const double *xi, const double *eta, double *tau, int o, int scheme)
 {
     int dr = (o & 4) ? -1 : 1, dt = (o & 2) ? -1 : 1, dp = (o & 1) ? -1 : 1;
     double err = 0.0;
@@ -332,7 +391,7 @@ static double sweep_lex(const geo *G, const source_factor *S, const double *s,
                 int k = swept(c, dp, 1, G->np - 2);
                 if (is_fixed(S, i, j, k)) continue;
                 long n = idx(G, i, j, k);
-                double v = lf_update(G, S, s, xi, eta, tau, i, j, k);
+                double v = local_update(G, S, s, xi, eta, tau, i, j, k, scheme);
                 err = fmax(err, fabs(v - tau[n]));
                 tau[n] = v;
             }
@@ -342,7 +401,7 @@ static double sweep_lex(const geo *G, const source_factor *S, const double *s,
 /* The same sweep visiting the nodes hyperplane by hyperplane (a + b + c = L, Sec. 3.4);
  * within a plane the nodes are visited in reverse lexicographic order on purpose. */
 static double sweep_planes(const geo *G, const source_factor *S, const double *s,
-                           const double *xi, const double *eta, double *tau, int o)
+                           const double *xi, const double *eta, double *tau, int o, int scheme)
 {
     int dr = (o & 4) ? -1 : 1, dt = (o & 2) ? -1 : 1, dp = (o & 1) ? -1 : 1;
     int na = G->nr - 2, nb = G->nt - 2, nc = G->np - 2;
@@ -357,7 +416,7 @@ static double sweep_planes(const geo *G, const source_factor *S, const double *s
                 int k = swept(c, dp, 1, G->np - 2);
                 if (is_fixed(S, i, j, k)) continue;
                 long n = idx(G, i, j, k);
-                double v = lf_update(G, S, s, xi, eta, tau, i, j, k);
+                double v = local_update(G, S, s, xi, eta, tau, i, j, k, scheme);
                 err = fmax(err, fabs(v - tau[n]));
                 tau[n] = v;
             }
@@ -366,7 +425,8 @@ static double sweep_planes(const geo *G, const source_factor *S, const double *s
 
 static int forward_impl(const or_grid *g, const double *s, const double *xi, const double *eta,
                         or_point src, double tol, int max_iter, const double *tau_init,
-                        double *tau, double *T, int *conv, double *last_err, int planes)
+                        double *tau, double *T, int *conv, double *last_err, int planes,
+                        int scheme)
 {
     geo G = make_geo(g);
     source_factor S = make_source(&G, s, xi, eta, src);
@@ -383,8 +443,8 @@ static int forward_impl(const or_grid *g, const double *s, const double *xi, con
     while (it < max_iter) {
         err = 0.0;
         for (int o = 0; o < 8; o++) {
-            double e = planes ? sweep_planes(&G, &S, s, xi, eta, tau, o)
-                              : sweep_lex(&G, &S, s, xi, eta, tau, o);
+            double e = planes ? sweep_planes(&G, &S, s, xi, eta, tau, o, scheme)
+                              : sweep_lex(&G, &S, s, xi, eta, tau, o, scheme);
             err = fmax(err, e);
             extrapolate_faces(&G, &S, tau);
         }
@@ -406,7 +466,16 @@ int or_forward(const or_grid *g, const double *s, const double *xi, const double
                or_point src, double tol, int max_iter, const double *tau_init,
                double *tau, double *T, int *conv, double *last_err)
 {
-    return forward_impl(g, s, xi, eta, src, tol, max_iter, tau_init, tau, T, conv, last_err, 0);
+    return forward_impl(g, s, xi, eta, src, tol, max_iter, tau_init, tau, T, conv, last_err, 0, 0);
+}
+
+/* The forward solve with the Godunov local solver (R11): xi and eta must be zero (isotropic);
+ * they enter only the factor's source values, as in or_forward. */
+int or_forward_godunov(const or_grid *g, const double *s, const double *xi, const double *eta,
+                       or_point src, double tol, int max_iter, const double *tau_init,
+                       double *tau, double *T, int *conv, double *last_err)
+{
+    return forward_impl(g, s, xi, eta, src, tol, max_iter, tau_init, tau, T, conv, last_err, 0, 1);
 }
 
 int or_forward_hyperplane(const or_grid *g, const double *s, const double *xi,
@@ -414,7 +483,7 @@ int or_forward_hyperplane(const or_grid *g, const double *s, const double *xi,
                           const double *tau_init, double *tau, double *T, int *conv,
                           double *last_err)
 {
-    return forward_impl(g, s, xi, eta, src, tol, max_iter, tau_init, tau, T, conv, last_err, 1);
+    return forward_impl(g, s, xi, eta, src, tol, max_iter, tau_init, tau, T, conv, last_err, 1, 0);
 }
 
 /* ---------------------------------------------------------------- misfit (Eqs. 2-3, A2-A3) */
@@ -698,7 +767,7 @@ void or_forward_sweeps(const or_grid *g, const double *s, const double *xi, cons
     long N = (long)G.nr * G.nt * G.np;
     for (long n = 0; n < N; n++) tau[n] = 1.0;
     for (int q = 0; q < n_sweeps; q++) {
-        sweep_lex(&G, &S, s, xi, eta, tau, q % 8);
+        sweep_lex(&G, &S, s, xi, eta, tau, q % 8, 0);
         extrapolate_faces(&G, &S, tau);
     }
 }
