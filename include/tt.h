@@ -119,6 +119,10 @@ typedef struct {
                                refill: one launch keeps S sources in flight and a source that
                                converges (or reaches max_iter_fwd) hands its slot to the next
                                one. Results and iteration counts do not depend on it. */
+    int scheme;             /* forward local solver: 0 = Lax-Friedrichs (Sec. 3.1, the paper's;
+                               any model); 1 = Godunov upwind (isotropic models only, xi = eta
+                               = 0: tt_forward returns TT_EINVAL otherwise, after the solve).
+                               Godunov runs on the node-hyperplane schedule. */
 } tt_opts;
 
 typedef struct tt_ctx tt_ctx;

@@ -80,7 +80,7 @@ def T0(g, s, xi, eta, src):
 def forward(g, s, xi, eta, src, tol=1e-8, max_iter=500, tau_init=None, hyperplane=False,
             scheme="lf"):
     """Returns (tau, T, iterations, converged, last_err). scheme: "lf" (Lax-Friedrichs, R4) or
-    "godunov" (R11; isotropic models only: xi = eta = 0)."""
+    "godunov" (R14; isotropic models only: xi = eta = 0)."""
     G = make_grid(g)
     shape = (G.n_r, G.n_t, G.n_p)
     s, ps = _f(s); xi, px = _f(xi); eta, pe = _f(eta)

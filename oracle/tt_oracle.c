@@ -21,7 +21,7 @@
  *      8 orderings over every node; the point source of Eq. 5 is spread to the 8 corners
  *      of the receiver's cell with the trilinear weights of R8, divided by the node volume.
  *  R10 Kernel gradients: central differences of nodal T, one-sided on the faces.
- *  R11 Godunov local solver (isotropic models, xi = eta = 0; an alternative to R4): one-sided
+ *  R14 Godunov local solver (isotropic models, xi = eta = 0; an alternative to R4): one-sided
  *      differences of tau toward the upwind neighbour of each axis, the neighbour with the
  *      smaller first-order estimate of T = T0 tau (T0 at the neighbour taken as
  *      T0_c (1 +- u_d / e_d), u = grad T0 / T0, e_d = 1 / (delta_d h_d)); tau_c is the
@@ -282,7 +282,7 @@ static double lf_update(const geo *G, const source_factor *S, const double *s,
     return num / den;
 }
 
-/* Godunov update of tau at interior node (i,j,k) (R11; xi = eta = 0). With sigma_d = +1 for a
+/* Godunov update of tau at interior node (i,j,k) (R14; xi = eta = 0). With sigma_d = +1 for a
  * backward (lower-neighbour) difference and -1 for a forward one, the physical gradient over
  * T0 along axis d is a_d tau_c - b_d, a_d = u_d + sigma_d e_d, b_d = sigma_d e_d tau_nb. */
 static double godunov_update(const geo *G, const source_factor *S, const double *s,
@@ -369,7 +369,7 @@ static void extrapolate_faces(const geo *G, const source_factor *S, double *tau)
 static int swept(int q, int dir, int lo, int hi) { return dir > 0 ? lo + q : hi - q; }
 
 /* One sweep of the interior in lexicographic order (R5); returns the largest |change|. */
-/* The local solver of the chosen scheme: 0 = Lax-Friedrichs (R4), 1 = Godunov (R11). */
+/* The local solver of the chosen scheme: 0 = Lax-Friedrichs (R4), 1 = Godunov (R14). */
 static double local_update(const geo *G, const source_factor *S, const double *s,
                            const double *xi, const double *eta, const double *tau, int i, int j,
                            int k, int scheme)
@@ -469,7 +469,7 @@ int or_forward(const or_grid *g, const double *s, const double *xi, const double
     return forward_impl(g, s, xi, eta, src, tol, max_iter, tau_init, tau, T, conv, last_err, 0, 0);
 }
 
-/* The forward solve with the Godunov local solver (R11): xi and eta must be zero (isotropic);
+/* The forward solve with the Godunov local solver (R14): xi and eta must be zero (isotropic);
  * they enter only the factor's source values, as in or_forward. */
 int or_forward_godunov(const or_grid *g, const double *s, const double *xi, const double *eta,
                        or_point src, double tol, int max_iter, const double *tau_init,

@@ -48,7 +48,7 @@ void or_T0(const or_grid *g, const double *s, const double *xi, const double *et
 int or_forward(const or_grid *g, const double *s, const double *xi, const double *eta,
                or_point src, double tol, int max_iter, const double *tau_init,
                double *tau, double *T, int *conv, double *last_err);
-/* or_forward with the Godunov local solver (R11) for isotropic models (xi = eta = 0). */
+/* or_forward with the Godunov local solver (R14) for isotropic models (xi = eta = 0). */
 int or_forward_godunov(const or_grid *g, const double *s, const double *xi, const double *eta,
                        or_point src, double tol, int max_iter, const double *tau_init,
                        double *tau, double *T, int *conv, double *last_err);

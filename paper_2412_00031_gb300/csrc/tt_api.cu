@@ -54,7 +54,7 @@ struct tt_ctx {
     // inversion step: multiple-grid tables (for mg_key), projection scratch, update scratch
     DevBuf mg_tab, mg_scr, upd_part;
     int mg_key[4] = {0, 0, 0, 0};
-    struct Tuned { int n_src, dtype, schedule, groups; };
+    struct Tuned { int n_src, dtype, scheme, schedule, groups; };
     std::vector<Tuned> tuned;
     int *h_pinned = nullptr;  // readback: [0..TT_MAX_BATCH) iterations, then flags
     PointD *h_pts = nullptr;  // staging for source / receiver positions
@@ -63,6 +63,7 @@ struct tt_ctx {
     cudaEvent_t ev_start[2] = {nullptr, nullptr}, ev_stop[2] = {nullptr, nullptr};
     cudaEvent_t ev_net[2] = {nullptr, nullptr};  // around the warm-start inference
     bool warm_last = false;                      // the last forward used the warm start
+    int scheme_last = 0;                         // local solver of the last forward
     tt_stats stats[2] = {};
     long long launches = 0;   // kernels launched by this context
 };
@@ -316,6 +317,7 @@ tt_status check_opts(tt_ctx *ctx, const tt_opts *o) {
     if (o->sweep_schedule < 0 || o->sweep_schedule > 1 + kNumTileShapes)
         return fail(ctx, TT_EINVAL, "sweep_schedule %d unknown", o->sweep_schedule);
     if (o->init < 0 || o->init > 2) return fail(ctx, TT_EINVAL, "init %d unknown", o->init);
+    if (o->scheme < 0 || o->scheme > 1) return fail(ctx, TT_EINVAL, "scheme %d unknown", o->scheme);
     if (o->fwd_slots < 0) return fail(ctx, TT_EINVAL, "fwd_slots %d < 0", o->fwd_slots);
     if (o->fwd_groups < 0 || o->fwd_groups > kMaxBarrierGroups)
         return fail(ctx, TT_EINVAL, "fwd_groups %d outside 0..%d", o->fwd_groups,
@@ -583,7 +585,7 @@ tt_status enq_forward(tt_ctx *ctx, Work<F> &W, const tt_model *m, int B, void *d
     // (B values) that are a multiple of 16 bytes. Automatic: node hyperplanes.
     const bool tiles_ok = B >= 32 && (B * sizeof(F)) % 16 == 0;
     int sched = o->sweep_schedule == 0 ? 1 : o->sweep_schedule;
-    if ((sched >= 2 && !tiles_ok) || W.n_slots > 0) sched = 1;
+    if ((sched >= 2 && !tiles_ok) || W.n_slots > 0 || o->scheme == 1) sched = 1;
     const int slice = W.t0c_slice;
 
     const GeoTab<F> &t = geo<F>(ctx);
@@ -591,6 +593,7 @@ tt_status enq_forward(tt_ctx *ctx, Work<F> &W, const tt_model *m, int B, void *d
     memset(&a, 0, sizeof a);
     a.g = g;
     a.B = B;
+    a.scheme = o->scheme;
     a.n_planes = ctx->interior.n_planes;
     a.er = (F)(0.5 / g.dr);
     a.rec = W.rec;
@@ -656,7 +659,8 @@ tt_status enq_forward(tt_ctx *ctx, Work<F> &W, const tt_model *m, int B, void *d
         a.src_n = S;
         a.idx32 = (unsigned long long)g.N * (unsigned long long)(S > 8 ? S : 8) < (1ull << 32);
         const int block = 256;
-        int per_sm = forward_blocks_per_sm<F>(block, fwd_smem_bytes<F>(S, block), a.idx32 != 0);
+        int per_sm = forward_blocks_per_sm<F>(block, fwd_smem_bytes<F>(S, block), a.idx32 != 0,
+                                              a.scheme);
         if (per_sm <= 0) return fail(ctx, TT_ECUDA, "sweep kernel cannot be resident");
         if (per_sm > kMaxBarrierGroups) per_sm = kMaxBarrierGroups;
         int max_grid = per_sm * ctx->n_sm;
@@ -690,7 +694,8 @@ tt_status enq_forward(tt_ctx *ctx, Work<F> &W, const tt_model *m, int B, void *d
             // 256-thread blocks; one barrier group per resident block slot of an SM, so
             // each SM interleaves the groups; each group gets a multiple of 32 sources.
             const int block = 256;
-            int per_sm = forward_blocks_per_sm<F>(block, fwd_smem_bytes<F>(n, block), a.idx32 != 0);
+            int per_sm = forward_blocks_per_sm<F>(block, fwd_smem_bytes<F>(n, block), a.idx32 != 0,
+                                                  a.scheme);
             if (per_sm <= 0) return fail(ctx, TT_ECUDA, "sweep kernel cannot be resident");
             if (per_sm > kMaxBarrierGroups) per_sm = kMaxBarrierGroups;
             int max_grid = per_sm * ctx->n_sm;
@@ -958,8 +963,11 @@ tt_status solve_status(tt_ctx *ctx, int B, const PointD *src, int *h_iters, int 
     Readback r = readback_view(ctx);
     const int *hi = which == TT_STATS_FORWARD ? r.iters_f : r.iters_a;
     const int *hc = which == TT_STATS_FORWARD ? r.conv_f : r.conv_a;
-    if (which == TT_STATS_FORWARD && r.flags[0])
+    if (which == TT_STATS_FORWARD && (r.flags[0] & 1))
         return fail(ctx, TT_EINVAL, "%s: model has s <= 0 or xi^2 + eta^2 >= 1/4", what);
+    if (which == TT_STATS_FORWARD && ctx->scheme_last == 1 && (r.flags[0] & 2))
+        return fail(ctx, TT_EINVAL, "%s: the Godunov solver needs an isotropic model (xi = eta = 0)",
+                    what);
     if (which == TT_STATS_FORWARD && ctx->warm_last && r.flags[3])
         return fail(ctx, TT_ETIMEOUT, "%s: a device-side wait of the warm start exceeded its limit",
                     what);
@@ -1018,6 +1026,7 @@ tt_status forward_impl(tt_ctx *ctx, const tt_model *m, const tt_point *h_src, in
         return s;
     CK(cudaStreamSynchronize(ctx->st));
     ctx->warm_last = o->init == 2;
+    ctx->scheme_last = o->scheme;
     return solve_status(ctx, B, ctx->h_pts, h_iters, o->max_iter_fwd, "tt_forward",
                         TT_STATS_FORWARD);
 }
@@ -1080,6 +1089,7 @@ void tt_default_opts(tt_opts *o, int dtype) {
     o->adj_chunk = 0;
     o->fwd_groups = 0;
     o->fwd_slots = 0;
+    o->scheme = 0;
 }
 
 const char *tt_last_error(const tt_ctx *ctx) { return ctx ? ctx->err : "no context"; }
@@ -1444,7 +1454,7 @@ tt_status autotune_impl(tt_ctx *ctx, const tt_model *m, const tt_point *h_src, i
         }
         if (h_ms) h_ms[c] = ms;
     }
-    ctx->tuned.push_back({B, m->dtype, best_sched, best_groups});
+    ctx->tuned.push_back({B, m->dtype, opts->scheme, best_sched, best_groups});
     opts->sweep_schedule = best_sched;
     opts->fwd_groups = best_groups;
     return TT_OK;
@@ -1460,7 +1470,7 @@ extern "C" tt_status tt_autotune(tt_ctx *ctx, const tt_model *model, const tt_po
     if ((s = check_sources(ctx, h_src, n_src)) != TT_OK) return s;
     if ((s = check_opts(ctx, opts)) != TT_OK) return s;
     for (const auto &t : ctx->tuned)
-        if (t.n_src == n_src && t.dtype == model->dtype) {
+        if (t.n_src == n_src && t.dtype == model->dtype && t.scheme == opts->scheme) {
             opts->sweep_schedule = t.schedule;
             opts->fwd_groups = t.groups;
             if (h_ms)
@@ -1836,6 +1846,7 @@ tt_status tt_plan_run(tt_plan *p, int *h_iters_fwd, int *h_iters_adj) {
     if (r.flags[1]) return fail(ctx, TT_EINVAL, "tt_plan_run: receiver index out of range");
     if (r.flags[2]) return fail(ctx, TT_EINVAL, "tt_plan_run: receiver outside the grid");
     ctx->warm_last = p->opts.init == 2;
+    ctx->scheme_last = p->opts.scheme;
     tt_status sf = solve_status(ctx, p->B, p->h_src.data(), h_iters_fwd, p->opts.max_iter_fwd,
                                 "tt_plan_run (forward)", TT_STATS_FORWARD);
     if (sf != TT_OK && sf != TT_ENOTCONVERGED) return sf;

@@ -122,7 +122,9 @@ __global__ void node_record_kernel(GridC g, const F *s, const F *xi, const F *et
     int j = (int)(t % g.nt);
     int i = (int)(t / g.nt);
     double sv = ld_model(s, n), xv = ld_model(xi, n), ev = ld_model(eta, n);
-    if (!(sv > 0.0) || !(xv * xv + ev * ev < 0.25)) atomicExch(bad, 1);
+    // bit 0: an invalid model; bit 1: an anisotropic node (refused by the Godunov solver)
+    if (!(sv > 0.0) || !(xv * xv + ev * ev < 0.25)) atomicOr(bad, 1);
+    if (xv != 0.0 || ev != 0.0) atomicOr(bad, 2);
     double er = 0.5 / g.dr;
     double et = 0.5 / (g.dt * h2[i]);
     double ep = 0.5 / (g.dp * h2[i] * cost[j]);

@@ -180,6 +180,66 @@ __device__ __forceinline__ F lf_core(F invT0, F ur, F ut, F up, F tc, F trp, F t
     return mul_(num, R.invW);
 }
 
+// Godunov update of tau at an interior node (isotropic models, xi = eta = 0; an alternative to
+// lf_core with the same arguments). Along axis d, with e_d = 1 / (delta_d h_d) = 2 x the
+// record's half-spacing factor and u the factor's gradient over T0, a one-sided difference
+// toward neighbour tau_nb gives the gradient over T0 as a_d tau - b_d, a_d = u_d + sg_d e_d,
+// b_d = sg_d e_d tau_nb, sg_d = +1 for the lower neighbour, -1 for the upper. The upwind
+// neighbour is the one with the smaller first-order estimate of T: tau_- (e - u) against
+// tau_+ (e + u) (both scaled by e / T0_c). tau_new is the smallest root, over the 7
+// non-empty subsets of axes, of sum (a_d tau - b_d)^2 = (s / T0)^2 (the larger root of each
+// quadratic) whose one-sided differences all keep the upwind sign; with none, tau_c.
+// The quadratic is solved for the increment delta = tau - tau_c, with the current one-sided
+// gradients c_d = a_d tau_c - b_d = u_d tau_c + sg_d e_d (tau_c - tau_nb): its coefficients
+// shrink as the sweep converges, and the larger root is taken in the form without
+// cancellation, so FP32 reaches its rounding floor (the direct form of the coefficients
+// loses ~1e-5 of tau to cancellation, which the sweeps carry downstream undamped).
+template <typename F>
+__device__ __forceinline__ F godunov_core(F invT0, F ur, F ut, F up, F tc, F trp, F trm, F ttp,
+                                          F ttm, F tpp, F tpm, const NodeRec<F> &R, F er) {
+    const F u[3] = {ur, ut, up};
+    const F e[3] = {(F)2 * er, (F)2 * R.et, (F)2 * R.ep};
+    const F lo[3] = {trm, ttm, tpm}, hi[3] = {trp, ttp, tpp};
+    F a[3], c[3], sg[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const bool lower = mul_(lo[d], sub_(e[d], u[d])) <= mul_(hi[d], add_(e[d], u[d]));
+        sg[d] = lower ? (F)1 : (F)-1;
+        const F se = mul_(sg[d], e[d]);
+        a[d] = add_(se, u[d]);
+        c[d] = fma_(u[d], tc, mul_(se, sub_(tc, lower ? lo[d] : hi[d])));
+    }
+    const F rhs = mul_(R.s, invT0);
+    const F r2 = mul_(rhs, rhs);
+    F best = (F)0;
+    bool found = false;
+#pragma unroll
+    for (int mask = 1; mask < 8; ++mask) {
+        F A = 0, B = 0, C = -r2;
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+            if (mask >> d & 1) {
+                A = fma_(a[d], a[d], A);
+                B = fma_(a[d], c[d], B);
+                C = fma_(c[d], c[d], C);
+            }
+        const F disc = fma_(B, B, -mul_(A, C));
+        if (!(A > (F)0) || disc < (F)0) continue;
+        const F q = sqrt_(disc);
+        // the larger root of A delta^2 + 2 B delta + C = 0
+        const F dl = B >= (F)0 ? div_(-C, add_(B, q)) : div_(sub_(q, B), A);
+        bool ok = true;
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+            if ((mask >> d & 1) && mul_(sg[d], fma_(a[d], dl, c[d])) < (F)0) ok = false;
+        if (ok && (!found || dl < best)) {
+            best = dl;
+            found = true;
+        }
+    }
+    return found ? add_(tc, best) : tc;
+}
+
 // ---------------------------------------------------------------------------------------
 // Grid-wide barrier for persistent cooperative launches. Arrivals go to a monotonic
 // per-launch counter: barrier number m of a launch is complete once m * nblocks arrivals

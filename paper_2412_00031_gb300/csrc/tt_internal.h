@@ -38,6 +38,7 @@ template <typename F> struct GeoTab {
 template <typename F> struct FwdArgs {
     GridC g;
     int B, slots, n_planes;
+    int scheme;                // local solver: 0 Lax-Friedrichs, 1 Godunov (isotropic models)
     F er;                      // 1 / (2 dr)
     const NodeRec<F> *rec;
     F *tau;
@@ -116,7 +117,7 @@ template <typename F> cudaError_t launch_forward(const FwdArgs<F> &a, int grid, 
                                                  cudaStream_t st);
 template <typename F> cudaError_t launch_adjoint(const AdjArgs<F> &a, int grid, int block,
                                                  cudaStream_t st);
-template <typename F> int forward_blocks_per_sm(int block, size_t smem, bool idx32);
+template <typename F> int forward_blocks_per_sm(int block, size_t smem, bool idx32, int scheme = 0);
 template <typename F> cudaError_t launch_t0_cache(const FwdArgs<F> &a, cudaStream_t st);
 // Slot table of the retire-and-refill mode: slot s < n_slots takes source s.
 template <typename F> cudaError_t launch_refill_setup(const FwdArgs<F> &a, cudaStream_t st);

@@ -247,19 +247,22 @@ __device__ __forceinline__ Vec4<double> ld_stream(const Vec4<double> *p) {
 
 // Lax-Friedrichs update of one (node, source): tau at p, its six neighbours at p +- sr,
 // p +- st, p +- sp; c = the cached factors. Returns |change| (0 on the fixed set).
-template <typename F>
+template <typename F, int SCHEME>
 __device__ __forceinline__ F update_one(F *p, const F *v, const Vec4<F> &c, const NodeRec<F> &R,
                                         F er) {
     if (!(c.x > (F)0)) return (F)0;
-    const F tn = lf_core<F>(c.x, c.y, c.z, c.w, v[0], v[1], v[2], v[3], v[4], v[5], v[6], R, er);
+    const F tn = SCHEME == 1
+                     ? godunov_core<F>(c.x, c.y, c.z, c.w, v[0], v[1], v[2], v[3], v[4], v[5], v[6], R, er)
+                     : lf_core<F>(c.x, c.y, c.z, c.w, v[0], v[1], v[2], v[3], v[4], v[5], v[6], R, er);
     *p = tn;
     return fabs(tn - v[0]);
 }
 
 // I: index type of the [node][source] fields (32-bit when every index fits).
 // REFILL: the retire-and-refill mode (compiled separately, so that the resident launch
-// carries none of its code).
-template <typename F, typename I, bool REFILL>
+// carries none of its code). SCHEME: the local solver, 0 Lax-Friedrichs (lf_core), 1 Godunov
+// (godunov_core, isotropic models).
+template <typename F, typename I, bool REFILL, int SCHEME>
 __global__ void __launch_bounds__(256, TTGB_FWD_MIN_BLOCKS) fwd_sweep_kernel(FwdArgs<F> a) {
     constexpr int NS = kFwdSourcesPerLane;              // sources of one lane: l0 + 32 h
     extern __shared__ unsigned char smem_raw[];
@@ -354,7 +357,7 @@ __global__ void __launch_bounds__(256, TTGB_FWD_MIN_BLOCKS) fwd_sweep_kernel(Fwd
 #pragma unroll
                         for (int h = 0; h < NS; ++h)
                             if (act[h])
-                                err[h] = fmax_(err[h], update_one<F>(p + 32 * h, v[h], c[h], R, a.er));
+                                err[h] = fmax_(err[h], update_one<F, SCHEME>(p + 32 * h, v[h], c[h], R, a.er));
                         pk = pkn;
                     }
                 }
@@ -1152,14 +1155,24 @@ __global__ void __launch_bounds__(256, TTGB_ADJ_MIN_BLOCKS) adj_face_kernel(AdjA
 
 // ------------------------------------------------------------------------ launchers
 
+// The node-hyperplane sweep kernel of one variant.
+template <typename F> void *fwd_kernel_ptr(bool refill, bool idx32, int scheme) {
+    if (scheme == 1)
+        return refill ? (idx32 ? (void *)fwd_sweep_kernel<F, unsigned, true, 1>
+                               : (void *)fwd_sweep_kernel<F, long long, true, 1>)
+                      : (idx32 ? (void *)fwd_sweep_kernel<F, unsigned, false, 1>
+                               : (void *)fwd_sweep_kernel<F, long long, false, 1>);
+    return refill ? (idx32 ? (void *)fwd_sweep_kernel<F, unsigned, true, 0>
+                           : (void *)fwd_sweep_kernel<F, long long, true, 0>)
+                  : (idx32 ? (void *)fwd_sweep_kernel<F, unsigned, false, 0>
+                           : (void *)fwd_sweep_kernel<F, long long, false, 0>);
+}
+
 template <typename F>
 cudaError_t launch_forward(const FwdArgs<F> &a, int grid, int block, cudaStream_t st) {
     void *args[] = {const_cast<FwdArgs<F> *>(&a)};
     const size_t smem = fwd_smem_bytes<F>(a.grp_src, block);
-    void *fn = a.refill ? (a.idx32 ? (void *)fwd_sweep_kernel<F, unsigned, true>
-                                   : (void *)fwd_sweep_kernel<F, long long, true>)
-                        : (a.idx32 ? (void *)fwd_sweep_kernel<F, unsigned, false>
-                                   : (void *)fwd_sweep_kernel<F, long long, false>);
+    void *fn = fwd_kernel_ptr<F>(a.refill != 0, a.idx32 != 0, a.scheme);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(block), args, smem, st);
@@ -1182,10 +1195,9 @@ template <typename F> size_t fwd_smem_bytes(int grp_src, int) {
     return fwd_err_bytes<F>(grp_src);
 }
 
-template <typename F> int forward_blocks_per_sm(int block, size_t smem, bool idx32) {
+template <typename F> int forward_blocks_per_sm(int block, size_t smem, bool idx32, int scheme) {
     int n = 0;
-    void *fn = idx32 ? (void *)fwd_sweep_kernel<F, unsigned, false>
-                     : (void *)fwd_sweep_kernel<F, long long, false>;
+    void *fn = fwd_kernel_ptr<F>(false, idx32, scheme);
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return 0;
@@ -1308,8 +1320,8 @@ template cudaError_t launch_adjoint<float>(const AdjArgs<float> &, int, int, cud
 template cudaError_t launch_adjoint<double>(const AdjArgs<double> &, int, int, cudaStream_t);
 template size_t fwd_smem_bytes<float>(int, int);
 template size_t fwd_smem_bytes<double>(int, int);
-template int forward_blocks_per_sm<float>(int, size_t, bool);
-template int forward_blocks_per_sm<double>(int, size_t, bool);
+template int forward_blocks_per_sm<float>(int, size_t, bool, int);
+template int forward_blocks_per_sm<double>(int, size_t, bool, int);
 template int adjoint_blocks_per_sm<float>(int, size_t);
 template int adjoint_blocks_per_sm<double>(int, size_t);
 

@@ -1,0 +1,116 @@
+"""The Godunov local solver on the GPU (opts.scheme = 1, isotropic models) against the
+oracle's Godunov solver (reading R14), through the C ABI (needs a GB300).
+
+- FP64 batch: traveltime to 1e-10 of the oracle and the same iteration counts;
+- FP32 batch: traveltime to the 1e-5 bar of the FP32 path;
+- retire-and-refill and barrier-group variants: bitwise the resident launch;
+- an anisotropic model is refused;
+- a 41^3 checkerboard: a few iterations where Lax-Friedrichs needs a count growing with the
+  grid;
+- the 81^3 isotropic checkerboard at full size (64 sources) against oracle solves of sampled
+  sources.
+"""
+import numpy as np
+import pytest
+
+import tt_inputs as I
+from gpu_helpers import gpu_solve, rel_linf, rounded_model
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tt():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2412_00031_gb300 as m
+    return m
+
+
+def _isotropic(seed, shape, n_src, amp=0.05):
+    w = I.small_case(seed, shape=shape, n_src=n_src, n_rec=4)
+    i, j, k = np.meshgrid(*[np.arange(n) for n in shape], indexing="ij")
+    w.s = (1 / 6.0) * (1 + amp * np.sin(np.pi * i / 6) * np.sin(np.pi * j / 5) *
+                       np.sin(np.pi * k / 7))
+    w.xi = np.zeros(shape)
+    w.eta = np.zeros(shape)
+    return w
+
+
+def _opts(tt, code, **kw):
+    return tt.default_opts(code, scheme=1, **kw)
+
+
+def test_fp64_batch_matches_the_oracle(tt):
+    import oracle as O
+    w = _isotropic(101, (13, 14, 15), 5)
+    out = gpu_solve(w, "f64", opts=_opts(tt, tt.TT_F64, tol_fwd=1e-12, max_iter_fwd=200),
+                    steps=("fwd",))
+    g = w.grid.as_dict()
+    for b in range(w.n_src):
+        _, T, it, conv, _ = O.forward(g, w.s, w.xi, w.eta, w.src[b], tol=1e-12, max_iter=200,
+                                      scheme="godunov")
+        assert conv
+        assert rel_linf(out["T"][..., b], T) <= 1e-10
+        assert abs(int(out["iters_fwd"][b]) - it) <= 1
+
+
+def test_fp32_batch_meets_the_bar(tt):
+    import oracle as O
+    w = _isotropic(102, (17, 16, 18), 40)
+    out = gpu_solve(w, "f32", opts=_opts(tt, tt.TT_F32), steps=("fwd",))
+    s, xi, eta = rounded_model(w, "f32")
+    g = w.grid.as_dict()
+    for b in (0, 17, 39):
+        _, T, it, conv, _ = O.forward(g, s, xi, eta, w.src[b], tol=1e-10, max_iter=200,
+                                      scheme="godunov")
+        assert conv
+        assert rel_linf(out["T"][..., b], T) <= 1e-5
+    assert int(np.max(out["iters_fwd"])) <= 10
+
+
+def test_launch_variants_are_bitwise(tt):
+    w = _isotropic(103, (15, 13, 17), 96)
+    ref = gpu_solve(w, "f32", opts=_opts(tt, tt.TT_F32), steps=("fwd",))
+    for kw in ({"fwd_groups": 1}, {"fwd_groups": 3}, {"fwd_slots": 32}):
+        out = gpu_solve(w, "f32", opts=_opts(tt, tt.TT_F32, **kw), steps=("fwd",))
+        assert np.array_equal(out["tau"], ref["tau"]), kw
+        assert np.array_equal(out["iters_fwd"], ref["iters_fwd"]), kw
+
+
+def test_anisotropic_model_is_refused(tt):
+    w = I.small_case(104, shape=(9, 10, 11), n_src=2, n_rec=3)
+    assert np.abs(w.xi).max() > 0
+    with pytest.raises(tt.TTError, match="isotropic"):
+        gpu_solve(w, "f32", opts=_opts(tt, tt.TT_F32), steps=("fwd",))
+
+
+def test_few_iterations_against_lax_friedrichs(tt):
+    w = _isotropic(105, (41, 41, 41), 8)
+    god = gpu_solve(w, "f32", opts=_opts(tt, tt.TT_F32), steps=("fwd",))
+    lf = gpu_solve(w, "f32", steps=("fwd",))
+    print("\nmean iterations: Godunov %.1f, Lax-Friedrichs %.1f" %
+          (np.mean(god["iters_fwd"]), np.mean(lf["iters_fwd"])))
+    assert np.max(god["iters_fwd"]) <= 8
+    assert np.mean(lf["iters_fwd"]) >= 2 * np.mean(god["iters_fwd"])
+
+
+@pytest.mark.slow
+def test_checkerboard_81_batch_against_oracle_solves(tt):
+    """The 81^3 isotropic checkerboard, 64 sources, FP32 Godunov batch: complete FP64 oracle
+    Godunov solves of the first and last source (traveltime to the 1e-5 bar); the source
+    alone gives its batch column's bits; no source needs more than 10 iterations."""
+    import oracle as O
+    w = I.checkerboard_81()
+    out = gpu_solve(w, "f32", opts=_opts(tt, tt.TT_F32), steps=("fwd",))
+    s, xi, eta = rounded_model(w, "f32")
+    g = w.grid.as_dict()
+    for b in (0, w.n_src - 1):
+        _, T, it, conv, _ = O.forward(g, s, xi, eta, w.src[b], tol=1e-10, max_iter=200,
+                                      scheme="godunov")
+        assert conv
+        assert rel_linf(out["T"][..., b], T) <= 1e-5
+    one = gpu_solve(w.subset([w.n_src - 1]), "f32", opts=_opts(tt, tt.TT_F32), steps=("fwd",))
+    assert np.array_equal(one["T"][..., 0], out["T"][..., -1])
+    assert int(np.max(out["iters_fwd"])) <= 10

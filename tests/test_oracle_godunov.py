@@ -1,4 +1,4 @@
-"""Pins of the oracle's Godunov local solver (reading R11 of oracle/tt_oracle.c; isotropic
+"""Pins of the oracle's Godunov local solver (reading R14 of oracle/tt_oracle.c; isotropic
 models): the homogeneous closed form (T = s x chord, tau = 1 exactly), first-order accuracy
 against the arccosh traveltime of a linear velocity, a fixed point that does not depend on
 the start, and the iteration counts that motivate the scheme (a few iterations where the
