@@ -110,3 +110,35 @@ def kernels(R, grad):
             Kx[n] += R[n, m] * grad[n, m]
             Kt[n] += R[n, m]
     return Kx, Kt
+
+
+def update(g, pts, tau, Kx, Kt, step_km, step_s):
+    """One gradient-descent step of the event locations and origin times (reading R15b: the
+    paper names gradient descent and gives no step rule). Each event moves by
+    -step_km K_x,n / max_n |K_x,n| km in physical components (up, north, east): depth by
+    +step_km K_r / max, latitude by -step_km K_theta / (max h2) radians, longitude by
+    -step_km K_phi / (max h3) radians, with h2 = r, h3 = r cos(theta) at the event (R_E for
+    both in flat geometry); then it is clamped to the grid. Origin times move by
+    -step_s K_tau,n / max_n |K_tau,n|. A zero maximum moves nothing. Returns new copies."""
+    n, re, org, d, flat = _geometry(g)
+    get = (lambda k: g[k]) if isinstance(g, dict) else (lambda k: getattr(g, k))
+    pts = np.array(pts, dtype=np.float64)
+    tau = np.array(tau, dtype=np.float64)
+    mx = max(float(np.sqrt((K ** 2).sum())) for K in Kx)
+    mt = float(np.abs(Kt).max())
+    for q in range(len(pts)):
+        if mx > 0:
+            dx = -step_km * Kx[q] / mx
+            r = re - pts[q, 0]
+            th = pts[q, 1] * DEG
+            h2 = re if flat else r
+            h3 = re if flat else r * np.cos(th)
+            pts[q, 0] -= dx[0]
+            pts[q, 1] += dx[1] / h2 / DEG
+            pts[q, 2] += dx[2] / h3 / DEG
+            pts[q, 0] = min(max(pts[q, 0], get("depth_min_km")), get("depth_max_km"))
+            pts[q, 1] = min(max(pts[q, 1], get("lat_min_deg")), get("lat_max_deg"))
+            pts[q, 2] = min(max(pts[q, 2], get("lon_min_deg")), get("lon_max_deg"))
+        if mt > 0:
+            tau[q] -= step_s * Kt[q] / mt
+    return pts, tau

@@ -160,3 +160,22 @@ def test_reciprocity_of_receiver_and_source_solves():
     assert gaps[1] <= 1e-3
     assert gaps[1] <= 0.7 * gaps[0]
     assert eik <= 5e-3
+
+
+def test_update_hand_values():
+    """Reading R15b by hand: the event with the largest |K_x| moves step_km against it (a
+    pure +r gradient deepens the event by step_km; a pure theta gradient moves it south by
+    step_km / r radians); the others move in proportion; clamping stops at the grid."""
+    import oracle.reloc as L
+    g = _grid().as_dict()
+    pts = np.array([[20.0, 10.5, 20.7], [10.0, 10.2, 21.0], [39.9, 10.9, 20.1]])
+    Kx = np.array([[2.0, 0.0, 0.0], [0.0, 1.0, 0.0], [-0.5, 0.0, 0.0]])
+    Kt = np.array([0.5, -2.0, 0.0])
+    p, t = L.update(g, pts, np.zeros(3), Kx, Kt, 3.0, 0.1)
+    r1 = g["earth_radius_km"] - 10.0
+    np.testing.assert_allclose(p[0], [23.0, 10.5, 20.7], rtol=0, atol=1e-12)
+    np.testing.assert_allclose(p[1], [10.0, 10.2 - 1.5 / r1 * 180 / np.pi, 21.0], rtol=0, atol=1e-12)
+    assert abs(p[2, 0] - (39.9 - 0.75)) <= 1e-12                       # moves up 0.75 km
+    np.testing.assert_allclose(t, [-0.025, 0.1, 0.0], rtol=0, atol=1e-15)
+    p, _ = L.update(g, pts, np.zeros(3), -Kx, Kt, 3.0, 0.1)
+    assert p[2, 0] == 40.0                                             # clamped at depth_max
