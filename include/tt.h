@@ -10,6 +10,8 @@
  *   tt_adjoint  upwind fast-sweeping solve of the adjoint equation (Eq. 5)
  *   tt_kernel   FP64 accumulation of the sensitivity kernels K_s, K_xi, K_eta (Eqs. 6-8)
  *   tt_misfit_cr   common-receiver differential times (Eqs. 4, A4)
+ *   tt_field_at_points, tt_misfit_table, tt_reloc_kernels, tt_reloc_update
+ *                  earthquake location and origin-time kernels and update (Eq. 10, B1-B11)
  *   tt_kernel_density, tt_kernel_normalize, tt_mgrid_project, tt_mgrid_expand,
  *   tt_model_update   regularisation and update of the inversion step (Eqs. 11-19)
  *
@@ -256,6 +258,50 @@ tt_status tt_mgrid_expand(tt_ctx *ctx, const tt_mgrid *mg, const double *d_G, do
  * that raises chi) is the caller's loop. */
 tt_status tt_model_update(tt_ctx *ctx, const tt_model *model, const double *d_Ds,
                           const double *d_Dxi, const double *d_Deta, double step);
+
+/* ---- Earthquake location and origin time (Eq. 10, Appendix B, Eqs. B1-B11). ----
+ * By reciprocity the time from event n to receiver m equals Gamma_m(x_n), the traveltime of
+ * a wavefront started at receiver m (run tt_forward with the receivers as the sources), and
+ * the arrival is Gamma_m(x_n) + tau_n with origin time tau_n. The misfits of Eqs. 2-4 and
+ * their adjoint sources R = dchi/dT (Eqs. A2-A4) evaluated on those arrivals give
+ *   K_x,n = sum_m R[n][m] grad Gamma_m(x_n),  K_tau,n = sum_m R[n][m]   (Eqs. B5-B11). */
+
+/* Values and gradients at points of M batched fields. d_G: device [N][M] of dtype (the
+ * layout tt_forward writes, field index fastest). d_pts: device double [n_pts][3] (depth km,
+ * latitude deg, longitude deg). Outputs (device double): d_val [n_pts][M], the trilinear
+ * interpolant in index space (as for receiver times); d_grad [n_pts][M][3], its gradient
+ * in physical components (d/dr, d/(r dtheta), d/(r cos(theta) dphi)) at the point. So
+ * K_x is the exact derivative of the discrete misfit with respect to the position.
+ * TT_EINVAL for a point outside the grid (after synchronising the stream; that row is
+ * computed from the nearest cell and holds no meaning). */
+tt_status tt_field_at_points(tt_ctx *ctx, const void *d_G, int dtype, int n_fields, int n_pts,
+                             const double *d_pts, double *d_val, double *d_grad);
+
+/* Misfit (Eqs. 2-3) and adjoint sources (Eqs. A2-A3) from given arrivals rather than
+ * fields: Tr[n][m] = d_val[n][m] + d_otime[n] (d_otime device double [n_src] or NULL = 0).
+ * data as for tt_misfit (its h_rec is not read and may be NULL); outputs as tt_misfit:
+ * d_Tr (may be NULL), d_chi [n_src][2] (may be NULL), d_R [n_src][n_rec]. For the
+ * common-receiver terms pass d_Tr on to tt_misfit_cr, which adds into d_R.
+ * TT_EINVAL: a record naming a receiver out of range (after synchronising the stream). */
+tt_status tt_misfit_table(tt_ctx *ctx, const double *d_val, const double *d_otime,
+                          const tt_data *data, double *d_Tr, double *d_chi, double *d_R);
+
+/* The location and origin-time kernels: d_Kx [n_src][3] = sum_m d_R[n][m] d_grad[n][m]
+ * (physical components, as d_grad) and d_Ktau [n_src] = sum_m d_R[n][m]. Device doubles;
+ * d_R and d_grad as written by tt_misfit_table (+ tt_misfit_cr) and tt_field_at_points with
+ * the events as the points. Fixed-order sums (bitwise reproducible). */
+tt_status tt_reloc_kernels(tt_ctx *ctx, int n_src, int n_rec, const double *d_R,
+                           const double *d_grad, double *d_Kx, double *d_Ktau);
+
+/* One gradient-descent step of the events, in place (the paper names gradient descent and
+ * gives no step rule; this is the normalised step also used for the model): each event moves
+ * by -step_km d_Kx[n] / max_n |d_Kx[n]| km in physical components and is then clamped to
+ * the grid; d_otime[n] (may be NULL) moves by -step_s d_Ktau[n] / max_n |d_Ktau[n]|. A zero
+ * maximum moves nothing. d_pts as for tt_field_at_points. step_km, step_s >= 0 and finite,
+ * else TT_EINVAL. Step-size control is the caller's loop. */
+tt_status tt_reloc_update(tt_ctx *ctx, int n_src, double *d_pts, double *d_otime,
+                          const double *d_Kx, const double *d_Ktau, double step_km,
+                          double step_s);
 
 /* Largest receiver count tt_misfit_noalloc accepts: the size of its static scratch. */
 #define TT_NOALLOC_MAX_REC 1024

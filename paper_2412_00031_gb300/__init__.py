@@ -87,7 +87,8 @@ EXPORTED = ["tt_default_opts", "tt_ctx_create", "tt_ctx_destroy", "tt_last_error
             "tt_net_param_count", "tt_net_features", "tt_net_forward", "tt_net_loss_grad",
             "tt_net_adam", "tt_net_set_weights", "tt_autotune", "tt_net_infer",
             "tt_kernel_density", "tt_kernel_normalize", "tt_mgrid_project", "tt_mgrid_expand",
-            "tt_model_update", "tt_misfit_cr"]
+            "tt_model_update", "tt_misfit_cr", "tt_field_at_points", "tt_misfit_table",
+            "tt_reloc_kernels", "tt_reloc_update"]
 TT_NOALLOC_MAX_REC = 1024
 
 
@@ -138,12 +139,19 @@ def _load():
     L.tt_mgrid_project.argtypes = [C.c_void_p, C.POINTER(TTMgrid), C.c_void_p, C.c_void_p]
     L.tt_mgrid_expand.argtypes = [C.c_void_p, C.POINTER(TTMgrid), C.c_void_p, C.c_void_p]
     L.tt_model_update.argtypes = [C.c_void_p, C.POINTER(TTModel)] + [C.c_void_p] * 3 + [C.c_double]
+    L.tt_field_at_points.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int] + \
+        [C.c_void_p] * 3
+    L.tt_misfit_table.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(TTData)] + \
+        [C.c_void_p] * 3
+    L.tt_reloc_kernels.argtypes = [C.c_void_p, C.c_int, C.c_int] + [C.c_void_p] * 4
+    L.tt_reloc_update.argtypes = [C.c_void_p, C.c_int] + [C.c_void_p] * 4 + [C.c_double] * 2
     for name in ("tt_ctx_create", "tt_forward", "tt_misfit", "tt_adjoint", "tt_kernel",
                  "tt_get_stats", "tt_misfit_noalloc", "tt_plan_create", "tt_plan_run",
                  "tt_net_param_count", "tt_net_features", "tt_net_forward", "tt_net_loss_grad",
                  "tt_net_adam", "tt_net_set_weights", "tt_autotune", "tt_net_infer",
                  "tt_kernel_density", "tt_kernel_normalize", "tt_mgrid_project",
-                 "tt_mgrid_expand", "tt_model_update", "tt_misfit_cr"):
+                 "tt_mgrid_expand", "tt_model_update", "tt_misfit_cr", "tt_field_at_points",
+                 "tt_misfit_table", "tt_reloc_kernels", "tt_reloc_update"):
         getattr(L, name).restype = C.c_int
     return L
 
@@ -356,6 +364,38 @@ def tt_misfit_cr(ctx, cr, Tr, chi_cr, R):
     _cuda_ok(Tr, chi_cr, R)
     D = cr.c_struct()
     _check(ctx, lib.tt_misfit_cr(ctx.handle, C.byref(D), _ptr(Tr), _ptr(chi_cr), _ptr(R)))
+
+
+def tt_field_at_points(ctx, G, pts, val, grad):
+    """Values val [n_pts, M] and physical gradients grad [n_pts, M, 3] (float64) at the points
+    pts [n_pts, 3] (float64: depth km, lat deg, lon deg) of the M batched fields G [..., M]
+    (for relocation: tt_forward's T with the receivers as the sources)."""
+    _cuda_ok(G, pts, val, grad)
+    _check(ctx, lib.tt_field_at_points(ctx.handle, _ptr(G), _dtype_code(G), G.shape[-1],
+                                       pts.shape[0], _ptr(pts), _ptr(val), _ptr(grad)))
+
+
+def tt_misfit_table(ctx, val, otime, data, Tr=None, chi=None, R=None):
+    """tt_misfit on given arrivals Tr = val + otime[:, None] (otime may be None)."""
+    _cuda_ok(val, otime, Tr, chi, R)
+    D = data.c_struct()
+    _check(ctx, lib.tt_misfit_table(ctx.handle, _ptr(val), _ptr(otime), C.byref(D), _ptr(Tr),
+                                    _ptr(chi), _ptr(R)))
+
+
+def tt_reloc_kernels(ctx, R, grad, Kx, Ktau):
+    """Kx [n_src, 3] = sum_m R grad, Ktau [n_src] = sum_m R (Eqs. B5-B11)."""
+    _cuda_ok(R, grad, Kx, Ktau)
+    _check(ctx, lib.tt_reloc_kernels(ctx.handle, R.shape[0], R.shape[1], _ptr(R), _ptr(grad),
+                                     _ptr(Kx), _ptr(Ktau)))
+
+
+def tt_reloc_update(ctx, pts, otime, Kx, Ktau, step_km, step_s):
+    """One normalised gradient step of the event positions pts [n, 3] and origin times
+    otime [n] (may be None), in place."""
+    _cuda_ok(pts, otime, Kx, Ktau)
+    _check(ctx, lib.tt_reloc_update(ctx.handle, pts.shape[0], _ptr(pts), _ptr(otime), _ptr(Kx),
+                                    _ptr(Ktau), step_km, step_s))
 
 
 def tt_kernel_density(ctx, P_hat, Kd):

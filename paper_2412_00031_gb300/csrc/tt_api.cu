@@ -16,6 +16,7 @@
 #include "tt_aux.h"
 #include "tt_internal.h"
 #include "tt_inv.h"
+#include "tt_reloc.h"
 #include "tt_net.h"
 
 using namespace ttgb;
@@ -545,7 +546,6 @@ tt_status enq_warm_start(tt_ctx *ctx, Work<F> &W, const tt_model *m, int B, F *t
                          unsigned long long spin) {
     const GridC &g = ctx->g;
     const GeoTab<F> &t = geo<F>(ctx);
-    tt_status s;
     for (int b0 = 0; b0 < B; b0 += W.net_chunk) {
         const int nb = W.net_chunk < B - b0 ? W.net_chunk : B - b0;
         CK(run_net_features<F>(g, B, b0, nb, W.src, W.tabT, W.tabP, t.rad, t.cost,
@@ -1293,6 +1293,84 @@ tt_status tt_kernel_density(tt_ctx *ctx, const void *d_P, int n_src, int dtype, 
     const long long N = ctx->g.N;
     CK(dtype == TT_F32 ? run_kernel_density<float>(N, n_src, (const float *)d_P, d_Kd, ctx->st)
                        : run_kernel_density<double>(N, n_src, (const double *)d_P, d_Kd, ctx->st));
+    ctx->launches += 1;
+    return TT_OK;
+}
+
+tt_status tt_field_at_points(tt_ctx *ctx, const void *d_G, int dtype, int n_fields, int n_pts,
+                             const double *d_pts, double *d_val, double *d_grad) {
+    if (!ctx) return TT_EINVAL;
+    if (!d_G || !d_pts || !d_val || !d_grad)
+        return fail(ctx, TT_EINVAL, "tt_field_at_points: NULL argument");
+    if (dtype != TT_F32 && dtype != TT_F64)
+        return fail(ctx, TT_EINVAL, "dtype %d is neither TT_F32 nor TT_F64", dtype);
+    if (n_fields < 1 || n_fields > TT_MAX_BATCH || n_pts < 1 || n_pts > (1 << 24))
+        return fail(ctx, TT_EINVAL, "tt_field_at_points: n_fields %d or n_pts %d out of range",
+                    n_fields, n_pts);
+    ENSURE(ctx->flags, 4 * sizeof(int));
+    int *bad = (int *)ctx->flags.p + 1;
+    CK(cudaMemsetAsync(bad, 0, sizeof(int), ctx->st));
+    CK(dtype == TT_F32 ? run_field_at_points<float>(ctx->g, n_fields, n_pts, d_G, d_pts, d_val,
+                                                    d_grad, bad, ctx->st)
+                       : run_field_at_points<double>(ctx->g, n_fields, n_pts, d_G, d_pts, d_val,
+                                                     d_grad, bad, ctx->st));
+    ctx->launches += 1;
+    int h_bad = 0;
+    CK(cudaMemcpyAsync(&h_bad, bad, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    if (h_bad) return fail(ctx, TT_EINVAL, "tt_field_at_points: a point lies outside the grid");
+    return TT_OK;
+}
+
+tt_status tt_misfit_table(tt_ctx *ctx, const double *d_val, const double *d_otime,
+                          const tt_data *d, double *d_Tr, double *d_chi, double *d_R) {
+    if (!ctx) return TT_EINVAL;
+    if (!d || !d->d_abs_off || !d->d_cs_off || !d_val || !d_R)
+        return fail(ctx, TT_EINVAL, "tt_misfit_table: NULL argument");
+    if (d->n_src < 1 || d->n_src > TT_MAX_BATCH)
+        return fail(ctx, TT_EINVAL, "n_src = %d outside 1..%d", d->n_src, TT_MAX_BATCH);
+    if (d->n_rec < 1) return fail(ctx, TT_EINVAL, "need at least one receiver");
+    if ((size_t)d->n_rec * 2 * 4 * sizeof(double) > 200 * 1024)
+        return fail(ctx, TT_EINVAL, "n_rec = %d too large for the misfit kernel", d->n_rec);
+    ENSURE(ctx->flags, 4 * sizeof(int));
+    int *bad = (int *)ctx->flags.p + 1;
+    CK(cudaMemsetAsync(bad, 0, sizeof(int), ctx->st));
+    CK(run_misfit_table(d->n_src, d->n_rec, d_val, d_otime, *d, d_Tr, d_chi, d_R, bad, ctx->st));
+    ctx->launches += 1;
+    int h_bad = 0;
+    CK(cudaMemcpyAsync(&h_bad, bad, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    if (h_bad) return fail(ctx, TT_EINVAL, "tt_misfit_table: receiver index out of range in the data");
+    return TT_OK;
+}
+
+tt_status tt_reloc_kernels(tt_ctx *ctx, int n_src, int n_rec, const double *d_R,
+                           const double *d_grad, double *d_Kx, double *d_Ktau) {
+    if (!ctx) return TT_EINVAL;
+    if (!d_R || !d_grad || !d_Kx || !d_Ktau)
+        return fail(ctx, TT_EINVAL, "tt_reloc_kernels: NULL argument");
+    if (n_src < 1 || n_src > (1 << 24) || n_rec < 1 || n_rec > TT_MAX_BATCH)
+        return fail(ctx, TT_EINVAL, "tt_reloc_kernels: n_src %d or n_rec %d out of range", n_src,
+                    n_rec);
+    CK(run_reloc_kernels(n_src, n_rec, d_R, d_grad, d_Kx, d_Ktau, ctx->st));
+    ctx->launches += 1;
+    return TT_OK;
+}
+
+tt_status tt_reloc_update(tt_ctx *ctx, int n_src, double *d_pts, double *d_otime,
+                          const double *d_Kx, const double *d_Ktau, double step_km,
+                          double step_s) {
+    if (!ctx) return TT_EINVAL;
+    if (!d_pts || !d_Kx || !d_Ktau) return fail(ctx, TT_EINVAL, "tt_reloc_update: NULL argument");
+    if (n_src < 1 || n_src > (1 << 24))
+        return fail(ctx, TT_EINVAL, "tt_reloc_update: n_src %d out of range", n_src);
+    if (!(step_km >= 0.0 && step_km < 1e300) || !(step_s >= 0.0 && step_s < 1e300))
+        return fail(ctx, TT_EINVAL, "tt_reloc_update: steps must be finite and >= 0");
+    const tt_grid &gr = ctx->grid;
+    const GridBox box{{gr.depth_min_km, gr.lat_min_deg, gr.lon_min_deg},
+                      {gr.depth_max_km, gr.lat_max_deg, gr.lon_max_deg}};
+    CK(run_reloc_update(ctx->g, box, n_src, d_pts, d_otime, d_Kx, d_Ktau, step_km, step_s,
+                        ctx->st));
     ctx->launches += 1;
     return TT_OK;
 }

@@ -117,7 +117,6 @@ __global__ void node_record_kernel(GridC g, const F *s, const F *xi, const F *et
                                    int *bad) {
     long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= g.N) return;
-    int k = (int)(n % g.np);
     long long t = n / g.np;
     int j = (int)(t % g.nt);
     int i = (int)(t / g.nt);
@@ -240,9 +239,12 @@ __global__ void point_source_kernel(const int *heads, const int *n_heads, const 
 // Misfit of one source per warp. Lanes own receivers m = lane (mod 32); every record is
 // applied by the owner lanes in record order, so the adjoint sources are bitwise
 // reproducible. Dynamic shared memory: per warp, Tr[n_rec] and R[n_rec] in double.
-template <typename F>
+// TABLE = false: the receiver times are interpolated from the fields T (cq, wq);
+// TABLE = true: they are given, Tr[b][m] = tab[b][m] + otime[b] (otime may be NULL).
+template <typename F, bool TABLE>
 __global__ void misfit_kernel(int B, int n_rec, const F *T, const long long *cq,
-                              const double *wq, const int *abs_off, const int *abs_rec,
+                              const double *wq, const double *tab, const double *otime,
+                              const int *abs_off, const int *abs_rec,
                               const double *abs_tobs, const double *abs_w, const int *cs_off,
                               const int *cs_m, const int *cs_i, const double *cs_dtobs,
                               const double *cs_w, double alpha, double beta, double *Tr_out,
@@ -253,10 +255,15 @@ __global__ void misfit_kernel(int B, int n_rec, const F *T, const long long *cq,
     if (b >= B) return;
     double *Tr = sh + (size_t)warp * 2 * n_rec;
     double *R = Tr + n_rec;
+    const double t0 = TABLE && otime ? otime[b] : 0.0;
     for (int m = lane; m < n_rec; m += 32) {
         double acc = 0.0;
-        for (int c = 0; c < 8; ++c)
-            acc += wq[8 * m + c] * (double)T[cq[8 * m + c] * B + b];
+        if (TABLE) {
+            acc = tab[(long long)b * n_rec + m] + t0;
+        } else {
+            for (int c = 0; c < 8; ++c)
+                acc += wq[8 * m + c] * (double)T[cq[8 * m + c] * B + b];
+        }
         Tr[m] = acc;
         R[m] = 0.0;
         if (Tr_out) Tr_out[(long long)b * n_rec + m] = acc;
@@ -448,14 +455,33 @@ cudaError_t run_misfit(int B, int n_rec, const void *T, const long long *cq, con
     const int warps = 4;
     size_t smem = (size_t)warps * 2 * n_rec * sizeof(double);
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(misfit_kernel<F>,
+        cudaError_t e = cudaFuncSetAttribute(misfit_kernel<F, false>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
     }
-    misfit_kernel<F><<<blocks_for(B, warps), warps * 32, smem, st>>>(
-        B, n_rec, (const F *)T, cq, wq, d.d_abs_off, d.d_abs_rec, d.d_abs_tobs, d.d_abs_w,
-        d.d_cs_off, d.d_cs_m, d.d_cs_i, d.d_cs_dtobs, d.d_cs_w, d.alpha, d.beta, Tr, chi, R, bad);
+    misfit_kernel<F, false><<<blocks_for(B, warps), warps * 32, smem, st>>>(
+        B, n_rec, (const F *)T, cq, wq, nullptr, nullptr, d.d_abs_off, d.d_abs_rec, d.d_abs_tobs,
+        d.d_abs_w, d.d_cs_off, d.d_cs_m, d.d_cs_i, d.d_cs_dtobs, d.d_cs_w, d.alpha, d.beta, Tr, chi,
+        R, bad);
+    return cudaGetLastError();
+}
+
+cudaError_t run_misfit_table(int B, int n_rec, const double *tab, const double *otime,
+                             const tt_data &d, double *Tr, double *chi, double *R, int *bad,
+                             cudaStream_t st) {
+    const int warps = 4;
+    size_t smem = (size_t)warps * 2 * n_rec * sizeof(double);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(misfit_kernel<double, true>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    misfit_kernel<double, true><<<blocks_for(B, warps), warps * 32, smem, st>>>(
+        B, n_rec, nullptr, nullptr, nullptr, tab, otime, d.d_abs_off, d.d_abs_rec, d.d_abs_tobs,
+        d.d_abs_w, d.d_cs_off, d.d_cs_m, d.d_cs_i, d.d_cs_dtobs, d.d_cs_w, d.alpha, d.beta, Tr, chi,
+        R, bad);
     return cudaGetLastError();
 }
 

@@ -37,6 +37,11 @@ template <typename F>
 cudaError_t run_misfit(int B, int n_rec, const void *T, const long long *cq, const double *wq,
                        const tt_data &d, double *Tr, double *chi, double *R, int *bad,
                        cudaStream_t st);
+// The same misfit from given receiver times: Tr[b][m] = tab[b][m] + otime[b] (otime may be
+// NULL).
+cudaError_t run_misfit_table(int B, int n_rec, const double *tab, const double *otime,
+                             const tt_data &d, double *Tr, double *chi, double *R, int *bad,
+                             cudaStream_t st);
 template <typename F>
 cudaError_t run_kernel_accum(const GridC &g, int B, const void *s, const void *T, const void *P,
                              const double *h2, const double *cost, double *Ks, double *Kxi,

@@ -22,16 +22,13 @@ constexpr int kHalo = kHZ * kHY * kHX;
 constexpr int kCK = 8;  // input channels staged per pass
 constexpr int kConvThreads = kTZ * kTY * kTX;
 
-__device__ __forceinline__ float to_f(float v) { return v; }
-__device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
-
-// TIN: input element type (float, or BF16 activations of the inference path). OUT_BF16:
-// write ReLU(result) as BF16 (inference) instead of the FP32 result.
-template <int COUT, typename TIN = float, bool OUT_BF16 = false>
+// FP32 3x3x3 convolution of the training path (the inference path runs on the tensor cores,
+// tt_umma.cu).
+template <int COUT>
 __global__ void __launch_bounds__(kConvThreads)
-    conv3d_kernel(ConvDims d, int cin, const TIN *__restrict__ in, int relu_in,
+    conv3d_kernel(ConvDims d, int cin, const float *__restrict__ in, int relu_in,
                   const float *__restrict__ w, const float *__restrict__ bias,
-                  const float *__restrict__ gate, void *__restrict__ out_) {
+                  const float *__restrict__ gate, float *__restrict__ out) {
     __shared__ float s_in[kHalo * (kCK + 1)];  // odd channel stride: no bank conflicts
     __shared__ __align__(16) float s_w[27 * kCK * COUT];
     const int tiles_x = (d.W + kTX - 1) / kTX, tiles_y = (d.H + kTY - 1) / kTY;
@@ -43,7 +40,7 @@ __global__ void __launch_bounds__(kConvThreads)
     const int b = blockIdx.y;
     const int lx = threadIdx.x % kTX, ly = (threadIdx.x / kTX) % kTY, lz = threadIdx.x / (kTX * kTY);
     const size_t grid_nodes = (size_t)d.D * d.H * d.W;
-    const TIN *inb = in + (size_t)b * grid_nodes * cin;
+    const float *inb = in + (size_t)b * grid_nodes * cin;
     float acc[COUT];
 #pragma unroll
     for (int co = 0; co < COUT; ++co) acc[co] = bias ? bias[co] : 0.0f;
@@ -56,7 +53,7 @@ __global__ void __launch_bounds__(kConvThreads)
             const int z = z0 + hz - 1, y = y0 + hy - 1, x = x0 + hx - 1;
             float v = 0.0f;
             if (z >= 0 && z < d.D && y >= 0 && y < d.H && x >= 0 && x < d.W) {
-                v = to_f(inb[(((size_t)z * d.H + y) * d.W + x) * cin + c0 + c]);
+                v = inb[(((size_t)z * d.H + y) * d.W + x) * cin + c0 + c];
                 if (relu_in) v = fmaxf(v, 0.0f);
             }
             s_in[node * (kCK + 1) + c] = v;
@@ -83,12 +80,8 @@ __global__ void __launch_bounds__(kConvThreads)
 #pragma unroll
         for (int co = 0; co < COUT; ++co) {
             float v = acc[co];
-            if (OUT_BF16) {
-                reinterpret_cast<__nv_bfloat16 *>(out_)[o + co] = __float2bfloat16_rn(fmaxf(v, 0.0f));
-            } else {
-                if (gate && !(gate[o + co] > 0.0f)) v = 0.0f;
-                reinterpret_cast<float *>(out_)[o + co] = v;
-            }
+            if (gate && !(gate[o + co] > 0.0f)) v = 0.0f;
+            out[o + co] = v;
         }
     }
 }
