@@ -498,6 +498,114 @@ def infer_only(args):
             "gpu_launches_per_call": 5}
 
 
+def inversion_batches(tt, ctx, w, batch, dev):
+    """Observations of the 201 x 201 x 101 inversion workload from FP32 solves in its true
+    model (tt_forward + tt_misfit's receiver times) plus seeded Gaussian noise, and per-batch
+    data: absolute times, common-source pairs (differences of the noisy picks) and
+    common-receiver pairs of sources closer than meta["cr_deg"] within a batch."""
+    import torch
+    g = w.grid
+    true = tuple(torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32), device=dev)
+                 for a in w.meta["true"])
+    rng = np.random.default_rng(w.meta["noise_seed"])
+    out = []
+    for b0 in range(0, w.n_src, batch):
+        idx = list(range(b0, min(b0 + batch, w.n_src)))
+        sub = w.subset(idx)
+        B, nr = len(idx), len(w.rec)
+        d0 = tt.DeviceData.from_workload(sub, device=dev)
+        tau = torch.empty(g.shape + (B,), dtype=torch.float32, device=dev)
+        T = torch.empty_like(tau)
+        tt.tt_forward(ctx, true, sub.src, tau, T)
+        Tr = torch.empty((B, nr), dtype=torch.float64, device=dev)
+        R = torch.empty_like(Tr)
+        tt.tt_misfit(ctx, T, d0, Tr, None, R)
+        del tau, T
+        pick = Tr.cpu().numpy() + w.meta["noise_s"] * rng.standard_normal((B, nr))
+        abs_tobs = np.concatenate([pick[n, sub.abs_rec[sub.abs_off[n]:sub.abs_off[n + 1]]]
+                                   for n in range(B)])
+        cs_n = np.repeat(np.arange(B), np.diff(sub.cs_off))
+        cs_dtobs = pick[cs_n, sub.cs_m] - pick[cs_n, sub.cs_i]
+        data = tt.DeviceData(w.rec, sub.abs_off, sub.abs_rec, abs_tobs, sub.abs_w, sub.cs_off,
+                             sub.cs_m, sub.cs_i, cs_dtobs, sub.cs_w, device=dev)
+        seen = np.zeros((B, nr), dtype=bool)
+        for n in range(B):
+            seen[n, sub.abs_rec[sub.abs_off[n]:sub.abs_off[n + 1]]] = True
+        pairs = []
+        ep = sub.src[:, 1:]
+        for a in range(B):
+            close = np.nonzero(np.hypot(*(ep[a + 1:] - ep[a]).T) < w.meta["cr_deg"])[0] + a + 1
+            for j in close:
+                for m in np.nonzero(seen[a] & seen[j])[0]:
+                    pairs.append((a, j, m, pick[a, m] - pick[j, m], 1.0))
+        cr = tt.CrData(B, nr, pairs, gamma=1.0, device=dev) if pairs else None
+        out.append((sub.src, data, cr))
+    return out
+
+
+def inversion_leg(args):
+    """Times the inversion loop (step 4 of Sec. 2 with Eqs. 11-19, absolute, common-source and
+    common-receiver data) on the 201 x 201 x 101 workload, args.n_src sources in batches of
+    args.inv_batch, 5 offset 11^3 inversion grids, args.inversion step attempts. One JSON
+    line: wall time per step attempt (each attempt is one evaluation: forward, misfit and two
+    adjoints of every source, kernels, kernel density, then the direction)."""
+    import torch
+    import paper_2412_00031_gb300 as tt
+    from paper_2412_00031_gb300.invert import Inversion
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    w = I.inversion_201(n_src=args.inv_sources)
+    g = w.grid
+    ctx = tt.tt_ctx_create(g.as_dict())
+    t0 = time.perf_counter()
+    batches = inversion_batches(tt, ctx, w, args.inv_batch, dev)
+    t_obs = time.perf_counter() - t0
+    model = tuple(torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32), device=dev)
+                  for a in (w.s, w.xi, w.eta))
+    inv = Inversion(ctx, model, None, None, g.shape, tt.mgrid(11, 11, 11, 5), batches=batches)
+    times, hist = [], []
+    step, chi = 0.02, None
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    chi = inv.evaluate()
+    inv.direction()
+    torch.cuda.synchronize()
+    times.append(time.perf_counter() - t0)
+    hist.append((chi, step, True))
+    its = [float(np.mean(np.concatenate([b.iters_fwd for b in inv.batches])))]
+    for _ in range(args.inversion):
+        t0 = time.perf_counter()
+        saved = [a.clone() for a in model]
+        tt.tt_model_update(ctx, model, *inv.D, step)
+        new = inv.evaluate()
+        if new < chi:
+            chi = new
+            inv.direction()
+            hist.append((new, step, True))
+        else:
+            for a, b in zip(model, saved):
+                a.copy_(b)
+            hist.append((new, step, False))
+            step *= 0.5
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+        its.append(float(np.mean(np.concatenate([b.iters_fwd for b in inv.batches]))))
+    ctx.close()
+    n_cr = sum(b[2].n_entries for b in batches if b[2] is not None)
+    return {"metric": "inversion step time at 201x201x101 (depth x lat x lon), %d sources"
+                      % w.n_src, "value": float(np.mean(times[1:])) if len(times) > 1 else times[0],
+            "unit": "s per step attempt", "higher_is_better": False,
+            "first_evaluation_s": times[0], "step_s": times[1:], "observations_s": t_obs,
+            "chi": [h[0] for h in hist], "step": [h[1] for h in hist],
+            "accepted": [h[2] for h in hist], "iters_fwd_mean": its,
+            "config": {"workload": "inversion 201x201x101, %d sources in batches of %d, "
+                                   "400 stations, 5 offset 11^3 inversion grids" % (w.n_src, args.inv_batch),
+                       "abs_records": int(len(w.abs_rec)), "cs_pairs": int(len(w.cs_m)),
+                       "cr_entries": int(n_cr), "precision": "fp32 sweeps, fp64 misfit and kernels"},
+            "data": "synthetic: observations from FP32 solves in the true checkerboard model + "
+                    "N(0, 0.05 s)"}
+
+
 # ----------------------------------------------------------------------------- CPU oracle
 
 def oracle_sample(w, n_threads, n_src_sample, sweeps=1):
@@ -646,9 +754,17 @@ def main():
     ap.add_argument("--ref-iters-adj", type=float, default=4.0)
     ap.add_argument("--infer-only", type=int, default=0,
                     help="time only the warm start's inference on this many sources")
+    ap.add_argument("--inversion", type=int, default=0,
+                    help="time this many step attempts of the inversion loop on the "
+                         "201x201x101 workload instead of the benchmark step")
+    ap.add_argument("--inv-sources", type=int, default=1024)
+    ap.add_argument("--inv-batch", type=int, default=256)
     args = ap.parse_args()
     if args.infer_only > 0:
         print(json.dumps(infer_only(args)))
+        return
+    if args.inversion > 0:
+        print(json.dumps(inversion_leg(args)))
         return
     rank, world = dist_init()
     if args.impl == "reference":

@@ -1,7 +1,8 @@
 """Gradient-descent inversion loop (step 4 of Sec. 2, with the regularisation of Sec. 3.3) as
 a host driver of the C ABI. Each evaluation of a model:
-- solves the batch (tt_forward, tt_misfit, and tt_misfit_cr when common-receiver pairs are
-  given, Eqs. 2-4; tt_adjoint) and accumulates the kernels (tt_kernel, Eqs. 6-8);
+- solves each batch of sources (tt_forward, tt_misfit, and tt_misfit_cr when
+  common-receiver pairs are given, Eqs. 2-4; tt_adjoint) and accumulates the kernels
+  (tt_kernel, Eqs. 6-8);
 - solves the adjoint again with R = 1 at every record of each source and sums those fields
   into the kernel density (tt_kernel_density, Eq. 19).
 
@@ -24,27 +25,15 @@ from . import (default_opts, mgrid, tt_adjoint, tt_forward, tt_kernel, tt_kernel
                tt_misfit_cr, tt_model_update)
 
 
-class Inversion:
-    """Buffers and calls of the loop for one batch of sources, data and inversion grids."""
+class _Batch:
+    """One batch's sources, data and per-batch buffers."""
 
-    def __init__(self, ctx, model, src, data, grid_shape, mg, opts=None, eps_rel=1e-2,
-                 zeta=0.5, cr=None):
-        import torch
-        self.torch = torch
-        self.ctx, self.model, self.src, self.data, self.mg = ctx, model, src, data, mg
-        s = model[0]
-        self.opts = opts if opts is not None else default_opts(0 if s.dtype == torch.float32 else 1)
-        self.eps_rel, self.zeta = float(eps_rel), float(zeta)
-        B, dev, F = len(src), s.device, s.dtype
-        shape = tuple(grid_shape) + (B,)
-        self.tau = torch.empty(shape, dtype=F, device=dev)
-        self.T = torch.empty_like(self.tau)
-        self.P = torch.empty_like(self.tau)
-        self.Phat = torch.empty_like(self.tau)
+    def __init__(self, torch, src, data, cr, dev):
+        B = len(src)
         f64 = dict(dtype=torch.float64, device=dev)
+        self.src, self.data, self.cr = src, data, cr
         self.chi = torch.empty((B, 2), **f64)
         self.R = torch.empty((B, data.n_rec), **f64)
-        self.cr = cr                                    # CrData or None
         self.Tr = torch.empty((B, data.n_rec), **f64)
         self.chi_cr = torch.zeros(B, **f64)
         # R = 1 at every record of each source (Eq. 19's adjoint sources)
@@ -52,29 +41,62 @@ class Inversion:
         for b in range(B):
             Rhat[b, data.h_abs_rec[data.h_abs_off[b]:data.h_abs_off[b + 1]]] = 1.0
         self.Rhat = torch.as_tensor(Rhat, **f64)
-        self.K = [torch.empty(tuple(grid_shape), **f64) for _ in range(3)]
-        self.Kd = torch.empty(tuple(grid_shape), **f64)
-        self.D = [torch.empty(tuple(grid_shape), **f64) for _ in range(3)]
+
+
+class Inversion:
+    """Buffers and calls of the loop for the sources, data and inversion grids. The sources
+    come as one batch (src, data, cr) or as several: batches = [(src, data, cr), ...], each
+    solved in turn on shared field buffers, with the kernels, kernel density and chi summed
+    over all of them (cr pairs stay within their batch)."""
+
+    def __init__(self, ctx, model, src, data, grid_shape, mg, opts=None, eps_rel=1e-2,
+                 zeta=0.5, cr=None, batches=None):
+        import torch
+        self.torch = torch
+        self.ctx, self.model, self.mg = ctx, model, mg
+        s = model[0]
+        self.opts = opts if opts is not None else default_opts(0 if s.dtype == torch.float32 else 1)
+        self.eps_rel, self.zeta = float(eps_rel), float(zeta)
+        dev, F = s.device, s.dtype
+        if batches is None:
+            batches = [(src, data, cr)]
+        self.batches = [_Batch(torch, b_src, b_data, b_cr, dev) for b_src, b_data, b_cr in batches]
+        Bmax = max(len(b.src) for b in self.batches)
+        self.shape = tuple(grid_shape)
+        self.buf = [torch.empty(self.shape + (Bmax,), dtype=F, device=dev) for _ in range(4)]
+        f64 = dict(dtype=torch.float64, device=dev)
+        self.K = [torch.empty(self.shape, **f64) for _ in range(3)]
+        self.Kd = torch.empty(self.shape, **f64)
+        self.D = [torch.empty(self.shape, **f64) for _ in range(3)]
         self.G = torch.empty((mg.n_grids, mg.n_r, mg.n_t, mg.n_p), **f64)
 
+    def _fields(self, B):
+        """tau, T, P, P_hat views for a batch of B sources (node-major, source fastest)."""
+        return [b.view(-1)[:int(np.prod(self.shape)) * B].view(self.shape + (B,))
+                for b in self.buf]
+
     def evaluate(self):
-        """chi of the current model; leaves its kernels and kernel density in the buffers."""
-        c, m, s = self.ctx, self.model, self.src
-        tt_forward(c, m, s, self.tau, self.T, self.opts)
-        tt_misfit(c, self.T, self.data, self.Tr, self.chi, self.R)
-        if self.cr is not None:
-            tt_misfit_cr(c, self.cr, self.Tr, self.chi_cr, self.R)
-        tt_adjoint(c, m, s, self.T, self.data.rec, self.R, self.P, self.opts)
+        """chi of the current model; leaves the kernels and kernel density of all batches in
+        the buffers."""
+        c, m = self.ctx, self.model
         for K in self.K:
             K.zero_()
-        tt_kernel(c, m, self.T, self.P, *self.K)
-        tt_adjoint(c, m, s, self.T, self.data.rec, self.Rhat, self.Phat, self.opts)
         self.Kd.zero_()
-        tt_kernel_density(c, self.Phat, self.Kd)
-        chi = self.chi.cpu().numpy()
-        total = self.data.alpha * chi[:, 0].sum() + self.data.beta * chi[:, 1].sum()
-        if self.cr is not None:
-            total += self.cr.gamma * self.chi_cr.cpu().numpy().sum()
+        total = 0.0
+        for bt in self.batches:
+            tau, T, P, Phat = self._fields(len(bt.src))
+            bt.iters_fwd = tt_forward(c, m, bt.src, tau, T, self.opts)
+            tt_misfit(c, T, bt.data, bt.Tr, bt.chi, bt.R)
+            if bt.cr is not None:
+                tt_misfit_cr(c, bt.cr, bt.Tr, bt.chi_cr, bt.R)
+            bt.iters_adj = tt_adjoint(c, m, bt.src, T, bt.data.rec, bt.R, P, self.opts)
+            tt_kernel(c, m, T, P, *self.K)
+            tt_adjoint(c, m, bt.src, T, bt.data.rec, bt.Rhat, Phat, self.opts)
+            tt_kernel_density(c, Phat, self.Kd)
+            chi = bt.chi.cpu().numpy()
+            total += bt.data.alpha * chi[:, 0].sum() + bt.data.beta * chi[:, 1].sum()
+            if bt.cr is not None:
+                total += bt.cr.gamma * bt.chi_cr.cpu().numpy().sum()
         return float(total)
 
     def direction(self):
@@ -108,9 +130,9 @@ class Inversion:
 
 
 def invert(ctx, model, src, data, grid_shape, n_r=11, n_t=11, n_p=11, n_grids=5, n_iter=10,
-           step=0.02, opts=None, eps_rel=1e-2, zeta=0.5, cr=None):
+           step=0.02, opts=None, eps_rel=1e-2, zeta=0.5, cr=None, batches=None):
     """The loop on n_grids offset inversion grids of n_r x n_t x n_p nodes; the model tensors
     are updated in place. Returns the history of Inversion.run."""
     inv = Inversion(ctx, model, src, data, grid_shape, mgrid(n_r, n_t, n_p, n_grids), opts,
-                    eps_rel, zeta, cr)
+                    eps_rel, zeta, cr, batches)
     return inv.run(n_iter, step)

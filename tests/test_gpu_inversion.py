@@ -197,3 +197,26 @@ def test_inversion_loop_reduces_the_misfit(tt):
     print("\nchi, step, accepted:", [("%.4g" % c, s, a) for c, s, a in hist])
     assert hist[1][2], "the first step along the computed direction raised chi"
     assert chis[-1] <= 0.95 * chis[0]
+
+
+def test_batches_sum_to_the_single_batch(tt):
+    """The same sources as one batch or as two (kernels, kernel density and chi summed over
+    batches): equal up to the order of the FP64 sums."""
+    import torch
+    from paper_2412_00031_gb300.invert import Inversion
+    w = I.small_case(87, shape=(13, 15, 17), n_src=7, n_rec=9)
+    g = w.grid.as_dict()
+    model = tuple(_dev(a, torch.float32) for a in (w.s, w.xi, w.eta))
+    ctx = tt.tt_ctx_create(g)
+    mg = tt.mgrid(4, 4, 4, 2)
+    one = Inversion(ctx, model, w.src, tt.DeviceData.from_workload(w), w.grid.shape, mg)
+    c1 = one.evaluate()
+    parts = [w.subset(range(0, 4)), w.subset(range(4, 7))]
+    two = Inversion(ctx, model, None, None, w.grid.shape, mg,
+                    batches=[(p.src, tt.DeviceData.from_workload(p), None) for p in parts])
+    c2 = two.evaluate()
+    assert abs(c1 - c2) <= 1e-12 * c1
+    for a, b in zip(one.K + [one.Kd], two.K + [two.Kd]):
+        a, b = a.cpu().numpy(), b.cpu().numpy()
+        assert np.abs(a - b).max() <= 1e-12 * np.abs(a).max()
+    ctx.close()

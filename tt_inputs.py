@@ -262,6 +262,35 @@ def anisotropic_batch(seed=SEED_BASE + 2, n_src=256, n_pool=200, shape=(121, 161
     return Workload(g, s, xi, eta, src, rec, name="anisotropic-121x161x161", **d)
 
 
+def inversion_201(seed=SEED_BASE + 4, n_src=1024, n_pool=400, shape=(101, 201, 201),
+                  count_range=(20, 200), cs_max_deg=0.5, cr_max_deg=0.3):
+    """201 (lat) x 201 (lon) x 101 (depth) grid, depth 0-200 km, 5 x 5 deg (2 km, 0.025 deg).
+    Start model: Vp 5 -> 8 km/s with depth, isotropic. True model (meta["true"] = (s, xi,
+    eta)): the start times a +-5 % checkerboard, with xi and eta checkerboards of amplitude
+    0.02. n_src sources at 5-180 km; each sees a seeded subset of U{20..200} of n_pool surface
+    stations; common-source pairs of a subset closer than cs_max_deg. meta["cr_deg"] is the
+    largest epicentral distance of a common-receiver source pair. The times here are
+    straight-ray placeholders; a caller that needs consistent data replaces them by solves
+    in the true model (meta["noise_s"] = 0.05 s of Gaussian noise)."""
+    rng = np.random.default_rng(seed)
+    g = GridSpec(shape[0], shape[1], shape[2], 0.0, 200.0, 0.0, 5.0, 0.0, 5.0)
+    v0 = background_velocity(g)
+    s = 1.0 / v0
+    z = np.zeros(g.shape)
+    s_true = 1.0 / (v0 * (1.0 + 0.05 * checker(g, 1.5, 2.5, 2.5)))
+    xi_true = 0.02 * checker(g, 1.5, 2.5, 2.5)
+    eta_true = 0.02 * checker(g, 1.5, 2.5, 2.5, phase_cos_phi=True)
+    src = random_sources(g, n_src, (5.0, 180.0), rng)
+    rec = surface_receivers(g, n_pool, rng)
+    tobs = synthetic_observations(g, src, rec, 6.5, 0.05, rng)
+    lo, hi = count_range
+    counts = rng.integers(lo, min(hi, n_pool) + 1, n_src)
+    d = build_data(g, src, rec, tobs, rng, counts=counts, cs_max_deg=cs_max_deg)
+    meta = dict(true=(s_true, xi_true, eta_true), cr_deg=cr_max_deg, noise_s=0.05,
+                noise_seed=seed + 1000)
+    return Workload(g, s, z, z.copy(), src, rec, name="inversion-201x201x101", meta=meta, **d)
+
+
 def random_field_models(seed=SEED_BASE + 3, n_models=250, shape=(81, 81, 81),
                         depth_km=60.0, extent_deg=2.0, corr_km=10.0, sigma_v=0.03,
                         sigma_aniso=0.02, clip_aniso=0.04, n_src=8, depth_range=(5.0, 40.0)):
