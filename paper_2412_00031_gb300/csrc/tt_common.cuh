@@ -211,7 +211,10 @@ __device__ __forceinline__ F godunov_core(F invT0, F ur, F ut, F up, F tc, F trp
     }
     const F rhs = mul_(R.s, invT0);
     const F r2 = mul_(rhs, rhs);
-    F best = (F)0;
+    // Each candidate root is kept as N / D with D > 0: the causality test sg (a N / D + c)
+    // >= 0 becomes sg (a N + c D) >= 0 and the comparison of two roots a comparison of
+    // cross products, so only the chosen root is divided.
+    F bestN = (F)0, bestD = (F)1;
     bool found = false;
 #pragma unroll
     for (int mask = 1; mask < 8; ++mask) {
@@ -227,17 +230,21 @@ __device__ __forceinline__ F godunov_core(F invT0, F ur, F ut, F up, F tc, F trp
         if (!(A > (F)0) || disc < (F)0) continue;
         const F q = sqrt_(disc);
         // the larger root of A delta^2 + 2 B delta + C = 0
-        const F dl = B >= (F)0 ? div_(-C, add_(B, q)) : div_(sub_(q, B), A);
+        const bool pos = B >= (F)0;
+        const F N = pos ? -C : sub_(q, B);
+        const F D = pos ? add_(B, q) : A;
+        if (!(D > (F)0)) continue;
         bool ok = true;
 #pragma unroll
         for (int d = 0; d < 3; ++d)
-            if ((mask >> d & 1) && mul_(sg[d], fma_(a[d], dl, c[d])) < (F)0) ok = false;
-        if (ok && (!found || dl < best)) {
-            best = dl;
+            if ((mask >> d & 1) && mul_(sg[d], fma_(a[d], N, mul_(c[d], D))) < (F)0) ok = false;
+        if (ok && (!found || mul_(N, bestD) < mul_(bestN, D))) {
+            bestN = N;
+            bestD = D;
             found = true;
         }
     }
-    return found ? add_(tc, best) : tc;
+    return found ? add_(tc, div_(bestN, bestD)) : tc;
 }
 
 // ---------------------------------------------------------------------------------------
