@@ -36,6 +36,7 @@ def lib():
         L.or_forward.restype = C.c_int
         L.or_forward_hyperplane.restype = C.c_int
         L.or_forward_godunov.restype = C.c_int
+        L.or_forward_godunov_aniso.restype = C.c_int
         L.or_adjoint.restype = C.c_int
         L.or_fixed_set_inflow.restype = C.c_double
         _lib = L
@@ -79,8 +80,9 @@ def T0(g, s, xi, eta, src):
 
 def forward(g, s, xi, eta, src, tol=1e-8, max_iter=500, tau_init=None, hyperplane=False,
             scheme="lf"):
-    """Returns (tau, T, iterations, converged, last_err). scheme: "lf" (Lax-Friedrichs, R4) or
-    "godunov" (R14; isotropic models only: xi = eta = 0)."""
+    """Returns (tau, T, iterations, converged, last_err). scheme: "lf" (Lax-Friedrichs, R4),
+    "godunov" (R14; isotropic models only: xi = eta = 0) or "godunov_aniso" (R16; any
+    model)."""
     G = make_grid(g)
     shape = (G.n_r, G.n_t, G.n_p)
     s, ps = _f(s); xi, px = _f(xi); eta, pe = _f(eta)
@@ -92,6 +94,9 @@ def forward(g, s, xi, eta, src, tol=1e-8, max_iter=500, tau_init=None, hyperplan
     if scheme == "godunov":
         assert not hyperplane and not xi.any() and not eta.any(), "Godunov: isotropic models"
         fn = lib().or_forward_godunov
+    elif scheme == "godunov_aniso":
+        assert not hyperplane
+        fn = lib().or_forward_godunov_aniso
     else:
         fn = lib().or_forward_hyperplane if hyperplane else lib().or_forward
     it = fn(C.byref(G), ps, px, pe, Point(*src), C.c_double(tol), C.c_int(max_iter),

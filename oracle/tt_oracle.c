@@ -28,6 +28,15 @@
  *      smallest root, over the 7 non-empty subsets of axes, of
  *      sum_d (a_d tau - b_d)^2 = (s / T0)^2 (the larger root of each quadratic) whose
  *      one-sided differences all have the upwind sign; with no such root tau_c is kept.
+ *  R16 Godunov local solver for anisotropic models (M of Eq. "4" with xi, eta; an alternative
+ *      to R4): as R14, with two changes. (a) Along theta and phi the upwind neighbour is the
+ *      side the characteristic comes from: the sign of (M g)_d, g the central-difference
+ *      gradient of T / T0 at the node (the quantity LF evaluates); along r, where M has no
+ *      cross term, the neighbour with the smaller estimate of T as in R14. (b) For a subset S
+ *      of axes the gradient components off S take the values that minimise H, so the
+ *      quadratic form on S is the Schur complement W = ((M^-1)_SS)^-1, and the causality
+ *      test is sg_d (W g_S)_d >= 0 for d in S (the characteristic M g enters from the
+ *      upwind side; it is zero along the axes off S).
  */
 #include "tt_oracle.h"
 
@@ -368,12 +377,90 @@ static void extrapolate_faces(const geo *G, const source_factor *S, double *tau)
  * over [lo, hi]. */
 static int swept(int q, int dir, int lo, int hi) { return dir > 0 ? lo + q : hi - q; }
 
+/* Godunov update for anisotropic models (R16). */
+static double godunov_aniso_update(const geo *G, const source_factor *S, const double *s,
+                                   const double *xi, const double *eta, const double *tau,
+                                   int i, int j, int k)
+{
+    long c = idx(G, i, j, k);
+    double p0[3];
+    double T0 = factor_at(G, S, i, j, k, p0);
+    double r = rad_of(G, i), th = lat_of(G, j);
+    double h[3] = {1.0, h2_at(G, r), h3_at(G, r, th)};
+    double del[3] = {G->dr, G->dt, G->dp};
+    double tp[3], tm[3];
+    tp[0] = tau[idx(G, i + 1, j, k)]; tm[0] = tau[idx(G, i - 1, j, k)];
+    tp[1] = tau[idx(G, i, j + 1, k)]; tm[1] = tau[idx(G, i, j - 1, k)];
+    tp[2] = tau[idx(G, i, j, k + 1)]; tm[2] = tau[idx(G, i, j, k - 1)];
+    double M[3][3], Mi[3][3];
+    aniso_M(xi[c], eta[c], M);
+    inverse3(M, Mi);
+    double u[3], e[3], gc[3];
+    for (int d = 0; d < 3; d++) {
+        u[d] = p0[d] / T0;
+        e[d] = 1.0 / (del[d] * h[d]);
+        gc[d] = u[d] * tau[c] + 0.5 * e[d] * (tp[d] - tm[d]);
+    }
+    double a[3], b[3], sg[3];
+    for (int d = 0; d < 3; d++) {
+        int lower;
+        if (d == 0) {
+            lower = tm[d] * (1.0 - u[d] / e[d]) <= tp[d] * (1.0 + u[d] / e[d]);
+        } else {
+            double f = M[d][0] * gc[0] + M[d][1] * gc[1] + M[d][2] * gc[2];
+            lower = f >= 0.0;
+        }
+        sg[d] = lower ? 1.0 : -1.0;
+        a[d] = u[d] + sg[d] * e[d];
+        b[d] = sg[d] * e[d] * (lower ? tm[d] : tp[d]);
+    }
+    double rhs = s[c] / T0;
+    double best = -1.0;
+    for (int mask = 1; mask < 8; mask++) {
+        int ax[3], n = 0;
+        for (int d = 0; d < 3; d++)
+            if (mask >> d & 1) ax[n++] = d;
+        /* W = ((M^-1)_SS)^-1, the form on S after minimising H over the other components */
+        double W[3][3];
+        if (n == 1) {
+            W[0][0] = 1.0 / Mi[ax[0]][ax[0]];
+        } else if (n == 2) {
+            double p = Mi[ax[0]][ax[0]], q = Mi[ax[0]][ax[1]], w = Mi[ax[1]][ax[1]];
+            double det = p * w - q * q;
+            W[0][0] = w / det; W[0][1] = W[1][0] = -q / det; W[1][1] = p / det;
+        } else {
+            for (int x = 0; x < 3; x++)
+                for (int y = 0; y < 3; y++) W[x][y] = M[x][y];
+        }
+        double A = 0.0, B = 0.0, C = -rhs * rhs;
+        for (int x = 0; x < n; x++)
+            for (int y = 0; y < n; y++) {
+                A += W[x][y] * a[ax[x]] * a[ax[y]];
+                B += W[x][y] * a[ax[x]] * b[ax[y]];
+                C += W[x][y] * b[ax[x]] * b[ax[y]];
+            }
+        double disc = B * B - A * C;
+        if (!(A > 0.0) || disc < 0.0) continue;
+        double t = (B + sqrt(disc)) / A;
+        int ok = 1;
+        for (int x = 0; x < n; x++) {
+            double f = 0.0;
+            for (int y = 0; y < n; y++) f += W[x][y] * (a[ax[y]] * t - b[ax[y]]);
+            if (sg[ax[x]] * f < 0.0) ok = 0;
+        }
+        if (ok && (best < 0.0 || t < best)) best = t;
+    }
+    return best < 0.0 ? tau[c] : best;
+}
+
 /* One sweep of the interior in lexicographic order (R5); returns the largest |change|. */
-/* The local solver of the chosen scheme: 0 = Lax-Friedrichs (R4), 1 = Godunov (R14). */
+/* The local solver of the chosen scheme: 0 = Lax-Friedrichs (R4), 1 = Godunov for isotropic
+ * models (R14), 2 = Godunov for anisotropic models (R16). */
 static double local_update(const geo *G, const source_factor *S, const double *s,
                            const double *xi, const double *eta, const double *tau, int i, int j,
                            int k, int scheme)
 {
+    if (scheme == 2) return godunov_aniso_update(G, S, s, xi, eta, tau, i, j, k);
     return scheme == 1 ? godunov_update(G, S, s, tau, i, j, k)
                        : lf_update(G, S, s, xi, eta, tau, i, j, k);
 }
@@ -476,6 +563,15 @@ int or_forward_godunov(const or_grid *g, const double *s, const double *xi, cons
                        double *tau, double *T, int *conv, double *last_err)
 {
     return forward_impl(g, s, xi, eta, src, tol, max_iter, tau_init, tau, T, conv, last_err, 0, 1);
+}
+
+/* The forward solve with the anisotropic Godunov local solver (R16): any model. */
+int or_forward_godunov_aniso(const or_grid *g, const double *s, const double *xi,
+                             const double *eta, or_point src, double tol, int max_iter,
+                             const double *tau_init, double *tau, double *T, int *conv,
+                             double *last_err)
+{
+    return forward_impl(g, s, xi, eta, src, tol, max_iter, tau_init, tau, T, conv, last_err, 0, 2);
 }
 
 int or_forward_hyperplane(const or_grid *g, const double *s, const double *xi,

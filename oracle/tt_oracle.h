@@ -52,6 +52,11 @@ int or_forward(const or_grid *g, const double *s, const double *xi, const double
 int or_forward_godunov(const or_grid *g, const double *s, const double *xi, const double *eta,
                        or_point src, double tol, int max_iter, const double *tau_init,
                        double *tau, double *T, int *conv, double *last_err);
+/* or_forward with the anisotropic Godunov local solver (R16), any model. */
+int or_forward_godunov_aniso(const or_grid *g, const double *s, const double *xi,
+                             const double *eta, or_point src, double tol, int max_iter,
+                             const double *tau_init, double *tau, double *T, int *conv,
+                             double *last_err);
 
 /* Trilinear interpolation of nodal T at n_rec points. */
 void or_receiver_times(const or_grid *g, const double *T, int n_rec, const or_point *rec,
