@@ -122,9 +122,12 @@ typedef struct {
                                converges (or reaches max_iter_fwd) hands its slot to the next
                                one. Results and iteration counts do not depend on it. */
     int scheme;             /* forward local solver: 0 = Lax-Friedrichs (Sec. 3.1, the paper's;
-                               any model); 1 = Godunov upwind (isotropic models only, xi = eta
-                               = 0: tt_forward returns TT_EINVAL otherwise, after the solve).
-                               Godunov runs on the node-hyperplane schedule. */
+                               any model); 1 = Godunov upwind for isotropic models (xi = eta
+                               = 0: tt_forward returns TT_EINVAL otherwise, after the solve);
+                               2 = Godunov upwind for anisotropic models (any model: upwind
+                               sides along theta and phi from the characteristic direction
+                               M grad T, the Schur-complement form of M on each axis subset).
+                               The Godunov solvers run on the node-hyperplane schedule. */
 } tt_opts;
 
 typedef struct tt_ctx tt_ctx;

@@ -318,7 +318,7 @@ tt_status check_opts(tt_ctx *ctx, const tt_opts *o) {
     if (o->sweep_schedule < 0 || o->sweep_schedule > 1 + kNumTileShapes)
         return fail(ctx, TT_EINVAL, "sweep_schedule %d unknown", o->sweep_schedule);
     if (o->init < 0 || o->init > 2) return fail(ctx, TT_EINVAL, "init %d unknown", o->init);
-    if (o->scheme < 0 || o->scheme > 1) return fail(ctx, TT_EINVAL, "scheme %d unknown", o->scheme);
+    if (o->scheme < 0 || o->scheme > 2) return fail(ctx, TT_EINVAL, "scheme %d unknown", o->scheme);
     if (o->fwd_slots < 0) return fail(ctx, TT_EINVAL, "fwd_slots %d < 0", o->fwd_slots);
     if (o->fwd_groups < 0 || o->fwd_groups > kMaxBarrierGroups)
         return fail(ctx, TT_EINVAL, "fwd_groups %d outside 0..%d", o->fwd_groups,
@@ -585,7 +585,7 @@ tt_status enq_forward(tt_ctx *ctx, Work<F> &W, const tt_model *m, int B, void *d
     // (B values) that are a multiple of 16 bytes. Automatic: node hyperplanes.
     const bool tiles_ok = B >= 32 && (B * sizeof(F)) % 16 == 0;
     int sched = o->sweep_schedule == 0 ? 1 : o->sweep_schedule;
-    if ((sched >= 2 && !tiles_ok) || W.n_slots > 0 || o->scheme == 1) sched = 1;
+    if ((sched >= 2 && !tiles_ok) || W.n_slots > 0 || o->scheme != 0) sched = 1;
     const int slice = W.t0c_slice;
 
     const GeoTab<F> &t = geo<F>(ctx);

@@ -247,6 +247,106 @@ __device__ __forceinline__ F godunov_core(F invT0, F ur, F ut, F up, F tc, F trp
     return found ? add_(tc, div_(bestN, bestD)) : tc;
 }
 
+// Godunov update for anisotropic models (an alternative to lf_core with the same arguments).
+// As godunov_core, with two changes. Along theta and phi the upwind neighbour is the side
+// the characteristic comes from: the sign of (M g)_d, where g = tau_c u + (tau_+ - tau_-) e_d / 2
+// is the central-difference gradient over T0 (the quantity lf_core evaluates). Along r,
+// where M has no cross term, it is the neighbour with the smaller estimate of T, as in
+// godunov_core. On an axis subset S the components off S take the values that minimise H,
+// so the form on S is the Schur complement W = ((M^-1)_SS)^-1:
+//   {r}: 1; {theta}: det / m_p; {phi}: det / m_t; {r, theta}, {r, phi}: diagonal;
+//   {theta, phi}: the (theta, phi) block of M; {r, theta, phi}: M,
+// with m_t = 1 - 2 xi, m_p = 1 + 2 xi, m = 2 eta, det = m_t m_p - m^2. The 1-D and diagonal
+// quadratics are scaled by m_p or m_t (> 0), which leaves their roots and signs unchanged and
+// needs no division. Causality: sg_d (W g)_d >= 0 on S. Increment form and division-free
+// selection as in godunov_core.
+template <typename F>
+__device__ __forceinline__ F godunov_aniso_core(F invT0, F ur, F ut, F up, F tc, F trp, F trm,
+                                                F ttp, F ttm, F tpp, F tpm, const NodeRec<F> &R,
+                                                F er) {
+    const F u[3] = {ur, ut, up};
+    const F eh[3] = {er, R.et, R.ep};
+    const F lo[3] = {trm, ttm, tpm}, hi[3] = {trp, ttp, tpp};
+    const F mt = fma_((F)-2, R.xi, (F)1), mp = fma_((F)2, R.xi, (F)1), m = (F)2 * R.eta;
+    const F det = fma_(mt, mp, -mul_(m, m));
+    F gc[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) gc[d] = fma_(tc, u[d], mul_(sub_(hi[d], lo[d]), eh[d]));
+    bool lower[3];
+    {
+        const F e0 = (F)2 * eh[0];
+        lower[0] = mul_(lo[0], sub_(e0, u[0])) <= mul_(hi[0], add_(e0, u[0]));
+        lower[1] = fma_(mt, gc[1], mul_(m, gc[2])) >= (F)0;
+        lower[2] = fma_(m, gc[1], mul_(mp, gc[2])) >= (F)0;
+    }
+    F a[3], c[3], sg[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        sg[d] = lower[d] ? (F)1 : (F)-1;
+        const F se = mul_(sg[d], (F)2 * eh[d]);
+        a[d] = add_(se, u[d]);
+        c[d] = fma_(u[d], tc, mul_(se, sub_(tc, lower[d] ? lo[d] : hi[d])));
+    }
+    const F rhs = mul_(R.s, invT0);
+    const F r2 = mul_(rhs, rhs);
+    // per-axis products shared by the subsets
+    const F aa0 = mul_(a[0], a[0]), ac0 = mul_(a[0], c[0]), cc0 = mul_(c[0], c[0]);
+    const F aa1 = mul_(a[1], a[1]), ac1 = mul_(a[1], c[1]), cc1 = mul_(c[1], c[1]);
+    const F aa2 = mul_(a[2], a[2]), ac2 = mul_(a[2], c[2]), cc2 = mul_(c[2], c[2]);
+    // the (theta, phi) block form
+    const F Atp = fma_(mt, aa1, fma_(mul_((F)2 * m, a[1]), a[2], mul_(mp, aa2)));
+    const F Btp = fma_(mt, ac1, fma_(m, fma_(a[1], c[2], mul_(a[2], c[1])), mul_(mp, ac2)));
+    const F Ctp = fma_(mt, cc1, fma_(mul_((F)2 * m, c[1]), c[2], mul_(mp, cc2)));
+    F bestN = (F)0, bestD = (F)1;
+    bool found = false;
+#pragma unroll
+    for (int mask = 1; mask < 8; ++mask) {
+        const bool hr = mask & 1, ht = mask & 2, hp = mask & 4;
+        F A, B, C;
+        if (ht && hp) {
+            A = hr ? add_(aa0, Atp) : Atp;
+            B = hr ? add_(ac0, Btp) : Btp;
+            C = sub_(hr ? add_(cc0, Ctp) : Ctp, r2);
+        } else if (ht || hp) {
+            const F sc = ht ? mp : mt;               // scale of the 1-D theta / phi form
+            const F aa = ht ? aa1 : aa2, ac = ht ? ac1 : ac2, cc = ht ? cc1 : cc2;
+            A = hr ? fma_(sc, aa0, mul_(det, aa)) : mul_(det, aa);
+            B = hr ? fma_(sc, ac0, mul_(det, ac)) : mul_(det, ac);
+            C = hr ? fma_(sc, cc0, fma_(det, cc, -mul_(sc, r2))) : fma_(det, cc, -mul_(sc, r2));
+        } else {
+            A = aa0;
+            B = ac0;
+            C = sub_(cc0, r2);
+        }
+        const F disc = fma_(B, B, -mul_(A, C));
+        if (!(A > (F)0) || disc < (F)0) continue;
+        const F q = sqrt_(disc);
+        const bool pos = B >= (F)0;
+        const F N = pos ? -C : sub_(q, B);
+        const F D = pos ? add_(B, q) : A;
+        if (!(D > (F)0)) continue;
+        // D (a delta + c) on each axis, then the causality test on W g
+        const F h0 = fma_(a[0], N, mul_(c[0], D));
+        const F h1 = fma_(a[1], N, mul_(c[1], D));
+        const F h2 = fma_(a[2], N, mul_(c[2], D));
+        bool ok = !hr || mul_(sg[0], h0) >= (F)0;
+        if (ht && hp) {
+            ok = ok && mul_(sg[1], fma_(mt, h1, mul_(m, h2))) >= (F)0 &&
+                 mul_(sg[2], fma_(m, h1, mul_(mp, h2))) >= (F)0;
+        } else if (ht) {
+            ok = ok && mul_(sg[1], h1) >= (F)0;
+        } else if (hp) {
+            ok = ok && mul_(sg[2], h2) >= (F)0;
+        }
+        if (ok && (!found || mul_(N, bestD) < mul_(bestN, D))) {
+            bestN = N;
+            bestD = D;
+            found = true;
+        }
+    }
+    return found ? add_(tc, div_(bestN, bestD)) : tc;
+}
+
 // ---------------------------------------------------------------------------------------
 // Grid-wide barrier for persistent cooperative launches. Arrivals go to a monotonic
 // per-launch counter: barrier number m of a launch is complete once m * nblocks arrivals

@@ -251,9 +251,10 @@ template <typename F, int SCHEME>
 __device__ __forceinline__ F update_one(F *p, const F *v, const Vec4<F> &c, const NodeRec<F> &R,
                                         F er) {
     if (!(c.x > (F)0)) return (F)0;
-    const F tn = SCHEME == 1
-                     ? godunov_core<F>(c.x, c.y, c.z, c.w, v[0], v[1], v[2], v[3], v[4], v[5], v[6], R, er)
-                     : lf_core<F>(c.x, c.y, c.z, c.w, v[0], v[1], v[2], v[3], v[4], v[5], v[6], R, er);
+    const F tn =
+        SCHEME == 2   ? godunov_aniso_core<F>(c.x, c.y, c.z, c.w, v[0], v[1], v[2], v[3], v[4], v[5], v[6], R, er)
+        : SCHEME == 1 ? godunov_core<F>(c.x, c.y, c.z, c.w, v[0], v[1], v[2], v[3], v[4], v[5], v[6], R, er)
+                      : lf_core<F>(c.x, c.y, c.z, c.w, v[0], v[1], v[2], v[3], v[4], v[5], v[6], R, er);
     *p = tn;
     return fabs(tn - v[0]);
 }
@@ -261,7 +262,7 @@ __device__ __forceinline__ F update_one(F *p, const F *v, const Vec4<F> &c, cons
 // I: index type of the [node][source] fields (32-bit when every index fits).
 // REFILL: the retire-and-refill mode (compiled separately, so that the resident launch
 // carries none of its code). SCHEME: the local solver, 0 Lax-Friedrichs (lf_core), 1 Godunov
-// (godunov_core, isotropic models).
+// (godunov_core, isotropic models), 2 Godunov for anisotropic models (godunov_aniso_core).
 template <typename F, typename I, bool REFILL, int SCHEME>
 __global__ void __launch_bounds__(256, TTGB_FWD_MIN_BLOCKS) fwd_sweep_kernel(FwdArgs<F> a) {
     constexpr int NS = kFwdSourcesPerLane;              // sources of one lane: l0 + 32 h
@@ -1157,6 +1158,11 @@ __global__ void __launch_bounds__(256, TTGB_ADJ_MIN_BLOCKS) adj_face_kernel(AdjA
 
 // The node-hyperplane sweep kernel of one variant.
 template <typename F> void *fwd_kernel_ptr(bool refill, bool idx32, int scheme) {
+    if (scheme == 2)
+        return refill ? (idx32 ? (void *)fwd_sweep_kernel<F, unsigned, true, 2>
+                               : (void *)fwd_sweep_kernel<F, long long, true, 2>)
+                      : (idx32 ? (void *)fwd_sweep_kernel<F, unsigned, false, 2>
+                               : (void *)fwd_sweep_kernel<F, long long, false, 2>);
     if (scheme == 1)
         return refill ? (idx32 ? (void *)fwd_sweep_kernel<F, unsigned, true, 1>
                                : (void *)fwd_sweep_kernel<F, long long, true, 1>)

@@ -8,7 +8,10 @@ oracle's Godunov solver (reading R14), through the C ABI (needs a GB300).
 - a 41^3 checkerboard: a few iterations where Lax-Friedrichs needs a count growing with the
   grid;
 - the 81^3 isotropic checkerboard at full size (64 sources) against oracle solves of sampled
-  sources.
+  sources;
+- the anisotropic solver (opts.scheme = 2, reading R16): FP64 batch to 1e-10 of the oracle
+  with the same iteration counts, FP32 batch to the 1e-5 bar with bitwise launch variants,
+  and an anisotropic 81^3 checkerboard at full size.
 """
 import numpy as np
 import pytest
@@ -114,3 +117,57 @@ def test_checkerboard_81_batch_against_oracle_solves(tt):
     one = gpu_solve(w.subset([w.n_src - 1]), "f32", opts=_opts(tt, tt.TT_F32), steps=("fwd",))
     assert np.array_equal(one["T"][..., 0], out["T"][..., -1])
     assert int(np.max(out["iters_fwd"])) <= 10
+
+
+# ---- the anisotropic Godunov solver (opts.scheme = 2, reading R16) ----
+
+def test_anisotropic_fp64_batch_matches_the_oracle(tt):
+    import oracle as O
+    w = I.small_case(111, shape=(13, 14, 15), n_src=5)
+    assert np.abs(w.xi).max() > 0 and np.abs(w.eta).max() > 0
+    o = tt.default_opts(tt.TT_F64, scheme=2, tol_fwd=1e-12, max_iter_fwd=200)
+    out = gpu_solve(w, "f64", opts=o, steps=("fwd",))
+    g = w.grid.as_dict()
+    for b in range(w.n_src):
+        _, T, it, conv, _ = O.forward(g, w.s, w.xi, w.eta, w.src[b], tol=1e-12, max_iter=200,
+                                      scheme="godunov_aniso")
+        assert conv
+        assert rel_linf(out["T"][..., b], T) <= 1e-10
+        assert abs(int(out["iters_fwd"][b]) - it) <= 1
+
+
+def test_anisotropic_fp32_batch_meets_the_bar_and_variants_are_bitwise(tt):
+    import oracle as O
+    w = I.small_case(112, shape=(17, 16, 18), n_src=40)
+    ref = gpu_solve(w, "f32", opts=tt.default_opts(tt.TT_F32, scheme=2), steps=("fwd",))
+    s, xi, eta = rounded_model(w, "f32")
+    g = w.grid.as_dict()
+    for b in (0, 21, 39):
+        _, T, it, conv, _ = O.forward(g, s, xi, eta, w.src[b], tol=1e-10, max_iter=200,
+                                      scheme="godunov_aniso")
+        assert conv
+        assert rel_linf(ref["T"][..., b], T) <= 1e-5
+    assert int(np.max(ref["iters_fwd"])) <= 10
+    for kw in ({"fwd_groups": 1}, {"fwd_groups": 3}, {"fwd_slots": 32}):
+        out = gpu_solve(w, "f32", opts=tt.default_opts(tt.TT_F32, scheme=2, **kw), steps=("fwd",))
+        assert np.array_equal(out["tau"], ref["tau"]), kw
+        assert np.array_equal(out["iters_fwd"], ref["iters_fwd"]), kw
+
+
+@pytest.mark.slow
+def test_anisotropic_81_batch_against_oracle_solves(tt):
+    """81^3 checkerboard with xi and eta checkerboards of amplitude 0.04, 64 sources, FP32:
+    complete FP64 oracle solves (R16) of the first and last source to the 1e-5 bar."""
+    import oracle as O
+    w = I.checkerboard_81()
+    w.xi = 0.04 * I.checker(w.grid)
+    w.eta = 0.04 * I.checker(w.grid, phase_cos_phi=True)
+    out = gpu_solve(w, "f32", opts=tt.default_opts(tt.TT_F32, scheme=2), steps=("fwd",))
+    s, xi, eta = rounded_model(w, "f32")
+    g = w.grid.as_dict()
+    for b in (0, w.n_src - 1):
+        _, T, it, conv, _ = O.forward(g, s, xi, eta, w.src[b], tol=1e-10, max_iter=200,
+                                      scheme="godunov_aniso")
+        assert conv
+        assert rel_linf(out["T"][..., b], T) <= 1e-5
+    assert int(np.max(out["iters_fwd"])) <= 12
