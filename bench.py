@@ -331,7 +331,52 @@ def gpu_arm(args, rank, world):
         result["refill"] = refill_leg(args, dev, world, w.n_src, gp)
     if args.warm_start and os.path.exists(args.warm_start):
         result["warm_start"] = warm_leg(args, gp, world)
+    if args.godunov:
+        result["godunov"] = godunov_leg(args, gp, world)
     return result, w, (float(itf.mean()), float(ita.mean()))
+
+
+def godunov_leg(args, gp, world):
+    """The same step with the Godunov local solver for anisotropic models (opts.scheme = 2)
+    in the forward sweep instead of Lax-Friedrichs: a different first-order discretisation of
+    the same equation (its fixed point differs at O(h); parity is against the oracle's
+    solver of the same scheme). Launch configuration autotuned for the scheme."""
+    torch, tt = gp.torch, gp.tt
+    if gp.plan is not None:
+        gp.plan.close()
+        gp.plan = None
+    gp.opts.init = 0
+    gp.opts.scheme = 2
+    tuned = None
+    if args.autotune and args.schedule == 0:
+        ms = tt.tt_autotune(gp.ctx, gp.model, gp.w.src, gp.opts)
+        tuned = {"ms_per_iteration": {k: round(v, 3) for k, v in ms.items()},
+                 "chosen": {"fwd_groups": gp.opts.fwd_groups}}
+    if args.plan:
+        gp.use_plan()
+    for _ in range(args.warmup):
+        gp.step()
+    gp.iters.clear()
+    dist_barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        gp.step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = dist_max(e0.elapsed_time(e1) / args.steps, world)
+    itf = np.concatenate([s[0] for s in gp.iters])
+    ita = np.concatenate([s[1] for s in gp.iters])
+    fwd = [s[2] for s in gp.iters]
+    adj = [s[3] for s in gp.iters]
+    return {"value": world * gp.w.n_src / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+            "scheme": "Godunov upwind for anisotropic models (opts.scheme = 2)",
+            "iters_fwd_mean": float(itf.mean()), "iters_fwd_max": int(itf.max()),
+            "iters_adj_mean": float(ita.mean()),
+            "forward_ms": float(np.mean([s["sweep_ms"] for s in fwd])),
+            "adjoint_ms": float(np.mean([s["sweep_ms"] for s in adj])),
+            "autotune": tuned}
 
 
 def refill_leg(args, dev, world, slots, gp):
@@ -754,6 +799,8 @@ def main():
     ap.add_argument("--ref-iters-adj", type=float, default=4.0)
     ap.add_argument("--infer-only", type=int, default=0,
                     help="time only the warm start's inference on this many sources")
+    ap.add_argument("--godunov", type=int, default=1,
+                    help="also time the step with the anisotropic Godunov solver (a leg)")
     ap.add_argument("--inversion", type=int, default=0,
                     help="time this many step attempts of the inversion loop on the "
                          "201x201x101 workload instead of the benchmark step")

@@ -213,6 +213,11 @@ template <typename F> __global__ void refill_setup_kernel(FwdArgs<F> a) {
 #ifndef TTGB_FWD_MIN_BLOCKS
 #define TTGB_FWD_MIN_BLOCKS 4
 #endif
+// The Godunov updates do several times the arithmetic of Lax-Friedrichs per node; their
+// instantiations get a larger register budget (fewer resident blocks per SM).
+#ifndef TTGB_GOD_MIN_BLOCKS
+#define TTGB_GOD_MIN_BLOCKS 3
+#endif
 
 // Sweep-local node (aa, bb, cc) -> offset of its node index from the sweep's first node.
 template <typename I>
@@ -264,7 +269,8 @@ __device__ __forceinline__ F update_one(F *p, const F *v, const Vec4<F> &c, cons
 // carries none of its code). SCHEME: the local solver, 0 Lax-Friedrichs (lf_core), 1 Godunov
 // (godunov_core, isotropic models), 2 Godunov for anisotropic models (godunov_aniso_core).
 template <typename F, typename I, bool REFILL, int SCHEME>
-__global__ void __launch_bounds__(256, TTGB_FWD_MIN_BLOCKS) fwd_sweep_kernel(FwdArgs<F> a) {
+__global__ void __launch_bounds__(256, SCHEME == 0 ? TTGB_FWD_MIN_BLOCKS : TTGB_GOD_MIN_BLOCKS)
+    fwd_sweep_kernel(FwdArgs<F> a) {
     constexpr int NS = kFwdSourcesPerLane;              // sources of one lane: l0 + 32 h
     extern __shared__ unsigned char smem_raw[];
     F *s_err = reinterpret_cast<F *>(smem_raw);
