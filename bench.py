@@ -242,6 +242,7 @@ def gpu_arm(args, rank, world):
     gp.opts.sweep_schedule = args.schedule
     gp.opts.adj_chunk = args.adj_chunk
     gp.opts.launch_blocks = args.launch_blocks
+    gp.opts.scheme = args.scheme
     if args.max_iter_fwd or args.max_iter_adj:  # profiling runs only: bounded iterations
         gp.opts.max_iter_fwd = args.max_iter_fwd or gp.opts.max_iter_fwd
         gp.opts.max_iter_adj = args.max_iter_adj or gp.opts.max_iter_adj
@@ -799,6 +800,8 @@ def main():
     ap.add_argument("--ref-iters-adj", type=float, default=4.0)
     ap.add_argument("--infer-only", type=int, default=0,
                     help="time only the warm start's inference on this many sources")
+    ap.add_argument("--scheme", type=int, default=0,
+                    help="profiling runs: forward local solver of the main step (tt_opts.scheme)")
     ap.add_argument("--godunov", type=int, default=1,
                     help="also time the step with the anisotropic Godunov solver (a leg)")
     ap.add_argument("--inversion", type=int, default=0,
