@@ -334,10 +334,13 @@ tt_status tt_misfit_noalloc(const tt_grid *grid, const void *d_T, int dtype,
  * workload and writes the fastest into opts (sweep_schedule, fwd_groups). Candidates, in
  * this order: node hyperplanes with 1, 2, 4 and 8 barrier groups, then tile hyperplanes
  * 2x4x8, 4x4x4, 2x8x8 (tiles need n_src >= 32 and rows of 16-byte multiples; skipped
- * ones time 0). Each runs max_iter_fwd = 2 iterations on a scratch tau owned by the context;
- * every candidate gives the same results, so only time decides. h_ms (host [7], may be NULL)
+ * ones time 0). With Lax-Friedrichs (opts->scheme = 0) each runs max_iter_fwd = 2
+ * iterations; with a Godunov solver each runs the whole solve on the node-hyperplane
+ * schedule (tile candidates time 0), since there the sources' unequal iteration counts decide
+ * how barrier groups share the GPU. The runs use a scratch tau owned by the context; every
+ * candidate gives the same results, so only time decides. h_ms (host [7], may be NULL)
  * receives each candidate's device time per iteration. The choice is cached per
- * (n_src, dtype): a later call with the same pair only writes it into opts. */
+ * (n_src, dtype, scheme): a later call with the same triple only writes it into opts. */
 tt_status tt_autotune(tt_ctx *ctx, const tt_model *model, const tt_point *h_src, int n_src,
                       tt_opts *opts, double *h_ms);
 

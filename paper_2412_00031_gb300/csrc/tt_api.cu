@@ -1514,11 +1514,14 @@ tt_status autotune_impl(tt_ctx *ctx, const tt_model *m, const tt_point *h_src, i
     for (int c = 0; c < kTuneCandidates; ++c) {
         tt_opts o = *opts;
         o.init = 0;
-        o.max_iter_fwd = 2;
+        // Lax-Friedrichs: two iterations show the per-iteration cost. The Godunov solvers
+        // converge in a handful of iterations, and the sources' unequal counts decide how
+        // barrier groups share the GPU, so they run the whole solve (node hyperplanes only).
+        if (opts->scheme == 0) o.max_iter_fwd = 2;
         o.sweep_schedule = c < 4 ? 1 : c - 2;
         o.fwd_groups = c < 4 ? (1 << c) : 0;
         double ms = 0.0;
-        if (c < 4 || tiles_ok) {
+        if (c < 4 || (tiles_ok && opts->scheme == 0)) {
             s = forward_impl<F>(ctx, m, h_src, B, ctx->tune_tau.p, nullptr, &o, it.data());
             if (s != TT_OK && s != TT_ENOTCONVERGED) return s;
             int imax = 0;

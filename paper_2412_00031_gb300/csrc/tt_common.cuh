@@ -213,11 +213,34 @@ __device__ __forceinline__ F godunov_core(F invT0, F ur, F ut, F up, F tc, F trp
     const F r2 = mul_(rhs, rhs);
     // Each candidate root is kept as N / D with D > 0: the causality test sg (a N / D + c)
     // >= 0 becomes sg (a N + c D) >= 0 and the comparison of two roots a comparison of
-    // cross products, so only the chosen root is divided.
+    // cross products, so only the chosen root is divided. A subset's form never exceeds the
+    // full one, so a causal root on all three axes is the smallest causal root (the other
+    // subsets' quadratics are <= 0 there); the subsets are solved only where it is not.
+    {
+        F A = 0, B = 0, C = -r2;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            A = fma_(a[d], a[d], A);
+            B = fma_(a[d], c[d], B);
+            C = fma_(c[d], c[d], C);
+        }
+        const F disc = fma_(B, B, -mul_(A, C));
+        if (A > (F)0 && disc >= (F)0) {
+            const F q = sqrt_(disc);
+            const bool pos = B >= (F)0;
+            const F N = pos ? -C : sub_(q, B);
+            const F D = pos ? add_(B, q) : A;
+            bool ok = D > (F)0;
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+                if (mul_(sg[d], fma_(a[d], N, mul_(c[d], D))) < (F)0) ok = false;
+            if (ok) return add_(tc, div_(N, D));
+        }
+    }
     F bestN = (F)0, bestD = (F)1;
     bool found = false;
 #pragma unroll
-    for (int mask = 1; mask < 8; ++mask) {
+    for (int mask = 1; mask < 7; ++mask) {
         F A = 0, B = 0, C = -r2;
 #pragma unroll
         for (int d = 0; d < 3; ++d)
@@ -297,10 +320,31 @@ __device__ __forceinline__ F godunov_aniso_core(F invT0, F ur, F ut, F up, F tc,
     const F Atp = fma_(mt, aa1, fma_(mul_((F)2 * m, a[1]), a[2], mul_(mp, aa2)));
     const F Btp = fma_(mt, ac1, fma_(m, fma_(a[1], c[2], mul_(a[2], c[1])), mul_(mp, ac2)));
     const F Ctp = fma_(mt, cc1, fma_(mul_((F)2 * m, c[1]), c[2], mul_(mp, cc2)));
+    // The form on a subset S is the minimum of the full form over the components off S, so
+    // it never exceeds the full form: at a causal 3-D root tau* every subset's quadratic is
+    // <= 0 and its larger root >= tau*. A causal 3-D root is therefore the answer, and the
+    // other subsets are solved only where it is not causal.
+    {
+        const F A = add_(aa0, Atp), B = add_(ac0, Btp), C = sub_(add_(cc0, Ctp), r2);
+        const F disc = fma_(B, B, -mul_(A, C));
+        if (A > (F)0 && disc >= (F)0) {
+            const F q = sqrt_(disc);
+            const bool pos = B >= (F)0;
+            const F N = pos ? -C : sub_(q, B);
+            const F D = pos ? add_(B, q) : A;
+            const F h0 = fma_(a[0], N, mul_(c[0], D));
+            const F h1 = fma_(a[1], N, mul_(c[1], D));
+            const F h2 = fma_(a[2], N, mul_(c[2], D));
+            if (D > (F)0 && mul_(sg[0], h0) >= (F)0 &&
+                mul_(sg[1], fma_(mt, h1, mul_(m, h2))) >= (F)0 &&
+                mul_(sg[2], fma_(m, h1, mul_(mp, h2))) >= (F)0)
+                return add_(tc, div_(N, D));
+        }
+    }
     F bestN = (F)0, bestD = (F)1;
     bool found = false;
 #pragma unroll
-    for (int mask = 1; mask < 8; ++mask) {
+    for (int mask = 1; mask < 7; ++mask) {
         const bool hr = mask & 1, ht = mask & 2, hp = mask & 4;
         F A, B, C;
         if (ht && hp) {
