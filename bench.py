@@ -614,7 +614,9 @@ def inversion_leg(args):
     t_obs = time.perf_counter() - t0
     model = tuple(torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32), device=dev)
                   for a in (w.s, w.xi, w.eta))
-    inv = Inversion(ctx, model, None, None, g.shape, tt.mgrid(11, 11, 11, 5), batches=batches)
+    opts = tt.default_opts(tt.TT_F32, scheme=args.inv_scheme)
+    inv = Inversion(ctx, model, None, None, g.shape, tt.mgrid(11, 11, 11, 5), opts=opts,
+                    batches=batches)
     times, hist = [], []
     step, chi = 0.02, None
     torch.cuda.synchronize()
@@ -652,6 +654,8 @@ def inversion_leg(args):
             "accepted": [h[2] for h in hist], "iters_fwd_mean": its,
             "config": {"workload": "inversion 201x201x101, %d sources in batches of %d, "
                                    "400 stations, 5 offset 11^3 inversion grids" % (w.n_src, args.inv_batch),
+                       "forward_scheme": ["Lax-Friedrichs", "Godunov (isotropic)",
+                                          "Godunov (anisotropic)"][args.inv_scheme],
                        "abs_records": int(len(w.abs_rec)), "cs_pairs": int(len(w.cs_m)),
                        "cr_entries": int(n_cr), "precision": "fp32 sweeps, fp64 misfit and kernels"},
             "data": "synthetic: observations from FP32 solves in the true checkerboard model + "
@@ -819,6 +823,8 @@ def main():
                          "201x201x101 workload instead of the benchmark step")
     ap.add_argument("--inv-sources", type=int, default=1024)
     ap.add_argument("--inv-batch", type=int, default=256)
+    ap.add_argument("--inv-scheme", type=int, default=0,
+                    help="forward local solver of the inversion loop (tt_opts.scheme)")
     args = ap.parse_args()
     if args.infer_only > 0:
         print(json.dumps(infer_only(args)))
