@@ -11,6 +11,8 @@ the FP64 oracle runs one source at a time on the host).
   the 1e-5 bar.
   The oracle's adjoint state, computed from its own traveltime, must match the GPU's P to
   the 1e-3 bar.
+- the same batch with the anisotropic Godunov forward (the benchmark's godunov leg), in its
+  launch configuration: sampled sources solved alone give their batch columns' bits.
 """
 import numpy as np
 import pytest
@@ -93,3 +95,36 @@ def test_anisotropic_batch_in_the_benchmark_configuration(tt):
     Po, _, aconv, _ = O.adjoint(gd, To, xi, eta, w.src[b], w.rec, Ro, tol=1e-8, max_iter=200)
     assert aconv
     assert rel_l2(P_b, Po) <= 1e-3
+
+
+def test_anisotropic_batch_with_the_godunov_solver_in_the_benchmark_configuration(tt):
+    """The benchmark's godunov leg at full size: 121 x 161 x 161, 256 sources, anisotropic
+    Godunov forward (R16) with the autotuned launch inside a captured graph. A cold oracle
+    solve takes minutes here, so the check is one that holds at any size: the slowest and
+    the fastest source, each solved alone with the default launch, give their batch
+    columns' bits (traveltime, adjoint field and iteration counts). Their agreement with the
+    oracle is tested at 81^3 (tests/test_gpu_godunov.py)."""
+    import torch
+    w = I.anisotropic_batch()
+    g = w.grid
+    model = tuple(to_dev(a, torch.float32) for a in (w.s, w.xi, w.eta))
+    ctx = tt.tt_ctx_create(g.as_dict())
+    o = tt.default_opts(tt.TT_F32, scheme=2)
+    tt.tt_autotune(ctx, model, w.src, o)
+    shape = g.shape + (w.n_src,)
+    tau, T, P = (torch.empty(shape, device="cuda") for _ in range(3))
+    data = tt.DeviceData.from_workload(w)
+    chi = torch.empty((w.n_src, 2), dtype=torch.float64, device="cuda")
+    R = torch.empty((w.n_src, data.n_rec), dtype=torch.float64, device="cuda")
+    K = [torch.zeros(g.shape, dtype=torch.float64, device="cuda") for _ in range(3)]
+    plan = tt.tt_plan_create(ctx, model, w.src, data, tau, T, P, chi, R, *K, opts=o)
+    itf, ita = tt.tt_plan_run(plan)
+    plan.close()
+    assert int(np.max(itf)) <= 15
+    for b in (int(np.argmax(itf)), int(np.argmin(itf))):
+        one = gpu_solve(w.subset([b]), "f32", opts=tt.default_opts(tt.TT_F32, scheme=2),
+                        ctx=ctx)
+        assert np.array_equal(one["T"][..., 0], T[..., b].cpu().numpy())
+        assert np.array_equal(one["P"][..., 0], P[..., b].cpu().numpy())
+        assert int(one["iters_fwd"][0]) == int(itf[b])
+    ctx.close()
