@@ -341,10 +341,9 @@ __device__ __forceinline__ F godunov_aniso_core(F invT0, F ur, F ut, F up, F tc,
                 return add_(tc, div_(N, D));
         }
     }
-    F bestN = (F)0, bestD = (F)1;
-    bool found = false;
-#pragma unroll
-    for (int mask = 1; mask < 7; ++mask) {
+    // One axis subset (bit 0 r, bit 1 theta, bit 2 phi): its root as N / D and whether it is
+    // valid and causal.
+    auto cand = [&](const int mask, F &N, F &D) -> bool {
         const bool hr = mask & 1, ht = mask & 2, hp = mask & 4;
         F A, B, C;
         if (ht && hp) {
@@ -363,12 +362,12 @@ __device__ __forceinline__ F godunov_aniso_core(F invT0, F ur, F ut, F up, F tc,
             C = sub_(cc0, r2);
         }
         const F disc = fma_(B, B, -mul_(A, C));
-        if (!(A > (F)0) || disc < (F)0) continue;
+        if (!(A > (F)0) || disc < (F)0) return false;
         const F q = sqrt_(disc);
         const bool pos = B >= (F)0;
-        const F N = pos ? -C : sub_(q, B);
-        const F D = pos ? add_(B, q) : A;
-        if (!(D > (F)0)) continue;
+        N = pos ? -C : sub_(q, B);
+        D = pos ? add_(B, q) : A;
+        if (!(D > (F)0)) return false;
         // D (a delta + c) on each axis, then the causality test on W g
         const F h0 = fma_(a[0], N, mul_(c[0], D));
         const F h1 = fma_(a[1], N, mul_(c[1], D));
@@ -382,12 +381,30 @@ __device__ __forceinline__ F godunov_aniso_core(F invT0, F ur, F ut, F up, F tc,
         } else if (hp) {
             ok = ok && mul_(sg[2], h2) >= (F)0;
         }
-        if (ok && (!found || mul_(N, bestD) < mul_(bestN, D))) {
+        return ok;
+    };
+    F bestN = (F)0, bestD = (F)1;
+    bool found = false;
+    auto take = [&](const F N, const F D) {
+        if (!found || mul_(N, bestD) < mul_(bestN, D)) {
             bestN = N;
             bestD = D;
             found = true;
         }
-    }
+    };
+    F N, D;
+    const bool ok3 = cand(3, N, D);
+    if (ok3) take(N, D);
+    const bool ok5 = cand(5, N, D);
+    if (ok5) take(N, D);
+    const bool ok6 = cand(6, N, D);
+    if (ok6) take(N, D);
+    // By the same argument a causal root on two axes is no larger than the roots on either
+    // of its single axes, so a single axis is solved only where neither pair holding it is
+    // causal.
+    if (!ok3 && !ok5 && cand(1, N, D)) take(N, D);
+    if (!ok3 && !ok6 && cand(2, N, D)) take(N, D);
+    if (!ok5 && !ok6 && cand(4, N, D)) take(N, D);
     return found ? add_(tc, div_(bestN, bestD)) : tc;
 }
 
