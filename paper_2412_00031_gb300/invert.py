@@ -15,14 +15,23 @@ The model moves along the direction (tt_model_update). Step-size control (the re
 the cited method, which the paper does not spell out): a step that raises chi is undone and
 the step size halved.
 
+With relocate = (step_km, step_s) the hypocentres and origin times are updated during the
+inversion too (Sec. 2, Eq. 10). The arrivals become T_n(x_m) + tau_n, so the misfit of each
+batch is taken from the table of receiver times plus origin times (tt_misfit_table). After
+each model step, the receivers are solved as sources in the current model (tt_forward,
+reciprocity) and each batch's events take one gradient step (tt_field_at_points,
+tt_reloc_kernels, tt_reloc_update). A step that raises that batch's chi is undone and its
+step sizes halved.
+
 Every step of the arithmetic runs in the library's kernels. This module sequences the calls
 and holds the buffers; it reads back chi (n_src x 2) and the largest K_d to set eps.
 """
 import numpy as np
 
-from . import (default_opts, mgrid, tt_adjoint, tt_forward, tt_kernel, tt_kernel_density,
-               tt_kernel_normalize, tt_mgrid_expand, tt_mgrid_project, tt_misfit,
-               tt_misfit_cr, tt_model_update)
+from . import (default_opts, mgrid, tt_adjoint, tt_field_at_points, tt_forward, tt_kernel,
+               tt_kernel_density, tt_kernel_normalize, tt_mgrid_expand, tt_mgrid_project,
+               tt_misfit, tt_misfit_cr, tt_misfit_table, tt_model_update, tt_reloc_kernels,
+               tt_reloc_update)
 
 
 class _Batch:
@@ -42,6 +51,23 @@ class _Batch:
             Rhat[b, data.h_abs_rec[data.h_abs_off[b]:data.h_abs_off[b + 1]]] = 1.0
         self.Rhat = torch.as_tensor(Rhat, **f64)
 
+    def enable_relocation(self, torch, dev, step_km, step_s):
+        """Device copies of the event positions and origin times, and the relocation
+        buffers."""
+        B, nr = len(self.src), self.data.n_rec
+        f64 = dict(dtype=torch.float64, device=dev)
+        self.pts = torch.as_tensor(np.asarray(self.src, dtype=np.float64), **f64).contiguous()
+        self.otime = torch.zeros(B, **f64)
+        self.rstep = [float(step_km), float(step_s)]
+        self.Tra = torch.empty((B, nr), **f64)
+        self.val = torch.empty((B, nr), **f64)
+        self.grad = torch.empty((B, nr, 3), **f64)
+        self.chi_r = torch.empty((B, 2), **f64)
+        self.R_r = torch.empty((B, nr), **f64)
+        self.chi_cr_r = torch.zeros(B, **f64)
+        self.Kx = torch.empty((B, 3), **f64)
+        self.Kt = torch.empty(B, **f64)
+
 
 class Inversion:
     """Buffers and calls of the loop for the sources, data and inversion grids. The sources
@@ -50,7 +76,7 @@ class Inversion:
     over all of them (cr pairs stay within their batch)."""
 
     def __init__(self, ctx, model, src, data, grid_shape, mg, opts=None, eps_rel=1e-2,
-                 zeta=0.5, cr=None, batches=None):
+                 zeta=0.5, cr=None, batches=None, relocate=None):
         import torch
         self.torch = torch
         self.ctx, self.model, self.mg = ctx, model, mg
@@ -69,6 +95,16 @@ class Inversion:
         self.Kd = torch.empty(self.shape, **f64)
         self.D = [torch.empty(self.shape, **f64) for _ in range(3)]
         self.G = torch.empty((mg.n_grids, mg.n_r, mg.n_t, mg.n_p), **f64)
+        self.relocate = relocate is not None
+        self.reloc_hist = []
+        if self.relocate:
+            rec = self.batches[0].data.rec
+            for bt in self.batches:
+                assert np.array_equal(bt.data.rec, rec), "batches must share the receiver list"
+                bt.enable_relocation(torch, dev, *relocate)
+            self.rec = rec
+            self.tauG = torch.empty(self.shape + (len(rec),), dtype=F, device=dev)
+            self.Gam = torch.empty_like(self.tauG)
 
     def _fields(self, B):
         """tau, T, P, P_hat views for a batch of B sources (node-major, source fastest)."""
@@ -87,8 +123,12 @@ class Inversion:
             tau, T, P, Phat = self._fields(len(bt.src))
             bt.iters_fwd = tt_forward(c, m, bt.src, tau, T, self.opts)
             tt_misfit(c, T, bt.data, bt.Tr, bt.chi, bt.R)
+            Tr = bt.Tr
+            if self.relocate:                   # arrivals with the origin times
+                tt_misfit_table(c, bt.Tr, bt.otime, bt.data, bt.Tra, bt.chi, bt.R)
+                Tr = bt.Tra
             if bt.cr is not None:
-                tt_misfit_cr(c, bt.cr, bt.Tr, bt.chi_cr, bt.R)
+                tt_misfit_cr(c, bt.cr, Tr, bt.chi_cr, bt.R)
             bt.iters_adj = tt_adjoint(c, m, bt.src, T, bt.data.rec, bt.R, P, self.opts)
             tt_kernel(c, m, T, P, *self.K)
             tt_adjoint(c, m, bt.src, T, bt.data.rec, bt.Rhat, Phat, self.opts)
@@ -106,6 +146,35 @@ class Inversion:
         for K, D in zip(self.K, self.D):
             tt_mgrid_project(self.ctx, self.mg, K, self.G)
             tt_mgrid_expand(self.ctx, self.mg, self.G, D)
+
+    def _reloc_chi(self, bt):
+        """chi of a batch's events from the receiver-started fields; leaves K_x, K_tau."""
+        c = self.ctx
+        tt_field_at_points(c, self.Gam, bt.pts, bt.val, bt.grad)
+        tt_misfit_table(c, bt.val, bt.otime, bt.data, bt.Tra, bt.chi_r, bt.R_r)
+        if bt.cr is not None:
+            tt_misfit_cr(c, bt.cr, bt.Tra, bt.chi_cr_r, bt.R_r)
+        tt_reloc_kernels(c, bt.R_r, bt.grad, bt.Kx, bt.Kt)
+        chi = bt.chi_r.cpu().numpy()
+        total = bt.data.alpha * chi[:, 0].sum() + bt.data.beta * chi[:, 1].sum()
+        if bt.cr is not None:
+            total += bt.cr.gamma * bt.chi_cr_r.cpu().numpy().sum()
+        return float(total)
+
+    def relocate_events(self):
+        """One relocation step of every batch's events in the current model."""
+        tt_forward(self.ctx, self.model, self.rec, self.tauG, self.Gam, self.opts)
+        for bt in self.batches:
+            before = self._reloc_chi(bt)
+            saved = (bt.pts.clone(), bt.otime.clone())
+            tt_reloc_update(self.ctx, bt.pts, bt.otime, bt.Kx, bt.Kt, *bt.rstep)
+            after = self._reloc_chi(bt)
+            if after >= before:
+                bt.pts.copy_(saved[0])
+                bt.otime.copy_(saved[1])
+                bt.rstep = [s * 0.5 for s in bt.rstep]
+            self.reloc_hist.append((before, after, after < before))
+            bt.src = bt.pts.cpu().numpy()
 
     def run(self, n_iter, step):
         """n_iter step attempts; returns the history [(chi, step, accepted)], first entry the
@@ -126,13 +195,17 @@ class Inversion:
                     a.copy_(b)
                 hist.append((new, step, False))
                 step *= 0.5
+            if self.relocate:                   # move the events, then refresh chi and kernels
+                self.relocate_events()
+                chi = self.evaluate()
+                self.direction()
         return hist
 
 
 def invert(ctx, model, src, data, grid_shape, n_r=11, n_t=11, n_p=11, n_grids=5, n_iter=10,
-           step=0.02, opts=None, eps_rel=1e-2, zeta=0.5, cr=None, batches=None):
+           step=0.02, opts=None, eps_rel=1e-2, zeta=0.5, cr=None, batches=None, relocate=None):
     """The loop on n_grids offset inversion grids of n_r x n_t x n_p nodes; the model tensors
     are updated in place. Returns the history of Inversion.run."""
     inv = Inversion(ctx, model, src, data, grid_shape, mgrid(n_r, n_t, n_p, n_grids), opts,
-                    eps_rel, zeta, cr, batches)
+                    eps_rel, zeta, cr, batches, relocate)
     return inv.run(n_iter, step)
