@@ -73,10 +73,13 @@ class Inversion:
     """Buffers and calls of the loop for the sources, data and inversion grids. The sources
     come as one batch (src, data, cr) or as several: batches = [(src, data, cr), ...], each
     solved in turn on shared field buffers, with the kernels, kernel density and chi summed
-    over all of them (cr pairs stay within their batch)."""
+    over all of them. A batch's cr pairs stay within it; cr_all (a CrData over all sources,
+    numbered in batch order) holds pairs across batches. Then every batch's traveltime field
+    is kept until the receiver-time tables of all batches give the common-receiver adjoint
+    sources (Eq. A4), and the adjoints follow."""
 
     def __init__(self, ctx, model, src, data, grid_shape, mg, opts=None, eps_rel=1e-2,
-                 zeta=0.5, cr=None, batches=None, relocate=None):
+                 zeta=0.5, cr=None, batches=None, relocate=None, cr_all=None):
         import torch
         self.torch = torch
         self.ctx, self.model, self.mg = ctx, model, mg
@@ -95,6 +98,18 @@ class Inversion:
         self.Kd = torch.empty(self.shape, **f64)
         self.D = [torch.empty(self.shape, **f64) for _ in range(3)]
         self.G = torch.empty((mg.n_grids, mg.n_r, mg.n_t, mg.n_p), **f64)
+        self.cr_all = cr_all
+        if cr_all is not None:
+            assert all(b.cr is None for b in self.batches), "cr pairs go in cr_all"
+            n_all = sum(len(b.src) for b in self.batches)
+            n_rec = self.batches[0].data.n_rec
+            assert cr_all.n_src == n_all and cr_all.n_rec == n_rec
+            # the traveltime fields of all batches, kept until the adjoints
+            self.T_all = [torch.empty(self.shape + (len(b.src),), dtype=F, device=dev)
+                          for b in self.batches]
+            self.Tr_all = torch.empty((n_all, n_rec), **f64)
+            self.R_all = torch.empty((n_all, n_rec), **f64)
+            self.chi_cr_all = torch.zeros(n_all, **f64)
         self.relocate = relocate is not None
         self.reloc_hist = []
         if self.relocate:
@@ -119,16 +134,15 @@ class Inversion:
             K.zero_()
         self.Kd.zero_()
         total = 0.0
-        for bt in self.batches:
+        if self.cr_all is not None:
+            total += self._forward_all()
+        for q, bt in enumerate(self.batches):
             tau, T, P, Phat = self._fields(len(bt.src))
-            bt.iters_fwd = tt_forward(c, m, bt.src, tau, T, self.opts)
-            tt_misfit(c, T, bt.data, bt.Tr, bt.chi, bt.R)
-            Tr = bt.Tr
-            if self.relocate:                   # arrivals with the origin times
-                tt_misfit_table(c, bt.Tr, bt.otime, bt.data, bt.Tra, bt.chi, bt.R)
-                Tr = bt.Tra
-            if bt.cr is not None:
-                tt_misfit_cr(c, bt.cr, Tr, bt.chi_cr, bt.R)
+            if self.cr_all is not None:
+                T = self.T_all[q]
+            else:
+                bt.iters_fwd = tt_forward(c, m, bt.src, tau, T, self.opts)
+                self._misfit(bt, T)
             bt.iters_adj = tt_adjoint(c, m, bt.src, T, bt.data.rec, bt.R, P, self.opts)
             tt_kernel(c, m, T, P, *self.K)
             tt_adjoint(c, m, bt.src, T, bt.data.rec, bt.Rhat, Phat, self.opts)
@@ -138,6 +152,40 @@ class Inversion:
             if bt.cr is not None:
                 total += bt.cr.gamma * bt.chi_cr.cpu().numpy().sum()
         return float(total)
+
+    def _misfit(self, bt, T):
+        """The batch's receiver times, misfit and adjoint sources (within-batch cr pairs);
+        returns the table of arrivals."""
+        c = self.ctx
+        tt_misfit(c, T, bt.data, bt.Tr, bt.chi, bt.R)
+        Tr = bt.Tr
+        if self.relocate:                       # arrivals with the origin times
+            tt_misfit_table(c, bt.Tr, bt.otime, bt.data, bt.Tra, bt.chi, bt.R)
+            Tr = bt.Tra
+        if bt.cr is not None:
+            tt_misfit_cr(c, bt.cr, Tr, bt.chi_cr, bt.R)
+        return Tr
+
+    def _forward_all(self):
+        """Forward solves and misfits of every batch, then the common-receiver terms across
+        batches on the joined tables; each batch's R gets its rows back. Returns gamma chi_cr."""
+        c, m = self.ctx, self.model
+        row = 0
+        for q, bt in enumerate(self.batches):
+            tau = self._fields(len(bt.src))[0]
+            bt.iters_fwd = tt_forward(c, m, bt.src, tau, self.T_all[q], self.opts)
+            Tr = self._misfit(bt, self.T_all[q])
+            B = len(bt.src)
+            self.Tr_all[row:row + B].copy_(Tr)
+            self.R_all[row:row + B].copy_(bt.R)
+            row += B
+        tt_misfit_cr(c, self.cr_all, self.Tr_all, self.chi_cr_all, self.R_all)
+        row = 0
+        for bt in self.batches:
+            B = len(bt.src)
+            bt.R.copy_(self.R_all[row:row + B])
+            row += B
+        return self.cr_all.gamma * float(self.chi_cr_all.sum())
 
     def direction(self):
         """The smoothed, density-normalised descent direction from the last evaluation."""
@@ -203,9 +251,10 @@ class Inversion:
 
 
 def invert(ctx, model, src, data, grid_shape, n_r=11, n_t=11, n_p=11, n_grids=5, n_iter=10,
-           step=0.02, opts=None, eps_rel=1e-2, zeta=0.5, cr=None, batches=None, relocate=None):
+           step=0.02, opts=None, eps_rel=1e-2, zeta=0.5, cr=None, batches=None, relocate=None,
+           cr_all=None):
     """The loop on n_grids offset inversion grids of n_r x n_t x n_p nodes; the model tensors
     are updated in place. Returns the history of Inversion.run."""
     inv = Inversion(ctx, model, src, data, grid_shape, mgrid(n_r, n_t, n_p, n_grids), opts,
-                    eps_rel, zeta, cr, batches, relocate)
+                    eps_rel, zeta, cr, batches, relocate, cr_all)
     return inv.run(n_iter, step)

@@ -271,3 +271,34 @@ def test_joint_relocation_lowers_chi_below_the_model_only_loop(tt):
     ctx.close()
     assert out["joint"][0] < 0.8 * out["model"][0]
     assert err1 < 0.8 * err0
+
+
+def test_common_receiver_pairs_across_batches_equal_one_batch(tt):
+    """Common-receiver pairs that span two batches (cr_all): the kept traveltime fields and
+    the joined receiver-time tables give the single batch's chi, kernels and kernel density
+    (up to the order of the FP64 sums)."""
+    import torch
+    from paper_2412_00031_gb300.invert import Inversion
+    w = I.small_case(89, shape=(13, 15, 17), n_src=7, n_rec=9)
+    g = w.grid.as_dict()
+    rng = np.random.default_rng(89)
+    nr = len(w.rec)
+    pairs = [(b, j, m, rng.normal(0, 0.3), rng.uniform(0.5, 1.5)) for m in range(nr)
+             for b in range(7) for j in range(b + 1, 7) if rng.uniform() < 0.5]
+    assert any(b < 4 <= j for b, j, _, _, _ in pairs), "no pair spans the two batches"
+    model = tuple(_dev(a, torch.float32) for a in (w.s, w.xi, w.eta))
+    ctx = tt.tt_ctx_create(g)
+    mg = tt.mgrid(4, 4, 4, 2)
+    one = Inversion(ctx, model, w.src, tt.DeviceData.from_workload(w), w.grid.shape, mg,
+                    cr=tt.CrData(7, nr, pairs, gamma=0.7))
+    c1 = one.evaluate()
+    parts = [w.subset(range(0, 4)), w.subset(range(4, 7))]
+    two = Inversion(ctx, model, None, None, w.grid.shape, mg,
+                    batches=[(p.src, tt.DeviceData.from_workload(p), None) for p in parts],
+                    cr_all=tt.CrData(7, nr, pairs, gamma=0.7))
+    c2 = two.evaluate()
+    assert abs(c1 - c2) <= 1e-12 * c1
+    for a, b in zip(one.K + [one.Kd], two.K + [two.Kd]):
+        a, b = a.cpu().numpy(), b.cpu().numpy()
+        assert np.abs(a - b).max() <= 1e-12 * np.abs(a).max()
+    ctx.close()
