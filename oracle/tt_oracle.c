@@ -28,6 +28,15 @@
  *      smallest root, over the 7 non-empty subsets of axes, of
  *      sum_d (a_d tau - b_d)^2 = (s / T0)^2 (the larger root of each quadratic) whose
  *      one-sided differences all have the upwind sign; with no such root tau_c is kept.
+ *  R17 Teleseismic sources (the boundary condition of Eq. "4" for an event outside the region):
+ *      the times on the region's faces come from a 2-D eikonal solve in a 1-D global model
+ *      s(r), in (r, Delta) with Delta the epicentral angle from the event. The 2-D solve is
+ *      factored as R2 (T0 = s(r_s) x chord) with R14's Godunov update in two dimensions,
+ *      mirror symmetry on the axis Delta = 0, R6's extrapolation on the other faces, and R3's
+ *      fixed set (3 x 2 nodes next to the event, on the axis). The faces of the 3-D region
+ *      take the bilinear interpolation of the 2-D times at their (r, Delta). The 3-D solve
+ *      is R4's Lax-Friedrichs update on T itself (T0 = 1, no factor), with the faces held
+ *      fixed (Dirichlet data, no extrapolation) and the interior swept from a given start.
  *  R16 Godunov local solver for anisotropic models (M of Eq. "4" with xi, eta; an alternative
  *      to R4): as R14, with two changes. (a) Along theta and phi the upwind neighbour is the
  *      side the characteristic comes from: the sign of (M g)_d, g the central-difference
@@ -880,4 +889,171 @@ void or_adjoint_sweeps(const or_grid *g, const double *T, const double *xi, cons
     for (long q = 0; q < N; q++) P[q] = 0.0;
     for (int q = 0; q < n_sweeps; q++) adj_sweep(&G, &S, T, xi, eta, P, JS, q % 8);
     free(JS);
+}
+
+/* ---------------------------------------------------------------- teleseismic (R17) */
+
+/* Slowness of the 1-D model at radius r: linear between the n_r samples s_r on
+ * [r_min, r_max]. */
+static double s_of_r(int n_r, double r_min, double dr, const double *s_r, double r)
+{
+    double f = (r - r_min) / dr;
+    int i = (int)floor(f);
+    if (i < 0) i = 0;
+    if (i > n_r - 2) i = n_r - 2;
+    double w = f - i;
+    return (1.0 - w) * s_r[i] + w * s_r[i + 1];
+}
+
+/* The 2-D factored Godunov update at (i, j) of the (r, Delta) grid: R14 in two dimensions.
+ * Physical gradient components (d/dr, d/(r dDelta)); the factor T0 = s_s L with L the chord
+ * from the event at (r_s, 0) to (r, Delta), u = grad T0 / T0 = (r - r_s cos D, r_s sin D) / L^2. */
+static double god2d_update(int n_r, int n_d, double r_min, double dr, double dd, double r_s,
+                           double s_s, const double *s_r, const double *tau, int i, int j)
+{
+    double r = r_min + i * dr, D = j * dd;
+    double L2 = r * r + r_s * r_s - 2.0 * r * r_s * cos(D);
+    double L = sqrt(L2), T0 = s_s * L;
+    double u[2] = {(r - r_s * cos(D)) / L2, r_s * sin(D) / L2};
+    double e[2] = {1.0 / dr, 1.0 / (r * dd)};
+    double lo[2] = {tau[(i - 1) * n_d + j], tau[i * n_d + (j > 0 ? j - 1 : 1)]};
+    double hi[2] = {tau[(i + 1) * n_d + j], tau[i * n_d + j + 1]};
+    double a[2], b[2], sg[2];
+    for (int d = 0; d < 2; d++) {
+        double tlo = lo[d] * (1.0 - u[d] / e[d]), thi = hi[d] * (1.0 + u[d] / e[d]);
+        sg[d] = tlo <= thi ? 1.0 : -1.0;
+        double nb = tlo <= thi ? lo[d] : hi[d];
+        a[d] = u[d] + sg[d] * e[d];
+        b[d] = sg[d] * e[d] * nb;
+    }
+    double rhs = s_of_r(n_r, r_min, dr, s_r, r) / T0;
+    double best = -1.0;
+    for (int mask = 1; mask < 4; mask++) {
+        double A = 0.0, B = 0.0, C = -rhs * rhs;
+        for (int d = 0; d < 2; d++)
+            if (mask >> d & 1) { A += a[d] * a[d]; B += a[d] * b[d]; C += b[d] * b[d]; }
+        double disc = B * B - A * C;
+        if (!(A > 0.0) || disc < 0.0) continue;
+        double t = (B + sqrt(disc)) / A;
+        int ok = 1;
+        for (int d = 0; d < 2; d++)
+            if ((mask >> d & 1) && sg[d] * (a[d] * t - b[d]) < 0.0) ok = 0;
+        if (ok && (best < 0.0 || t < best)) best = t;
+    }
+    return best < 0.0 ? tau[i * n_d + j] : best;
+}
+
+/* 2-D traveltimes from an event at radius r_s (R17): T [n_r][n_d] on r in [r_min, r_max],
+ * Delta in [0, d_max] (radians), 1-D slowness s_r [n_r]. Returns iterations; *conv = 1 when
+ * the largest change of an iteration fell below tol. */
+int or_tele2d(int n_r, int n_d, double r_min, double r_max, double d_max, const double *s_r,
+              double r_s, double tol, int max_iter, double *T, int *conv)
+{
+    double dr = (r_max - r_min) / (n_r - 1), dd = d_max / (n_d - 1);
+    double s_s = s_of_r(n_r, r_min, dr, s_r, r_s);
+    int is = (int)floor((r_s - r_min) / dr + 0.5);
+    if (is < 0) is = 0;
+    if (is > n_r - 1) is = n_r - 1;
+    double *tau = (double *)malloc(sizeof(double) * (size_t)n_r * n_d);
+    if (!tau) return -1;
+    for (long q = 0; q < (long)n_r * n_d; q++) tau[q] = 1.0;
+    int it = 0;
+    *conv = 0;
+    while (it < max_iter) {
+        double err = 0.0;
+        for (int o = 0; o < 4; o++) {
+            int di = (o & 2) ? -1 : 1, dj = (o & 1) ? -1 : 1;
+            for (int a = 0; a < n_r - 2; a++)
+                for (int b = 0; b < n_d - 1; b++) {
+                    int i = di > 0 ? 1 + a : n_r - 2 - a;
+                    int j = dj > 0 ? b : n_d - 2 - b;
+                    if (abs(i - is) <= 1 && j <= 1) continue;       /* fixed set */
+                    double v = god2d_update(n_r, n_d, r_min, dr, dd, r_s, s_s, s_r, tau, i, j);
+                    err = fmax(err, fabs(v - tau[i * n_d + j]));
+                    tau[i * n_d + j] = v;
+                }
+            /* faces r (low, high), then Delta = d_max (R6); the axis Delta = 0 is a mirror */
+            for (int j = 0; j < n_d; j++) {
+                if (!(abs(0 - is) <= 1 && j <= 1))
+                    tau[j] = fmax(2.0 * tau[n_d + j] - tau[2 * n_d + j], tau[2 * n_d + j]);
+                if (!(abs(n_r - 1 - is) <= 1 && j <= 1))
+                    tau[(n_r - 1) * n_d + j] = fmax(2.0 * tau[(n_r - 2) * n_d + j] - tau[(n_r - 3) * n_d + j],
+                                                    tau[(n_r - 3) * n_d + j]);
+            }
+            for (int i = 0; i < n_r; i++)
+                tau[i * n_d + n_d - 1] = fmax(2.0 * tau[i * n_d + n_d - 2] - tau[i * n_d + n_d - 3],
+                                              tau[i * n_d + n_d - 3]);
+        }
+        it++;
+        if (err < tol) { *conv = 1; break; }
+    }
+    for (int i = 0; i < n_r; i++)
+        for (int j = 0; j < n_d; j++) {
+            double r = r_min + i * dr, D = j * dd;
+            double L = sqrt(fmax(r * r + r_s * r_s - 2.0 * r * r_s * cos(D), 0.0));
+            T[i * n_d + j] = s_s * L * tau[i * n_d + j];
+        }
+    free(tau);
+    return it;
+}
+
+/* R4's Lax-Friedrichs update of T itself (T0 = 1, no factor) at an interior node. */
+static double lf_plain_update(const geo *G, const double *s, const double *xi, const double *eta,
+                              const double *T, int i, int j, int k)
+{
+    long c = idx(G, i, j, k);
+    double r = rad_of(G, i), th = lat_of(G, j);
+    double h[3] = {1.0, h2_at(G, r), h3_at(G, r, th)};
+    double del[3] = {G->dr, G->dt, G->dp};
+    double tp[3], tm[3];
+    tp[0] = T[idx(G, i + 1, j, k)]; tm[0] = T[idx(G, i - 1, j, k)];
+    tp[1] = T[idx(G, i, j + 1, k)]; tm[1] = T[idx(G, i, j - 1, k)];
+    tp[2] = T[idx(G, i, j, k + 1)]; tm[2] = T[idx(G, i, j, k - 1)];
+    double p[3];
+    for (int d = 0; d < 3; d++) p[d] = (tp[d] - tm[d]) / (2.0 * del[d]) / h[d];
+    double M[3][3];
+    aniso_M(xi[c], eta[c], M);
+    double q = 0.0;
+    for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++) q += p[a] * M[a][b] * p[b];
+    double sigma[3] = {1.0, sqrt(1.0 - 2.0 * xi[c]) / h[1], sqrt(1.0 + 2.0 * xi[c]) / h[2]};
+    double num = s[c] - sqrt(q), den = 0.0;
+    for (int d = 0; d < 3; d++) {
+        num += sigma[d] * (tp[d] + tm[d]) / (2.0 * del[d]);
+        den += sigma[d] / del[d];
+    }
+    return num / den;
+}
+
+/* The 3-D solve of a teleseismic event (R17): T [N] holds the start on entry, its boundary
+ * nodes (the six faces) being the Dirichlet data, which are kept; interior nodes are swept
+ * in the 8 orderings of R5 until the largest change of an iteration is below tol. */
+int or_forward_tele(const or_grid *g, const double *s, const double *xi, const double *eta,
+                    double tol, int max_iter, double *T, int *conv, double *last_err)
+{
+    geo G = make_geo(g);
+    int it = 0;
+    double err = 0.0;
+    *conv = 0;
+    while (it < max_iter) {
+        err = 0.0;
+        for (int o = 0; o < 8; o++) {
+            int dr = (o & 4) ? -1 : 1, dt = (o & 2) ? -1 : 1, dp = (o & 1) ? -1 : 1;
+            for (int a = 0; a < G.nr - 2; a++)
+                for (int b = 0; b < G.nt - 2; b++)
+                    for (int c = 0; c < G.np - 2; c++) {
+                        int i = swept(a, dr, 1, G.nr - 2);
+                        int j = swept(b, dt, 1, G.nt - 2);
+                        int k = swept(c, dp, 1, G.np - 2);
+                        long n = idx(&G, i, j, k);
+                        double v = lf_plain_update(&G, s, xi, eta, T, i, j, k);
+                        err = fmax(err, fabs(v - T[n]));
+                        T[n] = v;
+                    }
+        }
+        it++;
+        if (err < tol) { *conv = 1; break; }
+    }
+    if (last_err) *last_err = err;
+    return it;
 }

@@ -108,4 +108,11 @@ void or_adjoint_sweeps(const or_grid *g, const double *T, const double *xi, cons
 #ifdef __cplusplus
 }
 #endif
+/* Teleseismic events (R17): 2-D traveltimes in a 1-D model, and the 3-D solve with the
+ * faces of the region held fixed. */
+int or_tele2d(int n_r, int n_d, double r_min, double r_max, double d_max, const double *s_r,
+              double r_s, double tol, int max_iter, double *T, int *conv);
+int or_forward_tele(const or_grid *g, const double *s, const double *xi, const double *eta,
+                    double tol, int max_iter, double *T, int *conv, double *last_err);
+
 #endif
