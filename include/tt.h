@@ -12,6 +12,8 @@
  *   tt_misfit_cr   common-receiver differential times (Eqs. 4, A4)
  *   tt_field_at_points, tt_misfit_table, tt_reloc_kernels, tt_reloc_update
  *                  earthquake location and origin-time kernels and update (Eq. 10, B1-B11)
+ *   tt_tele2d, tt_tele_region_times
+ *                  teleseismic events: 2-D times in a 1-D model and the region's face data
  *   tt_kernel_density, tt_kernel_normalize, tt_mgrid_project, tt_mgrid_expand,
  *   tt_model_update   regularisation and update of the inversion step (Eqs. 11-19)
  *
@@ -305,6 +307,30 @@ tt_status tt_reloc_kernels(tt_ctx *ctx, int n_src, int n_rec, const double *d_R,
 tt_status tt_reloc_update(tt_ctx *ctx, int n_src, double *d_pts, double *d_otime,
                           const double *d_Kx, const double *d_Ktau, double step_km,
                           double step_s);
+
+/* ---- Teleseismic events (the boundary condition of Eq. "4" for an event outside the
+ * region): the times on the region's faces come from 2-D eikonal solves in a 1-D model. ---- */
+
+/* 2-D traveltimes of n_ev events in a 1-D model, in (r, Delta) with Delta the epicentral
+ * angle: r_min_km .. r_max_km on n_r nodes, 0 .. d_max_deg on n_d nodes (n_r, n_d >= 4).
+ * d_s_r: device [n_r] slowness at the grid radii, of dtype; h_r_src_km: host [n_ev] the
+ * events' radii (inside [r_min, r_max]); d_T: device [n_ev][n_r][n_d] output of dtype.
+ * Factored (T0 = s(r_s) x chord) Godunov sweeps, the axis Delta = 0 a mirror, the other
+ * faces extrapolated; each event stops when an iteration's largest change of tau is below
+ * tol. h_iters: host [n_ev] iterations (may be NULL). Synchronises the stream;
+ * TT_ENOTCONVERGED when an event reached max_iter. */
+tt_status tt_tele2d(tt_ctx *ctx, int dtype, int n_r, int n_d, double r_min_km, double r_max_km,
+                    double d_max_deg, const void *d_s_r, int n_ev, const double *h_r_src_km,
+                    double tol, int max_iter, void *d_T, int *h_iters);
+
+/* The 2-D times of tt_tele2d interpolated (bilinearly in r and Delta) at every node of the
+ * context's grid, for events at h_events (host [n_ev]; only latitude and longitude are read):
+ * d_T device [N][n_ev] of dtype, the layout of tt_forward. Its faces are the Dirichlet data
+ * of the region's solve and its interior a starting value. The 2-D grid must cover the
+ * region (radii and epicentral angles), else TT_EINVAL. */
+tt_status tt_tele_region_times(tt_ctx *ctx, int dtype, int n_r, int n_d, double r_min_km,
+                               double r_max_km, double d_max_deg, const void *d_T2, int n_ev,
+                               const tt_point *h_events, void *d_T);
 
 /* Largest receiver count tt_misfit_noalloc accepts: the size of its static scratch. */
 #define TT_NOALLOC_MAX_REC 1024

@@ -88,7 +88,7 @@ EXPORTED = ["tt_default_opts", "tt_ctx_create", "tt_ctx_destroy", "tt_last_error
             "tt_net_adam", "tt_net_set_weights", "tt_autotune", "tt_net_infer",
             "tt_kernel_density", "tt_kernel_normalize", "tt_mgrid_project", "tt_mgrid_expand",
             "tt_model_update", "tt_misfit_cr", "tt_field_at_points", "tt_misfit_table",
-            "tt_reloc_kernels", "tt_reloc_update"]
+            "tt_reloc_kernels", "tt_reloc_update", "tt_tele2d", "tt_tele_region_times"]
 TT_NOALLOC_MAX_REC = 1024
 
 
@@ -145,13 +145,20 @@ def _load():
         [C.c_void_p] * 3
     L.tt_reloc_kernels.argtypes = [C.c_void_p, C.c_int, C.c_int] + [C.c_void_p] * 4
     L.tt_reloc_update.argtypes = [C.c_void_p, C.c_int] + [C.c_void_p] * 4 + [C.c_double] * 2
+    L.tt_tele2d.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
+                            C.c_double, C.c_void_p, C.c_int, C.POINTER(C.c_double), C.c_double,
+                            C.c_int, C.c_void_p, C.POINTER(C.c_int)]
+    L.tt_tele_region_times.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_double,
+                                       C.c_double, C.c_double, C.c_void_p, C.c_int,
+                                       C.POINTER(TTPoint), C.c_void_p]
     for name in ("tt_ctx_create", "tt_forward", "tt_misfit", "tt_adjoint", "tt_kernel",
                  "tt_get_stats", "tt_misfit_noalloc", "tt_plan_create", "tt_plan_run",
                  "tt_net_param_count", "tt_net_features", "tt_net_forward", "tt_net_loss_grad",
                  "tt_net_adam", "tt_net_set_weights", "tt_autotune", "tt_net_infer",
                  "tt_kernel_density", "tt_kernel_normalize", "tt_mgrid_project",
                  "tt_mgrid_expand", "tt_model_update", "tt_misfit_cr", "tt_field_at_points",
-                 "tt_misfit_table", "tt_reloc_kernels", "tt_reloc_update"):
+                 "tt_misfit_table", "tt_reloc_kernels", "tt_reloc_update", "tt_tele2d",
+                 "tt_tele_region_times"):
         getattr(L, name).restype = C.c_int
     return L
 
@@ -396,6 +403,32 @@ def tt_reloc_update(ctx, pts, otime, Kx, Ktau, step_km, step_s):
     _cuda_ok(pts, otime, Kx, Ktau)
     _check(ctx, lib.tt_reloc_update(ctx.handle, pts.shape[0], _ptr(pts), _ptr(otime), _ptr(Kx),
                                     _ptr(Ktau), step_km, step_s))
+
+
+def tt_tele2d(ctx, s_r, r_min, r_max, d_max_deg, r_src, T, tol=1e-8, max_iter=500,
+              allow_unconverged=False):
+    """2-D traveltimes of teleseismic events in a 1-D model: s_r [n_r] (CUDA, float32 or
+    float64) slowness at the radii r_min..r_max (km); r_src [n_ev] the events' radii (host);
+    T [n_ev, n_r, n_d] output (CUDA, same dtype) on Delta = 0..d_max_deg. Returns the
+    iterations per event."""
+    _cuda_ok(s_r, T)
+    n_ev, n_r, n_d = T.shape
+    rs = np.ascontiguousarray(r_src, dtype=np.float64)
+    it = (C.c_int * n_ev)()
+    st = lib.tt_tele2d(ctx.handle, _dtype_code(T), n_r, n_d, r_min, r_max, d_max_deg, _ptr(s_r),
+                       n_ev, rs.ctypes.data_as(C.POINTER(C.c_double)), tol, max_iter, _ptr(T), it)
+    _check(ctx, st, (TT_ENOTCONVERGED,) if allow_unconverged else ())
+    return np.frombuffer(it, dtype=np.int32).copy()
+
+
+def tt_tele_region_times(ctx, T2, r_min, r_max, d_max_deg, events, T):
+    """The 2-D times T2 [n_ev, n_r, n_d] interpolated at every node of the context's grid
+    for events at (depth, lat, lon) points (only lat and lon are read): T [..., n_ev]."""
+    _cuda_ok(T2, T)
+    n_ev, n_r, n_d = T2.shape
+    pts, n = _points(events)
+    _check(ctx, lib.tt_tele_region_times(ctx.handle, _dtype_code(T2), n_r, n_d, r_min, r_max,
+                                         d_max_deg, _ptr(T2), n_ev, pts, _ptr(T)))
 
 
 def tt_kernel_density(ctx, P_hat, Kd):

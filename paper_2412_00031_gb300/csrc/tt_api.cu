@@ -17,6 +17,7 @@
 #include "tt_internal.h"
 #include "tt_inv.h"
 #include "tt_reloc.h"
+#include "tt_tele.h"
 #include "tt_net.h"
 
 using namespace ttgb;
@@ -54,6 +55,8 @@ struct tt_ctx {
     DevBuf tune_tau, tau_w, slot_srcc, slot_int;
     // inversion step: multiple-grid tables (for mg_key), projection scratch, update scratch
     DevBuf mg_tab, mg_scr, upd_part;
+    // teleseismic events: 2-D tau scratch, event radii / coordinates and iteration counts
+    DevBuf tele_tau, tele_aux;
     int mg_key[4] = {0, 0, 0, 0};
     struct Tuned { int n_src, dtype, scheme, schedule, groups; };
     std::vector<Tuned> tuned;
@@ -1171,7 +1174,8 @@ void tt_ctx_destroy(tt_ctx *ctx) {
                       &ctx->net_b, &ctx->net_y, &ctx->net_d1, &ctx->net_d2, &ctx->net_dy,
                       &ctx->net_wt, &ctx->net_part, &ctx->net_scr, &ctx->tune_tau, &ctx->tau_w,
                       &ctx->slot_srcc, &ctx->slot_int,
-                      &ctx->net_wbf, &ctx->mg_tab, &ctx->mg_scr, &ctx->upd_part};
+                      &ctx->net_wbf, &ctx->mg_tab, &ctx->mg_scr, &ctx->upd_part,
+                      &ctx->tele_tau, &ctx->tele_aux};
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     if (ctx->h_loss) cudaFreeHost(ctx->h_loss);
@@ -1372,6 +1376,92 @@ tt_status tt_reloc_update(tt_ctx *ctx, int n_src, double *d_pts, double *d_otime
     CK(run_reloc_update(ctx->g, box, n_src, d_pts, d_otime, d_Kx, d_Ktau, step_km, step_s,
                         ctx->st));
     ctx->launches += 1;
+    return TT_OK;
+}
+
+tt_status tt_tele2d(tt_ctx *ctx, int dtype, int n_r, int n_d, double r_min_km, double r_max_km,
+                    double d_max_deg, const void *d_s_r, int n_ev, const double *h_r_src_km,
+                    double tol, int max_iter, void *d_T, int *h_iters) {
+    if (!ctx) return TT_EINVAL;
+    if (dtype != TT_F32 && dtype != TT_F64)
+        return fail(ctx, TT_EINVAL, "dtype %d is neither TT_F32 nor TT_F64", dtype);
+    if (!d_s_r || !h_r_src_km || !d_T) return fail(ctx, TT_EINVAL, "tt_tele2d: NULL argument");
+    if (n_r < 4 || n_d < 4 || n_r > 1 << 14 || n_d > 1 << 14 || n_ev < 1 || n_ev > 1 << 16)
+        return fail(ctx, TT_EINVAL, "tt_tele2d: n_r %d, n_d %d (4..16384) or n_ev %d out of range",
+                    n_r, n_d, n_ev);
+    if (!(r_max_km > r_min_km) || !(r_min_km > 0.0) || !(d_max_deg > 0.0 && d_max_deg <= 180.0))
+        return fail(ctx, TT_EINVAL, "tt_tele2d: bad 2-D grid extent");
+    if (!(tol > 0.0) || max_iter < 1) return fail(ctx, TT_EINVAL, "tt_tele2d: bad tol or max_iter");
+    for (int e = 0; e < n_ev; ++e)
+        if (!(h_r_src_km[e] >= r_min_km && h_r_src_km[e] <= r_max_km))
+            return fail(ctx, TT_EINVAL, "tt_tele2d: event %d at radius %g outside the 2-D grid", e,
+                        h_r_src_km[e]);
+    const size_t fs = dtype == TT_F32 ? sizeof(float) : sizeof(double);
+    ENSURE(ctx->tele_tau, fs * (size_t)n_ev * n_r * n_d);
+    ENSURE(ctx->tele_aux, sizeof(double) * (size_t)n_ev + sizeof(int) * (size_t)n_ev);
+    double *d_rs = (double *)ctx->tele_aux.p;
+    int *d_it = (int *)(d_rs + n_ev);
+    CK(cudaMemcpyAsync(d_rs, h_r_src_km, sizeof(double) * n_ev, cudaMemcpyHostToDevice, ctx->st));
+    const double dr = (r_max_km - r_min_km) / (n_r - 1);
+    const double dd = d_max_deg * (3.14159265358979323846 / 180.0) / (n_d - 1);
+    CK(dtype == TT_F32 ? run_tele2d<float>(n_r, n_d, r_min_km, dr, dd, d_s_r, d_rs, n_ev, tol,
+                                           max_iter, ctx->tele_tau.p, d_T, d_it, ctx->st)
+                       : run_tele2d<double>(n_r, n_d, r_min_km, dr, dd, d_s_r, d_rs, n_ev, tol,
+                                            max_iter, ctx->tele_tau.p, d_T, d_it, ctx->st));
+    ctx->launches += 1;
+    std::vector<int> it(n_ev);
+    CK(cudaMemcpyAsync(it.data(), d_it, sizeof(int) * n_ev, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    int bad = 0;
+    for (int e = 0; e < n_ev; ++e) {
+        if (h_iters) h_iters[e] = it[e];
+        bad += it[e] >= max_iter;
+    }
+    if (bad)
+        return fail(ctx, TT_ENOTCONVERGED, "tt_tele2d: %d of %d events did not converge in %d iterations",
+                    bad, n_ev, max_iter);
+    return TT_OK;
+}
+
+tt_status tt_tele_region_times(tt_ctx *ctx, int dtype, int n_r, int n_d, double r_min_km,
+                               double r_max_km, double d_max_deg, const void *d_T2, int n_ev,
+                               const tt_point *h_events, void *d_T) {
+    if (!ctx) return TT_EINVAL;
+    if (dtype != TT_F32 && dtype != TT_F64)
+        return fail(ctx, TT_EINVAL, "dtype %d is neither TT_F32 nor TT_F64", dtype);
+    if (!d_T2 || !h_events || !d_T) return fail(ctx, TT_EINVAL, "tt_tele_region_times: NULL argument");
+    if (n_r < 4 || n_d < 4 || n_ev < 1 || n_ev > TT_MAX_BATCH)
+        return fail(ctx, TT_EINVAL, "tt_tele_region_times: sizes out of range");
+    const tt_grid &gr = ctx->grid;
+    const double deg = 3.14159265358979323846 / 180.0;
+    const double r_lo = gr.earth_radius_km - gr.depth_max_km, r_hi = gr.earth_radius_km - gr.depth_min_km;
+    if (gr.geometry != 0 || r_lo < r_min_km - 1e-9 || r_hi > r_max_km + 1e-9)
+        return fail(ctx, TT_EINVAL, "tt_tele_region_times: the 2-D radii do not cover the spherical region");
+    std::vector<double> ll(2 * (size_t)n_ev);
+    for (int e = 0; e < n_ev; ++e) {
+        ll[2 * e] = h_events[e].lat_deg * deg;
+        ll[2 * e + 1] = h_events[e].lon_deg * deg;
+        // the region's largest epicentral angle: its eight corners bound it on a small region
+        for (int c = 0; c < 4; ++c) {
+            const double th = (c & 1 ? gr.lat_max_deg : gr.lat_min_deg) * deg;
+            const double ph = (c & 2 ? gr.lon_max_deg : gr.lon_min_deg) * deg;
+            double cd = sin(th) * sin(ll[2 * e]) + cos(th) * cos(ll[2 * e]) * cos(ph - ll[2 * e + 1]);
+            cd = cd > 1.0 ? 1.0 : (cd < -1.0 ? -1.0 : cd);
+            if (acos(cd) > d_max_deg * deg)
+                return fail(ctx, TT_EINVAL, "tt_tele_region_times: event %d is farther than the 2-D grid's %g deg", e, d_max_deg);
+        }
+    }
+    ENSURE(ctx->tele_aux, sizeof(double) * 2 * (size_t)n_ev);
+    CK(cudaMemcpyAsync(ctx->tele_aux.p, ll.data(), sizeof(double) * 2 * n_ev, cudaMemcpyHostToDevice,
+                       ctx->st));
+    const double dr2 = (r_max_km - r_min_km) / (n_r - 1);
+    const double dd = d_max_deg * deg / (n_d - 1);
+    CK(dtype == TT_F32 ? run_region_times<float>(ctx->g, n_r, n_d, r_min_km, dr2, dd, d_T2, n_ev,
+                                                 (const double *)ctx->tele_aux.p, d_T, ctx->st)
+                       : run_region_times<double>(ctx->g, n_r, n_d, r_min_km, dr2, dd, d_T2, n_ev,
+                                                  (const double *)ctx->tele_aux.p, d_T, ctx->st));
+    ctx->launches += 1;
+    CK(cudaStreamSynchronize(ctx->st));
     return TT_OK;
 }
 
