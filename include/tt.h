@@ -12,8 +12,9 @@
  *   tt_misfit_cr   common-receiver differential times (Eqs. 4, A4)
  *   tt_field_at_points, tt_misfit_table, tt_reloc_kernels, tt_reloc_update
  *                  earthquake location and origin-time kernels and update (Eq. 10, B1-B11)
- *   tt_tele2d, tt_tele_region_times
- *                  teleseismic events: 2-D times in a 1-D model and the region's face data
+ *   tt_tele2d, tt_tele_region_times, tt_forward_tele
+ *                  teleseismic events: 2-D times in a 1-D model, the region's face data and
+ *                  the region's solve with those faces held fixed
  *   tt_kernel_density, tt_kernel_normalize, tt_mgrid_project, tt_mgrid_expand,
  *   tt_model_update   regularisation and update of the inversion step (Eqs. 11-19)
  *
@@ -331,6 +332,16 @@ tt_status tt_tele2d(tt_ctx *ctx, int dtype, int n_r, int n_d, double r_min_km, d
 tt_status tt_tele_region_times(tt_ctx *ctx, int dtype, int n_r, int n_d, double r_min_km,
                                double r_max_km, double d_max_deg, const void *d_T2, int n_ev,
                                const tt_point *h_events, void *d_T);
+
+/* The region's solve for teleseismic events: Lax-Friedrichs sweeps (Sec. 3.1) of T itself
+ * (no factor) in the 8 orderings, hyperplane by hyperplane, with the six faces held fixed.
+ * d_T: device [N][n_ev] of the model's dtype; on entry its faces are the Dirichlet data and
+ * its interior the start (tt_tele_region_times gives both); on return the solution. Each
+ * event stops when an iteration's largest change is below opts->tol_fwd (at most
+ * opts->max_iter_fwd iterations; TT_ENOTCONVERGED otherwise). h_iters: host [n_ev] (may be
+ * NULL). Synchronises the stream every iteration. */
+tt_status tt_forward_tele(tt_ctx *ctx, const tt_model *model, int n_ev, void *d_T,
+                          const tt_opts *opts, int *h_iters);
 
 /* Largest receiver count tt_misfit_noalloc accepts: the size of its static scratch. */
 #define TT_NOALLOC_MAX_REC 1024

@@ -88,7 +88,8 @@ EXPORTED = ["tt_default_opts", "tt_ctx_create", "tt_ctx_destroy", "tt_last_error
             "tt_net_adam", "tt_net_set_weights", "tt_autotune", "tt_net_infer",
             "tt_kernel_density", "tt_kernel_normalize", "tt_mgrid_project", "tt_mgrid_expand",
             "tt_model_update", "tt_misfit_cr", "tt_field_at_points", "tt_misfit_table",
-            "tt_reloc_kernels", "tt_reloc_update", "tt_tele2d", "tt_tele_region_times"]
+            "tt_reloc_kernels", "tt_reloc_update", "tt_tele2d", "tt_tele_region_times",
+            "tt_forward_tele"]
 TT_NOALLOC_MAX_REC = 1024
 
 
@@ -148,6 +149,8 @@ def _load():
     L.tt_tele2d.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
                             C.c_double, C.c_void_p, C.c_int, C.POINTER(C.c_double), C.c_double,
                             C.c_int, C.c_void_p, C.POINTER(C.c_int)]
+    L.tt_forward_tele.argtypes = [C.c_void_p, C.POINTER(TTModel), C.c_int, C.c_void_p,
+                                  C.POINTER(TTOpts), C.POINTER(C.c_int)]
     L.tt_tele_region_times.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_double,
                                        C.c_double, C.c_double, C.c_void_p, C.c_int,
                                        C.POINTER(TTPoint), C.c_void_p]
@@ -158,7 +161,7 @@ def _load():
                  "tt_kernel_density", "tt_kernel_normalize", "tt_mgrid_project",
                  "tt_mgrid_expand", "tt_model_update", "tt_misfit_cr", "tt_field_at_points",
                  "tt_misfit_table", "tt_reloc_kernels", "tt_reloc_update", "tt_tele2d",
-                 "tt_tele_region_times"):
+                 "tt_tele_region_times", "tt_forward_tele"):
         getattr(L, name).restype = C.c_int
     return L
 
@@ -429,6 +432,21 @@ def tt_tele_region_times(ctx, T2, r_min, r_max, d_max_deg, events, T):
     pts, n = _points(events)
     _check(ctx, lib.tt_tele_region_times(ctx.handle, _dtype_code(T2), n_r, n_d, r_min, r_max,
                                          d_max_deg, _ptr(T2), n_ev, pts, _ptr(T)))
+
+
+def tt_forward_tele(ctx, model, T, opts=None, allow_unconverged=False):
+    """The region's solve for teleseismic events with the faces of T [..., n_ev] held fixed
+    (T holds the faces' data and the interior's start on entry, the solution on return).
+    Returns the iterations per event."""
+    M = _model(model)
+    _cuda_ok(T)
+    n_ev = T.shape[-1]
+    if opts is None:
+        opts = default_opts(M.dtype)
+    it = (C.c_int * n_ev)()
+    st = lib.tt_forward_tele(ctx.handle, C.byref(M), n_ev, _ptr(T), C.byref(opts), it)
+    _check(ctx, st, (TT_ENOTCONVERGED,) if allow_unconverged else ())
+    return np.frombuffer(it, dtype=np.int32).copy()
 
 
 def tt_kernel_density(ctx, P_hat, Kd):

@@ -1465,6 +1465,63 @@ tt_status tt_tele_region_times(tt_ctx *ctx, int dtype, int n_r, int n_d, double 
     return TT_OK;
 }
 
+tt_status tt_forward_tele(tt_ctx *ctx, const tt_model *model, int n_ev, void *d_T,
+                          const tt_opts *opts, int *h_iters) {
+    if (!ctx) return TT_EINVAL;
+    tt_status s;
+    if ((s = check_model(ctx, model)) != TT_OK) return s;
+    if ((s = check_opts(ctx, opts)) != TT_OK) return s;
+    if (!d_T) return fail(ctx, TT_EINVAL, "tt_forward_tele: NULL field");
+    if (n_ev < 1 || n_ev > TT_MAX_BATCH)
+        return fail(ctx, TT_EINVAL, "n_ev = %d outside 1..%d", n_ev, TT_MAX_BATCH);
+    const Schedule &S = ctx->interior;
+    std::vector<int> off(S.n_planes + 1);
+    CK(cudaMemcpy(off.data(), S.off, sizeof(int) * off.size(), cudaMemcpyDeviceToHost));
+    ENSURE(ctx->tele_aux, (sizeof(unsigned long long) + sizeof(int)) * (size_t)n_ev);
+    unsigned long long *d_err = (unsigned long long *)ctx->tele_aux.p;
+    int *d_done = (int *)(d_err + n_ev);
+    CK(cudaMemsetAsync(d_done, 0, sizeof(int) * n_ev, ctx->st));
+    std::vector<unsigned long long> err(n_ev);
+    std::vector<int> done(n_ev, 0), iters(n_ev, 0);
+    const bool f32 = model->dtype == TT_F32;
+    int left = n_ev;
+    for (int it = 0; it < opts->max_iter_fwd && left > 0; ++it) {
+        CK(cudaMemsetAsync(d_err, 0, sizeof(unsigned long long) * n_ev, ctx->st));
+        for (int o = 0; o < 8; ++o)
+            for (int L = 0; L < S.n_planes; ++L) {
+                const int cnt = off[L + 1] - off[L];
+                if (cnt == 0) continue;
+                CK(f32 ? run_tele3d_plane<float>(ctx->g, model->d_s, model->d_xi, model->d_eta, S.nodes,
+                                                 off[L], cnt, o, n_ev, d_done, d_T, d_err, ctx->st)
+                       : run_tele3d_plane<double>(ctx->g, model->d_s, model->d_xi, model->d_eta,
+                                                  S.nodes, off[L], cnt, o, n_ev, d_done, d_T,
+                                                  d_err, ctx->st));
+                ctx->launches += 1;
+            }
+        CK(cudaMemcpyAsync(err.data(), d_err, sizeof(unsigned long long) * n_ev,
+                           cudaMemcpyDeviceToHost, ctx->st));
+        CK(cudaStreamSynchronize(ctx->st));
+        for (int e = 0; e < n_ev; ++e) {
+            if (done[e]) continue;
+            iters[e] = it + 1;
+            double ch;
+            memcpy(&ch, &err[e], sizeof ch);
+            if (ch < opts->tol_fwd) {
+                done[e] = 1;
+                --left;
+            }
+        }
+        CK(cudaMemcpyAsync(d_done, done.data(), sizeof(int) * n_ev, cudaMemcpyHostToDevice, ctx->st));
+    }
+    CK(cudaStreamSynchronize(ctx->st));
+    if (h_iters)
+        for (int e = 0; e < n_ev; ++e) h_iters[e] = iters[e];
+    if (left)
+        return fail(ctx, TT_ENOTCONVERGED, "tt_forward_tele: %d of %d events did not converge in %d iterations",
+                    left, n_ev, opts->max_iter_fwd);
+    return TT_OK;
+}
+
 tt_status tt_kernel_normalize(tt_ctx *ctx, double *d_Ks, double *d_Kxi, double *d_Keta,
                               const double *d_Kd, double eps, double zeta) {
     if (!ctx) return TT_EINVAL;

@@ -1,7 +1,8 @@
 """Teleseismic events on the GPU (reading R17) against the FP64 oracle (oracle/tele.py),
-through the C ABI (needs a GB300): the 2-D traveltimes of several events in two 1-D models
+through the C ABI (needs a GB300): the 2-D traveltimes of several events in three 1-D models
 (FP64 to 1e-10 of the largest time with the same iteration counts, FP32 to the 1e-5 bar),
-and their interpolation onto a region's nodes."""
+their interpolation onto a region's nodes, and the region's solve with those faces held
+fixed (the whole chain against the oracle's chain)."""
 import numpy as np
 import pytest
 
@@ -79,4 +80,46 @@ def test_region_times_match_the_oracle(tt):
     # an event beyond the 2-D grid's reach is refused
     with pytest.raises(tt.TTError, match="farther"):
         tt.tt_tele_region_times(ctx, T2, r_min, RE, 2.0, events, T)
+    ctx.close()
+
+
+def test_region_solve_matches_the_oracle_chain(tt):
+    """The whole chain on the GPU (2-D solves, face data, the region's solve with the faces
+    held fixed) against the oracle's own chain, on a heterogeneous anisotropic region with
+    two events: FP64 to 1e-9 of the largest time with iteration counts within 1, FP32 to
+    the 1e-5 bar."""
+    import torch
+    import oracle.tele as TL
+    n_r, n_d, r_min, dmax = 61, 97, RE - 400.0, 15.0
+    s_r = _models(n_r, r_min)["layered"]
+    events = np.array([[100.0, -6.0, 3.0], [30.0, 9.0, -4.0]])
+    w = I.small_case(97, shape=(11, 12, 13), n_src=1, depth_max=40.0, extent_deg=1.0)
+    g = w.grid
+    gd = g.as_dict()
+    ref, ref_it = [], []
+    for e in range(2):
+        T2o, _, conv = TL.tele2d(r_min, RE, n_r, dmax, n_d, s_r, RE - events[e, 0], tol=1e-10)
+        assert conv
+        start = TL.region_times(gd, T2o, r_min, RE, dmax, events[e, 1], events[e, 2])
+        To, it, conv = TL.forward_tele(gd, w.s, w.xi, w.eta, start, tol=1e-11, max_iter=500)
+        assert conv
+        ref.append(To)
+        ref_it.append(it)
+    ctx = tt.tt_ctx_create(gd)
+    for dtype, code, bar in ((torch.float64, tt.TT_F64, 1e-9), (torch.float32, tt.TT_F32, 1e-5)):
+        T2 = torch.empty((2, n_r, n_d), dtype=dtype, device="cuda")
+        tt.tt_tele2d(ctx, torch.as_tensor(s_r, dtype=dtype, device="cuda"), r_min, RE, dmax,
+                     RE - events[:, 0], T2, tol=1e-11 if code == tt.TT_F64 else 1e-6)
+        T = torch.empty(g.shape + (2,), dtype=dtype, device="cuda")
+        tt.tt_tele_region_times(ctx, T2, r_min, RE, dmax, events, T)
+        model = tuple(torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+                      for a in (w.s, w.xi, w.eta))
+        o = tt.default_opts(code, tol_fwd=1e-11 if code == tt.TT_F64 else 1e-6,
+                            max_iter_fwd=500)
+        it = tt.tt_forward_tele(ctx, model, T, o)
+        Tg = T.double().cpu().numpy()
+        for e in range(2):
+            assert np.abs(Tg[..., e] - ref[e]).max() <= bar * ref[e].max(), (dtype, e)
+            if code == tt.TT_F64:
+                assert abs(int(it[e]) - ref_it[e]) <= 1
     ctx.close()
