@@ -668,6 +668,64 @@ def inversion_leg(args):
                     "N(0, 0.05 s)"}
 
 
+def tele_leg(args):
+    """Times teleseismic events on the benchmark's 121 x 161 x 161 region: args.tele events
+    8-20 deg away at 30-300 km depth in a 1-D model (Vp 5.8 -> 8.8 km/s over 400 km), the
+    region's model the benchmark's anisotropic one. One JSON line: the 2-D solves, the
+    region's face data and the region's solve (Lax-Friedrichs with fixed faces), each timed
+    with CUDA events after a warm-up run."""
+    import torch
+    import paper_2412_00031_gb300 as tt
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    w = I.anisotropic_batch(n_src=1)
+    g = w.grid
+    rng = np.random.default_rng(20241205)
+    n_ev = args.tele
+    dist = rng.uniform(8.0, 20.0, n_ev)
+    az = rng.uniform(0.0, 2 * np.pi, n_ev)
+    lat0, lon0 = 0.5 * (g.lat_min_deg + g.lat_max_deg), 0.5 * (g.lon_min_deg + g.lon_max_deg)
+    events = np.stack([rng.uniform(30.0, 300.0, n_ev), lat0 + dist * np.cos(az),
+                       lon0 + dist * np.sin(az)], 1)
+    RE, n_r, n_d, dmax = g.earth_radius_km, 201, 401, 25.0
+    r = np.linspace(RE - 400.0, RE, n_r)
+    s_r = torch.as_tensor(1.0 / (5.8 + 3.0 * (RE - r) / 400.0), device=dev)
+    ctx = tt.tt_ctx_create(g.as_dict())
+    f32 = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32), device=dev)
+    model = (f32(w.s), f32(w.xi), f32(w.eta))
+    T2 = torch.empty((n_ev, n_r, n_d), dtype=torch.float64, device=dev)
+    T = torch.empty(g.shape + (n_ev,), dtype=torch.float32, device=dev)
+    T2f = torch.empty((n_ev, n_r, n_d), dtype=torch.float32, device=dev)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        out = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), out
+
+    res = {}
+    for rep in range(2):                         # the first run is the warm-up
+        ms2, it2 = timed(lambda: tt.tt_tele2d(ctx, s_r, RE - 400.0, RE, dmax, RE - events[:, 0],
+                                              T2, tol=1e-10))
+        T2f.copy_(T2)
+        msf, _ = timed(lambda: tt.tt_tele_region_times(ctx, T2f, RE - 400.0, RE, dmax, events, T))
+        ms3, it3 = timed(lambda: tt.tt_forward_tele(ctx, model, T))
+        res = {"tele2d_ms": ms2, "region_times_ms": msf, "region_solve_ms": ms3,
+               "iters_2d_mean": float(np.mean(it2)), "iters_3d_mean": float(np.mean(it3)),
+               "iters_3d_max": int(np.max(it3))}
+    ctx.close()
+    total = res["tele2d_ms"] + res["region_times_ms"] + res["region_solve_ms"]
+    return {"metric": "teleseismic events per second on 1 GB300 at 121x161x161",
+            "value": n_ev / (total * 1e-3), "unit": "events/s", "events": n_ev, **res,
+            "config": {"workload": "%d teleseismic events, 8-20 deg, 30-300 km deep; 2-D grid "
+                                   "%dx%d over 400 km x %g deg (FP64); region 121x161x161 "
+                                   "anisotropic (FP32)" % (n_ev, n_r, n_d, dmax)},
+            "note": "region solve: one launch per hyperplane (correctness-first kernel)"}
+
+
 # ----------------------------------------------------------------------------- CPU oracle
 
 def oracle_sample(w, n_threads, n_src_sample, sweeps=1):
@@ -829,6 +887,8 @@ def main():
                          "201x201x101 workload instead of the benchmark step")
     ap.add_argument("--inv-sources", type=int, default=1024)
     ap.add_argument("--inv-batch", type=int, default=256)
+    ap.add_argument("--tele", type=int, default=0,
+                    help="time this many teleseismic events on the benchmark region instead")
     ap.add_argument("--inv-scheme", type=int, default=0,
                     help="forward local solver of the inversion loop (tt_opts.scheme)")
     args = ap.parse_args()
@@ -837,6 +897,9 @@ def main():
         return
     if args.inversion > 0:
         print(json.dumps(inversion_leg(args)))
+        return
+    if args.tele > 0:
+        print(json.dumps(tele_leg(args)))
         return
     rank, world = dist_init()
     if args.impl == "reference":
