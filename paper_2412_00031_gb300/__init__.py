@@ -203,6 +203,25 @@ def _points(pts):
     return arr, len(pts)
 
 
+def _nodes(ctx):
+    g = ctx.grid
+    return int(g.n_r) * int(g.n_t) * int(g.n_p)
+
+
+def _room(**named):
+    """Each value is (tensor or None, elements the call touches). Raises ValueError when a
+    device argument holds fewer elements than that, before the library is called (the C ABI
+    takes plain pointers and cannot check sizes itself)."""
+    for name, (t, need) in named.items():
+        if t is not None and t.numel() < need:
+            raise ValueError("%s holds %d elements; the call touches %d" % (name, t.numel(), need))
+
+
+def _model_room(ctx, model):
+    N = _nodes(ctx)
+    _room(s=(model[0], N), xi=(model[1], N), eta=(model[2], N))
+
+
 def _cuda_ok(*tensors):
     for t in tensors:
         if t is not None and (not t.is_cuda or not t.is_contiguous()):
@@ -264,9 +283,11 @@ def _model(model):
 def tt_forward(ctx, model, src, tau, T=None, opts=None, allow_unconverged=False):
     """Forward solve; tau (in/out) and T have shape (n_r, n_t, n_p, n_src). Returns the
     per-source iteration counts (numpy int32)."""
+    pts, n = _points(src)
+    _model_room(ctx, model)
+    _room(tau=(tau, _nodes(ctx) * n), T=(T, _nodes(ctx) * n))
     M = _model(model)
     _cuda_ok(tau, T)
-    pts, n = _points(src)
     if opts is None:
         opts = default_opts(M.dtype)
     iters = (C.c_int * n)()
@@ -310,6 +331,8 @@ class DeviceData:
 def tt_misfit(ctx, T, data, Tr=None, chi=None, R=None):
     """Receiver times, misfits and adjoint sources; Tr, chi, R are float64 CUDA tensors of
     shape (n_src, n_rec), (n_src, 2), (n_src, n_rec)."""
+    nb = data.n_src * data.n_rec
+    _room(T=(T, _nodes(ctx) * data.n_src), Tr=(Tr, nb), chi=(chi, 2 * data.n_src), R=(R, nb))
     _cuda_ok(T, Tr, chi, R)
     D = data.c_struct()
     _check(ctx, lib.tt_misfit(ctx.handle, _ptr(T), _dtype_code(T), C.byref(D), _ptr(Tr),
@@ -317,10 +340,12 @@ def tt_misfit(ctx, T, data, Tr=None, chi=None, R=None):
 
 
 def tt_adjoint(ctx, model, src, T, rec, R, P, opts=None, allow_unconverged=False):
-    M = _model(model)
-    _cuda_ok(T, R, P)
     pts, n = _points(src)
     rpts, nr = _points(rec)
+    _model_room(ctx, model)
+    _room(T=(T, _nodes(ctx) * n), R=(R, n * nr), P=(P, _nodes(ctx) * n))
+    M = _model(model)
+    _cuda_ok(T, R, P)
     if opts is None:
         opts = default_opts(M.dtype)
     iters = (C.c_int * n)()
@@ -331,9 +356,12 @@ def tt_adjoint(ctx, model, src, T, rec, R, P, opts=None, allow_unconverged=False
 
 
 def tt_kernel(ctx, model, T, P, Ks, Kxi, Keta):
+    n_src = T.shape[-1]
+    N = _nodes(ctx)
+    _model_room(ctx, model)
+    _room(T=(T, N * n_src), P=(P, N * n_src), Ks=(Ks, N), Kxi=(Kxi, N), Keta=(Keta, N))
     M = _model(model)
     _cuda_ok(T, P, Ks, Kxi, Keta)
-    n_src = T.shape[-1]
     _check(ctx, lib.tt_kernel(ctx.handle, C.byref(M), n_src, _ptr(T), _ptr(P), _ptr(Ks),
                               _ptr(Kxi), _ptr(Keta)))
 
@@ -371,6 +399,7 @@ class CrData:
 
 def tt_misfit_cr(ctx, cr, Tr, chi_cr, R):
     """Eqs. 4 and A4: R += gamma dchi_cr/dT (in place), chi_cr [n_src] the sources' shares."""
+    _room(Tr=(Tr, cr.n_src * cr.n_rec), chi_cr=(chi_cr, cr.n_src), R=(R, cr.n_src * cr.n_rec))
     _cuda_ok(Tr, chi_cr, R)
     D = cr.c_struct()
     _check(ctx, lib.tt_misfit_cr(ctx.handle, C.byref(D), _ptr(Tr), _ptr(chi_cr), _ptr(R)))
@@ -380,6 +409,9 @@ def tt_field_at_points(ctx, G, pts, val, grad):
     """Values val [n_pts, M] and physical gradients grad [n_pts, M, 3] (float64) at the points
     pts [n_pts, 3] (float64: depth km, lat deg, lon deg) of the M batched fields G [..., M]
     (for relocation: tt_forward's T with the receivers as the sources)."""
+    M, n_pts = G.shape[-1], pts.shape[0]
+    _room(G=(G, _nodes(ctx) * M), pts=(pts, 3 * n_pts), val=(val, n_pts * M),
+          grad=(grad, 3 * n_pts * M))
     _cuda_ok(G, pts, val, grad)
     _check(ctx, lib.tt_field_at_points(ctx.handle, _ptr(G), _dtype_code(G), G.shape[-1],
                                        pts.shape[0], _ptr(pts), _ptr(val), _ptr(grad)))
@@ -387,6 +419,9 @@ def tt_field_at_points(ctx, G, pts, val, grad):
 
 def tt_misfit_table(ctx, val, otime, data, Tr=None, chi=None, R=None):
     """tt_misfit on given arrivals Tr = val + otime[:, None] (otime may be None)."""
+    nb = data.n_src * data.n_rec
+    _room(val=(val, nb), otime=(otime, data.n_src), Tr=(Tr, nb), chi=(chi, 2 * data.n_src),
+          R=(R, nb))
     _cuda_ok(val, otime, Tr, chi, R)
     D = data.c_struct()
     _check(ctx, lib.tt_misfit_table(ctx.handle, _ptr(val), _ptr(otime), C.byref(D), _ptr(Tr),
@@ -395,6 +430,8 @@ def tt_misfit_table(ctx, val, otime, data, Tr=None, chi=None, R=None):
 
 def tt_reloc_kernels(ctx, R, grad, Kx, Ktau):
     """Kx [n_src, 3] = sum_m R grad, Ktau [n_src] = sum_m R (Eqs. B5-B11)."""
+    n, m = R.shape[0], R.shape[1]
+    _room(grad=(grad, 3 * n * m), Kx=(Kx, 3 * n), Ktau=(Ktau, n))
     _cuda_ok(R, grad, Kx, Ktau)
     _check(ctx, lib.tt_reloc_kernels(ctx.handle, R.shape[0], R.shape[1], _ptr(R), _ptr(grad),
                                      _ptr(Kx), _ptr(Ktau)))
@@ -403,6 +440,8 @@ def tt_reloc_kernels(ctx, R, grad, Kx, Ktau):
 def tt_reloc_update(ctx, pts, otime, Kx, Ktau, step_km, step_s):
     """One normalised gradient step of the event positions pts [n, 3] and origin times
     otime [n] (may be None), in place."""
+    n = pts.shape[0]
+    _room(pts=(pts, 3 * n), otime=(otime, n), Kx=(Kx, 3 * n), Ktau=(Ktau, n))
     _cuda_ok(pts, otime, Kx, Ktau)
     _check(ctx, lib.tt_reloc_update(ctx.handle, pts.shape[0], _ptr(pts), _ptr(otime), _ptr(Kx),
                                     _ptr(Ktau), step_km, step_s))
@@ -414,8 +453,11 @@ def tt_tele2d(ctx, s_r, r_min, r_max, d_max_deg, r_src, T, tol=1e-8, max_iter=50
     float64) slowness at the radii r_min..r_max (km); r_src [n_ev] the events' radii (host);
     T [n_ev, n_r, n_d] output (CUDA, same dtype) on Delta = 0..d_max_deg. Returns the
     iterations per event."""
-    _cuda_ok(s_r, T)
     n_ev, n_r, n_d = T.shape
+    _room(s_r=(s_r, n_r))
+    if len(np.atleast_1d(r_src)) < n_ev:
+        raise ValueError("r_src holds %d radii for %d events" % (len(np.atleast_1d(r_src)), n_ev))
+    _cuda_ok(s_r, T)
     rs = np.ascontiguousarray(r_src, dtype=np.float64)
     it = (C.c_int * n_ev)()
     st = lib.tt_tele2d(ctx.handle, _dtype_code(T), n_r, n_d, r_min, r_max, d_max_deg, _ptr(s_r),
@@ -427,9 +469,12 @@ def tt_tele2d(ctx, s_r, r_min, r_max, d_max_deg, r_src, T, tol=1e-8, max_iter=50
 def tt_tele_region_times(ctx, T2, r_min, r_max, d_max_deg, events, T):
     """The 2-D times T2 [n_ev, n_r, n_d] interpolated at every node of the context's grid
     for events at (depth, lat, lon) points (only lat and lon are read): T [..., n_ev]."""
-    _cuda_ok(T2, T)
     n_ev, n_r, n_d = T2.shape
     pts, n = _points(events)
+    if n < n_ev:
+        raise ValueError("%d event positions for %d events" % (n, n_ev))
+    _room(T=(T, _nodes(ctx) * n_ev))
+    _cuda_ok(T2, T)
     _check(ctx, lib.tt_tele_region_times(ctx.handle, _dtype_code(T2), n_r, n_d, r_min, r_max,
                                          d_max_deg, _ptr(T2), n_ev, pts, _ptr(T)))
 
@@ -438,9 +483,11 @@ def tt_forward_tele(ctx, model, T, opts=None, allow_unconverged=False):
     """The region's solve for teleseismic events with the faces of T [..., n_ev] held fixed
     (T holds the faces' data and the interior's start on entry, the solution on return).
     Returns the iterations per event."""
+    n_ev = T.shape[-1]
+    _model_room(ctx, model)
+    _room(T=(T, _nodes(ctx) * n_ev))
     M = _model(model)
     _cuda_ok(T)
-    n_ev = T.shape[-1]
     if opts is None:
         opts = default_opts(M.dtype)
     it = (C.c_int * n_ev)()
@@ -451,6 +498,7 @@ def tt_forward_tele(ctx, model, T, opts=None, allow_unconverged=False):
 
 def tt_kernel_density(ctx, P_hat, Kd):
     """Kd += sum over sources of P_hat (Eq. 19); P_hat [..., n_src] from tt_adjoint with R = 1."""
+    _room(P_hat=(P_hat, _nodes(ctx) * P_hat.shape[-1]), Kd=(Kd, _nodes(ctx)))
     _cuda_ok(P_hat, Kd)
     _check(ctx, lib.tt_kernel_density(ctx.handle, _ptr(P_hat), P_hat.shape[-1],
                                       _dtype_code(P_hat), _ptr(Kd)))
@@ -458,6 +506,8 @@ def tt_kernel_density(ctx, P_hat, Kd):
 
 def tt_kernel_normalize(ctx, Ks, Kxi, Keta, Kd, eps, zeta):
     """Eq. 18 in place: K <- K / (Kd + eps)^zeta."""
+    N = _nodes(ctx)
+    _room(Ks=(Ks, N), Kxi=(Kxi, N), Keta=(Keta, N), Kd=(Kd, N))
     _cuda_ok(Ks, Kxi, Keta, Kd)
     _check(ctx, lib.tt_kernel_normalize(ctx.handle, _ptr(Ks), _ptr(Kxi), _ptr(Keta), _ptr(Kd),
                                         float(eps), float(zeta)))
@@ -470,18 +520,23 @@ def mgrid(n_r, n_t, n_p, n_grids):
 
 def tt_mgrid_project(ctx, mg, K, G):
     """Eq. 17: G [n_grids, n_r, n_t, n_p] (float64) from the kernel K (float64, grid shape)."""
+    _room(K=(K, _nodes(ctx)), G=(G, mg.n_grids * mg.n_r * mg.n_t * mg.n_p))
     _cuda_ok(K, G)
     _check(ctx, lib.tt_mgrid_project(ctx.handle, C.byref(mg), _ptr(K), _ptr(G)))
 
 
 def tt_mgrid_expand(ctx, mg, G, D):
     """Eq. 15: D (float64, grid shape) from the coefficients G."""
+    _room(G=(G, mg.n_grids * mg.n_r * mg.n_t * mg.n_p), D=(D, _nodes(ctx)))
     _cuda_ok(G, D)
     _check(ctx, lib.tt_mgrid_expand(ctx.handle, C.byref(mg), _ptr(G), _ptr(D)))
 
 
 def tt_model_update(ctx, model, Ds, Dxi, Deta, step):
     """One gradient-descent step on the model's arrays, in place (see tt.h)."""
+    N = _nodes(ctx)
+    _model_room(ctx, model)
+    _room(Ds=(Ds, N), Dxi=(Dxi, N), Deta=(Deta, N))
     M = _model(model)
     _cuda_ok(Ds, Dxi, Deta)
     _check(ctx, lib.tt_model_update(ctx.handle, C.byref(M), _ptr(Ds), _ptr(Dxi), _ptr(Deta),
@@ -531,9 +586,13 @@ class Plan:
 
 
 def tt_plan_create(ctx, model, src, data, tau, T, P, chi, R, Ks, Kxi, Keta, opts=None):
+    pts, n = _points(src)
+    N = _nodes(ctx)
+    _model_room(ctx, model)
+    _room(tau=(tau, N * n), T=(T, N * n), P=(P, N * n), chi=(chi, 2 * n),
+          R=(R, n * data.n_rec), Ks=(Ks, N), Kxi=(Kxi, N), Keta=(Keta, N))
     M = _model(model)
     _cuda_ok(tau, T, P, chi, R, Ks, Kxi, Keta)
-    pts, n = _points(src)
     if opts is None:
         opts = default_opts(M.dtype)
     D = data.c_struct()
