@@ -390,7 +390,9 @@ tt_status tt_autotune(tt_ctx *ctx, const tt_model *model, const tt_point *h_src,
  * offset D to the source in the source's (up, north, east) frame in units of 100 km (the
  * offset that defines T0). Network: four 3x3x3 convolutions 6 -> 32 -> 32 -> 32 -> 1, zero
  * padding outside the grid, ReLU after the first three; output y; warm start
- * tau = 1 + clamp(y, -0.5, 1) (the fixed set keeps tau = 1).
+ * tau = 1 + clamp(y, -0.5, 1), and tau = 1 where y is not a number (the fixed set keeps
+ * tau = 1). Any start in [0.5, 2] converges to the same fixed point, so a poor or broken
+ * network costs sweeps but not accuracy.
  * Parameters: one FP32 vector of tt_net_param_count() values: for each layer l, weights
  * W[27][C_in][C_out] (tap (dz * 3 + dy) * 3 + dx reads the node at offset (dz-1, dy-1, dx-1)
  * along (r, theta, phi)), then biases b[C_out].

@@ -241,3 +241,27 @@ def test_tensor_core_inference_wide_and_small_grids(tt):
             ref = N.forward(tb, xs[b].astype(np.float64))
             got = y[b].cpu().numpy()
             assert np.abs(got - ref).max() <= 2e-2 * np.abs(ref).max(), (shape, b)
+
+
+def test_broken_network_costs_sweeps_not_accuracy(tt):
+    """A network that predicts NaN everywhere (NaN weights) starts every node at tau = 1,
+    so the warm-started solve is bit for bit the cold one. A network with huge weights
+    (outputs overflow; the clamp keeps tau in [0.5, 2]) still converges to the cold solve's
+    fixed point within the tolerance."""
+    import torch
+    from gpu_helpers import gpu_solve
+    w = I.small_case(66, shape=(13, 14, 15), n_src=5, n_rec=4)
+    ctx = tt.tt_ctx_create(w.grid.as_dict())
+    n = tt.tt_net_param_count()
+    cold = gpu_solve(w, "f32", steps=("fwd",), ctx=ctx)
+    warm_opts = tt.default_opts(tt.TT_F32, init=2)
+    tt.tt_net_set_weights(ctx, torch.full((n,), float("nan"), device="cuda"))
+    warm = gpu_solve(w, "f32", opts=warm_opts, steps=("fwd",), ctx=ctx)
+    assert np.array_equal(warm["iters_fwd"], cold["iters_fwd"])
+    assert np.array_equal(warm["tau"], cold["tau"])
+    g = torch.Generator().manual_seed(66)
+    tt.tt_net_set_weights(ctx, (1e3 * torch.randn(n, generator=g)).to("cuda"))
+    warm = gpu_solve(w, "f32", opts=warm_opts, steps=("fwd",), ctx=ctx)
+    ctx.close()
+    assert np.all(np.isfinite(warm["tau"]))
+    assert rel_linf(warm["tau"], cold["tau"]) <= 1e-5
