@@ -315,14 +315,16 @@ def test_spherical_uniform_slowness_kernel(oracle):
     assert pred / np.sum(r["R"] * chord / 6.0) == pytest.approx(1.0, abs=0.06)
 
 
-@pytest.mark.parametrize("eta0", [0.1, -0.08])
-def test_adjoint_follows_straight_anisotropic_ray(oracle, eta0):
+@pytest.mark.parametrize("xi0,eta0", [(0.0, 0.1), (0.0, -0.08), (0.12, 0.0), (-0.1, 0.06)])
+def test_adjoint_follows_straight_anisotropic_ray(oracle, xi0, eta0):
     """Eq. 5 transports the adjoint source along -M grad T. In a homogeneous anisotropic
     flat medium M grad T is parallel to x - x_s, so the adjoint field of one receiver is
-    centred on the straight segment from the receiver to the source at every depth."""
+    centred on the straight segment from the receiver to the source at every depth. With
+    xi != 0 this pins the (1 -+ 2 xi) factors of the adjoint's face velocities, with
+    eta != 0 its cross terms."""
     g = I.GridSpec(31, 41, 41, 0.0, 15.0, 0.0, 0.2, 0.0, 0.2, flat=1)
     gd = g.as_dict()
-    s, xi, eta = np.full(g.shape, 1 / 6.0), np.zeros(g.shape), np.full(g.shape, eta0)
+    s, xi, eta = (np.full(g.shape, v) for v in (1 / 6.0, xi0, eta0))
     src, rec = np.array([14.0, 0.05, 0.06]), np.array([[0.0, 0.15, 0.14]])
     _, T, _, _, _ = oracle.forward(gd, s, xi, eta, src, 1e-12, 1000)
     P, _, conv, _ = oracle.adjoint(gd, T, xi, eta, src, rec, np.array([1.0]), 1e-12, 1000)
