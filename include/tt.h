@@ -359,8 +359,13 @@ tt_status tt_forward_tele(tt_ctx *ctx, const tt_model *model, int n_ev, void *d_
  * the last call left. Every call on a device shares that array, so calls whose GPU work
  * overlaps (other host threads, other streams) race; issue them one after another.
  * The first call on each device looks up the array's device address (cudaGetSymbolAddress,
- * with that device current); make that first call before any stream capture.
- * grid: the study region (validated as in tt_ctx_create). cuda_stream: the cudaStream_t to
+ * with that device current); make that first call before any stream capture. CUDA loads a
+ * library's device code lazily by default, so that first call may also be what loads this
+ * module onto the device and places the static array in device memory: make it before the
+ * device's memory is handed to the caller's pool, or that placement can fail for lack of
+ * memory (TT_ECUDA).
+ * grid: the study region, validated by the same rules as tt_ctx_create (spherical grids
+ * must stay inside latitudes (-89, 89)). cuda_stream: the cudaStream_t to
  * run on (NULL for the default stream). h_err/err_len: optional host buffer that receives a
  * one-line message (may be NULL). The call waits for its stream before returning. */
 tt_status tt_misfit_noalloc(const tt_grid *grid, const void *d_T, int dtype,

@@ -209,17 +209,35 @@ def _nodes(ctx):
 
 
 def _room(**named):
-    """Each value is (tensor or None, elements the call touches). Raises ValueError when a
-    device argument holds fewer elements than that, before the library is called (the C ABI
-    takes plain pointers and cannot check sizes itself)."""
-    for name, (t, need) in named.items():
-        if t is not None and t.numel() < need:
+    """Each value is (tensor or None, elements the call touches[, element type]). Raises
+    ValueError when a device argument holds fewer elements than that, and TypeError when its
+    element type is not the one the library reads or writes through that pointer, before the
+    library is called (the C ABI takes plain pointers and cannot check sizes or types). The
+    element type is a torch dtype or None (any); _F64 marks the double* arguments."""
+    for name, spec in named.items():
+        t, need = spec[0], spec[1]
+        want = spec[2] if len(spec) > 2 else None
+        if t is None:
+            continue
+        if want is not None and t.dtype != want:
+            raise TypeError("%s is %s; the call reads or writes it as %s" % (name, t.dtype, want))
+        if t.numel() < need:
             raise ValueError("%s holds %d elements; the call touches %d" % (name, t.numel(), need))
 
 
+def _f64():
+    import torch
+    return torch.float64
+
+
 def _model_room(ctx, model):
+    """The three model arrays: N elements each, all of the slowness's float type (the type
+    every batched field of the call must have too). Returns that type."""
     N = _nodes(ctx)
-    _room(s=(model[0], N), xi=(model[1], N), eta=(model[2], N))
+    ft = model[0].dtype
+    _dtype_code(model[0])
+    _room(s=(model[0], N), xi=(model[1], N, ft), eta=(model[2], N, ft))
+    return ft
 
 
 def _cuda_ok(*tensors):
@@ -284,8 +302,8 @@ def tt_forward(ctx, model, src, tau, T=None, opts=None, allow_unconverged=False)
     """Forward solve; tau (in/out) and T have shape (n_r, n_t, n_p, n_src). Returns the
     per-source iteration counts (numpy int32)."""
     pts, n = _points(src)
-    _model_room(ctx, model)
-    _room(tau=(tau, _nodes(ctx) * n), T=(T, _nodes(ctx) * n))
+    ft = _model_room(ctx, model)
+    _room(tau=(tau, _nodes(ctx) * n, ft), T=(T, _nodes(ctx) * n, ft))
     M = _model(model)
     _cuda_ok(tau, T)
     if opts is None:
@@ -332,7 +350,10 @@ def tt_misfit(ctx, T, data, Tr=None, chi=None, R=None):
     """Receiver times, misfits and adjoint sources; Tr, chi, R are float64 CUDA tensors of
     shape (n_src, n_rec), (n_src, 2), (n_src, n_rec)."""
     nb = data.n_src * data.n_rec
-    _room(T=(T, _nodes(ctx) * data.n_src), Tr=(Tr, nb), chi=(chi, 2 * data.n_src), R=(R, nb))
+    f64 = _f64()
+    _dtype_code(T)
+    _room(T=(T, _nodes(ctx) * data.n_src), Tr=(Tr, nb, f64), chi=(chi, 2 * data.n_src, f64),
+          R=(R, nb, f64))
     _cuda_ok(T, Tr, chi, R)
     D = data.c_struct()
     _check(ctx, lib.tt_misfit(ctx.handle, _ptr(T), _dtype_code(T), C.byref(D), _ptr(Tr),
@@ -342,8 +363,8 @@ def tt_misfit(ctx, T, data, Tr=None, chi=None, R=None):
 def tt_adjoint(ctx, model, src, T, rec, R, P, opts=None, allow_unconverged=False):
     pts, n = _points(src)
     rpts, nr = _points(rec)
-    _model_room(ctx, model)
-    _room(T=(T, _nodes(ctx) * n), R=(R, n * nr), P=(P, _nodes(ctx) * n))
+    ft = _model_room(ctx, model)
+    _room(T=(T, _nodes(ctx) * n, ft), R=(R, n * nr, _f64()), P=(P, _nodes(ctx) * n, ft))
     M = _model(model)
     _cuda_ok(T, R, P)
     if opts is None:
@@ -358,8 +379,9 @@ def tt_adjoint(ctx, model, src, T, rec, R, P, opts=None, allow_unconverged=False
 def tt_kernel(ctx, model, T, P, Ks, Kxi, Keta):
     n_src = T.shape[-1]
     N = _nodes(ctx)
-    _model_room(ctx, model)
-    _room(T=(T, N * n_src), P=(P, N * n_src), Ks=(Ks, N), Kxi=(Kxi, N), Keta=(Keta, N))
+    ft, f64 = _model_room(ctx, model), _f64()
+    _room(T=(T, N * n_src, ft), P=(P, N * n_src, ft), Ks=(Ks, N, f64), Kxi=(Kxi, N, f64),
+          Keta=(Keta, N, f64))
     M = _model(model)
     _cuda_ok(T, P, Ks, Kxi, Keta)
     _check(ctx, lib.tt_kernel(ctx.handle, C.byref(M), n_src, _ptr(T), _ptr(P), _ptr(Ks),
@@ -399,7 +421,9 @@ class CrData:
 
 def tt_misfit_cr(ctx, cr, Tr, chi_cr, R):
     """Eqs. 4 and A4: R += gamma dchi_cr/dT (in place), chi_cr [n_src] the sources' shares."""
-    _room(Tr=(Tr, cr.n_src * cr.n_rec), chi_cr=(chi_cr, cr.n_src), R=(R, cr.n_src * cr.n_rec))
+    f64 = _f64()
+    _room(Tr=(Tr, cr.n_src * cr.n_rec, f64), chi_cr=(chi_cr, cr.n_src, f64),
+          R=(R, cr.n_src * cr.n_rec, f64))
     _cuda_ok(Tr, chi_cr, R)
     D = cr.c_struct()
     _check(ctx, lib.tt_misfit_cr(ctx.handle, C.byref(D), _ptr(Tr), _ptr(chi_cr), _ptr(R)))
@@ -410,8 +434,10 @@ def tt_field_at_points(ctx, G, pts, val, grad):
     pts [n_pts, 3] (float64: depth km, lat deg, lon deg) of the M batched fields G [..., M]
     (for relocation: tt_forward's T with the receivers as the sources)."""
     M, n_pts = G.shape[-1], pts.shape[0]
-    _room(G=(G, _nodes(ctx) * M), pts=(pts, 3 * n_pts), val=(val, n_pts * M),
-          grad=(grad, 3 * n_pts * M))
+    f64 = _f64()
+    _dtype_code(G)
+    _room(G=(G, _nodes(ctx) * M), pts=(pts, 3 * n_pts, f64), val=(val, n_pts * M, f64),
+          grad=(grad, 3 * n_pts * M, f64))
     _cuda_ok(G, pts, val, grad)
     _check(ctx, lib.tt_field_at_points(ctx.handle, _ptr(G), _dtype_code(G), G.shape[-1],
                                        pts.shape[0], _ptr(pts), _ptr(val), _ptr(grad)))
@@ -420,8 +446,9 @@ def tt_field_at_points(ctx, G, pts, val, grad):
 def tt_misfit_table(ctx, val, otime, data, Tr=None, chi=None, R=None):
     """tt_misfit on given arrivals Tr = val + otime[:, None] (otime may be None)."""
     nb = data.n_src * data.n_rec
-    _room(val=(val, nb), otime=(otime, data.n_src), Tr=(Tr, nb), chi=(chi, 2 * data.n_src),
-          R=(R, nb))
+    f64 = _f64()
+    _room(val=(val, nb, f64), otime=(otime, data.n_src, f64), Tr=(Tr, nb, f64),
+          chi=(chi, 2 * data.n_src, f64), R=(R, nb, f64))
     _cuda_ok(val, otime, Tr, chi, R)
     D = data.c_struct()
     _check(ctx, lib.tt_misfit_table(ctx.handle, _ptr(val), _ptr(otime), C.byref(D), _ptr(Tr),
@@ -431,7 +458,9 @@ def tt_misfit_table(ctx, val, otime, data, Tr=None, chi=None, R=None):
 def tt_reloc_kernels(ctx, R, grad, Kx, Ktau):
     """Kx [n_src, 3] = sum_m R grad, Ktau [n_src] = sum_m R (Eqs. B5-B11)."""
     n, m = R.shape[0], R.shape[1]
-    _room(grad=(grad, 3 * n * m), Kx=(Kx, 3 * n), Ktau=(Ktau, n))
+    f64 = _f64()
+    _room(R=(R, n * m, f64), grad=(grad, 3 * n * m, f64), Kx=(Kx, 3 * n, f64),
+          Ktau=(Ktau, n, f64))
     _cuda_ok(R, grad, Kx, Ktau)
     _check(ctx, lib.tt_reloc_kernels(ctx.handle, R.shape[0], R.shape[1], _ptr(R), _ptr(grad),
                                      _ptr(Kx), _ptr(Ktau)))
@@ -441,7 +470,9 @@ def tt_reloc_update(ctx, pts, otime, Kx, Ktau, step_km, step_s):
     """One normalised gradient step of the event positions pts [n, 3] and origin times
     otime [n] (may be None), in place."""
     n = pts.shape[0]
-    _room(pts=(pts, 3 * n), otime=(otime, n), Kx=(Kx, 3 * n), Ktau=(Ktau, n))
+    f64 = _f64()
+    _room(pts=(pts, 3 * n, f64), otime=(otime, n, f64), Kx=(Kx, 3 * n, f64),
+          Ktau=(Ktau, n, f64))
     _cuda_ok(pts, otime, Kx, Ktau)
     _check(ctx, lib.tt_reloc_update(ctx.handle, pts.shape[0], _ptr(pts), _ptr(otime), _ptr(Kx),
                                     _ptr(Ktau), step_km, step_s))
@@ -454,7 +485,8 @@ def tt_tele2d(ctx, s_r, r_min, r_max, d_max_deg, r_src, T, tol=1e-8, max_iter=50
     T [n_ev, n_r, n_d] output (CUDA, same dtype) on Delta = 0..d_max_deg. Returns the
     iterations per event."""
     n_ev, n_r, n_d = T.shape
-    _room(s_r=(s_r, n_r))
+    _dtype_code(T)
+    _room(s_r=(s_r, n_r, T.dtype))
     if len(np.atleast_1d(r_src)) < n_ev:
         raise ValueError("r_src holds %d radii for %d events" % (len(np.atleast_1d(r_src)), n_ev))
     _cuda_ok(s_r, T)
@@ -473,7 +505,8 @@ def tt_tele_region_times(ctx, T2, r_min, r_max, d_max_deg, events, T):
     pts, n = _points(events)
     if n < n_ev:
         raise ValueError("%d event positions for %d events" % (n, n_ev))
-    _room(T=(T, _nodes(ctx) * n_ev))
+    _dtype_code(T2)
+    _room(T=(T, _nodes(ctx) * n_ev, T2.dtype))
     _cuda_ok(T2, T)
     _check(ctx, lib.tt_tele_region_times(ctx.handle, _dtype_code(T2), n_r, n_d, r_min, r_max,
                                          d_max_deg, _ptr(T2), n_ev, pts, _ptr(T)))
@@ -484,8 +517,8 @@ def tt_forward_tele(ctx, model, T, opts=None, allow_unconverged=False):
     (T holds the faces' data and the interior's start on entry, the solution on return).
     Returns the iterations per event."""
     n_ev = T.shape[-1]
-    _model_room(ctx, model)
-    _room(T=(T, _nodes(ctx) * n_ev))
+    ft = _model_room(ctx, model)
+    _room(T=(T, _nodes(ctx) * n_ev, ft))
     M = _model(model)
     _cuda_ok(T)
     if opts is None:
@@ -498,7 +531,8 @@ def tt_forward_tele(ctx, model, T, opts=None, allow_unconverged=False):
 
 def tt_kernel_density(ctx, P_hat, Kd):
     """Kd += sum over sources of P_hat (Eq. 19); P_hat [..., n_src] from tt_adjoint with R = 1."""
-    _room(P_hat=(P_hat, _nodes(ctx) * P_hat.shape[-1]), Kd=(Kd, _nodes(ctx)))
+    _dtype_code(P_hat)
+    _room(P_hat=(P_hat, _nodes(ctx) * P_hat.shape[-1]), Kd=(Kd, _nodes(ctx), _f64()))
     _cuda_ok(P_hat, Kd)
     _check(ctx, lib.tt_kernel_density(ctx.handle, _ptr(P_hat), P_hat.shape[-1],
                                       _dtype_code(P_hat), _ptr(Kd)))
@@ -507,7 +541,8 @@ def tt_kernel_density(ctx, P_hat, Kd):
 def tt_kernel_normalize(ctx, Ks, Kxi, Keta, Kd, eps, zeta):
     """Eq. 18 in place: K <- K / (Kd + eps)^zeta."""
     N = _nodes(ctx)
-    _room(Ks=(Ks, N), Kxi=(Kxi, N), Keta=(Keta, N), Kd=(Kd, N))
+    f64 = _f64()
+    _room(Ks=(Ks, N, f64), Kxi=(Kxi, N, f64), Keta=(Keta, N, f64), Kd=(Kd, N, f64))
     _cuda_ok(Ks, Kxi, Keta, Kd)
     _check(ctx, lib.tt_kernel_normalize(ctx.handle, _ptr(Ks), _ptr(Kxi), _ptr(Keta), _ptr(Kd),
                                         float(eps), float(zeta)))
@@ -520,14 +555,14 @@ def mgrid(n_r, n_t, n_p, n_grids):
 
 def tt_mgrid_project(ctx, mg, K, G):
     """Eq. 17: G [n_grids, n_r, n_t, n_p] (float64) from the kernel K (float64, grid shape)."""
-    _room(K=(K, _nodes(ctx)), G=(G, mg.n_grids * mg.n_r * mg.n_t * mg.n_p))
+    _room(K=(K, _nodes(ctx), _f64()), G=(G, mg.n_grids * mg.n_r * mg.n_t * mg.n_p, _f64()))
     _cuda_ok(K, G)
     _check(ctx, lib.tt_mgrid_project(ctx.handle, C.byref(mg), _ptr(K), _ptr(G)))
 
 
 def tt_mgrid_expand(ctx, mg, G, D):
     """Eq. 15: D (float64, grid shape) from the coefficients G."""
-    _room(G=(G, mg.n_grids * mg.n_r * mg.n_t * mg.n_p), D=(D, _nodes(ctx)))
+    _room(G=(G, mg.n_grids * mg.n_r * mg.n_t * mg.n_p, _f64()), D=(D, _nodes(ctx), _f64()))
     _cuda_ok(G, D)
     _check(ctx, lib.tt_mgrid_expand(ctx.handle, C.byref(mg), _ptr(G), _ptr(D)))
 
@@ -536,7 +571,8 @@ def tt_model_update(ctx, model, Ds, Dxi, Deta, step):
     """One gradient-descent step on the model's arrays, in place (see tt.h)."""
     N = _nodes(ctx)
     _model_room(ctx, model)
-    _room(Ds=(Ds, N), Dxi=(Dxi, N), Deta=(Deta, N))
+    f64 = _f64()
+    _room(Ds=(Ds, N, f64), Dxi=(Dxi, N, f64), Deta=(Deta, N, f64))
     M = _model(model)
     _cuda_ok(Ds, Dxi, Deta)
     _check(ctx, lib.tt_model_update(ctx.handle, C.byref(M), _ptr(Ds), _ptr(Dxi), _ptr(Deta),
@@ -554,10 +590,15 @@ def tt_misfit_noalloc(grid, T, data, Tr=None, chi=None, R=None, stream=None):
     """tt_misfit without a context and without device allocation (static scratch; at most
     TT_NOALLOC_MAX_REC receivers). Same outputs as tt_misfit."""
     import torch
+    G = make_grid(grid)
+    nb = data.n_src * data.n_rec
+    f64 = _f64()
+    _dtype_code(T)
+    _room(T=(T, int(G.n_r) * int(G.n_t) * int(G.n_p) * data.n_src), Tr=(Tr, nb, f64),
+          chi=(chi, 2 * data.n_src, f64), R=(R, nb, f64))
     _cuda_ok(T, Tr, chi, R)
     if stream is None:
         stream = torch.cuda.current_stream()
-    G = make_grid(grid)
     D = data.c_struct()
     err = C.create_string_buffer(256)
     st = lib.tt_misfit_noalloc(C.byref(G), _ptr(T), _dtype_code(T), C.byref(D), _ptr(Tr),
@@ -588,9 +629,9 @@ class Plan:
 def tt_plan_create(ctx, model, src, data, tau, T, P, chi, R, Ks, Kxi, Keta, opts=None):
     pts, n = _points(src)
     N = _nodes(ctx)
-    _model_room(ctx, model)
-    _room(tau=(tau, N * n), T=(T, N * n), P=(P, N * n), chi=(chi, 2 * n),
-          R=(R, n * data.n_rec), Ks=(Ks, N), Kxi=(Kxi, N), Keta=(Keta, N))
+    ft, f64 = _model_room(ctx, model), _f64()
+    _room(tau=(tau, N * n, ft), T=(T, N * n, ft), P=(P, N * n, ft), chi=(chi, 2 * n, f64),
+          R=(R, n * data.n_rec, f64), Ks=(Ks, N, f64), Kxi=(Kxi, N, f64), Keta=(Keta, N, f64))
     M = _model(model)
     _cuda_ok(tau, T, P, chi, R, Ks, Kxi, Keta)
     if opts is None:
@@ -626,26 +667,45 @@ def _f32(*tensors):
             raise TypeError("network buffers must be contiguous float32 CUDA tensors")
 
 
+# input channels of the network per node: s / s_ref - 1, xi, eta and the source offset
+NET_FEATURES = 6
+
+
+def _net_room(ctx, n_grids, **named):
+    """Sizes of the network's buffers: parameter-sized (theta, grad, m, v), inputs
+    n_grids x N x NET_FEATURES (x), per-node outputs n_grids x N (y, target, mask)."""
+    N = _nodes(ctx)
+    per = {"theta": tt_net_param_count(), "grad": tt_net_param_count(),
+           "m": tt_net_param_count(), "v": tt_net_param_count(),
+           "x": n_grids * N * NET_FEATURES, "y": n_grids * N, "target": n_grids * N,
+           "mask": n_grids * N}
+    _room(**{k: (v, per[k]) for k, v in named.items()})
+
+
 def tt_net_features(ctx, model, src, x):
     """x: float32 [n_src, N_r, N_t, N_p, 6] (or any contiguous shape of that size)."""
+    _model_room(ctx, model)
+    pts, n = _points(src)
+    _f32(x)
+    _room(x=(x, n * _nodes(ctx) * NET_FEATURES))
     M = _model(model)
     _cuda_ok(x)
-    _f32(x)
-    pts, n = _points(src)
     _check(ctx, lib.tt_net_features(ctx.handle, C.byref(M), pts, n, _ptr(x)))
 
 
 def tt_net_forward(ctx, theta, x, y):
     """y[n] = network(x[n]) for the n = x.shape[0] grids of the context."""
-    _cuda_ok(theta, x, y)
     _f32(theta, x, y)
+    _net_room(ctx, x.shape[0], theta=theta, x=x, y=y)
+    _cuda_ok(theta, x, y)
     _check(ctx, lib.tt_net_forward(ctx.handle, _ptr(theta), _ptr(x), x.shape[0], _ptr(y)))
 
 
 def tt_net_loss_grad(ctx, theta, x, target, mask, grad):
     """Masked MSE of the network output against target; writes grad, returns the loss."""
-    _cuda_ok(theta, x, target, mask, grad)
     _f32(theta, x, target, mask, grad)
+    _net_room(ctx, x.shape[0], theta=theta, x=x, target=target, mask=mask, grad=grad)
+    _cuda_ok(theta, x, target, mask, grad)
     loss = C.c_double()
     _check(ctx, lib.tt_net_loss_grad(ctx.handle, _ptr(theta), _ptr(x), _ptr(target), _ptr(mask),
                                      x.shape[0], _ptr(grad), C.byref(loss)))
@@ -653,15 +713,17 @@ def tt_net_loss_grad(ctx, theta, x, target, mask, grad):
 
 
 def tt_net_adam(ctx, theta, grad, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
-    _cuda_ok(theta, grad, m, v)
     _f32(theta, grad, m, v)
+    _net_room(ctx, 0, theta=theta, grad=grad, m=m, v=v)
+    _cuda_ok(theta, grad, m, v)
     _check(ctx, lib.tt_net_adam(ctx.handle, _ptr(theta), _ptr(grad), _ptr(m), _ptr(v), int(step),
                                 lr, beta1, beta2, eps))
 
 
 def tt_net_set_weights(ctx, theta):
-    _cuda_ok(theta)
     _f32(theta)
+    _net_room(ctx, 0, theta=theta)
+    _cuda_ok(theta)
     _check(ctx, lib.tt_net_set_weights(ctx.handle, _ptr(theta)))
 
 
@@ -672,6 +734,7 @@ AUTOTUNE_CANDIDATES = ("nodes/1 group", "nodes/2 groups", "nodes/4 groups", "nod
 def tt_autotune(ctx, model, src, opts):
     """Times the forward sweep's launch configurations on this workload and writes the
     fastest into opts; returns {candidate: ms per iteration} (0 = skipped or cached)."""
+    _model_room(ctx, model)
     M = _model(model)
     pts, n = _points(src)
     ms = (C.c_double * len(AUTOTUNE_CANDIDATES))()
@@ -681,6 +744,7 @@ def tt_autotune(ctx, model, src, opts):
 
 def tt_net_infer(ctx, x, y):
     """Warm-start inference with the weights of tt_net_set_weights (tensor cores)."""
-    _cuda_ok(x, y)
     _f32(x, y)
+    _net_room(ctx, x.shape[0], x=x, y=y)
+    _cuda_ok(x, y)
     _check(ctx, lib.tt_net_infer(ctx.handle, _ptr(x), x.shape[0], _ptr(y)))

@@ -1101,31 +1101,12 @@ tt_status tt_ctx_create(tt_ctx **out, const tt_grid *grid, void *cuda_stream) {
     if (!out || !grid) return TT_EINVAL;
     *out = nullptr;
     const tt_grid &G = *grid;
-    int dims[3] = {G.n_r, G.n_t, G.n_p};
-    for (int d : dims)
-        if (d < 4 || d > TT_MAX_DIM) return TT_EINVAL;
-    if (!(G.depth_max_km > G.depth_min_km) || !(G.lat_max_deg > G.lat_min_deg) ||
-        !(G.lon_max_deg > G.lon_min_deg) || !(G.earth_radius_km > G.depth_max_km))
-        return TT_EINVAL;
-    if (G.geometry != TT_GEOM_SPHERICAL && G.geometry != TT_GEOM_FLAT) return TT_EINVAL;
-    if (G.geometry == TT_GEOM_SPHERICAL &&
-        (G.lat_min_deg <= -89.0 || G.lat_max_deg >= 89.0))
-        return TT_EINVAL;
+    GridC gc;
+    if (!grid_constants(G, gc)) return TT_EINVAL;
     tt_ctx *ctx = new tt_ctx();
     ctx->grid = G;
     ctx->st = (cudaStream_t)cuda_stream;
-    const double deg = 3.14159265358979323846 / 180.0;
-    GridC &g = ctx->g;
-    g.nr = G.n_r; g.nt = G.n_t; g.np = G.n_p;
-    g.flat = G.geometry == TT_GEOM_FLAT;
-    g.N = (long long)g.nr * g.nt * g.np;
-    g.re = G.earth_radius_km;
-    g.r0 = G.earth_radius_km - G.depth_max_km;
-    g.dr = (G.depth_max_km - G.depth_min_km) / (g.nr - 1);
-    g.t0 = G.lat_min_deg * deg;
-    g.dt = (G.lat_max_deg - G.lat_min_deg) * deg / (g.nt - 1);
-    g.p0 = G.lon_min_deg * deg;
-    g.dp = (G.lon_max_deg - G.lon_min_deg) * deg / (g.np - 1);
+    ctx->g = gc;
     tt_status s = TT_OK;
     if (cudaGetDevice(&ctx->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, ctx->device) !=

@@ -12,6 +12,13 @@ struct PointD {  // same layout as tt_point
     double depth, lat, lon;
 };
 
+// Checks a grid description (3 < n <= TT_MAX_DIM per axis, ordered and non-empty extents,
+// a radius above the deepest layer, a known geometry, and for spherical grids latitudes
+// strictly inside (-89, 89) degrees, away from the poles where 1 / cos(theta) blows up) and
+// fills the device constants. Returns false for an invalid grid. Every entry point that
+// takes a tt_grid validates it here.
+bool grid_constants(const tt_grid &G, GridC &g);
+
 template <typename F>
 cudaError_t run_source_setup(const GridC &g, const void *s, const void *xi, const void *eta,
                              const PointD *d_pts, int n_src, SrcC *d_src, Vec2<F> *tabT,

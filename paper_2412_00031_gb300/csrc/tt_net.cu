@@ -281,7 +281,7 @@ __global__ void warm_tau_kernel(long long N, int B, int b0, int nb, const float 
     if (q >= N * nb) return;
     const int bl = (int)(q % nb);
     const long long n = q / nb;
-    // a non-finite prediction starts the node at tau = 1; the others are clamped
+    // a NaN prediction starts the node at tau = 1; the others (+-inf included) are clamped
     const float yv = y[(long long)bl * N + n];
     const float v = yv == yv ? fminf(fmaxf(yv, kNetClampLo), kNetClampHi) : 0.0f;
     tau[n * B + b0 + bl] = (F)(1.0f + v);

@@ -58,28 +58,6 @@ unsigned char *scratch_address(int dev, char *h_err, int err_len) {
     return g_scratch_ptr[dev];
 }
 
-bool grid_from(const tt_grid &G, GridC &g) {
-    int dims[3] = {G.n_r, G.n_t, G.n_p};
-    for (int d : dims)
-        if (d < 4 || d > TT_MAX_DIM) return false;
-    if (!(G.depth_max_km > G.depth_min_km) || !(G.lat_max_deg > G.lat_min_deg) ||
-        !(G.lon_max_deg > G.lon_min_deg) || !(G.earth_radius_km > G.depth_max_km))
-        return false;
-    if (G.geometry != TT_GEOM_SPHERICAL && G.geometry != TT_GEOM_FLAT) return false;
-    const double deg = 3.14159265358979323846 / 180.0;
-    g.nr = G.n_r; g.nt = G.n_t; g.np = G.n_p;
-    g.flat = G.geometry == TT_GEOM_FLAT;
-    g.N = (long long)g.nr * g.nt * g.np;
-    g.re = G.earth_radius_km;
-    g.r0 = G.earth_radius_km - G.depth_max_km;
-    g.dr = (G.depth_max_km - G.depth_min_km) / (g.nr - 1);
-    g.t0 = G.lat_min_deg * deg;
-    g.dt = (G.lat_max_deg - G.lat_min_deg) * deg / (g.nt - 1);
-    g.p0 = G.lon_min_deg * deg;
-    g.dp = (G.lon_max_deg - G.lon_min_deg) * deg / (g.np - 1);
-    return true;
-}
-
 bool point_inside(const tt_grid &G, const tt_point &p) {
     const double eps = 1e-9;
     double sd = G.depth_max_km - G.depth_min_km, st = G.lat_max_deg - G.lat_min_deg;
@@ -97,7 +75,7 @@ extern "C" tt_status tt_misfit_noalloc(const tt_grid *grid, const void *d_T, int
                                        double *d_R, void *cuda_stream, char *h_err,
                                        int err_len) {
     GridC g;
-    if (!grid || !grid_from(*grid, g)) {
+    if (!grid || !grid_constants(*grid, g)) {
         set_err(h_err, err_len, "tt_misfit_noalloc: invalid grid");
         return TT_EINVAL;
     }

@@ -59,3 +59,70 @@ def test_tables_smaller_than_the_data_are_refused(tt):
     with pytest.raises(ValueError, match="CUDA"):
         tt.tt_tele_region_times(ctx, _z(2, 5, 5), 6000.0, 6371.0, 10.0, np.zeros((2, 3)),
                                 _z(*shape, 2))
+
+
+def _f(*shape):
+    return torch.zeros(shape, dtype=torch.float32)
+
+
+def test_arguments_of_the_wrong_element_type_are_refused(tt):
+    """Sizes are counted in elements, so a buffer of the wrong float type would pass a size
+    check and then be read or written with the other element size: every batched field must
+    have the model's type, every double* argument must be float64."""
+    shape = (4, 5, 6)
+    ctx = _Ctx(tt, shape)
+    m64 = (_z(*shape), _z(*shape), _z(*shape))
+    m32 = (_f(*shape), _f(*shape), _f(*shape))
+    src = np.zeros((3, 3))
+    with pytest.raises(TypeError, match="tau is torch.float32"):
+        tt.tt_forward(ctx, m64, src, _f(*shape, 3), _z(*shape, 3))
+    with pytest.raises(TypeError, match="xi is torch.float32"):
+        tt.tt_forward(ctx, (m64[0], m32[1], m64[2]), src, _z(*shape, 3))
+    with pytest.raises(TypeError, match="Ks is torch.float32"):
+        tt.tt_kernel(ctx, m32, _f(*shape, 3), _f(*shape, 3), _f(*shape), _z(*shape), _z(*shape))
+    with pytest.raises(TypeError, match="R is torch.float32"):
+        tt.tt_adjoint(ctx, m32, src, _f(*shape, 3), np.zeros((7, 3)), _f(3, 7), _f(*shape, 3))
+    with pytest.raises(TypeError, match="P is torch.float64"):
+        tt.tt_adjoint(ctx, m32, src, _f(*shape, 3), np.zeros((7, 3)), _z(3, 7), _z(*shape, 3))
+
+    class D:
+        n_src, n_rec = 3, 7
+    with pytest.raises(TypeError, match="chi is torch.float32"):
+        tt.tt_misfit(ctx, _f(*shape, 3), D(), None, _f(3, 2), _z(3, 7))
+    with pytest.raises(TypeError, match="Kd is torch.float32"):
+        tt.tt_kernel_normalize(ctx, _z(*shape), _z(*shape), _z(*shape), _f(*shape), 1.0, 1.0)
+    with pytest.raises(TypeError, match="fields must be float32 or float64"):
+        tt.tt_forward(ctx, tuple(a.half() for a in m32), src, _f(*shape, 3).half())
+
+
+def test_no_alloc_misfit_and_network_buffers_are_size_checked(tt):
+    shape = (4, 5, 6)
+    grid = dict(n_r=4, n_t=5, n_p=6, depth_min_km=0.0, depth_max_km=10.0, lat_min_deg=0.0,
+                lat_max_deg=1.0, lon_min_deg=0.0, lon_max_deg=1.0, earth_radius_km=6371.0,
+                flat=0)
+
+    class D:
+        n_src, n_rec = 3, 7
+    with pytest.raises(ValueError, match="T holds 240 elements; the call touches 360"):
+        tt.tt_misfit_noalloc(grid, _f(*shape, 2), D(), None, _z(3, 2), _z(3, 7))
+    with pytest.raises(ValueError, match="R holds"):
+        tt.tt_misfit_noalloc(grid, _f(*shape, 3), D(), None, _z(3, 2), _z(3, 6))
+    with pytest.raises(TypeError, match="Tr is torch.float32"):
+        tt.tt_misfit_noalloc(grid, _f(*shape, 3), D(), _f(3, 7), _z(3, 2), _z(3, 7))
+    ctx = _Ctx(tt, shape)
+    n_par = tt.tt_net_param_count()
+    N = 4 * 5 * 6
+    with pytest.raises(ValueError, match="theta holds"):
+        tt.tt_net_set_weights(ctx, _f(n_par - 1))
+    with pytest.raises(ValueError, match="x holds"):
+        tt.tt_net_forward(ctx, _f(n_par), _f(2, N * 6 - 1), _f(2, N))
+    with pytest.raises(ValueError, match="y holds"):
+        tt.tt_net_infer(ctx, _f(2, N, 6), _f(2, N - 1))
+    with pytest.raises(ValueError, match="mask holds"):
+        tt.tt_net_loss_grad(ctx, _f(n_par), _f(2, N, 6), _f(2, N), _f(N), _f(n_par))
+    with pytest.raises(ValueError, match="v holds"):
+        tt.tt_net_adam(ctx, _f(n_par), _f(n_par), _f(n_par), _f(3), 1)
+    with pytest.raises(ValueError, match="x holds"):
+        tt.tt_net_features(ctx, (_f(*shape),) * 3, np.zeros((2, 3)), _f(N * 6))
+    with pytest.raises(ValueError, match="CUDA"):
+        tt.tt_net_set_weights(ctx, _f(n_par))

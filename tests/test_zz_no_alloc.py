@@ -78,3 +78,22 @@ def test_noalloc_rejects_too_many_receivers(tt):
         tt.tt_misfit_noalloc(w.grid.as_dict(), T, data, None, None, R)
     assert e.value.status == tt.TT_EINVAL
     assert "TT_NOALLOC_MAX_REC" in str(e.value)
+
+
+def test_noalloc_rejects_a_grid_that_tt_ctx_create_rejects(tt):
+    """Both entry points validate the grid with the same rules: a spherical grid reaching
+    latitude 89 is refused (TT_EINVAL) by each."""
+    import torch
+    w = I.small_case(34, shape=(9, 9, 9), n_src=1, n_rec=3)
+    g = w.grid.as_dict()
+    g.update(lat_min_deg=88.0, lat_max_deg=89.5)
+    with pytest.raises(tt.TTError) as e:
+        tt.tt_ctx_create(g)
+    assert e.value.status == tt.TT_EINVAL
+    T = torch.zeros(w.grid.shape + (1,), dtype=torch.float32, device="cuda")
+    data = tt.DeviceData.from_workload(w)
+    R = torch.empty((1, data.n_rec), dtype=torch.float64, device="cuda")
+    with pytest.raises(tt.TTError) as e:
+        tt.tt_misfit_noalloc(g, T, data, None, None, R)
+    assert e.value.status == tt.TT_EINVAL
+    assert "invalid grid" in str(e.value)
