@@ -44,6 +44,8 @@ FWD_BYTES_PER_UPDATE = 8      # FP32 tau read + write per (node, source) update
 FWD_BYTES_PER_NODE_SWEEP = 12  # s, xi, eta once per node per sweep (shared by the batch)
 ADJ_BYTES_PER_UPDATE = 12     # FP32 P read + write and T read per (node, source) update
 ADJ_BYTES_PER_NODE_SWEEP = 8  # xi, eta once per node per sweep
+KACC_BYTES_PER_PAIR = 8       # FP32 T and P read per (node, source) of the kernel accumulation
+KACC_BYTES_PER_NODE = 52      # s read + FP64 read-modify-write of K_s, K_xi, K_eta per node
 
 
 def peaks():
@@ -53,6 +55,22 @@ def peaks():
         return float(p["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def bf16_peak():
+    """Dense BF16 tensor peak (burst, for a kernel timed alone) in TFLOP/s."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured (burst)"
+    except Exception:
+        return 1900.0, "fallback"
+
+
+def hbm_kernel(ms, pairs, nodes, per_pair, per_node, hbm):
+    """HBM roofline entry of one launch: algorithmic bytes / CUDA-event time."""
+    b = pairs * per_pair + nodes * per_node
+    gbs = b / (ms * 1e-3) / 1e9
+    return {"ms": ms, "algorithmic_bytes": b, "GBps": gbs, "frac_hbm": gbs / hbm}
 
 
 def workload_config(w, n_gpus):
@@ -164,7 +182,7 @@ class GpuPath:
             itf, ita = tt.tt_plan_run(self.plan, allow_unconverged=self.allow_unconverged)
             fs = tt.tt_get_stats(self.ctx, tt.TT_STATS_FORWARD)
             as_ = tt.tt_get_stats(self.ctx, tt.TT_STATS_ADJOINT)
-            self.iters.append((itf, ita, fs, as_))
+            self.iters.append((itf, ita, fs, as_, self.kernel_stats()))
             return
         for k in self.K:
             k.zero_()
@@ -177,10 +195,13 @@ class GpuPath:
         tt.tt_kernel(self.ctx, self.model, self.T, self.P, *self.K)
         fs = tt.tt_get_stats(self.ctx, tt.TT_STATS_FORWARD)
         as_ = tt.tt_get_stats(self.ctx, tt.TT_STATS_ADJOINT)
-        self.iters.append((itf, ita, fs, as_))
+        self.iters.append((itf, ita, fs, as_, self.kernel_stats()))
 
     def launches(self):
         return self.tt.tt_get_stats(self.ctx, self.tt.TT_STATS_FORWARD)["launches"]
+
+    def kernel_stats(self):
+        return self.tt.tt_get_stats(self.ctx, self.tt.TT_STATS_KERNEL)
 
 
 def run_e2e(gp, w, steps):
@@ -259,6 +280,12 @@ def gpu_arm(args, rank, world):
         tuned = {"ms_per_iteration": {k: round(v, 3) for k, v in ms.items()},
                  "chosen": {"sweep_schedule": gp.opts.sweep_schedule,
                             "fwd_groups": gp.opts.fwd_groups}}
+    if args.autotune and args.adj_chunk == 0:
+        gp.step()                 # T and R of this batch for the adjoint tuner
+        ms = gp.tt.tt_autotune_adjoint(gp.ctx, gp.model, w.src, gp.T, w.rec, gp.R, gp.opts)
+        tuned = dict(tuned or {}, adjoint={
+            "ms_per_solve": {k: round(v, 3) for k, v in ms.items()},
+            "chosen": {"adj_chunk": gp.opts.adj_chunk, "adj_groups": gp.opts.adj_groups}})
     if args.plan:
         gp.use_plan()
     for _ in range(args.warmup):
@@ -305,6 +332,13 @@ def gpu_arm(args, rank, world):
     traffic = profiled_traffic(digest, f_upd)
     itf = np.concatenate([s[0] for s in gp.iters])
     ita = np.concatenate([s[1] for s in gp.iters])
+    kacc = [s[4] for s in gp.iters]
+    k_ms = float(np.mean([s["sweep_ms"] for s in kacc]))
+    kernel_accum = hbm_kernel(k_ms, float(np.mean([s["node_updates"] for s in kacc])),
+                              float(np.mean([s["node_sweeps"] for s in kacc])),
+                              KACC_BYTES_PER_PAIR, KACC_BYTES_PER_NODE, hbm)
+    kernel_accum["bytes_per_unit"] = "%d B per (node, source) + %d B per node" % (
+        KACC_BYTES_PER_PAIR, KACC_BYTES_PER_NODE)
     value = world * w.n_src / (ms * 1e-3)
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -324,7 +358,8 @@ def gpu_arm(args, rank, world):
             "adj_sweep": {"ms": a_ms, "node_updates": a_upd, "GBps": a_gbs,
                           "frac_hbm": a_gbs / hbm, "iters_mean": float(ita.mean()),
                           "iters_max": int(ita.max())},
-            "rest_ms": ms - f_ms - a_ms},
+            "kernel_accum": kernel_accum,
+            "rest_ms": ms - f_ms - a_ms - k_ms},
         "e2e": {"value": world * w.n_src / (e2e_ms * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "ms_per_step": e2e_ms},
@@ -377,7 +412,14 @@ def godunov_leg(args, gp, world):
     ita = np.concatenate([s[1] for s in gp.iters])
     fwd = [s[2] for s in gp.iters]
     adj = [s[3] for s in gp.iters]
+    hbm, _ = peaks()
+    f_ms = float(np.mean([s["sweep_ms"] for s in fwd]))
+    fwd_kernel = hbm_kernel(f_ms, float(np.mean([s["node_updates"] for s in fwd])),
+                            float(np.mean([s["node_sweeps"] for s in fwd])),
+                            FWD_BYTES_PER_UPDATE, FWD_BYTES_PER_NODE_SWEEP, hbm)
+    fwd_kernel["kernel"] = "fwd_sweep_kernel<float, unsigned, 0, 2>"
     return {"value": world * gp.w.n_src / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+            "forward_kernel": fwd_kernel,
             "scheme": "Godunov upwind for anisotropic models (opts.scheme = 2)",
             "iters_fwd_mean": float(itf.mean()), "iters_fwd_max": int(itf.max()),
             "iters_adj_mean": float(ita.mean()),
@@ -481,10 +523,17 @@ def warm_leg(args, gp, world):
     itf = np.concatenate([s[0] for s in gp.iters])
     fwd = [s[2] for s in gp.iters]
     meta = _json.loads(str(z["summary"]))
+    inf_ms = float(np.mean([s["warm_ms"] for s in fwd]))
+    sweep_ms = float(np.mean([s["sweep_ms"] for s in fwd]))
+    hbm, _ = peaks()
+    sweep = hbm_kernel(sweep_ms, float(np.mean([s["node_updates"] for s in fwd])),
+                       float(np.mean([s["node_sweeps"] for s in fwd])), FWD_BYTES_PER_UPDATE,
+                       FWD_BYTES_PER_NODE_SWEEP, hbm)
     return {"value": world * gp.w.n_src / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
             "iters_fwd_mean": float(itf.mean()), "iters_fwd_max": int(itf.max()),
-            "inference_ms": float(np.mean([s["warm_ms"] for s in fwd])),
-            "sweep_ms": float(np.mean([s["sweep_ms"] for s in fwd])),
+            "inference_ms": inf_ms, "sweep_ms": sweep_ms,
+            "inference_roofline": net_roofline(gp.w.grid.shape, gp.w.n_src, inf_ms),
+            "forward_kernel": sweep,
             "inference": "3x3x3 convolutions, all four layers on the tensor cores (tcgen05, BF16 "
                          "operands, FP32 accumulation in tensor memory)",
             "weights": "%s: trained on %d forward solves on %s random-field models, held-out "
@@ -500,6 +549,21 @@ def warm_leg(args, gp, world):
 NET_TILE_FLOP = 9 * 2 * 128 * 16 * (96 * 1 + 96 * 2 + 96 * 2 + 48 * 2)
 NET_TILE_ROWS = 126
 NET_USEFUL_FLOP_PER_NODE = 2 * 27 * (6 * 32 + 32 * 32 + 32 * 32 + 32 * 1)
+
+
+def net_roofline(shape, n_grids, ms):
+    """Tensor roofline of the warm start's inference over n_grids grids in ms (the whole
+    inference: features, packing, four tcgen05 convolution layers, the start of tau):
+    executed MMA FLOPs and useful network FLOPs against the dense BF16 peak."""
+    nodes = int(np.prod(shape))
+    rows = shape[0] * (shape[1] + 1) * (shape[2] + 1)
+    tiles = -(-rows // NET_TILE_ROWS) * n_grids
+    executed = NET_TILE_FLOP * tiles / (ms * 1e-3) / 1e12
+    useful = NET_USEFUL_FLOP_PER_NODE * nodes * n_grids / (ms * 1e-3) / 1e12
+    peak, src = bf16_peak()
+    return {"bound": "tensor", "kernel": "conv3d_tc_kernel (4 layers)", "achieved": executed,
+            "useful_tflops": useful, "peak": peak, "unit": "TFLOP/s", "frac": executed / peak,
+            "frac_useful": useful / peak, "peak_source": src}
 
 
 def infer_only(args):
@@ -532,21 +596,11 @@ def infer_only(args):
         times.append(e0.elapsed_time(e1))
     ctx.close()
     ms = float(np.median(times))
-    nodes = int(np.prod(g.shape))
-    rows = g.shape[0] * (g.shape[1] + 1) * (g.shape[2] + 1)
-    tiles = -(-rows // NET_TILE_ROWS) * nb
-    executed = NET_TILE_FLOP * tiles / (ms * 1e-3) / 1e12
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            peak, src = float(json.load(f)["bf16_tflops"]), "measured (burst)"
-    except Exception:
-        peak, src = 1900.0, "fallback"
+    roof = net_roofline(g.shape, nb, ms)
+    roof["note"] = "executed MMA FLOPs (padded channels, 126 of 128 rows per tile)"
     return {"metric": "warm-start inference throughput", "value": nb / (ms * 1e-3),
             "unit": "source-grids/s", "ms": ms, "grids": nb, "grid": list(g.shape),
-            "useful_tflops": NET_USEFUL_FLOP_PER_NODE * nodes * nb / (ms * 1e-3) / 1e12,
-            "roofline": {"bound": "tensor", "achieved": executed, "peak": peak, "unit": "TFLOP/s",
-                         "frac": executed / peak, "peak_source": src,
-                         "note": "executed MMA FLOPs (padded channels, 126 of 128 rows per tile)"},
+            "useful_tflops": roof["useful_tflops"], "roofline": roof,
             "gpu_launches_per_call": 5}
 
 

@@ -131,6 +131,9 @@ typedef struct {
                                sides along theta and phi from the characteristic direction
                                M grad T, the Schur-complement form of M on each axis subset).
                                The Godunov solvers run on the node-hyperplane schedule. */
+    int adj_groups;         /* adjoint: barrier groups per launch (1..8; each gets at least 32
+                               sources), 0 = automatic (one per 64 sources, at most 4).
+                               Results do not depend on it. */
 } tt_opts;
 
 typedef struct tt_ctx tt_ctx;
@@ -150,6 +153,8 @@ typedef struct {
 
 #define TT_STATS_FORWARD 0
 #define TT_STATS_ADJOINT 1
+#define TT_STATS_KERNEL 2   /* the last kernel accumulation (tt_kernel or a plan's): sweep_ms its
+                               device time, node_updates = nodes x sources, node_sweeps = nodes */
 
 /* Fills opts with the defaults for dtype: tol_fwd 1e-6 (F32) / 1e-8 (F64), tol_adj the
  * same, 500 iterations, init 0, spin limit 2 s. */
@@ -233,6 +238,19 @@ tt_status tt_kernel_density(tt_ctx *ctx, const void *d_P, int n_src, int dtype, 
  * K <- K / (d_Kd + eps)^zeta. eps > 0, zeta >= 0, else TT_EINVAL. */
 tt_status tt_kernel_normalize(tt_ctx *ctx, double *d_Ks, double *d_Kxi, double *d_Keta,
                               const double *d_Kd, double eps, double zeta);
+
+/* Eq. 18 with the damping taken relative to the density: eps = eps_rel * max_n d_Kd[n]
+ * (1e-300 if that maximum is 0), the maximum an FP64 reduction on the device, so the step
+ * needs no host round trip. eps_rel > 0, zeta >= 0, else TT_EINVAL. */
+tt_status tt_kernel_normalize_rel(tt_ctx *ctx, double *d_Ks, double *d_Kxi, double *d_Keta,
+                                  const double *d_Kd, double eps_rel, double zeta);
+
+/* Step-size control (step 4 of Sec. 2): the total misfit of a batch (Eqs. 2-4),
+ * alpha sum_b d_chi[b][0] + beta sum_b d_chi[b][1] + gamma sum_b d_chi_cr[b] over n_src sources
+ * (d_chi as tt_misfit writes it; d_chi_cr as tt_misfit_cr writes it, or NULL), an FP64 sum in a
+ * fixed order on the device. *h_total (host) receives it; the call waits for the stream. */
+tt_status tt_misfit_total(tt_ctx *ctx, int n_src, const double *d_chi, double alpha,
+                          double beta, const double *d_chi_cr, double gamma, double *h_total);
 
 /* H offset inversion grids of the multiple-grid parameterisation (Eqs. 11-14): n_grids
  * grids of n_r x n_t x n_p nodes (3..4096 per axis; 1..64 grids). Along each axis grid h has
@@ -386,6 +404,17 @@ tt_status tt_misfit_noalloc(const tt_grid *grid, const void *d_T, int dtype,
 tt_status tt_autotune(tt_ctx *ctx, const tt_model *model, const tt_point *h_src, int n_src,
                       tt_opts *opts, double *h_ms);
 
+/* Autotuner of the adjoint sweep (Eq. 5): times whole adjoint solves of this batch (d_T, n_rec,
+ * h_rec and d_R as for tt_adjoint; the adjoint field goes to a workspace buffer) in six launch
+ * configurations and writes the fastest into opts (adj_chunk, adj_groups). Candidates, in
+ * this order (adj_chunk, adj_groups): (all, 1), (all, 2), (all, 4), (all, 8), (128, auto),
+ * (64, 1); h_ms (host [6], may be NULL) receives each one's device time (0 = skipped: fewer
+ * than 32 sources per group, or a chunk no smaller than the batch). Results do not depend on
+ * the choice. Cached per (n_src, dtype) like tt_autotune. */
+tt_status tt_autotune_adjoint(tt_ctx *ctx, const tt_model *model, const tt_point *h_src,
+                              int n_src, const void *d_T, int n_rec, const tt_point *h_rec,
+                              const double *d_R, tt_opts *opts, double *h_ms);
+
 /* ---- Warm-start network. A small 3D convolutional network predicts the factored correction
  * tau of Sec. 3.1 (T = T0 tau) from local quantities, so that the forward sweep of Sec. 3.1
  * starts closer to its fixed point (opts.init = 2); the sweep still runs to tol_fwd, so the
@@ -452,7 +481,8 @@ tt_status tt_plan_run(tt_plan *plan, int *h_iters_fwd, int *h_iters_adj);
 void tt_plan_destroy(tt_plan *plan);
 
 /* Copies the measurements of the last forward (which = TT_STATS_FORWARD) or adjoint
- * (TT_STATS_ADJOINT) sweep. Host only; call after the solve returned. */
+ * (TT_STATS_ADJOINT) sweep, or of the last kernel accumulation (TT_STATS_KERNEL, which first
+ * waits for that accumulation to finish). Host only; call after the solve returned. */
 tt_status tt_get_stats(const tt_ctx *ctx, int which, tt_stats *out);
 
 #ifdef __cplusplus

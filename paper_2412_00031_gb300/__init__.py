@@ -70,7 +70,7 @@ class TTOpts(C.Structure):
                 ("max_iter_fwd", C.c_int), ("max_iter_adj", C.c_int), ("init", C.c_int),
                 ("spin_limit_ns", C.c_longlong), ("launch_blocks", C.c_int),
                 ("sweep_schedule", C.c_int), ("adj_chunk", C.c_int), ("fwd_groups", C.c_int),
-                ("fwd_slots", C.c_int), ("scheme", C.c_int)]
+                ("fwd_slots", C.c_int), ("scheme", C.c_int), ("adj_groups", C.c_int)]
 
 
 class TTStats(C.Structure):
@@ -79,7 +79,7 @@ class TTStats(C.Structure):
                 ("block_threads", C.c_int), ("launches", C.c_longlong), ("warm_ms", C.c_double)]
 
 
-TT_STATS_FORWARD, TT_STATS_ADJOINT = 0, 1
+TT_STATS_FORWARD, TT_STATS_ADJOINT, TT_STATS_KERNEL = 0, 1, 2
 
 EXPORTED = ["tt_default_opts", "tt_ctx_create", "tt_ctx_destroy", "tt_last_error",
             "tt_forward", "tt_misfit", "tt_adjoint", "tt_kernel", "tt_get_stats",
@@ -89,7 +89,8 @@ EXPORTED = ["tt_default_opts", "tt_ctx_create", "tt_ctx_destroy", "tt_last_error
             "tt_kernel_density", "tt_kernel_normalize", "tt_mgrid_project", "tt_mgrid_expand",
             "tt_model_update", "tt_misfit_cr", "tt_field_at_points", "tt_misfit_table",
             "tt_reloc_kernels", "tt_reloc_update", "tt_tele2d", "tt_tele_region_times",
-            "tt_forward_tele"]
+            "tt_forward_tele", "tt_autotune_adjoint", "tt_kernel_normalize_rel",
+            "tt_misfit_total"]
 TT_NOALLOC_MAX_REC = 1024
 
 
@@ -134,6 +135,12 @@ def _load():
     L.tt_net_infer.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]
     L.tt_autotune.argtypes = [C.c_void_p, C.POINTER(TTModel), C.POINTER(TTPoint), C.c_int,
                               C.POINTER(TTOpts), C.POINTER(C.c_double)]
+    L.tt_kernel_normalize_rel.argtypes = [C.c_void_p] * 5 + [C.c_double, C.c_double]
+    L.tt_misfit_total.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_double, C.c_double,
+                                  C.c_void_p, C.c_double, C.POINTER(C.c_double)]
+    L.tt_autotune_adjoint.argtypes = [C.c_void_p, C.POINTER(TTModel), C.POINTER(TTPoint),
+                                      C.c_int, C.c_void_p, C.c_int, C.POINTER(TTPoint),
+                                      C.c_void_p, C.POINTER(TTOpts), C.POINTER(C.c_double)]
     L.tt_misfit_cr.argtypes = [C.c_void_p, C.POINTER(TTCrData)] + [C.c_void_p] * 3
     L.tt_kernel_density.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p]
     L.tt_kernel_normalize.argtypes = [C.c_void_p] + [C.c_void_p] * 4 + [C.c_double] * 2
@@ -161,7 +168,8 @@ def _load():
                  "tt_kernel_density", "tt_kernel_normalize", "tt_mgrid_project",
                  "tt_mgrid_expand", "tt_model_update", "tt_misfit_cr", "tt_field_at_points",
                  "tt_misfit_table", "tt_reloc_kernels", "tt_reloc_update", "tt_tele2d",
-                 "tt_tele_region_times", "tt_forward_tele"):
+                 "tt_tele_region_times", "tt_forward_tele", "tt_autotune_adjoint",
+                 "tt_kernel_normalize_rel", "tt_misfit_total"):
         getattr(L, name).restype = C.c_int
     return L
 
@@ -548,6 +556,29 @@ def tt_kernel_normalize(ctx, Ks, Kxi, Keta, Kd, eps, zeta):
                                         float(eps), float(zeta)))
 
 
+def tt_kernel_normalize_rel(ctx, Ks, Kxi, Keta, Kd, eps_rel, zeta):
+    """Eq. 18 in place with eps = eps_rel max(Kd), the maximum taken on the device."""
+    N = _nodes(ctx)
+    f64 = _f64()
+    _room(Ks=(Ks, N, f64), Kxi=(Kxi, N, f64), Keta=(Keta, N, f64), Kd=(Kd, N, f64))
+    _cuda_ok(Ks, Kxi, Keta, Kd)
+    _check(ctx, lib.tt_kernel_normalize_rel(ctx.handle, _ptr(Ks), _ptr(Kxi), _ptr(Keta),
+                                            _ptr(Kd), float(eps_rel), float(zeta)))
+
+
+def tt_misfit_total(ctx, chi, alpha=1.0, beta=1.0, chi_cr=None, gamma=1.0):
+    """alpha sum chi[:, 0] + beta sum chi[:, 1] (+ gamma sum chi_cr) of a batch, an FP64 sum
+    on the device; chi [n_src, 2] and chi_cr [n_src] float64 CUDA tensors."""
+    n = chi.shape[0]
+    f64 = _f64()
+    _room(chi=(chi, 2 * n, f64), chi_cr=(chi_cr, n, f64))
+    _cuda_ok(chi, chi_cr)
+    out = C.c_double()
+    _check(ctx, lib.tt_misfit_total(ctx.handle, n, _ptr(chi), float(alpha), float(beta),
+                                    _ptr(chi_cr), float(gamma), C.byref(out)))
+    return out.value
+
+
 def mgrid(n_r, n_t, n_p, n_grids):
     """Description of n_grids offset inversion grids of n_r x n_t x n_p nodes."""
     return TTMgrid(n_r, n_t, n_p, n_grids)
@@ -740,6 +771,27 @@ def tt_autotune(ctx, model, src, opts):
     ms = (C.c_double * len(AUTOTUNE_CANDIDATES))()
     _check(ctx, lib.tt_autotune(ctx.handle, C.byref(M), pts, n, C.byref(opts), ms))
     return dict(zip(AUTOTUNE_CANDIDATES, list(ms)))
+
+
+ADJ_AUTOTUNE_CANDIDATES = ("all sources/1 group", "all sources/2 groups",
+                           "all sources/4 groups", "all sources/8 groups", "chunks of 128",
+                           "chunks of 64/1 group")
+
+
+def tt_autotune_adjoint(ctx, model, src, T, rec, R, opts):
+    """Times the adjoint sweep's launch configurations on this batch (T, R as for tt_adjoint)
+    and writes the fastest into opts; returns {candidate: ms per solve} (0 = skipped or
+    cached)."""
+    pts, n = _points(src)
+    rpts, nr = _points(rec)
+    ft = _model_room(ctx, model)
+    _room(T=(T, _nodes(ctx) * n, ft), R=(R, n * nr, _f64()))
+    M = _model(model)
+    _cuda_ok(T, R)
+    ms = (C.c_double * len(ADJ_AUTOTUNE_CANDIDATES))()
+    _check(ctx, lib.tt_autotune_adjoint(ctx.handle, C.byref(M), pts, n, _ptr(T), nr, rpts,
+                                        _ptr(R), C.byref(opts), ms))
+    return dict(zip(ADJ_AUTOTUNE_CANDIDATES, list(ms)))
 
 
 def tt_net_infer(ctx, x, y):

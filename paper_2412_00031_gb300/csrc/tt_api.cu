@@ -60,15 +60,19 @@ struct tt_ctx {
     int mg_key[4] = {0, 0, 0, 0};
     struct Tuned { int n_src, dtype, scheme, schedule, groups; };
     std::vector<Tuned> tuned;
+    struct TunedAdj { int n_src, dtype, chunk, groups; };
+    std::vector<TunedAdj> tuned_adj;
     int *h_pinned = nullptr;  // readback: [0..TT_MAX_BATCH) iterations, then flags
     PointD *h_pts = nullptr;  // staging for source / receiver positions
     size_t h_pts_cap = 0;
 
     cudaEvent_t ev_start[2] = {nullptr, nullptr}, ev_stop[2] = {nullptr, nullptr};
     cudaEvent_t ev_net[2] = {nullptr, nullptr};  // around the warm-start inference
+    cudaEvent_t ev_kacc[2] = {nullptr, nullptr}; // around the last kernel accumulation
+    int kacc_B = 0;                              // its source count
     bool warm_last = false;                      // the last forward used the warm start
     int scheme_last = 0;                         // local solver of the last forward
-    tt_stats stats[2] = {};
+    tt_stats stats[3] = {};
     long long launches = 0;   // kernels launched by this context
 };
 
@@ -326,6 +330,10 @@ tt_status check_opts(tt_ctx *ctx, const tt_opts *o) {
     if (o->fwd_groups < 0 || o->fwd_groups > kMaxBarrierGroups)
         return fail(ctx, TT_EINVAL, "fwd_groups %d outside 0..%d", o->fwd_groups,
                     kMaxBarrierGroups);
+    if (o->adj_groups < 0 || o->adj_groups > kMaxBarrierGroups)
+        return fail(ctx, TT_EINVAL, "adj_groups %d outside 0..%d", o->adj_groups,
+                    kMaxBarrierGroups);
+    if (o->adj_chunk < 0) return fail(ctx, TT_EINVAL, "adj_chunk %d < 0", o->adj_chunk);
     if (o->init == 2 && !ctx->has_net)
         return fail(ctx, TT_EINVAL, "init = 2 (warm start) needs tt_net_set_weights first");
     return TT_OK;
@@ -809,8 +817,9 @@ tt_status enq_adjoint(tt_ctx *ctx, Work<F> &W, const tt_model *m, int B, const v
         block = 256;
         int chunk = o->adj_chunk > 0 ? o->adj_chunk : B;
         chunk = chunk >= B ? B : (chunk + 31) / 32 * 32;
-        int groups = (chunk + 63) / 64;
-        if (groups > kAdjGroups) groups = kAdjGroups;
+        int groups = o->adj_groups > 0 ? o->adj_groups : (chunk + 63) / 64;
+        if (o->adj_groups <= 0 && groups > kAdjGroups) groups = kAdjGroups;
+        if (groups > (chunk + 31) / 32) groups = (chunk + 31) / 32;  // >= 32 sources a group
         grp_src = ((chunk + groups - 1) / groups + 31) / 32 * 32;
         groups = (chunk + grp_src - 1) / grp_src;
         n_bgroups = (B + grp_src - 1) / grp_src;  // groups over the whole batch
@@ -891,12 +900,15 @@ tt_status enq_adjoint(tt_ctx *ctx, Work<F> &W, const tt_model *m, int B, const v
 
 tt_status enq_kernel(tt_ctx *ctx, const tt_model *m, int B, const void *d_T, const void *d_P,
                      double *Ks, double *Kxi, double *Keta) {
+    CK(record(ctx, ctx->ev_kacc[0]));
+    ctx->kacc_B = B;
     if (m->dtype == TT_F32)
         CK(run_kernel_accum<float>(ctx->g, B, m->d_s, d_T, d_P, ctx->gd.h2, ctx->gd.cost, Ks, Kxi,
                                    Keta, ctx->n_sm, ctx->st));
     else
         CK(run_kernel_accum<double>(ctx->g, B, m->d_s, d_T, d_P, ctx->gd.h2, ctx->gd.cost, Ks,
                                     Kxi, Keta, ctx->n_sm, ctx->st));
+    CK(record(ctx, ctx->ev_kacc[1]));
     ctx->launches += 1;
     return TT_OK;
 }
@@ -941,8 +953,15 @@ Readback readback_view(tt_ctx *ctx) {
     return r;
 }
 
-size_t pinned_bytes() {
-    return sizeof(int) * (4 * TT_MAX_BATCH + 8) + 2 * sizeof(BarrierState) * kMaxBarrierGroups;
+// Pinned read-back buffer: the solves' state (readback_view), then one 64-byte slot for the
+// scalar results of the reductions (tt_misfit_total).
+size_t pinned_state_bytes() {
+    const size_t b = sizeof(int) * (4 * TT_MAX_BATCH + 8) + 2 * sizeof(BarrierState) * kMaxBarrierGroups;
+    return (b + 63) / 64 * 64;
+}
+size_t pinned_bytes() { return pinned_state_bytes() + 64; }
+double *pinned_scalar(tt_ctx *ctx) {
+    return reinterpret_cast<double *>(reinterpret_cast<char *>(ctx->h_pinned) + pinned_state_bytes());
 }
 
 // Enqueues the copies of one solve's state (forward or adjoint) into the pinned buffer.
@@ -1093,6 +1112,7 @@ void tt_default_opts(tt_opts *o, int dtype) {
     o->fwd_groups = 0;
     o->fwd_slots = 0;
     o->scheme = 0;
+    o->adj_groups = 0;
 }
 
 const char *tt_last_error(const tt_ctx *ctx) { return ctx ? ctx->err : "no context"; }
@@ -1121,7 +1141,8 @@ tt_status tt_ctx_create(tt_ctx **out, const tt_grid *grid, void *cuda_stream) {
     for (int q = 0; q < 2 && s == TT_OK; ++q)
         if (cudaEventCreate(&ctx->ev_start[q]) != cudaSuccess ||
             cudaEventCreate(&ctx->ev_stop[q]) != cudaSuccess ||
-            cudaEventCreate(&ctx->ev_net[q]) != cudaSuccess)
+            cudaEventCreate(&ctx->ev_net[q]) != cudaSuccess ||
+            cudaEventCreate(&ctx->ev_kacc[q]) != cudaSuccess)
             s = fail(ctx, TT_ECUDA, "cudaEventCreate failed");
     if (s == TT_OK && cudaMallocHost((void **)&ctx->h_pinned, pinned_bytes()) != cudaSuccess)
         s = fail(ctx, TT_ENOMEM, "pinned host allocation failed");
@@ -1164,6 +1185,7 @@ void tt_ctx_destroy(tt_ctx *ctx) {
         if (ctx->ev_start[q]) cudaEventDestroy(ctx->ev_start[q]);
         if (ctx->ev_stop[q]) cudaEventDestroy(ctx->ev_stop[q]);
         if (ctx->ev_net[q]) cudaEventDestroy(ctx->ev_net[q]);
+        if (ctx->ev_kacc[q]) cudaEventDestroy(ctx->ev_kacc[q]);
     }
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
     if (ctx->h_pts) cudaFreeHost(ctx->h_pts);
@@ -1591,6 +1613,38 @@ tt_status tt_mgrid_expand(tt_ctx *ctx, const tt_mgrid *mg, const double *d_G, do
     return TT_OK;
 }
 
+tt_status tt_kernel_normalize_rel(tt_ctx *ctx, double *d_Ks, double *d_Kxi, double *d_Keta,
+                                  const double *d_Kd, double eps_rel, double zeta) {
+    if (!ctx) return TT_EINVAL;
+    if (!d_Ks || !d_Kxi || !d_Keta || !d_Kd)
+        return fail(ctx, TT_EINVAL, "tt_kernel_normalize_rel: NULL argument");
+    if (!(eps_rel > 0) || !(zeta >= 0))
+        return fail(ctx, TT_EINVAL, "tt_kernel_normalize_rel: eps_rel must be > 0 and zeta >= 0");
+    constexpr int kParts = 304;
+    ENSURE(ctx->upd_part, sizeof(double) * (3 * kParts + 3));
+    CK(run_kernel_normalize_rel(ctx->g.N, d_Ks, d_Kxi, d_Keta, d_Kd, eps_rel, zeta,
+                                (double *)ctx->upd_part.p, kParts, ctx->st));
+    ctx->launches += 3;
+    return TT_OK;
+}
+
+tt_status tt_misfit_total(tt_ctx *ctx, int n_src, const double *d_chi, double alpha, double beta,
+                          const double *d_chi_cr, double gamma, double *h_total) {
+    if (!ctx) return TT_EINVAL;
+    if (!d_chi || !h_total || n_src < 1 || n_src > TT_MAX_BATCH)
+        return fail(ctx, TT_EINVAL, "tt_misfit_total: NULL argument or n_src outside 1..%d",
+                    TT_MAX_BATCH);
+    ENSURE(ctx->upd_part, sizeof(double) * (3 * 304 + 3));
+    double *d_out = (double *)ctx->upd_part.p;
+    CK(run_misfit_total(n_src, d_chi, alpha, beta, d_chi_cr, gamma, d_out, ctx->st));
+    ctx->launches += 1;
+    double *h = pinned_scalar(ctx);
+    CK(cudaMemcpyAsync(h, d_out, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    *h_total = *h;
+    return TT_OK;
+}
+
 tt_status tt_model_update(tt_ctx *ctx, const tt_model *model, const double *d_Ds,
                           const double *d_Dxi, const double *d_Deta, double step) {
     if (!ctx) return TT_EINVAL;
@@ -1615,8 +1669,26 @@ tt_status tt_model_update(tt_ctx *ctx, const tt_model *model, const double *d_Ds
 }
 
 tt_status tt_get_stats(const tt_ctx *ctx, int which, tt_stats *out) {
-    if (!ctx || !out || (which != TT_STATS_FORWARD && which != TT_STATS_ADJOINT))
+    if (!ctx || !out ||
+        (which != TT_STATS_FORWARD && which != TT_STATS_ADJOINT && which != TT_STATS_KERNEL))
         return TT_EINVAL;
+    if (which == TT_STATS_KERNEL) {
+        // the last kernel accumulation: waits for it, then reads its events
+        tt_stats S = {};
+        if (ctx->kacc_B > 0) {
+            float ms = 0.f;
+            if (cudaEventSynchronize(ctx->ev_kacc[1]) != cudaSuccess ||
+                cudaEventElapsedTime(&ms, ctx->ev_kacc[0], ctx->ev_kacc[1]) != cudaSuccess)
+                return TT_ECUDA;
+            S.sweep_ms = ms;
+            S.node_updates = ctx->g.N * (long long)ctx->kacc_B;
+            S.node_sweeps = ctx->g.N;
+            S.iters_max = 1;
+        }
+        *out = S;
+        out->launches = ctx->launches;
+        return TT_OK;
+    }
     *out = ctx->stats[which];
     out->launches = ctx->launches;
     return TT_OK;
@@ -1688,6 +1760,75 @@ extern "C" tt_status tt_autotune(tt_ctx *ctx, const tt_model *model, const tt_po
         }
     return model->dtype == TT_F32 ? autotune_impl<float>(ctx, model, h_src, n_src, opts, h_ms)
                                   : autotune_impl<double>(ctx, model, h_src, n_src, opts, h_ms);
+}
+
+// Adjoint launch configurations timed by tt_autotune_adjoint: (adj_chunk, adj_groups).
+constexpr int kAdjTuneCandidates = 6;
+constexpr int kAdjTuneChunk[kAdjTuneCandidates] = {0, 0, 0, 0, 128, 64};
+constexpr int kAdjTuneGroups[kAdjTuneCandidates] = {1, 2, 4, 8, 0, 1};
+
+namespace {
+
+template <typename F>
+tt_status autotune_adjoint_impl(tt_ctx *ctx, const tt_model *m, const tt_point *h_src, int B,
+                                const void *d_T, int n_rec, const tt_point *h_rec,
+                                const double *d_R, tt_opts *opts, double *h_ms) {
+    tt_status s;
+    ENSURE(ctx->tune_tau, sizeof(F) * (size_t)ctx->g.N * B);
+    double best = 1e300;
+    int best_c = 0;
+    std::vector<int> it(B);
+    for (int c = 0; c < kAdjTuneCandidates; ++c) {
+        tt_opts o = *opts;
+        o.adj_chunk = kAdjTuneChunk[c];
+        o.adj_groups = kAdjTuneGroups[c];
+        double ms = 0.0;
+        // a chunk no smaller than the batch repeats an all-sources candidate
+        const bool distinct = o.adj_chunk == 0 || o.adj_chunk < B;
+        if (distinct && (o.adj_groups == 0 || 32 * o.adj_groups <= B)) {
+            s = adjoint_impl<F>(ctx, m, h_src, B, d_T, n_rec, h_rec, d_R, ctx->tune_tau.p, &o,
+                                it.data());
+            if (s != TT_OK && s != TT_ENOTCONVERGED) return s;
+            ms = ctx->stats[TT_STATS_ADJOINT].sweep_ms;
+            if (ms < best) {
+                best = ms;
+                best_c = c;
+            }
+        }
+        if (h_ms) h_ms[c] = ms;
+    }
+    ctx->tuned_adj.push_back({B, m->dtype, kAdjTuneChunk[best_c], kAdjTuneGroups[best_c]});
+    opts->adj_chunk = kAdjTuneChunk[best_c];
+    opts->adj_groups = kAdjTuneGroups[best_c];
+    return TT_OK;
+}
+
+}  // namespace
+
+extern "C" tt_status tt_autotune_adjoint(tt_ctx *ctx, const tt_model *model,
+                                         const tt_point *h_src, int n_src, const void *d_T,
+                                         int n_rec, const tt_point *h_rec, const double *d_R,
+                                         tt_opts *opts, double *h_ms) {
+    if (!ctx) return TT_EINVAL;
+    tt_status s;
+    if ((s = check_model(ctx, model)) != TT_OK) return s;
+    if ((s = check_sources(ctx, h_src, n_src)) != TT_OK) return s;
+    if ((s = check_opts(ctx, opts)) != TT_OK) return s;
+    if (!d_T || !d_R || !h_rec || n_rec < 1)
+        return fail(ctx, TT_EINVAL, "tt_autotune_adjoint: NULL argument or no receivers");
+    for (const auto &t : ctx->tuned_adj)
+        if (t.n_src == n_src && t.dtype == model->dtype) {
+            opts->adj_chunk = t.chunk;
+            opts->adj_groups = t.groups;
+            if (h_ms)
+                for (int c = 0; c < kAdjTuneCandidates; ++c) h_ms[c] = 0.0;
+            return TT_OK;
+        }
+    return model->dtype == TT_F32
+               ? autotune_adjoint_impl<float>(ctx, model, h_src, n_src, d_T, n_rec, h_rec, d_R,
+                                              opts, h_ms)
+               : autotune_adjoint_impl<double>(ctx, model, h_src, n_src, d_T, n_rec, h_rec, d_R,
+                                               opts, h_ms);
 }
 
 // ---------------------------------------------------------------- warm-start network

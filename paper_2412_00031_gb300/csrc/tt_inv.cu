@@ -203,6 +203,40 @@ __global__ void absmax_final_kernel(int nb, const double *part, double *mx) {
     mx[threadIdx.x] = m;
 }
 
+// Eq. 18 with eps = eps_rel max(Kd) (Kd >= 0 is a sum of adjoint fields of unit sources): the
+// maximum comes from absmax_final_kernel's first slot; 1e-300 when it is 0.
+__global__ void normalize_rel_kernel(long long N, double *Ks, double *Kxi, double *Keta,
+                                     const double *Kd, const double *mx, double eps_rel,
+                                     double zeta) {
+    const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const double e = fmax(eps_rel * mx[0], 1e-300);
+    const double f = pow(Kd[n] + e, -zeta);
+    Ks[n] *= f;
+    Kxi[n] *= f;
+    Keta[n] *= f;
+}
+
+// Total misfit alpha sum chi[b][0] + beta sum chi[b][1] + gamma sum chi_cr[b] over n sources:
+// one block, each thread sums a fixed stride of sources in order, then a fixed tree.
+__global__ void misfit_total_kernel(int n, const double *chi, double alpha, double beta,
+                                    const double *chi_cr, double gamma, double *out) {
+    __shared__ double s[256];
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < n; b += blockDim.x) {
+        double v = alpha * chi[2 * (long long)b] + beta * chi[2 * (long long)b + 1];
+        if (chi_cr) v += gamma * chi_cr[b];
+        acc += v;
+    }
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = s[0];
+}
+
 // The update: s <- s (1 - a D_s / max|D_s|), xi <- xi - a D_xi / max|D_xi|, eta likewise
 // (a zero direction leaves its field unchanged).
 template <typename F>
@@ -289,6 +323,23 @@ cudaError_t run_model_update(long long N, F *s, F *xi, F *eta, const double *Ds,
     absmax_final_kernel<<<1, 32, 0, st>>>(n_part, part, part + 3 * n_part);
     update_kernel<F><<<nblocks(N, 256), 256, 0, st>>>(N, s, xi, eta, Ds, Dxi, Deta,
                                                       part + 3 * n_part, step);
+    return cudaGetLastError();
+}
+
+cudaError_t run_kernel_normalize_rel(long long N, double *Ks, double *Kxi, double *Keta,
+                                     const double *Kd, double eps_rel, double zeta, double *part,
+                                     int n_part, cudaStream_t st) {
+    // the partial maxima of Kd (the kernel takes three fields: Kd three times)
+    absmax_partial_kernel<<<n_part, 256, 0, st>>>(N, Kd, Kd, Kd, part);
+    absmax_final_kernel<<<1, 32, 0, st>>>(n_part, part, part + 3 * n_part);
+    normalize_rel_kernel<<<nblocks(N, 256), 256, 0, st>>>(N, Ks, Kxi, Keta, Kd,
+                                                          part + 3 * n_part, eps_rel, zeta);
+    return cudaGetLastError();
+}
+
+cudaError_t run_misfit_total(int n, const double *chi, double alpha, double beta,
+                             const double *chi_cr, double gamma, double *out, cudaStream_t st) {
+    misfit_total_kernel<<<1, 256, 0, st>>>(n, chi, alpha, beta, chi_cr, gamma, out);
     return cudaGetLastError();
 }
 

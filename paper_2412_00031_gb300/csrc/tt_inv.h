@@ -37,6 +37,15 @@ cudaError_t run_mgrid_project(const MgDims &d, const double *K, const double *h2
 // Eq. 15: D at the forward nodes from the coefficients G; lo = the three axes' lo tables.
 cudaError_t run_mgrid_expand(const MgDims &d, const double *G, const int *lo, const double *Wr,
                              const double *Wt, const double *Wp, double *D, cudaStream_t st);
+// Eq. 18 with eps = eps_rel max(Kd), the maximum taken on the device; part: scratch of
+// 3 n_part + 3 doubles.
+cudaError_t run_kernel_normalize_rel(long long N, double *Ks, double *Kxi, double *Keta,
+                                     const double *Kd, double eps_rel, double zeta, double *part,
+                                     int n_part, cudaStream_t st);
+// *out = alpha sum chi[b][0] + beta sum chi[b][1] + gamma sum chi_cr[b] (chi_cr may be NULL),
+// FP64 in a fixed order.
+cudaError_t run_misfit_total(int n, const double *chi, double alpha, double beta,
+                             const double *chi_cr, double gamma, double *out, cudaStream_t st);
 // The model update; part: scratch of 3 n_part + 3 doubles.
 template <typename F>
 cudaError_t run_model_update(long long N, F *s, F *xi, F *eta, const double *Ds,

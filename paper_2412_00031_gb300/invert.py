@@ -7,7 +7,8 @@ a host driver of the C ABI. Each evaluation of a model:
   into the kernel density (tt_kernel_density, Eq. 19).
 
 A descent direction is then formed:
-- normalise the kernels (tt_kernel_normalize, Eq. 18), with eps = eps_rel max K_d;
+- normalise the kernels (tt_kernel_normalize_rel, Eq. 18), with eps = eps_rel max K_d (the
+  maximum taken on the device);
 - project each onto the inversion grids and expand it back (tt_mgrid_project /
   tt_mgrid_expand, Eqs. 15 and 17).
 
@@ -23,15 +24,17 @@ reciprocity) and each batch's events take one gradient step (tt_field_at_points,
 tt_reloc_kernels, tt_reloc_update). A step that raises that batch's chi is undone and its
 step sizes halved.
 
-Every step of the arithmetic runs in the library's kernels. This module sequences the calls
-and holds the buffers; it reads back chi (n_src x 2) and the largest K_d to set eps.
+Every step of the arithmetic runs in the library's kernels, the step-control reductions
+included (tt_misfit_total: each batch's total misfit as an FP64 sum on the device; the largest
+K_d inside tt_kernel_normalize_rel). This module sequences the calls and holds the buffers;
+it reads back one total misfit per batch.
 """
 import numpy as np
 
 from . import (default_opts, mgrid, tt_adjoint, tt_field_at_points, tt_forward, tt_kernel,
-               tt_kernel_density, tt_kernel_normalize, tt_mgrid_expand, tt_mgrid_project,
-               tt_misfit, tt_misfit_cr, tt_misfit_table, tt_model_update, tt_reloc_kernels,
-               tt_reloc_update)
+               tt_kernel_density, tt_kernel_normalize_rel, tt_mgrid_expand, tt_mgrid_project,
+               tt_misfit, tt_misfit_cr, tt_misfit_table, tt_misfit_total, tt_model_update,
+               tt_reloc_kernels, tt_reloc_update)
 
 
 class _Batch:
@@ -110,6 +113,7 @@ class Inversion:
             self.Tr_all = torch.empty((n_all, n_rec), **f64)
             self.R_all = torch.empty((n_all, n_rec), **f64)
             self.chi_cr_all = torch.zeros(n_all, **f64)
+            self.chi_zero_all = torch.zeros((n_all, 2), **f64)   # no chi_t / chi_cs terms
         self.relocate = relocate is not None
         self.reloc_hist = []
         if self.relocate:
@@ -147,10 +151,9 @@ class Inversion:
             tt_kernel(c, m, T, P, *self.K)
             tt_adjoint(c, m, bt.src, T, bt.data.rec, bt.Rhat, Phat, self.opts)
             tt_kernel_density(c, Phat, self.Kd)
-            chi = bt.chi.cpu().numpy()
-            total += bt.data.alpha * chi[:, 0].sum() + bt.data.beta * chi[:, 1].sum()
-            if bt.cr is not None:
-                total += bt.cr.gamma * bt.chi_cr.cpu().numpy().sum()
+            total += tt_misfit_total(c, bt.chi, bt.data.alpha, bt.data.beta,
+                                     bt.chi_cr if bt.cr is not None else None,
+                                     bt.cr.gamma if bt.cr is not None else 0.0)
         return float(total)
 
     def _misfit(self, bt, T):
@@ -185,12 +188,12 @@ class Inversion:
             B = len(bt.src)
             bt.R.copy_(self.R_all[row:row + B])
             row += B
-        return self.cr_all.gamma * float(self.chi_cr_all.sum())
+        return tt_misfit_total(c, self.chi_zero_all, 0.0, 0.0, self.chi_cr_all,
+                               self.cr_all.gamma)
 
     def direction(self):
         """The smoothed, density-normalised descent direction from the last evaluation."""
-        eps = self.eps_rel * float(self.Kd.max())
-        tt_kernel_normalize(self.ctx, *self.K, self.Kd, max(eps, 1e-300), self.zeta)
+        tt_kernel_normalize_rel(self.ctx, *self.K, self.Kd, self.eps_rel, self.zeta)
         for K, D in zip(self.K, self.D):
             tt_mgrid_project(self.ctx, self.mg, K, self.G)
             tt_mgrid_expand(self.ctx, self.mg, self.G, D)
@@ -203,11 +206,9 @@ class Inversion:
         if bt.cr is not None:
             tt_misfit_cr(c, bt.cr, bt.Tra, bt.chi_cr_r, bt.R_r)
         tt_reloc_kernels(c, bt.R_r, bt.grad, bt.Kx, bt.Kt)
-        chi = bt.chi_r.cpu().numpy()
-        total = bt.data.alpha * chi[:, 0].sum() + bt.data.beta * chi[:, 1].sum()
-        if bt.cr is not None:
-            total += bt.cr.gamma * bt.chi_cr_r.cpu().numpy().sum()
-        return float(total)
+        return tt_misfit_total(c, bt.chi_r, bt.data.alpha, bt.data.beta,
+                               bt.chi_cr_r if bt.cr is not None else None,
+                               bt.cr.gamma if bt.cr is not None else 0.0)
 
     def relocate_events(self):
         """One relocation step of every batch's events in the current model."""

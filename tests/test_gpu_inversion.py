@@ -63,6 +63,42 @@ def test_normalisation_matches_oracle(tt):
     ctx.close()
 
 
+def test_relative_normalisation_takes_the_density_maximum_on_the_device(tt):
+    """Eq. 18 with eps = eps_rel max(Kd): the oracle's normalisation with eps computed from
+    the maximum of Kd (and the smallest positive eps when Kd is zero everywhere)."""
+    import oracle.inversion as V
+    w = I.small_case(83, shape=(9, 10, 11), n_src=1)
+    rng = np.random.default_rng(83)
+    ctx = tt.tt_ctx_create(w.grid.as_dict())
+    for Kd in (rng.uniform(0.0, 5.0, w.grid.shape), np.zeros(w.grid.shape)):
+        K = [rng.standard_normal(w.grid.shape) for _ in range(3)]
+        Kdev = [_dev(k) for k in K]
+        tt.tt_kernel_normalize_rel(ctx, *Kdev, _dev(Kd), 0.02, 0.7)
+        eps = max(0.02 * Kd.max(), 1e-300)
+        for a, k in zip(Kdev, K):
+            ref = V.normalize(k, Kd, eps, 0.7)
+            assert np.abs(a.cpu().numpy() - ref).max() <= 1e-13 * np.abs(ref).max()
+    ctx.close()
+
+
+@pytest.mark.parametrize("n_src", [1, 37, 300, 4096])
+def test_misfit_total_is_the_weighted_sum(tt, n_src):
+    """The step control's total misfit: alpha sum chi_t + beta sum chi_cs + gamma sum chi_cr
+    of a batch, an FP64 sum on the device, equals the exact sum (math.fsum) to 1e-14."""
+    import math
+    w = I.small_case(84, shape=(9, 10, 11), n_src=1)
+    rng = np.random.default_rng(84 + n_src)
+    chi = rng.uniform(0.0, 3.0, (n_src, 2))
+    cr = rng.uniform(0.0, 1.0, n_src)
+    ctx = tt.tt_ctx_create(w.grid.as_dict())
+    got = tt.tt_misfit_total(ctx, _dev(chi), 0.7, 1.3, _dev(cr), 0.4)
+    ref = math.fsum(list(0.7 * chi[:, 0]) + list(1.3 * chi[:, 1]) + list(0.4 * cr))
+    assert abs(got - ref) <= 1e-14 * ref
+    got2 = tt.tt_misfit_total(ctx, _dev(chi), 1.0, 1.0)
+    assert abs(got2 - math.fsum(chi.ravel())) <= 1e-14 * got2
+    ctx.close()
+
+
 @pytest.mark.parametrize("shape,coarse,H", [((9, 10, 11), (4, 5, 4), 3),
                                             ((17, 23, 19), (11, 11, 11), 5),
                                             ((13, 12, 33), (6, 3, 9), 2)])

@@ -242,6 +242,37 @@ def test_autotuner_picks_a_measured_candidate_with_identical_results(tt):
     ctx.close()
 
 
+def test_adjoint_autotuner_picks_a_measured_candidate_with_identical_results(tt):
+    """The adjoint tuner times whole adjoint solves in each launch configuration (source
+    chunks, barrier groups) and keeps the fastest; every configuration gives the default
+    solve's bits, and a second call reuses the cached choice."""
+    import torch
+    w = I.small_case(17, shape=(14, 17, 19), n_src=160, n_rec=7)
+    ctx = tt.tt_ctx_create(w.grid.as_dict())
+    model = tuple(to_dev(a, torch.float32) for a in (w.s, w.xi, w.eta))
+    ref = gpu_solve(w, "f32", ctx=ctx, steps=("fwd", "misfit", "adj"))
+    T = to_dev(ref["T"], torch.float32)
+    R = to_dev(ref["R"], torch.float64)
+    o = tt.default_opts(tt.TT_F32)
+    ms = tt.tt_autotune_adjoint(ctx, model, w.src, T, w.rec, R, o)
+    timed = {k: v for k, v in ms.items() if v > 0}
+    assert len(timed) == 6          # 160 sources: every candidate runs
+    best = min(timed, key=timed.get)
+    c = list(ms).index(best)
+    assert (o.adj_chunk, o.adj_groups) == ([0, 0, 0, 0, 128, 64][c], [1, 2, 4, 8, 0, 1][c])
+    o2 = tt.default_opts(tt.TT_F32)
+    assert all(v == 0 for v in tt.tt_autotune_adjoint(ctx, model, w.src, T, w.rec, R,
+                                                       o2).values())
+    assert (o2.adj_chunk, o2.adj_groups) == (o.adj_chunk, o.adj_groups)
+    for chunk, groups in ((0, 1), (0, 8), (64, 1), (128, 0), (96, 3)):
+        P = torch.empty_like(T)
+        it = tt.tt_adjoint(ctx, model, w.src, T, w.rec, R, P,
+                           tt.default_opts(tt.TT_F32, adj_chunk=chunk, adj_groups=groups))
+        assert np.array_equal(P.cpu().numpy(), ref["P"]), (chunk, groups)
+        assert np.array_equal(it, ref["iters_adj"])
+    ctx.close()
+
+
 @pytest.mark.parametrize("slots", [32, 64])
 def test_retire_and_refill_gives_the_resident_bits(tt, slots):
     """One launch with `slots` sources in flight, each converged source handing its slot to
