@@ -356,8 +356,11 @@ tt_status tt_tele_region_times(tt_ctx *ctx, int dtype, int n_r, int n_d, double 
  * d_T: device [N][n_ev] of the model's dtype; on entry its faces are the Dirichlet data and
  * its interior the start (tt_tele_region_times gives both); on return the solution. Each
  * event stops when an iteration's largest change is below opts->tol_fwd (at most
- * opts->max_iter_fwd iterations; TT_ENOTCONVERGED otherwise). h_iters: host [n_ev] (may be
- * NULL). Synchronises the stream every iteration. */
+ * opts->max_iter_fwd iterations; TT_ENOTCONVERGED otherwise). The update is computed in the
+ * fields' precision: in FP32, T of order 100 s is resolved to about 1e-5 s, so tol_fwd should
+ * not be set below that. All events run in one persistent launch (the sweep kernel of
+ * tt_forward) that tests convergence on the device. h_iters: host [n_ev] (may be NULL). Waits
+ * for the stream before returning. */
 tt_status tt_forward_tele(tt_ctx *ctx, const tt_model *model, int n_ev, void *d_T,
                           const tt_opts *opts, int *h_iters);
 

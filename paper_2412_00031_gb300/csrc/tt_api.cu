@@ -1468,6 +1468,135 @@ tt_status tt_tele_region_times(tt_ctx *ctx, int dtype, int n_r, int n_d, double 
     return TT_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// The region's solve of teleseismic events (R17): one persistent cooperative launch of the
+// node-hyperplane sweep with SCHEME 3 (Lax-Friedrichs on T itself, faces held fixed), the
+// events as the batch, each stopping on its own criterion inside the launch.
+template <typename F>
+tt_status forward_tele_impl(tt_ctx *ctx, const tt_model *m, int n_ev, void *d_T,
+                            const tt_opts *o, int *h_iters) {
+    const GridC &g = ctx->g;
+    ENSURE(ctx->rec, sizeof(NodeRec<F>) * (size_t)g.N);
+    ENSURE(ctx->partial, partial_bytes(ctx, n_ev, sizeof(F)));
+    ENSURE(ctx->conv, sizeof(int) * (size_t)n_ev);
+    ENSURE(ctx->iters, sizeof(int) * (size_t)n_ev);
+    ENSURE(ctx->nact, sizeof(int) * kMaxBarrierGroups);
+    ENSURE(ctx->bar, sizeof(BarrierState) * kMaxBarrierGroups);
+    ENSURE(ctx->flags, 4 * sizeof(int));
+    NodeRec<F> *rec = (NodeRec<F> *)ctx->rec.p;
+    int *conv = (int *)ctx->conv.p, *iters = (int *)ctx->iters.p, *flags = (int *)ctx->flags.p;
+    BarrierState *bar = (BarrierState *)ctx->bar.p;
+    CK(cudaMemsetAsync(conv, 0, sizeof(int) * (size_t)n_ev, ctx->st));
+    CK(cudaMemsetAsync(iters, 0, sizeof(int) * (size_t)n_ev, ctx->st));
+    CK(cudaMemsetAsync(ctx->nact.p, 0, sizeof(int) * kMaxBarrierGroups, ctx->st));
+    CK(cudaMemsetAsync(bar, 0, sizeof(BarrierState) * kMaxBarrierGroups, ctx->st));
+    CK(cudaMemsetAsync(flags, 0, 4 * sizeof(int), ctx->st));
+    CK(run_node_records<F>(g, m->d_s, m->d_xi, m->d_eta, ctx->gd.h2, ctx->gd.cost, rec, flags,
+                           ctx->st));
+    ENSURE(ctx->tele_aux, sizeof(F) * (size_t)n_ev);
+    CK(run_tele_shift<F>(g.N, n_ev, d_T, ctx->tele_aux.p, -1, ctx->st));
+    FwdArgs<F> a;
+    memset(&a, 0, sizeof a);
+    a.g = g;
+    a.B = n_ev;
+    a.scheme = 3;
+    a.n_planes = ctx->interior.n_planes;
+    a.er = (F)(0.5 / g.dr);
+    a.rec = rec;
+    a.tau = (F *)d_T;
+    a.nodes = ctx->interior.nodes;
+    a.off = ctx->interior.off;
+    a.bar = bar;
+    a.partial = (F *)ctx->partial.p;
+    a.conv = conv;
+    a.iters = iters;
+    a.n_active = (int *)ctx->nact.p;
+    a.tol = (F)o->tol_fwd;
+    a.max_iter = o->max_iter_fwd;
+    a.spin_ns = spin_ns(o);
+    a.src_lo = 0;
+    a.src_n = n_ev;
+    a.idx32 = (unsigned long long)g.N * (unsigned long long)(n_ev > 8 ? n_ev : 8) < (1ull << 32);
+    // 256-thread blocks, one barrier group per resident block slot of an SM (as the
+    // forward sweep), each group a multiple of one warp's sources
+    const int block = 256;
+    int per_sm = forward_blocks_per_sm<F>(block, fwd_smem_bytes<F>(n_ev, block), a.idx32 != 0, 3);
+    if (per_sm <= 0) return fail(ctx, TT_ECUDA, "teleseismic sweep cannot be resident");
+    if (per_sm > kMaxBarrierGroups) per_sm = kMaxBarrierGroups;
+    int max_grid = per_sm * ctx->n_sm;
+    if (o->launch_blocks > 0 && o->launch_blocks < max_grid) max_grid = o->launch_blocks;
+    const int wsrc = 32 * kFwdSourcesPerLane;
+    int groups = o->fwd_groups > 0 ? o->fwd_groups : per_sm;
+    if (groups > (n_ev + wsrc - 1) / wsrc) groups = (n_ev + wsrc - 1) / wsrc;
+    if (groups > max_grid) groups = max_grid;
+    int gsrc = ((n_ev + groups - 1) / groups + wsrc - 1) / wsrc * wsrc;
+    groups = (n_ev + gsrc - 1) / gsrc;
+    int gblocks = max_grid / groups;
+    if ((long long)gblocks * block < gsrc) {
+        const int need = (gsrc + block - 1) / block;
+        if ((long long)need * groups > (long long)per_sm * ctx->n_sm)
+            return fail(ctx, TT_EINVAL, "%d events exceed one resident launch", n_ev);
+        gblocks = need;
+    }
+    a.n_bgroups = groups;
+    a.grp_blocks = gblocks;
+    a.grp_src = gsrc;
+    CK(record(ctx, ctx->ev_start[TT_STATS_FORWARD]));
+    CK(launch_forward<F>(a, gblocks * groups, block, ctx->st));
+    CK(record(ctx, ctx->ev_stop[TT_STATS_FORWARD]));
+    CK(run_tele_shift<F>(g.N, n_ev, d_T, ctx->tele_aux.p, 1, ctx->st));
+    ctx->launches += 5;
+    Readback r = readback_view(ctx);
+    CK(cudaMemcpyAsync(r.iters_f, iters, sizeof(int) * (size_t)n_ev, cudaMemcpyDeviceToHost,
+                       ctx->st));
+    CK(cudaMemcpyAsync(r.conv_f, conv, sizeof(int) * (size_t)n_ev, cudaMemcpyDeviceToHost,
+                       ctx->st));
+    CK(cudaMemcpyAsync(r.flags, flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaMemcpyAsync(r.bar_f, bar, sizeof(BarrierState) * kMaxBarrierGroups,
+                       cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    if (r.flags[0] & 1)
+        return fail(ctx, TT_EINVAL, "tt_forward_tele: model has s <= 0 or xi^2 + eta^2 >= 1/4");
+    for (int q = 0; q < kMaxBarrierGroups; ++q) {
+        int st;
+        memcpy(&st, r.bar_f + q * sizeof(BarrierState) + offsetof(BarrierState, status),
+               sizeof st);
+        if (st == kDevTimeout)
+            return fail(ctx, TT_ETIMEOUT, "tt_forward_tele: a device-side wait exceeded its limit");
+    }
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, ctx->ev_start[TT_STATS_FORWARD], ctx->ev_stop[TT_STATS_FORWARD]));
+    tt_stats &S = ctx->stats[TT_STATS_FORWARD];
+    S = tt_stats{};
+    S.sweep_ms = ms;
+    long long upd = 0;
+    int imax = 0, left = 0;
+    const long long inner = (long long)(g.nr - 2) * (g.nt - 2) * (g.np - 2);
+    for (int e = 0; e < n_ev; ++e) {
+        upd += 8LL * r.iters_f[e] * inner;
+        imax = r.iters_f[e] > imax ? r.iters_f[e] : imax;
+        left += r.conv_f[e] == 0;
+        if (h_iters) h_iters[e] = r.iters_f[e];
+    }
+    S.node_updates = upd;
+    S.node_sweeps = 8LL * imax * inner;
+    S.iters_max = imax;
+    S.grid_blocks = gblocks * groups;
+    S.block_threads = block;
+    if (left)
+        return fail(ctx, TT_ENOTCONVERGED,
+                    "tt_forward_tele: %d of %d events did not converge in %d iterations", left,
+                    n_ev, o->max_iter_fwd);
+    return TT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 tt_status tt_forward_tele(tt_ctx *ctx, const tt_model *model, int n_ev, void *d_T,
                           const tt_opts *opts, int *h_iters) {
     if (!ctx) return TT_EINVAL;
@@ -1477,52 +1606,8 @@ tt_status tt_forward_tele(tt_ctx *ctx, const tt_model *model, int n_ev, void *d_
     if (!d_T) return fail(ctx, TT_EINVAL, "tt_forward_tele: NULL field");
     if (n_ev < 1 || n_ev > TT_MAX_BATCH)
         return fail(ctx, TT_EINVAL, "n_ev = %d outside 1..%d", n_ev, TT_MAX_BATCH);
-    const Schedule &S = ctx->interior;
-    std::vector<int> off(S.n_planes + 1);
-    CK(cudaMemcpy(off.data(), S.off, sizeof(int) * off.size(), cudaMemcpyDeviceToHost));
-    ENSURE(ctx->tele_aux, (sizeof(unsigned long long) + sizeof(int)) * (size_t)n_ev);
-    unsigned long long *d_err = (unsigned long long *)ctx->tele_aux.p;
-    int *d_done = (int *)(d_err + n_ev);
-    CK(cudaMemsetAsync(d_done, 0, sizeof(int) * n_ev, ctx->st));
-    std::vector<unsigned long long> err(n_ev);
-    std::vector<int> done(n_ev, 0), iters(n_ev, 0);
-    const bool f32 = model->dtype == TT_F32;
-    int left = n_ev;
-    for (int it = 0; it < opts->max_iter_fwd && left > 0; ++it) {
-        CK(cudaMemsetAsync(d_err, 0, sizeof(unsigned long long) * n_ev, ctx->st));
-        for (int o = 0; o < 8; ++o)
-            for (int L = 0; L < S.n_planes; ++L) {
-                const int cnt = off[L + 1] - off[L];
-                if (cnt == 0) continue;
-                CK(f32 ? run_tele3d_plane<float>(ctx->g, model->d_s, model->d_xi, model->d_eta, S.nodes,
-                                                 off[L], cnt, o, n_ev, d_done, d_T, d_err, ctx->st)
-                       : run_tele3d_plane<double>(ctx->g, model->d_s, model->d_xi, model->d_eta,
-                                                  S.nodes, off[L], cnt, o, n_ev, d_done, d_T,
-                                                  d_err, ctx->st));
-                ctx->launches += 1;
-            }
-        CK(cudaMemcpyAsync(err.data(), d_err, sizeof(unsigned long long) * n_ev,
-                           cudaMemcpyDeviceToHost, ctx->st));
-        CK(cudaStreamSynchronize(ctx->st));
-        for (int e = 0; e < n_ev; ++e) {
-            if (done[e]) continue;
-            iters[e] = it + 1;
-            double ch;
-            memcpy(&ch, &err[e], sizeof ch);
-            if (ch < opts->tol_fwd) {
-                done[e] = 1;
-                --left;
-            }
-        }
-        CK(cudaMemcpyAsync(d_done, done.data(), sizeof(int) * n_ev, cudaMemcpyHostToDevice, ctx->st));
-    }
-    CK(cudaStreamSynchronize(ctx->st));
-    if (h_iters)
-        for (int e = 0; e < n_ev; ++e) h_iters[e] = iters[e];
-    if (left)
-        return fail(ctx, TT_ENOTCONVERGED, "tt_forward_tele: %d of %d events did not converge in %d iterations",
-                    left, n_ev, opts->max_iter_fwd);
-    return TT_OK;
+    return model->dtype == TT_F32 ? forward_tele_impl<float>(ctx, model, n_ev, d_T, opts, h_iters)
+                                  : forward_tele_impl<double>(ctx, model, n_ev, d_T, opts, h_iters);
 }
 
 tt_status tt_kernel_normalize(tt_ctx *ctx, double *d_Ks, double *d_Kxi, double *d_Keta,

@@ -162,6 +162,14 @@ __device__ __forceinline__ F factor_T0(const SrcReg<F> &S, int i, F r, F cth, F 
 //   tau_new = [s / T0 - H / T0 + sum_d c_d (tau_d+ + tau_d-)] / (2 sum_d c_d)
 // with c_d = kappa_d e_d, kappa = (1, sqrt(1 - 2 xi), sqrt(1 + 2 xi)): the Cauchy-Schwarz
 // bounds of |dH/dp_d| that make the scheme monotone (the Lax-Friedrichs viscosity).
+// It is evaluated as an increment of the centre value,
+//   tau_new = tau_c + [s / T0 - H / T0 + sum_d c_d ((tau_d+ - tau_c) + (tau_d- - tau_c))]
+//                     / (2 sum_d c_d),
+// the same value in exact arithmetic. In the direct form the numerator is dominated by the
+// neighbour sum (order 2 sum c_d) while the equation's own terms s / T0 - H / T0 are ~100x
+// smaller at the benchmark's spacings, so FP32 rounding of that sum acts as a slowness error
+// of ~1e-5 and moves the fixed point by ~1.5e-5 of T; the differences to the centre are exact
+// (Sterbenz) and small, and the fixed point then sits at FP32's rounding floor.
 // trp/trm etc. are tau at the + and - neighbours along r, theta, phi in physical order;
 // (invT0, ur, ut, up) are 1/T0 and u, as returned by factor_T0.
 template <typename F>
@@ -175,9 +183,11 @@ __device__ __forceinline__ F lf_core(F invT0, F ur, F ut, F up, F tc, F trp, F t
     const F q = fma_(vr, vr, fma_(mul_(kt, vt), vt,
                                   fma_(mul_(kp, vp), vp, mul_(mul_((F)4 * R.eta, vt), vp))));
     const F H = sqrt_(q);
-    const F num = fma_(er, add_(trp, trm),
-                       fma_(R.ct, add_(ttp, ttm), fma_(R.cp, add_(tpp, tpm), fma_(R.s, invT0, -H))));
-    return mul_(num, R.invW);
+    const F sr = add_(sub_(trp, tc), sub_(trm, tc));
+    const F st = add_(sub_(ttp, tc), sub_(ttm, tc));
+    const F sp = add_(sub_(tpp, tc), sub_(tpm, tc));
+    const F num = fma_(er, sr, fma_(R.ct, st, fma_(R.cp, sp, fma_(R.s, invT0, -H))));
+    return fma_(num, R.invW, tc);
 }
 
 // Godunov update of tau at an interior node (isotropic models, xi = eta = 0; an alternative to

@@ -240,6 +240,38 @@ template <typename F> __device__ __forceinline__ NodeRec<F> rec_from_lanes(F v) 
     return R;
 }
 
+// Prefetch of the next node's lines while the current node is computed (the loads then hit
+// a cache instead of HBM). TTGB_FWD_PF: 0 off; 1 into L2; 2 into L1; + 4: also the first node
+// of the next hyperplane into L2 before the grid barrier (its factor, its own tau and the
+// downstream neighbours do not change during the current hyperplane; a prefetch never
+// changes results, only where a line is cached).
+#ifndef TTGB_FWD_PF
+#define TTGB_FWD_PF 0
+#endif
+template <int LEVEL> __device__ __forceinline__ void prefetch_line(const void *p) {
+    if (LEVEL == 1) asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+    else asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+// One warp prefetches every line that the update of node n reads for its 64 sources
+// (32 x NS; NS = 2): lanes 0-13 the seven tau rows (2 lines of 128 B each), lanes 14-21 the
+// factor cache's 1 KB. p0: tau of the warp's first source at node n; c0: its factor.
+template <int LEVEL, typename F, typename I>
+__device__ __forceinline__ void prefetch_node(const F *p0, const Vec4<F> *c0, I sr, I st, I sp,
+                                              int lane) {
+    if (sizeof(F) != 4) return;
+    if (c0 == nullptr && lane >= 14) return;  // no factor cache
+    if (lane < 14) {
+        const int r = lane >> 1;
+        // signed element offsets (I may be unsigned)
+        const long long d = r == 0 ? 0 : (r == 1 || r == 2) ? (long long)sr
+                          : (r == 3 || r == 4) ? (long long)st : (long long)sp;
+        prefetch_line<LEVEL>(p0 + ((r & 1) || r == 0 ? d : -d) + 32 * (lane & 1));
+    } else if (lane < 22) {
+        prefetch_line<LEVEL>(reinterpret_cast<const char *>(c0) + 128 * (lane - 14));
+    }
+}
+
 __device__ __forceinline__ Vec4<float> ld_stream(const Vec4<float> *p) {
     const float4 v = __ldcs(reinterpret_cast<const float4 *>(p));
     return Vec4<float>{v.x, v.y, v.z, v.w};
@@ -267,9 +299,13 @@ __device__ __forceinline__ F update_one(F *p, const F *v, const Vec4<F> &c, cons
 // I: index type of the [node][source] fields (32-bit when every index fits).
 // REFILL: the retire-and-refill mode (compiled separately, so that the resident launch
 // carries none of its code). SCHEME: the local solver, 0 Lax-Friedrichs (lf_core), 1 Godunov
-// (godunov_core, isotropic models), 2 Godunov for anisotropic models (godunov_aniso_core).
+// (godunov_core, isotropic models), 2 Godunov for anisotropic models (godunov_aniso_core),
+// 3 Lax-Friedrichs on T itself with the faces held fixed (the region's solve of teleseismic
+// events: lf_core with T0 = 1 and no factor gradient, no factor cache read, no fixed set,
+// no face extrapolation; the "sources" are the events).
 template <typename F, typename I, bool REFILL, int SCHEME>
-__global__ void __launch_bounds__(256, SCHEME == 0 ? TTGB_FWD_MIN_BLOCKS : TTGB_GOD_MIN_BLOCKS)
+__global__ void __launch_bounds__(256, (SCHEME == 0 || SCHEME == 3) ? TTGB_FWD_MIN_BLOCKS
+                                                                    : TTGB_GOD_MIN_BLOCKS)
     fwd_sweep_kernel(FwdArgs<F> a) {
     constexpr int NS = kFwdSourcesPerLane;              // sources of one lane: l0 + 32 h
     extern __shared__ unsigned char smem_raw[];
@@ -303,6 +339,13 @@ __global__ void __launch_bounds__(256, SCHEME == 0 ? TTGB_FWD_MIN_BLOCKS : TTGB_
     const Vec4<F> *t0c = a.t0c + (b - a.src_lo);
     const I src_n = (I)a.src_n;
     F *tau = a.tau;
+#if TTGB_FWD_PF != 0
+    // the warp's first source (uniform over the warp; its 64-source rows stay inside the
+    // arrays for every swept node, which is never the last node of the grid)
+    const int wsrc0 = src0 + (bl >> 5) * (32 * NS);
+    const F *tau_w = a.tau + wsrc0;
+    const Vec4<F> *t0c_w = a.t0c + (wsrc0 - a.src_lo);
+#endif
 
     // retire-and-refill: load the group's first sources into their slots
     if (REFILL) {
@@ -342,6 +385,14 @@ __global__ void __launch_bounds__(256, SCHEME == 0 ? TTGB_FWD_MIN_BLOCKS : TTGB_
                         const int qn = q + slots;
                         const unsigned pkn = qn < qe ? __ldg(a.nodes + qn) : 0u;
                         const I n = n0 + node_local(pk, sa, sb, sc);
+#if (TTGB_FWD_PF & 3) != 0
+                        if (NS == 2 && qn < qe) {
+                            const I nn = n0 + node_local(pkn, sa, sb, sc);
+                            prefetch_node<(TTGB_FWD_PF & 3) == 2 ? 1 : 2, F, I>(
+                                tau_w + nn * (I)B, SCHEME == 3 ? nullptr : t0c_w + nn * src_n,
+                                sr, st, sp, lane);
+                        }
+#endif
                         F *p = tau + (n * (I)B + (I)b);
                         const Vec4<F> *pc = t0c + n * src_n;
                         F v[NS][7], rv = 0;
@@ -357,7 +408,8 @@ __global__ void __launch_bounds__(256, SCHEME == 0 ? TTGB_FWD_MIN_BLOCKS : TTGB_
                             v[h][4] = *(ph - st);
                             v[h][5] = ph[sp];
                             v[h][6] = *(ph - sp);
-                            c[h] = ld_stream(pc + 32 * h);
+                            c[h] = SCHEME == 3 ? Vec4<F>{(F)1, (F)0, (F)0, (F)0}
+                                               : ld_stream(pc + 32 * h);
                         }
                         if (lane < 8) rv = __ldg(recf + n * (I)8 + (I)lane);
                         const NodeRec<F> R = rec_from_lanes<F>(rv);  // uniform loop: whole warp
@@ -370,15 +422,26 @@ __global__ void __launch_bounds__(256, SCHEME == 0 ? TTGB_FWD_MIN_BLOCKS : TTGB_
                 }
                 // first node of the next plane (static: needs no barrier)
                 const int qa_next = qe + slot;
-                if (busy && !last && qa_next < qe_next) pk = __ldg(a.nodes + qa_next);
+                if (busy && !last && qa_next < qe_next) {
+                    pk = __ldg(a.nodes + qa_next);
+#if (TTGB_FWD_PF & 4) != 0
+                    if (NS == 2) {
+                        const I nn = n0 + node_local(pk, sa, sb, sc);
+                        prefetch_node<2, F, I>(tau_w + nn * (I)B,
+                                               SCHEME == 3 ? nullptr : t0c_w + nn * src_n, sr,
+                                               st, sp, lane);
+                    }
+#endif
+                }
                 if (!grid_barrier(bar, a.spin_ns, nblk)) return;
                 qa = qa_next;
                 qe = qe_next;
             }
-            for (int axis = 0; axis < 3; ++axis) {
-                if (any) extrapolate_lane<F, NS>(a, b, act, axis, slot, slots);
-                if (!grid_barrier(bar, a.spin_ns, nblk)) return;
-            }
+            if (SCHEME != 3)  // SCHEME 3 holds the faces fixed
+                for (int axis = 0; axis < 3; ++axis) {
+                    if (any) extrapolate_lane<F, NS>(a, b, act, axis, slot, slots);
+                    if (!grid_barrier(bar, a.spin_ns, nblk)) return;
+                }
         }
         // Per-source largest update of this iteration: block maximum, then a fixed-order
         // maximum over the group's blocks by its first block, which also decides convergence.
@@ -1164,6 +1227,9 @@ __global__ void __launch_bounds__(256, TTGB_ADJ_MIN_BLOCKS) adj_face_kernel(AdjA
 
 // The node-hyperplane sweep kernel of one variant.
 template <typename F> void *fwd_kernel_ptr(bool refill, bool idx32, int scheme) {
+    if (scheme == 3)  // no refill mode
+        return idx32 ? (void *)fwd_sweep_kernel<F, unsigned, false, 3>
+                     : (void *)fwd_sweep_kernel<F, long long, false, 3>;
     if (scheme == 2)
         return refill ? (idx32 ? (void *)fwd_sweep_kernel<F, unsigned, true, 2>
                                : (void *)fwd_sweep_kernel<F, long long, true, 2>)

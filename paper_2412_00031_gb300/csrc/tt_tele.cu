@@ -215,64 +215,35 @@ __global__ void region_times_kernel(GridC g, int n_r, int n_d, double r_min, dou
                (1 - u) * v * (double)Te[c + 1] + u * v * (double)Te[c + n_d + 1]);
 }
 
-// One hyperplane of one ordering of the region's solve (R4's Lax-Friedrichs update of T
-// itself, no factor; the faces are never written): threads over (node of the plane, event),
-// events fastest. A done event (its last iteration changed no node by tol) is skipped.
-// err_bits[e] takes the largest change of event e (non-negative doubles order as their
-// bit patterns).
+// The region's solve of an event only sees differences of T (the Lax-Friedrichs update is
+// unchanged when a constant is added to T), so it runs on T - c_e with c_e = T at node 0 (a
+// corner: face data, held fixed). Teleseismic times of a few hundred seconds then become
+// values within the region's spread of times, whose FP32 resolution is several times finer.
 template <typename F>
-__global__ void tele3d_plane_kernel(GridC g, const F *s, const F *xi, const F *eta,
-                                    const unsigned *nodes, int p0, int cnt, int o, int n_ev,
-                                    const int *done, F *T, unsigned long long *err_bits) {
+__global__ void tele_shift_save_kernel(int n_ev, const F *T, F *c) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n_ev) c[e] = T[e];
+}
+template <typename F>
+__global__ void tele_shift_kernel(long long N, int n_ev, F *T, const F *c, int sign) {
     const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= (long long)cnt * n_ev) return;
+    if (q >= N * n_ev) return;
     const int e = (int)(q % n_ev);
-    if (done[e]) return;
-    const unsigned code = nodes[p0 + (int)(q / n_ev)];
-    const int a = (int)(code >> 20), b = (int)((code >> 10) & 1023u), c = (int)(code & 1023u);
-    const int i = (o & 4) ? g.nr - 2 - a : 1 + a;
-    const int j = (o & 2) ? g.nt - 2 - b : 1 + b;
-    const int k = (o & 1) ? g.np - 2 - c : 1 + c;
-    const long long n = node_index(g, i, j, k);
-    const long long si = (long long)g.nt * g.np, sj = g.np;
-    const double tp[3] = {(double)T[(n + si) * n_ev + e], (double)T[(n + sj) * n_ev + e],
-                          (double)T[(n + 1) * n_ev + e]};
-    const double tm[3] = {(double)T[(n - si) * n_ev + e], (double)T[(n - sj) * n_ev + e],
-                          (double)T[(n - 1) * n_ev + e]};
-    const double r = g.r0 + i * g.dr, th = g.t0 + j * g.dt;
-    const double h[3] = {1.0, g.flat ? g.re : r, g.flat ? g.re : r * cos(th)};
-    const double del[3] = {g.dr, g.dt, g.dp};
-    const double x = (double)xi[n], et = (double)eta[n];
-    double p[3];
-    for (int d = 0; d < 3; ++d) p[d] = (tp[d] - tm[d]) / (2.0 * del[d]) / h[d];
-    const double qf = p[0] * p[0] + (1.0 - 2.0 * x) * p[1] * p[1] + (1.0 + 2.0 * x) * p[2] * p[2] +
-                      4.0 * et * p[1] * p[2];
-    const double sig[3] = {1.0, sqrt(1.0 - 2.0 * x) / h[1], sqrt(1.0 + 2.0 * x) / h[2]};
-    double num = (double)s[n] - sqrt(qf), den = 0.0;
-    for (int d = 0; d < 3; ++d) {
-        num += sig[d] * (tp[d] + tm[d]) / (2.0 * del[d]);
-        den += sig[d] / del[d];
-    }
-    const F v = (F)(num / den);
-    const F old = T[n * n_ev + e];
-    const double ch = fabs((double)v - (double)old);
-    atomicMax(err_bits + e, (unsigned long long)__double_as_longlong(ch));
-    T[n * n_ev + e] = v;
+    T[q] = sign < 0 ? T[q] - c[e] : T[q] + c[e];
 }
 
 }  // namespace
 
 template <typename F>
-cudaError_t run_tele3d_plane(const GridC &g, const void *s, const void *xi, const void *eta,
-                             const unsigned *nodes, int p0, int cnt, int o, int n_ev,
-                             const int *done, void *T, unsigned long long *err_bits,
-                             cudaStream_t st) {
-    const long long total = (long long)cnt * n_ev;
-    const unsigned blocks = (unsigned)((total + 255) / 256);
-    tele3d_plane_kernel<F><<<blocks, 256, 0, st>>>(g, (const F *)s, (const F *)xi, (const F *)eta,
-                                                   nodes, p0, cnt, o, n_ev, done, (F *)T, err_bits);
+cudaError_t run_tele_shift(long long N, int n_ev, void *T, void *c, int sign, cudaStream_t st) {
+    if (sign < 0) tele_shift_save_kernel<F><<<(n_ev + 255) / 256, 256, 0, st>>>(n_ev, (const F *)T, (F *)c);
+    const long long total = N * n_ev;
+    tele_shift_kernel<F><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(N, n_ev, (F *)T, (const F *)c,
+                                                                         sign);
     return cudaGetLastError();
 }
+template cudaError_t run_tele_shift<float>(long long, int, void *, void *, int, cudaStream_t);
+template cudaError_t run_tele_shift<double>(long long, int, void *, void *, int, cudaStream_t);
 
 template <typename F>
 cudaError_t run_tele2d(int n_r, int n_d, double r_min, double dr, double dd, const void *s_r,
@@ -301,14 +272,6 @@ template cudaError_t run_tele2d<float>(int, int, double, double, double, const v
 template cudaError_t run_tele2d<double>(int, int, double, double, double, const void *,
                                         const double *, int, double, int, void *, void *, int *,
                                         cudaStream_t);
-template cudaError_t run_tele3d_plane<float>(const GridC &, const void *, const void *,
-                                             const void *, const unsigned *, int, int, int, int,
-                                             const int *, void *, unsigned long long *,
-                                             cudaStream_t);
-template cudaError_t run_tele3d_plane<double>(const GridC &, const void *, const void *,
-                                              const void *, const unsigned *, int, int, int, int,
-                                              const int *, void *, unsigned long long *,
-                                              cudaStream_t);
 template cudaError_t run_region_times<float>(const GridC &, int, int, double, double, double,
                                              const void *, int, const double *, void *,
                                              cudaStream_t);

@@ -20,13 +20,10 @@ cudaError_t run_region_times(const GridC &g, int n_r, int n_d, double r_min, dou
                              double dd, const void *T2, int n_ev, const double *ev_ll, void *T,
                              cudaStream_t st);
 
-// One hyperplane (ordering o; nodes[p0 .. p0 + cnt) of the interior schedule) of the region's
-// Lax-Friedrichs solve of T with fixed faces: T [N][n_ev]; err_bits [n_ev] the largest change
-// of each event (as double bits); events with done[e] are skipped.
+// The region's solve itself is the node-hyperplane sweep (tt_sweep.cu) with SCHEME 3, on
+// T - c_e: sign < 0 saves c_e = T[node 0][e] into c [n_ev] and subtracts it from every node of
+// event e; sign > 0 adds it back.
 template <typename F>
-cudaError_t run_tele3d_plane(const GridC &g, const void *s, const void *xi, const void *eta,
-                             const unsigned *nodes, int p0, int cnt, int o, int n_ev,
-                             const int *done, void *T, unsigned long long *err_bits,
-                             cudaStream_t st);
+cudaError_t run_tele_shift(long long N, int n_ev, void *T, void *c, int sign, cudaStream_t st);
 
 }  // namespace ttgb

@@ -114,7 +114,9 @@ def test_region_solve_matches_the_oracle_chain(tt):
         tt.tt_tele_region_times(ctx, T2, r_min, RE, dmax, events, T)
         model = tuple(torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
                       for a in (w.s, w.xi, w.eta))
-        o = tt.default_opts(code, tol_fwd=1e-11 if code == tt.TT_F64 else 1e-6,
+        # FP32 resolves T of order 100 s to ~1e-5 s (one unit in the last place): its
+        # convergence tolerance is a few of those
+        o = tt.default_opts(code, tol_fwd=1e-11 if code == tt.TT_F64 else 3e-5,
                             max_iter_fwd=500)
         it = tt.tt_forward_tele(ctx, model, T, o)
         Tg = T.double().cpu().numpy()
