@@ -240,42 +240,53 @@ template <typename F> __device__ __forceinline__ NodeRec<F> rec_from_lanes(F v) 
     return R;
 }
 
-// Prefetch of the next node's lines while the current node is computed (the loads then hit
-// a cache instead of HBM). TTGB_FWD_PF: 0 off; 1 into L2; 2 into L1; + 4: also the first node
-// of the next hyperplane into L2 before the grid barrier (its factor, its own tau and the
-// downstream neighbours do not change during the current hyperplane; a prefetch never
-// changes results, only where a line is cached).
-#ifndef TTGB_FWD_PF
-#define TTGB_FWD_PF 0
+// L2 eviction policy of the forward sweep's loads (TTGB_FWD_LDPOL): 0 the factor stream with
+// ld.global.cs; 1 the factor with an evict-first L2 policy and no L1 allocation; 2 as 1, and
+// the tau loads and stores with an evict-last policy (tau lines are read on three
+// consecutive hyperplanes, the factor's once per sweep).
+#ifndef TTGB_FWD_LDPOL
+#define TTGB_FWD_LDPOL 0
 #endif
-template <int LEVEL> __device__ __forceinline__ void prefetch_line(const void *p) {
-    if (LEVEL == 1) asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
-    else asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+__device__ __forceinline__ unsigned long long policy_evict_first() {
+    unsigned long long p;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
 }
-
-// One warp prefetches every line that the update of node n reads for its 64 sources
-// (32 x NS; NS = 2): lanes 0-13 the seven tau rows (2 lines of 128 B each), lanes 14-21 the
-// factor cache's 1 KB. p0: tau of the warp's first source at node n; c0: its factor.
-template <int LEVEL, typename F, typename I>
-__device__ __forceinline__ void prefetch_node(const F *p0, const Vec4<F> *c0, I sr, I st, I sp,
-                                              int lane) {
-    if (sizeof(F) != 4) return;
-    if (c0 == nullptr && lane >= 14) return;  // no factor cache
-    if (lane < 14) {
-        const int r = lane >> 1;
-        // signed element offsets (I may be unsigned)
-        const long long d = r == 0 ? 0 : (r == 1 || r == 2) ? (long long)sr
-                          : (r == 3 || r == 4) ? (long long)st : (long long)sp;
-        prefetch_line<LEVEL>(p0 + ((r & 1) || r == 0 ? d : -d) + 32 * (lane & 1));
-    } else if (lane < 22) {
-        prefetch_line<LEVEL>(reinterpret_cast<const char *>(c0) + 128 * (lane - 14));
-    }
+__device__ __forceinline__ unsigned long long policy_evict_last() {
+    unsigned long long p;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
 }
-
 __device__ __forceinline__ Vec4<float> ld_stream(const Vec4<float> *p) {
+#if TTGB_FWD_LDPOL >= 1
+    Vec4<float> v;
+    asm volatile("ld.global.L1::no_allocate.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(p), "l"(policy_evict_first()));
+    return v;
+#else
     const float4 v = __ldcs(reinterpret_cast<const float4 *>(p));
     return Vec4<float>{v.x, v.y, v.z, v.w};
+#endif
 }
+__device__ __forceinline__ float ld_tau(const float *p) {
+#if TTGB_FWD_LDPOL >= 2
+    float v;
+    asm volatile("ld.global.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(policy_evict_last()));
+    return v;
+#else
+    return *p;
+#endif
+}
+__device__ __forceinline__ double ld_tau(const double *p) { return *p; }
+__device__ __forceinline__ void st_tau(float *p, float v) {
+#if TTGB_FWD_LDPOL >= 2
+    asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(v), "l"(policy_evict_last()) : "memory");
+#else
+    *p = v;
+#endif
+}
+__device__ __forceinline__ void st_tau(double *p, double v) { *p = v; }
 __device__ __forceinline__ Vec4<double> ld_stream(const Vec4<double> *p) {
     const double2 v0 = __ldcs(reinterpret_cast<const double2 *>(p));
     const double2 v1 = __ldcs(reinterpret_cast<const double2 *>(p) + 1);
@@ -292,7 +303,7 @@ __device__ __forceinline__ F update_one(F *p, const F *v, const Vec4<F> &c, cons
         SCHEME == 2   ? godunov_aniso_core<F>(c.x, c.y, c.z, c.w, v[0], v[1], v[2], v[3], v[4], v[5], v[6], R, er)
         : SCHEME == 1 ? godunov_core<F>(c.x, c.y, c.z, c.w, v[0], v[1], v[2], v[3], v[4], v[5], v[6], R, er)
                       : lf_core<F>(c.x, c.y, c.z, c.w, v[0], v[1], v[2], v[3], v[4], v[5], v[6], R, er);
-    *p = tn;
+    st_tau(p, tn);
     return fabs(tn - v[0]);
 }
 
@@ -339,13 +350,6 @@ __global__ void __launch_bounds__(256, (SCHEME == 0 || SCHEME == 3) ? TTGB_FWD_M
     const Vec4<F> *t0c = a.t0c + (b - a.src_lo);
     const I src_n = (I)a.src_n;
     F *tau = a.tau;
-#if TTGB_FWD_PF != 0
-    // the warp's first source (uniform over the warp; its 64-source rows stay inside the
-    // arrays for every swept node, which is never the last node of the grid)
-    const int wsrc0 = src0 + (bl >> 5) * (32 * NS);
-    const F *tau_w = a.tau + wsrc0;
-    const Vec4<F> *t0c_w = a.t0c + (wsrc0 - a.src_lo);
-#endif
 
     // retire-and-refill: load the group's first sources into their slots
     if (REFILL) {
@@ -385,14 +389,6 @@ __global__ void __launch_bounds__(256, (SCHEME == 0 || SCHEME == 3) ? TTGB_FWD_M
                         const int qn = q + slots;
                         const unsigned pkn = qn < qe ? __ldg(a.nodes + qn) : 0u;
                         const I n = n0 + node_local(pk, sa, sb, sc);
-#if (TTGB_FWD_PF & 3) != 0
-                        if (NS == 2 && qn < qe) {
-                            const I nn = n0 + node_local(pkn, sa, sb, sc);
-                            prefetch_node<(TTGB_FWD_PF & 3) == 2 ? 1 : 2, F, I>(
-                                tau_w + nn * (I)B, SCHEME == 3 ? nullptr : t0c_w + nn * src_n,
-                                sr, st, sp, lane);
-                        }
-#endif
                         F *p = tau + (n * (I)B + (I)b);
                         const Vec4<F> *pc = t0c + n * src_n;
                         F v[NS][7], rv = 0;
@@ -401,13 +397,13 @@ __global__ void __launch_bounds__(256, (SCHEME == 0 || SCHEME == 3) ? TTGB_FWD_M
                         for (int h = 0; h < NS; ++h) {
                             if (!act[h]) continue;
                             const F *ph = p + 32 * h;
-                            v[h][0] = ph[0];
-                            v[h][1] = ph[sr];
-                            v[h][2] = *(ph - sr);
-                            v[h][3] = ph[st];
-                            v[h][4] = *(ph - st);
-                            v[h][5] = ph[sp];
-                            v[h][6] = *(ph - sp);
+                            v[h][0] = ld_tau(ph);
+                            v[h][1] = ld_tau(ph + sr);
+                            v[h][2] = ld_tau(ph - sr);
+                            v[h][3] = ld_tau(ph + st);
+                            v[h][4] = ld_tau(ph - st);
+                            v[h][5] = ld_tau(ph + sp);
+                            v[h][6] = ld_tau(ph - sp);
                             c[h] = SCHEME == 3 ? Vec4<F>{(F)1, (F)0, (F)0, (F)0}
                                                : ld_stream(pc + 32 * h);
                         }
@@ -422,17 +418,7 @@ __global__ void __launch_bounds__(256, (SCHEME == 0 || SCHEME == 3) ? TTGB_FWD_M
                 }
                 // first node of the next plane (static: needs no barrier)
                 const int qa_next = qe + slot;
-                if (busy && !last && qa_next < qe_next) {
-                    pk = __ldg(a.nodes + qa_next);
-#if (TTGB_FWD_PF & 4) != 0
-                    if (NS == 2) {
-                        const I nn = n0 + node_local(pk, sa, sb, sc);
-                        prefetch_node<2, F, I>(tau_w + nn * (I)B,
-                                               SCHEME == 3 ? nullptr : t0c_w + nn * src_n, sr,
-                                               st, sp, lane);
-                    }
-#endif
-                }
+                if (busy && !last && qa_next < qe_next) pk = __ldg(a.nodes + qa_next);
                 if (!grid_barrier(bar, a.spin_ns, nblk)) return;
                 qa = qa_next;
                 qe = qe_next;

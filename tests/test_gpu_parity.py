@@ -247,7 +247,7 @@ def test_adjoint_autotuner_picks_a_measured_candidate_with_identical_results(tt)
     chunks, barrier groups) and keeps the fastest; every configuration gives the default
     solve's bits, and a second call reuses the cached choice."""
     import torch
-    w = I.small_case(17, shape=(14, 17, 19), n_src=160, n_rec=7)
+    w = I.small_case(17, shape=(14, 17, 19), n_src=256, n_rec=7)
     ctx = tt.tt_ctx_create(w.grid.as_dict())
     model = tuple(to_dev(a, torch.float32) for a in (w.s, w.xi, w.eta))
     ref = gpu_solve(w, "f32", ctx=ctx, steps=("fwd", "misfit", "adj"))
@@ -256,7 +256,7 @@ def test_adjoint_autotuner_picks_a_measured_candidate_with_identical_results(tt)
     o = tt.default_opts(tt.TT_F32)
     ms = tt.tt_autotune_adjoint(ctx, model, w.src, T, w.rec, R, o)
     timed = {k: v for k, v in ms.items() if v > 0}
-    assert len(timed) == 6          # 160 sources: every candidate runs
+    assert len(timed) == 6          # 256 sources: every candidate runs (8 groups of 32)
     best = min(timed, key=timed.get)
     c = list(ms).index(best)
     assert (o.adj_chunk, o.adj_groups) == ([0, 0, 0, 0, 128, 64][c], [1, 2, 4, 8, 0, 1][c])
