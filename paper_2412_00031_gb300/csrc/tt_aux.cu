@@ -329,6 +329,27 @@ __global__ void misfit_kernel(int B, int n_rec, const F *T, const long long *cq,
     }
 }
 
+// Compensated accumulator of a lane's terms: (hi, lo) with hi + lo the sum to about twice
+// the working precision (Knuth's TwoSum: hi + lo = old hi + term exactly, each step). In
+// FP32 it keeps ~48 significant bits without the FP64 pipe, whose rate on this GPU is a
+// small fraction of the FP32 rate; in FP64 it is plain double accumulation plus a
+// correction word.
+template <typename F> struct CompSum {
+    F hi = 0, lo = 0;
+    __device__ __forceinline__ void add(F x) {
+        const F s = __fadd_rn_t(hi, x);
+        const F bp = __fsub_rn_t(s, hi);
+        const F err = __fadd_rn_t(__fsub_rn_t(hi, __fsub_rn_t(s, bp)), __fsub_rn_t(x, bp));
+        hi = s;
+        lo = __fadd_rn_t(lo, err);
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+    static __device__ __forceinline__ float __fadd_rn_t(float a, float b) { return __fadd_rn(a, b); }
+    static __device__ __forceinline__ float __fsub_rn_t(float a, float b) { return __fsub_rn(a, b); }
+    static __device__ __forceinline__ double __fadd_rn_t(double a, double b) { return __dadd_rn(a, b); }
+    static __device__ __forceinline__ double __fsub_rn_t(double a, double b) { return __dsub_rn(a, b); }
+};
+
 // Kernels of Eqs. 6-8, one warp per node; lanes stride over the sources and the warp sum
 // runs in a fixed shuffle order.
 template <typename F>
@@ -339,7 +360,9 @@ __global__ void kernel_accum_kernel(GridC g, int B, const F *s, const F *T, cons
     const int lane = threadIdx.x & 31;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     // Each source's term in the fields' precision F (its inputs are F values; reciprocals
-    // instead of divisions), the sum over sources in FP64 in a fixed order.
+    // instead of divisions). A lane sums its sources' terms with a compensated accumulator
+    // in F (TwoSum); the lanes' sums, the batch's total and the kernels themselves are FP64,
+    // combined in a fixed order.
     const F idt = (F)(1.0 / g.dt), idp = (F)(1.0 / g.dp);
     for (long long n = warp; n < g.N; n += nwarps) {
         int k = (int)(n % g.np);
@@ -352,17 +375,19 @@ __global__ void kernel_accum_kernel(GridC g, int B, const F *s, const F *T, cons
         const long long st = (long long)g.np * B, sp = B;
         const long long ot_hi = j < g.nt - 1 ? st : 0, ot_lo = j > 0 ? st : 0;
         const long long op_hi = k < g.np - 1 ? sp : 0, op_lo = k > 0 ? sp : 0;
-        double aP = 0, aX = 0, aE = 0;
+        CompSum<F> sP, sX, sE;
+#pragma unroll 4
         for (int b = lane; b < B; b += 32) {
             const long long x = n * B + b;
             // central differences inside, one-sided on the faces (R10)
             const F gt = (T[x + ot_hi] - T[x - ot_lo]) * ct;
             const F gp = (T[x + op_hi] - T[x - op_lo]) * cp;
             const F p = P[x];
-            aP += (double)p;
-            aX += (double)(p * (gt * gt - gp * gp));
-            aE += (double)((F)-2 * p * gt * gp);
+            sP.add(p);
+            sX.add(p * (gt * gt - gp * gp));
+            sE.add((F)-2 * p * gt * gp);
         }
+        double aP = sP.value(), aX = sX.value(), aE = sE.value();
         for (int o = 16; o > 0; o >>= 1) {
             aP += __shfl_xor_sync(0xffffffffu, aP, o);
             aX += __shfl_xor_sync(0xffffffffu, aX, o);

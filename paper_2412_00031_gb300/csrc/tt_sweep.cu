@@ -240,53 +240,10 @@ template <typename F> __device__ __forceinline__ NodeRec<F> rec_from_lanes(F v) 
     return R;
 }
 
-// L2 eviction policy of the forward sweep's loads (TTGB_FWD_LDPOL): 0 the factor stream with
-// ld.global.cs; 1 the factor with an evict-first L2 policy and no L1 allocation; 2 as 1, and
-// the tau loads and stores with an evict-last policy (tau lines are read on three
-// consecutive hyperplanes, the factor's once per sweep).
-#ifndef TTGB_FWD_LDPOL
-#define TTGB_FWD_LDPOL 0
-#endif
-__device__ __forceinline__ unsigned long long policy_evict_first() {
-    unsigned long long p;
-    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-    return p;
-}
-__device__ __forceinline__ unsigned long long policy_evict_last() {
-    unsigned long long p;
-    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
-    return p;
-}
 __device__ __forceinline__ Vec4<float> ld_stream(const Vec4<float> *p) {
-#if TTGB_FWD_LDPOL >= 1
-    Vec4<float> v;
-    asm volatile("ld.global.L1::no_allocate.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
-                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-                 : "l"(p), "l"(policy_evict_first()));
-    return v;
-#else
     const float4 v = __ldcs(reinterpret_cast<const float4 *>(p));
     return Vec4<float>{v.x, v.y, v.z, v.w};
-#endif
 }
-__device__ __forceinline__ float ld_tau(const float *p) {
-#if TTGB_FWD_LDPOL >= 2
-    float v;
-    asm volatile("ld.global.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(policy_evict_last()));
-    return v;
-#else
-    return *p;
-#endif
-}
-__device__ __forceinline__ double ld_tau(const double *p) { return *p; }
-__device__ __forceinline__ void st_tau(float *p, float v) {
-#if TTGB_FWD_LDPOL >= 2
-    asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(v), "l"(policy_evict_last()) : "memory");
-#else
-    *p = v;
-#endif
-}
-__device__ __forceinline__ void st_tau(double *p, double v) { *p = v; }
 __device__ __forceinline__ Vec4<double> ld_stream(const Vec4<double> *p) {
     const double2 v0 = __ldcs(reinterpret_cast<const double2 *>(p));
     const double2 v1 = __ldcs(reinterpret_cast<const double2 *>(p) + 1);
@@ -303,7 +260,7 @@ __device__ __forceinline__ F update_one(F *p, const F *v, const Vec4<F> &c, cons
         SCHEME == 2   ? godunov_aniso_core<F>(c.x, c.y, c.z, c.w, v[0], v[1], v[2], v[3], v[4], v[5], v[6], R, er)
         : SCHEME == 1 ? godunov_core<F>(c.x, c.y, c.z, c.w, v[0], v[1], v[2], v[3], v[4], v[5], v[6], R, er)
                       : lf_core<F>(c.x, c.y, c.z, c.w, v[0], v[1], v[2], v[3], v[4], v[5], v[6], R, er);
-    st_tau(p, tn);
+    *p = tn;
     return fabs(tn - v[0]);
 }
 
@@ -397,13 +354,13 @@ __global__ void __launch_bounds__(256, (SCHEME == 0 || SCHEME == 3) ? TTGB_FWD_M
                         for (int h = 0; h < NS; ++h) {
                             if (!act[h]) continue;
                             const F *ph = p + 32 * h;
-                            v[h][0] = ld_tau(ph);
-                            v[h][1] = ld_tau(ph + sr);
-                            v[h][2] = ld_tau(ph - sr);
-                            v[h][3] = ld_tau(ph + st);
-                            v[h][4] = ld_tau(ph - st);
-                            v[h][5] = ld_tau(ph + sp);
-                            v[h][6] = ld_tau(ph - sp);
+                            v[h][0] = ph[0];
+                            v[h][1] = ph[sr];
+                            v[h][2] = *(ph - sr);
+                            v[h][3] = ph[st];
+                            v[h][4] = *(ph - st);
+                            v[h][5] = ph[sp];
+                            v[h][6] = *(ph - sp);
                             c[h] = SCHEME == 3 ? Vec4<F>{(F)1, (F)0, (F)0, (F)0}
                                                : ld_stream(pc + 32 * h);
                         }
