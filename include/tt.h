@@ -480,6 +480,19 @@ tt_status tt_plan_create(tt_plan **out, tt_ctx *ctx, const tt_model *model,
                          const tt_point *h_src, int n_src, const tt_data *data,
                          const tt_opts *opts, void *d_tau, void *d_T, void *d_P, double *d_chi,
                          double *d_R, double *d_Ks, double *d_Kxi, double *d_Keta);
+/* tt_plan_create with the common-receiver differential times of the batch in the step
+ * (Eq. 4 and its adjoint source, Eq. A4; tt_cr_data as for tt_misfit_cr, its n_src and
+ * n_rec those of the batch): after the misfit the graph writes the receiver-time table to
+ * d_Tr (device double [n_src][n_rec]), adds gamma dchi_cr/dT into d_R and writes each
+ * source's share of chi_cr to d_chi_cr (device double [n_src]), then runs the adjoint. Every
+ * entry's other source is checked once at creation (TT_EINVAL if outside the batch);
+ * entries must not change between runs. Pairs across batches need the joined tables and stay
+ * with tt_misfit_cr. */
+tt_status tt_plan_create_cr(tt_plan **out, tt_ctx *ctx, const tt_model *model,
+                            const tt_point *h_src, int n_src, const tt_data *data,
+                            const tt_cr_data *cr, const tt_opts *opts, void *d_tau, void *d_T,
+                            void *d_P, double *d_chi, double *d_Tr, double *d_chi_cr,
+                            double *d_R, double *d_Ks, double *d_Kxi, double *d_Keta);
 /* Replays the step and waits for it; h_iters_fwd / h_iters_adj (host [n_src], may be NULL)
  * receive the iteration counts. Statuses as tt_forward and tt_adjoint. */
 tt_status tt_plan_run(tt_plan *plan, int *h_iters_fwd, int *h_iters_adj);

@@ -90,7 +90,7 @@ EXPORTED = ["tt_default_opts", "tt_ctx_create", "tt_ctx_destroy", "tt_last_error
             "tt_model_update", "tt_misfit_cr", "tt_field_at_points", "tt_misfit_table",
             "tt_reloc_kernels", "tt_reloc_update", "tt_tele2d", "tt_tele_region_times",
             "tt_forward_tele", "tt_autotune_adjoint", "tt_kernel_normalize_rel",
-            "tt_misfit_total"]
+            "tt_misfit_total", "tt_plan_create_cr"]
 TT_NOALLOC_MAX_REC = 1024
 
 
@@ -121,6 +121,9 @@ def _load():
     L.tt_plan_create.argtypes = [C.POINTER(C.c_void_p), C.c_void_p, C.POINTER(TTModel),
                                  C.POINTER(TTPoint), C.c_int, C.POINTER(TTData),
                                  C.POINTER(TTOpts)] + [C.c_void_p] * 8
+    L.tt_plan_create_cr.argtypes = [C.POINTER(C.c_void_p), C.c_void_p, C.POINTER(TTModel),
+                                    C.POINTER(TTPoint), C.c_int, C.POINTER(TTData),
+                                    C.POINTER(TTCrData), C.POINTER(TTOpts)] + [C.c_void_p] * 10
     L.tt_plan_run.argtypes = [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]
     L.tt_plan_destroy.argtypes = [C.c_void_p]
     L.tt_plan_destroy.restype = None
@@ -169,7 +172,7 @@ def _load():
                  "tt_mgrid_expand", "tt_model_update", "tt_misfit_cr", "tt_field_at_points",
                  "tt_misfit_table", "tt_reloc_kernels", "tt_reloc_update", "tt_tele2d",
                  "tt_tele_region_times", "tt_forward_tele", "tt_autotune_adjoint",
-                 "tt_kernel_normalize_rel", "tt_misfit_total"):
+                 "tt_kernel_normalize_rel", "tt_misfit_total", "tt_plan_create_cr"):
         getattr(L, name).restype = C.c_int
     return L
 
@@ -657,23 +660,40 @@ class Plan:
             pass
 
 
-def tt_plan_create(ctx, model, src, data, tau, T, P, chi, R, Ks, Kxi, Keta, opts=None):
+def tt_plan_create(ctx, model, src, data, tau, T, P, chi, R, Ks, Kxi, Keta, opts=None,
+                   cr=None, Tr=None, chi_cr=None):
+    """A captured step (see tt.h). With cr (the batch's CrData), Tr [n_src, n_rec] and
+    chi_cr [n_src] (float64 CUDA tensors) the step includes the common-receiver terms
+    (tt_plan_create_cr)."""
     pts, n = _points(src)
     N = _nodes(ctx)
     ft, f64 = _model_room(ctx, model), _f64()
     _room(tau=(tau, N * n, ft), T=(T, N * n, ft), P=(P, N * n, ft), chi=(chi, 2 * n, f64),
           R=(R, n * data.n_rec, f64), Ks=(Ks, N, f64), Kxi=(Kxi, N, f64), Keta=(Keta, N, f64))
+    if cr is not None:
+        if Tr is None or chi_cr is None:
+            raise ValueError("cr needs the Tr and chi_cr buffers")
+        _room(Tr=(Tr, n * data.n_rec, f64), chi_cr=(chi_cr, n, f64))
     M = _model(model)
-    _cuda_ok(tau, T, P, chi, R, Ks, Kxi, Keta)
+    _cuda_ok(tau, T, P, chi, R, Ks, Kxi, Keta, Tr, chi_cr)
     if opts is None:
         opts = default_opts(M.dtype)
     D = data.c_struct()
     h = C.c_void_p()
-    st = lib.tt_plan_create(C.byref(h), ctx.handle, C.byref(M), pts, n, C.byref(D),
-                            C.byref(opts), _ptr(tau), _ptr(T), _ptr(P), _ptr(chi), _ptr(R),
-                            _ptr(Ks), _ptr(Kxi), _ptr(Keta))
+    if cr is None:
+        st = lib.tt_plan_create(C.byref(h), ctx.handle, C.byref(M), pts, n, C.byref(D),
+                                C.byref(opts), _ptr(tau), _ptr(T), _ptr(P), _ptr(chi), _ptr(R),
+                                _ptr(Ks), _ptr(Kxi), _ptr(Keta))
+        crs = None
+    else:
+        crs = cr.c_struct()
+        st = lib.tt_plan_create_cr(C.byref(h), ctx.handle, C.byref(M), pts, n, C.byref(D),
+                                   C.byref(crs), C.byref(opts), _ptr(tau), _ptr(T), _ptr(P),
+                                   _ptr(chi), _ptr(Tr), _ptr(chi_cr), _ptr(R), _ptr(Ks),
+                                   _ptr(Kxi), _ptr(Keta))
     _check(ctx, st)
-    return Plan(ctx, h, n, (model, data, tau, T, P, chi, R, Ks, Kxi, Keta, pts, D, opts))
+    return Plan(ctx, h, n, (model, data, tau, T, P, chi, R, Ks, Kxi, Keta, pts, D, opts, cr,
+                            crs, Tr, chi_cr))
 
 
 def tt_plan_run(plan, allow_unconverged=False):

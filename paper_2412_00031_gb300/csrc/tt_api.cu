@@ -2085,6 +2085,12 @@ struct tt_plan {
     int B = 0, n_rec = 0;
     void *tau = nullptr, *T = nullptr, *P = nullptr;
     double *chi = nullptr, *R = nullptr, *K[3] = {nullptr, nullptr, nullptr};
+    // common-receiver terms (Eq. 4, A4) inside the graph: their data, the receiver-time table
+    // they read and the sources' shares of chi_cr (has_cr = 0: none)
+    int has_cr = 0;
+    tt_cr_data cr;
+    double *Tr = nullptr, *chi_cr = nullptr;
+    int *cr_bad = nullptr;
     std::vector<void *> allocs;
     std::vector<PointD> h_src;
     Work<float> wf;
@@ -2143,6 +2149,11 @@ template <typename F> tt_status plan_alloc(tt_plan *p, Work<F> &W) {
     TTGB_GET(heads, sizeof(int) * S);
     TTGB_GET(nheads, sizeof(int));
     TTGB_GET(JS, sizeof(F) * (size_t)S * B);
+    if (p->has_cr) {
+        void *q_;
+        if ((s = get(sizeof(int), &q_)) != TT_OK) return s;
+        p->cr_bad = (int *)q_;
+    }
     const int n_slots = refill_slots_for(&p->opts, B, W.t0c_slice);
     if (n_slots > 0) {
         TTGB_GET(tau_w, sizeof(F) * (size_t)g.N * n_slots);
@@ -2175,9 +2186,14 @@ template <typename F> tt_status plan_enqueue(tt_plan *p, Work<F> &W) {
     if ((s = enq_readback(ctx, p->B, W.iters_f, W.conv_f, W.flags, W.bar, TT_STATS_FORWARD)) !=
         TT_OK)
         return s;
-    if ((s = enq_misfit(ctx, p->T, p->model.dtype, &p->data, W.cq, W.wq, W.flags, nullptr, p->chi,
+    if ((s = enq_misfit(ctx, p->T, p->model.dtype, &p->data, W.cq, W.wq, W.flags, p->Tr, p->chi,
                         p->R)) != TT_OK)
         return s;
+    if (p->has_cr) {  // Eq. 4 terms and their adjoint source (A4), added into R
+        CK(run_misfit_cr(p->cr.n_src, p->cr.n_rec, p->cr.d_off, p->cr.d_other, p->cr.d_dtobs,
+                         p->cr.d_w, p->cr.gamma, p->Tr, p->chi_cr, p->R, p->cr_bad, ctx->st));
+        ctx->launches += 1;
+    }
     if ((s = enq_adjoint<F>(ctx, W, &p->model, p->B, p->T, p->n_rec, p->R, p->P, &p->opts)) !=
         TT_OK)
         return s;
@@ -2228,10 +2244,25 @@ template <typename F> tt_status plan_build(tt_plan *p, Work<F> &W, const tt_poin
 
 extern "C" {
 
+tt_status tt_plan_create_cr(tt_plan **out, tt_ctx *ctx, const tt_model *model,
+                            const tt_point *h_src, int n_src, const tt_data *data,
+                            const tt_cr_data *cr, const tt_opts *opts, void *d_tau, void *d_T,
+                            void *d_P, double *d_chi, double *d_Tr, double *d_chi_cr,
+                            double *d_R, double *d_Ks, double *d_Kxi, double *d_Keta);
+
 tt_status tt_plan_create(tt_plan **out, tt_ctx *ctx, const tt_model *model,
                          const tt_point *h_src, int n_src, const tt_data *data,
                          const tt_opts *opts, void *d_tau, void *d_T, void *d_P, double *d_chi,
                          double *d_R, double *d_Ks, double *d_Kxi, double *d_Keta) {
+    return tt_plan_create_cr(out, ctx, model, h_src, n_src, data, nullptr, opts, d_tau, d_T,
+                             d_P, d_chi, nullptr, nullptr, d_R, d_Ks, d_Kxi, d_Keta);
+}
+
+tt_status tt_plan_create_cr(tt_plan **out, tt_ctx *ctx, const tt_model *model,
+                            const tt_point *h_src, int n_src, const tt_data *data,
+                            const tt_cr_data *cr, const tt_opts *opts, void *d_tau, void *d_T,
+                            void *d_P, double *d_chi, double *d_Tr, double *d_chi_cr,
+                            double *d_R, double *d_Ks, double *d_Kxi, double *d_Keta) {
     if (!out || !ctx) return TT_EINVAL;
     *out = nullptr;
     tt_status s;
@@ -2243,7 +2274,33 @@ tt_status tt_plan_create(tt_plan **out, tt_ctx *ctx, const tt_model *model,
                                           data->n_src, n_src);
     if (!d_tau || !d_T || !d_P || !d_R || !d_Ks || !d_Kxi || !d_Keta)
         return fail(ctx, TT_EINVAL, "tt_plan_create: NULL buffer");
+    if (cr) {
+        if (!d_Tr || !d_chi_cr || !cr->d_off)
+            return fail(ctx, TT_EINVAL, "tt_plan_create_cr: NULL argument");
+        if (cr->n_src != n_src || cr->n_rec != data->n_rec)
+            return fail(ctx, TT_EINVAL, "tt_plan_create_cr: cr data for %d sources and %d "
+                        "receivers, the batch has %d and %d", cr->n_src, cr->n_rec, n_src,
+                        data->n_rec);
+        if (cr->n_entries > 0) {
+            if (!cr->d_other || !cr->d_dtobs || !cr->d_w)
+                return fail(ctx, TT_EINVAL, "tt_plan_create_cr: NULL entry arrays");
+            // every entry must name a source of the batch: checked once, on the host
+            std::vector<int> other(cr->n_entries);
+            CK(cudaMemcpy(other.data(), cr->d_other, sizeof(int) * other.size(),
+                          cudaMemcpyDeviceToHost));
+            for (int q : other)
+                if (q < 0 || q >= n_src)
+                    return fail(ctx, TT_EINVAL, "tt_plan_create_cr: an entry names source %d "
+                                "outside the batch", q);
+        }
+    }
     tt_plan *p = new tt_plan();
+    if (cr) {
+        p->has_cr = 1;
+        p->cr = *cr;
+        p->Tr = d_Tr;
+        p->chi_cr = d_chi_cr;
+    }
     p->ctx = ctx;
     p->model = *model;
     p->data = *data;

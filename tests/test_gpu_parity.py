@@ -319,3 +319,53 @@ def test_retire_and_refill_gives_the_resident_bits(tt, slots):
     assert np.array_equal(P.cpu().numpy(), full["P"])
     plan.close()
     ctx.close()
+
+
+def test_plan_with_common_receiver_terms_equals_the_calls(tt):
+    """A plan that includes the common-receiver terms (Eq. 4, A4) gives the bits of the
+    individual calls: forward, misfit (receiver times), tt_misfit_cr, adjoint, kernels; and a
+    plan whose entries name a source outside the batch is refused at creation."""
+    import torch
+    w = I.small_case(18, shape=(13, 14, 16), n_src=37, n_rec=9)
+    rng = np.random.default_rng(18)
+    pairs = [(b, j, m, rng.normal(0, 0.3), rng.uniform(0.5, 2.0))
+             for m in range(9) for b in range(37) for j in range(b + 1, 37)
+             if rng.uniform() < 0.1]
+    ctx = tt.tt_ctx_create(w.grid.as_dict())
+    model = tuple(to_dev(a, torch.float32) for a in (w.s, w.xi, w.eta))
+    shape = w.grid.shape + (w.n_src,)
+    data = tt.DeviceData.from_workload(w)
+    cr = tt.CrData(w.n_src, data.n_rec, pairs, gamma=0.8)
+    f64 = dict(dtype=torch.float64, device="cuda")
+    # the calls
+    tau, T, P = (torch.empty(shape, device="cuda") for _ in range(3))
+    Tr, chi, R = (torch.empty((w.n_src, data.n_rec), **f64), torch.empty((w.n_src, 2), **f64),
+                  torch.empty((w.n_src, data.n_rec), **f64))
+    chi_cr = torch.empty(w.n_src, **f64)
+    itf = tt.tt_forward(ctx, model, w.src, tau, T)
+    tt.tt_misfit(ctx, T, data, Tr, chi, R)
+    tt.tt_misfit_cr(ctx, cr, Tr, chi_cr, R)
+    ita = tt.tt_adjoint(ctx, model, w.src, T, w.rec, R, P)
+    K = [torch.zeros(w.grid.shape, **f64) for _ in range(3)]
+    tt.tt_kernel(ctx, model, T, P, *K)
+    ref = [x.cpu().numpy() for x in (tau, P, Tr, chi, R, chi_cr, *K)]
+    # the plan
+    tau2, T2, P2 = (torch.empty(shape, device="cuda") for _ in range(3))
+    Tr2, chi2, R2 = (torch.empty_like(Tr), torch.empty_like(chi), torch.empty_like(R))
+    chi_cr2 = torch.empty_like(chi_cr)
+    K2 = [torch.empty(w.grid.shape, **f64) for _ in range(3)]
+    plan = tt.tt_plan_create(ctx, model, w.src, data, tau2, T2, P2, chi2, R2, *K2, cr=cr,
+                             Tr=Tr2, chi_cr=chi_cr2)
+    for _ in range(2):
+        itf2, ita2 = tt.tt_plan_run(plan)
+        assert np.array_equal(itf2, itf) and np.array_equal(ita2, ita)
+        got = [x.cpu().numpy() for x in (tau2, P2, Tr2, chi2, R2, chi_cr2, *K2)]
+        for a, b in zip(got, ref):
+            assert np.array_equal(a, b)
+    assert np.abs(ref[5]).max() > 0
+    plan.close()
+    cr.other[0] = w.n_src + 2
+    with pytest.raises(tt.TTError, match="outside the batch"):
+        tt.tt_plan_create(ctx, model, w.src, data, tau2, T2, P2, chi2, R2, *K2, cr=cr,
+                          Tr=Tr2, chi_cr=chi_cr2)
+    ctx.close()
