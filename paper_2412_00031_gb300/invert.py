@@ -124,6 +124,25 @@ class Inversion:
             self.rec = rec
             self.tauG = torch.empty(self.shape + (len(rec),), dtype=F, device=dev)
             self.Gam = torch.empty_like(self.tauG)
+            if cr_all is not None:
+                # common-receiver pairs across batches in the relocation too: the events'
+                # positions, origin times, arrival tables, adjoint sources and kernels of all
+                # batches in joined arrays, each batch's buffers views of its rows
+                def joined(name):
+                    return torch.cat([getattr(b, name) for b in self.batches]).contiguous()
+                self.pts_all, self.otime_all = joined("pts"), joined("otime")
+                self.Tra_all, self.Rr_all = joined("Tra"), joined("R_r")
+                self.Kx_all, self.Kt_all = joined("Kx"), joined("Kt")
+                self.chi_cr_r_all = torch.zeros(n_all, **f64)
+                self.rstep = [float(relocate[0]), float(relocate[1])]
+                views = {"pts": self.pts_all, "otime": self.otime_all, "Tra": self.Tra_all,
+                         "R_r": self.Rr_all, "Kx": self.Kx_all, "Kt": self.Kt_all}
+                row = 0
+                for bt in self.batches:
+                    B = len(bt.src)
+                    for name, buf in views.items():
+                        setattr(bt, name, buf[row:row + B])
+                    row += B
 
     def _fields(self, B):
         """tau, T, P, P_hat views for a batch of B sources (node-major, source fastest)."""
@@ -210,9 +229,42 @@ class Inversion:
                                bt.chi_cr_r if bt.cr is not None else None,
                                bt.cr.gamma if bt.cr is not None else 0.0)
 
+    def _reloc_chi_all(self):
+        """chi of all events when common-receiver pairs span batches: each batch's arrivals
+        and misfit, then Eqs. 4 and A4 on the joined arrival table (adding into the joined
+        adjoint sources), then each batch's K_x, K_tau. Returns the total chi."""
+        c = self.ctx
+        total = 0.0
+        for bt in self.batches:
+            tt_field_at_points(c, self.Gam, bt.pts, bt.val, bt.grad)
+            tt_misfit_table(c, bt.val, bt.otime, bt.data, bt.Tra, bt.chi_r, bt.R_r)
+            total += tt_misfit_total(c, bt.chi_r, bt.data.alpha, bt.data.beta)
+        tt_misfit_cr(c, self.cr_all, self.Tra_all, self.chi_cr_r_all, self.Rr_all)
+        total += tt_misfit_total(c, self.chi_zero_all, 0.0, 0.0, self.chi_cr_r_all,
+                                 self.cr_all.gamma)
+        for bt in self.batches:
+            tt_reloc_kernels(c, bt.R_r, bt.grad, bt.Kx, bt.Kt)
+        return total
+
     def relocate_events(self):
-        """One relocation step of every batch's events in the current model."""
+        """One relocation step of every batch's events in the current model. With pairs
+        across batches (cr_all) all events take one joint step, normalised over all of them,
+        and the step control acts on the total chi."""
         tt_forward(self.ctx, self.model, self.rec, self.tauG, self.Gam, self.opts)
+        if self.cr_all is not None:
+            before = self._reloc_chi_all()
+            saved = (self.pts_all.clone(), self.otime_all.clone())
+            tt_reloc_update(self.ctx, self.pts_all, self.otime_all, self.Kx_all, self.Kt_all,
+                            *self.rstep)
+            after = self._reloc_chi_all()
+            if after >= before:
+                self.pts_all.copy_(saved[0])
+                self.otime_all.copy_(saved[1])
+                self.rstep = [s * 0.5 for s in self.rstep]
+            self.reloc_hist.append((before, after, after < before))
+            for bt in self.batches:
+                bt.src = bt.pts.cpu().numpy()
+            return
         for bt in self.batches:
             before = self._reloc_chi(bt)
             saved = (bt.pts.clone(), bt.otime.clone())

@@ -338,3 +338,42 @@ def test_common_receiver_pairs_across_batches_equal_one_batch(tt):
         a, b = a.cpu().numpy(), b.cpu().numpy()
         assert np.abs(a - b).max() <= 1e-12 * np.abs(a).max()
     ctx.close()
+
+
+def test_relocation_with_pairs_across_batches_equals_one_batch(tt):
+    """Double-difference (common-receiver) relocation across batches: two batches with the
+    pairs in cr_all move their events exactly as one batch with the same pairs does (joint
+    step normalised over all events, step control on the total chi), to the order of the FP64
+    sums, over two relocation steps."""
+    import torch
+    from paper_2412_00031_gb300.invert import Inversion
+    w = I.small_case(90, shape=(13, 15, 17), n_src=7, n_rec=9)
+    g = w.grid.as_dict()
+    rng = np.random.default_rng(90)
+    nr = len(w.rec)
+    pairs = [(b, j, m, rng.normal(0, 0.3), rng.uniform(0.5, 1.5)) for m in range(nr)
+             for b in range(7) for j in range(b + 1, 7) if rng.uniform() < 0.5]
+    assert any(b < 4 <= j for b, j, _, _, _ in pairs), "no pair spans the two batches"
+    model = tuple(_dev(a, torch.float32) for a in (w.s, w.xi, w.eta))
+    ctx = tt.tt_ctx_create(g)
+    mg = tt.mgrid(4, 4, 4, 2)
+    one = Inversion(ctx, model, w.src, tt.DeviceData.from_workload(w), w.grid.shape, mg,
+                    cr=tt.CrData(7, nr, pairs, gamma=0.7), relocate=(0.6, 0.1))
+    parts = [w.subset(range(0, 4)), w.subset(range(4, 7))]
+    two = Inversion(ctx, model, None, None, w.grid.shape, mg,
+                    batches=[(p.src, tt.DeviceData.from_workload(p), None) for p in parts],
+                    cr_all=tt.CrData(7, nr, pairs, gamma=0.7), relocate=(0.6, 0.1))
+    for _ in range(2):
+        one.relocate_events()
+        two.relocate_events()
+    for (b1, a1, ok1), (b2, a2, ok2) in zip(one.reloc_hist, two.reloc_hist):
+        assert abs(b1 - b2) <= 1e-12 * b1 and abs(a1 - a2) <= 1e-12 * a1 and ok1 == ok2
+    assert any(h[2] for h in one.reloc_hist)
+    p1 = one.batches[0].pts.cpu().numpy()
+    p2 = np.concatenate([bt.pts.cpu().numpy() for bt in two.batches])
+    assert np.abs(p1 - p2).max() <= 1e-9
+    t1 = one.batches[0].otime.cpu().numpy()
+    t2 = np.concatenate([bt.otime.cpu().numpy() for bt in two.batches])
+    assert np.abs(t1 - t2).max() <= 1e-12
+    assert np.abs(p1 - w.src).max() > 1e-3          # the events did move
+    ctx.close()
