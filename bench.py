@@ -375,7 +375,50 @@ def gpu_arm(args, rank, world):
         result["warm_start"] = warm_leg(args, gp, world)
     if args.godunov:
         result["godunov"] = godunov_leg(args, gp, world)
+    if args.train_timing:
+        result["warm_start_training"] = training_leg(dev)
     return result, w, (float(itf.mean()), float(ita.mean()))
+
+
+def training_leg(dev, steps=10, warmup=3):
+    """One training step of the warm-start network (masked MSE and its gradient over a batch of
+    8 grids of 81^3, the trainer's batch) with the FP32 convolutions and with the convolutions
+    on the tensor cores (tt_net_loss_grad_tc), timed with CUDA events after a warm-up."""
+    import torch
+    import paper_2412_00031_gb300 as tt
+    from paper_2412_00031_gb300 import warmstart as WS
+    g, models = I.random_field_models(seed=I.SEED_BASE + 40, n_models=1, shape=(81, 81, 81),
+                                      n_src=8)
+    s, xi, eta, src = models[0]
+    ctx = tt.tt_ctx_create(g.as_dict())
+    model = tuple(torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32), device=dev)
+                  for a in (s, xi, eta))
+    x = torch.empty((len(src),) + g.shape + (6,), dtype=torch.float32, device=dev)
+    tt.tt_net_features(ctx, model, src, x)
+    gen = torch.Generator(device=dev).manual_seed(7)
+    target = 1.0 + 0.05 * torch.randn(x.shape[:-1], generator=gen, device=dev)
+    mask = torch.ones_like(target)
+    theta = torch.as_tensor(WS.init_params(3), device=dev)
+    grad = torch.empty_like(theta)
+    out = {}
+    for name, fn in (("fp32", tt.tt_net_loss_grad), ("tensor_cores", tt.tt_net_loss_grad_tc)):
+        for _ in range(warmup):
+            fn(ctx, theta, x, target, mask, grad)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            fn(ctx, theta, x, target, mask, grad)
+        e1.record()
+        torch.cuda.synchronize()
+        out[name] = e0.elapsed_time(e1) / steps
+    ctx.close()
+    return {"batch": "%d grids of 81^3" % len(src), "fp32_ms_per_step": out["fp32"],
+            "tensor_core_ms_per_step": out["tensor_cores"],
+            "speedup": out["fp32"] / out["tensor_cores"],
+            "note": "loss and gradient of the warm-start network; tensor cores: forward and "
+                    "input-gradient convolutions on tcgen05 (BF16 operands), weight gradients "
+                    "on the CUDA cores"}
 
 
 def godunov_leg(args, gp, world):
@@ -968,6 +1011,8 @@ def main():
                     help="time only the warm start's inference on this many sources")
     ap.add_argument("--scheme", type=int, default=0,
                     help="profiling runs: forward local solver of the main step (tt_opts.scheme)")
+    ap.add_argument("--train-timing", type=int, default=1,
+                    help="time a training step of the warm-start network (FP32 and tensor cores)")
     ap.add_argument("--godunov", type=int, default=1,
                     help="also time the step with the anisotropic Godunov solver (a leg)")
     ap.add_argument("--inversion", type=int, default=0,

@@ -452,6 +452,16 @@ tt_status tt_net_forward(tt_ctx *ctx, const float *d_theta, const float *d_x, in
 tt_status tt_net_loss_grad(tt_ctx *ctx, const float *d_theta, const float *d_x,
                            const float *d_target, const float *d_mask, int n_grids,
                            float *d_grad, double *h_loss);
+/* tt_net_loss_grad with the convolutions on the tensor cores: the forward pass and the
+ * gradients through the layers' inputs (transposed convolutions, gated by the ReLU of the
+ * layer below) run on tcgen05 with BF16 operands (weights, activations and gradients rounded
+ * to BF16) and FP32 accumulation in tensor memory; the weight gradients are FP32 sums on the
+ * CUDA cores over those BF16 rows. Same arguments and outputs as tt_net_loss_grad; the
+ * result is that gradient to BF16 accuracy (bar stated in the tests). Deterministic.
+ * TT_ETIMEOUT if a device-side wait exceeds 2 s. */
+tt_status tt_net_loss_grad_tc(tt_ctx *ctx, const float *d_theta, const float *d_x,
+                              const float *d_target, const float *d_mask, int n_grids,
+                              float *d_grad, double *h_loss);
 /* One Adam step (Kingma & Ba) on d_theta with first and second moments d_m, d_v (device,
  * zero before step 1); step counts from 1. */
 tt_status tt_net_adam(tt_ctx *ctx, float *d_theta, const float *d_grad, float *d_m, float *d_v,

@@ -90,7 +90,7 @@ EXPORTED = ["tt_default_opts", "tt_ctx_create", "tt_ctx_destroy", "tt_last_error
             "tt_model_update", "tt_misfit_cr", "tt_field_at_points", "tt_misfit_table",
             "tt_reloc_kernels", "tt_reloc_update", "tt_tele2d", "tt_tele_region_times",
             "tt_forward_tele", "tt_autotune_adjoint", "tt_kernel_normalize_rel",
-            "tt_misfit_total", "tt_plan_create_cr"]
+            "tt_misfit_total", "tt_plan_create_cr", "tt_net_loss_grad_tc"]
 TT_NOALLOC_MAX_REC = 1024
 
 
@@ -133,6 +133,8 @@ def _load():
     L.tt_net_forward.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]
     L.tt_net_loss_grad.argtypes = [C.c_void_p] + [C.c_void_p] * 4 + [C.c_int, C.c_void_p,
                                                                        C.POINTER(C.c_double)]
+    L.tt_net_loss_grad_tc.argtypes = [C.c_void_p] + [C.c_void_p] * 4 + [C.c_int, C.c_void_p,
+                                                                          C.POINTER(C.c_double)]
     L.tt_net_adam.argtypes = [C.c_void_p] + [C.c_void_p] * 4 + [C.c_int] + [C.c_float] * 4
     L.tt_net_set_weights.argtypes = [C.c_void_p, C.c_void_p]
     L.tt_net_infer.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]
@@ -172,7 +174,8 @@ def _load():
                  "tt_mgrid_expand", "tt_model_update", "tt_misfit_cr", "tt_field_at_points",
                  "tt_misfit_table", "tt_reloc_kernels", "tt_reloc_update", "tt_tele2d",
                  "tt_tele_region_times", "tt_forward_tele", "tt_autotune_adjoint",
-                 "tt_kernel_normalize_rel", "tt_misfit_total", "tt_plan_create_cr"):
+                 "tt_kernel_normalize_rel", "tt_misfit_total", "tt_plan_create_cr",
+                 "tt_net_loss_grad_tc"):
         getattr(L, name).restype = C.c_int
     return L
 
@@ -760,6 +763,17 @@ def tt_net_loss_grad(ctx, theta, x, target, mask, grad):
     loss = C.c_double()
     _check(ctx, lib.tt_net_loss_grad(ctx.handle, _ptr(theta), _ptr(x), _ptr(target), _ptr(mask),
                                      x.shape[0], _ptr(grad), C.byref(loss)))
+    return loss.value
+
+
+def tt_net_loss_grad_tc(ctx, theta, x, target, mask, grad):
+    """tt_net_loss_grad with the convolutions on the tensor cores (BF16 operands)."""
+    _f32(theta, x, target, mask, grad)
+    _net_room(ctx, x.shape[0], theta=theta, x=x, target=target, mask=mask, grad=grad)
+    _cuda_ok(theta, x, target, mask, grad)
+    loss = C.c_double()
+    _check(ctx, lib.tt_net_loss_grad_tc(ctx.handle, _ptr(theta), _ptr(x), _ptr(target),
+                                        _ptr(mask), x.shape[0], _ptr(grad), C.byref(loss)))
     return loss.value
 
 

@@ -49,6 +49,8 @@ struct tt_ctx {
     // warm-start network: inference weights (BF16-rounded) and its workspace
     DevBuf net_theta, net_x, net_a, net_b, net_y, net_d1, net_d2, net_dy, net_wt, net_part,
         net_scr, net_wbf;  // net_wbf: BF16 weight images of the four layers (tensor cores)
+    // tensor-core training: weight images of theta and of the transposed layers, BF16 rows
+    DevBuf net_img, net_timg, net_rows;
     bool has_net = false;
     double *h_loss = nullptr;  // pinned
     // autotuner: scratch tau and the choices made, per (n_src, dtype)
@@ -1177,7 +1179,8 @@ void tt_ctx_destroy(tt_ctx *ctx) {
                       &ctx->net_wt, &ctx->net_part, &ctx->net_scr, &ctx->tune_tau, &ctx->tau_w,
                       &ctx->slot_srcc, &ctx->slot_int,
                       &ctx->net_wbf, &ctx->mg_tab, &ctx->mg_scr, &ctx->upd_part,
-                      &ctx->tele_tau, &ctx->tele_aux};
+                      &ctx->tele_tau, &ctx->tele_aux, &ctx->net_img, &ctx->net_timg,
+                      &ctx->net_rows};
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     if (ctx->h_loss) cudaFreeHost(ctx->h_loss);
@@ -2057,6 +2060,45 @@ tt_status tt_net_loss_grad(tt_ctx *ctx, const float *d_theta, const float *d_x,
     ctx->launches += 3 + 2 * kNetLayers + 2 * (kNetLayers - 1);
     CK(cudaMemcpyAsync(ctx->h_loss, loss, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
+    if (h_loss) *h_loss = *ctx->h_loss;
+    return TT_OK;
+}
+
+tt_status tt_net_loss_grad_tc(tt_ctx *ctx, const float *d_theta, const float *d_x,
+                              const float *d_target, const float *d_mask, int n_grids,
+                              float *d_grad, double *h_loss) {
+    if (!ctx) return TT_EINVAL;
+    if (!d_theta || !d_x || !d_target || !d_mask || !d_grad || n_grids < 1)
+        return fail(ctx, TT_EINVAL, "tt_net_loss_grad_tc: NULL buffer or n_grids < 1");
+    const GridC &g = ctx->g;
+    const ConvDims d{n_grids, g.nr, g.nt, g.np};
+    const size_t M = (size_t)g.N * n_grids;
+    ENSURE(ctx->net_img, sizeof(__nv_bfloat16) * net_weight_image_elems());
+    ENSURE(ctx->net_timg, sizeof(__nv_bfloat16) * net_tweight_image_elems());
+    ENSURE(ctx->net_wt, sizeof(float) * 27 * kNetHidden * kNetHidden);
+    ENSURE(ctx->net_rows, sizeof(__nv_bfloat16) * net_train_row_elems(d));
+    ENSURE(ctx->net_y, sizeof(float) * M);
+    ENSURE(ctx->net_dy, sizeof(float) * M);
+    ENSURE(ctx->net_part, sizeof(float) * wgrad_partial_floats());
+    ENSURE(ctx->net_scr, sizeof(double) * 4096);
+    ENSURE(ctx->flags, 4 * sizeof(int));
+    if (!ctx->h_loss) CK(cudaMallocHost((void **)&ctx->h_loss, sizeof(double)));
+    int *err = (int *)ctx->flags.p + 3;
+    double *loss = (double *)ctx->net_scr.p + 4000;
+    CK(cudaMemsetAsync(err, 0, sizeof(int), ctx->st));
+    CK(run_net_loss_grad_tc(d, d_theta, d_x, d_target, d_mask, d_grad, loss,
+                            (__nv_bfloat16 *)ctx->net_img.p, (__nv_bfloat16 *)ctx->net_timg.p,
+                            (float *)ctx->net_wt.p, (__nv_bfloat16 *)ctx->net_rows.p,
+                            (float *)ctx->net_y.p, (float *)ctx->net_dy.p,
+                            (float *)ctx->net_part.p, (double *)ctx->net_scr.p, ctx->n_sm, err,
+                            kDefaultSpinNs, ctx->st));
+    ctx->launches += 2 + 2 * (kNetLayers - 1) + kNetLayers + 2 + 2 * kNetLayers + (kNetLayers - 1);
+    int h_err = 0;
+    CK(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaMemcpyAsync(ctx->h_loss, loss, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    if (h_err)
+        return fail(ctx, TT_ETIMEOUT, "tt_net_loss_grad_tc: a device-side wait exceeded its limit");
     if (h_loss) *h_loss = *ctx->h_loss;
     return TT_OK;
 }

@@ -234,13 +234,19 @@ __device__ __forceinline__ bool pad_row(const RowGeo &G, int n) {
     return n % G.Sj == G.np || (n / G.Sj) % (G.nt + 1) == G.nt;
 }
 
-// FINAL: write channel 0 + bias as FP32 y[grid][node] (real nodes), else ReLU(out + bias)
-// as BF16 rows of 32 channels (zero on the padding rows).
-template <int KC, int NO, bool FINAL>
+// Epilogue modes: kEpiRelu writes ReLU(out + bias) as BF16 rows of 32 channels (a hidden
+// layer); kEpiFinal writes channel 0 + bias as FP32 y[grid][node] (real nodes, the last
+// layer); kEpiGate writes out * [gate > 0] as BF16 rows, gate being the BF16 rows of the
+// layer below (training: the input gradient of a layer through the ReLU of the one below,
+// computed with the flipped, transposed weights; no bias). Padding rows are written as zero.
+constexpr int kEpiRelu = 0, kEpiFinal = 1, kEpiGate = 2;
+template <int KC, int NO, int MODE>
 __global__ void __launch_bounds__(kThreads, 1)
     conv3d_tc_kernel(const __grid_constant__ CUtensorMap map, RowGeo G,
                      const uint4 *__restrict__ wimg, const float *__restrict__ bias,
-                     void *__restrict__ out_, int *err, unsigned long long limit) {
+                     const uint4 *__restrict__ gate, void *__restrict__ out_, int *err,
+                     unsigned long long limit) {
+    constexpr bool FINAL = MODE == kEpiFinal;
     using L = Smem<KC, NO>;
     extern __shared__ unsigned char smem_raw[];
     const unsigned raw = saddr(smem_raw);
@@ -351,7 +357,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         float *exch = reinterpret_cast<float *>(sm + L::EXCH);   // [2][4][2 lanes][2][32]
         float bz[FINAL ? 1 : 32];
 #pragma unroll
-        for (int c = 0; c < (FINAL ? 1 : 32); ++c) bz[c] = bias[c];
+        for (int c = 0; c < (FINAL ? 1 : 32); ++c) bz[c] = MODE == kEpiGate ? 0.0f : bias[c];
         unsigned aph = 0;
         for (long long T = blockIdx.x + (long long)a * gridDim.x; T < total; T += 2LL * gridDim.x) {
             // all 128 threads of the group agree (TMEM loads are warp-collective, the
@@ -408,6 +414,18 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 epi_sync(a);
                 const bool zero = !out_ok || pad_row(G, n);
+                unsigned gw[16];   // kEpiGate: the gate row's 32 BF16 channels
+                if (MODE == kEpiGate && !zero) {
+                    const uint4 *gr = gate + ((long long)g * G.R + n) * 4;
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const uint4 v = gr[c];
+                        gw[4 * c] = v.x;
+                        gw[4 * c + 1] = v.y;
+                        gw[4 * c + 2] = v.z;
+                        gw[4 * c + 3] = v.w;
+                    }
+                }
                 unsigned w[16];
 #pragma unroll
                 for (int c = 0; c < 32; c += 2) {
@@ -420,7 +438,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                             if (lane == 31) s1 = ex[(((quarter + 1) * 2 + 0) * 2 + 0) * 32 + c + u];
                             if (lane >= 30) s2 = ex[(((quarter + 1) * 2 + lane - 30) * 2 + 1) * 32 + c + u];
                         }
-                        v[u] = zero ? 0.0f : fmaxf((d0[c + u] + s1) + s2 + bz[c + u], 0.0f);
+                        if (MODE == kEpiGate) {
+                            const unsigned short hb = (unsigned short)(gw[c / 2] >> (16 * u));
+                            const bool open = !zero && __bfloat162float(__ushort_as_bfloat16(hb)) > 0.0f;
+                            v[u] = open ? (d0[c + u] + s1) + s2 : 0.0f;
+                        } else {
+                            v[u] = zero ? 0.0f : fmaxf((d0[c + u] + s1) + s2 + bz[c + u], 0.0f);
+                        }
                     }
                     const __nv_bfloat162 p = __floats2bfloat162_rn(v[0], v[1]);
                     w[c / 2] = *reinterpret_cast<const unsigned *>(&p);
@@ -466,6 +490,23 @@ __global__ void pack_features_kernel(RowGeo G, const float *__restrict__ x, uint
     }
     xp[2 * q] = make_uint4(w[0], w[1], w[2], w[3]);
     xp[2 * q + 1] = make_uint4(0u, 0u, 0u, 0u);
+}
+
+// dL/dy [grid][node] (FP32) -> rows [grid][R][16] (BF16, channel 0; the rest and the padding
+// rows zero): the input of the last layer's transposed convolution in training.
+__global__ void pack_dy_kernel(RowGeo G, const float *__restrict__ dy, uint4 *__restrict__ out) {
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= (long long)G.nb * G.R) return;
+    const int g = (int)(q / G.R), n = (int)(q - (long long)g * G.R);
+    unsigned w0 = 0u;
+    if (!pad_row(G, n)) {
+        const int k = n % G.Sj, j = (n / G.Sj) % (G.nt + 1), i = n / G.Si;
+        const float v = dy[(long long)g * G.nr * G.nt * G.np + ((long long)i * G.nt + j) * G.np + k];
+        const __nv_bfloat162 p = __floats2bfloat162_rn(v, 0.0f);
+        w0 = *reinterpret_cast<const unsigned *>(&p);
+    }
+    out[2 * q] = make_uint4(w0, 0u, 0u, 0u);
+    out[2 * q + 1] = make_uint4(0u, 0u, 0u, 0u);
 }
 
 // Layer l's weights W[27][cin][cout] (FP32) -> the shared-memory image of the B operands
@@ -523,22 +564,23 @@ cudaError_t encode_rows(CUtensorMap *map, const void *base, const RowGeo &G, int
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-template <int KC, int NO, bool FINAL>
+template <int KC, int NO, int MODE>
 cudaError_t launch_layer(const void *in, const RowGeo &G, const __nv_bfloat16 *wimg,
                          const float *bias, void *out, int n_sm, int *err,
-                         unsigned long long limit, cudaStream_t st) {
+                         unsigned long long limit, cudaStream_t st, const void *gate = nullptr) {
     CUtensorMap map;
     cudaError_t e = encode_rows(&map, in, G, KC);
     if (e != cudaSuccess) return e;
     // more than half the shared memory of an SM: one CTA per SM, which owns its TMEM
     constexpr int smem = Smem<KC, NO>::TOTAL > 120 * 1024 ? Smem<KC, NO>::TOTAL : 120 * 1024;
-    const void *fn = (const void *)conv3d_tc_kernel<KC, NO, FINAL>;
+    const void *fn = (const void *)conv3d_tc_kernel<KC, NO, MODE>;
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     const long long total = (long long)G.nb * G.tiles;
     const unsigned grid = (unsigned)(total < n_sm ? total : n_sm);
-    conv3d_tc_kernel<KC, NO, FINAL><<<grid, kThreads, smem, st>>>(
-        map, G, reinterpret_cast<const uint4 *>(wimg), bias, out, err, limit);
+    conv3d_tc_kernel<KC, NO, MODE><<<grid, kThreads, smem, st>>>(
+        map, G, reinterpret_cast<const uint4 *>(wimg), bias, reinterpret_cast<const uint4 *>(gate),
+        out, err, limit);
     return cudaGetLastError();
 }
 
@@ -582,6 +624,95 @@ cudaError_t run_net_weight_images(const float *theta, __nv_bfloat16 *img, cudaSt
     return cudaGetLastError();
 }
 
+// Sizes of the transposed layers' images (layers 1-3; layer 0 has none): the gradient of
+// layer l's output (cout_l channels, 1 -> 16 padded for the last layer) to its input (32).
+static size_t image_offset_t(int l) {
+    const size_t sz[kNetLayers] = {0u, 27u * 4 * 32 * 8, 27u * 4 * 32 * 8, 27u * 2 * 32 * 8};
+    size_t o = 0;
+    for (int q = 0; q < l; ++q) o += sz[q];
+    return o;
+}
+size_t net_tweight_image_elems() { return image_offset_t(kNetLayers - 1) + 27u * 2 * 32 * 8; }
+
+size_t net_train_row_elems(const ConvDims &d) {
+    return (size_t)row_geo(d).R * d.nb * (16 + 3 * 32 + 16 + 3 * 32);
+}
+
+cudaError_t run_net_loss_grad_tc(const ConvDims &d, const float *theta, const float *x,
+                                 const float *target, const float *mask, float *grad,
+                                 double *loss, __nv_bfloat16 *img, __nv_bfloat16 *timg,
+                                 float *wt, __nv_bfloat16 *rows, float *y, float *dy,
+                                 float *partial, double *scratch, int n_sm, int *err,
+                                 unsigned long long limit, cudaStream_t st) {
+    const RowGeo G = row_geo(d);
+    const size_t R = (size_t)G.R * G.nb;
+    // rows: X (16 channels), A1..A3 (32), DY (16), G3, G2, G1 (32); A_l is layer l's output
+    __nv_bfloat16 *X = rows, *A[3], *DY, *Gr[3];
+    A[0] = X + 16 * R;
+    A[1] = A[0] + 32 * R;
+    A[2] = A[1] + 32 * R;
+    DY = A[2] + 32 * R;
+    Gr[0] = DY + 16 * R;      // gradient at the output of layer 1 (before its ReLU)
+    Gr[1] = Gr[0] + 32 * R;   // ... of layer 2
+    Gr[2] = Gr[1] + 32 * R;   // ... of layer 3
+    cudaError_t e = run_net_weight_images(theta, img, st);
+    if (e != cudaSuccess) return e;
+    for (int l = 1; l < kNetLayers; ++l) {
+        const int ci = kNetCin[l], co = kNetCout[l];
+        if ((e = run_conv3d_flip(ci, co, theta + net_weight_offset(l), wt, st)) != cudaSuccess)
+            return e;
+        const int KC = co <= 16 ? 2 : 4, n = 27 * KC * 32 * 8;
+        weight_image_kernel<<<blocks_for(n, 256), 256, 0, st>>>(wt, co, ci, KC, 32,
+                                                                timg + image_offset_t(l));
+    }
+    pack_features_kernel<<<blocks_for((long long)R, 256), 256, 0, st>>>(
+        G, x, reinterpret_cast<uint4 *>(X));
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const float *bias[kNetLayers];
+    for (int l = 0; l < kNetLayers; ++l)
+        bias[l] = theta + net_weight_offset(l) + 27 * kNetCin[l] * kNetCout[l];
+    // forward, every layer's output kept
+    if ((e = launch_layer<2, 32, kEpiRelu>(X, G, img + image_offset(0), bias[0], A[0], n_sm, err,
+                                           limit, st)) != cudaSuccess)
+        return e;
+    for (int l = 1; l < 3; ++l)
+        if ((e = launch_layer<4, 32, kEpiRelu>(A[l - 1], G, img + image_offset(l), bias[l], A[l],
+                                               n_sm, err, limit, st)) != cudaSuccess)
+            return e;
+    if ((e = launch_layer<4, 16, kEpiFinal>(A[2], G, img + image_offset(3), bias[3], y, n_sm, err,
+                                            limit, st)) != cudaSuccess)
+        return e;
+    if ((e = run_mse((long long)d.nb * d.D * d.H * d.W, y, target, mask, dy, scratch, loss, st)) !=
+        cudaSuccess)
+        return e;
+    pack_dy_kernel<<<blocks_for((long long)R, 256), 256, 0, st>>>(G, dy, reinterpret_cast<uint4 *>(DY));
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // backward, last layer first: the weight gradient of layer l from its input rows and the
+    // gradient rows of its output; the gradient of its input through the transposed
+    // convolution, gated by the ReLU of the layer below
+    const __nv_bfloat16 *gout = DY;
+    int gch = 16;
+    for (int l = kNetLayers - 1; l >= 0; --l) {
+        const int ci = kNetCin[l], co = kNetCout[l];
+        const __nv_bfloat16 *in = l == 0 ? X : A[l - 1];
+        float *gw = grad + net_weight_offset(l);
+        if ((e = run_conv3d_wgrad_rows(G.nb, G.R, G.Sj, G.Si, ci, l == 0 ? 16 : 32, co, gch, in, gout,
+                                       partial, gw, gw + 27 * ci * co, st)) != cudaSuccess)
+            return e;
+        if (l == 0) break;
+        __nv_bfloat16 *gin = Gr[l - 1];
+        e = l == kNetLayers - 1
+                ? launch_layer<2, 32, kEpiGate>(gout, G, timg + image_offset_t(l), nullptr, gin,
+                                                n_sm, err, limit, st, A[l - 1])
+                : launch_layer<4, 32, kEpiGate>(gout, G, timg + image_offset_t(l), nullptr, gin,
+                                                n_sm, err, limit, st, A[l - 1]);
+        if (e != cudaSuccess) return e;
+        gout = gin;
+        gch = 32;
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t run_net_infer(const ConvDims &d, const float *theta, const __nv_bfloat16 *img,
                           const float *x, __nv_bfloat16 *a, __nv_bfloat16 *b, float *y, int n_sm,
                           int *err, unsigned long long limit, cudaStream_t st) {
@@ -596,16 +727,16 @@ cudaError_t run_net_infer(const ConvDims &d, const float *theta, const __nv_bflo
     const float *bias[kNetLayers];
     for (int l = 0; l < kNetLayers; ++l)
         bias[l] = theta + net_weight_offset(l) + 27 * kNetCin[l] * kNetCout[l];
-    if ((e = launch_layer<2, 32, false>(b, G, img + image_offset(0), bias[0], a, n_sm, err, limit, st)) !=
+    if ((e = launch_layer<2, 32, kEpiRelu>(b, G, img + image_offset(0), bias[0], a, n_sm, err, limit, st)) !=
         cudaSuccess)
         return e;
-    if ((e = launch_layer<4, 32, false>(a, G, img + image_offset(1), bias[1], b, n_sm, err, limit, st)) !=
+    if ((e = launch_layer<4, 32, kEpiRelu>(a, G, img + image_offset(1), bias[1], b, n_sm, err, limit, st)) !=
         cudaSuccess)
         return e;
-    if ((e = launch_layer<4, 32, false>(b, G, img + image_offset(2), bias[2], a, n_sm, err, limit, st)) !=
+    if ((e = launch_layer<4, 32, kEpiRelu>(b, G, img + image_offset(2), bias[2], a, n_sm, err, limit, st)) !=
         cudaSuccess)
         return e;
-    return launch_layer<4, 16, true>(a, G, img + image_offset(3), bias[3], y, n_sm, err, limit, st);
+    return launch_layer<4, 16, kEpiFinal>(a, G, img + image_offset(3), bias[3], y, n_sm, err, limit, st);
 }
 
 }  // namespace ttgb

@@ -30,6 +30,8 @@ def main(argv=None):
     ap.add_argument("--batch", type=int, default=8)
     ap.add_argument("--lr", type=float, default=2e-3)
     ap.add_argument("--seed", type=int, default=20241203)
+    ap.add_argument("--tensor-cores", action="store_true",
+                    help="gradients with the convolutions on the tensor cores (BF16 operands)")
     ap.add_argument("--out", default=os.path.join(os.path.dirname(os.path.abspath(__file__)),
                                                   "warmstart_81.npz"))
     a = ap.parse_args(argv)
@@ -50,7 +52,8 @@ def main(argv=None):
     torch.cuda.synchronize()
     t2 = time.time()
     theta, losses = WS.train(ctx, x, t, m, WS.init_params(a.seed), steps=a.steps,
-                             batch=a.batch, lr=a.lr, seed=a.seed, log_every=100)
+                             batch=a.batch, lr=a.lr, seed=a.seed, log_every=100,
+                             tensor_cores=a.tensor_cores)
     torch.cuda.synchronize()
     t3 = time.time()
     del x, t, m
@@ -79,6 +82,7 @@ def main(argv=None):
         "held_out_rms_err": rms_net, "held_out_rms_err_tau1": rms_one,
         "held_out_sweeps_cold": float(cold.mean()), "held_out_sweeps_warm": float(warm.mean()),
         "seconds_data": t2 - t1, "seconds_train": t3 - t2, "seconds_models": t1 - t0,
+        "gradient": "tensor cores (BF16 operands)" if a.tensor_cores else "FP32",
     }
     np.savez(a.out, theta=theta.cpu().numpy(), losses=np.asarray(losses),
              summary=json.dumps(summary))

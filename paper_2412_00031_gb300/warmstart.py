@@ -3,7 +3,8 @@
 Every arithmetic step runs in libttgb's kernels. The steps are:
 - the forward solves that produce the targets (tt_forward);
 - the input features (tt_net_features);
-- the loss and its gradient (tt_net_loss_grad);
+- the loss and its gradient (tt_net_loss_grad in FP32, or tt_net_loss_grad_tc with the
+  convolutions on the tensor cores);
 - the optimiser (tt_net_adam).
 
 This module only orders the calls, draws the seeded initial weights and the sample order,
@@ -16,7 +17,7 @@ y = 0, which the clamp of the warm start does not need).
 import numpy as np
 
 from . import (TT_F32, default_opts, tt_forward, tt_net_adam, tt_net_features,
-               tt_net_loss_grad, tt_net_param_count)
+               tt_net_loss_grad, tt_net_loss_grad_tc, tt_net_param_count)
 
 LAYERS = ((6, 32), (32, 32), (32, 32), (32, 1))
 
@@ -56,10 +57,13 @@ def make_samples(ctx, grid_shape, models, device="cuda", opts=None):
     return torch.cat(xs), torch.cat(ts), torch.cat(ms), np.concatenate(iters)
 
 
-def train(ctx, x, t, m, theta0, steps, batch, lr=1e-3, seed=0, log_every=0):
+def train(ctx, x, t, m, theta0, steps, batch, lr=1e-3, seed=0, log_every=0,
+          tensor_cores=False):
     """Adam on the masked MSE over mini-batches of whole grids. The sample order is a
     seeded permutation, re-drawn each epoch; a batch is a contiguous block of the permuted
-    samples (gathered once per epoch). Returns (theta, losses)."""
+    samples (gathered once per epoch). tensor_cores: gradients from tt_net_loss_grad_tc
+    (convolutions on tcgen05, BF16 operands) instead of the FP32 tt_net_loss_grad. Returns
+    (theta, losses)."""
     import torch
     theta = torch.as_tensor(theta0, dtype=torch.float32, device=x.device).clone()
     grad = torch.zeros_like(theta)
@@ -75,8 +79,8 @@ def train(ctx, x, t, m, theta0, steps, batch, lr=1e-3, seed=0, log_every=0):
         for b0 in range(0, n - batch + 1, batch):
             if step >= steps:
                 break
-            loss = tt_net_loss_grad(ctx, theta, xp[b0:b0 + batch], tp[b0:b0 + batch],
-                                    mp[b0:b0 + batch], grad)
+            fn = tt_net_loss_grad_tc if tensor_cores else tt_net_loss_grad
+            loss = fn(ctx, theta, xp[b0:b0 + batch], tp[b0:b0 + batch], mp[b0:b0 + batch], grad)
             step += 1
             tt_net_adam(ctx, theta, grad, mom1, mom2, step, lr)
             losses.append(loss)

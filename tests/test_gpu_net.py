@@ -10,6 +10,16 @@ from oracle import net as N
 
 pytestmark = pytest.mark.gpu
 
+# Tensor-core training (BF16 operands). With u = 2^-9, the unit roundoff of BF16, the input
+# gradient reaching layer 1 has been rounded about 8 times (the output gradient, three
+# transposed convolutions' BF16 weights and outputs, the activations that gate them), so the
+# per-layer bar is 16 u, the whole gradient's 8 u and the loss's (one forward pass) 5 u.
+# Measured: 8.5 u for layer 1's weights, 2.3 u in all, 0.34 u for the loss.
+BF16_U = 2.0 ** -9
+TC_LOSS_BAR = 5 * BF16_U
+TC_GRAD_BAR_LAYER = 16 * BF16_U
+TC_GRAD_BAR = 8 * BF16_U
+
 
 @pytest.fixture(scope="module")
 def tt():
@@ -105,6 +115,44 @@ def test_loss_gradient_matches_oracle(tt):
     ctx.close()
 
 
+def test_tensor_core_loss_gradient_matches_oracle_to_bf16_accuracy(tt):
+    """Training with the convolutions on the tensor cores (tt_net_loss_grad_tc): BF16
+    weights, activations and gradients, FP32 accumulation. Against the FP64 oracle's loss
+    and gradient on the inputs of the FP32 test, per layer (weights and biases), and
+    bitwise deterministic."""
+    import torch
+    w, xs = _oracle_inputs(62, shape=(10, 9, 12), n=3)
+    rng = np.random.default_rng(8)
+    theta = _theta(9)
+    taus = [(1.0 + 0.05 * rng.standard_normal(w.grid.shape)).astype(np.float32) for _ in xs]
+    masks = [(rng.uniform(size=w.grid.shape) > 0.3).astype(np.float32) for _ in xs]
+    loss_ref, g_ref = N.loss_and_grad(theta.astype(np.float64), [x.astype(np.float64) for x in xs],
+                                      [t.astype(np.float64) - 1.0 for t in taus],
+                                      [m.astype(np.float64) for m in masks])
+    ctx = tt.tt_ctx_create(w.grid.as_dict())
+    d = lambda a: torch.as_tensor(np.ascontiguousarray(np.stack(a)), device="cuda")
+    grad = torch.empty(tt.tt_net_param_count(), dtype=torch.float32, device="cuda")
+    th = torch.as_tensor(theta, device="cuda")
+    loss = tt.tt_net_loss_grad_tc(ctx, th, d(xs), d(taus), d(masks), grad)
+    g = grad.cpu().numpy().astype(np.float64)
+    errs = []
+    k = 0
+    for ci, co in N.LAYERS:
+        for n in (27 * ci * co, co):
+            a, b = g[k:k + n], g_ref[k:k + n]
+            errs.append(np.linalg.norm(a - b) / np.linalg.norm(b))
+            k += n
+    total = np.linalg.norm(g - g_ref) / np.linalg.norm(g_ref)
+    print("\ntensor-core gradient: loss rel err %.2e, total %.2e, per layer %s" % (
+        abs(loss / loss_ref - 1), total, " ".join("%.2e" % e for e in errs)))
+    assert abs(loss / loss_ref - 1) <= TC_LOSS_BAR
+    assert total <= TC_GRAD_BAR and max(errs) <= TC_GRAD_BAR_LAYER
+    grad2 = torch.empty_like(grad)
+    loss2 = tt.tt_net_loss_grad_tc(ctx, th, d(xs), d(taus), d(masks), grad2)
+    assert loss2 == loss and torch.equal(grad, grad2)
+    ctx.close()
+
+
 def test_adam_step(tt):
     import torch
     rng = np.random.default_rng(10)
@@ -148,11 +196,13 @@ def test_warm_start_needs_weights(tt):
     ctx.close()
 
 
-def test_trained_network_gains_over_the_cold_start(tt, capsys):
+@pytest.mark.parametrize("tensor_cores", [False, True], ids=["fp32-gradient", "tensor-core-gradient"])
+def test_trained_network_gains_over_the_cold_start(tt, capsys, tensor_cores):
     """Trains the network on the GPU (forward solves of random-field models as data, the
-    library's loss, gradient and Adam kernels) and measures on held-out models: the
-    prediction is closer to the converged tau than tau = 1, the warm-started sweep meets
-    the same tolerance, and it takes no more sweeps than the cold start."""
+    library's loss, gradient and Adam kernels; the gradient in FP32 or with the convolutions
+    on the tensor cores) and measures on held-out models: the prediction is closer to the
+    converged tau than tau = 1, the warm-started sweep meets the same tolerance, and it takes
+    no more sweeps than the cold start."""
     import torch
     from paper_2412_00031_gb300 import warmstart as WS
     g, models = I.random_field_models(seed=I.SEED_BASE + 30, n_models=14, shape=(25, 25, 25),
@@ -160,7 +210,8 @@ def test_trained_network_gains_over_the_cold_start(tt, capsys):
                                       depth_range=(4.0, 20.0))
     ctx = tt.tt_ctx_create(g.as_dict())
     x, t, m, _ = WS.make_samples(ctx, g.shape, models[:12])
-    theta, losses = WS.train(ctx, x, t, m, WS.init_params(1), steps=300, batch=4, lr=2e-3, seed=2)
+    theta, losses = WS.train(ctx, x, t, m, WS.init_params(1), steps=300, batch=4, lr=2e-3, seed=2,
+                             tensor_cores=tensor_cores)
     assert np.mean(losses[-20:]) < 0.2 * np.mean(losses[:5])
     tt.tt_net_set_weights(ctx, theta)
     xh, th, _, cold_iters = WS.make_samples(ctx, g.shape, models[12:])
@@ -181,8 +232,9 @@ def test_trained_network_gains_over_the_cold_start(tt, capsys):
         assert rel_linf(tau_w.cpu().numpy(), tau_c.cpu().numpy()) <= 1e-5
     warm_iters = np.concatenate(warm_iters)
     with capsys.disabled():
-        print("\nwarm start: held-out max |tau - tau*| %.3e (tau = 1: %.3e); sweeps %.2f -> %.2f"
-              % (err_net, err_one, cold_iters.mean(), warm_iters.mean()))
+        print("\nwarm start (%s gradient): held-out max |tau - tau*| %.3e (tau = 1: %.3e); "
+              "sweeps %.2f -> %.2f" % ("tensor-core" if tensor_cores else "FP32", err_net, err_one,
+                                      cold_iters.mean(), warm_iters.mean()))
     assert warm_iters.mean() <= cold_iters.mean()
     ctx.close()
 
