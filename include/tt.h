@@ -198,8 +198,9 @@ tt_status tt_adjoint(tt_ctx *ctx, const tt_model *model, const tt_point *h_src, 
  * sum_b -2 P (d_theta T / r)(d_phi T / (r cos theta)) to d_Keta (device double [N], read
  * and written; zero them before the first batch). Each source's term is formed in the
  * fields' precision; every 32nd source is summed by one lane with a compensated (TwoSum)
- * accumulator in that precision, and the lanes' sums, the batch's total and the kernels
- * are FP64. The sums run in a fixed order, so the result is bitwise reproducible. */
+ * accumulator in that precision, the warp merges the lanes' accumulators the same way, and
+ * the batch's total is added to the FP64 kernels. The sums run in a fixed order, so the
+ * result is bitwise reproducible. */
 tt_status tt_kernel(tt_ctx *ctx, const tt_model *model, int n_src, const void *d_T,
                     const void *d_P, double *d_Ks, double *d_Kxi, double *d_Keta);
 

@@ -343,6 +343,11 @@ template <typename F> struct CompSum {
         hi = s;
         lo = __fadd_rn_t(lo, err);
     }
+    // adds another accumulator's (hi, lo): TwoSum of the hi parts, the lo parts summed
+    __device__ __forceinline__ void merge(F ohi, F olo) {
+        add(ohi);
+        lo = __fadd_rn_t(lo, olo);
+    }
     __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
     static __device__ __forceinline__ float __fadd_rn_t(float a, float b) { return __fadd_rn(a, b); }
     static __device__ __forceinline__ float __fsub_rn_t(float a, float b) { return __fsub_rn(a, b); }
@@ -361,8 +366,8 @@ __global__ void kernel_accum_kernel(GridC g, int B, const F *s, const F *T, cons
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     // Each source's term in the fields' precision F (its inputs are F values; reciprocals
     // instead of divisions). A lane sums its sources' terms with a compensated accumulator
-    // in F (TwoSum); the lanes' sums, the batch's total and the kernels themselves are FP64,
-    // combined in a fixed order.
+    // in F (TwoSum), the warp merges the lanes' accumulators in a fixed butterfly, and lane 0
+    // adds the batch's total to the FP64 kernels: only those three adds use the FP64 pipe.
     const F idt = (F)(1.0 / g.dt), idp = (F)(1.0 / g.dp);
     for (long long n = warp; n < g.N; n += nwarps) {
         int k = (int)(n % g.np);
@@ -387,13 +392,14 @@ __global__ void kernel_accum_kernel(GridC g, int B, const F *s, const F *T, cons
             sX.add(p * (gt * gt - gp * gp));
             sE.add((F)-2 * p * gt * gp);
         }
-        double aP = sP.value(), aX = sX.value(), aE = sE.value();
+#pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            aP += __shfl_xor_sync(0xffffffffu, aP, o);
-            aX += __shfl_xor_sync(0xffffffffu, aX, o);
-            aE += __shfl_xor_sync(0xffffffffu, aE, o);
+            sP.merge(__shfl_xor_sync(0xffffffffu, sP.hi, o), __shfl_xor_sync(0xffffffffu, sP.lo, o));
+            sX.merge(__shfl_xor_sync(0xffffffffu, sX.hi, o), __shfl_xor_sync(0xffffffffu, sX.lo, o));
+            sE.merge(__shfl_xor_sync(0xffffffffu, sE.hi, o), __shfl_xor_sync(0xffffffffu, sE.lo, o));
         }
         if (lane == 0) {
+            const double aP = sP.value(), aX = sX.value(), aE = sE.value();
             const double sv = (double)s[n];
             Ks[n] += sv * sv * aP;
             Kxi[n] += aX;
