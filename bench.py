@@ -430,7 +430,7 @@ def godunov_leg(args, gp, world):
     if gp.plan is not None:
         gp.plan.close()
         gp.plan = None
-    gp.opts.init = 0
+    gp.opts.init = tt.TT_INIT_ABOVE
     gp.opts.scheme = 2
     tuned = None
     if args.autotune and args.schedule == 0:
@@ -461,13 +461,22 @@ def godunov_leg(args, gp, world):
                             float(np.mean([s["node_sweeps"] for s in fwd])),
                             FWD_BYTES_PER_UPDATE, FWD_BYTES_PER_NODE_SWEEP, hbm)
     fwd_kernel["kernel"] = "fwd_sweep_kernel<float, unsigned, 0, 2>"
+    # The same forward from tau = 1 (opts.init = 0), for comparison with the start from above.
+    o1 = tt.default_opts(tt.TT_F32, scheme=2, fwd_groups=gp.opts.fwd_groups)
+    it1 = tt.tt_forward(gp.ctx, gp.model, gp.w.src, gp.tau, None, o1)
+    ms1 = tt.tt_get_stats(gp.ctx, tt.TT_STATS_FORWARD)["sweep_ms"]
     return {"value": world * gp.w.n_src / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
             "forward_kernel": fwd_kernel,
             "scheme": "Godunov upwind for anisotropic models (opts.scheme = 2)",
+            "start": "from above (opts.init = 3)",
             "iters_fwd_mean": float(itf.mean()), "iters_fwd_max": int(itf.max()),
             "iters_adj_mean": float(ita.mean()),
             "forward_ms": float(np.mean([s["sweep_ms"] for s in fwd])),
             "adjoint_ms": float(np.mean([s["sweep_ms"] for s in adj])),
+            "start_from_one": {"iters_fwd_mean": float(it1.mean()),
+                               "iters_fwd_max": int(it1.max()), "forward_ms": ms1},
+            "ideal_start_bound": start_bound(gp, scheme=2, cold_init=tt.TT_INIT_ABOVE,
+                                             above=True),
             "autotune": tuned}
 
 
@@ -538,16 +547,19 @@ def unbatched_leg(args, w, dev, world):
             "sources": len(ms), "note": "one source per step, same kernels and graph"}
 
 
-def start_bound(gp, rel=3e-3):
+def start_bound(gp, rel=3e-3, scheme=0, cold_init=0, above=False):
     """How many sweeps an ideal warm start could save: the forward solve started from the
-    converged tau of a cold solve times (1 + rel * a smooth field of unit amplitude, one
-    sinusoid per axis with a phase per source), the same tolerance, against the cold solve.
+    converged tau of a solve from opts.init = cold_init times (1 + rel * f), f a smooth field
+    of unit amplitude (one sinusoid per axis with a phase per source; |f| when above, so that
+    the start lies above the solution), the same tolerance, against that solve.
     LF sweeping contracts the error at a roughly fixed rate and its slow last phase sits
-    next to the downstream faces, so the count depends little on the starting error."""
+    next to the downstream faces, so the count depends little on the starting error. The
+    Godunov update converges fast from any start above the solution (opts.init = 3), which
+    leaves an ideal predictor little to save."""
     torch, tt = gp.torch, gp.tt
     g = gp.w.grid
     B = gp.w.n_src
-    o = tt.default_opts(tt.TT_F32, fwd_groups=gp.opts.fwd_groups)
+    o = tt.default_opts(tt.TT_F32, fwd_groups=gp.opts.fwd_groups, scheme=scheme, init=cold_init)
     tau = torch.empty(g.shape + (B,), dtype=torch.float32, device=gp.dev)
     it_cold = tt.tt_forward(gp.ctx, gp.model, gp.w.src, tau, None, o)
     ms_cold = tt.tt_get_stats(gp.ctx, tt.TT_STATS_FORWARD)["sweep_ms"]
@@ -555,8 +567,9 @@ def start_bound(gp, rel=3e-3):
     ph = torch.linspace(0, 2 * np.pi, B, device=gp.dev)
     f = (torch.sin(ax[0][:, None, None, None] + ph) * torch.sin(2 * ax[1][None, :, None, None] + ph)
          * torch.sin(3 * ax[2][None, None, :, None] + ph))
-    tau.mul_(1.0 + rel * f)
-    o.init = 1
+    tau.mul_(1.0 + rel * (f.abs() if above else f))
+    del f
+    o.init = tt.TT_INIT_GIVEN
     it_warm = tt.tt_forward(gp.ctx, gp.model, gp.w.src, tau, None, o)
     ms_warm = tt.tt_get_stats(gp.ctx, tt.TT_STATS_FORWARD)["sweep_ms"]
     return {"relative_start_error": rel, "iters_fwd_mean_cold": float(it_cold.mean()),
@@ -564,7 +577,8 @@ def start_bound(gp, rel=3e-3):
             "iters_fwd_max": int(it_warm.max()), "forward_ms_cold": ms_cold,
             "forward_ms": ms_warm,
             "note": "forward solve started from the converged tau with a smooth relative error "
-                    "of %g (an ideal predictor's bound)" % rel}
+                    "of %g%s (an ideal predictor's bound), against the start opts.init = %d"
+                    % (rel, " above the solution" if above else "", cold_init)}
 
 
 def warm_leg(args, gp, world):

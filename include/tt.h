@@ -61,6 +61,8 @@ typedef enum {
 
 typedef enum { TT_F32 = 0, TT_F64 = 1 } tt_dtype;
 typedef enum { TT_GEOM_SPHERICAL = 0, TT_GEOM_FLAT = 1 } tt_geometry;
+/* Values of tt_opts.init (the forward's starting tau). */
+typedef enum { TT_INIT_ONE = 0, TT_INIT_GIVEN = 1, TT_INIT_NET = 2, TT_INIT_ABOVE = 3 } tt_init;
 
 /* Study region (Sec. 2.1 problem statement; Sec. 4 for the spherical parameterisation).
  * TT_GEOM_FLAT is a Cartesian test geometry: theta and phi become lengths R_E*theta and
@@ -107,7 +109,14 @@ typedef struct {
     double tol_adj;         /* stop when the largest |P change| <= tol_adj * max |P| */
     int max_iter_fwd, max_iter_adj;
     int init;               /* tt_forward: 0 = start from tau = 1, 1 = start from the tau passed
-                               in, 2 = start from the warm-start network (tt_net_set_weights) */
+                               in, 2 = start from the warm-start network (tt_net_set_weights),
+                               3 = start from above: every node outside the fixed set starts
+                               at 2 hi / lo, hi = max s / sqrt(1 - 2 g), lo = min s /
+                               sqrt(1 + 2 g), g = sqrt(xi^2 + eta^2) over the model's nodes
+                               (twice a straight-ray bound of tau; computed on the device).
+                               The fast sweeping method's own start: the Godunov update then
+                               only lowers tau, and converges in fewer iterations than from
+                               tau = 1. Every start reaches the same fixed point. */
     long long spin_limit_ns;/* bound on every device-side wait; 0 = 2 s */
     int launch_blocks;      /* persistent sweep launch: 0 = automatic, else at most this many
                                blocks (results do not depend on it) */

@@ -24,6 +24,7 @@ LIB_PATH = os.path.join(_HERE, "libttgb.so")
 
 TT_OK, TT_EINVAL, TT_ENOTCONVERGED, TT_ECUDA, TT_ETIMEOUT, TT_ENOMEM = range(6)
 TT_F32, TT_F64 = 0, 1
+TT_INIT_ONE, TT_INIT_GIVEN, TT_INIT_NET, TT_INIT_ABOVE = 0, 1, 2, 3  # tt_opts.init
 STATUS_NAMES = {0: "TT_OK", 1: "TT_EINVAL", 2: "TT_ENOTCONVERGED", 3: "TT_ECUDA",
                 4: "TT_ETIMEOUT", 5: "TT_ENOMEM"}
 TT_MAX_BATCH = 4096

@@ -81,6 +81,9 @@ struct tt_ctx {
 namespace {
 
 constexpr long long kDefaultSpinNs = 2000000000LL;
+// Device flags of a context or plan: [0] model, [1] data index, [2] receiver position,
+// [3] network wait (read back after each call); [4], [5] the start-from-above bound.
+constexpr int kFlagInts = 6;
 // Largest per-(node, source) coefficient array the adjoint keeps in its workspace.
 constexpr size_t kCoefBudgetBytes = 64ull << 30;
 // Largest factor cache (1/T0 and grad T0 / T0 per node and source) one forward slice keeps.
@@ -326,7 +329,7 @@ tt_status check_opts(tt_ctx *ctx, const tt_opts *o) {
         return fail(ctx, TT_EINVAL, "tolerances must be > 0 and iteration limits >= 1");
     if (o->sweep_schedule < 0 || o->sweep_schedule > 1 + kNumTileShapes)
         return fail(ctx, TT_EINVAL, "sweep_schedule %d unknown", o->sweep_schedule);
-    if (o->init < 0 || o->init > 2) return fail(ctx, TT_EINVAL, "init %d unknown", o->init);
+    if (o->init < 0 || o->init > 3) return fail(ctx, TT_EINVAL, "init %d unknown", o->init);
     if (o->scheme < 0 || o->scheme > 2) return fail(ctx, TT_EINVAL, "scheme %d unknown", o->scheme);
     if (o->fwd_slots < 0) return fail(ctx, TT_EINVAL, "fwd_slots %d < 0", o->fwd_slots);
     if (o->fwd_groups < 0 || o->fwd_groups > kMaxBarrierGroups)
@@ -415,7 +418,7 @@ template <typename F> tt_status work_from_ctx(tt_ctx *ctx, Work<F> &W, int B, in
     ENSURE(ctx->iters, sizeof(int) * (size_t)B);
     ENSURE(ctx->nact, sizeof(int) * kMaxBarrierGroups);
     ENSURE(ctx->bar, sizeof(BarrierState) * kMaxBarrierGroups);
-    ENSURE(ctx->flags, 4 * sizeof(int));
+    ENSURE(ctx->flags, kFlagInts * sizeof(int));
     W.src = (SrcC *)ctx->src.p;
     W.tabT = (Vec2<F> *)ctx->tabT.p;
     W.tabP = (Vec2<F> *)ctx->tabP.p;
@@ -591,8 +594,11 @@ tt_status enq_forward(tt_ctx *ctx, Work<F> &W, const tt_model *m, int B, void *d
         if ((s = enq_warm_start<F>(ctx, W, m, B, (F *)d_tau, spin_ns(o))) != TT_OK) return s;
         CK(record(ctx, ctx->ev_net[1]));
     }
+    if (o->init == 3)
+        CK(run_upper_start<F>(g, B, m->d_s, m->d_xi, m->d_eta, (F *)d_tau,
+                              (unsigned *)(W.flags + 4), ctx->st));
     CK(run_tau_init<F>(g, B, W.src, (F *)d_tau, o->init == 0, ctx->st));
-    ctx->launches += 1 + (o->init == 0 ? 2 : 1);
+    ctx->launches += 1 + (o->init == 0 ? 2 : o->init == 3 ? 3 : 1);
 
     // Tile schedules stage 32 sources per task with TMA: they need B >= 32 and rows of tau
     // (B values) that are a multiple of 16 bytes. Automatic: node hyperplanes.
@@ -1216,7 +1222,7 @@ tt_status tt_misfit(tt_ctx *ctx, const void *d_T, int dtype, const tt_data *d, d
     if (!d_T || !d_R) return fail(ctx, TT_EINVAL, "tt_misfit: NULL argument");
     if (dtype != TT_F32 && dtype != TT_F64) return fail(ctx, TT_EINVAL, "bad dtype %d", dtype);
     const int S = 8 * d->n_rec;
-    ENSURE(ctx->flags, 4 * sizeof(int));
+    ENSURE(ctx->flags, kFlagInts * sizeof(int));
     ENSURE(ctx->rpts, sizeof(PointD) * (size_t)d->n_rec);
     ENSURE(ctx->cq, sizeof(long long) * S);
     ENSURE(ctx->wq, sizeof(double) * S);
@@ -1280,7 +1286,7 @@ tt_status tt_misfit_cr(tt_ctx *ctx, const tt_cr_data *d, const double *d_Tr, dou
                     d->n_rec);
     if (d->n_entries > 0 && (!d->d_other || !d->d_dtobs || !d->d_w))
         return fail(ctx, TT_EINVAL, "tt_misfit_cr: NULL entry arrays");
-    ENSURE(ctx->flags, 4 * sizeof(int));
+    ENSURE(ctx->flags, kFlagInts * sizeof(int));
     int *bad = (int *)ctx->flags.p + 1;
     CK(cudaMemsetAsync(bad, 0, sizeof(int), ctx->st));
     CK(run_misfit_cr(d->n_src, d->n_rec, d->d_off, d->d_other, d->d_dtobs, d->d_w, d->gamma, d_Tr,
@@ -1317,7 +1323,7 @@ tt_status tt_field_at_points(tt_ctx *ctx, const void *d_G, int dtype, int n_fiel
     if (n_fields < 1 || n_fields > TT_MAX_BATCH || n_pts < 1 || n_pts > (1 << 24))
         return fail(ctx, TT_EINVAL, "tt_field_at_points: n_fields %d or n_pts %d out of range",
                     n_fields, n_pts);
-    ENSURE(ctx->flags, 4 * sizeof(int));
+    ENSURE(ctx->flags, kFlagInts * sizeof(int));
     int *bad = (int *)ctx->flags.p + 1;
     CK(cudaMemsetAsync(bad, 0, sizeof(int), ctx->st));
     CK(dtype == TT_F32 ? run_field_at_points<float>(ctx->g, n_fields, n_pts, d_G, d_pts, d_val,
@@ -1342,7 +1348,7 @@ tt_status tt_misfit_table(tt_ctx *ctx, const double *d_val, const double *d_otim
     if (d->n_rec < 1) return fail(ctx, TT_EINVAL, "need at least one receiver");
     if ((size_t)d->n_rec * 2 * 4 * sizeof(double) > 200 * 1024)
         return fail(ctx, TT_EINVAL, "n_rec = %d too large for the misfit kernel", d->n_rec);
-    ENSURE(ctx->flags, 4 * sizeof(int));
+    ENSURE(ctx->flags, kFlagInts * sizeof(int));
     int *bad = (int *)ctx->flags.p + 1;
     CK(cudaMemsetAsync(bad, 0, sizeof(int), ctx->st));
     CK(run_misfit_table(d->n_src, d->n_rec, d_val, d_otime, *d, d_Tr, d_chi, d_R, bad, ctx->st));
@@ -1488,7 +1494,7 @@ tt_status forward_tele_impl(tt_ctx *ctx, const tt_model *m, int n_ev, void *d_T,
     ENSURE(ctx->iters, sizeof(int) * (size_t)n_ev);
     ENSURE(ctx->nact, sizeof(int) * kMaxBarrierGroups);
     ENSURE(ctx->bar, sizeof(BarrierState) * kMaxBarrierGroups);
-    ENSURE(ctx->flags, 4 * sizeof(int));
+    ENSURE(ctx->flags, kFlagInts * sizeof(int));
     NodeRec<F> *rec = (NodeRec<F> *)ctx->rec.p;
     int *conv = (int *)ctx->conv.p, *iters = (int *)ctx->iters.p, *flags = (int *)ctx->flags.p;
     BarrierState *bar = (BarrierState *)ctx->bar.p;
@@ -1971,7 +1977,7 @@ tt_status tt_net_infer(tt_ctx *ctx, const float *d_x, int n_grids, float *d_y) {
     const size_t M = net_grid_rows(g) * n_grids;
     ENSURE(ctx->net_a, sizeof(__nv_bfloat16) * kNetHidden * M);
     ENSURE(ctx->net_b, sizeof(__nv_bfloat16) * kNetHidden * M);
-    ENSURE(ctx->flags, 4 * sizeof(int));
+    ENSURE(ctx->flags, kFlagInts * sizeof(int));
     int *err = (int *)ctx->flags.p + 3;
     CK(cudaMemsetAsync(err, 0, sizeof(int), ctx->st));
     CK(run_net_infer(ConvDims{n_grids, g.nr, g.nt, g.np}, (const float *)ctx->net_theta.p,
@@ -2081,7 +2087,7 @@ tt_status tt_net_loss_grad_tc(tt_ctx *ctx, const float *d_theta, const float *d_
     ENSURE(ctx->net_dy, sizeof(float) * M);
     ENSURE(ctx->net_part, sizeof(float) * wgrad_partial_floats());
     ENSURE(ctx->net_scr, sizeof(double) * 4096);
-    ENSURE(ctx->flags, 4 * sizeof(int));
+    ENSURE(ctx->flags, kFlagInts * sizeof(int));
     if (!ctx->h_loss) CK(cudaMallocHost((void **)&ctx->h_loss, sizeof(double)));
     int *err = (int *)ctx->flags.p + 3;
     double *loss = (double *)ctx->net_scr.p + 4000;
@@ -2182,7 +2188,7 @@ template <typename F> tt_status plan_alloc(tt_plan *p, Work<F> &W) {
     TTGB_GET(conv_a, sizeof(int) * B);
     TTGB_GET(iters_a, sizeof(int) * B);
     TTGB_GET(nact, sizeof(int) * kMaxBarrierGroups);
-    TTGB_GET(flags, 4 * sizeof(int));
+    TTGB_GET(flags, kFlagInts * sizeof(int));
     TTGB_GET(bar, sizeof(BarrierState) * kMaxBarrierGroups);
     TTGB_GET(cq, sizeof(long long) * S);
     TTGB_GET(wq, sizeof(double) * S);

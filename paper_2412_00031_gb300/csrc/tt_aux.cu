@@ -153,6 +153,65 @@ __global__ void fix_set_kernel(GridC g, const SrcC *S, int n_src, F *tau) {
     tau[node_index(g, i, j, k) * n_src + b] = (F)1;
 }
 
+// Start from above (opts.init = 3). The fast sweeping method starts from large values
+// outside the fixed set, so that the upwind (Godunov) update only lowers them toward the
+// solution. The value used is twice a bound of tau. Along the straight ray of length L from
+// the source, T <= max_ray(s N) L, where N(d) = sqrt(d^T M^-1 d) is the direction factor of
+// the local metric M of the Hamiltonian (eigenvalues 1 and 1 +- 2 g, g = sqrt(xi^2 + eta^2)).
+// The factor is T0 = s0 N0(d) L, so tau <= hi / lo with
+//   hi = max_n s_n / sqrt(1 - 2 g_n),   lo = min_n s_n / sqrt(1 + 2 g_n).
+// The factor 2 leaves room for the discretisation error. Where the start is not above the
+// solution the sweep still reaches the same fixed point, only in more iterations.
+// hilo[0] and hilo[1] hold hi and lo as the bits of positive floats (their unsigned order is
+// the float order); the caller sets them to 0 and to a large float first.
+template <typename F>
+__global__ void upper_bound_kernel(long long N, const F *s, const F *xi, const F *eta,
+                                   unsigned *hilo) {
+    float hi = 0.f, lo = 3.0e38f;
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N;
+         n += (long long)gridDim.x * blockDim.x) {
+        const float sv = (float)s[n], a = (float)xi[n], b = (float)eta[n];
+        const float g2 = sqrtf(a * a + b * b) * 2.f;
+        if (sv > 0.f) {
+            hi = fmaxf(hi, sv / sqrtf(fmaxf(1.f - g2, 1e-6f)));
+            lo = fminf(lo, sv / sqrtf(1.f + g2));
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    }
+    __shared__ float shi[32], slo[32];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    if (lane == 0) {
+        shi[w] = hi;
+        slo[w] = lo;
+    }
+    __syncthreads();
+    if (w == 0) {
+        hi = lane < nw ? shi[lane] : 0.f;
+        lo = lane < nw ? slo[lane] : 3.0e38f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+            lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        }
+        if (lane == 0) {
+            atomicMax(hilo, __float_as_uint(hi));
+            atomicMin(hilo + 1, __float_as_uint(lo));
+        }
+    }
+}
+
+template <typename F>
+__global__ void upper_fill_kernel(F *tau, long long n, const unsigned *hilo) {
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const float hi = __uint_as_float(hilo[0]), lo = __uint_as_float(hilo[1]);
+    tau[q] = (F)(2.f * hi / lo);
+}
+
 // T = T0 tau at every (node, source).
 template <typename F>
 __global__ void traveltime_kernel(GridC g, int B, const SrcC *src, const Vec2<F> *tabT,
@@ -448,6 +507,19 @@ cudaError_t run_tau_init(const GridC &g, int n_src, const SrcC *d_src, F *tau, b
 }
 
 template <typename F>
+cudaError_t run_upper_start(const GridC &g, int n_src, const void *s, const void *xi,
+                            const void *eta, F *tau, unsigned *hilo, cudaStream_t st) {
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(hilo, 0, sizeof(unsigned), st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(hilo + 1, 0x7f, sizeof(unsigned), st)) != cudaSuccess) return e;
+    const unsigned nb = blocks_for(g.N, 256);
+    upper_bound_kernel<F><<<nb < 1216u ? nb : 1216u, 256, 0, st>>>(
+        g.N, (const F *)s, (const F *)xi, (const F *)eta, hilo);
+    upper_fill_kernel<F><<<blocks_for(g.N * n_src, 256), 256, 0, st>>>(tau, g.N * n_src, hilo);
+    return cudaGetLastError();
+}
+
+template <typename F>
 cudaError_t run_traveltime(const GridC &g, int B, const SrcC *src, const Vec2<F> *tabT,
                            const Vec2<F> *tabP, const F *rad, const F *cost, const F *sint,
                            const F *tau, F *T, cudaStream_t st) {
@@ -538,6 +610,8 @@ cudaError_t run_kernel_accum(const GridC &g, int B, const void *s, const void *T
                                              NodeRec<F> *, int *, cudaStream_t);               \
     template cudaError_t run_tau_init<F>(const GridC &, int, const SrcC *, F *, bool,          \
                                          cudaStream_t);                                        \
+    template cudaError_t run_upper_start<F>(const GridC &, int, const void *, const void *,    \
+                                            const void *, F *, unsigned *, cudaStream_t);      \
     template cudaError_t run_traveltime<F>(const GridC &, int, const SrcC *, const Vec2<F> *,  \
                                            const Vec2<F> *, const F *, const F *, const F *,   \
                                            const F *, F *, cudaStream_t);                      \

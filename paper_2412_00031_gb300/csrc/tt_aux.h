@@ -30,6 +30,11 @@ cudaError_t run_node_records(const GridC &g, const void *s, const void *xi, cons
 template <typename F>
 cudaError_t run_tau_init(const GridC &g, int n_src, const SrcC *d_src, F *tau, bool fill,
                          cudaStream_t st);
+// Fills tau [N][n_src] with the start from above of opts.init = 3 (twice a bound of tau
+// from the model's slowness and anisotropy); hilo: 2 unsigned of device scratch.
+template <typename F>
+cudaError_t run_upper_start(const GridC &g, int n_src, const void *s, const void *xi,
+                            const void *eta, F *tau, unsigned *hilo, cudaStream_t st);
 template <typename F>
 cudaError_t run_traveltime(const GridC &g, int B, const SrcC *src, const Vec2<F> *tabT,
                            const Vec2<F> *tabP, const F *rad, const F *cost, const F *sint,

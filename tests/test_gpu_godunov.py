@@ -11,7 +11,10 @@ oracle's Godunov solver (reading R14), through the C ABI (needs a GB300).
   sources;
 - the anisotropic solver (opts.scheme = 2, reading R16): FP64 batch to 1e-10 of the oracle
   with the same iteration counts, FP32 batch to the 1e-5 bar with bitwise launch variants,
-  and an anisotropic 81^3 checkerboard at full size.
+  and an anisotropic 81^3 checkerboard at full size;
+- the start from above (opts.init = 3), with either update: FP64 batch to 1e-10 of the
+  oracle started from the same value, with its iteration counts; FP32 batch to the 1e-5 bar
+  of the oracle's converged solve, bitwise across launch variants.
 """
 import numpy as np
 import pytest
@@ -171,3 +174,61 @@ def test_anisotropic_81_batch_against_oracle_solves(tt):
         assert conv
         assert rel_linf(out["T"][..., b], T) <= 1e-5
     assert int(np.max(out["iters_fwd"])) <= 12
+
+
+# ---- the start from above (opts.init = 3) ----
+
+def _upper_start(w):
+    """The value opts.init = 3 starts from, restated in FP32: twice max s / sqrt(1 - 2 g) over
+    min s / sqrt(1 + 2 g), g = sqrt(xi^2 + eta^2) over the model's nodes."""
+    s, xi, eta = (np.asarray(a, dtype=np.float32) for a in (w.s, w.xi, w.eta))
+    g2 = np.sqrt(xi * xi + eta * eta) * np.float32(2)
+    hi = np.max(s / np.sqrt(np.maximum(np.float32(1) - g2, np.float32(1e-6))))
+    lo = np.min(s / np.sqrt(np.float32(1) + g2))
+    return float(np.float32(2) * hi / lo)
+
+
+@pytest.mark.parametrize("scheme,name", [(2, "godunov_aniso"), (0, "lf")])
+def test_start_from_above_fp64_matches_the_oracle_from_the_same_start(tt, scheme, name):
+    import oracle as O
+    w = I.small_case(113, shape=(13, 14, 15), n_src=5)
+    assert np.abs(w.xi).max() > 0 and np.abs(w.eta).max() > 0
+    o = tt.default_opts(tt.TT_F64, scheme=scheme, init=tt.TT_INIT_ABOVE, tol_fwd=1e-12,
+                        max_iter_fwd=500)
+    out = gpu_solve(w, "f64", opts=o, steps=("fwd",))
+    g = w.grid.as_dict()
+    start = np.full(w.grid.shape, _upper_start(w))
+    assert start.flat[0] > 1.5
+    for b in range(w.n_src):
+        _, T, it, conv, _ = O.forward(g, w.s, w.xi, w.eta, w.src[b], tol=1e-12, max_iter=500,
+                                      tau_init=start, scheme=name)
+        assert conv
+        assert rel_linf(out["T"][..., b], T) <= 1e-10
+        assert abs(int(out["iters_fwd"][b]) - it) <= 1
+
+
+def test_start_from_above_fp32_meets_the_bar_and_variants_are_bitwise(tt):
+    """On this small grid both starts need about 3 iterations; the saving from above shows
+    at the benchmark size (the full-size test)."""
+    import oracle as O
+    w = I.small_case(114, shape=(17, 16, 18), n_src=40)
+    one = gpu_solve(w, "f32", opts=tt.default_opts(tt.TT_F32, scheme=2), steps=("fwd",))
+    ref = gpu_solve(w, "f32", opts=tt.default_opts(tt.TT_F32, scheme=2, init=tt.TT_INIT_ABOVE),
+                    steps=("fwd",))
+    s, xi, eta = rounded_model(w, "f32")
+    g = w.grid.as_dict()
+    for b in (0, 19, 39):
+        _, T, _, conv, _ = O.forward(g, s, xi, eta, w.src[b], tol=1e-10, max_iter=200,
+                                     scheme="godunov_aniso")
+        assert conv
+        assert rel_linf(ref["T"][..., b], T) <= 1e-5
+    print("\nGodunov iterations: from tau = 1 mean %.2f max %d, from above mean %.2f max %d" %
+          (np.mean(one["iters_fwd"]), np.max(one["iters_fwd"]), np.mean(ref["iters_fwd"]),
+           np.max(ref["iters_fwd"])))
+    assert np.max(ref["iters_fwd"]) <= np.max(one["iters_fwd"]) + 1
+    for kw in ({"fwd_groups": 1}, {"fwd_groups": 3}, {"fwd_slots": 32}):
+        out = gpu_solve(w, "f32", opts=tt.default_opts(tt.TT_F32, scheme=2,
+                                                       init=tt.TT_INIT_ABOVE, **kw),
+                        steps=("fwd",))
+        assert np.array_equal(out["tau"], ref["tau"]), kw
+        assert np.array_equal(out["iters_fwd"], ref["iters_fwd"]), kw
