@@ -416,9 +416,9 @@ def training_leg(dev, steps=10, warmup=3):
     return {"batch": "%d grids of 81^3" % len(src), "fp32_ms_per_step": out["fp32"],
             "tensor_core_ms_per_step": out["tensor_cores"],
             "speedup": out["fp32"] / out["tensor_cores"],
-            "note": "loss and gradient of the warm-start network; tensor cores: forward and "
-                    "input-gradient convolutions on tcgen05 (BF16 operands), weight gradients "
-                    "on the CUDA cores"}
+            "note": "loss and gradient of the warm-start network; tensor cores: the forward, "
+                    "input-gradient and weight-gradient convolutions on tcgen05 (BF16 operands, "
+                    "FP32 accumulation)"}
 
 
 def godunov_leg(args, gp, world):

@@ -462,11 +462,12 @@ tt_status tt_net_forward(tt_ctx *ctx, const float *d_theta, const float *d_x, in
 tt_status tt_net_loss_grad(tt_ctx *ctx, const float *d_theta, const float *d_x,
                            const float *d_target, const float *d_mask, int n_grids,
                            float *d_grad, double *h_loss);
-/* tt_net_loss_grad with the convolutions on the tensor cores: the forward pass and the
+/* tt_net_loss_grad with the convolutions on the tensor cores: the forward pass, the
  * gradients through the layers' inputs (transposed convolutions, gated by the ReLU of the
- * layer below) run on tcgen05 with BF16 operands (weights, activations and gradients rounded
- * to BF16) and FP32 accumulation in tensor memory; the weight gradients are FP32 sums on the
- * CUDA cores over those BF16 rows. Same arguments and outputs as tt_net_loss_grad; the
+ * layer below) and the weight and bias gradients (input rows times output-gradient rows,
+ * summed over the rows) run on tcgen05 with BF16 operands (weights, activations and
+ * gradients rounded to BF16) and FP32 accumulation in tensor memory; the per-SM sums are
+ * added in FP64 in a fixed order. Same arguments and outputs as tt_net_loss_grad; the
  * result is that gradient to BF16 accuracy (bar stated in the tests). Deterministic.
  * TT_ETIMEOUT if a device-side wait exceeds 2 s. */
 tt_status tt_net_loss_grad_tc(tt_ctx *ctx, const float *d_theta, const float *d_x,

@@ -155,66 +155,6 @@ __global__ void __launch_bounds__(kWgThreads)
     }
 }
 
-// The same stage 1 over the padded row layout of the tensor-core training path: positions are
-// rows of nb grids, a tap is the row shift (di - 1) Si + (dj - 1) Sj + dk - 1, inputs and
-// gradients are BF16 rows of in_ch and g_ch channels (padding rows hold zeros). The bias
-// block (t = 27) sums the gradient rows.
-template <int COUT>
-__global__ void __launch_bounds__(kWgThreads)
-    conv3d_wgrad_rows_kernel(int nb, int R, int Sj, int Si, int cin, int in_ch, int g_ch,
-                             const __nv_bfloat16 *__restrict__ in,
-                             const __nv_bfloat16 *__restrict__ g, float *__restrict__ partial) {
-    __shared__ float s_x[kWgChunk * 33];
-    __shared__ float s_dy[kWgChunk * COUT];
-    const int r = blockIdx.x, Rb = gridDim.x, t = blockIdx.y;
-    const bool is_bias = t == 27;
-    const int rows = is_bias ? 1 : cin;
-    const int E = rows * COUT;
-    const int shift = (t / 9 - 1) * Si + ((t / 3) % 3 - 1) * Sj + (t % 3 - 1);
-    const long long chunks_per_grid = (R + kWgChunk - 1) / kWgChunk;
-    const long long chunks = chunks_per_grid * nb;
-    float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-    for (long long ch = r; ch < chunks; ch += Rb) {
-        const int b = (int)(ch / chunks_per_grid);
-        const int p0 = (int)((ch - (long long)b * chunks_per_grid) * kWgChunk);
-        const int np = min(kWgChunk, R - p0);
-        const long long base = (long long)b * R;
-        __syncthreads();
-        for (int e = threadIdx.x; e < kWgChunk * COUT; e += kWgThreads) {
-            const int q = e / COUT, co = e - q * COUT;
-            s_dy[e] = q < np ? __bfloat162float(g[(base + p0 + q) * g_ch + co]) : 0.0f;
-        }
-        if (!is_bias) {
-            for (int e = threadIdx.x; e < kWgChunk * cin; e += kWgThreads) {
-                const int q = e / cin, c = e - q * cin;
-                const int src = p0 + q + shift;
-                s_x[q * 33 + c] = q < np && src >= 0 && src < R
-                                      ? __bfloat162float(in[(base + src) * in_ch + c])
-                                      : 0.0f;
-            }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int e = threadIdx.x + k * kWgThreads;
-            if (e >= E) break;
-            const int ci = e / COUT, co = e - ci * COUT;
-            float a = acc[k];
-            if (is_bias) {
-                for (int q = 0; q < np; ++q) a += s_dy[q * COUT + co];
-            } else {
-                for (int q = 0; q < np; ++q) a = fmaf(s_x[q * 33 + ci], s_dy[q * COUT + co], a);
-            }
-            acc[k] = a;
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const int e = threadIdx.x + k * kWgThreads;
-        if (e < E) partial[((size_t)r * 28 + t) * 1024 + e] = acc[k];
-    }
-}
-
 // Weight gradient, stage 2: fixed-order sum over the R partial rows.
 __global__ void wgrad_reduce_kernel(int cin, int cout, int R, const float *__restrict__ partial,
                                     float *__restrict__ gw, float *__restrict__ gb) {
@@ -386,21 +326,11 @@ cudaError_t run_conv3d_wgrad(const ConvDims &d, int cin, int cout, const float *
     return cudaGetLastError();
 }
 
-cudaError_t run_conv3d_wgrad_rows(int nb, int R, int Sj, int Si, int cin, int in_ch, int cout,
-                                  int g_ch, const __nv_bfloat16 *in, const __nv_bfloat16 *g,
-                                  float *partial, float *gw, float *gb, cudaStream_t st) {
-    if (cin > 32 || cin > in_ch || cout > g_ch || cin * cout > 1024) return cudaErrorInvalidValue;
-    dim3 grid(kWgradBlocks, 28);
-    if (cout == 32)
-        conv3d_wgrad_rows_kernel<32><<<grid, kWgThreads, 0, st>>>(nb, R, Sj, Si, cin, in_ch, g_ch,
-                                                                 in, g, partial);
-    else if (cout == 1)
-        conv3d_wgrad_rows_kernel<1><<<grid, kWgThreads, 0, st>>>(nb, R, Sj, Si, cin, in_ch, g_ch,
-                                                                in, g, partial);
-    else
-        return cudaErrorInvalidValue;
+cudaError_t run_wgrad_reduce(int cin, int cout, int parts, const float *partial, float *gw,
+                             float *gb, cudaStream_t st) {
+    if (parts < 1 || parts > kWgradBlocks || cin * cout > 1024) return cudaErrorInvalidValue;
     const int n = 27 * cin * cout + cout;
-    wgrad_reduce_kernel<<<blocks_of(n, 256), 256, 0, st>>>(cin, cout, kWgradBlocks, partial, gw, gb);
+    wgrad_reduce_kernel<<<blocks_of(n, 256), 256, 0, st>>>(cin, cout, parts, partial, gw, gb);
     return cudaGetLastError();
 }
 

@@ -76,10 +76,10 @@ cudaError_t run_net_weight_images(const float *theta, __nv_bfloat16 *img, cudaSt
 cudaError_t run_net_infer(const ConvDims &d, const float *theta, const __nv_bfloat16 *img,
                           const float *x, __nv_bfloat16 *a, __nv_bfloat16 *b, float *y, int n_sm,
                           int *err, unsigned long long limit_ns, cudaStream_t st);
-// Training with the convolutions on the tensor cores (tt_umma.cu): the forward pass and the
-// input gradients (transposed convolutions gated by the ReLU of the layer below) run on
-// tcgen05 with BF16 operands and FP32 accumulation, over the padded row layout; the weight
-// gradients are FP32 sums on the CUDA cores over the BF16 rows (run_conv3d_wgrad_rows).
+// Training with the convolutions on the tensor cores (tt_umma.cu): the forward pass, the
+// input gradients (transposed convolutions gated by the ReLU of the layer below) and the
+// weight and bias gradients (input rows times output-gradient rows, summed over the rows)
+// run on tcgen05 with BF16 operands and FP32 accumulation, over the padded row layout.
 // Writes the masked MSE to *loss (device double) and its gradient to grad (FP32, overwritten).
 // Workspace: img (net_weight_image_elems), timg (net_tweight_image_elems), wt (27 x 32 x 32
 // floats), rows (net_train_row_elems), y and dy (nb x nodes floats), partial
@@ -92,14 +92,10 @@ cudaError_t run_net_loss_grad_tc(const ConvDims &d, const float *theta, const fl
                                  float *wt, __nv_bfloat16 *rows, float *y, float *dy,
                                  float *partial, double *scratch, int n_sm, int *err,
                                  unsigned long long limit_ns, cudaStream_t st);
-// Weight gradient of one layer over rows (nb grids of R rows; a tap is the row shift
-// (di - 1) Si + (dj - 1) Sj + dk - 1): gw[t][ci][co] = sum_r in[r + shift(t)][ci] g[r][co],
-// gb[co] = sum_r g[r][co]; in has in_ch BF16 channels per row (ci < cin), g has g_ch (co <
-// cout). Rows outside [0, R) read as zero. FP32 sums in a fixed order (partial, then
-// FP64 over the partial rows).
-cudaError_t run_conv3d_wgrad_rows(int nb, int R, int Sj, int Si, int cin, int in_ch, int cout,
-                                  int g_ch, const __nv_bfloat16 *in, const __nv_bfloat16 *g,
-                                  float *partial, float *gw, float *gb, cudaStream_t st);
+// Fixed-order sum of `parts` partial rows ([parts][28][1024]: rows t < 27 hold the taps'
+// [cin][cout] sums, row 27 the bias sums) into gw [27][cin][cout] and gb [cout] (FP64 sums).
+cudaError_t run_wgrad_reduce(int cin, int cout, int parts, const float *partial, float *gw,
+                             float *gb, cudaStream_t st);
 // Rounds every value to the nearest BF16 (kept in FP32 storage).
 cudaError_t run_round_bf16(int n, const float *in, float *out, cudaStream_t st);
 

@@ -528,6 +528,233 @@ __global__ void weight_image_kernel(const float *__restrict__ w, int cin, int co
     img[((size_t)q * 3 * NO + r) * C + cs * 8 + ci % 8] = __float2bfloat16_rn(v);
 }
 
+// ------------------------------------------------------------------------ weight gradients
+//
+// Training: the weight gradient of a layer with input rows X (C_in BF16 channels) and
+// output-gradient rows G (C_g channels),
+//   dW[t][ci][co] = sum_r X[r + s(di, dj) + dk - 1][ci] G[r][co],   t = 9 di + 3 dj + dk,
+// with s(di, dj) = (di - 1) Si + (dj - 1) Sj the row shift of the (di, dj) taps. Writing
+// r' = r + dk - 1 moves the dk shift onto G: dW[t] = sum_r' X[r' + s(di, dj)] G[r' - dk + 1],
+// r' over [-1, R + 1) (rows outside [0, R) are zero). A chunk of 64 rows r' is one GEMM step
+// with K = rows: A = the nine (di, dj) slabs of X rows, B = the three dk slabs of G rows. Both
+// are the row buffers as they are (channels contiguous), i.e. MN-major operands: an M group
+// of 128 stacks 128 / C_in slabs (one swizzle atom of C_in channels each, LBO apart), N is
+// C_g, and 8-row groups are SBO apart. Accumulator (dk, M group) holds, in TMEM lane
+// (slab, ci), the sums of its taps over this CTA's chunks. One slab position of the last M
+// group holds ones: its lanes collect sum_r G[r][co], the bias gradient (dk = 1 reads every
+// row of G once). Each CTA writes its sums as a partial row; wgrad_reduce sums the rows in a
+// fixed order, so the result is bitwise reproducible. Roles: warp 0 issues the tensor copies
+// into a ring of stages, warp 1 owns the tensor memory and issues the MMAs, warps 2-5 read
+// the accumulators once at the end. Every wait is bounded as in conv3d_tc_kernel.
+constexpr int kWgRows = 64;        // K rows of one chunk
+constexpr int kWgStages = 3;
+constexpr int kWgThreads = 192;
+constexpr int kWgTmemCols = 512;
+
+template <int KCI, int KCG> struct WgSmem {
+    static constexpr int CI = KCI * 8, CG = KCG * 8;             // channels of X and G rows
+    static constexpr int XROW = KCI * 16, GROW = KCG * 16;        // bytes of one row
+    static constexpr int SPG = 128 / CI;                          // slabs of one M group
+    static constexpr int MG = (9 + 1 + SPG - 1) / SPG;            // M groups: 9 slabs + ones
+    static constexpr int ONES = MG * SPG - 1;                     // slab position of the ones
+    static constexpr int XSLAB = kWgRows * XROW, GSLAB = kWgRows * GROW;
+    static constexpr int GOFF = MG * SPG * XSLAB;                 // G slabs within a stage
+    static constexpr int STAGE = GOFF + 3 * GSLAB;
+    static constexpr int BAR = kWgStages * STAGE;
+    static constexpr int NBAR = 2 * kWgStages + 2;                // full, empty, acc, drain
+    static constexpr int MISC = BAR + NBAR * 8;
+    static constexpr int TOTAL = MISC + 16 + 1024;
+    static constexpr unsigned XLAYOUT = XROW == 64 ? 4u : 6u, GLAYOUT = GROW == 64 ? 4u : 6u;
+    static constexpr int N = CG;
+};
+static_assert(WgSmem<4, 4>::TOTAL <= 227 * 1024 && WgSmem<4, 4>::STAGE % 1024 == 0 &&
+                  WgSmem<4, 2>::STAGE % 1024 == 0 && WgSmem<2, 4>::STAGE % 1024 == 0,
+              "weight-gradient stages: shared memory and swizzle-atom alignment");
+static_assert(3 * WgSmem<4, 4>::MG * WgSmem<4, 4>::N <= kWgTmemCols &&
+                  3 * WgSmem<2, 4>::MG * WgSmem<2, 4>::N <= kWgTmemCols,
+              "weight-gradient accumulators fit the tensor memory");
+
+// Shared-memory matrix descriptor of an MN-major operand with swizzle `layout`: swizzle atoms
+// of the MN dimension lbo bytes apart, 8-row groups of the K dimension sbo bytes apart.
+__device__ __forceinline__ unsigned long long mdesc_mn(unsigned addr, unsigned lbo, unsigned sbo,
+                                                       unsigned layout) {
+    return (unsigned long long)((addr >> 4) & 0x3FFFu) |
+           ((unsigned long long)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((unsigned long long)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46) |
+           ((unsigned long long)layout << 61);
+}
+
+// Instruction descriptor of kind::f16 with both operands MN-major (FP32 accumulator, BF16).
+template <int N> __host__ __device__ constexpr unsigned idesc_bf16_mn() {
+    return idesc_bf16<N>() | (1u << 15) | (1u << 16);
+}
+
+template <int N> __device__ __forceinline__ void tmem_ld_cols(unsigned taddr, float (&v)[N]);
+template <> __device__ __forceinline__ void tmem_ld_cols<16>(unsigned taddr, float (&v)[16]) {
+    unsigned r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int c = 0; c < 16; ++c) v[c] = __uint_as_float(r[c]);
+}
+template <> __device__ __forceinline__ void tmem_ld_cols<32>(unsigned taddr, float (&v)[32]) {
+    float a[16], b[16];
+    tmem_ld_cols<16>(taddr, a);
+    tmem_ld_cols<16>(taddr + 16, b);
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+        v[c] = a[c];
+        v[16 + c] = b[c];
+    }
+}
+
+template <int KCI, int KCG>
+__global__ void __launch_bounds__(kWgThreads, 1)
+    conv3d_wgrad_tc_kernel(const __grid_constant__ CUtensorMap mx,
+                           const __grid_constant__ CUtensorMap mgr, RowGeo G, int cin, int cout,
+                           float *__restrict__ partial, int *err, unsigned long long limit) {
+    using L = WgSmem<KCI, KCG>;
+    extern __shared__ unsigned char smem_raw[];
+    const unsigned raw = saddr(smem_raw);
+    const unsigned base = (raw + 1023u) & ~1023u;
+    unsigned char *sm = smem_raw + (base - raw);
+    const unsigned sBar = base + L::BAR;
+    unsigned *s_tmem = reinterpret_cast<unsigned *>(sm + L::MISC);
+    volatile int *s_abort = reinterpret_cast<volatile int *>(sm + L::MISC + 4);
+    auto full = [&](int s) { return sBar + 8u * s; };
+    auto empty = [&](int s) { return sBar + 8u * (kWgStages + s); };
+    const unsigned acc_full = sBar + 8u * (2 * kWgStages), drain = acc_full + 8u;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long cpg = (G.R + 2 + kWgRows - 1) / kWgRows;   // chunks of one grid
+    const long long total = (long long)G.nb * cpg;
+
+    // the ones slab of every stage (never overwritten by the copies)
+    for (int s = 0; s < kWgStages; ++s) {
+        uint4 *o = reinterpret_cast<uint4 *>(sm + s * L::STAGE + L::ONES * L::XSLAB);
+        for (int e = threadIdx.x; e < L::XSLAB / 16; e += kWgThreads)
+            o[e] = make_uint4(0x3F803F80u, 0x3F803F80u, 0x3F803F80u, 0x3F803F80u);  // BF16 1.0
+    }
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kWgStages; ++s) {
+            bar_init(full(s), 1);
+            bar_init(empty(s), 1);
+        }
+        bar_init(acc_full, 1);
+        bar_init(drain, 1);
+        *s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (warp == 1) {
+        __syncwarp();
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         saddr(s_tmem)),
+                     "r"(kWgTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tmem = *s_tmem;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // copier: per chunk, nine X slabs and three G slabs into one stage
+            int s = 0;
+            unsigned ph = 0, armed = 0, armed_par = 0;
+            for (long long c = blockIdx.x; c < total; c += gridDim.x) {
+                const int g = (int)(c / cpg);
+                const int r0 = (int)(c - (long long)g * cpg) * kWgRows - 1;
+                if (!bar_wait(empty(s), ph ^ 1u, limit, s_abort)) break;
+                bar_expect_tx(full(s), 9 * L::XSLAB + 3 * L::GSLAB);
+                const unsigned st = base + s * L::STAGE;
+                for (int q = 0; q < 9; ++q)
+                    tma_rows(st + q * L::XSLAB, &mx, r0 + (q / 3 - 1) * G.Si + (q % 3 - 1) * G.Sj,
+                             g, full(s));
+                for (int dk = 0; dk < 3; ++dk)
+                    tma_rows(st + L::GOFF + dk * L::GSLAB, &mgr, r0 - dk + 1, g, full(s));
+                armed |= 1u << s;
+                armed_par = (armed_par & ~(1u << s)) | (ph << s);
+                if (++s == kWgStages) { s = 0; ph ^= 1u; }
+            }
+            for (int q = 0; q < kWgStages; ++q)
+                if (armed >> q & 1u) bar_drain(full(q), (armed_par >> q) & 1u, limit);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr unsigned ID = idesc_bf16_mn<L::N>();
+            int s = 0;
+            unsigned ph = 0;
+            bool ok = true, first = true;
+            for (long long c = blockIdx.x; c < total; c += gridDim.x) {
+                if (!bar_wait(full(s), ph, limit, s_abort)) { ok = false; break; }
+                tc_fence_after();
+                const unsigned st = base + s * L::STAGE;
+                for (int dk = 0; dk < 3; ++dk)
+                    for (int mg = 0; mg < L::MG; ++mg)
+#pragma unroll
+                        for (int ks = 0; ks < kWgRows / 16; ++ks) {
+                            const unsigned long long ad =
+                                mdesc_mn(st + mg * L::SPG * L::XSLAB + ks * 16 * L::XROW, L::XSLAB,
+                                         8 * L::XROW, L::XLAYOUT);
+                            const unsigned long long bd =
+                                mdesc_mn(st + L::GOFF + dk * L::GSLAB + ks * 16 * L::GROW, L::GSLAB,
+                                         8 * L::GROW, L::GLAYOUT);
+                            mma_bf16(tmem + (unsigned)((dk * L::MG + mg) * L::N), ad, bd, ID,
+                                     !(first && ks == 0));
+                        }
+                mma_commit(empty(s));   // the stage is free once these MMAs have read it
+                first = false;
+                if (++s == kWgStages) { s = 0; ph ^= 1u; }
+            }
+            if (ok) mma_commit(acc_full);
+            mma_commit(drain);
+            bar_drain(drain, 0, limit);
+        }
+    } else {
+        // warps 2-5: TMEM lane quarter warp % 4; lane m = (slab within the M group, channel)
+        const int quarter = warp & 3;
+        const int m = quarter * 32 + lane;
+        const int p_in = m / L::CI, ch = m - p_in * L::CI;
+        if (epi_all(0, bar_wait(acc_full, 0, limit, s_abort))) {
+            tc_fence_after();
+            for (int dk = 0; dk < 3; ++dk)
+                for (int mg = 0; mg < L::MG; ++mg) {
+                    float v[L::N];
+                    tmem_ld_cols<L::N>(tmem + ((unsigned)(quarter * 32) << 16) +
+                                           (unsigned)((dk * L::MG + mg) * L::N),
+                                       v);
+                    const int p = mg * L::SPG + p_in;
+                    float *row = nullptr;
+                    if (p < 9 && ch < cin)
+                        row = partial + ((size_t)blockIdx.x * 28 + 3 * p + dk) * 1024 + ch * cout;
+                    else if (p == L::ONES && ch == 0 && dk == 1)
+                        row = partial + ((size_t)blockIdx.x * 28 + 27) * 1024;
+                    if (row)
+#pragma unroll
+                        for (int n = 0; n < L::N; ++n)
+                            if (n < cout) row[n] = v[n];
+                }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(kWgTmemCols)
+                     : "memory");
+    }
+    if (threadIdx.x == 0 && *s_abort) atomicExch(err, 1);
+}
+
 inline unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
 PFN_cuTensorMapEncodeTiled_v12000 map_encoder() {
@@ -548,14 +775,15 @@ PFN_cuTensorMapEncodeTiled_v12000 map_encoder() {
 }
 
 // Tensor map over rows of 8 KC BF16 channels: dims (channels, R rows, nb grids); a box is
-// 128 rows of one grid, swizzled as the descriptors expect.
-cudaError_t encode_rows(CUtensorMap *map, const void *base, const RowGeo &G, int KC) {
+// box_rows rows of one grid, swizzled as the descriptors expect.
+cudaError_t encode_rows(CUtensorMap *map, const void *base, const RowGeo &G, int KC,
+                        int box_rows = kTileRows) {
     PFN_cuTensorMapEncodeTiled_v12000 enc = map_encoder();
     if (!enc) return cudaErrorNotSupported;
     const cuuint64_t row = (cuuint64_t)KC * 16;
     cuuint64_t dims[3] = {(cuuint64_t)KC * 8, (cuuint64_t)G.R, (cuuint64_t)G.nb};
     cuuint64_t strides[2] = {row, row * (cuuint64_t)G.R};
-    cuuint32_t box[3] = {(cuuint32_t)KC * 8, (cuuint32_t)kTileRows, 1};
+    cuuint32_t box[3] = {(cuuint32_t)KC * 8, (cuuint32_t)box_rows, 1};
     cuuint32_t estr[3] = {1, 1, 1};
     const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), dims,
                            strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -582,6 +810,33 @@ cudaError_t launch_layer(const void *in, const RowGeo &G, const __nv_bfloat16 *w
         map, G, reinterpret_cast<const uint4 *>(wimg), bias, reinterpret_cast<const uint4 *>(gate),
         out, err, limit);
     return cudaGetLastError();
+}
+
+// Weight and bias gradients of one layer on the tensor cores: per-CTA partial rows, then the
+// fixed-order reduction into gw [27][cin][cout] and gb [cout].
+template <int KCI, int KCG>
+cudaError_t launch_wgrad(const void *in, const void *g, const RowGeo &G, int cin, int cout,
+                         float *partial, float *gw, float *gb, int n_sm, int *err,
+                         unsigned long long limit, cudaStream_t st) {
+    using L = WgSmem<KCI, KCG>;
+    if (cin > L::CI || cout > L::N || cin * cout > 1024) return cudaErrorInvalidValue;
+    CUtensorMap mx, mgr;
+    cudaError_t e = encode_rows(&mx, in, G, KCI, kWgRows);
+    if (e != cudaSuccess) return e;
+    if ((e = encode_rows(&mgr, g, G, KCG, kWgRows)) != cudaSuccess) return e;
+    // more than half the shared memory of an SM: one CTA per SM, which owns its TMEM
+    constexpr int smem = L::TOTAL > 120 * 1024 ? L::TOTAL : 120 * 1024;
+    const void *fn = (const void *)conv3d_wgrad_tc_kernel<KCI, KCG>;
+    if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) !=
+        cudaSuccess)
+        return e;
+    const long long total = (long long)G.nb * ((G.R + 2 + kWgRows - 1) / kWgRows);
+    long long grid = n_sm < kWgradBlocks ? n_sm : kWgradBlocks;
+    if (grid > total) grid = total;
+    conv3d_wgrad_tc_kernel<KCI, KCG><<<(unsigned)grid, kWgThreads, smem, st>>>(
+        mx, mgr, G, cin, cout, partial, err, limit);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return run_wgrad_reduce(cin, cout, (int)grid, partial, gw, gb, st);
 }
 
 RowGeo row_geo(const ConvDims &d) {
@@ -688,17 +943,21 @@ cudaError_t run_net_loss_grad_tc(const ConvDims &d, const float *theta, const fl
     pack_dy_kernel<<<blocks_for((long long)R, 256), 256, 0, st>>>(G, dy, reinterpret_cast<uint4 *>(DY));
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // backward, last layer first: the weight gradient of layer l from its input rows and the
-    // gradient rows of its output; the gradient of its input through the transposed
-    // convolution, gated by the ReLU of the layer below
+    // gradient rows of its output (conv3d_wgrad_tc_kernel); the gradient of its input through
+    // the transposed convolution, gated by the ReLU of the layer below
     const __nv_bfloat16 *gout = DY;
     int gch = 16;
     for (int l = kNetLayers - 1; l >= 0; --l) {
         const int ci = kNetCin[l], co = kNetCout[l];
         const __nv_bfloat16 *in = l == 0 ? X : A[l - 1];
         float *gw = grad + net_weight_offset(l);
-        if ((e = run_conv3d_wgrad_rows(G.nb, G.R, G.Sj, G.Si, ci, l == 0 ? 16 : 32, co, gch, in, gout,
-                                       partial, gw, gw + 27 * ci * co, st)) != cudaSuccess)
-            return e;
+        e = l == 0 ? launch_wgrad<2, 4>(in, gout, G, ci, co, partial, gw, gw + 27 * ci * co, n_sm,
+                                        err, limit, st)
+            : gch == 16 ? launch_wgrad<4, 2>(in, gout, G, ci, co, partial, gw, gw + 27 * ci * co,
+                                             n_sm, err, limit, st)
+                        : launch_wgrad<4, 4>(in, gout, G, ci, co, partial, gw, gw + 27 * ci * co,
+                                             n_sm, err, limit, st);
+        if (e != cudaSuccess) return e;
         if (l == 0) break;
         __nv_bfloat16 *gin = Gr[l - 1];
         e = l == kNetLayers - 1
