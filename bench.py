@@ -587,7 +587,10 @@ def warm_leg(args, gp, world):
     import json as _json
     torch, tt = gp.torch, gp.tt
     z = np.load(args.warm_start)
+    meta = _json.loads(str(z["summary"]))
+    stride = int(meta.get("stride", 1))
     theta = torch.as_tensor(z["theta"], device=gp.dev)
+    tt.tt_net_set_stride(gp.ctx, stride)
     tt.tt_net_set_weights(gp.ctx, theta)
     if gp.plan is not None:
         gp.plan.close()
@@ -608,8 +611,9 @@ def warm_leg(args, gp, world):
     ms = dist_max(e0.elapsed_time(e1) / args.steps, world)
     itf = np.concatenate([s[0] for s in gp.iters])
     fwd = [s[2] for s in gp.iters]
-    meta = _json.loads(str(z["summary"]))
     inf_ms = float(np.mean([s["warm_ms"] for s in fwd]))
+    from paper_2412_00031_gb300.warmstart import net_shape
+    fwd_it_ms = float(np.mean([s["sweep_ms"] / max(1, s["iters_max"]) for s in fwd]))
     sweep_ms = float(np.mean([s["sweep_ms"] for s in fwd]))
     hbm, _ = peaks()
     sweep = hbm_kernel(sweep_ms, float(np.mean([s["node_updates"] for s in fwd])),
@@ -618,11 +622,16 @@ def warm_leg(args, gp, world):
     return {"value": world * gp.w.n_src / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
             "iters_fwd_mean": float(itf.mean()), "iters_fwd_max": int(itf.max()),
             "inference_ms": inf_ms, "sweep_ms": sweep_ms,
-            "inference_roofline": net_roofline(gp.w.grid.shape, gp.w.n_src, inf_ms),
+            "network_grid": list(net_shape(gp.w.grid.shape, stride)),
+            "inference_in_forward_iterations": inf_ms / fwd_it_ms,
+            "inference_roofline": net_roofline(net_shape(gp.w.grid.shape, stride), gp.w.n_src,
+                                               inf_ms),
             "ideal_start_bound": start_bound(gp),
             "forward_kernel": sweep,
             "inference": "3x3x3 convolutions, all four layers on the tensor cores (tcgen05, BF16 "
-                         "operands, FP32 accumulation in tensor memory)",
+                         "operands, FP32 accumulation in tensor memory)%s"
+                         % ("" if stride == 1 else ", on every other node along each axis, "
+                            "the prediction interpolated trilinearly to the others"),
             "weights": "%s: trained on %d forward solves on %s random-field models, held-out "
                        "sweeps %.1f -> %.1f" % (os.path.basename(args.warm_start),
                                                 meta["solves_train"], "x".join(map(str, meta["grid"])),
@@ -665,9 +674,13 @@ def infer_only(args):
     g = w.grid
     ctx = tt.tt_ctx_create(g.as_dict())
     z = np.load(args.warm_start)
+    stride = int(json.loads(str(z["summary"])).get("stride", 1))
+    from paper_2412_00031_gb300.warmstart import net_shape
+    shape = net_shape(g.shape, stride)
+    tt.tt_net_set_stride(ctx, stride)
     tt.tt_net_set_weights(ctx, torch.as_tensor(z["theta"], device=dev))
     f32 = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32), device=dev)
-    x = torch.empty((nb,) + g.shape + (6,), dtype=torch.float32, device=dev)
+    x = torch.empty((nb,) + shape + (6,), dtype=torch.float32, device=dev)
     tt.tt_net_features(ctx, (f32(w.s), f32(w.xi), f32(w.eta)), w.src, x)
     y = torch.empty(x.shape[:-1], dtype=torch.float32, device=dev)
     for _ in range(args.warmup):
@@ -683,10 +696,11 @@ def infer_only(args):
         times.append(e0.elapsed_time(e1))
     ctx.close()
     ms = float(np.median(times))
-    roof = net_roofline(g.shape, nb, ms)
+    roof = net_roofline(shape, nb, ms)
     roof["note"] = "executed MMA FLOPs (padded channels, 126 of 128 rows per tile)"
     return {"metric": "warm-start inference throughput", "value": nb / (ms * 1e-3),
             "unit": "source-grids/s", "ms": ms, "grids": nb, "grid": list(g.shape),
+            "network_grid": list(shape),
             "useful_tflops": roof["useful_tflops"], "roofline": roof,
             "gpu_launches_per_call": 5}
 

@@ -445,17 +445,30 @@ tt_status tt_autotune_adjoint(tt_ctx *ctx, const tt_model *model, const tt_point
  * Parameters: one FP32 vector of tt_net_param_count() values: for each layer l, weights
  * W[27][C_in][C_out] (tap (dz * 3 + dy) * 3 + dx reads the node at offset (dz-1, dy-1, dx-1)
  * along (r, theta, phi)), then biases b[C_out].
- * Fields are channels-last FP32 on the context's grid: features [n][N][6], outputs [n][N].
+ * Fields are channels-last FP32 on the network's grid: features [n][Nn][6], outputs
+ * [n][Nn], where Nn = tt_net_nodes(ctx). The network's grid is the context's grid (stride 1,
+ * the default) or, after tt_net_set_stride(ctx, 2), every other node along each axis with the
+ * last node of an axis always included (n -> ceil((n - 1) / 2) + 1 nodes): the warm start
+ * then evaluates the network there, about 8x fewer nodes, and interpolates its clamped
+ * prediction trilinearly to every node. A network is trained for one stride (its 3x3x3
+ * taps span that spacing), so the stride goes with the weights.
  * All calls below wait for the context's stream before returning. */
 int tt_net_param_count(void);
-/* d_x (device [n_src][N][6] float) = the network input for each source. */
+/* Sets the stride of the network's grid (1 or 2; TT_EINVAL otherwise). Affects every call
+ * below and opts.init = 2 of later forward calls and plans (a plan keeps the stride it was
+ * created with). */
+tt_status tt_net_set_stride(tt_ctx *ctx, int stride);
+/* Nn: the node count of the network's grid (0 for a NULL context). */
+int tt_net_nodes(const tt_ctx *ctx);
+/* d_x (device [n_src][Nn][6] float) = the network input for each source at the nodes of the
+ * network's grid (the values of the solver-grid node each one sits on). */
 tt_status tt_net_features(tt_ctx *ctx, const tt_model *model, const tt_point *h_src, int n_src,
                           float *d_x);
-/* d_y (device [n_grids][N] float) = network output y for n_grids inputs d_x, FP32 weights. */
+/* d_y (device [n_grids][Nn] float) = network output y for n_grids inputs d_x, FP32 weights. */
 tt_status tt_net_forward(tt_ctx *ctx, const float *d_theta, const float *d_x, int n_grids,
                          float *d_y);
 /* Masked mean squared error loss = sum m (y - (tau - 1))^2 / sum m over n_grids grids
- * (d_target = the converged tau and d_mask, device [n_grids][N] float) and its gradient
+ * (d_target = the converged tau and d_mask, device [n_grids][Nn] float) and its gradient
  * with respect to the parameters
  * (d_grad, device [tt_net_param_count()], overwritten). The loss goes to *h_loss (may be
  * NULL). Deterministic: fixed-order reductions. */
@@ -480,12 +493,18 @@ tt_status tt_net_adam(tt_ctx *ctx, float *d_theta, const float *d_grad, float *d
 /* Stores the weights the warm start uses (device FP32 vector, rounded to BF16 and kept by
  * the context; inference accumulates in FP32). Needed before opts.init = 2. */
 tt_status tt_net_set_weights(tt_ctx *ctx, const float *d_theta);
-/* The warm start's inference with the stored weights: d_y (device [n_grids][N] float) =
- * network output for d_x (device [n_grids][N][6] float, as tt_net_features writes it). All
+/* The warm start's inference with the stored weights: d_y (device [n_grids][Nn] float) =
+ * network output for d_x (device [n_grids][Nn][6] float, as tt_net_features writes it). All
  * four layers run on the tensor cores (tcgen05, BF16 operands: the features are rounded
  * to BF16; FP32 accumulation); activations between layers are BF16. Agrees with
  * tt_net_forward to BF16 accuracy. TT_ETIMEOUT if a device-side wait exceeds 2 s. */
 tt_status tt_net_infer(tt_ctx *ctx, const float *d_x, int n_grids, float *d_y);
+/* The start of opts.init = 2 without the sweep: d_tau (device [N][n_src], the model's dtype)
+ * = 1 + the clamped network prediction (interpolated from the network's grid when its stride
+ * is 2), and 1 on each source's fixed set. Needs tt_net_set_weights. TT_ETIMEOUT if a
+ * device-side wait exceeds 2 s. */
+tt_status tt_net_start(tt_ctx *ctx, const tt_model *model, const tt_point *h_src, int n_src,
+                       void *d_tau);
 
 /* A plan: one whole step over one batch (forward, misfit and adjoint sources, adjoint,
  * kernels) captured once into a CUDA graph and replayed by tt_plan_run, so that a step costs

@@ -151,6 +151,48 @@ def warm_start(theta, x):
     return 1.0 + np.clip(forward(theta, x), CLAMP_LO, CLAMP_HI)
 
 
+# --------------------------------------------------------------- the network on a coarser grid
+
+def coarse_nodes(n, c):
+    """Node indices, along one axis of n nodes, of the network grid of stride c: every c-th
+    node, the last node of the axis always included (index min(a c, n - 1))."""
+    na = n if c == 1 else (n + c - 2) // c + 1
+    return np.minimum(np.arange(na) * c, n - 1)
+
+
+def _axis_weights(n, c):
+    """For every node i of an axis: the lower network node a and the weight f of the upper
+    one. Node i lies between the network nodes' positions p0 = a c and p1 = min(p0 + c, n - 1),
+    a = min(i // c, na - 2), f = (i - p0) / (p1 - p0)."""
+    na = len(coarse_nodes(n, c))
+    i = np.arange(n)
+    a = np.minimum(i // c, na - 2)
+    p0 = a * c
+    p1 = np.minimum(p0 + c, n - 1)
+    return a, (i - p0) / (p1 - p0)
+
+
+def upsample(yc, shape, c):
+    """Trilinear interpolation of a field on the stride-c network grid to every node of a grid
+    of `shape`: the sum over the eight surrounding network nodes of the products of the
+    per-axis weights (1 - f or f) times their values."""
+    (ar, fr), (at, ft), (ap, fp) = (_axis_weights(n, c) for n in shape)
+    out = np.zeros(shape)
+    for di in (0, 1):
+        for dj in (0, 1):
+            for dk in (0, 1):
+                w = ((fr if di else 1 - fr)[:, None, None] * (ft if dj else 1 - ft)[None, :, None]
+                     * (fp if dk else 1 - fp)[None, None, :])
+                out += w * yc[np.ix_(ar + di, at + dj, ap + dk)]
+    return out
+
+
+def warm_start_coarse(theta, xc, shape, c):
+    """The warm start with the network on the stride-c grid (xc: the features at its nodes):
+    clamp(y) at the network nodes, interpolated to every node, plus 1."""
+    return 1.0 + upsample(np.clip(forward(theta, xc), CLAMP_LO, CLAMP_HI), shape, c)
+
+
 def loss_and_grad(theta, xs, targets, masks):
     """Masked mean squared error over a batch and its gradient.
 

@@ -91,7 +91,8 @@ EXPORTED = ["tt_default_opts", "tt_ctx_create", "tt_ctx_destroy", "tt_last_error
             "tt_model_update", "tt_misfit_cr", "tt_field_at_points", "tt_misfit_table",
             "tt_reloc_kernels", "tt_reloc_update", "tt_tele2d", "tt_tele_region_times",
             "tt_forward_tele", "tt_autotune_adjoint", "tt_kernel_normalize_rel",
-            "tt_misfit_total", "tt_plan_create_cr", "tt_net_loss_grad_tc"]
+            "tt_misfit_total", "tt_plan_create_cr", "tt_net_loss_grad_tc", "tt_net_set_stride",
+            "tt_net_nodes", "tt_net_start"]
 TT_NOALLOC_MAX_REC = 1024
 
 
@@ -139,6 +140,11 @@ def _load():
     L.tt_net_adam.argtypes = [C.c_void_p] + [C.c_void_p] * 4 + [C.c_int] + [C.c_float] * 4
     L.tt_net_set_weights.argtypes = [C.c_void_p, C.c_void_p]
     L.tt_net_infer.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]
+    L.tt_net_set_stride.argtypes = [C.c_void_p, C.c_int]
+    L.tt_net_nodes.argtypes = [C.c_void_p]
+    L.tt_net_nodes.restype = C.c_int
+    L.tt_net_start.argtypes = [C.c_void_p, C.POINTER(TTModel), C.POINTER(TTPoint), C.c_int,
+                               C.c_void_p]
     L.tt_autotune.argtypes = [C.c_void_p, C.POINTER(TTModel), C.POINTER(TTPoint), C.c_int,
                               C.POINTER(TTOpts), C.POINTER(C.c_double)]
     L.tt_kernel_normalize_rel.argtypes = [C.c_void_p] * 5 + [C.c_double, C.c_double]
@@ -176,7 +182,7 @@ def _load():
                  "tt_misfit_table", "tt_reloc_kernels", "tt_reloc_update", "tt_tele2d",
                  "tt_tele_region_times", "tt_forward_tele", "tt_autotune_adjoint",
                  "tt_kernel_normalize_rel", "tt_misfit_total", "tt_plan_create_cr",
-                 "tt_net_loss_grad_tc"):
+                 "tt_net_loss_grad_tc", "tt_net_set_stride", "tt_net_start"):
         getattr(L, name).restype = C.c_int
     return L
 
@@ -726,10 +732,28 @@ def _f32(*tensors):
 NET_FEATURES = 6
 
 
+def tt_net_nodes(ctx):
+    """Node count of the network's grid (the context's grid, or every other node along each
+    axis after tt_net_set_stride(ctx, 2)): the sizes the library's tt_net_nodes reports, from
+    the grid and the stride this binding set."""
+    c = getattr(ctx, "net_stride", 1)
+    g = ctx.grid
+    axis = lambda n: int(n) if c == 1 else (int(n) + c - 2) // c + 1
+    return axis(g.n_r) * axis(g.n_t) * axis(g.n_p)
+
+
+def tt_net_set_stride(ctx, stride):
+    """The network's grid: 1 = the context's grid, 2 = every other node along each axis (the
+    warm start interpolates the prediction to the other nodes). Goes with the weights."""
+    _check(ctx, lib.tt_net_set_stride(ctx.handle, int(stride)))
+    ctx.net_stride = int(stride)
+
+
 def _net_room(ctx, n_grids, **named):
     """Sizes of the network's buffers: parameter-sized (theta, grad, m, v), inputs
-    n_grids x N x NET_FEATURES (x), per-node outputs n_grids x N (y, target, mask)."""
-    N = _nodes(ctx)
+    n_grids x Nn x NET_FEATURES (x), per-node outputs n_grids x Nn (y, target, mask), Nn the
+    network grid's nodes."""
+    N = tt_net_nodes(ctx)
     per = {"theta": tt_net_param_count(), "grad": tt_net_param_count(),
            "m": tt_net_param_count(), "v": tt_net_param_count(),
            "x": n_grids * N * NET_FEATURES, "y": n_grids * N, "target": n_grids * N,
@@ -738,11 +762,12 @@ def _net_room(ctx, n_grids, **named):
 
 
 def tt_net_features(ctx, model, src, x):
-    """x: float32 [n_src, N_r, N_t, N_p, 6] (or any contiguous shape of that size)."""
+    """x: float32 [n_src, Nn, 6] at the network grid's nodes (for stride 1 any contiguous
+    shape of that size, e.g. [n_src, N_r, N_t, N_p, 6])."""
     _model_room(ctx, model)
     pts, n = _points(src)
     _f32(x)
-    _room(x=(x, n * _nodes(ctx) * NET_FEATURES))
+    _room(x=(x, n * tt_net_nodes(ctx) * NET_FEATURES))
     M = _model(model)
     _cuda_ok(x)
     _check(ctx, lib.tt_net_features(ctx.handle, C.byref(M), pts, n, _ptr(x)))
@@ -827,6 +852,17 @@ def tt_autotune_adjoint(ctx, model, src, T, rec, R, opts):
     _check(ctx, lib.tt_autotune_adjoint(ctx.handle, C.byref(M), pts, n, _ptr(T), nr, rpts,
                                         _ptr(R), C.byref(opts), ms))
     return dict(zip(ADJ_AUTOTUNE_CANDIDATES, list(ms)))
+
+
+def tt_net_start(ctx, model, src, tau):
+    """The warm start's tau (opts.init = 2) without the sweep: tau [N_r, N_t, N_p, n_src] of
+    the model's dtype = 1 + the clamped prediction, 1 on the fixed sets."""
+    pts, n = _points(src)
+    ft = _model_room(ctx, model)
+    _room(tau=(tau, _nodes(ctx) * n, ft))
+    M = _model(model)
+    _cuda_ok(tau)
+    _check(ctx, lib.tt_net_start(ctx.handle, C.byref(M), pts, n, _ptr(tau)))
 
 
 def tt_net_infer(ctx, x, y):

@@ -52,6 +52,7 @@ struct tt_ctx {
     // tensor-core training: weight images of theta and of the transposed layers, BF16 rows
     DevBuf net_img, net_timg, net_rows;
     bool has_net = false;
+    int net_stride = 1;        // the warm-start network's grid: every net_stride-th node
     double *h_loss = nullptr;  // pinned
     // autotuner: scratch tau and the choices made, per (n_src, dtype)
     DevBuf tune_tau, tau_w, slot_srcc, slot_int;
@@ -379,16 +380,28 @@ template <typename F> struct Work {
     int net_chunk = 0;
 };
 
-// Rows of one grid in the padded row layout of the tensor-core inference.
-size_t net_grid_rows(const GridC &g) { return net_rows(ConvDims{1, g.nr, g.nt, g.np}); }
+// The warm-start network's grid (net_grid_of with the context's stride), its extent as
+// convolution dimensions, and its node count.
+NetGrid net_grid(const tt_ctx *ctx) { return net_grid_of(ctx->g, ctx->net_stride); }
+ConvDims net_dims(const tt_ctx *ctx, int nb) {
+    const NetGrid n = net_grid(ctx);
+    return ConvDims{nb, n.nr, n.nt, n.np};
+}
+long long net_nodes(const tt_ctx *ctx) {
+    const NetGrid n = net_grid(ctx);
+    return (long long)n.nr * n.nt * n.np;
+}
+
+// Rows of one network grid in the padded row layout of the tensor-core inference.
+size_t net_grid_rows(const tt_ctx *ctx) { return net_rows(net_dims(ctx, 1)); }
 
 // Sources per warm-start inference pass: two BF16 activation buffers of at most ~8 GB
-// together.
-int net_chunk(const GridC &g, int B) {
-    const size_t per_src = net_grid_rows(g) * kNetHidden * sizeof(__nv_bfloat16);
+// together, and at most 64 sources.
+int net_chunk(const tt_ctx *ctx, int B) {
+    const size_t per_src = net_grid_rows(ctx) * kNetHidden * sizeof(__nv_bfloat16);
     long long c = (long long)((4ull << 30) / per_src);
     if (c < 1) c = 1;
-    if (c > 16) c = 16;
+    if (c > 64) c = 64;
     return (int)(c < B ? c : B);
 }
 
@@ -480,12 +493,12 @@ template <typename F> tt_status refill_work_from_ctx(tt_ctx *ctx, Work<F> &W, in
 
 // Warm-start inference buffers from the context workspace.
 template <typename F> tt_status net_work_from_ctx(tt_ctx *ctx, Work<F> &W, int B) {
-    const GridC &g = ctx->g;
-    const int c = net_chunk(g, B);
-    ENSURE(ctx->net_x, sizeof(float) * kNetFeatures * (size_t)g.N * c);
-    ENSURE(ctx->net_a, sizeof(__nv_bfloat16) * kNetHidden * net_grid_rows(g) * c);
-    ENSURE(ctx->net_b, sizeof(__nv_bfloat16) * kNetHidden * net_grid_rows(g) * c);
-    ENSURE(ctx->net_y, sizeof(float) * (size_t)g.N * c);
+    const int c = net_chunk(ctx, B);
+    const size_t Nn = (size_t)net_nodes(ctx);
+    ENSURE(ctx->net_x, sizeof(float) * kNetFeatures * Nn * c);
+    ENSURE(ctx->net_a, sizeof(__nv_bfloat16) * kNetHidden * net_grid_rows(ctx) * c);
+    ENSURE(ctx->net_b, sizeof(__nv_bfloat16) * kNetHidden * net_grid_rows(ctx) * c);
+    ENSURE(ctx->net_y, sizeof(float) * Nn * c);
     W.net_x = (float *)ctx->net_x.p;
     W.net_a = (__nv_bfloat16 *)ctx->net_a.p;
     W.net_b = (__nv_bfloat16 *)ctx->net_b.p;
@@ -555,22 +568,23 @@ tt_status enq_net_forward(tt_ctx *ctx, const float *theta, const float *x, const
     return TT_OK;
 }
 
-// tau = 1 + clamp(net(features), -0.5, 1) for every source, in chunks of W.net_chunk. A
+// tau = 1 + clamp(net(features), -0.5, 1) for every source, in chunks of W.net_chunk, the
+// network evaluated on its grid (net_grid) and interpolated to every node when coarser. A
 // device-side wait of the tensor-core kernels that exceeds spin sets flags[3].
 template <typename F>
 tt_status enq_warm_start(tt_ctx *ctx, Work<F> &W, const tt_model *m, int B, F *tau,
                          unsigned long long spin) {
     const GridC &g = ctx->g;
+    const NetGrid ng = net_grid(ctx);
     const GeoTab<F> &t = geo<F>(ctx);
     for (int b0 = 0; b0 < B; b0 += W.net_chunk) {
         const int nb = W.net_chunk < B - b0 ? W.net_chunk : B - b0;
-        CK(run_net_features<F>(g, B, b0, nb, W.src, W.tabT, W.tabP, t.rad, t.cost,
+        CK(run_net_features<F>(g, ng, B, b0, nb, W.src, W.tabT, W.tabP, t.rad, t.cost,
                                (const F *)m->d_s, (const F *)m->d_xi, (const F *)m->d_eta,
                                W.net_x, ctx->st));
-        const ConvDims d{nb, g.nr, g.nt, g.np};
-        CK(run_net_infer(d, W.net_theta, W.net_wbf, W.net_x, W.net_a, W.net_b, W.net_y,
-                         ctx->n_sm, W.flags + 3, spin, ctx->st));
-        CK(run_warm_tau<F>(g.N, B, b0, nb, W.net_y, tau, ctx->st));
+        CK(run_net_infer(net_dims(ctx, nb), W.net_theta, W.net_wbf, W.net_x, W.net_a, W.net_b,
+                         W.net_y, ctx->n_sm, W.flags + 3, spin, ctx->st));
+        CK(run_warm_tau<F>(g, ng, B, b0, nb, W.net_y, tau, ctx->st));
         ctx->launches += 3 + kNetLayers;
     }
     return TT_OK;
@@ -1939,11 +1953,33 @@ tt_status net_features_impl(tt_ctx *ctx, const tt_model *m, const tt_point *h_sr
     if ((s = stage_to(ctx, h_src, B, W.src_pts)) != TT_OK) return s;
     if ((s = enq_sources<F>(ctx, W, m, B)) != TT_OK) return s;
     const GeoTab<F> &t = geo<F>(ctx);
-    CK(run_net_features<F>(ctx->g, B, 0, B, W.src, W.tabT, W.tabP, t.rad, t.cost,
+    CK(run_net_features<F>(ctx->g, net_grid(ctx), B, 0, B, W.src, W.tabT, W.tabP, t.rad, t.cost,
                            (const F *)m->d_s, (const F *)m->d_xi, (const F *)m->d_eta, d_x,
                            ctx->st));
     ctx->launches += 1;
     CK(cudaStreamSynchronize(ctx->st));
+    return TT_OK;
+}
+
+// The start of opts.init = 2 without the sweep: the network's tau and the fixed sets.
+template <typename F>
+tt_status net_start_impl(tt_ctx *ctx, const tt_model *m, const tt_point *h_src, int B,
+                         void *d_tau) {
+    tt_status s;
+    ENSURE(ctx->pts, sizeof(PointD) * (size_t)B);
+    Work<F> W;
+    if ((s = work_from_ctx<F>(ctx, W, B, 0)) != TT_OK) return s;
+    if ((s = net_work_from_ctx<F>(ctx, W, B)) != TT_OK) return s;
+    if ((s = stage_to(ctx, h_src, B, W.src_pts)) != TT_OK) return s;
+    if ((s = enq_sources<F>(ctx, W, m, B)) != TT_OK) return s;
+    CK(cudaMemsetAsync(W.flags + 3, 0, sizeof(int), ctx->st));
+    if ((s = enq_warm_start<F>(ctx, W, m, B, (F *)d_tau, kDefaultSpinNs)) != TT_OK) return s;
+    CK(run_tau_init<F>(ctx->g, B, W.src, (F *)d_tau, false, ctx->st));
+    ctx->launches += 1;
+    int h_err = 0;
+    CK(cudaMemcpyAsync(&h_err, W.flags + 3, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    if (h_err) return fail(ctx, TT_ETIMEOUT, "tt_net_start: a device-side wait exceeded its limit");
     return TT_OK;
 }
 
@@ -1952,6 +1988,28 @@ tt_status net_features_impl(tt_ctx *ctx, const tt_model *m, const tt_point *h_sr
 extern "C" {
 
 int tt_net_param_count(void) { return net_param_count(); }
+
+tt_status tt_net_set_stride(tt_ctx *ctx, int stride) {
+    if (!ctx) return TT_EINVAL;
+    if (stride != 1 && stride != 2)
+        return fail(ctx, TT_EINVAL, "tt_net_set_stride: stride %d is not 1 or 2", stride);
+    ctx->net_stride = stride;
+    return TT_OK;
+}
+
+int tt_net_nodes(const tt_ctx *ctx) { return ctx ? (int)net_nodes(ctx) : 0; }
+
+tt_status tt_net_start(tt_ctx *ctx, const tt_model *model, const tt_point *h_src, int n_src,
+                       void *d_tau) {
+    if (!ctx) return TT_EINVAL;
+    tt_status s;
+    if ((s = check_model(ctx, model)) != TT_OK) return s;
+    if ((s = check_sources(ctx, h_src, n_src)) != TT_OK) return s;
+    if (!d_tau) return fail(ctx, TT_EINVAL, "tt_net_start: NULL output");
+    if (!ctx->has_net) return fail(ctx, TT_EINVAL, "tt_net_start: no weights (tt_net_set_weights)");
+    return model->dtype == TT_F32 ? net_start_impl<float>(ctx, model, h_src, n_src, d_tau)
+                                  : net_start_impl<double>(ctx, model, h_src, n_src, d_tau);
+}
 
 tt_status tt_net_set_weights(tt_ctx *ctx, const float *d_theta) {
     if (!ctx) return TT_EINVAL;
@@ -1973,14 +2031,13 @@ tt_status tt_net_infer(tt_ctx *ctx, const float *d_x, int n_grids, float *d_y) {
     if (!d_x || !d_y || n_grids < 1)
         return fail(ctx, TT_EINVAL, "tt_net_infer: NULL buffer or n_grids < 1");
     if (!ctx->has_net) return fail(ctx, TT_EINVAL, "tt_net_infer: no weights (tt_net_set_weights)");
-    const GridC &g = ctx->g;
-    const size_t M = net_grid_rows(g) * n_grids;
+    const size_t M = net_grid_rows(ctx) * n_grids;
     ENSURE(ctx->net_a, sizeof(__nv_bfloat16) * kNetHidden * M);
     ENSURE(ctx->net_b, sizeof(__nv_bfloat16) * kNetHidden * M);
     ENSURE(ctx->flags, kFlagInts * sizeof(int));
     int *err = (int *)ctx->flags.p + 3;
     CK(cudaMemsetAsync(err, 0, sizeof(int), ctx->st));
-    CK(run_net_infer(ConvDims{n_grids, g.nr, g.nt, g.np}, (const float *)ctx->net_theta.p,
+    CK(run_net_infer(net_dims(ctx, n_grids), (const float *)ctx->net_theta.p,
                      (const __nv_bfloat16 *)ctx->net_wbf.p, d_x, (__nv_bfloat16 *)ctx->net_a.p,
                      (__nv_bfloat16 *)ctx->net_b.p, d_y, ctx->n_sm, err, kDefaultSpinNs, ctx->st));
     ctx->launches += 1 + kNetLayers;
@@ -2007,11 +2064,10 @@ tt_status tt_net_forward(tt_ctx *ctx, const float *d_theta, const float *d_x, in
     if (!ctx) return TT_EINVAL;
     if (!d_theta || !d_x || !d_y || n_grids < 1)
         return fail(ctx, TT_EINVAL, "tt_net_forward: NULL buffer or n_grids < 1");
-    const GridC &g = ctx->g;
-    const size_t M = (size_t)g.N * n_grids;
+    const size_t M = (size_t)net_nodes(ctx) * n_grids;
     ENSURE(ctx->net_a, sizeof(float) * kNetHidden * M);
     ENSURE(ctx->net_b, sizeof(float) * kNetHidden * M);
-    const ConvDims d{n_grids, g.nr, g.nt, g.np};
+    const ConvDims d = net_dims(ctx, n_grids);
     tt_status s = enq_net_forward(ctx, d_theta, d_x, d, (float *)ctx->net_a.p,
                                   (float *)ctx->net_b.p, (float *)ctx->net_a.p, d_y);
     if (s != TT_OK) return s;
@@ -2025,8 +2081,7 @@ tt_status tt_net_loss_grad(tt_ctx *ctx, const float *d_theta, const float *d_x,
     if (!ctx) return TT_EINVAL;
     if (!d_theta || !d_x || !d_target || !d_mask || !d_grad || n_grids < 1)
         return fail(ctx, TT_EINVAL, "tt_net_loss_grad: NULL buffer or n_grids < 1");
-    const GridC &g = ctx->g;
-    const size_t M = (size_t)g.N * n_grids;
+    const size_t M = (size_t)net_nodes(ctx) * n_grids;
     ENSURE(ctx->net_a, sizeof(float) * kNetHidden * M * 3);
     ENSURE(ctx->net_y, sizeof(float) * M);
     ENSURE(ctx->net_dy, sizeof(float) * M);
@@ -2041,7 +2096,7 @@ tt_status tt_net_loss_grad(tt_ctx *ctx, const float *d_theta, const float *d_x,
     float *y = (float *)ctx->net_y.p, *dy = (float *)ctx->net_dy.p;
     float *wt = (float *)ctx->net_wt.p, *part = (float *)ctx->net_part.p;
     double *scr = (double *)ctx->net_scr.p, *loss = scr + 4000;
-    const ConvDims d{n_grids, g.nr, g.nt, g.np};
+    const ConvDims d = net_dims(ctx, n_grids);
     tt_status s = enq_net_forward(ctx, d_theta, d_x, d, a[0], a[1], a[2], y);
     if (s != TT_OK) return s;
     CK(run_mse((long long)M, y, d_target, d_mask, dy, scr, loss, ctx->st));
@@ -2076,9 +2131,8 @@ tt_status tt_net_loss_grad_tc(tt_ctx *ctx, const float *d_theta, const float *d_
     if (!ctx) return TT_EINVAL;
     if (!d_theta || !d_x || !d_target || !d_mask || !d_grad || n_grids < 1)
         return fail(ctx, TT_EINVAL, "tt_net_loss_grad_tc: NULL buffer or n_grids < 1");
-    const GridC &g = ctx->g;
-    const ConvDims d{n_grids, g.nr, g.nt, g.np};
-    const size_t M = (size_t)g.N * n_grids;
+    const ConvDims d = net_dims(ctx, n_grids);
+    const size_t M = (size_t)net_nodes(ctx) * n_grids;
     ENSURE(ctx->net_img, sizeof(__nv_bfloat16) * net_weight_image_elems());
     ENSURE(ctx->net_timg, sizeof(__nv_bfloat16) * net_tweight_image_elems());
     ENSURE(ctx->net_wt, sizeof(float) * 27 * kNetHidden * kNetHidden);
@@ -2210,11 +2264,12 @@ template <typename F> tt_status plan_alloc(tt_plan *p, Work<F> &W) {
         W.n_slots = n_slots;
     }
     if (p->opts.init == 2) {
-        W.net_chunk = net_chunk(g, B);
-        TTGB_GET(net_x, sizeof(float) * kNetFeatures * (size_t)g.N * W.net_chunk);
-        TTGB_GET(net_a, sizeof(__nv_bfloat16) * kNetHidden * net_grid_rows(g) * W.net_chunk);
-        TTGB_GET(net_b, sizeof(__nv_bfloat16) * kNetHidden * net_grid_rows(g) * W.net_chunk);
-        TTGB_GET(net_y, sizeof(float) * (size_t)g.N * W.net_chunk);
+        W.net_chunk = net_chunk(ctx, B);
+        const size_t Nn = (size_t)net_nodes(ctx);
+        TTGB_GET(net_x, sizeof(float) * kNetFeatures * Nn * W.net_chunk);
+        TTGB_GET(net_a, sizeof(__nv_bfloat16) * kNetHidden * net_grid_rows(ctx) * W.net_chunk);
+        TTGB_GET(net_b, sizeof(__nv_bfloat16) * kNetHidden * net_grid_rows(ctx) * W.net_chunk);
+        TTGB_GET(net_y, sizeof(float) * Nn * W.net_chunk);
         W.net_theta = (const float *)ctx->net_theta.p;
         W.net_wbf = (const __nv_bfloat16 *)ctx->net_wbf.p;
     }

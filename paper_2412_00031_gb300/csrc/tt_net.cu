@@ -248,19 +248,25 @@ __global__ void adam_kernel(int n, float *__restrict__ th, const float *__restri
 }
 
 template <typename F>
-__global__ void features_kernel(GridC g, int B, int b0, int nb, const SrcC *__restrict__ src,
+__global__ void features_kernel(GridC g, NetGrid ng, int B, int b0, int nb,
+                                const SrcC *__restrict__ src,
                                 const Vec2<F> *__restrict__ tabT, const Vec2<F> *__restrict__ tabP,
                                 const F *__restrict__ rad, const F *__restrict__ cost,
                                 const F *__restrict__ s, const F *__restrict__ xi,
                                 const F *__restrict__ eta, float *__restrict__ x) {
+    const long long Nn = (long long)ng.nr * ng.nt * ng.np;
     const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= g.N * nb) return;
-    const int bl = (int)(q / g.N);
-    const long long n = q - (long long)bl * g.N;
+    if (q >= Nn * nb) return;
+    const int bl = (int)(q / Nn);
+    const long long nn = q - (long long)bl * Nn;
     const int b = b0 + bl;
-    const int k = (int)(n % g.np);
-    const long long tq = n / g.np;
-    const int j = (int)(tq % g.nt), i = (int)(tq / g.nt);
+    // node of the network grid -> node of the solver grid
+    const int kc = (int)(nn % ng.np);
+    const long long tq = nn / ng.np;
+    const int jc = (int)(tq % ng.nt), ic = (int)(tq / ng.nt);
+    const int i = min(ic * ng.c, g.nr - 1), j = min(jc * ng.c, g.nt - 1),
+              k = min(kc * ng.c, g.np - 1);
+    const long long n = node_index(g, i, j, k);
     const SrcReg<F> S = load_src<F>(src, b, g.dr);
     F du, dn, de;
     source_offset<F>(S, i, rad[i], cost[j], tabT[(long long)j * B + b], tabP[(long long)k * B + b],
@@ -284,6 +290,45 @@ __global__ void warm_tau_kernel(long long N, int B, int b0, int nb, const float 
     // a NaN prediction starts the node at tau = 1; the others (+-inf included) are clamped
     const float yv = y[(long long)bl * N + n];
     const float v = yv == yv ? fminf(fmaxf(yv, kNetClampLo), kNetClampHi) : 0.0f;
+    tau[n * B + b0 + bl] = (F)(1.0f + v);
+}
+
+// Position of a node of the solver grid within the network grid along one axis: the lower
+// network node a and the weight f of the upper one (network node a sits at min(a c, n - 1)).
+__device__ __forceinline__ void net_axis_pos(int i, int c, int nc, int n, int &a, float &f) {
+    a = min(i / c, nc - 2);
+    const int p0 = a * c, p1 = min(p0 + c, n - 1);
+    f = (float)(i - p0) / (float)(p1 - p0);
+}
+
+// tau = 1 + the trilinear interpolation of clamp(y) from the network grid (a NaN prediction
+// counts as 0), for the network-grid stride ng.c > 1.
+template <typename F>
+__global__ void warm_tau_up_kernel(GridC g, NetGrid ng, int B, int b0, int nb,
+                                   const float *__restrict__ y, F *__restrict__ tau) {
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= g.N * nb) return;
+    const int bl = (int)(q % nb);
+    const long long n = q / nb;
+    const int k = (int)(n % g.np);
+    const long long tq = n / g.np;
+    const int j = (int)(tq % g.nt), i = (int)(tq / g.nt);
+    int a[3];
+    float f[3];
+    net_axis_pos(i, ng.c, ng.nr, g.nr, a[0], f[0]);
+    net_axis_pos(j, ng.c, ng.nt, g.nt, a[1], f[1]);
+    net_axis_pos(k, ng.c, ng.np, g.np, a[2], f[2]);
+    const float *yb = y + (long long)bl * ng.nr * ng.nt * ng.np;
+    float v = 0.0f;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        const int di = u >> 2, dj = (u >> 1) & 1, dk = u & 1;
+        const float w = (di ? f[0] : 1.0f - f[0]) * (dj ? f[1] : 1.0f - f[1]) *
+                        (dk ? f[2] : 1.0f - f[2]);
+        const float yv = yb[((long long)(a[0] + di) * ng.nt + a[1] + dj) * ng.np + a[2] + dk];
+        const float c = yv == yv ? fminf(fmaxf(yv, kNetClampLo), kNetClampHi) : 0.0f;
+        v = fmaf(w, c, v);
+    }
     tau[n * B + b0 + bl] = (F)(1.0f + v);
 }
 
@@ -355,19 +400,23 @@ cudaError_t run_adam(int n, float *theta, const float *grad, float *m, float *v,
 }
 
 template <typename F>
-cudaError_t run_net_features(const GridC &g, int B, int b0, int nb, const SrcC *src,
-                             const Vec2<F> *tabT, const Vec2<F> *tabP, const F *rad,
-                             const F *cost, const F *s, const F *xi, const F *eta, float *x,
-                             cudaStream_t st) {
-    features_kernel<F><<<blocks_of(g.N * nb, 256), 256, 0, st>>>(g, B, b0, nb, src, tabT, tabP,
-                                                                 rad, cost, s, xi, eta, x);
+cudaError_t run_net_features(const GridC &g, const NetGrid &ng, int B, int b0, int nb,
+                             const SrcC *src, const Vec2<F> *tabT, const Vec2<F> *tabP,
+                             const F *rad, const F *cost, const F *s, const F *xi, const F *eta,
+                             float *x, cudaStream_t st) {
+    const long long Nn = (long long)ng.nr * ng.nt * ng.np;
+    features_kernel<F><<<blocks_of(Nn * nb, 256), 256, 0, st>>>(g, ng, B, b0, nb, src, tabT, tabP,
+                                                                rad, cost, s, xi, eta, x);
     return cudaGetLastError();
 }
 
 template <typename F>
-cudaError_t run_warm_tau(long long N, int B, int b0, int nb, const float *y, F *tau,
-                         cudaStream_t st) {
-    warm_tau_kernel<F><<<blocks_of(N * nb, 256), 256, 0, st>>>(N, B, b0, nb, y, tau);
+cudaError_t run_warm_tau(const GridC &g, const NetGrid &ng, int B, int b0, int nb,
+                         const float *y, F *tau, cudaStream_t st) {
+    if (ng.c == 1)
+        warm_tau_kernel<F><<<blocks_of(g.N * nb, 256), 256, 0, st>>>(g.N, B, b0, nb, y, tau);
+    else
+        warm_tau_up_kernel<F><<<blocks_of(g.N * nb, 256), 256, 0, st>>>(g, ng, B, b0, nb, y, tau);
     return cudaGetLastError();
 }
 
@@ -377,12 +426,12 @@ cudaError_t run_round_bf16(int n, const float *in, float *out, cudaStream_t st) 
 }
 
 #define TTGB_NET_INST(F)                                                                      \
-    template cudaError_t run_net_features<F>(const GridC &, int, int, int, const SrcC *,       \
-                                             const Vec2<F> *, const Vec2<F> *, const F *,     \
+    template cudaError_t run_net_features<F>(const GridC &, const NetGrid &, int, int, int,    \
+                                             const SrcC *, const Vec2<F> *, const Vec2<F> *,  \
                                              const F *, const F *, const F *, const F *,      \
-                                             float *, cudaStream_t);                          \
-    template cudaError_t run_warm_tau<F>(long long, int, int, int, const float *, F *,        \
-                                         cudaStream_t);
+                                             const F *, float *, cudaStream_t);               \
+    template cudaError_t run_warm_tau<F>(const GridC &, const NetGrid &, int, int, int,       \
+                                         const float *, F *, cudaStream_t);
 TTGB_NET_INST(float)
 TTGB_NET_INST(double)
 #undef TTGB_NET_INST

@@ -31,6 +31,17 @@ struct ConvDims {
     int nb, D, H, W;  // grids in the batch and their extent
 };
 
+// The grid the warm-start network runs on: every c-th node of the solver grid along each
+// axis, the last node of an axis always included (node a of an axis sits at min(a c, n - 1)),
+// so nr = ceil((n_r - 1) / c) + 1 and likewise. c = 1: the solver grid itself.
+struct NetGrid {
+    int c, nr, nt, np;
+};
+inline int net_axis(int n, int c) { return c == 1 ? n : (n + c - 2) / c + 1; }
+inline NetGrid net_grid_of(const GridC &g, int c) {
+    return NetGrid{c, net_axis(g.nr, c), net_axis(g.nt, c), net_axis(g.np, c)};
+}
+
 // Partial sums of the weight gradient: one row of 28 x 32 x 32 per reduction block.
 constexpr int kWgradBlocks = 152;
 inline size_t wgrad_partial_floats() { return (size_t)kWgradBlocks * 28 * 32 * 32; }
@@ -53,17 +64,19 @@ cudaError_t run_mse(long long total, const float *y, const float *target, const 
                     float *dy, double *scratch, double *loss, cudaStream_t st);
 cudaError_t run_adam(int n, float *theta, const float *grad, float *m, float *v, int step,
                      float lr, float beta1, float beta2, float eps, cudaStream_t st);
-// Features of sources [b0, b0 + nb) of a set-up batch (SrcC, angle tables of B sources):
-// x[b - b0][node][6] = (s / s0 - 1, xi, eta, D / 100 km).
+// Features of sources [b0, b0 + nb) of a set-up batch (SrcC, angle tables of B sources) at
+// the nodes of the network grid ng: x[b - b0][net node][6] = (s / s0 - 1, xi, eta,
+// D / 100 km) of the solver node it sits on.
 template <typename F>
-cudaError_t run_net_features(const GridC &g, int B, int b0, int nb, const SrcC *src,
-                             const Vec2<F> *tabT, const Vec2<F> *tabP, const F *rad,
-                             const F *cost, const F *s, const F *xi, const F *eta, float *x,
-                             cudaStream_t st);
-// tau[node][b0 + b] = 1 + clamp(y[b][node], -0.5, 1) for b < nb.
+cudaError_t run_net_features(const GridC &g, const NetGrid &ng, int B, int b0, int nb,
+                             const SrcC *src, const Vec2<F> *tabT, const Vec2<F> *tabP,
+                             const F *rad, const F *cost, const F *s, const F *xi, const F *eta,
+                             float *x, cudaStream_t st);
+// tau[node][b0 + b] = 1 + clamp(y[b][node], -0.5, 1) for b < nb, y on the network grid ng:
+// with ng.c > 1 the clamped prediction is interpolated trilinearly to every solver node.
 template <typename F>
-cudaError_t run_warm_tau(long long N, int B, int b0, int nb, const float *y, F *tau,
-                         cudaStream_t st);
+cudaError_t run_warm_tau(const GridC &g, const NetGrid &ng, int B, int b0, int nb,
+                         const float *y, F *tau, cudaStream_t st);
 // Inference (warm start, tt_umma.cu): the four convolutions on the tensor cores (tcgen05,
 // BF16 operands, FP32 accumulation in tensor memory) over the padded row layout of the
 // activations: features x [nb][node][6] (FP32) are packed into b, the layers run

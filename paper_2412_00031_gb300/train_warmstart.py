@@ -7,6 +7,8 @@ clipped to +-0.04; 5 -> 8 km/s background) on an 81 x 81 x 81 grid (depth 0-60 k
 - the training loss;
 - the prediction error against the converged tau;
 - the sweeps to convergence with and without the warm start on the held-out models.
+With --stride 2 the network runs on every other node along each axis (its targets are the
+converged tau there) and the warm start interpolates its prediction to the other nodes.
 
 Run from the repository root (it draws the models with tt_inputs):
 
@@ -32,6 +34,9 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=20241203)
     ap.add_argument("--tensor-cores", action="store_true",
                     help="gradients with the convolutions on the tensor cores (BF16 operands)")
+    ap.add_argument("--stride", type=int, default=1, choices=(1, 2),
+                    help="the network's grid: 1 = every node, 2 = every other node along each "
+                         "axis (the warm start interpolates to the others)")
     ap.add_argument("--out", default=os.path.join(os.path.dirname(os.path.abspath(__file__)),
                                                   "warmstart_81.npz"))
     a = ap.parse_args(argv)
@@ -47,6 +52,7 @@ def main(argv=None):
     n_hold = max(1, a.models // 10)
     train_models, hold_models = models[:-n_hold], models[-n_hold:]
     ctx = tt.tt_ctx_create(g.as_dict())
+    tt.tt_net_set_stride(ctx, a.stride)
     t1 = time.time()
     x, t, m, iters = WS.make_samples(ctx, g.shape, train_models)
     torch.cuda.synchronize()
@@ -83,6 +89,7 @@ def main(argv=None):
         "held_out_sweeps_cold": float(cold.mean()), "held_out_sweeps_warm": float(warm.mean()),
         "seconds_data": t2 - t1, "seconds_train": t3 - t2, "seconds_models": t1 - t0,
         "gradient": "tensor cores (BF16 operands)" if a.tensor_cores else "FP32",
+        "stride": a.stride,
     }
     np.savez(a.out, theta=theta.cpu().numpy(), losses=np.asarray(losses),
              summary=json.dumps(summary))

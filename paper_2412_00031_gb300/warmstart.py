@@ -35,23 +35,36 @@ def init_params(seed):
     return theta
 
 
+def net_shape(grid_shape, stride):
+    """Shape of the network's grid: every stride-th node along each axis, the last included."""
+    return tuple(n if stride == 1 else (n + stride - 2) // stride + 1 for n in grid_shape)
+
+
 def make_samples(ctx, grid_shape, models, device="cuda", opts=None):
     """Forward-solves every (model, source) pair in FP32 and returns device tensors
-    x [n, N_r, N_t, N_p, 6], t [n, N_r, N_t, N_p] (the converged tau), m (mask), and the forward
-    iteration counts. models: list of (s, xi, eta, src) numpy arrays. The loss compares
-    the network output with t - 1."""
+    x [n, Nr, Nt, Np, 6] (the features on the network's grid, tt_net_set_stride), t
+    [n, Nr, Nt, Np] (the converged tau at those nodes), m (mask), and the forward iteration
+    counts. models: list of (s, xi, eta, src) numpy arrays. The loss compares the network
+    output with t - 1."""
     import torch
     xs, ts, ms, iters = [], [], [], []
     o = opts if opts is not None else default_opts(TT_F32)
+    c = getattr(ctx, "net_stride", 1)
+    shape = net_shape(grid_shape, c)
+    # node indices of the network grid along each axis (min(a c, n - 1))
+    idx = [torch.as_tensor(np.minimum(np.arange(m) * c, n - 1), device=device)
+           for m, n in zip(shape, grid_shape)]
     for s, xi, eta, src in models:
         model = tuple(torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device=device)
                       for a in (s, xi, eta))
         B = len(src)
         tau = torch.empty(tuple(grid_shape) + (B,), dtype=torch.float32, device=device)
         iters.append(tt_forward(ctx, model, src, tau, None, o))
-        x = torch.empty((B,) + tuple(grid_shape) + (6,), dtype=torch.float32, device=device)
+        x = torch.empty((B,) + shape + (6,), dtype=torch.float32, device=device)
         tt_net_features(ctx, model, src, x)
         xs.append(x)
+        if c > 1:
+            tau = tau.index_select(0, idx[0]).index_select(1, idx[1]).index_select(2, idx[2])
         ts.append(tau.permute(3, 0, 1, 2).contiguous())
         ms.append(torch.ones_like(ts[-1]))
     return torch.cat(xs), torch.cat(ts), torch.cat(ms), np.concatenate(iters)

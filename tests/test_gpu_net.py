@@ -295,6 +295,50 @@ def test_tensor_core_inference_wide_and_small_grids(tt):
             assert np.abs(got - ref).max() <= 2e-2 * np.abs(ref).max(), (shape, b)
 
 
+@pytest.mark.parametrize("dt_name", ["f32", "f64"])
+def test_coarse_grid_warm_start_matches_oracle(tt, dt_name):
+    """The network on every other node (tt_net_set_stride(ctx, 2)) and its clamped prediction
+    interpolated trilinearly to every node (tt_net_start), against the oracle: the features
+    at the network nodes against the oracle's features of those nodes; the start against the
+    oracle's FP64 network with the same BF16 weights on those features, interpolated
+    (warm_start_coarse). 13 x 14 x 15 nodes: a 7 x 8 x 8 network grid, whose last interval
+    along the even axis is half as long. Bound as for the inference (2 % of the prediction's
+    range); tau = 1 at the node nearest each source (its fixed set)."""
+    import torch
+    w = I.small_case(68, shape=(13, 14, 15), n_src=3, n_rec=4)
+    theta = _theta(13)
+    dtype = torch.float32 if dt_name == "f32" else torch.float64
+    ctx = tt.tt_ctx_create(w.grid.as_dict())
+    tt.tt_net_set_stride(ctx, 2)
+    assert tt.tt_net_nodes(ctx) == 7 * 8 * 8 == tt.lib.tt_net_nodes(ctx.handle)
+    model = tuple(to_dev(a, dtype) for a in (w.s, w.xi, w.eta))
+    x = torch.empty((w.n_src, 7 * 8 * 8, 6), dtype=torch.float32, device="cuda")
+    tt.tt_net_features(ctx, model, w.src, x)
+    tt.tt_net_set_weights(ctx, torch.as_tensor(theta, device="cuda"))
+    tau = torch.empty(w.grid.shape + (w.n_src,), dtype=dtype, device="cuda")
+    tt.tt_net_start(ctx, model, w.src, tau)
+    ctx.close()
+    got = tau.cpu().numpy()
+    idx = [N.coarse_nodes(n, 2) for n in w.grid.shape]
+    tb = _bf16(theta).astype(np.float64)
+    r, th, ph, re, _ = N._axes_rad(w.grid.as_dict())
+    for b in range(w.n_src):
+        xc = N.features(w.grid.as_dict(), w.s, w.xi, w.eta, w.src[b])[np.ix_(*idx)]
+        xg = x[b].cpu().numpy().reshape(xc.shape)
+        assert np.abs(xg - xc).max() <= 1e-5 * max(1.0, np.abs(xc).max())
+        ref = N.warm_start_coarse(tb, xg.astype(np.float64), w.grid.shape, 2)
+        depth, lat, lon = w.src[b]
+        near = [int(round(v)) for v in ((re - depth - r[0]) / (r[1] - r[0]),
+                                         (np.deg2rad(lat) - th[0]) / (th[1] - th[0]),
+                                         (np.deg2rad(lon) - ph[0]) / (ph[1] - ph[0]))]
+        I3 = np.meshgrid(*[np.arange(n) for n in w.grid.shape], indexing="ij")
+        away = np.max([np.abs(I3[a] - near[a]) for a in range(3)], axis=0) > 2
+        scale = np.abs(ref - 1).max()
+        assert scale > 0.05
+        assert np.abs(got[..., b][away] - ref[away]).max() <= 2e-2 * scale
+        assert got[..., b][tuple(near)] == 1.0
+
+
 def test_broken_network_costs_sweeps_not_accuracy(tt):
     """A network that predicts NaN everywhere (NaN weights) starts every node at tau = 1,
     so the warm-started solve is bit for bit the cold one. A network with huge weights

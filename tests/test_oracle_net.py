@@ -93,3 +93,45 @@ def test_biases_only_network_is_constant():
     x = np.random.default_rng(6).standard_normal((3, 4, 5, 6))
     assert np.all(N.forward(theta, x) == 0.25)
     assert np.all(N.warm_start(theta, x) == 1.25)
+
+
+# ---- the network on the stride-2 grid: node selection and the interpolation back
+
+
+@pytest.mark.parametrize("n", [9, 10, 13, 2, 3])
+def test_coarse_nodes_take_every_other_node_and_the_last(n):
+    idx = N.coarse_nodes(n, 2)
+    assert idx[0] == 0 and idx[-1] == n - 1
+    assert np.all(np.diff(idx) >= 1) and np.all(np.diff(idx)[:-1] == 2)
+    assert len(idx) == -(-(n - 1) // 2) + 1
+    assert np.array_equal(N.coarse_nodes(n, 1), np.arange(n))
+
+
+@pytest.mark.parametrize("shape", [(9, 10, 13), (8, 11, 6)])
+def test_upsample_is_exact_for_trilinear_fields_and_keeps_the_network_nodes(shape):
+    """A field a + b i + c j + d k + e i j k (trilinear in the node indices) sampled at the
+    network nodes comes back exactly at every node, whether the last interval of an axis is
+    whole or half; the network nodes keep their values; stride 1 is the identity."""
+    rng = np.random.default_rng(5)
+    co = rng.standard_normal(5)
+    f = lambda i, j, k: co[0] + co[1] * i + co[2] * j + co[3] * k + co[4] * i * j * k
+    I, J, K = np.meshgrid(*[np.arange(n, dtype=float) for n in shape], indexing="ij")
+    full = f(I, J, K)
+    idx = [N.coarse_nodes(n, 2) for n in shape]
+    yc = full[np.ix_(*idx)]
+    up = N.upsample(yc, shape, 2)
+    assert np.max(np.abs(up - full)) <= 1e-12 * np.max(np.abs(full))
+    assert np.array_equal(up[np.ix_(*idx)], yc) or np.max(np.abs(up[np.ix_(*idx)] - yc)) <= 1e-13
+    noise = rng.standard_normal(shape)
+    assert np.array_equal(N.upsample(noise, shape, 1), noise)
+
+
+def test_upsample_of_a_non_trilinear_field_stays_between_its_neighbours():
+    """Every interpolated value lies within the range of the network values around it (the
+    weights are non-negative and sum to one): a bump does not overshoot."""
+    shape = (9, 11, 13)
+    rng = np.random.default_rng(6)
+    idx = [N.coarse_nodes(n, 2) for n in shape]
+    yc = rng.uniform(-1, 1, [len(i) for i in idx])
+    up = N.upsample(yc, shape, 2)
+    assert up.min() >= yc.min() - 1e-15 and up.max() <= yc.max() + 1e-15
