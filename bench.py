@@ -1017,7 +1017,7 @@ def main():
                     help="1: replay the step as one captured CUDA graph (tt_plan); 0: the four "
                          "individual calls")
     ap.add_argument("--warm-start", default=os.path.join(ROOT, "paper_2412_00031_gb300",
-                                                      "warmstart_81.npz"),
+                                                      "warmstart_81_s2.npz"),
                     help="weights of the warm-start network; '' skips the warm-started leg")
     ap.add_argument("--autotune", type=int, default=1,
                     help="1: pick the forward launch configuration with tt_autotune first")

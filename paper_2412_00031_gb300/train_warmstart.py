@@ -2,8 +2,9 @@
 
 The data are forward solves that the library itself computes, over random-field models
 (Gaussian random fields of correlation length 10 km; sigma 3 % on Vp, 2 % on xi and eta
-clipped to +-0.04; 5 -> 8 km/s background) on an 81 x 81 x 81 grid (depth 0-60 km,
-2 x 2 deg), 8 sources per model. 10 % of the models are held out. The script reports:
+clipped to +-0.04; 5 -> 8 km/s background) on a grid of the given shape, depth and extents
+(default 81 x 81 x 81, depth 0-60 km, 2 x 2 deg), with --sources sources per model (default
+8). 10 % of the models are held out. The script reports:
 - the training loss;
 - the prediction error against the converged tau;
 - the sweeps to convergence with and without the warm start on the held-out models.
@@ -13,6 +14,12 @@ converged tau there) and the warm start interpolates its prediction to the other
 Run from the repository root (it draws the models with tt_inputs):
 
     python -m paper_2412_00031_gb300.train_warmstart --models 250 --out warmstart_81.npz
+
+The committed weights: warmstart_81.npz (the network on every node) and warmstart_81_s2.npz
+(every other node; the benchmark's warm start), the latter from
+
+    python -m paper_2412_00031_gb300.train_warmstart --stride 2 --tensor-cores \
+        --out paper_2412_00031_gb300/warmstart_81_s2.npz
 """
 import argparse
 import json
@@ -28,6 +35,11 @@ def main(argv=None):
     ap.add_argument("--models", type=int, default=250)
     ap.add_argument("--sources", type=int, default=8)
     ap.add_argument("--shape", type=int, nargs=3, default=(81, 81, 81))
+    ap.add_argument("--depth-km", type=float, default=60.0)
+    ap.add_argument("--extent-deg", type=float, nargs=2, default=(2.0, 2.0),
+                    help="latitude and longitude extents of the grid")
+    ap.add_argument("--src-depth", type=float, nargs=2, default=(5.0, 40.0),
+                    help="source depth range in km")
     ap.add_argument("--steps", type=int, default=1500)
     ap.add_argument("--batch", type=int, default=8)
     ap.add_argument("--lr", type=float, default=2e-3)
@@ -48,7 +60,8 @@ def main(argv=None):
 
     t0 = time.time()
     g, models = I.random_field_models(seed=a.seed, n_models=a.models, shape=tuple(a.shape),
-                                      n_src=a.sources)
+                                      depth_km=a.depth_km, extent_deg=tuple(a.extent_deg),
+                                      n_src=a.sources, depth_range=tuple(a.src_depth))
     n_hold = max(1, a.models // 10)
     train_models, hold_models = models[:-n_hold], models[-n_hold:]
     ctx = tt.tt_ctx_create(g.as_dict())
@@ -81,7 +94,9 @@ def main(argv=None):
         warm.append(tt.tt_forward(ctx, model, src, tau, None, tt.default_opts(tt.TT_F32, init=2)))
     warm = np.concatenate(warm)
     summary = {
-        "grid": list(g.shape), "models_train": len(train_models), "models_held_out": n_hold,
+        "grid": list(g.shape), "depth_km": a.depth_km, "extent_deg": list(a.extent_deg),
+        "src_depth_km": list(a.src_depth), "sources_per_model": a.sources,
+        "models_train": len(train_models), "models_held_out": n_hold,
         "solves_train": int(len(iters)), "steps": a.steps, "batch": a.batch, "lr": a.lr,
         "loss_first": float(np.mean(losses[:10])), "loss_last": float(np.mean(losses[-50:])),
         "held_out_max_err": err_net, "held_out_max_err_tau1": err_one,

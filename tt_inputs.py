@@ -295,12 +295,14 @@ def random_field_models(seed=SEED_BASE + 3, n_models=250, shape=(81, 81, 81),
                         depth_km=60.0, extent_deg=2.0, corr_km=10.0, sigma_v=0.03,
                         sigma_aniso=0.02, clip_aniso=0.04, n_src=8, depth_range=(5.0, 40.0)):
     """Training models of the warm-start network: on an n_r x n_t x n_p grid (depth 0 to
-    depth_km, extent_deg square), Vp = (5 -> 8 km/s with depth) x (1 + GRF), the GRF of
-    correlation length corr_km and standard deviation sigma_v; xi, eta independent GRFs of
-    standard deviation sigma_aniso clipped to +-clip_aniso; n_src sources per model uniform
-    in depth_range. Returns the grid and a list of (s, xi, eta, src) per model."""
+    depth_km, extent_deg square, or (lat, lon) extents), Vp = (5 -> 8 km/s with depth) x
+    (1 + GRF), the GRF of correlation length corr_km and standard deviation sigma_v; xi, eta
+    independent GRFs of standard deviation sigma_aniso clipped to +-clip_aniso; n_src sources
+    per model uniform in depth_range. Returns the grid and a list of (s, xi, eta, src) per
+    model."""
     rng = np.random.default_rng(seed)
-    g = GridSpec(shape[0], shape[1], shape[2], 0.0, depth_km, 0.0, extent_deg, 0.0, extent_deg)
+    ext_t, ext_p = (extent_deg, extent_deg) if np.isscalar(extent_deg) else extent_deg
+    g = GridSpec(shape[0], shape[1], shape[2], 0.0, depth_km, 0.0, ext_t, 0.0, ext_p)
     vb = background_velocity(g)
     out = []
     for _ in range(n_models):
