@@ -143,6 +143,11 @@ typedef struct {
     int adj_groups;         /* adjoint: barrier groups per launch (1..8; each gets at least 32
                                sources), 0 = automatic (one per 64 sources, at most 4).
                                Results do not depend on it. */
+    int fwd_order;          /* plans: 0 = each run sweeps its batch in the order of the previous
+                               run's forward iteration counts, fewest first (the first run in
+                               the given order), so that a barrier group holds sources that
+                               converge together; 1 = always the given order. Results do not
+                               depend on it. Single calls use the given order. */
 } tt_opts;
 
 typedef struct tt_ctx tt_ctx;

@@ -71,7 +71,8 @@ class TTOpts(C.Structure):
                 ("max_iter_fwd", C.c_int), ("max_iter_adj", C.c_int), ("init", C.c_int),
                 ("spin_limit_ns", C.c_longlong), ("launch_blocks", C.c_int),
                 ("sweep_schedule", C.c_int), ("adj_chunk", C.c_int), ("fwd_groups", C.c_int),
-                ("fwd_slots", C.c_int), ("scheme", C.c_int), ("adj_groups", C.c_int)]
+                ("fwd_slots", C.c_int), ("scheme", C.c_int), ("adj_groups", C.c_int),
+                ("fwd_order", C.c_int)]
 
 
 class TTStats(C.Structure):

@@ -340,6 +340,8 @@ tt_status check_opts(tt_ctx *ctx, const tt_opts *o) {
         return fail(ctx, TT_EINVAL, "adj_groups %d outside 0..%d", o->adj_groups,
                     kMaxBarrierGroups);
     if (o->adj_chunk < 0) return fail(ctx, TT_EINVAL, "adj_chunk %d < 0", o->adj_chunk);
+    if (o->fwd_order < 0 || o->fwd_order > 1)
+        return fail(ctx, TT_EINVAL, "fwd_order %d is not 0 or 1", o->fwd_order);
     if (o->init == 2 && !ctx->has_net)
         return fail(ctx, TT_EINVAL, "init = 2 (warm start) needs tt_net_set_weights first");
     return TT_OK;
@@ -1135,6 +1137,7 @@ void tt_default_opts(tt_opts *o, int dtype) {
     o->fwd_slots = 0;
     o->scheme = 0;
     o->adj_groups = 0;
+    o->fwd_order = 0;
 }
 
 const char *tt_last_error(const tt_ctx *ctx) { return ctx ? ctx->err : "no context"; }
@@ -2197,6 +2200,13 @@ struct tt_plan {
     std::vector<PointD> h_src;
     Work<float> wf;
     Work<double> wd;
+    // batch order of the forward (opts.fwd_order = 0): perm[q] = the source at position q; the
+    // ordered batch's source points, set-up, iteration counts and tau
+    int ordered = 0;
+    int *perm = nullptr, *iters_o = nullptr, *conv_o = nullptr;
+    PointD *src_pts_o = nullptr;
+    SrcC *src_o = nullptr;
+    void *tabT_o = nullptr, *tabP_o = nullptr, *tau_o = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     long long launches_per_run = 0;  // kernels in the graph, added to ctx->launches per run
@@ -2263,6 +2273,23 @@ template <typename F> tt_status plan_alloc(tt_plan *p, Work<F> &W) {
         TTGB_GET(slot_int, sizeof(int) * (4 * (size_t)n_slots + 1));
         W.n_slots = n_slots;
     }
+    if (p->ordered) {
+        void *q_;
+#define TTGB_PGET(field, type, bytes)                                        \
+    do {                                                                     \
+        if ((s = get((bytes), &q_)) != TT_OK) return s;                      \
+        p->field = reinterpret_cast<type>(q_);                               \
+    } while (0)
+        TTGB_PGET(perm, int *, sizeof(int) * B);
+        TTGB_PGET(iters_o, int *, sizeof(int) * B);
+        TTGB_PGET(conv_o, int *, sizeof(int) * B);
+        TTGB_PGET(src_pts_o, PointD *, sizeof(PointD) * B);
+        TTGB_PGET(src_o, SrcC *, sizeof(SrcC) * B);
+        TTGB_PGET(tabT_o, void *, sizeof(Vec2<F>) * (size_t)g.nt * B);
+        TTGB_PGET(tabP_o, void *, sizeof(Vec2<F>) * (size_t)g.np * B);
+        TTGB_PGET(tau_o, void *, sizeof(F) * (size_t)g.N * B);
+#undef TTGB_PGET
+    }
     if (p->opts.init == 2) {
         W.net_chunk = net_chunk(ctx, B);
         const size_t Nn = (size_t)net_nodes(ctx);
@@ -2285,7 +2312,33 @@ template <typename F> tt_status plan_enqueue(tt_plan *p, Work<F> &W) {
     CK(cudaMemsetAsync(W.flags, 0, 4 * sizeof(int), ctx->st));
     if ((s = enq_receivers(ctx, W.rec_pts, p->n_rec, W.cq, W.wq, W.flags)) != TT_OK) return s;
     if ((s = enq_sources<F>(ctx, W, &p->model, p->B)) != TT_OK) return s;
-    if ((s = enq_forward<F>(ctx, W, &p->model, p->B, p->tau, p->T, &p->opts)) != TT_OK) return s;
+    if (p->ordered) {
+        // the forward over the ordered batch: its own source set-up, tau and counts, then
+        // tau and the counts back in the batch's order and T from them
+        Work<F> Wo = W;
+        Wo.src_pts = p->src_pts_o;
+        Wo.src = p->src_o;
+        Wo.tabT = (Vec2<F> *)p->tabT_o;
+        Wo.tabP = (Vec2<F> *)p->tabP_o;
+        Wo.iters_f = p->iters_o;
+        Wo.conv_f = p->conv_o;
+        CK(run_gather_points(p->B, p->perm, W.src_pts, Wo.src_pts, ctx->st));
+        if ((s = enq_sources<F>(ctx, Wo, &p->model, p->B)) != TT_OK) return s;
+        if (p->opts.init == 1)
+            CK(run_permute_rows<F>(g.N, p->B, p->perm, (F *)p->tau, (F *)p->tau_o, true,
+                                   ctx->st));
+        if ((s = enq_forward<F>(ctx, Wo, &p->model, p->B, p->tau_o, nullptr, &p->opts)) != TT_OK)
+            return s;
+        CK(run_permute_rows<F>(g.N, p->B, p->perm, (F *)p->tau, (F *)p->tau_o, false, ctx->st));
+        CK(run_unpermute_ints(p->B, p->perm, p->iters_o, p->conv_o, W.iters_f, W.conv_f,
+                              ctx->st));
+        const GeoTab<F> &t = geo<F>(ctx);
+        CK(run_traveltime<F>(g, p->B, W.src, W.tabT, W.tabP, t.rad, t.cost, t.sint,
+                             (const F *)p->tau, (F *)p->T, ctx->st));
+        ctx->launches += 4 + (p->opts.init == 1);
+    } else if ((s = enq_forward<F>(ctx, W, &p->model, p->B, p->tau, p->T, &p->opts)) != TT_OK) {
+        return s;
+    }
     if ((s = enq_readback(ctx, p->B, W.iters_f, W.conv_f, W.flags, W.bar, TT_STATS_FORWARD)) !=
         TT_OK)
         return s;
@@ -2304,6 +2357,10 @@ template <typename F> tt_status plan_enqueue(tt_plan *p, Work<F> &W) {
         CK(cudaMemsetAsync(p->K[q], 0, sizeof(double) * (size_t)g.N, ctx->st));
     if ((s = enq_kernel(ctx, &p->model, p->B, p->T, p->P, p->K[0], p->K[1], p->K[2])) != TT_OK)
         return s;
+    if (p->ordered) {  // the next run's order: this run's forward counts, fewest first
+        CK(run_order_update(p->B, W.iters_f, p->perm, ctx->st));
+        ctx->launches += 1;
+    }
     return enq_readback(ctx, p->B, W.iters_a, W.conv_a, W.flags, W.bar, TT_STATS_ADJOINT);
 }
 
@@ -2311,6 +2368,7 @@ template <typename F> tt_status plan_build(tt_plan *p, Work<F> &W, const tt_poin
     tt_ctx *ctx = p->ctx;
     tt_status s;
     if ((s = plan_alloc<F>(p, W)) != TT_OK) return s;
+    if (p->ordered) CK(run_order_identity(p->B, p->perm, ctx->st));
     if ((s = stage_to(ctx, p->data.h_rec, p->n_rec, W.rec_pts)) != TT_OK) return s;
     if ((s = stage_to(ctx, h_src, p->B, W.src_pts)) != TT_OK) return s;
     CK(cudaStreamSynchronize(ctx->st));
@@ -2421,6 +2479,8 @@ tt_status tt_plan_create_cr(tt_plan **out, tt_ctx *ctx, const tt_model *model,
     p->h_src.resize(n_src);
     for (int b = 0; b < n_src; ++b)
         p->h_src[b] = PointD{h_src[b].depth_km, h_src[b].lat_deg, h_src[b].lon_deg};
+    // the batch order matters where the sweep runs several barrier groups side by side
+    p->ordered = opts->fwd_order == 0 && opts->fwd_slots == 0 && n_src >= 64;
     s = model->dtype == TT_F32 ? plan_build<float>(p, p->wf, h_src)
                                : plan_build<double>(p, p->wd, h_src);
     if (s != TT_OK) {

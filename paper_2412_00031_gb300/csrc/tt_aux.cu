@@ -212,6 +212,59 @@ __global__ void upper_fill_kernel(F *tau, long long n, const unsigned *hilo) {
     tau[q] = (F)(2.f * hi / lo);
 }
 
+// Batch order of a plan's forward sweep. The sweep's barrier groups take consecutive sources
+// of the batch; ordered by their previous forward iteration counts, a group holds sources that
+// converge together and retires early instead of holding its SMs for one slow source. perm[q]
+// is the source at position q of the ordered batch. Each source's arithmetic does not depend
+// on its position, so the results are the same bits in any order.
+__global__ void gather_points_kernel(int B, const int *__restrict__ perm,
+                                     const PointD *__restrict__ in, PointD *__restrict__ out) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < B) out[q] = in[perm[q]];
+}
+
+// tau_o[n][q] = tau[n][perm[q]] (to_order) or tau[n][perm[q]] = tau_o[n][q] (back); rows of B.
+template <typename F>
+__global__ void permute_rows_kernel(long long N, int B, const int *__restrict__ perm,
+                                    F *__restrict__ tau, F *__restrict__ tau_o, bool to_order) {
+    const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= N * B) return;
+    const long long n = x / B;
+    const int q = (int)(x - n * B);
+    const long long y = n * B + perm[q];
+    if (to_order) tau_o[x] = tau[y];
+    else tau[y] = tau_o[x];
+}
+
+__global__ void unpermute_ints_kernel(int B, const int *__restrict__ perm,
+                                      const int *__restrict__ a_o, const int *__restrict__ b_o,
+                                      int *__restrict__ a, int *__restrict__ b) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= B) return;
+    a[perm[q]] = a_o[q];
+    b[perm[q]] = b_o[q];
+}
+
+// perm = the sources sorted by (iterations, index), ascending: the rank of source i is the
+// number of sources before it in that order. One block; O(B^2) comparisons (B <= 4096).
+__global__ void order_by_iterations_kernel(int B, const int *__restrict__ iters,
+                                           int *__restrict__ perm) {
+    for (int i = threadIdx.x; i < B; i += blockDim.x) {
+        const int ti = iters[i];
+        int rank = 0;
+        for (int j = 0; j < B; ++j) {
+            const int tj = iters[j];
+            rank += tj < ti || (tj == ti && j < i);
+        }
+        perm[rank] = i;
+    }
+}
+
+__global__ void identity_kernel(int B, int *__restrict__ perm) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < B) perm[q] = q;
+}
+
 // T = T0 tau at every (node, source).
 template <typename F>
 __global__ void traveltime_kernel(GridC g, int B, const SrcC *src, const Vec2<F> *tabT,
@@ -506,6 +559,36 @@ cudaError_t run_tau_init(const GridC &g, int n_src, const SrcC *d_src, F *tau, b
     return cudaGetLastError();
 }
 
+cudaError_t run_order_identity(int B, int *perm, cudaStream_t st) {
+    identity_kernel<<<blocks_for(B, 256), 256, 0, st>>>(B, perm);
+    return cudaGetLastError();
+}
+
+cudaError_t run_order_update(int B, const int *iters, int *perm, cudaStream_t st) {
+    order_by_iterations_kernel<<<1, 1024, 0, st>>>(B, iters, perm);
+    return cudaGetLastError();
+}
+
+cudaError_t run_gather_points(int B, const int *perm, const PointD *in, PointD *out,
+                              cudaStream_t st) {
+    gather_points_kernel<<<blocks_for(B, 256), 256, 0, st>>>(B, perm, in, out);
+    return cudaGetLastError();
+}
+
+template <typename F>
+cudaError_t run_permute_rows(long long N, int B, const int *perm, F *tau, F *tau_o, bool to_order,
+                             cudaStream_t st) {
+    permute_rows_kernel<F><<<blocks_for(N * B, 256), 256, 0, st>>>(N, B, perm, tau, tau_o,
+                                                                   to_order);
+    return cudaGetLastError();
+}
+
+cudaError_t run_unpermute_ints(int B, const int *perm, const int *a_o, const int *b_o, int *a,
+                               int *b, cudaStream_t st) {
+    unpermute_ints_kernel<<<blocks_for(B, 256), 256, 0, st>>>(B, perm, a_o, b_o, a, b);
+    return cudaGetLastError();
+}
+
 template <typename F>
 cudaError_t run_upper_start(const GridC &g, int n_src, const void *s, const void *xi,
                             const void *eta, F *tau, unsigned *hilo, cudaStream_t st) {
@@ -610,6 +693,8 @@ cudaError_t run_kernel_accum(const GridC &g, int B, const void *s, const void *T
                                              NodeRec<F> *, int *, cudaStream_t);               \
     template cudaError_t run_tau_init<F>(const GridC &, int, const SrcC *, F *, bool,          \
                                          cudaStream_t);                                        \
+    template cudaError_t run_permute_rows<F>(long long, int, const int *, F *, F *, bool,     \
+                                             cudaStream_t);                                    \
     template cudaError_t run_upper_start<F>(const GridC &, int, const void *, const void *,    \
                                             const void *, F *, unsigned *, cudaStream_t);      \
     template cudaError_t run_traveltime<F>(const GridC &, int, const SrcC *, const Vec2<F> *,  \

@@ -214,6 +214,43 @@ def test_plan_replays_the_step_bitwise(tt):
     ctx.close()
 
 
+@pytest.mark.parametrize("init", [0, 3])
+def test_plan_in_iteration_order_gives_the_same_bits(tt, init):
+    """From its second run a plan sweeps the batch in the order of the previous run's forward
+    iteration counts, fewest first (opts.fwd_order = 0, batches of 64 sources or more): every
+    run gives the bits of the individual calls and of a plan that keeps the given order
+    (fwd_order = 1), with the iteration counts in the batch's order."""
+    import torch
+    w = I.small_case(19, shape=(13, 14, 16), n_src=96, n_rec=6)
+    ref = gpu_solve(w, "f32", opts=tt.default_opts(tt.TT_F32, init=init))
+    assert len(set(ref["iters_fwd"].tolist())) > 1     # an order that differs from the given one
+    ctx = tt.tt_ctx_create(w.grid.as_dict())
+    model = tuple(to_dev(a, torch.float32) for a in (w.s, w.xi, w.eta))
+    shape = w.grid.shape + (w.n_src,)
+    data = tt.DeviceData.from_workload(w)
+    outs = []
+    for order in (0, 1):
+        tau, T, P = (torch.empty(shape, device="cuda") for _ in range(3))
+        chi = torch.empty((w.n_src, 2), dtype=torch.float64, device="cuda")
+        R = torch.empty((w.n_src, data.n_rec), dtype=torch.float64, device="cuda")
+        K = [torch.empty(w.grid.shape, dtype=torch.float64, device="cuda") for _ in range(3)]
+        o = tt.default_opts(tt.TT_F32, init=init, fwd_order=order)
+        plan = tt.tt_plan_create(ctx, model, w.src, data, tau, T, P, chi, R, *K, opts=o)
+        for _ in range(3):
+            itf, ita = tt.tt_plan_run(plan)
+            assert np.array_equal(itf, ref["iters_fwd"]) and np.array_equal(ita, ref["iters_adj"])
+            assert np.array_equal(tau.cpu().numpy(), ref["tau"])
+            assert np.array_equal(T.cpu().numpy(), ref["T"])
+            assert np.array_equal(P.cpu().numpy(), ref["P"])
+            assert np.array_equal(R.cpu().numpy(), ref["R"])
+            for a, b in zip(K, ref["K"]):
+                assert np.array_equal(a.cpu().numpy(), b)
+        outs.append(chi.cpu().numpy())
+        plan.close()
+    assert np.array_equal(outs[0], outs[1])
+    ctx.close()
+
+
 def test_autotuner_picks_a_measured_candidate_with_identical_results(tt):
     """The tuner times every launch configuration and keeps the fastest; the tuned solve
     gives the default solve's bits, and a second call reuses the cached choice."""
