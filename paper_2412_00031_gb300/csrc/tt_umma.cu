@@ -538,9 +538,10 @@ __global__ void weight_image_kernel(const float *__restrict__ w, int cin, int co
 // r' over [-1, R + 1) (rows outside [0, R) are zero). A chunk of 64 rows r' is one GEMM step
 // with K = rows: A = the nine (di, dj) slabs of X rows, B = the three dk slabs of G rows. Both
 // are the row buffers as they are (channels contiguous), i.e. MN-major operands: an M group
-// of 128 stacks 128 / C_in slabs (one swizzle atom of C_in channels each, LBO apart), N is
-// C_g, and 8-row groups are SBO apart. Accumulator (dk, M group) holds, in TMEM lane
-// (slab, ci), the sums of its taps over this CTA's chunks. One slab position of the last M
+// of 128 stacks 128 / C_in slabs (one swizzle atom of C_in channels each, LBO apart), N = 3
+// C_g stacks the three dk slabs the same way, and 8-row groups are SBO apart. The
+// accumulator of an M group holds, in TMEM lane (slab, ci) and column (dk, co), the sums of
+// its taps over this CTA's chunks. One slab position of the last M
 // group holds ones: its lanes collect sum_r G[r][co], the bias gradient (dk = 1 reads every
 // row of G once). Each CTA writes its sums as a partial row; wgrad_reduce sums the rows in a
 // fixed order, so the result is bitwise reproducible. Roles: warp 0 issues the tensor copies
@@ -565,13 +566,13 @@ template <int KCI, int KCG> struct WgSmem {
     static constexpr int MISC = BAR + NBAR * 8;
     static constexpr int TOTAL = MISC + 16 + 1024;
     static constexpr unsigned XLAYOUT = XROW == 64 ? 4u : 6u, GLAYOUT = GROW == 64 ? 4u : 6u;
-    static constexpr int N = CG;
+    static constexpr int N = 3 * CG;   // one MMA covers the three dk slabs (N atoms LBO apart)
 };
 static_assert(WgSmem<4, 4>::TOTAL <= 227 * 1024 && WgSmem<4, 4>::STAGE % 1024 == 0 &&
                   WgSmem<4, 2>::STAGE % 1024 == 0 && WgSmem<2, 4>::STAGE % 1024 == 0,
               "weight-gradient stages: shared memory and swizzle-atom alignment");
-static_assert(3 * WgSmem<4, 4>::MG * WgSmem<4, 4>::N <= kWgTmemCols &&
-                  3 * WgSmem<2, 4>::MG * WgSmem<2, 4>::N <= kWgTmemCols,
+static_assert(WgSmem<4, 4>::MG * WgSmem<4, 4>::N <= kWgTmemCols &&
+                  WgSmem<2, 4>::MG * WgSmem<2, 4>::N <= kWgTmemCols,
               "weight-gradient accumulators fit the tensor memory");
 
 // Shared-memory matrix descriptor of an MN-major operand with swizzle `layout`: swizzle atoms
@@ -696,19 +697,18 @@ __global__ void __launch_bounds__(kWgThreads, 1)
                 if (!bar_wait(full(s), ph, limit, s_abort)) { ok = false; break; }
                 tc_fence_after();
                 const unsigned st = base + s * L::STAGE;
-                for (int dk = 0; dk < 3; ++dk)
-                    for (int mg = 0; mg < L::MG; ++mg)
+                for (int mg = 0; mg < L::MG; ++mg)
 #pragma unroll
-                        for (int ks = 0; ks < kWgRows / 16; ++ks) {
-                            const unsigned long long ad =
-                                mdesc_mn(st + mg * L::SPG * L::XSLAB + ks * 16 * L::XROW, L::XSLAB,
-                                         8 * L::XROW, L::XLAYOUT);
-                            const unsigned long long bd =
-                                mdesc_mn(st + L::GOFF + dk * L::GSLAB + ks * 16 * L::GROW, L::GSLAB,
-                                         8 * L::GROW, L::GLAYOUT);
-                            mma_bf16(tmem + (unsigned)((dk * L::MG + mg) * L::N), ad, bd, ID,
-                                     !(first && ks == 0));
-                        }
+                    for (int ks = 0; ks < kWgRows / 16; ++ks) {
+                        // A: the M group's slabs; B: the three dk slabs, one N atom each
+                        const unsigned long long ad =
+                            mdesc_mn(st + mg * L::SPG * L::XSLAB + ks * 16 * L::XROW, L::XSLAB,
+                                     8 * L::XROW, L::XLAYOUT);
+                        const unsigned long long bd =
+                            mdesc_mn(st + L::GOFF + ks * 16 * L::GROW, L::GSLAB, 8 * L::GROW,
+                                     L::GLAYOUT);
+                        mma_bf16(tmem + (unsigned)(mg * L::N), ad, bd, ID, !(first && ks == 0));
+                    }
                 mma_commit(empty(s));   // the stage is free once these MMAs have read it
                 first = false;
                 if (++s == kWgStages) { s = 0; ph ^= 1u; }
@@ -726,10 +726,10 @@ __global__ void __launch_bounds__(kWgThreads, 1)
             tc_fence_after();
             for (int dk = 0; dk < 3; ++dk)
                 for (int mg = 0; mg < L::MG; ++mg) {
-                    float v[L::N];
-                    tmem_ld_cols<L::N>(tmem + ((unsigned)(quarter * 32) << 16) +
-                                           (unsigned)((dk * L::MG + mg) * L::N),
-                                       v);
+                    float v[L::CG];
+                    tmem_ld_cols<L::CG>(tmem + ((unsigned)(quarter * 32) << 16) +
+                                            (unsigned)(mg * L::N + dk * L::CG),
+                                        v);
                     const int p = mg * L::SPG + p_in;
                     float *row = nullptr;
                     if (p < 9 && ch < cin)
@@ -738,7 +738,7 @@ __global__ void __launch_bounds__(kWgThreads, 1)
                         row = partial + ((size_t)blockIdx.x * 28 + 27) * 1024;
                     if (row)
 #pragma unroll
-                        for (int n = 0; n < L::N; ++n)
+                        for (int n = 0; n < L::CG; ++n)
                             if (n < cout) row[n] = v[n];
                 }
         }
@@ -819,7 +819,7 @@ cudaError_t launch_wgrad(const void *in, const void *g, const RowGeo &G, int cin
                          float *partial, float *gw, float *gb, int n_sm, int *err,
                          unsigned long long limit, cudaStream_t st) {
     using L = WgSmem<KCI, KCG>;
-    if (cin > L::CI || cout > L::N || cin * cout > 1024) return cudaErrorInvalidValue;
+    if (cin > L::CI || cout > L::CG || cin * cout > 1024) return cudaErrorInvalidValue;
     CUtensorMap mx, mgr;
     cudaError_t e = encode_rows(&mx, in, G, KCI, kWgRows);
     if (e != cudaSuccess) return e;
