@@ -143,11 +143,13 @@ typedef struct {
     int adj_groups;         /* adjoint: barrier groups per launch (1..8; each gets at least 32
                                sources), 0 = automatic (one per 64 sources, at most 4).
                                Results do not depend on it. */
-    int fwd_order;          /* plans: 0 = each run sweeps its batch in the order of the previous
-                               run's forward iteration counts, fewest first (the first run in
-                               the given order), so that a barrier group holds sources that
-                               converge together; 1 = always the given order. Results do not
-                               depend on it. Single calls use the given order. */
+    int fwd_order;          /* 0 = sweep a batch of 64 sources or more in the order of its last
+                               forward iteration counts, fewest first, so that a barrier group
+                               holds sources that converge together: a plan from its second
+                               run on, a tt_forward call when the context has solved the same
+                               source positions before (it remembers the last 64 source sets);
+                               otherwise, and with retire-and-refill, the given order. 1 =
+                               always the given order. Results do not depend on it. */
 } tt_opts;
 
 typedef struct tt_ctx tt_ctx;

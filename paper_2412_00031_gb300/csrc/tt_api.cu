@@ -5,6 +5,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -56,6 +57,15 @@ struct tt_ctx {
     double *h_loss = nullptr;  // pinned
     // autotuner: scratch tau and the choices made, per (n_src, dtype)
     DevBuf tune_tau, tau_w, slot_srcc, slot_int;
+    // batch order of single forward calls: the last iteration counts of recent source sets
+    // (keyed by a hash of the positions) and the ordered batch's buffers
+    struct OrderMemo {
+        unsigned long long key;
+        int B;
+        std::vector<int> iters;
+    };
+    std::vector<OrderMemo> order_memo;
+    DevBuf ord_perm, ord_pts, ord_src, ord_tabT, ord_tabP, ord_tau, ord_iters, ord_conv;
     // inversion step: multiple-grid tables (for mg_key), projection scratch, update scratch
     DevBuf mg_tab, mg_scr, upd_part;
     // teleseismic events: 2-D tau scratch, event radii / coordinates and iteration counts
@@ -794,6 +804,33 @@ tt_status enq_forward(tt_ctx *ctx, Work<F> &W, const tt_model *m, int B, void *d
     return TT_OK;
 }
 
+// The forward over the batch in the order perm (perm[q] = the source at position q): the
+// ordered batch gets its own source set-up (Wo: points, SrcC, angle tables, counts) and tau
+// (tau_o); tau and the counts then go back to the batch's order (d_tau, W's counts) and T is
+// computed from them. Each source's arithmetic does not depend on its position, so the
+// results are those of the given order.
+template <typename F>
+tt_status enq_forward_ordered(tt_ctx *ctx, Work<F> &W, Work<F> &Wo, const int *perm,
+                              const tt_model *m, int B, void *d_tau, void *tau_o, void *d_T,
+                              const tt_opts *o) {
+    const GridC &g = ctx->g;
+    tt_status s;
+    CK(run_gather_points(B, perm, W.src_pts, Wo.src_pts, ctx->st));
+    if ((s = enq_sources<F>(ctx, Wo, m, B)) != TT_OK) return s;
+    if (o->init == 1) CK(run_permute_rows<F>(g.N, B, perm, (F *)d_tau, (F *)tau_o, true, ctx->st));
+    if ((s = enq_forward<F>(ctx, Wo, m, B, tau_o, nullptr, o)) != TT_OK) return s;
+    CK(run_permute_rows<F>(g.N, B, perm, (F *)d_tau, (F *)tau_o, false, ctx->st));
+    CK(run_unpermute_ints(B, perm, Wo.iters_f, Wo.conv_f, W.iters_f, W.conv_f, ctx->st));
+    ctx->launches += 3 + (o->init == 1);
+    if (d_T) {
+        const GeoTab<F> &t = geo<F>(ctx);
+        CK(run_traveltime<F>(g, B, W.src, W.tabT, W.tabP, t.rad, t.cost, t.sint, (const F *)d_tau,
+                             (F *)d_T, ctx->st));
+        ctx->launches += 1;
+    }
+    return TT_OK;
+}
+
 tt_status enq_receivers(tt_ctx *ctx, const PointD *rec_pts, int n_rec, long long *cq,
                         double *wq, int *flags) {
     CK(run_receiver_setup(ctx->g, rec_pts, n_rec, cq, wq, flags + 2, ctx->st));
@@ -1055,6 +1092,29 @@ tt_status solve_status(tt_ctx *ctx, int B, const PointD *src, int *h_iters, int 
 
 // ---------------------------------------------------------------- immediate calls
 
+// FNV-1a hash of a batch's source positions and dtype: the key of its remembered counts. A
+// collision only changes the order of a sweep, never its results.
+unsigned long long source_set_key(const tt_point *h_src, int B, int dtype) {
+    unsigned long long h = 1469598103934665603ull ^ (unsigned long long)dtype;
+    const unsigned char *p = reinterpret_cast<const unsigned char *>(h_src);
+    for (size_t i = 0; i < sizeof(tt_point) * (size_t)B; ++i) {
+        h ^= p[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+// Keeps the forward iteration counts of the last solve of a source set (at most 64 sets).
+void remember_counts(tt_ctx *ctx, unsigned long long key, int B, const int *iters) {
+    for (auto &e : ctx->order_memo)
+        if (e.key == key && e.B == B) {
+            e.iters.assign(iters, iters + B);
+            return;
+        }
+    if (ctx->order_memo.size() >= 64) ctx->order_memo.erase(ctx->order_memo.begin());
+    ctx->order_memo.push_back(tt_ctx::OrderMemo{key, B, std::vector<int>(iters, iters + B)});
+}
+
 template <typename F>
 tt_status forward_impl(tt_ctx *ctx, const tt_model *m, const tt_point *h_src, int B, void *d_tau,
                        void *d_T, const tt_opts *o, int *h_iters) {
@@ -1067,14 +1127,52 @@ tt_status forward_impl(tt_ctx *ctx, const tt_model *m, const tt_point *h_src, in
     if (S > 0 && (s = refill_work_from_ctx<F>(ctx, W, S)) != TT_OK) return s;
     if ((s = stage_to(ctx, h_src, B, W.src_pts)) != TT_OK) return s;
     if ((s = enq_sources<F>(ctx, W, m, B)) != TT_OK) return s;
-    if ((s = enq_forward<F>(ctx, W, m, B, d_tau, d_T, o)) != TT_OK) return s;
+    // the batch order: the last counts of the same source set, fewest first
+    const unsigned long long key = source_set_key(h_src, B, m->dtype);
+    const std::vector<int> *prev = nullptr;
+    if (o->fwd_order == 0 && S == 0 && B >= 64)
+        for (const auto &e : ctx->order_memo)
+            if (e.key == key && e.B == B) prev = &e.iters;
+    if (prev) {
+        std::vector<int> perm(B);
+        for (int q = 0; q < B; ++q) perm[q] = q;
+        std::stable_sort(perm.begin(), perm.end(),
+                         [prev](int a, int b) { return (*prev)[a] < (*prev)[b]; });
+        ENSURE(ctx->ord_perm, sizeof(int) * (size_t)B);
+        ENSURE(ctx->ord_pts, sizeof(PointD) * (size_t)B);
+        ENSURE(ctx->ord_src, sizeof(SrcC) * (size_t)B);
+        ENSURE(ctx->ord_tabT, sizeof(Vec2<F>) * (size_t)ctx->g.nt * B);
+        ENSURE(ctx->ord_tabP, sizeof(Vec2<F>) * (size_t)ctx->g.np * B);
+        ENSURE(ctx->ord_tau, sizeof(F) * (size_t)ctx->g.N * B);
+        ENSURE(ctx->ord_iters, sizeof(int) * (size_t)B);
+        ENSURE(ctx->ord_conv, sizeof(int) * (size_t)B);
+        CK(cudaMemcpyAsync(ctx->ord_perm.p, perm.data(), sizeof(int) * (size_t)B,
+                           cudaMemcpyHostToDevice, ctx->st));
+        Work<F> Wo = W;
+        Wo.src_pts = (PointD *)ctx->ord_pts.p;
+        Wo.src = (SrcC *)ctx->ord_src.p;
+        Wo.tabT = (Vec2<F> *)ctx->ord_tabT.p;
+        Wo.tabP = (Vec2<F> *)ctx->ord_tabP.p;
+        Wo.iters_f = (int *)ctx->ord_iters.p;
+        Wo.conv_f = (int *)ctx->ord_conv.p;
+        if ((s = enq_forward_ordered<F>(ctx, W, Wo, (const int *)ctx->ord_perm.p, m, B, d_tau,
+                                        ctx->ord_tau.p, d_T, o)) != TT_OK)
+            return s;
+        // the host copy of perm must outlive the copy above
+        CK(cudaStreamSynchronize(ctx->st));
+    } else if ((s = enq_forward<F>(ctx, W, m, B, d_tau, d_T, o)) != TT_OK) {
+        return s;
+    }
     if ((s = enq_readback(ctx, B, W.iters_f, W.conv_f, W.flags, W.bar, TT_STATS_FORWARD)) != TT_OK)
         return s;
     CK(cudaStreamSynchronize(ctx->st));
     ctx->warm_last = o->init == 2;
     ctx->scheme_last = o->scheme;
-    return solve_status(ctx, B, ctx->h_pts, h_iters, o->max_iter_fwd, "tt_forward",
-                        TT_STATS_FORWARD);
+    const tt_status st = solve_status(ctx, B, ctx->h_pts, h_iters, o->max_iter_fwd, "tt_forward",
+                                      TT_STATS_FORWARD);
+    if ((st == TT_OK || st == TT_ENOTCONVERGED) && o->fwd_order == 0 && S == 0 && B >= 64)
+        remember_counts(ctx, key, B, readback_view(ctx).iters_f);
+    return st;
 }
 
 template <typename F>
@@ -1203,7 +1301,9 @@ void tt_ctx_destroy(tt_ctx *ctx) {
                       &ctx->slot_srcc, &ctx->slot_int,
                       &ctx->net_wbf, &ctx->mg_tab, &ctx->mg_scr, &ctx->upd_part,
                       &ctx->tele_tau, &ctx->tele_aux, &ctx->net_img, &ctx->net_timg,
-                      &ctx->net_rows};
+                      &ctx->net_rows, &ctx->ord_perm, &ctx->ord_pts, &ctx->ord_src,
+                      &ctx->ord_tabT, &ctx->ord_tabP, &ctx->ord_tau, &ctx->ord_iters,
+                      &ctx->ord_conv};
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     if (ctx->h_loss) cudaFreeHost(ctx->h_loss);
@@ -2313,8 +2413,6 @@ template <typename F> tt_status plan_enqueue(tt_plan *p, Work<F> &W) {
     if ((s = enq_receivers(ctx, W.rec_pts, p->n_rec, W.cq, W.wq, W.flags)) != TT_OK) return s;
     if ((s = enq_sources<F>(ctx, W, &p->model, p->B)) != TT_OK) return s;
     if (p->ordered) {
-        // the forward over the ordered batch: its own source set-up, tau and counts, then
-        // tau and the counts back in the batch's order and T from them
         Work<F> Wo = W;
         Wo.src_pts = p->src_pts_o;
         Wo.src = p->src_o;
@@ -2322,20 +2420,9 @@ template <typename F> tt_status plan_enqueue(tt_plan *p, Work<F> &W) {
         Wo.tabP = (Vec2<F> *)p->tabP_o;
         Wo.iters_f = p->iters_o;
         Wo.conv_f = p->conv_o;
-        CK(run_gather_points(p->B, p->perm, W.src_pts, Wo.src_pts, ctx->st));
-        if ((s = enq_sources<F>(ctx, Wo, &p->model, p->B)) != TT_OK) return s;
-        if (p->opts.init == 1)
-            CK(run_permute_rows<F>(g.N, p->B, p->perm, (F *)p->tau, (F *)p->tau_o, true,
-                                   ctx->st));
-        if ((s = enq_forward<F>(ctx, Wo, &p->model, p->B, p->tau_o, nullptr, &p->opts)) != TT_OK)
+        if ((s = enq_forward_ordered<F>(ctx, W, Wo, p->perm, &p->model, p->B, p->tau, p->tau_o,
+                                        p->T, &p->opts)) != TT_OK)
             return s;
-        CK(run_permute_rows<F>(g.N, p->B, p->perm, (F *)p->tau, (F *)p->tau_o, false, ctx->st));
-        CK(run_unpermute_ints(p->B, p->perm, p->iters_o, p->conv_o, W.iters_f, W.conv_f,
-                              ctx->st));
-        const GeoTab<F> &t = geo<F>(ctx);
-        CK(run_traveltime<F>(g, p->B, W.src, W.tabT, W.tabP, t.rad, t.cost, t.sint,
-                             (const F *)p->tau, (F *)p->T, ctx->st));
-        ctx->launches += 4 + (p->opts.init == 1);
     } else if ((s = enq_forward<F>(ctx, W, &p->model, p->B, p->tau, p->T, &p->opts)) != TT_OK) {
         return s;
     }

@@ -251,6 +251,35 @@ def test_plan_in_iteration_order_gives_the_same_bits(tt, init):
     ctx.close()
 
 
+def test_repeated_forward_calls_in_iteration_order_give_the_same_bits(tt):
+    """A context remembers the forward iteration counts of a source set; the next tt_forward
+    of the same sources sweeps them fewest first. The results are the given order's bits:
+    from tau = 1, from a caller's start (opts.init = 1) and with T, with the counts in the
+    batch's order."""
+    import torch
+    w = I.small_case(20, shape=(13, 14, 16), n_src=80, n_rec=4)
+    model = tuple(to_dev(a, torch.float32) for a in (w.s, w.xi, w.eta))
+    shape = w.grid.shape + (w.n_src,)
+    rng = np.random.default_rng(20)
+    start = torch.as_tensor((1.0 + 0.2 * rng.uniform(size=shape)).astype(np.float32), device="cuda")
+    outs = {}
+    for order in (1, 0):
+        ctx = tt.tt_ctx_create(w.grid.as_dict())
+        for rep in range(2):
+            for init in (0, 1):
+                tau = start.clone() if init == 1 else torch.empty(shape, device="cuda")
+                T = torch.empty(shape, device="cuda")
+                it = tt.tt_forward(ctx, model, w.src, tau, T,
+                                   tt.default_opts(tt.TT_F32, init=init, fwd_order=order))
+                outs[(order, rep, init)] = (it, tau.cpu().numpy(), T.cpu().numpy())
+        ctx.close()
+    assert len(set(outs[(1, 0, 0)][0].tolist())) > 1
+    for key, (it, tau, T) in outs.items():
+        ref = outs[(1, 0, key[2])]
+        assert np.array_equal(it, ref[0]), key
+        assert np.array_equal(tau, ref[1]) and np.array_equal(T, ref[2]), key
+
+
 def test_autotuner_picks_a_measured_candidate_with_identical_results(tt):
     """The tuner times every launch configuration and keeps the fastest; the tuned solve
     gives the default solve's bits, and a second call reuses the cached choice."""
