@@ -146,8 +146,9 @@ typedef struct {
     int fwd_order;          /* 0 = sweep a batch of 64 sources or more in the order of its last
                                forward iteration counts, fewest first, so that a barrier group
                                holds sources that converge together: a plan from its second
-                               run on, a tt_forward call when the context has solved the same
-                               source positions before (it remembers the last 64 source sets);
+                               run on (its adjoint likewise, by the adjoint counts), a
+                               tt_forward call when the context has solved the same source
+                               positions before (it remembers the last 64 source sets);
                                otherwise, and with retire-and-refill, the given order. 1 =
                                always the given order. Results do not depend on it. */
 } tt_opts;

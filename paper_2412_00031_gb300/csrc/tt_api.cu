@@ -2307,6 +2307,11 @@ struct tt_plan {
     PointD *src_pts_o = nullptr;
     SrcC *src_o = nullptr;
     void *tabT_o = nullptr, *tabP_o = nullptr, *tau_o = nullptr;
+    // the adjoint's order (its own previous counts): perm_a, the ordered residuals and P; the
+    // ordered set-up, counts and T reuse the forward's buffers, free by then
+    int *perm_a = nullptr;
+    double *R_o = nullptr;
+    void *P_o = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     long long launches_per_run = 0;  // kernels in the graph, added to ctx->launches per run
@@ -2388,6 +2393,9 @@ template <typename F> tt_status plan_alloc(tt_plan *p, Work<F> &W) {
         TTGB_PGET(tabT_o, void *, sizeof(Vec2<F>) * (size_t)g.nt * B);
         TTGB_PGET(tabP_o, void *, sizeof(Vec2<F>) * (size_t)g.np * B);
         TTGB_PGET(tau_o, void *, sizeof(F) * (size_t)g.N * B);
+        TTGB_PGET(perm_a, int *, sizeof(int) * B);
+        TTGB_PGET(R_o, double *, sizeof(double) * (size_t)B * (p->n_rec > 0 ? p->n_rec : 1));
+        TTGB_PGET(P_o, void *, sizeof(F) * (size_t)g.N * B);
 #undef TTGB_PGET
     }
     if (p->opts.init == 2) {
@@ -2437,16 +2445,39 @@ template <typename F> tt_status plan_enqueue(tt_plan *p, Work<F> &W) {
                          p->cr.d_w, p->cr.gamma, p->Tr, p->chi_cr, p->R, p->cr_bad, ctx->st));
         ctx->launches += 1;
     }
-    if ((s = enq_adjoint<F>(ctx, W, &p->model, p->B, p->T, p->n_rec, p->R, p->P, &p->opts)) !=
-        TT_OK)
+    if (p->ordered) {
+        // the adjoint over the batch ordered by the previous run's adjoint counts: T, R and
+        // the set-up in that order, then P and the counts back in the batch's order
+        Work<F> Wa = W;
+        Wa.src_pts = p->src_pts_o;
+        Wa.src = p->src_o;
+        Wa.tabT = (Vec2<F> *)p->tabT_o;
+        Wa.tabP = (Vec2<F> *)p->tabP_o;
+        Wa.iters_a = p->iters_o;
+        Wa.conv_a = p->conv_o;
+        CK(run_gather_points(p->B, p->perm_a, W.src_pts, Wa.src_pts, ctx->st));
+        if ((s = enq_sources<F>(ctx, Wa, &p->model, p->B)) != TT_OK) return s;
+        CK(run_permute_rows<F>(g.N, p->B, p->perm_a, (F *)p->T, (F *)p->tau_o, true, ctx->st));
+        CK(run_gather_rows(p->B, p->n_rec, p->perm_a, p->R, p->R_o, ctx->st));
+        if ((s = enq_adjoint<F>(ctx, Wa, &p->model, p->B, p->tau_o, p->n_rec, p->R_o, p->P_o,
+                                &p->opts)) != TT_OK)
+            return s;
+        CK(run_permute_rows<F>(g.N, p->B, p->perm_a, (F *)p->P, (F *)p->P_o, false, ctx->st));
+        CK(run_unpermute_ints(p->B, p->perm_a, p->iters_o, p->conv_o, W.iters_a, W.conv_a,
+                              ctx->st));
+        ctx->launches += 5;
+    } else if ((s = enq_adjoint<F>(ctx, W, &p->model, p->B, p->T, p->n_rec, p->R, p->P,
+                                   &p->opts)) != TT_OK) {
         return s;
+    }
     for (int q = 0; q < 3; ++q)
         CK(cudaMemsetAsync(p->K[q], 0, sizeof(double) * (size_t)g.N, ctx->st));
     if ((s = enq_kernel(ctx, &p->model, p->B, p->T, p->P, p->K[0], p->K[1], p->K[2])) != TT_OK)
         return s;
-    if (p->ordered) {  // the next run's order: this run's forward counts, fewest first
+    if (p->ordered) {  // the next run's orders: this run's counts, fewest first
         CK(run_order_update(p->B, W.iters_f, p->perm, ctx->st));
-        ctx->launches += 1;
+        CK(run_order_update(p->B, W.iters_a, p->perm_a, ctx->st));
+        ctx->launches += 2;
     }
     return enq_readback(ctx, p->B, W.iters_a, W.conv_a, W.flags, W.bar, TT_STATS_ADJOINT);
 }
@@ -2455,7 +2486,10 @@ template <typename F> tt_status plan_build(tt_plan *p, Work<F> &W, const tt_poin
     tt_ctx *ctx = p->ctx;
     tt_status s;
     if ((s = plan_alloc<F>(p, W)) != TT_OK) return s;
-    if (p->ordered) CK(run_order_identity(p->B, p->perm, ctx->st));
+    if (p->ordered) {
+        CK(run_order_identity(p->B, p->perm, ctx->st));
+        CK(run_order_identity(p->B, p->perm_a, ctx->st));
+    }
     if ((s = stage_to(ctx, p->data.h_rec, p->n_rec, W.rec_pts)) != TT_OK) return s;
     if ((s = stage_to(ctx, h_src, p->B, W.src_pts)) != TT_OK) return s;
     CK(cudaStreamSynchronize(ctx->st));

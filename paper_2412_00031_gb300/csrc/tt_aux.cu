@@ -236,6 +236,15 @@ __global__ void permute_rows_kernel(long long N, int B, const int *__restrict__ 
     else tau[y] = tau_o[x];
 }
 
+// out[q][c] = in[perm[q]][c] for rows of n doubles (a batch's receiver residuals, ordered).
+__global__ void gather_rows_kernel(int B, int n, const int *__restrict__ perm,
+                                  const double *__restrict__ in, double *__restrict__ out) {
+    const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= (long long)B * n) return;
+    const int q = (int)(x / n), c = (int)(x - (long long)q * n);
+    out[x] = in[(long long)perm[q] * n + c];
+}
+
 __global__ void unpermute_ints_kernel(int B, const int *__restrict__ perm,
                                       const int *__restrict__ a_o, const int *__restrict__ b_o,
                                       int *__restrict__ a, int *__restrict__ b) {
@@ -580,6 +589,13 @@ cudaError_t run_permute_rows(long long N, int B, const int *perm, F *tau, F *tau
                              cudaStream_t st) {
     permute_rows_kernel<F><<<blocks_for(N * B, 256), 256, 0, st>>>(N, B, perm, tau, tau_o,
                                                                    to_order);
+    return cudaGetLastError();
+}
+
+cudaError_t run_gather_rows(int B, int n, const int *perm, const double *in, double *out,
+                            cudaStream_t st) {
+    if (n > 0)
+        gather_rows_kernel<<<blocks_for((long long)B * n, 256), 256, 0, st>>>(B, n, perm, in, out);
     return cudaGetLastError();
 }
 

@@ -32,7 +32,8 @@ cudaError_t run_tau_init(const GridC &g, int n_src, const SrcC *d_src, F *tau, b
                          cudaStream_t st);
 // Batch order of a plan's forward (sources sorted by their previous iteration counts):
 // perm = identity; perm = sources sorted by (iters, index); out[q] = in[perm[q]];
-// tau_o[n][q] = tau[n][perm[q]] (to_order) or the reverse; a[perm[q]] = a_o[q] (and b).
+// tau_o[n][q] = tau[n][perm[q]] (to_order) or the reverse; a[perm[q]] = a_o[q] (and b);
+// out[q][:] = in[perm[q]][:] for rows of n doubles.
 cudaError_t run_order_identity(int B, int *perm, cudaStream_t st);
 cudaError_t run_order_update(int B, const int *iters, int *perm, cudaStream_t st);
 cudaError_t run_gather_points(int B, const int *perm, const PointD *in, PointD *out,
@@ -42,6 +43,8 @@ cudaError_t run_permute_rows(long long N, int B, const int *perm, F *tau, F *tau
                              cudaStream_t st);
 cudaError_t run_unpermute_ints(int B, const int *perm, const int *a_o, const int *b_o, int *a,
                                int *b, cudaStream_t st);
+cudaError_t run_gather_rows(int B, int n, const int *perm, const double *in, double *out,
+                            cudaStream_t st);
 // Fills tau [N][n_src] with the start from above of opts.init = 3 (twice a bound of tau
 // from the model's slowness and anisotropy); hilo: 2 unsigned of device scratch.
 template <typename F>
