@@ -246,6 +246,19 @@ typedef struct {
 tt_status tt_misfit_cr(tt_ctx *ctx, const tt_cr_data *d, const double *d_Tr, double *d_chi_cr,
                        double *d_R);
 
+/* The entry table of tt_cr_data from a list of unordered pairs (Eq. 4's pairs of sources at a
+ * common receiver), on the host. h_pairs: n_pairs rows (b, j, m, dT_obs, w) of doubles, the
+ * pair {b, j} observed at receiver m with T_b^obs(x_m) - T_j^obs(x_m) = dT_obs and weight w.
+ * Writes host arrays the caller allocates: h_off (n_src * n_rec + 1 ints) and h_other,
+ * h_dtobs, h_w (2 * n_pairs each). Each pair is entered twice, under (b, m) with (j, dT_obs,
+ * w) and under (j, m) with (b, -dT_obs, w); within one (source, receiver) the entries keep
+ * the order of the list, first-source listings before second-source ones, so the
+ * fixed-order sums of tt_misfit_cr are reproducible. b, j and m must be integral, in range
+ * and b != j, else TT_EINVAL with nothing written. ctx may be NULL (it only receives the
+ * error message). Touches no device memory and needs no GPU. */
+tt_status tt_cr_pack(tt_ctx *ctx, int n_src, int n_rec, int n_pairs, const double *h_pairs,
+                     int *h_off, int *h_other, double *h_dtobs, double *h_w);
+
 /* ---- The inversion step's regularisation and update (Sec. 3.3; step 4 of Sec. 2). ---- */
 
 /* Kernel density (Eq. 19): adds sum over the n_src sources of d_P[node][b] to d_Kd (device

@@ -93,7 +93,7 @@ EXPORTED = ["tt_default_opts", "tt_ctx_create", "tt_ctx_destroy", "tt_last_error
             "tt_reloc_kernels", "tt_reloc_update", "tt_tele2d", "tt_tele_region_times",
             "tt_forward_tele", "tt_autotune_adjoint", "tt_kernel_normalize_rel",
             "tt_misfit_total", "tt_plan_create_cr", "tt_net_loss_grad_tc", "tt_net_set_stride",
-            "tt_net_nodes", "tt_net_start"]
+            "tt_net_nodes", "tt_net_start", "tt_cr_pack"]
 TT_NOALLOC_MAX_REC = 1024
 
 
@@ -155,6 +155,7 @@ def _load():
                                       C.c_int, C.c_void_p, C.c_int, C.POINTER(TTPoint),
                                       C.c_void_p, C.POINTER(TTOpts), C.POINTER(C.c_double)]
     L.tt_misfit_cr.argtypes = [C.c_void_p, C.POINTER(TTCrData)] + [C.c_void_p] * 3
+    L.tt_cr_pack.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int] + [C.c_void_p] * 5
     L.tt_kernel_density.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p]
     L.tt_kernel_normalize.argtypes = [C.c_void_p] + [C.c_void_p] * 4 + [C.c_double] * 2
     L.tt_mgrid_project.argtypes = [C.c_void_p, C.POINTER(TTMgrid), C.c_void_p, C.c_void_p]
@@ -183,7 +184,7 @@ def _load():
                  "tt_misfit_table", "tt_reloc_kernels", "tt_reloc_update", "tt_tele2d",
                  "tt_tele_region_times", "tt_forward_tele", "tt_autotune_adjoint",
                  "tt_kernel_normalize_rel", "tt_misfit_total", "tt_plan_create_cr",
-                 "tt_net_loss_grad_tc", "tt_net_set_stride", "tt_net_start"):
+                 "tt_net_loss_grad_tc", "tt_net_set_stride", "tt_net_start", "tt_cr_pack"):
         getattr(L, name).restype = C.c_int
     return L
 
@@ -410,6 +411,22 @@ def tt_kernel(ctx, model, T, P, Ks, Kxi, Keta):
                               _ptr(Kxi), _ptr(Keta)))
 
 
+def cr_pack(n_src, n_rec, pairs):
+    """tt_cr_pack on host arrays: (off, other, dtobs, w) numpy arrays of tt_cr_data's table
+    from rows (b, j, m, dT_obs, w) of unordered pairs."""
+    P = np.ascontiguousarray(np.asarray(pairs, dtype=np.float64).reshape(-1, 5))
+    n = P.shape[0]
+    off = np.zeros(int(n_src) * int(n_rec) + 1, dtype=np.int32)
+    other = np.zeros(2 * n, dtype=np.int32)
+    dtobs = np.zeros(2 * n, dtype=np.float64)
+    w = np.zeros(2 * n, dtype=np.float64)
+    p = lambda a: a.ctypes.data_as(C.c_void_p)
+    st = lib.tt_cr_pack(None, int(n_src), int(n_rec), n, p(P), p(off), p(other), p(dtobs), p(w))
+    if st != 0:
+        raise TTError(st, "tt_cr_pack refused the pair list (sources, receiver or b == j)")
+    return off, other, dtobs, w
+
+
 class CrData:
     """Common-receiver differential times (Eq. 4) of one batch, in the layout of tt_cr_data.
     pairs: rows (b, j, m, dT_obs, w), an unordered source pair {b, j} observed at receiver m
@@ -417,23 +434,12 @@ class CrData:
 
     def __init__(self, n_src, n_rec, pairs, gamma=1.0, device="cuda"):
         import torch
-        P = np.asarray(pairs, dtype=np.float64).reshape(-1, 5)
-        b, j, m = (P[:, c].astype(np.int64) for c in range(3))
-        src = np.concatenate([b, j])                    # each pair under both sources
-        oth = np.concatenate([j, b])
-        rec = np.concatenate([m, m])
-        dt = np.concatenate([P[:, 3], -P[:, 3]])
-        w = np.concatenate([P[:, 4], P[:, 4]])
-        key = src * n_rec + rec
-        order = np.argsort(key, kind="stable")
-        off = np.zeros(n_src * n_rec + 1, dtype=np.int64)
-        np.add.at(off, key + 1, 1)
-        off = np.cumsum(off)
-        i32 = lambda a: torch.as_tensor(np.asarray(a, dtype=np.int32), device=device)
-        f64 = lambda a: torch.as_tensor(np.asarray(a, dtype=np.float64), device=device)
-        self.n_src, self.n_rec, self.n_entries = int(n_src), int(n_rec), int(len(order))
-        self.off, self.other = i32(off), i32(oth[order])
-        self.dtobs, self.w = f64(dt[order]), f64(w[order])
+        off, other, dtobs, w = cr_pack(n_src, n_rec, pairs)
+        self.n_src, self.n_rec, self.n_entries = int(n_src), int(n_rec), int(len(other))
+        self.off = torch.as_tensor(off, device=device)
+        self.other = torch.as_tensor(other, device=device)
+        self.dtobs = torch.as_tensor(dtobs, device=device)
+        self.w = torch.as_tensor(w, device=device)
         self.gamma = float(gamma)
 
     def c_struct(self):

@@ -1416,6 +1416,52 @@ tt_status tt_misfit_cr(tt_ctx *ctx, const tt_cr_data *d, const double *d_Tr, dou
     return TT_OK;
 }
 
+tt_status tt_cr_pack(tt_ctx *ctx, int n_src, int n_rec, int n_pairs, const double *h_pairs,
+                     int *h_off, int *h_other, double *h_dtobs, double *h_w) {
+    if (n_src < 1 || n_src > TT_MAX_BATCH || n_rec < 1 || n_pairs < 0)
+        return fail(ctx, TT_EINVAL, "tt_cr_pack: n_src %d, n_rec %d or n_pairs %d out of range",
+                    n_src, n_rec, n_pairs);
+    if (!h_off || (n_pairs > 0 && (!h_pairs || !h_other || !h_dtobs || !h_w)))
+        return fail(ctx, TT_EINVAL, "tt_cr_pack: NULL argument");
+    if ((long long)n_src * n_rec + 1 > 0x7fffffffLL || 2LL * n_pairs > 0x7fffffffLL)
+        return fail(ctx, TT_EINVAL, "tt_cr_pack: table too large for int offsets");
+    // source, other source and receiver of every pair, checked before anything is written
+    for (int p = 0; p < n_pairs; ++p) {
+        const double *e = h_pairs + 5LL * p;
+        const double b = e[0], j = e[1], m = e[2];
+        if (!(b >= 0 && b < n_src && b == (double)(int)b) ||
+            !(j >= 0 && j < n_src && j == (double)(int)j) ||
+            !(m >= 0 && m < n_rec && m == (double)(int)m) || b == j)
+            return fail(ctx, TT_EINVAL,
+                        "tt_cr_pack: pair %d (%g, %g, %g) is not two distinct sources below %d "
+                        "at a receiver below %d",
+                        p, b, j, m, n_src, n_rec);
+    }
+    // Counting sort by (source, receiver). The pairs are listed first under their first
+    // source with dT_obs, then under their second with -dT_obs, each in the order given;
+    // that order is kept among the entries of one (source, receiver).
+    const long long n_keys = (long long)n_src * n_rec;
+    for (long long q = 0; q <= n_keys; ++q) h_off[q] = 0;
+    for (int p = 0; p < n_pairs; ++p) {
+        const double *e = h_pairs + 5LL * p;
+        const int m = (int)e[2];
+        h_off[(long long)(int)e[0] * n_rec + m + 1] += 1;
+        h_off[(long long)(int)e[1] * n_rec + m + 1] += 1;
+    }
+    for (long long q = 0; q < n_keys; ++q) h_off[q + 1] += h_off[q];
+    std::vector<int> next(h_off, h_off + n_keys);
+    for (int pass = 0; pass < 2; ++pass)
+        for (int p = 0; p < n_pairs; ++p) {
+            const double *e = h_pairs + 5LL * p;
+            const int src = (int)e[pass], oth = (int)e[1 - pass], m = (int)e[2];
+            const int q = next[(long long)src * n_rec + m]++;
+            h_other[q] = oth;
+            h_dtobs[q] = pass == 0 ? e[3] : -e[3];
+            h_w[q] = e[4];
+        }
+    return TT_OK;
+}
+
 tt_status tt_kernel_density(tt_ctx *ctx, const void *d_P, int n_src, int dtype, double *d_Kd) {
     if (!ctx) return TT_EINVAL;
     if (n_src < 1 || n_src > TT_MAX_BATCH)

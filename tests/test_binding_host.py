@@ -126,3 +126,31 @@ def test_no_alloc_misfit_and_network_buffers_are_size_checked(tt):
         tt.tt_net_features(ctx, (_f(*shape),) * 3, np.zeros((2, 3)), _f(N * 6))
     with pytest.raises(ValueError, match="CUDA"):
         tt.tt_net_set_weights(ctx, _f(n_par))
+
+
+def test_common_receiver_table_is_packed_by_the_library(tt):
+    """tt_cr_pack (host side, no GPU): every unordered pair of Eq. 4 appears under both of its
+    sources at its receiver, with dT_obs and -dT_obs, in the order the header states."""
+    rng = np.random.default_rng(7)
+    ns, nr = 5, 4
+    rows = []
+    for _ in range(23):
+        b, j = rng.choice(ns, 2, replace=False)
+        rows.append((b, j, rng.integers(nr), rng.normal(), rng.uniform(0.5, 2.0)))
+    rows.append(rows[3][:3] + (0.25, 1.0))            # a repeated pair keeps its own entry
+    off, other, dtobs, w = tt.cr_pack(ns, nr, rows)
+    assert off.dtype == np.int32 and other.dtype == np.int32 and off[-1] == 2 * len(rows)
+    for b in range(ns):
+        for m in range(nr):
+            want = [(j, dt, ww) for (bb, j, mm, dt, ww) in rows if bb == b and mm == m]
+            want += [(bb, -dt, ww) for (bb, j, mm, dt, ww) in rows if j == b and mm == m]
+            q0, q1 = off[b * nr + m], off[b * nr + m + 1]
+            got = list(zip(other[q0:q1], dtobs[q0:q1], w[q0:q1]))
+            assert [(int(g[0]), g[1], g[2]) for g in got] == [(int(a), c, d) for a, c, d in want]
+    # refusals: a source out of range, b == j, a receiver out of range, a fractional index
+    for bad in [(5, 0, 0, 0.1, 1.0), (2, 2, 0, 0.1, 1.0), (0, 1, 4, 0.1, 1.0),
+                (0.5, 1, 0, 0.1, 1.0), (0, -1, 0, 0.1, 1.0)]:
+        with pytest.raises(tt.TTError):
+            tt.cr_pack(ns, nr, rows[:2] + [bad])
+    off, other, dtobs, w = tt.cr_pack(ns, nr, [])
+    assert len(other) == 0 and not off.any()
