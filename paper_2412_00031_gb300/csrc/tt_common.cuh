@@ -422,7 +422,8 @@ __device__ __forceinline__ F godunov_aniso_core(F invT0, F ur, F ut, F up, F tc,
 // Grid-wide barrier for persistent cooperative launches. Arrivals go to a monotonic
 // per-launch counter: barrier number m of a launch is complete once m * nblocks arrivals
 // have been counted, so a barrier costs one acquire-release fence, one fire-and-forget
-// atomic and the polling of one L2 line. Every wait is bounded by a deadline on the global nanosecond timer; on expiry
+// atomic and the polling of one L2 line (the status word, on the same line, is read with
+// the first poll). Every wait is bounded by a deadline on the global nanosecond timer; on expiry
 // the status word gets kDevTimeout and the caller returns. All blocks eventually leave: a
 // block that gave up never arrives again, so the others' waits expire too. The status word
 // is sticky, so later launches of the same solve stop at their first barrier.
@@ -482,10 +483,15 @@ __device__ __forceinline__ bool grid_barrier(BarrierState *bs, unsigned long lon
         // blocks' fences, and __syncthreads passes the ordering on to the whole block
         fence_acq_rel_gpu();
         red_relaxed_add(&bs->arrived, 1ull);
+        // another block's timeout, read together with the first poll rather than after the
+        // wait, so that it adds no round trip to the barrier (a timeout during this wait is
+        // then seen at the next barrier, which the block that timed out never reaches)
+        const int st0 = ld_status(&bs->status);
         if (ld_acquire(&bs->arrived) < target) {
+            if (st0 != 0) good = 0;  // a block gave up earlier: no one waits for it
             const unsigned long long t0 = global_ns();
             unsigned int ns = 16;
-            while (ld_acquire(&bs->arrived) < target) {
+            while (good && ld_acquire(&bs->arrived) < target) {
                 if (global_ns() - t0 > limit_ns) {
                     atomicExch(&bs->status, (int)kDevTimeout);
                     good = 0;
@@ -495,7 +501,7 @@ __device__ __forceinline__ bool grid_barrier(BarrierState *bs, unsigned long lon
                 if (ns < 64) ns <<= 1;
             }
         }
-        if (good && ld_status(&bs->status) != 0) good = 0;
+        if (good && st0 != 0) good = 0;
         ok = good;
     }
     __syncthreads();

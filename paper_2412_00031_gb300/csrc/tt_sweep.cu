@@ -207,9 +207,9 @@ template <typename F> __global__ void refill_setup_kernel(FwdArgs<F> a) {
 // slot + slots, ... The schedule is static, so the index of a thread's next node, the
 // bounds of the next hyperplane and the index of its first node there are read one step
 // ahead (the latter two before the barrier), off the critical path. The node record (8
-// values shared by the warp) is loaded by lanes 0-7 in one 32-byte transaction and
-// broadcast by shuffles. The factor cache is read once per sweep and streamed past L2
-// (evict-first), so that it does not push out the tau lines the next hyperplane reads.
+// values shared by the warp) is read by every lane as two broadcast 16-byte loads. The
+// factor cache is read once per sweep and streamed past L2 (evict-first), so that it does
+// not push out the tau lines the next hyperplane reads.
 #ifndef TTGB_FWD_MIN_BLOCKS
 #define TTGB_FWD_MIN_BLOCKS 4
 #endif
@@ -227,16 +227,22 @@ __device__ __forceinline__ I node_local(unsigned pk, I sa, I sb, I sc) {
     return (I)aa * sa + (I)bb * sb + (I)cc * sc;
 }
 
-template <typename F> __device__ __forceinline__ NodeRec<F> rec_from_lanes(F v) {
-    NodeRec<F> R;
-    R.s = __shfl_sync(0xffffffffu, v, 0);
-    R.xi = __shfl_sync(0xffffffffu, v, 1);
-    R.eta = __shfl_sync(0xffffffffu, v, 2);
-    R.ct = __shfl_sync(0xffffffffu, v, 3);
-    R.cp = __shfl_sync(0xffffffffu, v, 4);
-    R.invW = __shfl_sync(0xffffffffu, v, 5);
-    R.et = __shfl_sync(0xffffffffu, v, 6);
-    R.ep = __shfl_sync(0xffffffffu, v, 7);
+// The node record read by every lane as broadcast vector loads (one 16-byte request per
+// half, served to the whole warp).
+__device__ __forceinline__ NodeRec<float> rec_vec(const NodeRec<float> *r) {
+    const float4 a = __ldg(reinterpret_cast<const float4 *>(r));
+    const float4 b = __ldg(reinterpret_cast<const float4 *>(r) + 1);
+    NodeRec<float> R;
+    R.s = a.x; R.xi = a.y; R.eta = a.z; R.ct = a.w;
+    R.cp = b.x; R.invW = b.y; R.et = b.z; R.ep = b.w;
+    return R;
+}
+__device__ __forceinline__ NodeRec<double> rec_vec(const NodeRec<double> *r) {
+    const double2 *q = reinterpret_cast<const double2 *>(r);
+    const double2 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2), d = __ldg(q + 3);
+    NodeRec<double> R;
+    R.s = a.x; R.xi = a.y; R.eta = b.x; R.ct = b.y;
+    R.cp = c.x; R.invW = c.y; R.et = d.x; R.ep = d.y;
     return R;
 }
 
@@ -302,8 +308,8 @@ __global__ void __launch_bounds__(256, (SCHEME == 0 || SCHEME == 3) ? TTGB_FWD_M
     for (int h = 0; h < NS; ++h) okh[h] = lane_ok && l0 + 32 * h < Bg;
     const int b = src0 + (okh[0] ? l0 : 0);             // the lane's sources: b + 32 h
     const I sp = (I)B, st = (I)g.np * (I)B, sr = (I)g.nt * (I)g.np * (I)B;
+    const long long osr = (long long)sr, ost = (long long)st, osp = (long long)sp;  // signed
     const I snode_r = (I)g.nt * (I)g.np, snode_t = (I)g.np;
-    const F *recf = reinterpret_cast<const F *>(a.rec);
     const Vec4<F> *t0c = a.t0c + (b - a.src_lo);
     const I src_n = (I)a.src_n;
     F *tau = a.tau;
@@ -348,24 +354,23 @@ __global__ void __launch_bounds__(256, (SCHEME == 0 || SCHEME == 3) ? TTGB_FWD_M
                         const I n = n0 + node_local(pk, sa, sb, sc);
                         F *p = tau + (n * (I)B + (I)b);
                         const Vec4<F> *pc = t0c + n * src_n;
-                        F v[NS][7], rv = 0;
+                        F v[NS][7];
                         Vec4<F> c[NS];
 #pragma unroll
                         for (int h = 0; h < NS; ++h) {
                             if (!act[h]) continue;
                             const F *ph = p + 32 * h;
                             v[h][0] = ph[0];
-                            v[h][1] = ph[sr];
-                            v[h][2] = *(ph - sr);
-                            v[h][3] = ph[st];
-                            v[h][4] = *(ph - st);
-                            v[h][5] = ph[sp];
-                            v[h][6] = *(ph - sp);
+                            v[h][1] = ph[osr];
+                            v[h][2] = ph[-osr];
+                            v[h][3] = ph[ost];
+                            v[h][4] = ph[-ost];
+                            v[h][5] = ph[osp];
+                            v[h][6] = ph[-osp];
                             c[h] = SCHEME == 3 ? Vec4<F>{(F)1, (F)0, (F)0, (F)0}
                                                : ld_stream(pc + 32 * h);
                         }
-                        if (lane < 8) rv = __ldg(recf + n * (I)8 + (I)lane);
-                        const NodeRec<F> R = rec_from_lanes<F>(rv);  // uniform loop: whole warp
+                        const NodeRec<F> R = rec_vec(a.rec + n);
 #pragma unroll
                         for (int h = 0; h < NS; ++h)
                             if (act[h])
