@@ -258,6 +258,11 @@ __device__ __forceinline__ Vec4<double> ld_stream(const Vec4<double> *p) {
 
 // Lax-Friedrichs update of one (node, source): tau at p, its six neighbours at p +- sr,
 // p +- st, p +- sp; c = the cached factors. Returns |change| (0 on the fixed set).
+__device__ __forceinline__ unsigned bits_of(float x) { return __float_as_uint(x); }
+__device__ __forceinline__ unsigned long long bits_of(double x) {
+    return (unsigned long long)__double_as_longlong(x);
+}
+
 template <typename F, int SCHEME>
 __device__ __forceinline__ F update_one(F *p, const F *v, const Vec4<F> &c, const NodeRec<F> &R,
                                         F er) {
@@ -266,7 +271,9 @@ __device__ __forceinline__ F update_one(F *p, const F *v, const Vec4<F> &c, cons
         SCHEME == 2   ? godunov_aniso_core<F>(c.x, c.y, c.z, c.w, v[0], v[1], v[2], v[3], v[4], v[5], v[6], R, er)
         : SCHEME == 1 ? godunov_core<F>(c.x, c.y, c.z, c.w, v[0], v[1], v[2], v[3], v[4], v[5], v[6], R, er)
                       : lf_core<F>(c.x, c.y, c.z, c.w, v[0], v[1], v[2], v[3], v[4], v[5], v[6], R, er);
-    *p = tn;
+    // a value that keeps its bits is not stored, so that its line is not made dirty (late
+    // in a solve most values have stopped changing)
+    if (bits_of(tn) != bits_of(v[0])) *p = tn;
     return fabs(tn - v[0]);
 }
 
