@@ -15,10 +15,11 @@ Events move along the normalised gradient (tt_reloc_update). Step-size control f
 model loop: a step that raises chi is undone and both step sizes are halved.
 
 Every step of the arithmetic runs in the library's kernels. This module sequences the calls
-and holds the buffers; it reads back chi (n_src x 2, and the common-receiver shares).
+and holds the buffers; it reads back one double per evaluation, the total misfit that
+tt_misfit_total sums on the device.
 """
 from . import (default_opts, tt_field_at_points, tt_forward, tt_misfit_cr, tt_misfit_table,
-               tt_reloc_kernels, tt_reloc_update)
+               tt_misfit_total, tt_reloc_kernels, tt_reloc_update)
 
 
 class Relocation:
@@ -56,11 +57,10 @@ class Relocation:
         if self.cr is not None:
             tt_misfit_cr(c, self.cr, self.Tr, self.chi_cr, self.R)
         tt_reloc_kernels(c, self.R, self.grad, self.Kx, self.Kt)
-        chi = self.chi.cpu().numpy()
-        total = self.data.alpha * chi[:, 0].sum() + self.data.beta * chi[:, 1].sum()
-        if self.cr is not None:
-            total += self.cr.gamma * self.chi_cr.cpu().numpy().sum()
-        return float(total)
+        # the step control's total misfit, an FP64 sum on the device
+        return tt_misfit_total(c, self.chi, self.data.alpha, self.data.beta,
+                               self.chi_cr if self.cr is not None else None,
+                               self.cr.gamma if self.cr is not None else 0.0)
 
     def run(self, n_iter, step_km, step_s=0.0):
         """n_iter step attempts; returns the history [(chi, step_km, accepted)], first entry
