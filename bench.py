@@ -344,9 +344,9 @@ def gpu_arm(args, rank, world):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": dict(workload_config(w, world),
-                       step="one captured CUDA graph per step (tt_plan)" if args.plan
-                       else "four C-ABI calls per step"),
+        "config": workload_config(w, world),
+        "step_form": ("one captured CUDA graph per step (tt_plan)" if args.plan
+                      else "four C-ABI calls per step"),
         "roofline": {"bound": "hbm", "kernel": "fwd_sweep_kernel<float>", "achieved": f_gbs,
                      "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s", "frac": f_gbs / hbm,
                      "traffic": traffic, "algorithmic_bytes_per_launch": f_bytes,
